@@ -1,0 +1,569 @@
+// Plain FP64 CPU oracle for the frozen Gaussian approximation (FGA) of
+// Yang, Lu and Fomel, "Seismic modeling using the frozen Gaussian approximation".
+//
+// TEST INFRASTRUCTURE ONLY. Nothing in the product path may load or call this
+// file: only the tests, the smoke check and the benchmark's CPU-baseline leg do.
+// It shares no code, header, table or helper with the CUDA implementation.
+//
+// What is here (the FBI step itself lives in fga_oracle.py, where the paper's
+// "FFT on the small box" is a library call):
+//   * the velocity medium: tensor-product cubic B-spline with analytic
+//     derivatives up to third order (the paper does not say how c is
+//     interpolated; the cubic B-spline is the reading chosen because the
+//     dynamic ray equations need second derivatives of c);
+//   * the Hamiltonian H = sigma c(Q)|P| (Eq. hamiltonian) and its first and
+//     second derivatives, written out from their definitions;
+//   * the ray equations (Eq. characline), the dynamic ray equations (Eqs. dzQ,
+//     dzP), the amplitude equation (Eq. a_formu with Z from Eq. op_zZ) and the
+//     action S, integrated with classical fourth-order Runge-Kutta (Numerical
+//     test section);
+//   * the reconstruction sum (Eq. recons), evaluated term by term with
+//     std::exp of the full complex exponent;
+//   * a brute-force FBI direct sum (Eq. psi) used only to pin the FFT route.
+//
+// Every routine is FP64, per Gaussian or per output point, with OpenMP only
+// over independent Gaussians / output points (each result is summed in the
+// same order whatever the thread count).
+
+#include <cmath>
+#include <complex>
+#include <cstdint>
+#include <cstring>
+#include <vector>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+typedef std::complex<double> cplx;
+static const double kPi = 3.14159265358979323846;
+
+namespace {
+
+struct Grid {
+  int dim;
+  int64_t n[3];
+  double h[3], o[3];
+  int periodic[3];
+};
+
+Grid make_grid(int dim, const int64_t* n, const double* h, const double* o, const int* periodic) {
+  Grid g;
+  g.dim = dim;
+  for (int k = 0; k < 3; ++k) {
+    g.n[k] = k < dim ? n[k] : 1;
+    g.h[k] = k < dim ? h[k] : 1.0;
+    g.o[k] = k < dim ? o[k] : 0.0;
+    g.periodic[k] = k < dim ? periodic[k] : 0;
+  }
+  return g;
+}
+
+// ---------------------------------------------------------------------------
+// Cubic B-spline beta_3 and its derivatives (order 0..3), piecewise by |t|.
+// ---------------------------------------------------------------------------
+double beta3(double t, int order) {
+  double at = std::fabs(t);
+  double sg = t < 0 ? -1.0 : 1.0;
+  if (at >= 2.0) return 0.0;
+  if (at < 1.0) {
+    switch (order) {
+      case 0: return 2.0 / 3.0 - t * t + 0.5 * at * at * at;
+      case 1: return -2.0 * t + 1.5 * t * at;
+      case 2: return -2.0 + 3.0 * at;
+      default: return 3.0 * sg;
+    }
+  }
+  double u = 2.0 - at;
+  switch (order) {
+    case 0: return u * u * u / 6.0;
+    case 1: return -sg * u * u / 2.0;
+    case 2: return u;
+    default: return -sg;
+  }
+}
+
+// Coefficient index along one axis: clamped on open axes, wrapped on periodic ones.
+int64_t coef_index(const Grid& g, int k, int64_t i) {
+  int64_t n = g.n[k];
+  if (g.periodic[k]) {
+    int64_t r = i % n;
+    return r < 0 ? r + n : r;
+  }
+  if (i < 0) return 0;
+  if (i > n - 1) return n - 1;
+  return i;
+}
+
+// c(x) = sum_i C_i prod_k beta3((x_k - o_k)/h_k - i_k), and its derivatives.
+// deriv[k] is the derivative order taken along axis k.
+double spline_value(const Grid& g, const double* C, const double* x, const int* deriv) {
+  int64_t base[3];
+  double u[3];
+  for (int k = 0; k < g.dim; ++k) {
+    u[k] = (x[k] - g.o[k]) / g.h[k];
+    base[k] = (int64_t)std::floor(u[k]) - 1;
+  }
+  double total = 0.0;
+  int ntaps = 1;
+  for (int k = 0; k < g.dim; ++k) ntaps *= 4;
+  for (int t = 0; t < ntaps; ++t) {
+    int rem = t;
+    int64_t flat = 0;
+    double w = 1.0;
+    for (int k = 0; k < g.dim; ++k) {
+      int tk = rem % 4;
+      rem /= 4;
+      int64_t i = base[k] + tk;
+      w *= beta3(u[k] - (double)i, deriv[k]) / std::pow(g.h[k], deriv[k]);
+      flat = flat * g.n[k] + coef_index(g, k, i);
+    }
+    total += C[flat] * w;
+  }
+  return total;
+}
+
+struct Medium {
+  double c;
+  double grad[3];
+  double hess[3][3];
+};
+
+Medium medium_at(const Grid& g, const double* C, const double* x) {
+  Medium m;
+  int d0[3] = {0, 0, 0};
+  m.c = spline_value(g, C, x, d0);
+  for (int k = 0; k < g.dim; ++k) {
+    int d1[3] = {0, 0, 0};
+    d1[k] = 1;
+    m.grad[k] = spline_value(g, C, x, d1);
+    for (int l = 0; l < g.dim; ++l) {
+      int d2[3] = {0, 0, 0};
+      d2[k] += 1;
+      d2[l] += 1;
+      m.hess[k][l] = spline_value(g, C, x, d2);
+    }
+  }
+  return m;
+}
+
+// ---------------------------------------------------------------------------
+// Hamiltonian H = sigma c(Q) |P| (Eq. hamiltonian) and its derivatives.
+// ---------------------------------------------------------------------------
+struct HamDerivs {
+  double H;
+  double dHdQ[3], dHdP[3];
+  double HQQ[3][3], HQP[3][3], HPP[3][3], HPQ[3][3];  // HQP[l][k] = d2H/dQ_l dP_k
+};
+
+HamDerivs hamiltonian(const Grid& g, const double* C, int sigma, const double* Q, const double* P) {
+  HamDerivs r;
+  int d = g.dim;
+  Medium m = medium_at(g, C, Q);
+  double pn = 0.0;
+  for (int k = 0; k < d; ++k) pn += P[k] * P[k];
+  pn = std::sqrt(pn);
+  double nh[3];
+  for (int k = 0; k < d; ++k) nh[k] = P[k] / pn;
+  double s = (double)sigma;
+  r.H = s * m.c * pn;
+  for (int k = 0; k < d; ++k) {
+    r.dHdQ[k] = s * pn * m.grad[k];
+    r.dHdP[k] = s * m.c * nh[k];
+  }
+  for (int l = 0; l < d; ++l)
+    for (int k = 0; k < d; ++k) {
+      r.HQQ[l][k] = s * pn * m.hess[l][k];
+      r.HQP[l][k] = s * m.grad[l] * nh[k];
+      r.HPQ[l][k] = s * nh[l] * m.grad[k];
+      r.HPP[l][k] = s * m.c * ((l == k ? 1.0 : 0.0) - nh[l] * nh[k]) / pn;
+    }
+  return r;
+}
+
+// ---------------------------------------------------------------------------
+// Per-Gaussian state and the right-hand side of the FGA ODE system.
+// A = d_z Q and B = d_z P with (j,k) entry d_{z_j} Q_k (resp. P_k).
+// ---------------------------------------------------------------------------
+struct State {
+  double Q[3], P[3];
+  cplx A[3][3], B[3][3];
+  cplx a;
+  double S;
+};
+
+void state_zero(State& s) {
+  std::memset(&s, 0, sizeof(State));
+}
+
+// out = y + h * k
+void state_axpy(int d, const State& y, double h, const State& k, State& out) {
+  for (int i = 0; i < d; ++i) {
+    out.Q[i] = y.Q[i] + h * k.Q[i];
+    out.P[i] = y.P[i] + h * k.P[i];
+    for (int j = 0; j < d; ++j) {
+      out.A[i][j] = y.A[i][j] + h * k.A[i][j];
+      out.B[i][j] = y.B[i][j] + h * k.B[i][j];
+    }
+  }
+  out.a = y.a + h * k.a;
+  out.S = y.S + h * k.S;
+}
+
+// tr(Z^{-1} W) by solving Z X = W with Gaussian elimination (partial pivoting).
+cplx trace_solve(int d, const cplx Zin[3][3], const cplx Win[3][3]) {
+  cplx Z[3][3], W[3][3];
+  for (int i = 0; i < d; ++i)
+    for (int j = 0; j < d; ++j) {
+      Z[i][j] = Zin[i][j];
+      W[i][j] = Win[i][j];
+    }
+  for (int col = 0; col < d; ++col) {
+    int piv = col;
+    for (int r = col + 1; r < d; ++r)
+      if (std::abs(Z[r][col]) > std::abs(Z[piv][col])) piv = r;
+    if (piv != col)
+      for (int j = 0; j < d; ++j) {
+        std::swap(Z[col][j], Z[piv][j]);
+        std::swap(W[col][j], W[piv][j]);
+      }
+    for (int r = col + 1; r < d; ++r) {
+      cplx f = Z[r][col] / Z[col][col];
+      for (int j = 0; j < d; ++j) {
+        Z[r][j] -= f * Z[col][j];
+        W[r][j] -= f * W[col][j];
+      }
+    }
+  }
+  cplx X[3][3];
+  for (int j = 0; j < d; ++j)
+    for (int r = d - 1; r >= 0; --r) {
+      cplx acc = W[r][j];
+      for (int c = r + 1; c < d; ++c) acc -= Z[r][c] * X[c][j];
+      X[r][j] = acc / Z[r][r];
+    }
+  cplx tr = 0.0;
+  for (int i = 0; i < d; ++i) tr += X[i][i];
+  return tr;
+}
+
+void rhs(const Grid& g, const double* C, int sigma, const State& y, State& dy) {
+  int d = g.dim;
+  state_zero(dy);
+  HamDerivs hd = hamiltonian(g, C, sigma, y.Q, y.P);
+  // Eq. characline
+  for (int k = 0; k < d; ++k) {
+    dy.Q[k] = hd.dHdP[k];
+    dy.P[k] = -hd.dHdQ[k];
+  }
+  // Eqs. dzQ, dzP (componentwise form, summation over l)
+  for (int j = 0; j < d; ++j)
+    for (int k = 0; k < d; ++k) {
+      cplx dA = 0.0, dB = 0.0;
+      for (int l = 0; l < d; ++l) {
+        dA += y.A[j][l] * hd.HQP[l][k] + y.B[j][l] * hd.HPP[l][k];
+        dB += -y.A[j][l] * hd.HQQ[l][k] - y.B[j][l] * hd.HPQ[l][k];
+      }
+      dy.A[j][k] = dA;
+      dy.B[j][k] = dB;
+    }
+  // Eq. a_formu with Z = d_z(Q + iP) = A + iB (Eq. op_zZ)
+  const cplx I(0.0, 1.0);
+  cplx Z[3][3], dZ[3][3];
+  for (int j = 0; j < d; ++j)
+    for (int k = 0; k < d; ++k) {
+      Z[j][k] = y.A[j][k] + I * y.B[j][k];
+      dZ[j][k] = dy.A[j][k] + I * dy.B[j][k];
+    }
+  double dot = 0.0;
+  for (int k = 0; k < d; ++k) dot += hd.dHdP[k] * hd.dHdQ[k];
+  dy.a = y.a * (dot / hd.H) + 0.5 * y.a * trace_solve(d, Z, dZ);
+  // action: dS/dt = P . dQ/dt - H
+  double pq = 0.0;
+  for (int k = 0; k < d; ++k) pq += y.P[k] * dy.Q[k];
+  dy.S = pq - hd.H;
+}
+
+void wrap_periodic(const Grid& g, State& y) {
+  for (int k = 0; k < g.dim; ++k) {
+    if (!g.periodic[k]) continue;
+    double L = g.n[k] * g.h[k];
+    double r = std::fmod(y.Q[k] - g.o[k], L);
+    if (r < 0) r += L;
+    y.Q[k] = g.o[k] + r;
+  }
+}
+
+void rk4_step(const Grid& g, const double* C, int sigma, State& y, double dt) {
+  int d = g.dim;
+  State k1, k2, k3, k4, tmp;
+  state_zero(tmp);
+  rhs(g, C, sigma, y, k1);
+  state_axpy(d, y, 0.5 * dt, k1, tmp);
+  rhs(g, C, sigma, tmp, k2);
+  state_axpy(d, y, 0.5 * dt, k2, tmp);
+  rhs(g, C, sigma, tmp, k3);
+  state_axpy(d, y, dt, k3, tmp);
+  rhs(g, C, sigma, tmp, k4);
+  State out = y;
+  for (int i = 0; i < d; ++i) {
+    out.Q[i] = y.Q[i] + dt / 6.0 * (k1.Q[i] + 2.0 * k2.Q[i] + 2.0 * k3.Q[i] + k4.Q[i]);
+    out.P[i] = y.P[i] + dt / 6.0 * (k1.P[i] + 2.0 * k2.P[i] + 2.0 * k3.P[i] + k4.P[i]);
+    for (int j = 0; j < d; ++j) {
+      out.A[i][j] = y.A[i][j] + dt / 6.0 * (k1.A[i][j] + 2.0 * k2.A[i][j] + 2.0 * k3.A[i][j] + k4.A[i][j]);
+      out.B[i][j] = y.B[i][j] + dt / 6.0 * (k1.B[i][j] + 2.0 * k2.B[i][j] + 2.0 * k3.B[i][j] + k4.B[i][j]);
+    }
+  }
+  out.a = y.a + dt / 6.0 * (k1.a + 2.0 * k2.a + 2.0 * k3.a + k4.a);
+  out.S = y.S + dt / 6.0 * (k1.S + 2.0 * k2.S + 2.0 * k3.S + k4.S);
+  wrap_periodic(g, out);
+  y = out;
+}
+
+void set_threads(int nthreads) {
+#ifdef _OPENMP
+  if (nthreads > 0) omp_set_num_threads(nthreads);
+#else
+  (void)nthreads;
+#endif
+}
+
+}  // namespace
+
+extern "C" {
+
+int orc_num_threads_available(void) {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}
+
+// c, grad c, Hessian of c and third derivatives at npts points x[npts][dim].
+// Any of grad/hess/d3 may be NULL.
+int orc_medium_eval(int dim, const int64_t* n, const double* h, const double* o, const int* periodic,
+                    const double* C, int64_t npts, const double* x, double* c, double* grad,
+                    double* hess, double* d3) {
+  if (dim < 1 || dim > 3) return 1;
+  Grid g = make_grid(dim, n, h, o, periodic);
+  for (int64_t ip = 0; ip < npts; ++ip) {
+    const double* xp = x + ip * dim;
+    int d0[3] = {0, 0, 0};
+    c[ip] = spline_value(g, C, xp, d0);
+    for (int k = 0; k < dim; ++k) {
+      if (grad) {
+        int d1[3] = {0, 0, 0};
+        d1[k] = 1;
+        grad[ip * dim + k] = spline_value(g, C, xp, d1);
+      }
+      for (int l = 0; l < dim; ++l) {
+        if (hess) {
+          int d2[3] = {0, 0, 0};
+          d2[k] += 1;
+          d2[l] += 1;
+          hess[(ip * dim + k) * dim + l] = spline_value(g, C, xp, d2);
+        }
+        if (d3)
+          for (int m = 0; m < dim; ++m) {
+            int dd[3] = {0, 0, 0};
+            dd[k] += 1;
+            dd[l] += 1;
+            dd[m] += 1;
+            d3[((ip * dim + k) * dim + l) * dim + m] = spline_value(g, C, xp, dd);
+          }
+      }
+    }
+  }
+  return 0;
+}
+
+// H and its derivatives at one phase-space point (used by the tests to check
+// the written-out derivatives against finite differences of H itself).
+// out layout: H, dHdQ[d], dHdP[d], HQQ[d*d], HQP[d*d], HPP[d*d], HPQ[d*d].
+int orc_hamiltonian(int dim, const int64_t* n, const double* h, const double* o, const int* periodic,
+                    const double* C, int sigma, const double* Q, const double* P, double* out) {
+  if (dim < 1 || dim > 3) return 1;
+  Grid g = make_grid(dim, n, h, o, periodic);
+  HamDerivs r = hamiltonian(g, C, sigma, Q, P);
+  int d = dim, at = 0;
+  out[at++] = r.H;
+  for (int k = 0; k < d; ++k) out[at++] = r.dHdQ[k];
+  for (int k = 0; k < d; ++k) out[at++] = r.dHdP[k];
+  for (int l = 0; l < d; ++l)
+    for (int k = 0; k < d; ++k) out[at++] = r.HQQ[l][k];
+  for (int l = 0; l < d; ++l)
+    for (int k = 0; k < d; ++k) out[at++] = r.HQP[l][k];
+  for (int l = 0; l < d; ++l)
+    for (int k = 0; k < d; ++k) out[at++] = r.HPP[l][k];
+  for (int l = 0; l < d; ++l)
+    for (int k = 0; k < d; ++k) out[at++] = r.HPQ[l][k];
+  return 0;
+}
+
+// Integrate nG Gaussians from t = 0 to t = nsteps*dt with RK4.
+// Initial values: Q = q, P = p, A = I, B = -iI, a = 2^{d/2}, S = 0.
+// Outputs (all [nG]-major): Q,P [nG][d]; A,B [nG][d][d][2] (re,im);
+// a [nG][2]; S [nG]. |P| = 0 is rejected (returns 2).
+int orc_propagate(int dim, const int64_t* n, const double* h, const double* o, const int* periodic,
+                  const double* C, int64_t nsteps, double dt, int64_t nG, const int* sigma,
+                  const double* q, const double* p, double* Qout, double* Pout, double* Aout,
+                  double* Bout, double* aout, double* Sout, int nthreads) {
+  if (dim < 1 || dim > 3) return 1;
+  Grid g = make_grid(dim, n, h, o, periodic);
+  int d = dim;
+  for (int64_t i = 0; i < nG; ++i) {
+    double pn = 0.0;
+    for (int k = 0; k < d; ++k) pn += p[i * d + k] * p[i * d + k];
+    if (!(pn > 0.0)) return 2;
+  }
+  set_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 16)
+  for (int64_t i = 0; i < nG; ++i) {
+    State y;
+    state_zero(y);
+    for (int k = 0; k < d; ++k) {
+      y.Q[k] = q[i * d + k];
+      y.P[k] = p[i * d + k];
+      y.A[k][k] = cplx(1.0, 0.0);
+      y.B[k][k] = cplx(0.0, -1.0);
+    }
+    y.a = cplx(std::pow(2.0, 0.5 * d), 0.0);
+    y.S = 0.0;
+    for (int64_t s = 0; s < nsteps; ++s) rk4_step(g, C, sigma[i], y, dt);
+    for (int k = 0; k < d; ++k) {
+      Qout[i * d + k] = y.Q[k];
+      Pout[i * d + k] = y.P[k];
+      for (int l = 0; l < d; ++l) {
+        Aout[((i * d + k) * d + l) * 2 + 0] = y.A[k][l].real();
+        Aout[((i * d + k) * d + l) * 2 + 1] = y.A[k][l].imag();
+        Bout[((i * d + k) * d + l) * 2 + 0] = y.B[k][l].real();
+        Bout[((i * d + k) * d + l) * 2 + 1] = y.B[k][l].imag();
+      }
+    }
+    aout[2 * i + 0] = y.a.real();
+    aout[2 * i + 1] = y.a.imag();
+    Sout[i] = y.S;
+  }
+  return 0;
+}
+
+// Reconstruction sum (Eq. recons) at npts points x[npts][dim]:
+//   u(x) = sum_g W a_g psi_g (2 pi eps)^{-3d/2} e^{i S_g/eps}
+//            e^{ i P_g.(x-Q_g)/eps - |x-Q_g|^2/(2 eps) }
+// restricted to the square window |x_k - Q_k| <= kappa sqrt(eps) on every
+// axis; on periodic axes (period L[k] > 0) every image x - Q + l L with
+// |l| <= 2 inside the window contributes. Gaussians of both branches are
+// passed together (the branch only mattered for the rays).
+// a, psi: [nG][2] (re,im). Output ure, uim: [npts].
+int orc_reconstruct(int dim, const double* L, double eps, double kappa, double W, int64_t nG,
+                    const double* Q, const double* P, const double* a, const double* psi,
+                    const double* S, int64_t npts, const double* x, double* ure, double* uim,
+                    int nthreads) {
+  if (dim < 1 || dim > 3) return 1;
+  int d = dim;
+  double cut = kappa * std::sqrt(eps);
+  double norm = std::pow(2.0 * kPi * eps, -1.5 * d);
+  const cplx I(0.0, 1.0);
+  set_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 64)
+  for (int64_t ip = 0; ip < npts; ++ip) {
+    const double* xp = x + ip * d;
+    cplx u = 0.0;
+    for (int64_t gi = 0; gi < nG; ++gi) {
+      // images inside the window, per axis
+      double img[3][5];
+      int nimg[3];
+      bool any = true;
+      for (int k = 0; k < d; ++k) {
+        nimg[k] = 0;
+        double d0 = xp[k] - Q[gi * d + k];
+        if (L[k] > 0.0) {
+          for (int l = -2; l <= 2; ++l) {
+            double dk = d0 + l * L[k];
+            if (std::fabs(dk) <= cut) img[k][nimg[k]++] = dk;
+          }
+        } else if (std::fabs(d0) <= cut) {
+          img[k][nimg[k]++] = d0;
+        }
+        if (nimg[k] == 0) any = false;
+      }
+      if (!any) continue;
+      cplx sum = 0.0;
+      int combos = 1;
+      for (int k = 0; k < d; ++k) combos *= nimg[k];
+      for (int cidx = 0; cidx < combos; ++cidx) {
+        int rem = cidx;
+        double phase = 0.0, r2 = 0.0;
+        for (int k = 0; k < d; ++k) {
+          double dk = img[k][rem % nimg[k]];
+          rem /= nimg[k];
+          phase += P[gi * d + k] * dk;
+          r2 += dk * dk;
+        }
+        sum += std::exp(I * phase / eps - r2 / (2.0 * eps));
+      }
+      cplx ag(a[2 * gi], a[2 * gi + 1]);
+      cplx pg(psi[2 * gi], psi[2 * gi + 1]);
+      u += W * ag * pg * norm * std::exp(I * S[gi] / eps) * sum;
+    }
+    ure[ip] = u.real();
+    uim[ip] = u.imag();
+  }
+  return 0;
+}
+
+// Brute-force FBI (Eq. psi discretised on the box): for each requested
+// (q, p) pair,
+//   psi(q,p) = prod_k h_k * sum_{j in box} f(q + r_j) w(r_j) e^{-i p.r_j/eps},
+// r_{j,k} = (j_k - nb_k/2) h_k, w = prod_k w_k, w_k(r) = e^{-r^2/(2 eps)} on open
+// axes and sum_{|l|<=2} e^{-(r + l L_k)^2/(2 eps)} on periodic ones; samples
+// outside an open axis are zero, periodic ones wrap. q is given by its
+// grid index qi[npairs][dim], p by its value pv[npairs][dim].
+int orc_fbi_direct(int dim, const int64_t* n, const double* h, const int* periodic,
+                   const double* f, double eps, const int64_t* nb, int64_t npairs,
+                   const int64_t* qi, const double* pv, double* out /*[npairs][2]*/) {
+  if (dim < 1 || dim > 3) return 1;
+  int d = dim;
+  const cplx I(0.0, 1.0);
+  for (int64_t ip = 0; ip < npairs; ++ip) {
+    int64_t total = 1;
+    for (int k = 0; k < d; ++k) total *= nb[k];
+    cplx acc = 0.0;
+    for (int64_t t = 0; t < total; ++t) {
+      int64_t rem = t;
+      int64_t jj[3];
+      for (int k = d - 1; k >= 0; --k) {
+        jj[k] = rem % nb[k];
+        rem /= nb[k];
+      }
+      bool inside = true;
+      int64_t flat = 0;
+      double w = 1.0, phase = 0.0;
+      for (int k = 0; k < d; ++k) {
+        double r = (double)(jj[k] - nb[k] / 2) * h[k];
+        int64_t i = qi[ip * d + k] + jj[k] - nb[k] / 2;
+        if (periodic[k]) {
+          i %= n[k];
+          if (i < 0) i += n[k];
+          double Lk = n[k] * h[k], wk = 0.0;
+          for (int l = -2; l <= 2; ++l) wk += std::exp(-(r + l * Lk) * (r + l * Lk) / (2.0 * eps));
+          w *= wk;
+        } else {
+          if (i < 0 || i >= n[k]) inside = false;
+          w *= std::exp(-r * r / (2.0 * eps));
+        }
+        flat = flat * n[k] + (inside ? i : 0);
+        phase += pv[ip * d + k] * r;
+      }
+      if (!inside) continue;
+      acc += f[flat] * w * std::exp(-I * phase / eps);
+    }
+    double hv = 1.0;
+    for (int k = 0; k < d; ++k) hv *= h[k];
+    out[2 * ip] = (hv * acc).real();
+    out[2 * ip + 1] = (hv * acc).imag();
+  }
+  return 0;
+}
+
+}  // extern "C"
