@@ -1,0 +1,169 @@
+/*
+ * fga.h -- C ABI of the GB300 (sm_103a) frozen Gaussian approximation library.
+ *
+ * The library computes the frozen Gaussian approximation (FGA) of the acoustic
+ * wave equation u_tt = c(x)^2 Laplace(u), u(0) = f0, u_t(0) = f1 (Theory
+ * section, Eqs. wave, f0, f1) in the three steps of the Algorithm section:
+ *   fga_decompose   -- FBI transform of f0, f1 (Eq. psi, Initial wavefield
+ *                      decomposition section), branch split and thresholding
+ *                      into the set of frozen Gaussians;
+ *   fga_propagate   -- RK4 on the ray equations (Eqs. hamiltonian,
+ *                      characline), the dynamic ray equations (Eqs. dzQ, dzP),
+ *                      the amplitude equation (Eq. a_formu, Z of Eq. op_zZ) and
+ *                      the action S, up to time T (Numerical test section: RK4);
+ *   fga_reconstruct -- the Gaussian sum of Eq. recons on the grid.
+ *
+ * Conventions
+ *   * Grids: x_i = origin + i*h per axis, arrays C-contiguous with the last axis
+ *     fastest. The velocity, the initial data and the output share one grid.
+ *   * Pointers marked "host or device" may point to either; the library asks
+ *     the CUDA driver which it is. Device pointers must be on the current
+ *     device. The caller owns every pointer it passes; the plan owns all the
+ *     device memory it allocates and frees it in fga_destroy.
+ *   * All work is issued on the plan's stream. fga_decompose synchronises that
+ *     stream once (it reads the Gaussian counts back to size later launches);
+ *     the other calls return before the device finishes, except when a host
+ *     output pointer is given, in which case they wait for the copy.
+ *   * Errors never abort or print: every call returns an fga_status and, on
+ *     failure, records a message retrievable with fga_last_error. After a
+ *     failure in a device-side step the plan is marked failed and every later
+ *     call except fga_destroy / fga_last_error returns FGA_ERR_STATE.
+ *   * A plan is not thread-safe; distinct plans are independent.
+ *   * Only the + branch is propagated: for real f0, f1 the - branch terms are
+ *     the complex conjugates of the + branch terms at -p (the p-grid is
+ *     symmetric), so u = 2 Re(sum over the + branch).
+ */
+#ifndef FGA_H
+#define FGA_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fga_plan_s* fga_plan_t;
+
+typedef enum {
+  FGA_OK = 0,
+  FGA_ERR_INVALID = 1,  /* bad argument or configuration */
+  FGA_ERR_OOM = 2,      /* a device allocation failed */
+  FGA_ERR_CUDA = 3,     /* a CUDA runtime call failed */
+  FGA_ERR_TIMEOUT = 4,  /* a bounded device-side wait gave up */
+  FGA_ERR_STATE = 5,    /* call out of order, or the plan failed earlier */
+  FGA_ERR_NUMERIC = 6,  /* a ray met |P| = 0, det Z = 0 or a non-finite value */
+  FGA_ERR_CAPACITY = 7  /* a fixed capacity of the plan was exceeded */
+} fga_status;
+
+typedef enum {
+  FGA_FP64 = 0,         /* every step in FP64 */
+  FGA_MIXED_TF32X2 = 1, /* reserved: split-TF32 contractions, FP32 accumulate */
+  FGA_MIXED_BF16X3 = 2  /* reserved: split-BF16 contractions, FP32 accumulate */
+} fga_precision;
+
+typedef struct {
+  int dim;            /* 1 or 2 */
+  int64_t n[3];       /* grid points per axis (>= 4) */
+  double h[3];        /* grid spacing per axis (> 0) */
+  double origin[3];   /* first grid point per axis */
+  int periodic[3];    /* 1: axis is periodic (box = one period, n % q_stride == 0) */
+  int nshots;         /* number of independent sets of initial data (>= 1) */
+  const double* eps;  /* host [nshots]: FGA width parameter eps > 0 (a length) */
+  const int* q_stride;/* host [nshots][dim] q-grid stride in grid points, or NULL:
+                         round(0.5 sqrt(eps)/h) (reduced to divide n on periodic axes) */
+  const int* box;     /* host [nshots][dim] FBI box points (even), or NULL:
+                         ceil(12 sqrt(eps)/h) rounded up to a multiple of 32; n on
+                         periodic axes (where any given value must equal n) */
+  double T;           /* final time >= 0 */
+  double dt;          /* RK4 step; T/dt must be an integer to within 1e-9 */
+  double kappa;       /* reconstruction window half-width in units of sqrt(eps) */
+  double tau;         /* relative threshold: keep |psi+| >= tau * max|psi+-| */
+  int precision;      /* fga_precision */
+} fga_config;
+
+/* Create a plan: validate cfg, copy the velocity (host or device, [n...] FP64,
+ * every value finite and > 0) to the device as the cubic B-spline coefficients
+ * of the medium c(x) = sum_i c_i prod_k beta3((x_k - origin_k)/h_k - i_k) (indices
+ * clamped on open axes, wrapped on periodic ones), and bind the CUDA stream
+ * (a cudaStream_t; NULL = the legacy default stream).
+ * Errors: FGA_ERR_INVALID (cfg, velocity <= 0 or NaN), FGA_ERR_OOM, FGA_ERR_CUDA. */
+fga_status fga_plan(const fga_config* cfg, const double* velocity, void* stream,
+                    fga_plan_t* out);
+
+/* Step 1 (Eq. psi and the Initial wavefield decomposition section). u0, u1:
+ * host or device, [nshots][n...] FP64. For every shot: the FBI transforms
+ *   psi_j(q,p) = prod_k h_k sum_{j in box} f_j(q + r_j) w(r_j) exp(-i p.r_j/eps)
+ * over the q-grid q = origin + s*m*h and the p-grid p = 2 pi eps m/(n_b h),
+ * m = -n_b/2+1 .. n_b/2-1 (p = 0 left out), w the Gaussian window
+ * exp(-|r|^2/(2 eps)) (periodised on periodic axes); the branch split
+ * psi+ = 1/2 (psi_0 + i eps psi_1/(c(q)|p|)); and the selection of every (q,p)
+ * with |psi+| >= tau * max|psi+|. counts_host (or NULL): host [nshots], the
+ * number of Gaussians kept per shot. Synchronises the plan's stream.
+ * Errors: FGA_ERR_INVALID (NULL data), FGA_ERR_OOM, FGA_ERR_CUDA, FGA_ERR_STATE. */
+fga_status fga_decompose(fga_plan_t plan, const double* u0, const double* u1,
+                         int64_t* counts_host);
+
+/* Step 2. Integrates every kept Gaussian from (Q,P) = (q,p), d_zQ = I,
+ * d_zP = -iI, a = 2^{d/2}, S = 0 to time T with T/dt classical RK4 steps.
+ * Errors: FGA_ERR_STATE (no decomposition yet), FGA_ERR_CUDA. A ray that meets
+ * |P| = 0, det Z = 0 or a non-finite value is reported as FGA_ERR_NUMERIC by
+ * the next call that synchronises (fga_reconstruct, fga_sync). */
+fga_status fga_propagate(fga_plan_t plan);
+
+/* Step 3 (Eq. recons). u_out: host or device, [nshots][n...] FP64, receives
+ *   u(x) = 2 Re sum_{g in G+} W a_g psi_g (2 pi eps)^{-3d/2} exp(i S_g/eps)
+ *            exp(i P_g.(x - Q_g)/eps - |x - Q_g|^2/(2 eps))
+ * with every term cut to the window |x_k - Q_k| <= kappa sqrt(eps) on each axis
+ * (all images on periodic axes) and W = prod_k (s_k h_k)(2 pi eps/(n_b,k h_k))
+ * the phase-space cell of one Gaussian. Errors: FGA_ERR_STATE (not propagated),
+ * FGA_ERR_INVALID, FGA_ERR_OOM, FGA_ERR_CUDA, FGA_ERR_NUMERIC. */
+fga_status fga_reconstruct(fga_plan_t plan, double* u_out);
+
+/* Waits for the plan's stream and reports any device-side error flag. */
+fga_status fga_sync(fga_plan_t plan);
+
+/* Frees everything the plan owns. NULL is accepted. */
+fga_status fga_destroy(fga_plan_t plan);
+
+const char* fga_status_string(fga_status s);
+/* Message of the last failure on this plan ("" if none); NULL plan: the last
+ * failure of fga_plan itself. The string lives until the next call. */
+const char* fga_last_error(fga_plan_t plan);
+
+/* ---- inspection (tests and diagnostics; each synchronises the stream) ---- */
+
+/* Number of kept Gaussians of a shot (-1 before fga_decompose). */
+int64_t fga_count(fga_plan_t plan, int shot);
+
+/* The q-grid, p-grid and FBI box sizes of a shot: nq[dim], np[dim], nb[dim],
+ * s[dim] (any may be NULL). np counts every p index j = m + n_b/2, j in [0, n_b). */
+fga_status fga_shot_grid(fga_plan_t plan, int shot, int64_t* nq, int64_t* np, int64_t* nb,
+                         int64_t* s);
+
+/* psi+ over the whole q-grid x p-grid of a shot, host [n_q][n_p][2] (re, im),
+ * p index j = m + n_b/2 in C order; zero outside the data's support and at the
+ * left-out p values. max_abs (or NULL): max |psi+| of the shot. */
+fga_status fga_psi(fga_plan_t plan, int shot, double* psi_host, double* max_abs);
+
+/* The kept Gaussians of a shot in their stored order: host arrays of length
+ * fga_count(shot): qidx (flat q-grid index), pidx (flat p-grid index), psi [2]. */
+fga_status fga_gaussians(fga_plan_t plan, int shot, int64_t* qidx, int64_t* pidx,
+                         double* psi);
+
+/* Ray state after fga_propagate, host arrays over the shot's Gaussians:
+ * Q,P [G][dim]; A = d_zQ, B = d_zP [G][dim][dim][2] ((j,k) = d_{z_j} Q_k);
+ * a [G][2]; S [G]. Any pointer may be NULL. */
+fga_status fga_state(fga_plan_t plan, int shot, double* Q, double* P, double* A, double* B,
+                     double* a, double* S);
+
+/* Per-stage device times in ms of the last decompose/propagate/reconstruct
+ * (CUDA events on the plan's stream): out[0..4] = FBI, selection, rays,
+ * binning, reconstruction; and the number of kernel launches issued by the
+ * library since the plan was created. */
+fga_status fga_stage_times(fga_plan_t plan, double* ms5, int64_t* launches);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FGA_H */

@@ -1,0 +1,628 @@
+// C ABI of libfga (declared in include/fga.h): plan set-up, validation, device
+// memory, and the order of the three steps of the Algorithm section.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "fga_internal.cuh"
+
+using fga::GridDev;
+using fga::ShotDev;
+
+namespace {
+
+thread_local std::string g_plan_error;
+
+const double kPi = 3.14159265358979323846;
+
+fga_status fail(fga_plan_s* p, fga_status st, const std::string& msg, bool mark_failed = false) {
+  if (p) {
+    p->last_error = msg;
+    if (mark_failed) p->failed = true;
+  } else {
+    g_plan_error = msg;
+  }
+  return st;
+}
+
+#define CUDA_OR_FAIL(p, call)                                                             \
+  do {                                                                                    \
+    cudaError_t e_ = (call);                                                              \
+    if (e_ != cudaSuccess) {                                                              \
+      fga_status st_ = (e_ == cudaErrorMemoryAllocation) ? FGA_ERR_OOM : FGA_ERR_CUDA;    \
+      return fail(p, st_, std::string(#call) + ": " + cudaGetErrorString(e_), true);      \
+    }                                                                                     \
+  } while (0)
+
+bool is_device_ptr(const void* ptr) {
+  cudaPointerAttributes a;
+  cudaError_t e = cudaPointerGetAttributes(&a, ptr);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+template <typename T>
+cudaError_t grow(T** ptr, size_t* cap, size_t need) {
+  if (need <= *cap && *ptr) return cudaSuccess;
+  if (*ptr) cudaFree(*ptr);
+  *ptr = nullptr;
+  *cap = 0;
+  size_t n = std::max<size_t>(need, 1);
+  cudaError_t e = cudaMalloc((void**)ptr, n * sizeof(T));
+  if (e == cudaSuccess) *cap = n;
+  return e;
+}
+
+__global__ void k_check_velocity(const double* c, int64_t n, int* bad) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    double v = c[i];
+    if (!(v > 0.0) || !isfinite(v)) atomicOr(bad, 1);
+  }
+}
+
+// Window-DFT matrix of one axis: E[jp][j] = w(r_j) exp(-i p_jp r_j/eps), with
+// p_jp r_j/eps = 2 pi m r/n_b for the integers m = jp - n_b/2, r = j - n_b/2
+// (reduced mod n_b before scaling, so the angle is exact to rounding).
+std::vector<double> window_dft(int nb, double h, double eps, bool periodic, double L) {
+  std::vector<double> E((size_t)nb * nb * 2);
+  std::vector<double> w(nb);
+  for (int j = 0; j < nb; ++j) {
+    double r = (double)(j - nb / 2) * h;
+    if (periodic) {
+      double s = 0.0;
+      for (int l = -2; l <= 2; ++l) s += std::exp(-(r + l * L) * (r + l * L) / (2.0 * eps));
+      w[j] = s;
+    } else {
+      w[j] = std::exp(-r * r / (2.0 * eps));
+    }
+  }
+  for (int jp = 0; jp < nb; ++jp) {
+    long long m = jp - nb / 2;
+    for (int j = 0; j < nb; ++j) {
+      long long r = j - nb / 2;
+      long long k = ((m * r) % nb + nb) % nb;
+      double ang = 2.0 * kPi * (double)k / (double)nb;
+      E[((size_t)jp * nb + j) * 2 + 0] = w[j] * std::cos(ang);
+      E[((size_t)jp * nb + j) * 2 + 1] = -w[j] * std::sin(ang);
+    }
+  }
+  return E;
+}
+
+fga_status check_usable(fga_plan_s* p) {
+  if (!p) return fail(nullptr, FGA_ERR_INVALID, "plan is NULL");
+  if (p->failed) return FGA_ERR_STATE;
+  return FGA_OK;
+}
+
+fga_status read_status(fga_plan_s* p) {
+  int st = 0;
+  CUDA_OR_FAIL(p, cudaMemcpyAsync(&st, p->d_status, sizeof(int), cudaMemcpyDeviceToHost, p->stream));
+  CUDA_OR_FAIL(p, cudaStreamSynchronize(p->stream));
+  if (st & fga::kStatusNumeric)
+    return fail(p, FGA_ERR_NUMERIC, "a ray met |P| = 0, det Z = 0 or a non-finite value", true);
+  if (st & fga::kStatusCapacity) return fail(p, FGA_ERR_CAPACITY, "a plan capacity was exceeded", true);
+  return FGA_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* fga_status_string(fga_status s) {
+  switch (s) {
+    case FGA_OK: return "ok";
+    case FGA_ERR_INVALID: return "invalid argument";
+    case FGA_ERR_OOM: return "out of device memory";
+    case FGA_ERR_CUDA: return "CUDA error";
+    case FGA_ERR_TIMEOUT: return "device wait timed out";
+    case FGA_ERR_STATE: return "call out of order or plan failed";
+    case FGA_ERR_NUMERIC: return "numerical failure on a ray";
+    case FGA_ERR_CAPACITY: return "capacity exceeded";
+  }
+  return "unknown status";
+}
+
+const char* fga_last_error(fga_plan_t plan) {
+  return plan ? plan->last_error.c_str() : g_plan_error.c_str();
+}
+
+fga_status fga_destroy(fga_plan_t p) {
+  if (!p) return FGA_OK;
+  cudaStreamSynchronize(p->stream);
+  void* bufs[] = {p->d_coef, p->d_shots, p->d_in0, p->d_bbox, p->d_psi, p->d_g1,
+                  p->d_max2, p->d_blk, p->d_counts, p->d_blk_first, p->d_gshot, p->d_gq, p->d_gp,
+                  p->d_gpsi, p->d_state, p->d_gcoef, p->d_tile_cnt, p->d_tile_off,
+                  p->d_tile_list, p->d_out, p->d_status};
+  for (void* b : bufs)
+    if (b) cudaFree(b);
+  for (double* e : p->E)
+    if (e) cudaFree(e);
+  for (auto& ev : p->ev)
+    if (ev) cudaEventDestroy(ev);
+  delete p;
+  return FGA_OK;
+}
+
+fga_status fga_plan(const fga_config* cfg, const double* velocity, void* stream, fga_plan_t* out) {
+  if (!out) return fail(nullptr, FGA_ERR_INVALID, "out is NULL");
+  *out = nullptr;
+  if (!cfg || !velocity) return fail(nullptr, FGA_ERR_INVALID, "cfg or velocity is NULL");
+  const int d = cfg->dim;
+  if (d < 1 || d > fga::kMaxDim) return fail(nullptr, FGA_ERR_INVALID, "dim must be 1 or 2");
+  if (cfg->nshots < 1 || cfg->nshots > fga::kMaxShots)
+    return fail(nullptr, FGA_ERR_INVALID, "nshots out of range");
+  if (!cfg->eps) return fail(nullptr, FGA_ERR_INVALID, "eps is NULL");
+  if (cfg->precision != FGA_FP64)
+    return fail(nullptr, FGA_ERR_INVALID, "only FGA_FP64 is available in this build");
+  if (!(cfg->dt > 0.0) || !(cfg->T >= 0.0) || !std::isfinite(cfg->T))
+    return fail(nullptr, FGA_ERR_INVALID, "need T >= 0 and dt > 0");
+  double steps = cfg->T / cfg->dt;
+  if (std::fabs(steps - std::round(steps)) > 1e-9 * std::max(1.0, steps))
+    return fail(nullptr, FGA_ERR_INVALID, "T/dt must be an integer");
+  if (!(cfg->kappa > 0.0) || !std::isfinite(cfg->kappa))
+    return fail(nullptr, FGA_ERR_INVALID, "kappa must be > 0");
+  if (!(cfg->tau >= 0.0) || !std::isfinite(cfg->tau))
+    return fail(nullptr, FGA_ERR_INVALID, "tau must be >= 0");
+  GridDev gd;
+  std::memset(&gd, 0, sizeof(gd));
+  gd.dim = d;
+  gd.npts = 1;
+  for (int k = 0; k < d; ++k) {
+    if (cfg->n[k] < 4 || cfg->n[k] > (int64_t)1 << 30)
+      return fail(nullptr, FGA_ERR_INVALID, "grid size out of range");
+    if (!(cfg->h[k] > 0.0) || !std::isfinite(cfg->h[k]) || !std::isfinite(cfg->origin[k]))
+      return fail(nullptr, FGA_ERR_INVALID, "grid spacing must be finite and > 0");
+    gd.n[k] = cfg->n[k];
+    gd.h[k] = cfg->h[k];
+    gd.o[k] = cfg->origin[k];
+    gd.inv_h[k] = 1.0 / cfg->h[k];
+    gd.periodic[k] = cfg->periodic[k] ? 1 : 0;
+    gd.L[k] = gd.periodic[k] ? (double)cfg->n[k] * cfg->h[k] : 0.0;
+    gd.npts *= cfg->n[k];
+  }
+  for (int k = d; k < fga::kMaxDim; ++k) {
+    gd.n[k] = 1;
+    gd.h[k] = gd.inv_h[k] = 1.0;
+  }
+  fga_plan_s* p = new fga_plan_s();
+  p->grid = gd;
+  p->nshots = cfg->nshots;
+  p->T = cfg->T;
+  p->dt = cfg->dt;
+  p->nsteps = (int64_t)std::llround(steps);
+  p->kappa = cfg->kappa;
+  p->tau = cfg->tau;
+  p->precision = cfg->precision;
+  p->stream = (cudaStream_t)stream;
+  p->nfields = fga::state_fields(d);
+  const int TS = fga::tile_edge(d);
+  int64_t tile_off = 0;
+  p->shots.resize(cfg->nshots);
+  for (int s = 0; s < cfg->nshots; ++s) {
+    ShotDev& sh = p->shots[s];
+    std::memset(&sh, 0, sizeof(sh));
+    double eps = cfg->eps[s];
+    if (!(eps > 0.0) || !std::isfinite(eps)) {
+      delete p;
+      return fail(nullptr, FGA_ERR_INVALID, "eps must be finite and > 0");
+    }
+    sh.eps = eps;
+    sh.sqrt_eps = std::sqrt(eps);
+    sh.inv_eps = 1.0 / eps;
+    sh.norm = std::pow(2.0 * kPi * eps, -1.5 * d);
+    sh.W = 1.0;
+    sh.np = 1;
+    for (int k = 0; k < d; ++k) {
+      int sk = cfg->q_stride ? cfg->q_stride[s * d + k] : (int)std::lround(0.5 * sh.sqrt_eps / gd.h[k]);
+      if (sk < 1) sk = 1;
+      int nbk;
+      if (gd.periodic[k]) {
+        if (!cfg->q_stride)
+          while (gd.n[k] % sk) --sk;
+        nbk = cfg->box ? cfg->box[s * d + k] : (int)gd.n[k];
+        if (nbk != gd.n[k] || gd.n[k] % sk) {
+          delete p;
+          return fail(nullptr, FGA_ERR_INVALID,
+                      "on a periodic axis the box must be one period and n a multiple of the q-stride");
+        }
+        if (cfg->kappa * sh.sqrt_eps > 2.0 * gd.L[k]) {
+          delete p;
+          return fail(nullptr, FGA_ERR_INVALID, "kappa sqrt(eps) must not exceed two periods");
+        }
+      } else {
+        nbk = cfg->box ? cfg->box[s * d + k]
+                       : 32 * (((int)std::ceil(12.0 * sh.sqrt_eps / gd.h[k]) + 31) / 32);
+      }
+      if (nbk < 2 || (nbk & 1) || nbk > 4096) {
+        delete p;
+        return fail(nullptr, FGA_ERR_INVALID, "box must be even, >= 2 and <= 4096");
+      }
+      sh.s[k] = sk;
+      sh.nb[k] = nbk;
+      sh.nq[k] = gd.periodic[k] ? gd.n[k] / sk : (gd.n[k] - 1) / sk + 1;
+      sh.pscale[k] = 2.0 * kPi * eps / ((double)nbk * gd.h[k]);
+      sh.W *= (double)sk * gd.h[k] * sh.pscale[k];
+      sh.np *= nbk;
+      sh.ntile[k] = (int)((gd.n[k] + TS - 1) / TS);
+    }
+    sh.tile_off = tile_off;
+    int64_t nt = 1;
+    for (int k = 0; k < d; ++k) nt *= sh.ntile[k];
+    tile_off += nt;
+  }
+  p->ntiles = tile_off;
+  // device buffers that do not depend on the data
+  cudaError_t e;
+#define PLAN_CUDA(call)                                                              \
+  do {                                                                               \
+    e = (call);                                                                      \
+    if (e != cudaSuccess) {                                                          \
+      std::string m_ = std::string(#call) + ": " + cudaGetErrorString(e);            \
+      fga_destroy(p);                                                                \
+      return fail(nullptr, e == cudaErrorMemoryAllocation ? FGA_ERR_OOM : FGA_ERR_CUDA, m_); \
+    }                                                                                \
+  } while (0)
+  PLAN_CUDA(cudaMalloc(&p->d_coef, sizeof(double) * gd.npts));
+  PLAN_CUDA(cudaMemcpyAsync(p->d_coef, velocity, sizeof(double) * gd.npts, cudaMemcpyDefault,
+                            p->stream));
+  PLAN_CUDA(cudaMalloc(&p->d_status, sizeof(int)));
+  PLAN_CUDA(cudaMemsetAsync(p->d_status, 0, sizeof(int), p->stream));
+  k_check_velocity<<<256, 256, 0, p->stream>>>(p->d_coef, gd.npts, p->d_status);
+  p->launches += 1;
+  int bad = 0;
+  PLAN_CUDA(cudaMemcpyAsync(&bad, p->d_status, sizeof(int), cudaMemcpyDeviceToHost, p->stream));
+  PLAN_CUDA(cudaStreamSynchronize(p->stream));
+  if (bad) {
+    fga_destroy(p);
+    return fail(nullptr, FGA_ERR_INVALID, "velocity must be finite and > 0 everywhere");
+  }
+  PLAN_CUDA(cudaMemsetAsync(p->d_status, 0, sizeof(int), p->stream));
+  p->E.assign((size_t)cfg->nshots * d, nullptr);
+  for (int s = 0; s < cfg->nshots; ++s) {
+    for (int k = 0; k < d; ++k) {
+      ShotDev& sh = p->shots[s];
+      std::vector<double> E = window_dft(sh.nb[k], gd.h[k], sh.eps, gd.periodic[k] != 0, gd.L[k]);
+      double* dE = nullptr;
+      PLAN_CUDA(cudaMalloc(&dE, sizeof(double) * E.size()));
+      p->E[(size_t)s * d + k] = dE;
+      PLAN_CUDA(cudaMemcpy(dE, E.data(), sizeof(double) * E.size(), cudaMemcpyHostToDevice));
+      sh.E[k] = reinterpret_cast<const double2*>(dE);
+    }
+  }
+  PLAN_CUDA(cudaMalloc(&p->d_shots, sizeof(ShotDev) * cfg->nshots));
+  PLAN_CUDA(cudaMalloc(&p->d_bbox, sizeof(int) * cfg->nshots * d * 2));
+  PLAN_CUDA(cudaMalloc(&p->d_max2, sizeof(unsigned long long) * cfg->nshots));
+  PLAN_CUDA(cudaMalloc(&p->d_counts, sizeof(int64_t) * cfg->nshots));
+  PLAN_CUDA(cudaMalloc(&p->d_blk_first, sizeof(int64_t) * (cfg->nshots + 1)));
+  PLAN_CUDA(cudaMalloc(&p->d_tile_off, sizeof(int64_t) * (p->ntiles + 1)));
+  for (auto& ev : p->ev) PLAN_CUDA(cudaEventCreate(&ev));
+#undef PLAN_CUDA
+  *out = p;
+  return FGA_OK;
+}
+
+fga_status fga_decompose(fga_plan_t p, const double* u0, const double* u1, int64_t* counts_host) {
+  fga_status st = check_usable(p);
+  if (st != FGA_OK) return st;
+  if (!u0 || !u1) return fail(p, FGA_ERR_INVALID, "u0 and u1 must not be NULL");
+  const GridDev& gd = p->grid;
+  const int d = gd.dim;
+  const size_t n_all = (size_t)p->nshots * gd.npts;
+  const double* du0 = u0;
+  const double* du1 = u1;
+  if (!is_device_ptr(u0) || !is_device_ptr(u1)) {
+    // host data: one staging buffer holds both fields
+    CUDA_OR_FAIL(p, grow(&p->d_in0, &p->in_cap, 2 * n_all));
+    p->d_in1 = p->d_in0 + n_all;
+    CUDA_OR_FAIL(p, cudaMemcpyAsync(p->d_in0, u0, sizeof(double) * n_all, cudaMemcpyDefault, p->stream));
+    CUDA_OR_FAIL(p, cudaMemcpyAsync(p->d_in1, u1, sizeof(double) * n_all, cudaMemcpyDefault, p->stream));
+    du0 = p->d_in0;
+    du1 = p->d_in1;
+  }
+  CUDA_OR_FAIL(p, cudaEventRecord(p->ev[0], p->stream));
+  CUDA_OR_FAIL(p, fga::launch_support_bbox(p, du0, du1));
+  std::vector<int> bbox((size_t)p->nshots * d * 2);
+  CUDA_OR_FAIL(p, cudaMemcpyAsync(bbox.data(), p->d_bbox, sizeof(int) * bbox.size(),
+                                  cudaMemcpyDeviceToHost, p->stream));
+  CUDA_OR_FAIL(p, cudaStreamSynchronize(p->stream));
+  // active q rectangle per shot: q whose box meets the data's bounding box
+  int64_t psi_total = 0, g1_total = 0;
+  p->blk_first.assign(p->nshots + 1, 0);
+  for (int s = 0; s < p->nshots; ++s) {
+    ShotDev& sh = p->shots[s];
+    bool empty = false;
+    for (int k = 0; k < d; ++k) {
+      int lo = bbox[(s * d + k) * 2], hi = bbox[(s * d + k) * 2 + 1];
+      if (hi < 0) empty = true;
+      if (gd.periodic[k]) {
+        sh.qlo[k] = 0;
+        sh.qn[k] = sh.nq[k];
+      } else {
+        int64_t half = sh.nb[k] / 2;
+        int64_t mlo = (int64_t)std::ceil((double)(lo - half + 1) / sh.s[k]);
+        int64_t mhi = (int64_t)std::floor((double)(hi + half) / sh.s[k]);
+        mlo = std::max<int64_t>(mlo, 0);
+        mhi = std::min<int64_t>(mhi, sh.nq[k] - 1);
+        sh.qlo[k] = mlo;
+        sh.qn[k] = std::max<int64_t>(mhi - mlo + 1, 0);
+      }
+    }
+    if (empty)
+      for (int k = 0; k < d; ++k) sh.qn[k] = 0;
+    int64_t qt = 1;
+    for (int k = 0; k < d; ++k) qt *= sh.qn[k];
+    sh.psi_off = psi_total;
+    sh.psi_len = qt * sh.np;
+    psi_total += ((sh.psi_len + fga::kScanBlock - 1) / fga::kScanBlock) * fga::kScanBlock;
+    p->blk_first[s] = sh.psi_off / fga::kScanBlock;
+    if (d == 2) {
+      sh.row_lo = (int64_t)sh.s[0] * sh.qlo[0] - sh.nb[0] / 2;
+      sh.nrows = sh.qn[0] > 0 ? (int64_t)sh.s[0] * (sh.qn[0] - 1) + sh.nb[0] : 0;
+      sh.g1_off = g1_total;
+      g1_total += 2 * sh.nrows * sh.qn[1] * sh.nb[1];
+    }
+    sh.g_off = sh.g_cnt = 0;
+  }
+  p->blk_first[p->nshots] = psi_total / fga::kScanBlock;
+  p->nblocks = psi_total / fga::kScanBlock;
+  CUDA_OR_FAIL(p, grow(&p->d_psi, &p->psi_cap, (size_t)psi_total));
+  if (d == 2) CUDA_OR_FAIL(p, grow(&p->d_g1, &p->g1_cap, (size_t)g1_total));
+  CUDA_OR_FAIL(p, grow(&p->d_blk, &p->blk_cap, (size_t)p->nblocks + 1));
+  CUDA_OR_FAIL(p, cudaMemcpyAsync(p->d_blk_first, p->blk_first.data(),
+                                  sizeof(int64_t) * (p->nshots + 1), cudaMemcpyHostToDevice, p->stream));
+  CUDA_OR_FAIL(p, cudaMemcpyAsync(p->d_shots, p->shots.data(), sizeof(ShotDev) * p->nshots,
+                                  cudaMemcpyHostToDevice, p->stream));
+  CUDA_OR_FAIL(p, fga::launch_fbi(p, du0, du1));
+  CUDA_OR_FAIL(p, cudaEventRecord(p->ev[1], p->stream));
+  CUDA_OR_FAIL(p, fga::launch_select_count(p));
+  std::vector<int64_t> counts(p->nshots, 0);
+  if (p->nblocks > 0)
+    CUDA_OR_FAIL(p, cudaMemcpyAsync(counts.data(), p->d_counts, sizeof(int64_t) * p->nshots,
+                                    cudaMemcpyDeviceToHost, p->stream));
+  CUDA_OR_FAIL(p, cudaStreamSynchronize(p->stream));
+  int64_t G = 0;
+  for (int s = 0; s < p->nshots; ++s) {
+    p->shots[s].g_off = G;
+    p->shots[s].g_cnt = counts[s];
+    G += counts[s];
+  }
+  if (G > ((int64_t)1 << 31) - 1) return fail(p, FGA_ERR_CAPACITY, "more than 2^31-1 Gaussians", true);
+  p->G = G;
+  if ((size_t)G > p->g_cap || !p->d_gshot) {
+    size_t cap = std::max<size_t>((size_t)G, 1);
+    size_t c;
+    c = 0; if (p->d_gshot) { cudaFree(p->d_gshot); p->d_gshot = nullptr; }
+    CUDA_OR_FAIL(p, grow(&p->d_gshot, &c, cap));
+    c = 0; if (p->d_gq) { cudaFree(p->d_gq); p->d_gq = nullptr; }
+    CUDA_OR_FAIL(p, grow(&p->d_gq, &c, cap));
+    c = 0; if (p->d_gp) { cudaFree(p->d_gp); p->d_gp = nullptr; }
+    CUDA_OR_FAIL(p, grow(&p->d_gp, &c, cap));
+    c = 0; if (p->d_gpsi) { cudaFree(p->d_gpsi); p->d_gpsi = nullptr; }
+    CUDA_OR_FAIL(p, grow(&p->d_gpsi, &c, cap));
+    c = 0; if (p->d_gcoef) { cudaFree(p->d_gcoef); p->d_gcoef = nullptr; }
+    CUDA_OR_FAIL(p, grow(&p->d_gcoef, &c, cap));
+    c = 0; if (p->d_state) { cudaFree(p->d_state); p->d_state = nullptr; }
+    CUDA_OR_FAIL(p, grow(&p->d_state, &c, cap * p->nfields));
+    p->g_cap = cap;
+  }
+  CUDA_OR_FAIL(p, fga::launch_select(p));
+  CUDA_OR_FAIL(p, cudaEventRecord(p->ev[2], p->stream));
+  if (counts_host)
+    for (int s = 0; s < p->nshots; ++s) counts_host[s] = counts[s];
+  p->stage = 1;
+  return FGA_OK;
+}
+
+fga_status fga_propagate(fga_plan_t p) {
+  fga_status st = check_usable(p);
+  if (st != FGA_OK) return st;
+  if (p->stage < 1) return fail(p, FGA_ERR_STATE, "fga_propagate before fga_decompose");
+  CUDA_OR_FAIL(p, cudaEventRecord(p->ev[3], p->stream));
+  CUDA_OR_FAIL(p, fga::launch_rays(p));
+  CUDA_OR_FAIL(p, cudaEventRecord(p->ev[4], p->stream));
+  p->stage = 2;
+  return FGA_OK;
+}
+
+fga_status fga_reconstruct(fga_plan_t p, double* u_out) {
+  fga_status st = check_usable(p);
+  if (st != FGA_OK) return st;
+  if (p->stage < 2) return fail(p, FGA_ERR_STATE, "fga_reconstruct before fga_propagate");
+  if (!u_out) return fail(p, FGA_ERR_INVALID, "u_out must not be NULL");
+  const GridDev& gd = p->grid;
+  const int d = gd.dim;
+  const int TS = fga::tile_edge(d);
+  // capacity of the tile lists: every Gaussian meets at most prod_k m_k tiles,
+  // m_k = (floor(window points / tile) + 2) per image, times 5 images on periodic axes
+  size_t pairs = 0;
+  for (const auto& sh : p->shots) {
+    size_t per = 1;
+    for (int k = 0; k < d; ++k) {
+      double wpts = 2.0 * p->kappa * sh.sqrt_eps * gd.inv_h[k] + 6.0;
+      size_t mk = (size_t)(wpts / TS) + 2;
+      if (gd.periodic[k]) mk *= 5;
+      mk = std::min<size_t>(mk, (size_t)sh.ntile[k]);
+      per *= mk;
+    }
+    pairs += per * (size_t)sh.g_cnt;
+  }
+  CUDA_OR_FAIL(p, grow(&p->d_tile_list, &p->list_cap, pairs));
+  CUDA_OR_FAIL(p, cudaEventRecord(p->ev[5], p->stream));
+  CUDA_OR_FAIL(p, fga::launch_binning(p, nullptr));
+  CUDA_OR_FAIL(p, fga::launch_binning_fill(p));
+  CUDA_OR_FAIL(p, cudaEventRecord(p->ev[6], p->stream));
+  const size_t n_all = (size_t)p->nshots * gd.npts;
+  double* dst = u_out;
+  bool host_out = !is_device_ptr(u_out);
+  if (host_out) {
+    CUDA_OR_FAIL(p, grow(&p->d_out, &p->out_cap, n_all));
+    dst = p->d_out;
+  }
+  CUDA_OR_FAIL(p, cudaMemsetAsync(dst, 0, sizeof(double) * n_all, p->stream));
+  CUDA_OR_FAIL(p, fga::launch_reconstruct(p, dst));
+  CUDA_OR_FAIL(p, cudaEventRecord(p->ev[7], p->stream));
+  if (host_out) {
+    CUDA_OR_FAIL(p, cudaMemcpyAsync(u_out, dst, sizeof(double) * n_all, cudaMemcpyDeviceToHost,
+                                    p->stream));
+    return read_status(p);
+  }
+  return FGA_OK;
+}
+
+fga_status fga_sync(fga_plan_t p) {
+  fga_status st = check_usable(p);
+  if (st != FGA_OK) return st;
+  return read_status(p);
+}
+
+int64_t fga_count(fga_plan_t p, int shot) {
+  if (!p || shot < 0 || shot >= p->nshots || p->stage < 1) return -1;
+  return p->shots[shot].g_cnt;
+}
+
+fga_status fga_shot_grid(fga_plan_t p, int shot, int64_t* nq, int64_t* np, int64_t* nb, int64_t* s) {
+  if (!p || shot < 0 || shot >= p->nshots) return fail(p, FGA_ERR_INVALID, "bad plan or shot");
+  const ShotDev& sh = p->shots[shot];
+  for (int k = 0; k < p->grid.dim; ++k) {
+    if (nq) nq[k] = sh.nq[k];
+    if (np) np[k] = sh.nb[k];
+    if (nb) nb[k] = sh.nb[k];
+    if (s) s[k] = sh.s[k];
+  }
+  return FGA_OK;
+}
+
+fga_status fga_psi(fga_plan_t p, int shot, double* psi_host, double* max_abs) {
+  fga_status st = check_usable(p);
+  if (st != FGA_OK) return st;
+  if (shot < 0 || shot >= p->nshots) return fail(p, FGA_ERR_INVALID, "bad shot");
+  if (p->stage < 1) return fail(p, FGA_ERR_STATE, "no decomposition yet");
+  const ShotDev& sh = p->shots[shot];
+  const int d = p->grid.dim;
+  int64_t nqt = 1;
+  for (int k = 0; k < d; ++k) nqt *= sh.nq[k];
+  if (psi_host) {
+    std::memset(psi_host, 0, sizeof(double) * 2 * nqt * sh.np);
+    std::vector<double> seg((size_t)sh.psi_len * 2);
+    if (sh.psi_len > 0)
+      CUDA_OR_FAIL(p, cudaMemcpyAsync(seg.data(), p->d_psi + sh.psi_off, sizeof(double2) * sh.psi_len,
+                                      cudaMemcpyDeviceToHost, p->stream));
+    CUDA_OR_FAIL(p, cudaStreamSynchronize(p->stream));
+    int64_t qtl = sh.psi_len / std::max<int64_t>(sh.np, 1);
+    for (int64_t ql = 0; ql < qtl; ++ql) {
+      int64_t qf;
+      if (d == 1) {
+        qf = sh.qlo[0] + ql;
+      } else {
+        int64_t mx = ql / sh.qn[1], mz = ql % sh.qn[1];
+        qf = (sh.qlo[0] + mx) * sh.nq[1] + sh.qlo[1] + mz;
+      }
+      std::memcpy(psi_host + 2 * qf * sh.np, seg.data() + 2 * ql * sh.np, sizeof(double) * 2 * sh.np);
+    }
+  }
+  if (max_abs) {
+    unsigned long long bits = 0;
+    CUDA_OR_FAIL(p, cudaMemcpyAsync(&bits, p->d_max2 + shot, sizeof(bits), cudaMemcpyDeviceToHost,
+                                    p->stream));
+    CUDA_OR_FAIL(p, cudaStreamSynchronize(p->stream));
+    double m2;
+    std::memcpy(&m2, &bits, sizeof(m2));
+    *max_abs = std::sqrt(m2);
+  }
+  return FGA_OK;
+}
+
+fga_status fga_gaussians(fga_plan_t p, int shot, int64_t* qidx, int64_t* pidx, double* psi) {
+  fga_status st = check_usable(p);
+  if (st != FGA_OK) return st;
+  if (shot < 0 || shot >= p->nshots) return fail(p, FGA_ERR_INVALID, "bad shot");
+  if (p->stage < 1) return fail(p, FGA_ERR_STATE, "no decomposition yet");
+  const ShotDev& sh = p->shots[shot];
+  int64_t n = sh.g_cnt;
+  if (n == 0) return FGA_OK;
+  if (qidx)
+    CUDA_OR_FAIL(p, cudaMemcpyAsync(qidx, p->d_gq + sh.g_off, sizeof(int64_t) * n,
+                                    cudaMemcpyDeviceToHost, p->stream));
+  if (pidx) {
+    std::vector<int32_t> tmp(n);
+    CUDA_OR_FAIL(p, cudaMemcpyAsync(tmp.data(), p->d_gp + sh.g_off, sizeof(int32_t) * n,
+                                    cudaMemcpyDeviceToHost, p->stream));
+    CUDA_OR_FAIL(p, cudaStreamSynchronize(p->stream));
+    for (int64_t i = 0; i < n; ++i) pidx[i] = tmp[i];
+  }
+  if (psi)
+    CUDA_OR_FAIL(p, cudaMemcpyAsync(psi, p->d_gpsi + sh.g_off, sizeof(double2) * n,
+                                    cudaMemcpyDeviceToHost, p->stream));
+  CUDA_OR_FAIL(p, cudaStreamSynchronize(p->stream));
+  return FGA_OK;
+}
+
+fga_status fga_state(fga_plan_t p, int shot, double* Q, double* P, double* A, double* B, double* a,
+                     double* S) {
+  fga_status st = check_usable(p);
+  if (st != FGA_OK) return st;
+  if (shot < 0 || shot >= p->nshots) return fail(p, FGA_ERR_INVALID, "bad shot");
+  if (p->stage < 2) return fail(p, FGA_ERR_STATE, "not propagated yet");
+  const ShotDev& sh = p->shots[shot];
+  const int d = p->grid.dim;
+  const int64_t n = sh.g_cnt;
+  if (n == 0) return FGA_OK;
+  std::vector<double> f((size_t)p->nfields * n);
+  for (int i = 0; i < p->nfields; ++i)
+    CUDA_OR_FAIL(p, cudaMemcpyAsync(f.data() + (size_t)i * n, p->d_state + (size_t)i * p->g_cap + sh.g_off,
+                                    sizeof(double) * n, cudaMemcpyDeviceToHost, p->stream));
+  CUDA_OR_FAIL(p, cudaStreamSynchronize(p->stream));
+  auto F = [&](int field, int64_t g) { return f[(size_t)field * n + g]; };
+  const int AR = 2 * d, AI = AR + d * d, BR = AI + d * d, BI = BR + d * d, aR = BI + d * d;
+  for (int64_t g = 0; g < n; ++g) {
+    for (int k = 0; k < d; ++k) {
+      if (Q) Q[g * d + k] = F(k, g);
+      if (P) P[g * d + k] = F(d + k, g);
+      for (int l = 0; l < d; ++l) {
+        int e = k * d + l;
+        if (A) {
+          A[((g * d + k) * d + l) * 2] = F(AR + e, g);
+          A[((g * d + k) * d + l) * 2 + 1] = F(AI + e, g);
+        }
+        if (B) {
+          B[((g * d + k) * d + l) * 2] = F(BR + e, g);
+          B[((g * d + k) * d + l) * 2 + 1] = F(BI + e, g);
+        }
+      }
+    }
+    if (a) {
+      a[2 * g] = F(aR, g);
+      a[2 * g + 1] = F(aR + 1, g);
+    }
+    if (S) S[g] = F(aR + 2, g);
+  }
+  return FGA_OK;
+}
+
+fga_status fga_stage_times(fga_plan_t p, double* ms5, int64_t* launches) {
+  if (!p) return fail(nullptr, FGA_ERR_INVALID, "plan is NULL");
+  if (ms5) {
+    CUDA_OR_FAIL(p, cudaStreamSynchronize(p->stream));
+    const int from[5] = {0, 1, 3, 5, 6}, to[5] = {1, 2, 4, 6, 7};
+    for (int i = 0; i < 5; ++i) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, p->ev[from[i]], p->ev[to[i]]) != cudaSuccess) {
+        cudaGetLastError();
+        ms = -1.f;
+      }
+      ms5[i] = ms;
+    }
+  }
+  if (launches) *launches = p->launches;
+  return FGA_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,391 @@
+// Step 1 of the method (Initial wavefield decomposition section): the FBI
+// transform of f0 and f1 on a box of n_b points per axis around every q, and
+// the branch split of Eq. psi.
+//
+// The paper evaluates each box with an FFT. Here the box transform is the
+// separable contraction with the constant window-DFT matrix of each axis,
+//   E_k[jp][j] = w_k(r_j) exp(-i p_jp r_j/eps),  r_j = (j - n_b/2) h_k,
+// which is the same sum: psi(q, p) = h^d sum_j f(q + r_j) prod_k E_k[jp_k][j_k].
+// In 2D the contraction along the last axis does not depend on the q-row, so it
+// is done once per data row (stage 1, shared by every q of a column) and the
+// contraction along the first axis is a dense complex GEMM per q (stage 2).
+// Both stages are FP64 tiled GEMMs; the stage that yields psi fuses the branch
+// split psi+ = 1/2 (psi_0 + i eps psi_1/(c(q)|p|)), the removal of the left-out
+// p values and the running max of |psi+|^2 per shot.
+#include <algorithm>
+#include <climits>
+
+#include "fga_internal.cuh"
+#include "fga_medium.cuh"
+
+namespace fga {
+
+namespace {
+
+constexpr int BM = 32, BN = 32, BK = 16, NT = 256;
+
+__device__ __forceinline__ int64_t wrap_or_invalid(int64_t i, int64_t n, int periodic) {
+  if (periodic) {
+    int64_t r = i % n;
+    return r < 0 ? r + n : r;
+  }
+  return (i >= 0 && i < n) ? i : -1;
+}
+
+__device__ __forceinline__ void atomic_max_nonneg(unsigned long long* addr, double v) {
+  atomicMax(addr, (unsigned long long)__double_as_longlong(v));
+}
+
+__global__ void k_bbox_init(int* bbox, int n) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) bbox[i] = (i & 1) ? -1 : INT_MAX;
+}
+
+// Bounding box of the nonzero samples of (u0, u1) per shot: bbox[s][k] = {lo, hi}.
+__global__ void k_support_bbox(GridDev gd, const double* __restrict__ u0,
+                               const double* __restrict__ u1, int* bbox) {
+  int s = blockIdx.y;
+  const double* a = u0 + (int64_t)s * gd.npts;
+  const double* b = u1 + (int64_t)s * gd.npts;
+  int lo[kMaxDim], hi[kMaxDim];
+  for (int k = 0; k < kMaxDim; ++k) {
+    lo[k] = INT_MAX;
+    hi[k] = -1;
+  }
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < gd.npts;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    if (a[i] != 0.0 || b[i] != 0.0) {
+      int64_t rem = i;
+      for (int k = gd.dim - 1; k >= 0; --k) {
+        int c = (int)(rem % gd.n[k]);
+        rem /= gd.n[k];
+        lo[k] = min(lo[k], c);
+        hi[k] = max(hi[k], c);
+      }
+    }
+  }
+  for (int k = 0; k < gd.dim; ++k) {
+    for (int off = 16; off > 0; off >>= 1) {
+      lo[k] = min(lo[k], __shfl_xor_sync(0xffffffffu, lo[k], off));
+      hi[k] = max(hi[k], __shfl_xor_sync(0xffffffffu, hi[k], off));
+    }
+    if ((threadIdx.x & 31) == 0 && hi[k] >= 0) {
+      atomicMin(bbox + (s * gd.dim + k) * 2 + 0, lo[k]);
+      atomicMax(bbox + (s * gd.dim + k) * 2 + 1, hi[k]);
+    }
+  }
+}
+
+// Branch split, left-out p values and max |psi+|^2 for one output element.
+template <int D>
+__device__ __forceinline__ double psi_plus(const ShotDev& sh, int64_t jp, double2 p0, double2 p1,
+                                           double cq, double2& out) {
+  bool valid;
+  double pn;
+  if constexpr (D == 1) {
+    int64_t m = jp - sh.nb[0] / 2;
+    valid = (jp != 0) && (m != 0);
+    pn = fabs((double)m) * sh.pscale[0];
+  } else {
+    int64_t j0 = jp / sh.nb[1], j1 = jp - j0 * sh.nb[1];
+    int64_t m0 = j0 - sh.nb[0] / 2, m1 = j1 - sh.nb[1] / 2;
+    valid = (j0 != 0) && (j1 != 0) && !(m0 == 0 && m1 == 0);
+    double a = (double)m0 * sh.pscale[0], b = (double)m1 * sh.pscale[1];
+    pn = sqrt(a * a + b * b);
+  }
+  if (!valid) {
+    out = make_double2(0.0, 0.0);
+    return 0.0;
+  }
+  double r = sh.eps / (cq * pn);
+  out = make_double2(0.5 * (p0.x - r * p1.y), 0.5 * (p0.y + r * p1.x));
+  return out.x * out.x + out.y * out.y;
+}
+
+// Stage 1: C_f[m][n] = sum_k data_f(m, k) * E_last[n][k], f = 0, 1.
+// D == 2: m = (row r, q_z local), k runs along the last axis of the box; the
+//         result goes to the stage-1 buffer.
+// D == 1: m = q local, and the epilogue forms psi+.
+template <int D>
+__global__ void __launch_bounds__(NT) k_fbi_stage1(GridDev gd, const ShotDev* __restrict__ shots,
+                                                   const double* __restrict__ u0,
+                                                   const double* __restrict__ u1,
+                                                   const double* __restrict__ C,
+                                                   double2* __restrict__ g1,
+                                                   double2* __restrict__ psi,
+                                                   unsigned long long* __restrict__ max2) {
+  const int s = blockIdx.z;
+  const ShotDev sh = shots[s];
+  constexpr int L = D - 1;  // last axis
+  const int64_t nbl = sh.nb[L];
+  const int64_t M = (D == 2) ? sh.nrows * sh.qn[1] : sh.qn[0];
+  const int64_t N = nbl, K = nbl;
+  const int64_t m0 = (int64_t)blockIdx.y * BM, n0 = (int64_t)blockIdx.x * BN;
+  if (m0 >= M || n0 >= N) return;
+  __shared__ double As[2][BK][BM];
+  __shared__ double2 Bs[BK][BN];
+  __shared__ double cq_s[BM];
+  const int t = threadIdx.x, tx = t % 16, ty = t / 16;
+  const double* f0 = u0 + (int64_t)s * gd.npts;
+  const double* f1 = u1 + (int64_t)s * gd.npts;
+  double2 acc0[2][2], acc1[2][2];
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      acc0[i][j] = make_double2(0, 0);
+      acc1[i][j] = make_double2(0, 0);
+    }
+  const double2* ELAST = sh.E[L];  // last-axis window-DFT matrix [n_b][n_b]
+  for (int64_t k0 = 0; k0 < K; k0 += BK) {
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+      int e = t + NT * i;
+      int mm = e / BK, kk = e % BK;
+      int64_t m = m0 + mm, k = k0 + kk;
+      double v0 = 0.0, v1 = 0.0;
+      if (m < M && k < K) {
+        int64_t idx;
+        if constexpr (D == 2) {
+          int64_t r = m / sh.qn[1], mzl = m - r * sh.qn[1];
+          int64_t ix = wrap_or_invalid(sh.row_lo + r, gd.n[0], gd.periodic[0]);
+          int64_t iz = wrap_or_invalid(sh.s[1] * (sh.qlo[1] + mzl) + k - nbl / 2, gd.n[1],
+                                       gd.periodic[1]);
+          idx = (ix < 0 || iz < 0) ? -1 : ix * gd.n[1] + iz;
+        } else {
+          idx = wrap_or_invalid(sh.s[0] * (sh.qlo[0] + m) + k - nbl / 2, gd.n[0],
+                                gd.periodic[0]);
+        }
+        if (idx >= 0) {
+          v0 = __ldg(f0 + idx);
+          v1 = __ldg(f1 + idx);
+        }
+      }
+      As[0][kk][mm] = v0;
+      As[1][kk][mm] = v1;
+    }
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+      int e = t + NT * i;
+      int nn = e / BK, kk = e % BK;
+      int64_t n = n0 + nn, k = k0 + kk;
+      double2 v = make_double2(0, 0);
+      if (n < N && k < K) v = __ldg(ELAST + n * K + k);
+      Bs[kk][nn] = v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < BK; ++kk) {
+      double a0[2], a1[2];
+      double2 b[2];
+#pragma unroll
+      for (int i = 0; i < 2; ++i) {
+        a0[i] = As[0][kk][ty + 16 * i];
+        a1[i] = As[1][kk][ty + 16 * i];
+        b[i] = Bs[kk][tx + 16 * i];
+      }
+#pragma unroll
+      for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+          acc0[i][j].x = fma(a0[i], b[j].x, acc0[i][j].x);
+          acc0[i][j].y = fma(a0[i], b[j].y, acc0[i][j].y);
+          acc1[i][j].x = fma(a1[i], b[j].x, acc1[i][j].x);
+          acc1[i][j].y = fma(a1[i], b[j].y, acc1[i][j].y);
+        }
+    }
+    __syncthreads();
+  }
+  if constexpr (D == 2) {
+    const int64_t plane = M * N;
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+      for (int j = 0; j < 2; ++j) {
+        int64_t m = m0 + ty + 16 * i, n = n0 + tx + 16 * j;
+        if (m < M && n < N) {
+          g1[sh.g1_off + m * N + n] = acc0[i][j];
+          g1[sh.g1_off + plane + m * N + n] = acc1[i][j];
+        }
+      }
+  } else {
+    // c(q) for the rows of this tile
+    if (t < BM) {
+      int64_t m = m0 + t;
+      double q = gd.o[0] + (double)(sh.s[0] * (sh.qlo[0] + m)) * gd.h[0];
+      cq_s[t] = (m < M) ? medium_value<1>(gd, C, &q) : 1.0;
+    }
+    __syncthreads();
+    const double hv = gd.h[0];
+    double mymax = 0.0;
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+      for (int j = 0; j < 2; ++j) {
+        int64_t m = m0 + ty + 16 * i, n = n0 + tx + 16 * j;
+        if (m < M && n < N) {
+          double2 p0 = make_double2(hv * acc0[i][j].x, hv * acc0[i][j].y);
+          double2 p1 = make_double2(hv * acc1[i][j].x, hv * acc1[i][j].y);
+          double2 o;
+          double a2 = psi_plus<1>(sh, n, p0, p1, cq_s[ty + 16 * i], o);
+          psi[sh.psi_off + m * sh.np + n] = o;
+          mymax = fmax(mymax, a2);
+        }
+      }
+    for (int off = 16; off > 0; off >>= 1) mymax = fmax(mymax, __shfl_xor_sync(0xffffffffu, mymax, off));
+    if ((t & 31) == 0) atomic_max_nonneg(max2 + s, mymax);
+  }
+}
+
+// Stage 2 (2D): for one q, psi_f[jpx][jpz] = h_x h_z sum_jx E_x[jpx][jx] G1_f[row(jx)][jpz],
+// then the branch split.
+__global__ void __launch_bounds__(NT) k_fbi_stage2(GridDev gd, const ShotDev* __restrict__ shots,
+                                                   const double* __restrict__ C,
+                                                   const double2* __restrict__ g1,
+                                                   double2* __restrict__ psi,
+                                                   unsigned long long* __restrict__ max2) {
+  const int s = blockIdx.z;
+  const ShotDev sh = shots[s];
+  const int64_t qtot = sh.qn[0] * sh.qn[1];
+  const int64_t ql = blockIdx.y;
+  if (ql >= qtot) return;
+  const int64_t nbx = sh.nb[0], nbz = sh.nb[1];
+  const int64_t tiles_n = (nbz + BN - 1) / BN;
+  const int64_t m0 = (blockIdx.x / tiles_n) * BM, n0 = (blockIdx.x % tiles_n) * BN;
+  if (m0 >= nbx) return;
+  const int64_t mxl = ql / sh.qn[1], mzl = ql - mxl * sh.qn[1];
+  const int64_t M1 = sh.nrows * sh.qn[1];
+  const int64_t plane = M1 * nbz;
+  const double2* G0 = g1 + sh.g1_off;
+  const double2* G1p = G0 + plane;
+  const double2* Ex = sh.E[0];
+  __shared__ double2 As[BK][BM];
+  __shared__ double2 Bs[2][BK][BN];
+  __shared__ double cq_s;
+  const int t = threadIdx.x, tx = t % 16, ty = t / 16;
+  if (t == 0) {
+    double q[2] = {gd.o[0] + (double)(sh.s[0] * (sh.qlo[0] + mxl)) * gd.h[0],
+                   gd.o[1] + (double)(sh.s[1] * (sh.qlo[1] + mzl)) * gd.h[1]};
+    cq_s = medium_value<2>(gd, C, q);
+  }
+  double2 acc0[2][2], acc1[2][2];
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      acc0[i][j] = make_double2(0, 0);
+      acc1[i][j] = make_double2(0, 0);
+    }
+  const int64_t row0 = sh.s[0] * mxl;  // stage-1 row of box index jx = 0
+  for (int64_t k0 = 0; k0 < nbx; k0 += BK) {
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+      int e = t + NT * i;
+      int mm = e / BK, kk = e % BK;
+      int64_t m = m0 + mm, k = k0 + kk;
+      As[kk][mm] = (m < nbx && k < nbx) ? __ldg(Ex + m * nbx + k) : make_double2(0, 0);
+    }
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+      int e = t + NT * i;
+      int kk = e / BN, nn = e % BN;
+      int64_t k = k0 + kk, n = n0 + nn;
+      double2 v0 = make_double2(0, 0), v1 = make_double2(0, 0);
+      if (k < nbx && n < nbz) {
+        int64_t off = ((row0 + k) * sh.qn[1] + mzl) * nbz + n;
+        v0 = __ldg(G0 + off);
+        v1 = __ldg(G1p + off);
+      }
+      Bs[0][kk][nn] = v0;
+      Bs[1][kk][nn] = v1;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < BK; ++kk) {
+      double2 a[2], b0[2], b1[2];
+#pragma unroll
+      for (int i = 0; i < 2; ++i) {
+        a[i] = As[kk][ty + 16 * i];
+        b0[i] = Bs[0][kk][tx + 16 * i];
+        b1[i] = Bs[1][kk][tx + 16 * i];
+      }
+#pragma unroll
+      for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+          acc0[i][j].x = fma(a[i].x, b0[j].x, fma(-a[i].y, b0[j].y, acc0[i][j].x));
+          acc0[i][j].y = fma(a[i].x, b0[j].y, fma(a[i].y, b0[j].x, acc0[i][j].y));
+          acc1[i][j].x = fma(a[i].x, b1[j].x, fma(-a[i].y, b1[j].y, acc1[i][j].x));
+          acc1[i][j].y = fma(a[i].x, b1[j].y, fma(a[i].y, b1[j].x, acc1[i][j].y));
+        }
+    }
+    __syncthreads();
+  }
+  const double hv = gd.h[0] * gd.h[1];
+  double mymax = 0.0;
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      int64_t m = m0 + ty + 16 * i, n = n0 + tx + 16 * j;
+      if (m < nbx && n < nbz) {
+        double2 p0 = make_double2(hv * acc0[i][j].x, hv * acc0[i][j].y);
+        double2 p1 = make_double2(hv * acc1[i][j].x, hv * acc1[i][j].y);
+        double2 o;
+        int64_t jp = m * nbz + n;
+        double a2 = psi_plus<2>(sh, jp, p0, p1, cq_s, o);
+        psi[sh.psi_off + ql * sh.np + jp] = o;
+        mymax = fmax(mymax, a2);
+      }
+    }
+  for (int off = 16; off > 0; off >>= 1) mymax = fmax(mymax, __shfl_xor_sync(0xffffffffu, mymax, off));
+  if ((t & 31) == 0) atomic_max_nonneg(max2 + s, mymax);
+}
+
+}  // namespace
+
+cudaError_t launch_support_bbox(fga_plan_s* p, const double* u0, const double* u1) {
+  int n = p->nshots * p->grid.dim * 2;
+  k_bbox_init<<<(n + 255) / 256, 256, 0, p->stream>>>(p->d_bbox, n);
+  int64_t blocks = (p->grid.npts + 255) / 256;
+  if (blocks > 1024) blocks = 1024;
+  k_support_bbox<<<dim3((unsigned)blocks, p->nshots), 256, 0, p->stream>>>(p->grid, u0, u1,
+                                                                          p->d_bbox);
+  p->launches += 2;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fbi(fga_plan_s* p, const double* u0, const double* u1) {
+  cudaMemsetAsync(p->d_max2, 0, sizeof(unsigned long long) * p->nshots, p->stream);
+  int64_t maxM = 0, maxN = 0, maxQ = 0, maxTiles = 0;
+  const int D = p->grid.dim;
+  for (const auto& sh : p->shots) {
+    int64_t M = (D == 2) ? sh.nrows * sh.qn[1] : sh.qn[0];
+    if (sh.qn[0] == 0 || (D == 2 && sh.qn[1] == 0)) continue;
+    maxM = std::max(maxM, M);
+    maxN = std::max<int64_t>(maxN, sh.nb[D - 1]);
+    if (D == 2) {
+      maxQ = std::max(maxQ, sh.qn[0] * sh.qn[1]);
+      maxTiles = std::max<int64_t>(maxTiles, ((sh.nb[0] + BM - 1) / BM) * ((sh.nb[1] + BN - 1) / BN));
+    }
+  }
+  if (maxM == 0) return cudaSuccess;
+  dim3 g1grid((unsigned)((maxN + BN - 1) / BN), (unsigned)((maxM + BM - 1) / BM), p->nshots);
+  if (g1grid.y > 65535) return cudaErrorInvalidConfiguration;
+  if (D == 1) {
+    k_fbi_stage1<1><<<g1grid, NT, 0, p->stream>>>(p->grid, p->d_shots, u0, u1, p->d_coef, p->d_g1,
+                                                  p->d_psi, p->d_max2);
+    p->launches += 1;
+    return cudaGetLastError();
+  }
+  k_fbi_stage1<2><<<g1grid, NT, 0, p->stream>>>(p->grid, p->d_shots, u0, u1, p->d_coef, p->d_g1,
+                                                p->d_psi, p->d_max2);
+  if (maxQ > 65535) return cudaErrorInvalidConfiguration;
+  dim3 g2grid((unsigned)maxTiles, (unsigned)maxQ, p->nshots);
+  k_fbi_stage2<<<g2grid, NT, 0, p->stream>>>(p->grid, p->d_shots, p->d_coef, p->d_g1, p->d_psi,
+                                             p->d_max2);
+  p->launches += 2;
+  return cudaGetLastError();
+}
+
+}  // namespace fga

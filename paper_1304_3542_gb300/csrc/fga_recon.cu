@@ -1,0 +1,327 @@
+// Step 3 of the method: the Gaussian sum of Eq. recons on the output grid.
+//
+// Every term is cut to the window |x_k - Q_k| <= kappa sqrt(eps) on each axis and
+// is a product over axes,
+//   term(x) = coef * prod_k X_k(x_k),  X_k(xi) = sum_images exp(i P_k (xi - Q_k)/eps
+//                                                          - (xi - Q_k)^2/(2 eps)),
+// so the sum over the Gaussians that touch an output tile is a complex
+// contraction U = X^T diag(coef) Z over the Gaussian index (a GEMM of rank one
+// terms). Binning (K4) builds, per (shot, tile), the ordered list of Gaussians
+// whose window meets the tile; the gather (K5) runs one CTA per tile, generates
+// the per-axis factors of a chunk of Gaussians into shared memory and
+// accumulates the tile in registers, FP64 throughout. The scatter-free form
+// needs no atomics on the output and gives a deterministic summation order.
+#include "fga_internal.cuh"
+
+namespace fga {
+
+namespace {
+
+constexpr int NT = 256;
+constexpr int T2 = 64;   // 2D tile edge (points)
+constexpr int T1 = 256;  // 1D tile length
+constexpr int CH = 16;   // Gaussians per chunk (2D)
+constexpr int CH1 = 32;  // Gaussians per chunk (1D)
+
+__device__ __forceinline__ int shot_of_tile(const ShotDev* shots, int nshots, int64_t t) {
+  int lo = 0, hi = nshots - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (shots[mid].tile_off <= t) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// Window of Gaussian (Q, cut) along one axis as a conservative grid-index range,
+// for the image shifted by l periods.
+__device__ __forceinline__ void window_range(const GridDev& gd, int k, double Q, double cut,
+                                             int64_t& lo, int64_t& hi) {
+  lo = (int64_t)floor((Q - cut - gd.o[k]) * gd.inv_h[k]) - 1;
+  hi = (int64_t)ceil((Q + cut - gd.o[k]) * gd.inv_h[k]) + 1;
+}
+
+// Does the window of the Gaussian with centre Q meet the index box [a, b] on all axes?
+template <int D>
+__device__ __forceinline__ bool overlaps(const GridDev& gd, const double* Q, double cut,
+                                         const int64_t* a, const int64_t* b) {
+#pragma unroll
+  for (int k = 0; k < D; ++k) {
+    bool any = false;
+    int lmax = gd.periodic[k] ? 2 : 0;
+    for (int l = -lmax; l <= lmax; ++l) {
+      int64_t lo, hi;
+      window_range(gd, k, Q[k] + l * gd.L[k], cut, lo, hi);
+      any = any || (lo <= b[k] && hi >= a[k]);
+    }
+    if (!any) return false;
+  }
+  return true;
+}
+
+template <int D>
+__device__ __forceinline__ void tile_box(const GridDev& gd, const ShotDev& sh, int64_t tloc,
+                                         int64_t* a, int64_t* b) {
+  const int TS = (D == 1) ? T1 : T2;
+  int64_t t[D];
+  if constexpr (D == 1) {
+    t[0] = tloc;
+  } else {
+    t[0] = tloc / sh.ntile[1];
+    t[1] = tloc - t[0] * sh.ntile[1];
+  }
+#pragma unroll
+  for (int k = 0; k < D; ++k) {
+    a[k] = t[k] * TS;
+    b[k] = min(a[k] + TS - 1, gd.n[k] - 1);
+  }
+}
+
+// Pass 1 (FILL = false): number of Gaussians per tile. Pass 2 (FILL = true): the
+// ordered list, written at the tile's offset. One CTA per tile scans the shot's
+// Gaussians in order (block-wide ordered compaction per chunk of NT).
+template <int D, bool FILL>
+__global__ void __launch_bounds__(NT) k_bin(GridDev gd, const ShotDev* __restrict__ shots, int nshots,
+                                            double kappa, const double* __restrict__ state,
+                                            int64_t ld, int64_t* __restrict__ cnt,
+                                            const int64_t* __restrict__ off,
+                                            int32_t* __restrict__ list, int64_t list_cap,
+                                            int* __restrict__ status) {
+  const int64_t t = blockIdx.x;
+  const int s = shot_of_tile(shots, nshots, t);
+  const ShotDev& sh = shots[s];
+  int64_t a[D], b[D];
+  tile_box<D>(gd, sh, t - sh.tile_off, a, b);
+  const double cut = kappa * sh.sqrt_eps;
+  __shared__ int warp_tot[NT / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int64_t base = FILL ? off[t] : 0;
+  int64_t total = 0;
+  for (int64_t g0 = sh.g_off; g0 < sh.g_off + sh.g_cnt; g0 += NT) {
+    int64_t g = g0 + threadIdx.x;
+    bool f = false;
+    if (g < sh.g_off + sh.g_cnt) {
+      double Q[D];
+#pragma unroll
+      for (int k = 0; k < D; ++k) Q[k] = state[k * ld + g];
+      f = overlaps<D>(gd, Q, cut, a, b);
+    }
+    unsigned bal = __ballot_sync(0xffffffffu, f);
+    if (lane == 0) warp_tot[warp] = __popc(bal);
+    __syncthreads();
+    int before = 0, all = 0;
+    for (int w = 0; w < NT / 32; ++w) {
+      if (w < warp) before += warp_tot[w];
+      all += warp_tot[w];
+    }
+    if (FILL && f) {
+      int64_t at = base + total + before + __popc(bal & ((1u << lane) - 1u));
+      if (at < list_cap)
+        list[at] = (int32_t)g;
+      else
+        atomicOr(status, kStatusCapacity);
+    }
+    total += all;
+    __syncthreads();
+  }
+  if (!FILL && threadIdx.x == 0) cnt[t] = total;
+}
+
+// Per-axis factor of one Gaussian at grid index i (all images inside the window).
+__device__ __forceinline__ double2 axis_factor(const GridDev& gd, int k, int64_t i, double Q, double P,
+                                               double cut, double inv_eps) {
+  double x = gd.o[k] + (double)i * gd.h[k];
+  double re = 0.0, im = 0.0;
+  int lmax = gd.periodic[k] ? 2 : 0;
+  for (int l = -lmax; l <= lmax; ++l) {
+    double d = x - Q + l * gd.L[k];
+    if (fabs(d) <= cut) {
+      double gs = exp(-0.5 * d * d * inv_eps);
+      double sn, cs;
+      sincos(P * d * inv_eps, &sn, &cs);
+      re = fma(gs, cs, re);
+      im = fma(gs, sn, im);
+    }
+  }
+  return make_double2(re, im);
+}
+
+__global__ void __launch_bounds__(NT) k_recon1(GridDev gd, const ShotDev* __restrict__ shots,
+                                               int nshots, double kappa,
+                                               const double* __restrict__ state, int64_t ld,
+                                               const double2* __restrict__ coef,
+                                               const int64_t* __restrict__ off,
+                                               const int32_t* __restrict__ list, int64_t list_cap,
+                                               double* __restrict__ out) {
+  const int64_t t = blockIdx.x;
+  const int s = shot_of_tile(shots, nshots, t);
+  const ShotDev& sh = shots[s];
+  const double cut = kappa * sh.sqrt_eps, inv_eps = sh.inv_eps;
+  const int64_t i = (t - sh.tile_off) * T1 + threadIdx.x;
+  __shared__ double sQ[CH1], sP[CH1];
+  __shared__ double2 sC[CH1];
+  double re = 0.0;
+  const int64_t l0 = min(off[t], list_cap), l1 = min(off[t + 1], list_cap);
+  for (int64_t c0 = l0; c0 < l1; c0 += CH1) {
+    int nc = (int)((l1 - c0) < CH1 ? (l1 - c0) : CH1);
+    if (threadIdx.x < nc) {
+      int32_t g = list[c0 + threadIdx.x];
+      sQ[threadIdx.x] = state[0 * ld + g];
+      sP[threadIdx.x] = state[1 * ld + g];
+      sC[threadIdx.x] = coef[g];
+    }
+    __syncthreads();
+    if (i < gd.n[0]) {
+      for (int j = 0; j < nc; ++j) {
+        double2 x = axis_factor(gd, 0, i, sQ[j], sP[j], cut, inv_eps);
+        re = fma(sC[j].x, x.x, fma(-sC[j].y, x.y, re));
+      }
+    }
+    __syncthreads();
+  }
+  if (i < gd.n[0]) out[(int64_t)s * gd.npts + i] = re;
+}
+
+// 2D gather: 64 x 64 tile, 8 warps each covering a 16 x 32 patch (4 x 8 threads of
+// 4 x 4 points); a warp skips a Gaussian whose window misses its patch.
+__global__ void __launch_bounds__(NT) k_recon2(GridDev gd, const ShotDev* __restrict__ shots,
+                                               int nshots, double kappa,
+                                               const double* __restrict__ state, int64_t ld,
+                                               const double2* __restrict__ coef,
+                                               const int64_t* __restrict__ off,
+                                               const int32_t* __restrict__ list, int64_t list_cap,
+                                               double* __restrict__ out) {
+  const int64_t t = blockIdx.x;
+  const int s = shot_of_tile(shots, nshots, t);
+  const ShotDev& sh = shots[s];
+  const double cut = kappa * sh.sqrt_eps, inv_eps = sh.inv_eps;
+  int64_t a[2], b[2];
+  tile_box<2>(gd, sh, t - sh.tile_off, a, b);
+  __shared__ double2 Xs[CH][T2];
+  __shared__ double2 Zs[CH][T2];
+  __shared__ int win[CH][4];  // tile-local [xlo, xhi, zlo, zhi]
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int wx = warp >> 1, wz = warp & 1;
+  const int lx = lane >> 3, lz = lane & 7;
+  const int x0 = wx * 16 + lx * 4, z0 = wz * 32 + lz * 4;
+  const int px0 = wx * 16, px1 = wx * 16 + 15, pz0 = wz * 32, pz1 = wz * 32 + 31;
+  // only Re(sum) is needed: u = 2 Re(...) and the 2 is inside coef
+  double accr[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) accr[i][j] = 0.0;
+  const int64_t l0 = min(off[t], list_cap), l1 = min(off[t + 1], list_cap);
+  for (int64_t c0 = l0; c0 < l1; c0 += CH) {
+    const int nc = (int)((l1 - c0) < CH ? (l1 - c0) : CH);
+    // factor generation: thread -> (gaussian, axis, 8 consecutive points)
+    {
+      const int gi = threadIdx.x >> 4, axis = (threadIdx.x >> 3) & 1, part = threadIdx.x & 7;
+      if (gi < nc) {
+        int32_t g = list[c0 + gi];
+        double Q = state[axis * ld + g], P = state[(2 + axis) * ld + g];
+        double2 cf = axis == 0 ? coef[g] : make_double2(1.0, 0.0);
+        double2* dst = axis == 0 ? Xs[gi] : Zs[gi];
+#pragma unroll 2
+        for (int r = 0; r < 8; ++r) {
+          int li = part * 8 + r;
+          double2 f = axis_factor(gd, axis, a[axis] + li, Q, P, cut, inv_eps);
+          dst[li] = make_double2(cf.x * f.x - cf.y * f.y, cf.x * f.y + cf.y * f.x);
+        }
+        if (part == 0) {
+          if (gd.periodic[axis]) {
+            win[gi][2 * axis] = 0;
+            win[gi][2 * axis + 1] = T2 - 1;
+          } else {
+            int64_t lo, hi;
+            window_range(gd, axis, Q, cut, lo, hi);
+            win[gi][2 * axis] = (int)((lo - a[axis]) > -1 ? (lo - a[axis]) : -1);
+            win[gi][2 * axis + 1] = (int)((hi - a[axis]) < T2 ? (hi - a[axis]) : T2);
+          }
+        }
+      }
+    }
+    __syncthreads();
+    for (int gi = 0; gi < nc; ++gi) {
+      if (win[gi][0] > px1 || win[gi][1] < px0 || win[gi][2] > pz1 || win[gi][3] < pz0) continue;
+      double2 xv[4], zv[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        xv[i] = Xs[gi][x0 + i];
+        zv[i] = Zs[gi][z0 + i];
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          accr[i][j] = fma(xv[i].x, zv[j].x, fma(-xv[i].y, zv[j].y, accr[i][j]));
+        }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    int64_t ix = a[0] + x0 + i;
+    if (ix > b[0]) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      int64_t iz = a[1] + z0 + j;
+      if (iz > b[1]) continue;
+      out[(int64_t)s * gd.npts + ix * gd.n[1] + iz] = accr[i][j];
+    }
+  }
+}
+
+}  // namespace
+
+// Counts per tile, then the exclusive scan; *needed_pairs is not known until the
+// caller reads d_tile_off[ntiles] back.
+cudaError_t launch_binning(fga_plan_s* p, size_t* needed_pairs) {
+  (void)needed_pairs;
+  if (p->ntiles == 0) return cudaSuccess;
+  if (p->grid.dim == 1)
+    k_bin<1, false><<<(unsigned)p->ntiles, NT, 0, p->stream>>>(
+        p->grid, p->d_shots, p->nshots, p->kappa, p->d_state, (int64_t)p->g_cap, p->d_tile_off,
+        nullptr, nullptr, 0, p->d_status);
+  else
+    k_bin<2, false><<<(unsigned)p->ntiles, NT, 0, p->stream>>>(
+        p->grid, p->d_shots, p->nshots, p->kappa, p->d_state, (int64_t)p->g_cap, p->d_tile_off,
+        nullptr, nullptr, 0, p->d_status);
+  p->launches += 1;
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return launch_scan(p, p->d_tile_off, p->ntiles);
+}
+
+cudaError_t launch_binning_fill(fga_plan_s* p) {
+  if (p->ntiles == 0) return cudaSuccess;
+  if (p->grid.dim == 1)
+    k_bin<1, true><<<(unsigned)p->ntiles, NT, 0, p->stream>>>(
+        p->grid, p->d_shots, p->nshots, p->kappa, p->d_state, (int64_t)p->g_cap, nullptr,
+        p->d_tile_off, p->d_tile_list, (int64_t)p->list_cap, p->d_status);
+  else
+    k_bin<2, true><<<(unsigned)p->ntiles, NT, 0, p->stream>>>(
+        p->grid, p->d_shots, p->nshots, p->kappa, p->d_state, (int64_t)p->g_cap, nullptr,
+        p->d_tile_off, p->d_tile_list, (int64_t)p->list_cap, p->d_status);
+  p->launches += 1;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_reconstruct(fga_plan_s* p, double* u_dev) {
+  if (p->ntiles == 0) return cudaSuccess;
+  if (p->grid.dim == 1)
+    k_recon1<<<(unsigned)p->ntiles, NT, 0, p->stream>>>(p->grid, p->d_shots, p->nshots, p->kappa,
+                                                        p->d_state, (int64_t)p->g_cap, p->d_gcoef,
+                                                        p->d_tile_off, p->d_tile_list,
+                                                        (int64_t)p->list_cap, u_dev);
+  else
+    k_recon2<<<(unsigned)p->ntiles, NT, 0, p->stream>>>(p->grid, p->d_shots, p->nshots, p->kappa,
+                                                        p->d_state, (int64_t)p->g_cap, p->d_gcoef,
+                                                        p->d_tile_off, p->d_tile_list,
+                                                        (int64_t)p->list_cap, u_dev);
+  p->launches += 1;
+  return cudaGetLastError();
+}
+
+int tile_edge(int dim) { return dim == 1 ? T1 : T2; }
+
+}  // namespace fga

@@ -1,0 +1,208 @@
+// Choice of the set G+ (thresholding paragraph of the Initial wavefield
+// decomposition section): every valid (q,p) with |psi+| >= tau * max|psi+| is
+// kept. Because the p-grid is symmetric and the data real, max|psi+| over the
+// + branch equals the maximum over both branches.
+//
+// Deterministic stream compaction in three passes over the psi+ segments
+// (each shot's segment is padded to whole blocks of kScanBlock entries):
+// count per block, one exclusive scan over the blocks, and an ordered scatter
+// that keeps the (q, p) order of the segment. The Gaussian list therefore comes
+// out shot-major, q-major, p-minor, whatever the launch order.
+#include "fga_internal.cuh"
+
+namespace fga {
+
+namespace {
+
+constexpr int NT = 256;
+constexpr int PER = kScanBlock / NT;  // entries per thread
+
+__device__ __forceinline__ int shot_of_block(const ShotDev* shots, int nshots, int64_t e) {
+  int lo = 0, hi = nshots - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (shots[mid].psi_off <= e) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+template <int D>
+__device__ __forceinline__ bool p_valid(const ShotDev& sh, int64_t jp) {
+  if constexpr (D == 1) {
+    return jp != 0 && jp != sh.nb[0] / 2;
+  } else {
+    int64_t j0 = jp / sh.nb[1], j1 = jp - j0 * sh.nb[1];
+    return j0 != 0 && j1 != 0 && !(j0 == sh.nb[0] / 2 && j1 == sh.nb[1] / 2);
+  }
+}
+
+template <int D>
+__device__ __forceinline__ bool keep(const ShotDev& sh, const double2* psi, int64_t e, double thr2) {
+  int64_t loc = e - sh.psi_off;
+  if (loc < 0 || loc >= sh.psi_len) return false;
+  int64_t jp = loc % sh.np;
+  if (!p_valid<D>(sh, jp)) return false;
+  double2 v = psi[e];
+  return v.x * v.x + v.y * v.y >= thr2;
+}
+
+template <int D>
+__global__ void __launch_bounds__(NT) k_select_count(const ShotDev* __restrict__ shots, int nshots,
+                                                     const double2* __restrict__ psi,
+                                                     const unsigned long long* __restrict__ max2,
+                                                     double tau2, int64_t* blk) {
+  int64_t base = (int64_t)blockIdx.x * kScanBlock;
+  int s = shot_of_block(shots, nshots, base);
+  const ShotDev& sh = shots[s];
+  double thr2 = tau2 * __longlong_as_double((long long)max2[s]);
+  int c = 0;
+  for (int i = 0; i < PER; ++i) c += keep<D>(sh, psi, base + threadIdx.x + NT * i, thr2) ? 1 : 0;
+  __shared__ int red[NT / 32];
+  for (int off = 16; off > 0; off >>= 1) c += __shfl_xor_sync(0xffffffffu, c, off);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = c;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int sum = 0;
+    for (int w = 0; w < NT / 32; ++w) sum += red[w];
+    blk[blockIdx.x] = sum;
+  }
+}
+
+// Exclusive scan of n int64 values in place; a[n] receives the total. One block.
+__global__ void __launch_bounds__(1024) k_scan_exclusive(int64_t* a, int64_t n) {
+  __shared__ int64_t warp_sums[32];
+  __shared__ int64_t carry;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int64_t base = 0; base < n; base += 1024) {
+    int64_t i = base + threadIdx.x;
+    int64_t v = (i < n) ? a[i] : 0;
+    int64_t x = v;
+    for (int off = 1; off < 32; off <<= 1) {
+      int64_t y = __shfl_up_sync(0xffffffffu, x, off);
+      if (lane >= off) x += y;
+    }
+    if (lane == 31) warp_sums[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+      int64_t w = warp_sums[lane];
+      for (int off = 1; off < 32; off <<= 1) {
+        int64_t y = __shfl_up_sync(0xffffffffu, w, off);
+        if (lane >= off) w += y;
+      }
+      warp_sums[lane] = w;
+    }
+    __syncthreads();
+    int64_t excl = x - v + (warp > 0 ? warp_sums[warp - 1] : 0) + carry;
+    if (i < n) a[i] = excl;
+    __syncthreads();
+    if (threadIdx.x == 1023) carry = excl + v;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) a[n] = carry;
+}
+
+template <int D>
+__global__ void __launch_bounds__(NT) k_select_scatter(const ShotDev* __restrict__ shots, int nshots,
+                                                       const double2* __restrict__ psi,
+                                                       const unsigned long long* __restrict__ max2,
+                                                       double tau2, const int64_t* __restrict__ blk,
+                                                       int32_t* gshot, int64_t* gq, int32_t* gp,
+                                                       double2* gpsi) {
+  int64_t base = (int64_t)blockIdx.x * kScanBlock;
+  int s = shot_of_block(shots, nshots, base);
+  const ShotDev& sh = shots[s];
+  double thr2 = tau2 * __longlong_as_double((long long)max2[s]);
+  // thread t owns PER consecutive entries, so the block order is the entry order
+  int64_t e0 = base + (int64_t)threadIdx.x * PER;
+  bool f[PER];
+  int c = 0;
+  for (int i = 0; i < PER; ++i) {
+    f[i] = keep<D>(sh, psi, e0 + i, thr2);
+    c += f[i] ? 1 : 0;
+  }
+  __shared__ int warp_tot[NT / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int x = c;
+  for (int off = 1; off < 32; off <<= 1) {
+    int y = __shfl_up_sync(0xffffffffu, x, off);
+    if (lane >= off) x += y;
+  }
+  if (lane == 31) warp_tot[warp] = x;
+  __syncthreads();
+  int wbase = 0;
+  for (int w = 0; w < warp; ++w) wbase += warp_tot[w];
+  int64_t pos = blk[blockIdx.x] + wbase + (x - c);
+  for (int i = 0; i < PER; ++i) {
+    if (!f[i]) continue;
+    int64_t loc = e0 + i - sh.psi_off;
+    int64_t ql = loc / sh.np, jp = loc - ql * sh.np;
+    int64_t qflat;
+    if constexpr (D == 1) {
+      qflat = sh.qlo[0] + ql;
+    } else {
+      int64_t mxl = ql / sh.qn[1], mzl = ql - mxl * sh.qn[1];
+      qflat = (sh.qlo[0] + mxl) * sh.nq[1] + (sh.qlo[1] + mzl);
+    }
+    gshot[pos] = s;
+    gq[pos] = qflat;
+    gp[pos] = (int32_t)jp;
+    gpsi[pos] = psi[e0 + i];
+    ++pos;
+  }
+}
+
+// Per-shot Gaussian segment [g_off, g_off + g_cnt) from the scanned block offsets.
+__global__ void k_select_counts(ShotDev* shots, int nshots, const int64_t* blk,
+                                const int64_t* blk_first, int64_t* counts) {
+  int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= nshots) return;
+  int64_t a = blk[blk_first[s]], b = blk[blk_first[s + 1]];
+  shots[s].g_off = a;
+  shots[s].g_cnt = b - a;
+  counts[s] = b - a;
+}
+
+}  // namespace
+
+// Pass 1 + scan: block counts and offsets; per-shot counts to p->d_counts.
+cudaError_t launch_select_count(fga_plan_s* p) {
+  const int64_t* d_blk_first = p->d_blk_first;
+  double tau2 = p->tau * p->tau;
+  if (p->nblocks == 0) return cudaSuccess;
+  if (p->grid.dim == 1)
+    k_select_count<1><<<(unsigned)p->nblocks, NT, 0, p->stream>>>(p->d_shots, p->nshots, p->d_psi,
+                                                                   p->d_max2, tau2, p->d_blk);
+  else
+    k_select_count<2><<<(unsigned)p->nblocks, NT, 0, p->stream>>>(p->d_shots, p->nshots, p->d_psi,
+                                                                   p->d_max2, tau2, p->d_blk);
+  k_scan_exclusive<<<1, 1024, 0, p->stream>>>(p->d_blk, p->nblocks);
+  k_select_counts<<<(p->nshots + 127) / 128, 128, 0, p->stream>>>(p->d_shots, p->nshots, p->d_blk,
+                                                                  d_blk_first, p->d_counts);
+  p->launches += 3;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_select(fga_plan_s* p) {
+  double tau2 = p->tau * p->tau;
+  if (p->nblocks == 0) return cudaSuccess;
+  if (p->grid.dim == 1)
+    k_select_scatter<1><<<(unsigned)p->nblocks, NT, 0, p->stream>>>(
+        p->d_shots, p->nshots, p->d_psi, p->d_max2, tau2, p->d_blk, p->d_gshot, p->d_gq, p->d_gp,
+        p->d_gpsi);
+  else
+    k_select_scatter<2><<<(unsigned)p->nblocks, NT, 0, p->stream>>>(
+        p->d_shots, p->nshots, p->d_psi, p->d_max2, tau2, p->d_blk, p->d_gshot, p->d_gq, p->d_gp,
+        p->d_gpsi);
+  p->launches += 1;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scan(fga_plan_s* p, int64_t* a, int64_t n) {
+  k_scan_exclusive<<<1, 1024, 0, p->stream>>>(a, n);
+  p->launches += 1;
+  return cudaGetLastError();
+}
+
+}  // namespace fga

@@ -1,0 +1,86 @@
+"""The C ABI library loads, exports every entry point include/fga.h declares, and
+rejects bad configurations on the host (no GPU needed for any of this)."""
+
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_1304_3542_gb300 import fga as F
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if not fn.endswith(".h"):
+            continue
+        src = open(os.path.join(ROOT, "include", fn)).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        src = re.sub(r"//[^\n]*", "", src)
+        for m in re.finditer(r"\b(fga_\w+)\s*\(", src):
+            names.add(m.group(1))
+    return sorted(names)
+
+
+def test_library_exports_every_declared_symbol():
+    lib = F.load()
+    names = declared_functions()
+    assert "fga_plan" in names and "fga_reconstruct" in names
+    missing = [n for n in names if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_status_strings():
+    lib = F.load()
+    for code in range(8):
+        assert lib.fga_status_string(code)
+    assert lib.fga_status_string(1) == b"invalid argument"
+
+
+def _plan(**kw):
+    args = dict(dim=2, n=(16, 16), h=(0.1, 0.1), origin=(0.0, 0.0), periodic=(False, False),
+                velocity=np.ones(256), eps=[0.01], T=1.0, dt=0.1, kappa=6.0, tau=1e-3)
+    args.update(kw)
+    return F.Plan(**args)
+
+
+@pytest.mark.parametrize("kw, msg", [
+    (dict(dt=0.3), "T/dt"),
+    (dict(dim=3, n=(4, 4, 4), h=(1, 1, 1), origin=(0, 0, 0), periodic=(0, 0, 0),
+          velocity=np.ones(64)), "dim"),
+    (dict(eps=[-1.0]), "eps"),
+    (dict(eps=[float("nan")]), "eps"),
+    (dict(kappa=0.0), "kappa"),
+    (dict(tau=-1.0), "tau"),
+    (dict(h=(0.0, 0.1)), "spacing"),
+    (dict(n=(2, 16), velocity=np.ones(32)), "grid size"),
+    (dict(box=[[7, 8]]), "box"),
+    (dict(periodic=(True, False), box=[[8, 32]], q_stride=[[2, 2]]), "periodic"),
+    (dict(precision=F.FGA_MIXED_BF16X3), "FGA_FP64"),
+])
+def test_invalid_configurations_are_rejected_on_the_host(kw, msg):
+    with pytest.raises(F.FGAError) as ei:
+        _plan(**kw)
+    assert ei.value.status == 1  # FGA_ERR_INVALID
+    assert msg in str(ei.value)
+
+
+def test_null_arguments():
+    lib = F.load()
+    out = ctypes.c_void_p()
+    assert lib.fga_plan(None, None, None, ctypes.byref(out)) == 1
+    assert lib.fga_plan(None, None, None, None) == 1
+    assert lib.fga_destroy(None) == 0
+    assert lib.fga_count(None, 0) == -1
+    assert lib.fga_decompose(None, None, None, None) == 1
+
+
+def test_wrong_dtype_and_size_rejected_in_binding():
+    with pytest.raises(TypeError):
+        _plan(velocity=np.ones(256, dtype=np.float32))
+    with pytest.raises(ValueError):
+        _plan(velocity=np.ones(255))
