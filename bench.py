@@ -1,0 +1,420 @@
+#!/usr/bin/env python3
+"""Throughput of the FGA hot path on one GB300: Gaussian.gridpoint evaluations per second.
+
+One step = the whole path on one batch of synthetic input: decompose (FBI,
+branch split, thresholding), propagate (RK4 rays, dynamic rays, amplitude,
+action) and reconstruct (binning + gather on the grid). The workload is the
+layered model (737 x 241 at 12.5 m, 12 dipping layers, 3 faults, smoothed),
+one 15 Hz Ricker-ring source at 10 m depth, eps from 15 Hz, T = 2 s, dt = 1 ms,
+tau = 1e-3, kappa = 6.
+
+A Gaussian.gridpoint evaluation is one (Gaussian, grid point) pair inside the
+Gaussian's kappa*sqrt(eps) square window, counted over both branches of the
+method (the GPU evaluates the + branch and obtains the - branch as its complex
+conjugate).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank runs its own replica of the workload (the
+shots are independent problems, no collective on the data path); value is the
+evaluations of all ranks divided by the slowest rank's time. --impl reference
+times the FP64 CPU oracle on the host cores on a bounded sample of the same
+workload (rank 0 only).
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "FGA Gaussian·gridpoint evals/s and rel-L2 err; mixed-prec vs FP64, 1 GB300"
+UNIT = "evals/s"
+L2_FLUSH_BYTES = 256 << 20
+# FP64 operations of one RK4 ray step in 2D, counted from the source of the ray
+# kernel (add/sub/mul/div/rsqrt = 1, fma = 2): 4 right-hand sides of 460 (spline
+# weights 76, 4x4 tap contraction 144, derivative scaling 8, ray and dynamic-ray
+# algebra 145, tr(Z^-1 dZ/dt) with da/dt 81, dS/dt 6) plus 322 for the stage
+# combinations of the 23 state values.
+FLOPS_PER_RAY_STEP_2D = 2162
+# FP64 peak from the unit counts and clocks: 152 SMs x 2 DFMA/clk/SM x 2 flop x 2.07 GHz
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+
+
+def workload():
+    from paper_1304_3542_gb300 import workloads as WL
+
+    return WL.layered_single()
+
+
+def workload_name(prob):
+    sh = prob.shots[0]
+    return ("layered model %dx%d at %.1f m, 1 shot %g Hz Ricker ring at (%.2f, %.2f) km, "
+            "T=%g s, dt=%g s" % (prob.n[0], prob.n[1], prob.h[0] * 1000, sh.freq, sh.source[0],
+                                  sh.source[1], prob.T, prob.dt))
+
+
+def window_evals(prob, Q, eps):
+    """Grid points inside the kappa sqrt(eps) square window of each centre, summed."""
+    cut = prob.kappa * math.sqrt(eps)
+    tot = np.ones(Q.shape[0])
+    for k in range(prob.dim):
+        lo = np.ceil((Q[:, k] - cut - prob.origin[k]) / prob.h[k])
+        hi = np.floor((Q[:, k] + cut - prob.origin[k]) / prob.h[k])
+        lo = np.clip(lo, 0, prob.n[k] - 1)
+        hi = np.clip(hi, 0, prob.n[k] - 1)
+        cnt = np.where((Q[:, k] + cut >= prob.origin[k]) &
+                       (Q[:, k] - cut <= prob.origin[k] + (prob.n[k] - 1) * prob.h[k]),
+                       hi - lo + 1, 0)
+        tot *= np.maximum(cnt, 0)
+    return float(tot.sum())
+
+
+def source_hash(files):
+    h = hashlib.sha256()
+    for f in files:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic():
+    """DRAM bytes per launch of the ray kernel from the committed ncu summary, if it was
+    taken on the kernel source as it is now (else None)."""
+    path = os.path.join(ROOT, "profiles", "k_rays_layered_single.json")
+    if not os.path.exists(path):
+        return None
+    try:
+        rec = json.load(open(path))
+        cur = source_hash(rec["sources"])
+        if rec.get("source_hash") != cur:
+            return None
+        return rec.get("dram_bytes_per_launch")
+    except Exception:
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.QUERY,
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+                out = ""
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in getattr(self, "lines", []):
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for name, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+
+    from paper_1304_3542_gb300 import fga as F
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    prob = workload()
+    stream = torch.cuda.current_stream(dev)
+    plan = F.plan_from_problem(prob, stream=stream.cuda_stream)
+    u0, u1 = F.stacked_initial_data(prob)
+    d_u0 = torch.from_numpy(u0).to(dev)
+    d_u1 = torch.from_numpy(u1).to(dev)
+    d_out = torch.zeros((1,) + prob.n, dtype=torch.float64, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def step(a, b, out):
+        plan.decompose(a, b)
+        plan.propagate()
+        plan.reconstruct(out)
+
+    # first pass: Gaussian count and algorithmic evaluation count of the workload
+    step(d_u0, d_u1, d_out)
+    plan.sync()
+    G = plan.count(0)
+    st = plan.state(0)
+    evals_plus = window_evals(prob, st["Q"], prob.shots[0].eps)
+    evals = 2.0 * evals_plus
+    for _ in range(args.warmup):
+        step(d_u0, d_u1, d_out)
+    plan.sync()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize(dev)
+    _, launches0 = plan.stage_times()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ray_ms, recon_ms, fbi_ms = [], [], []
+    with ClockSampler(local_rank) as clk:
+        t0 = time.perf_counter()
+        for i in range(args.steps):
+            flush.fill_(float(i))  # L2 flush between timed steps (outside the events)
+            starts[i].record(stream)
+            step(d_u0, d_u1, d_out)
+            ends[i].record(stream)
+            stt, _ = plan.stage_times()
+            ray_ms.append(stt["rays"])
+            recon_ms.append(stt["reconstruct"] + stt["binning"])
+            fbi_ms.append(stt["fbi"])
+        torch.cuda.synchronize(dev)
+        wall = time.perf_counter() - t0
+    _, launches1 = plan.stage_times()
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    total_s = sum(step_ms) / 1e3
+    if world > 1:
+        t = torch.tensor([total_s], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_s = float(t.item())
+    value = world * evals * args.steps / total_s
+    ms_per_step = total_s * 1e3 / args.steps
+
+    # end to end through the C ABI with host buffers (pinned), copies inside the timing
+    h_u0 = torch.from_numpy(u0).pin_memory()
+    h_u1 = torch.from_numpy(u1).pin_memory()
+    h_out = torch.empty((1,) + prob.n, dtype=torch.float64).pin_memory()
+    e2e_times = []
+    for i in range(args.steps):
+        flush.fill_(float(i))
+        torch.cuda.synchronize(dev)
+        t1 = time.perf_counter()
+        step(h_u0, h_u1, h_out)  # reconstruct into host memory waits for the copy
+        e2e_times.append(time.perf_counter() - t1)
+    e2e_s = sum(e2e_times)
+    if world > 1:
+        t = torch.tensor([e2e_s], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e_value = world * evals * args.steps / e2e_s
+    npts = prob.npoints
+
+    ray_s = statistics.mean(ray_ms) / 1e3
+    ray_flops = FLOPS_PER_RAY_STEP_2D * prob.nsteps * G
+    achieved = ray_flops / ray_s / 1e12
+    clocks = clk.summary()
+    line = {
+        "metric": METRIC,
+        "value": value,
+        "unit": UNIT,
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms_per_step,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64",
+        "data": "synthetic (seeded layered model and Ricker ring; no dataset)",
+        "config": {
+            "workload": workload_name(prob),
+            "grid": list(prob.n),
+            "eps_km": prob.shots[0].eps,
+            "q_stride": list(prob.shots[0].q_stride),
+            "box": list(prob.shots[0].box),
+            "tau": prob.tau,
+            "kappa": prob.kappa,
+            "gaussians_plus_branch": G,
+            "evals_per_step_both_branches": evals,
+            "precision": "fp64",
+            "stage_ms_mean": {"fbi": statistics.mean(fbi_ms), "rays": statistics.mean(ray_ms),
+                              "binning+reconstruct": statistics.mean(recon_ms)},
+            "l2": "256 MiB buffer written between timed steps",
+            "parallelism": "replicas" if world > 1 else "single GPU",
+            "wall_s_timed_region": wall,
+        },
+        "roofline": {
+            "kernel": "k_rays<2> (RK4 rays, dynamic rays, amplitude, action)",
+            "bound": "alu",
+            "achieved": achieved,
+            "peak": FP64_PEAK_TFLOPS,
+            "unit": "TFLOP/s",
+            "frac": achieved / FP64_PEAK_TFLOPS,
+            "traffic": ncu_traffic(),
+            "flops_per_launch": ray_flops,
+            "peak_source": "FP64 from unit counts and clock (152 SM x 2 DFMA/clk x 2.07 GHz)",
+        },
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 2 * 8 * npts,
+                "d2h_bytes_per_step": 8 * npts},
+        "gpu_launches": int(launches1 - launches0),
+        "clocks": clocks,
+    }
+    plan.close()
+    return line, prob, evals
+
+
+def oracle_sample(prob, n_sample, nthreads):
+    """One bounded oracle pass: the full decomposition, then n_sample Gaussians (half
+    of each branch) propagated to T and summed on every grid point. Returns
+    (estimated seconds for the whole workload, description, evals of the workload)."""
+    import oracle as O
+
+    sh = prob.shots[0]
+    g = O.Grid(prob.n, prob.h, prob.origin, prob.periodic)
+    nz = (sh.u0 != 0) | (sh.u1 != 0)
+    nq = O.q_counts(g, sh.q_stride)
+    keep = []
+    for k in range(prob.dim):
+        other = tuple(a for a in range(prob.dim) if a != k)
+        idx = np.flatnonzero(np.any(nz, axis=other))
+        m = np.arange(nq[k]) * sh.q_stride[k]
+        keep.append((m - sh.box[k] // 2 <= idx.max()) & (m + sh.box[k] // 2 - 1 >= idx.min()))
+    mesh = np.meshgrid(*keep, indexing="ij")
+    rows = np.flatnonzero(np.logical_and.reduce([x.ravel() for x in mesh]))
+    t0 = time.perf_counter()
+    dec = O.decompose(g, prob.velocity, sh.u0, sh.u1, sh.eps, sh.q_stride, sh.box, prob.tau,
+                      q_subset=rows)
+    t_dec = time.perf_counter() - t0
+    gs = dec["gauss"]
+    G2 = gs["sigma"].size
+    rng = np.random.default_rng(1304)
+    pick = np.concatenate([rng.choice(np.flatnonzero(gs["sigma"] == s), n_sample // 2,
+                                      replace=False) for s in (1, -1)])
+    t0 = time.perf_counter()
+    st = O.propagate(g, prob.velocity, prob.nsteps, prob.dt, gs["sigma"][pick], gs["q"][pick],
+                     gs["p"][pick], nthreads)
+    t_prop = time.perf_counter() - t0
+    W = O.quadrature_weight(g, sh.eps, sh.q_stride, sh.box)
+    t0 = time.perf_counter()
+    O.reconstruct(g, sh.eps, prob.kappa, W, st["Q"], st["P"], st["a"], gs["psi"][pick], st["S"],
+                  prob.grid_points(), nthreads)
+    t_rec = time.perf_counter() - t0
+    scale = G2 / pick.size
+    est = t_dec + scale * (t_prop + t_rec)
+    evals_sample = window_evals(prob, st["Q"], sh.eps)
+    evals = evals_sample * scale
+    desc = ("full decomposition (%.1f s) + %d of %d Gaussians propagated %d steps (%.1f s) and "
+            "summed on all %d grid points (%.1f s), time scaled by %.0fx"
+            % (t_dec, pick.size, G2, prob.nsteps, t_prop, prob.npoints, t_rec, scale))
+    return est, desc, evals, t_dec + t_prop + t_rec
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return None
+    prob = workload()
+    cores = os.cpu_count() or 1
+    vals = []
+    for i in range(args.warmup + args.steps):
+        est, desc, evals, spent = oracle_sample(prob, 256, cores)
+        if i >= args.warmup:
+            vals.append(evals / est)
+    value = statistics.mean(vals)
+    return {
+        "impl": "reference",
+        "metric": METRIC,
+        "value": value,
+        "unit": UNIT,
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": None,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64",
+        "data": "synthetic (seeded layered model and Ricker ring; no dataset)",
+        "config": {"workload": workload_name(prob), "precision": "fp64",
+                   "parallelism": "CPU oracle, OpenMP over Gaussians / grid points"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": desc},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample", type=int, default=512)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be at least 3")
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+
+        if args.impl == "ours":
+            torch.cuda.set_device(local_rank)
+            dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+        else:
+            dist.init_process_group("gloo")
+    if args.impl == "reference":
+        line = run_reference(args, rank, world)
+        if line is not None:
+            print(json.dumps(line), flush=True)
+        if world > 1:
+            import torch.distributed as dist
+
+            dist.destroy_process_group()
+        return
+    line, prob, evals = run_ours(args, rank, world, local_rank)
+    if rank == 0:
+        if world == 1 and not args.no_cpu_baseline:
+            cores = os.cpu_count() or 1
+            est, desc, ev_o, spent = oracle_sample(prob, args.cpu_sample, cores)
+            line["cpu_baseline"] = {"value": ev_o / est, "unit": UNIT, "cores": cores,
+                                    "kind": "oracle", "sample": desc}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -215,14 +215,15 @@ def window_axis(grid: Grid, eps: float, box: Sequence[int], k: int) -> np.ndarra
 
 
 def fbi(grid: Grid, f: np.ndarray, eps: float, stride: Sequence[int], box: Sequence[int],
-        q_chunk: int = 256) -> np.ndarray:
+        q_chunk: int = 256, q_subset: Optional[np.ndarray] = None) -> np.ndarray:
     """psi(q, p) for every q on the q-grid and every p on the box DFT grid
     (Initial wavefield decomposition section):
         psi(q, p) = prod_k h_k * sum_{j in box} f(q + r_j) w(r_j) e^{-i p.r_j/eps},
     evaluated per q as the FFT of g_q = f(q + r) w(r) on the box. With
     p_m r_j/eps = 2 pi m (j - n_b/2)/n_b the phase is e^{-2 pi i m j/n_b} (-1)^m,
     so psi(q, p_m) = prod h * (-1)^m * FFT(g_q)[m mod n_b].
-    Returns a complex array [n_q total][n_p total], p in C order over j = m + n_b/2."""
+    Returns a complex array [n_q total][n_p total], p in C order over j = m + n_b/2;
+    with q_subset (flat q-grid indices) only those rows, in that order."""
     d = grid.dim
     f = _f64(f).reshape(tuple(int(v) for v in grid.n))
     nq = q_counts(grid, stride)
@@ -250,8 +251,10 @@ def fbi(grid: Grid, f: np.ndarray, eps: float, stride: Sequence[int], box: Seque
     hv = float(np.prod(grid.h))
     nqt = int(np.prod(nq))
     npt = int(np.prod(box))
-    out = np.empty((nqt, npt), dtype=np.complex128)
-    qmulti = np.stack(np.unravel_index(np.arange(nqt), tuple(nq)), axis=1)
+    rows = np.arange(nqt) if q_subset is None else np.asarray(q_subset, dtype=np.int64)
+    out = np.empty((rows.size, npt), dtype=np.complex128)
+    qmulti = np.stack(np.unravel_index(rows, tuple(nq)), axis=1)
+    nqt = rows.size
     for start in range(0, nqt, q_chunk):
         qs = qmulti[start:start + q_chunk]
         B = qs.shape[0]
@@ -300,10 +303,12 @@ def fbi_direct(grid: Grid, f: np.ndarray, eps: float, box: Sequence[int], qi: np
 
 
 def branch_split(grid: Grid, coef: np.ndarray, eps: float, stride, box, psi0: np.ndarray,
-                 psi1: np.ndarray):
+                 psi1: np.ndarray, q_subset: Optional[np.ndarray] = None):
     """psi+- = 1/2 (psi0 +- i eps psi1/(c(q)|p|)) (Eq. psi, u+-,0), on valid (q,p) only;
     zero on the left-out p values. Returns (psi_plus, psi_minus, valid_mask[n_p])."""
     qpts = q_points(grid, stride)
+    if q_subset is not None:
+        qpts = qpts[np.asarray(q_subset, dtype=np.int64)]
     cq, _, _, _ = medium_eval(grid, coef, qpts, order=0)
     pp = p_points(grid, eps, box)
     pn = np.sqrt(np.sum(pp * pp, axis=1))
@@ -397,28 +402,32 @@ def reconstruct(grid: Grid, eps: float, kappa: float, W: float, Q, P, a, psi, S,
 # The whole algorithm for one set of initial data
 # ---------------------------------------------------------------------------
 
-def decompose(grid: Grid, coef, f0, f1, eps, stride, box, tau, keep_n=0):
-    psi0 = fbi(grid, f0, eps, stride, box)
-    psi1 = fbi(grid, f1, eps, stride, box)
-    plus, minus, valid = branch_split(grid, coef, eps, stride, box, psi0, psi1)
+def decompose(grid: Grid, coef, f0, f1, eps, stride, box, tau, keep_n=0, q_subset=None):
+    """Step 1. With q_subset (flat q indices), psi is computed for those q only: the
+    rows left out are taken as psi = 0 (exact when their boxes hold no data)."""
+    psi0 = fbi(grid, f0, eps, stride, box, q_subset=q_subset)
+    psi1 = fbi(grid, f1, eps, stride, box, q_subset=q_subset)
+    plus, minus, valid = branch_split(grid, coef, eps, stride, box, psi0, psi1, q_subset)
     sel_p, sel_m, M = select(plus, minus, valid, tau, keep_n)
     npt = plus.shape[1]
     qpts = q_points(grid, stride)
     ppts = p_points(grid, eps, box)
+    rows = np.arange(qpts.shape[0]) if q_subset is None else np.asarray(q_subset, dtype=np.int64)
     gs = []
     for sigma, sel, arr in ((1, sel_p, plus), (-1, sel_m, minus)):
-        qi, pi = np.divmod(sel, npt)
+        ri, pi = np.divmod(sel, npt)
+        qi = rows[ri]
         gs.append({"sigma": np.full(sel.size, sigma, dtype=np.int32), "qidx": qi, "pidx": pi,
                    "q": qpts[qi], "p": ppts[pi], "psi": arr.ravel()[sel]})
     gauss = {k: np.concatenate([gs[0][k], gs[1][k]]) for k in gs[0]}
     return {"psi0": psi0, "psi1": psi1, "psi_plus": plus, "psi_minus": minus, "valid": valid,
-            "M": M, "gauss": gauss}
+            "M": M, "gauss": gauss, "rows": rows}
 
 
 def fga(grid: Grid, coef, f0, f1, eps, stride, box, tau, kappa, nsteps, dt, x=None, keep_n=0,
-        nthreads=None) -> Dict[str, object]:
+        nthreads=None, q_subset=None) -> Dict[str, object]:
     """Decompose, propagate to nsteps*dt, reconstruct at x (default: the grid)."""
-    dec = decompose(grid, coef, f0, f1, eps, stride, box, tau, keep_n)
+    dec = decompose(grid, coef, f0, f1, eps, stride, box, tau, keep_n, q_subset)
     g = dec["gauss"]
     st = propagate(grid, coef, nsteps, dt, g["sigma"], g["q"], g["p"], nthreads)
     W = quadrature_weight(grid, eps, stride, box)

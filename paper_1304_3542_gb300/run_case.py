@@ -1,0 +1,57 @@
+"""Run one workload through libfga and print the Gaussian count and stage times.
+
+  python -m paper_1304_3542_gb300.run_case [--workload layered_single] [--T 0.1]
+                                           [--tau 1e-3] [--repeat 1] [--nshots 4]
+
+A small driver for trying the library on the seeded workloads (and the command
+the kernel profiles are taken with).
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+
+import numpy as np
+
+
+def main():
+    import torch
+
+    from . import fga as F
+    from . import workloads as WL
+
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--workload", default="layered_single",
+                    choices=["layered_single", "layered_batch", "lens_2d", "periodic_1d"])
+    ap.add_argument("--T", type=float, default=None)
+    ap.add_argument("--tau", type=float, default=None)
+    ap.add_argument("--nshots", type=int, default=4)
+    ap.add_argument("--repeat", type=int, default=1)
+    args = ap.parse_args()
+    kw = {}
+    if args.T is not None:
+        kw["T"] = args.T
+    if args.tau is not None:
+        kw["tau"] = args.tau
+    if args.workload == "layered_batch":
+        kw["nshots"] = args.nshots
+    prob = WL.by_name(args.workload, **kw)
+    plan = F.plan_from_problem(prob, stream=torch.cuda.current_stream().cuda_stream)
+    u0, u1 = F.stacked_initial_data(prob)
+    a, b = torch.from_numpy(u0).cuda(), torch.from_numpy(u1).cuda()
+    out = torch.zeros((len(prob.shots),) + prob.n, dtype=torch.float64, device="cuda")
+    for _ in range(args.repeat):
+        counts = plan.decompose(a, b)
+        plan.propagate()
+        plan.reconstruct(out)
+        plan.sync()
+    times, launches = plan.stage_times()
+    print(json.dumps({"workload": args.workload, "counts": counts.tolist(),
+                      "stage_ms": {k: float(v) for k, v in times.items()},
+                      "launches": launches, "field_norm": float(out.norm())}))
+    plan.close()
+
+
+if __name__ == "__main__":
+    main()

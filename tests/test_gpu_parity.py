@@ -1,0 +1,345 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Element by element at sizes the oracle finishes in seconds (several tiles and a
+ragged tail), and at the full sizes of the benchmark's workload on sampled
+outputs and on properties that hold at any size. Tolerances: rel-L2 <= 1e-10 for
+the field (FP64 path vs oracle), psi+ within 1e-12 of max|psi+|, ray states within
+1e-9 (relative for a), identical Gaussian sets outside a 1e-9 guard band around
+the threshold (set membership is discontinuous in |psi|).
+"""
+
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1304_3542_gb300 import fga as F
+from paper_1304_3542_gb300 import workloads as WL
+
+pytestmark = pytest.mark.gpu
+
+FIELD_TOL = 1e-10
+
+
+def _torch():
+    import torch
+
+    return torch
+
+
+def _grid(prob):
+    return O.Grid(prob.n, prob.h, prob.origin, prob.periodic)
+
+
+def run_gpu(prob, device=True):
+    torch = _torch()
+    plan = F.plan_from_problem(prob, stream=torch.cuda.current_stream().cuda_stream)
+    u0, u1 = F.stacked_initial_data(prob)
+    if device:
+        a, b = torch.from_numpy(u0).cuda(), torch.from_numpy(u1).cuda()
+        out = torch.zeros((prob_nshots(prob),) + prob.n, dtype=torch.float64, device="cuda")
+    else:
+        a, b = u0, u1
+        out = np.zeros((prob_nshots(prob),) + prob.n)
+    counts = plan.decompose(a, b)
+    plan.propagate()
+    plan.reconstruct(out)
+    plan.sync()
+    u = out.cpu().numpy() if device else out
+    return plan, counts, u
+
+
+def prob_nshots(prob):
+    return len(prob.shots)
+
+
+def active_q(prob, shot):
+    """q-grid rows whose FBI box meets the nonzero data (others have psi = 0 exactly)."""
+    g = _grid(prob)
+    nz = (shot.u0 != 0) | (shot.u1 != 0)
+    nq = O.q_counts(g, shot.q_stride)
+    keep = []
+    for k in range(prob.dim):
+        other = tuple(a for a in range(prob.dim) if a != k)
+        idx = np.flatnonzero(np.any(nz, axis=other) if other else nz)
+        m = np.arange(nq[k]) * shot.q_stride[k]
+        half = shot.box[k] // 2
+        if prob.periodic[k]:
+            keep.append(np.ones(nq[k], dtype=bool))
+        else:
+            keep.append((m - half <= idx.max()) & (m + half - 1 >= idx.min()))
+    mesh = np.meshgrid(*keep, indexing="ij")
+    return np.flatnonzero(np.logical_and.reduce([x.ravel() for x in mesh]))
+
+
+def guard_band_keys(dec, tau):
+    """Keys of the + branch whose |psi+| lies within 1e-9 of the threshold."""
+    if tau <= 0:
+        return set()
+    a = np.abs(dec["psi_plus"]) / (tau * dec["M"])
+    r, pi = np.nonzero(np.abs(a - 1.0) < 1e-9)
+    return set(zip(dec["rows"][r].tolist(), pi.tolist()))
+
+
+def check_decomposition(plan, prob, dec, shot=0):
+    psi_gpu, M_gpu = plan.psi(shot)
+    rows = dec["rows"]
+    valid = dec["valid"]
+    M = dec["M"]
+    assert abs(M_gpu - M) <= 1e-12 * M
+    diff = np.abs(psi_gpu[rows][:, valid] - dec["psi_plus"][:, valid])
+    assert diff.max() <= 1e-12 * M, diff.max() / M
+    # rows the oracle skipped must be exactly zero on the GPU as well
+    others = np.setdiff1d(np.arange(psi_gpu.shape[0]), rows)
+    if others.size:
+        assert np.all(psi_gpu[others] == 0)
+    qi, pi, ps = plan.gaussians(shot)
+    gs = dec["gauss"]
+    plus = gs["sigma"] == 1
+    okeys = set(zip(gs["qidx"][plus].tolist(), gs["pidx"][plus].tolist()))
+    gkeys = set(zip(qi.tolist(), pi.tolist()))
+    band = guard_band_keys(dec, prob.tau)
+    assert (gkeys ^ okeys) <= band, len((gkeys ^ okeys) - band)
+    return qi, pi
+
+
+def check_rays(plan, prob, shot_idx, keys_q, keys_p, tol_q=1e-9, tol_a=1e-9):
+    """Oracle rays from the (q, p) grid indices; compare with the GPU state."""
+    sh = prob.shots[shot_idx]
+    g = _grid(prob)
+    qi, pi, _ = plan.gaussians(shot_idx)
+    pos = {k: i for i, k in enumerate(zip(qi.tolist(), pi.tolist()))}
+    idx = np.array([pos[(a, b)] for a, b in zip(keys_q.tolist(), keys_p.tolist())])
+    st = plan.state(shot_idx)
+    q = O.q_points(g, sh.q_stride)[keys_q]
+    p = O.p_points(g, sh.eps, sh.box)[keys_p]
+    ost = O.propagate(g, prob.velocity, prob.nsteps, prob.dt, np.ones(len(keys_q)), q, p)
+    scale = max(1.0, float(np.max(np.abs(ost["Q"]))))
+    dQ = st["Q"][idx] - ost["Q"]
+    for k in range(prob.dim):  # centres on a periodic axis agree modulo the period
+        if prob.periodic[k]:
+            L = prob.n[k] * prob.h[k]
+            dQ[:, k] -= L * np.round(dQ[:, k] / L)
+    assert np.max(np.abs(dQ)) <= tol_q * scale
+    assert np.max(np.abs(st["P"][idx] - ost["P"])) <= tol_q * max(1.0, np.max(np.abs(ost["P"])))
+    assert np.max(np.abs(st["a"][idx] - ost["a"]) / np.abs(ost["a"])) <= tol_a
+    amax = max(1.0, float(np.max(np.abs(ost["A"]))), float(np.max(np.abs(ost["B"]))))
+    assert np.max(np.abs(st["A"][idx] - ost["A"])) <= tol_a * amax
+    assert np.max(np.abs(st["B"][idx] - ost["B"])) <= tol_a * amax
+    assert np.max(np.abs(st["S"])) <= 1e-12
+
+
+def oracle_field(prob, shot_idx, dec, x):
+    sh = prob.shots[shot_idx]
+    g = _grid(prob)
+    gs = dec["gauss"]
+    st = O.propagate(g, prob.velocity, prob.nsteps, prob.dt, gs["sigma"], gs["q"], gs["p"])
+    W = O.quadrature_weight(g, sh.eps, sh.q_stride, sh.box)
+    return O.reconstruct(g, sh.eps, prob.kappa, W, st["Q"], st["P"], st["a"], gs["psi"], st["S"], x)
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+# ---------------------------------------------------------------------------
+# element-wise parity at oracle-sized problems
+# ---------------------------------------------------------------------------
+
+def test_periodic_1d_elementwise():
+    prob = WL.periodic_1d()  # N = 512 (two 256-point tiles), eps = 1/128, T = 0.25, tau = 0
+    plan, counts, u = run_gpu(prob)
+    sh = prob.shots[0]
+    g = _grid(prob)
+    dec = O.decompose(g, prob.velocity, sh.u0, sh.u1, sh.eps, sh.q_stride, sh.box, prob.tau)
+    qi, pi = check_decomposition(plan, prob, dec)
+    assert counts[0] == int(np.sum(dec["gauss"]["sigma"] == 1))
+    check_rays(plan, prob, 0, qi[::37], pi[::37], tol_q=1e-12, tol_a=1e-11)
+    uo = oracle_field(prob, 0, dec, prob.grid_points())
+    assert np.linalg.norm(uo.imag) <= 1e-12 * np.linalg.norm(uo.real)
+    assert rel(u[0].ravel(), uo.real) <= FIELD_TOL
+    plan.close()
+
+
+@pytest.mark.parametrize("N, tau", [(96, 1e-3), (150, 1e-2)])
+def test_lens_2d_elementwise_ragged(N, tau):
+    # 96 = 64 + 32 and 150 = 2*64 + 22 points per axis: full and ragged tiles
+    prob = WL.lens_2d(N=N, eps=1.0 / 400 * (96 / N) ** 2, T=0.05, dt=1e-3, s=2, box=64,
+                      tau=tau, k0=30 * math.pi * N / 96, width2=0.004 * (96 / N) ** 2,
+                      x0=(0.45, 0.3))
+    plan, counts, u = run_gpu(prob)
+    sh = prob.shots[0]
+    g = _grid(prob)
+    dec = O.decompose(g, prob.velocity, sh.u0, sh.u1, sh.eps, sh.q_stride, sh.box, prob.tau)
+    qi, pi = check_decomposition(plan, prob, dec)
+    check_rays(plan, prob, 0, qi[::97], pi[::97], tol_q=1e-12, tol_a=1e-11)
+    uo = oracle_field(prob, 0, dec, prob.grid_points())
+    assert rel(u[0].ravel(), uo.real) <= FIELD_TOL
+    plan.close()
+
+
+def test_host_and_device_pointers_agree():
+    prob = WL.lens_2d(N=96, eps=1.0 / 400, T=0.02, dt=1e-3, s=2, box=64, tau=1e-3,
+                      k0=30 * math.pi, width2=0.004, x0=(0.45, 0.3))
+    p1, c1, u1 = run_gpu(prob, device=True)
+    p2, c2, u2 = run_gpu(prob, device=False)
+    assert np.array_equal(c1, c2)
+    assert np.array_equal(u1, u2)
+    p1.close()
+    p2.close()
+
+
+def test_batched_shots_equal_single_shots_bitwise():
+    full = WL.layered_batch(nshots=3, T=0.03)
+    pb, cb, ub = run_gpu(full)
+    for s in range(3):
+        single = full.with_(shots=[full.shots[s]])
+        ps, cs, us = run_gpu(single)
+        assert cs[0] == cb[s]
+        assert np.array_equal(us[0], ub[s])
+        ps.close()
+    # and one shot of the batch against the oracle at sampled points
+    sh = full.shots[1]
+    g = _grid(full)
+    rows = active_q(full, sh)
+    dec = O.decompose(g, full.velocity, sh.u0, sh.u1, sh.eps, sh.q_stride, sh.box, 1e-2,
+                      q_subset=rows)
+    prob2 = full.with_(shots=[sh], tau=1e-2)
+    p2, c2, u2 = run_gpu(prob2)
+    x = full.grid_points()
+    pick = np.random.default_rng(3).choice(x.shape[0], 600, replace=False)
+    uo = oracle_field(prob2, 0, dec, x[pick])
+    assert rel(u2[0].ravel()[pick], uo.real) <= FIELD_TOL
+    pb.close()
+    p2.close()
+
+
+# ---------------------------------------------------------------------------
+# the benchmark's workload at full size: sampled outputs and invariants
+# ---------------------------------------------------------------------------
+
+def _bspline_c(prob, x):
+    """c(x) of the cubic B-spline medium, evaluated independently with scipy's basis."""
+    from scipy.interpolate import BSpline
+
+    b = BSpline.basis_element([-2.0, -1.0, 0.0, 1.0, 2.0], extrapolate=False)
+    c = np.zeros(x.shape[0])
+    u = [(x[:, k] - prob.origin[k]) / prob.h[k] for k in range(prob.dim)]
+    base = [np.floor(uk).astype(np.int64) - 1 for uk in u]
+    for ta in range(4):
+        ia = base[0] + ta
+        wa = np.nan_to_num(b(u[0] - ia))
+        ia = np.clip(ia, 0, prob.n[0] - 1)
+        for tb in range(4):
+            ib = base[1] + tb
+            wb = np.nan_to_num(b(u[1] - ib))
+            ib = np.clip(ib, 0, prob.n[1] - 1)
+            c += prob.velocity[ia, ib] * wa * wb
+    return c
+
+
+def test_layered_full_size_sampled_and_invariants():
+    prob = WL.layered_single()  # 737 x 241, 15 Hz, T = 2 s: the benchmark's workload
+    plan, counts, u = run_gpu(prob)
+    sh = prob.shots[0]
+    g = _grid(prob)
+    rows = active_q(prob, sh)
+    dec = O.decompose(g, prob.velocity, sh.u0, sh.u1, sh.eps, sh.q_stride, sh.box, prob.tau,
+                      q_subset=rows)
+    qi, pi = check_decomposition(plan, prob, dec)
+    # 96 rays through the layered model, sampled from the oracle's own set
+    gs = dec["gauss"]
+    plus = np.flatnonzero(gs["sigma"] == 1)
+    pick = np.random.default_rng(11).choice(plus, 96, replace=False)
+    check_rays(plan, prob, 0, gs["qidx"][pick], gs["pidx"][pick], tol_q=1e-8, tol_a=1e-8)
+    # invariants for every GPU ray: c(Q)|P| = c(q)|p| and a^2/(c(Q)^2 det Z) = 1/c(q)^2
+    st = plan.state(0)
+    q = O.q_points(g, sh.q_stride)[qi]
+    p = O.p_points(g, sh.eps, sh.box)[pi]
+    cq = _bspline_c(prob, q)
+    cQ = _bspline_c(prob, st["Q"])
+    H0 = cq * np.linalg.norm(p, axis=1)
+    H = cQ * np.linalg.norm(st["P"], axis=1)
+    assert np.max(np.abs(H - H0) / H0) <= 1e-8
+    Z = st["A"] + 1j * st["B"]
+    inv = st["a"] ** 2 / (cQ ** 2 * np.linalg.det(Z))
+    assert np.max(np.abs(inv * cq ** 2 - 1.0)) <= 1e-8
+    assert np.max(np.abs(st["S"])) <= 1e-12
+    assert np.all(np.isfinite(u))
+    plan.close()
+
+
+def test_layered_short_time_field_sampled():
+    # the same model and source over 50 steps with a 1e-2 threshold: the oracle
+    # propagates every Gaussian of both branches and sums them at sampled points
+    prob = WL.layered_single(T=0.05, tau=1e-2)
+    plan, counts, u = run_gpu(prob)
+    sh = prob.shots[0]
+    g = _grid(prob)
+    dec = O.decompose(g, prob.velocity, sh.u0, sh.u1, sh.eps, sh.q_stride, sh.box, prob.tau,
+                      q_subset=active_q(prob, sh))
+    check_decomposition(plan, prob, dec)
+    x = prob.grid_points()
+    near = np.flatnonzero(np.hypot(x[:, 0] - 4.6, x[:, 1]) < 1.2)
+    pick = np.random.default_rng(5).choice(near, 800, replace=False)
+    uo = oracle_field(prob, 0, dec, x[pick])
+    assert rel(u[0].ravel()[pick], uo.real) <= FIELD_TOL
+    plan.close()
+
+
+# ---------------------------------------------------------------------------
+# edge cases
+# ---------------------------------------------------------------------------
+
+def test_zero_data_gives_no_gaussians_and_zero_field():
+    prob = WL.lens_2d(N=64, eps=1.0 / 400, T=0.01, dt=1e-3, s=2, box=64)
+    sh = prob.shots[0]
+    prob = prob.with_(shots=[WL.Shot(eps=sh.eps, u0=np.zeros_like(sh.u0), u1=np.zeros_like(sh.u1),
+                                     q_stride=sh.q_stride, box=sh.box)])
+    plan, counts, u = run_gpu(prob)
+    assert counts[0] == 0
+    assert np.all(u == 0)
+    plan.close()
+
+
+def test_threshold_one_keeps_the_maximum_only():
+    prob = WL.lens_2d(N=96, eps=1.0 / 400, T=0.01, dt=1e-3, s=2, box=64, tau=1.0,
+                      k0=30 * math.pi, width2=0.004, x0=(0.45, 0.3))
+    plan, counts, u = run_gpu(prob)
+    psi, M = plan.psi(0)
+    assert counts[0] >= 1
+    qi, pi, ps = plan.gaussians(0)
+    assert np.all(np.abs(ps) >= M * (1 - 1e-15))
+    plan.close()
+
+
+def test_zero_time_reproduces_the_frame():
+    # T = 0: no RK4 step; f1 = 0 and tau = 0 on the periodic 1D grid give back f0
+    prob = WL.periodic_1d(width2=0.01, T=0.0)
+    sh = prob.shots[0]
+    prob = prob.with_(shots=[WL.Shot(eps=sh.eps, u0=sh.u0, u1=np.zeros_like(sh.u1),
+                                     q_stride=sh.q_stride, box=sh.box)])
+    plan, counts, u = run_gpu(prob)
+    assert rel(u[0], sh.u0) <= 1e-10
+    plan.close()
+
+
+def test_bad_velocity_and_call_order():
+    prob = WL.lens_2d(N=64, eps=1.0 / 400, T=0.01, dt=1e-3, s=2, box=64)
+    bad = prob.velocity.copy()
+    bad[3, 4] = -1.0
+    with pytest.raises(F.FGAError) as ei:
+        F.plan_from_problem(prob, velocity=bad)
+    assert ei.value.status == 1
+    bad[3, 4] = float("nan")
+    with pytest.raises(F.FGAError):
+        F.plan_from_problem(prob, velocity=bad)
+    plan = F.plan_from_problem(prob)
+    with pytest.raises(F.FGAError) as ei:
+        plan.propagate()
+    assert ei.value.status == 5  # FGA_ERR_STATE
+    with pytest.raises(F.FGAError) as ei:
+        plan.reconstruct()
+    assert ei.value.status == 5
+    plan.close()
