@@ -193,7 +193,7 @@ def run_ours(args, rank, world, local_rank):
     _, launches0 = plan.stage_times()
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    ray_ms, recon_ms, fbi_ms = [], [], []
+    ray_ms, recon_ms, fbi_ms, ray_steps = [], [], [], []
     with ClockSampler(local_rank) as clk:
         t0 = time.perf_counter()
         for i in range(args.steps):
@@ -202,6 +202,7 @@ def run_ours(args, rank, world, local_rank):
             step(d_u0, d_u1, d_out)
             ends[i].record(stream)
             stt, _ = plan.stage_times()
+            ray_steps.append(plan.ray_steps())
             ray_ms.append(stt["rays"])
             recon_ms.append(stt["reconstruct"] + stt["binning"])
             fbi_ms.append(stt["fbi"])
@@ -237,7 +238,8 @@ def run_ours(args, rank, world, local_rank):
     npts = prob.npoints
 
     ray_s = statistics.mean(ray_ms) / 1e3
-    ray_flops = FLOPS_PER_RAY_STEP_2D * prob.nsteps * G
+    steps_done = statistics.mean(ray_steps)
+    ray_flops = FLOPS_PER_RAY_STEP_2D * steps_done
     achieved = ray_flops / ray_s / 1e12
     clocks = clk.summary()
     line = {
@@ -262,6 +264,8 @@ def run_ours(args, rank, world, local_rank):
             "tau": prob.tau,
             "kappa": prob.kappa,
             "gaussians_plus_branch": G,
+            "ray_steps_integrated": steps_done,
+            "ray_steps_all_to_T": G * prob.nsteps,
             "evals_per_step_both_branches": evals,
             "precision": "fp64",
             "stage_ms_mean": {"fbi": statistics.mean(fbi_ms), "rays": statistics.mean(ray_ms),

@@ -79,6 +79,13 @@ typedef struct {
   double kappa;       /* reconstruction window half-width in units of sqrt(eps) */
   double tau;         /* relative threshold: keep |psi+| >= tau * max|psi+-| */
   int precision;      /* fga_precision */
+  int integrate_exited; /* 0 (default): a ray stops once its window has left an open
+                           axis for good (|Q_k - edge| > kappa sqrt(eps) + 2 h_k outside
+                           the grid with P_k pointing away; beyond the spline's clamped
+                           margin c does not vary along that axis, so P_k keeps its sign
+                           and the Gaussian never touches the grid again: the field is
+                           unchanged, its stored state is the state at exit).
+                           1: every ray is integrated to T. */
 } fga_config;
 
 /* Create a plan: validate cfg, copy the velocity (host or device, [n...] FP64,
@@ -155,6 +162,11 @@ fga_status fga_gaussians(fga_plan_t plan, int shot, int64_t* qidx, int64_t* pidx
  * a [G][2]; S [G]. Any pointer may be NULL. */
 fga_status fga_state(fga_plan_t plan, int shot, double* Q, double* P, double* A, double* B,
                      double* a, double* S);
+
+/* Ray steps integrated by the last fga_propagate, summed over all Gaussians
+ * (G * T/dt when every ray is integrated to T; fewer when exited rays stop);
+ * -1 before the first propagation. Synchronises the plan's stream. */
+int64_t fga_ray_steps(fga_plan_t plan);
 
 /* Per-stage device times in ms of the last decompose/propagate/reconstruct
  * (CUDA events on the plan's stream): out[0..4] = FBI, selection, rays,

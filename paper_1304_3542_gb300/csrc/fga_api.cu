@@ -140,7 +140,8 @@ fga_status fga_destroy(fga_plan_t p) {
   void* bufs[] = {p->d_coef, p->d_shots, p->d_in0, p->d_bbox, p->d_psi, p->d_g1,
                   p->d_max2, p->d_blk, p->d_counts, p->d_blk_first, p->d_gshot, p->d_gq, p->d_gp,
                   p->d_gpsi, p->d_state, p->d_gcoef, p->d_tile_cnt, p->d_tile_off,
-                  p->d_tile_list, p->d_out, p->d_status};
+                  p->d_tile_list, p->d_seg_off, p->d_partial, p->d_out, p->d_status,
+                  p->d_steps};
   for (void* b : bufs)
     if (b) cudaFree(b);
   for (double* e : p->E)
@@ -201,6 +202,7 @@ fga_status fga_plan(const fga_config* cfg, const double* velocity, void* stream,
   p->kappa = cfg->kappa;
   p->tau = cfg->tau;
   p->precision = cfg->precision;
+  p->integrate_exited = cfg->integrate_exited ? 1 : 0;
   p->stream = (cudaStream_t)stream;
   p->nfields = fga::state_fields(d);
   const int TS = fga::tile_edge(d);
@@ -274,6 +276,7 @@ fga_status fga_plan(const fga_config* cfg, const double* velocity, void* stream,
   PLAN_CUDA(cudaMemcpyAsync(p->d_coef, velocity, sizeof(double) * gd.npts, cudaMemcpyDefault,
                             p->stream));
   PLAN_CUDA(cudaMalloc(&p->d_status, sizeof(int)));
+  PLAN_CUDA(cudaMalloc(&p->d_steps, sizeof(unsigned long long)));
   PLAN_CUDA(cudaMemsetAsync(p->d_status, 0, sizeof(int), p->stream));
   k_check_velocity<<<256, 256, 0, p->stream>>>(p->d_coef, gd.npts, p->d_status);
   p->launches += 1;
@@ -303,6 +306,7 @@ fga_status fga_plan(const fga_config* cfg, const double* velocity, void* stream,
   PLAN_CUDA(cudaMalloc(&p->d_counts, sizeof(int64_t) * cfg->nshots));
   PLAN_CUDA(cudaMalloc(&p->d_blk_first, sizeof(int64_t) * (cfg->nshots + 1)));
   PLAN_CUDA(cudaMalloc(&p->d_tile_off, sizeof(int64_t) * (p->ntiles + 1)));
+  PLAN_CUDA(cudaMalloc(&p->d_seg_off, sizeof(int64_t) * (p->ntiles + 1)));
   for (auto& ev : p->ev) PLAN_CUDA(cudaEventCreate(&ev));
 #undef PLAN_CUDA
   *out = p;
@@ -455,6 +459,8 @@ fga_status fga_reconstruct(fga_plan_t p, double* u_out) {
     pairs += per * (size_t)sh.g_cnt;
   }
   CUDA_OR_FAIL(p, grow(&p->d_tile_list, &p->list_cap, pairs));
+  CUDA_OR_FAIL(p, grow(&p->d_partial, &p->partial_cap,
+                       fga::partial_items(p) * fga::tile_points(d)));
   CUDA_OR_FAIL(p, cudaEventRecord(p->ev[5], p->stream));
   CUDA_OR_FAIL(p, fga::launch_binning(p, nullptr));
   CUDA_OR_FAIL(p, fga::launch_binning_fill(p));
@@ -466,7 +472,6 @@ fga_status fga_reconstruct(fga_plan_t p, double* u_out) {
     CUDA_OR_FAIL(p, grow(&p->d_out, &p->out_cap, n_all));
     dst = p->d_out;
   }
-  CUDA_OR_FAIL(p, cudaMemsetAsync(dst, 0, sizeof(double) * n_all, p->stream));
   CUDA_OR_FAIL(p, fga::launch_reconstruct(p, dst));
   CUDA_OR_FAIL(p, cudaEventRecord(p->ev[7], p->stream));
   if (host_out) {
@@ -605,6 +610,17 @@ fga_status fga_state(fga_plan_t p, int shot, double* Q, double* P, double* A, do
     if (S) S[g] = F(aR + 2, g);
   }
   return FGA_OK;
+}
+
+int64_t fga_ray_steps(fga_plan_t p) {
+  if (!p || p->stage < 2 || p->failed) return -1;
+  unsigned long long v = 0;
+  if (cudaMemcpyAsync(&v, p->d_steps, sizeof(v), cudaMemcpyDeviceToHost, p->stream) != cudaSuccess ||
+      cudaStreamSynchronize(p->stream) != cudaSuccess) {
+    cudaGetLastError();
+    return -1;
+  }
+  return (int64_t)v;
 }
 
 fga_status fga_stage_times(fga_plan_t p, double* ms5, int64_t* launches) {

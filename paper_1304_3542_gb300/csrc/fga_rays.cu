@@ -14,7 +14,8 @@
 // read-only cache (its spline coefficients stay resident in L2). The epilogue stores
 // the state (structure of arrays, coalesced) and the complex coefficient of the
 // reconstruction sum, 2 W a psi (2 pi eps)^{-3d/2} e^{i S/eps} (the 2 accounts for the
-// conjugate - branch).
+// conjugate - branch). Unless asked to integrate every ray to T, a ray stops once its
+// window has left an open axis for good (see fga_config.integrate_exited).
 #include "fga_internal.cuh"
 #include "fga_medium.cuh"
 
@@ -125,8 +126,10 @@ __global__ void __launch_bounds__(128) k_rays(GridDev gd, const ShotDev* __restr
                                               const int64_t* __restrict__ gq,
                                               const int32_t* __restrict__ gp,
                                               const double2* __restrict__ gpsi, int64_t nsteps,
-                                              double dt, double* __restrict__ state, int64_t ld,
-                                              double2* __restrict__ coef, int* status) {
+                                              double dt, double kappa, int integrate_exited,
+                                              double* __restrict__ state, int64_t ld,
+                                              double2* __restrict__ coef, int* status,
+                                              unsigned long long* steps_done) {
   using Lo = Layout<D>;
   constexpr int NF = Lo::NF;
   int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -156,9 +159,27 @@ __global__ void __launch_bounds__(128) k_rays(GridDev gd, const ShotDev* __restr
     y[Lo::BI + i * D + i] = -1.0;
   }
   y[Lo::aR] = (D == 1) ? 1.4142135623730951 : 2.0;
+  // exit box: beyond these bounds on an open axis the window misses the grid and the
+  // spline's taps are all clamped, so c does not depend on Q_k there
+  double lo[D], hi[D];
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+    double reach = kappa * sh.sqrt_eps + 2.0 * gd.h[i];
+    lo[i] = gd.o[i] - reach;
+    hi[i] = gd.o[i] + (double)(gd.n[i] - 1) * gd.h[i] + reach;
+  }
   bool ok = true;
   const double h2 = 0.5 * dt, h6 = dt / 6.0, h3 = dt / 3.0;
-  for (int64_t step = 0; step < nsteps; ++step) {
+  int64_t step = 0;
+  for (; step < nsteps; ++step) {
+    if (!integrate_exited) {
+      bool gone = false;
+#pragma unroll
+      for (int i = 0; i < D; ++i)
+        gone = gone || (!gd.periodic[i] && ((y[Lo::Q + i] < lo[i] && y[Lo::P + i] <= 0.0) ||
+                                            (y[Lo::Q + i] > hi[i] && y[Lo::P + i] >= 0.0)));
+      if (gone) break;
+    }
     double acc[NF], tmp[NF], k[NF];
     ok &= rhs<D>(gd, C, y, k);
 #pragma unroll
@@ -190,6 +211,12 @@ __global__ void __launch_bounds__(128) k_rays(GridDev gd, const ShotDev* __restr
       }
     }
   }
+  // count of the steps integrated, summed over the converged lanes of the warp
+  {
+    unsigned mask = __activemask();
+    unsigned tot = __reduce_add_sync(mask, (unsigned)step);
+    if ((int)(threadIdx.x & 31) == __ffs(mask) - 1) atomicAdd(steps_done, (unsigned long long)tot);
+  }
   bool fin = isfinite(y[Lo::aR]) && isfinite(y[Lo::aI]) && isfinite(y[Lo::S]);
 #pragma unroll
   for (int i = 0; i < D; ++i) fin = fin && isfinite(y[Lo::Q + i]) && isfinite(y[Lo::P + i]);
@@ -209,16 +236,20 @@ __global__ void __launch_bounds__(128) k_rays(GridDev gd, const ShotDev* __restr
 }  // namespace
 
 cudaError_t launch_rays(fga_plan_s* p) {
+  cudaError_t e = cudaMemsetAsync(p->d_steps, 0, sizeof(unsigned long long), p->stream);
+  if (e != cudaSuccess) return e;
   if (p->G == 0) return cudaSuccess;
   unsigned blocks = (unsigned)((p->G + 127) / 128);
   if (p->grid.dim == 1)
     k_rays<1><<<blocks, 128, 0, p->stream>>>(p->grid, p->d_shots, p->d_coef, p->G, p->d_gshot,
-                                             p->d_gq, p->d_gp, p->d_gpsi, p->nsteps, p->dt,
-                                             p->d_state, (int64_t)p->g_cap, p->d_gcoef, p->d_status);
+                                             p->d_gq, p->d_gp, p->d_gpsi, p->nsteps, p->dt, p->kappa,
+                                             p->integrate_exited, p->d_state, (int64_t)p->g_cap,
+                                             p->d_gcoef, p->d_status, p->d_steps);
   else
     k_rays<2><<<blocks, 128, 0, p->stream>>>(p->grid, p->d_shots, p->d_coef, p->G, p->d_gshot,
-                                             p->d_gq, p->d_gp, p->d_gpsi, p->nsteps, p->dt,
-                                             p->d_state, (int64_t)p->g_cap, p->d_gcoef, p->d_status);
+                                             p->d_gq, p->d_gp, p->d_gpsi, p->nsteps, p->dt, p->kappa,
+                                             p->integrate_exited, p->d_state, (int64_t)p->g_cap,
+                                             p->d_gcoef, p->d_status, p->d_steps);
   p->launches += 1;
   return cudaGetLastError();
 }

@@ -22,6 +22,8 @@ constexpr int T2 = 64;   // 2D tile edge (points)
 constexpr int T1 = 256;  // 1D tile length
 constexpr int CH = 16;   // Gaussians per chunk (2D)
 constexpr int CH1 = 32;  // Gaussians per chunk (1D)
+constexpr int64_t SEG2 = 1024;  // Gaussians per work item (2D)
+constexpr int64_t SEG1 = 512;   // Gaussians per work item (1D)
 
 __device__ __forceinline__ int shot_of_tile(const ShotDev* shots, int nshots, int64_t t) {
   int lo = 0, hi = nshots - 1;
@@ -145,14 +147,71 @@ __device__ __forceinline__ double2 axis_factor(const GridDev& gd, int k, int64_t
   return make_double2(re, im);
 }
 
-__global__ void __launch_bounds__(NT) k_recon1(GridDev gd, const ShotDev* __restrict__ shots,
-                                               int nshots, double kappa,
-                                               const double* __restrict__ state, int64_t ld,
-                                               const double2* __restrict__ coef,
-                                               const int64_t* __restrict__ off,
-                                               const int32_t* __restrict__ list, int64_t list_cap,
-                                               double* __restrict__ out) {
-  const int64_t t = blockIdx.x;
+// Factors of one Gaussian along an open axis at the 8 grid points i0 .. i0+7,
+// times cf: E_i = exp(-d_i^2/(2 eps)) exp(i P d_i/eps), d_i = x_i - Q, zero outside
+// |d_i| <= cut. Evaluated directly at the first point inside the window and then by
+// the exact recurrence E_{i+1} = E_i R_i rot, R_{i+1} = R_i rho with
+// R_i = exp(-(d_i h + h^2/2)/eps), rot = exp(i P h/eps), rho = exp(-h^2/eps)
+// (relative rounding growth below 1e-14 over 8 points).
+__device__ __forceinline__ void axis_factors8(double xi0, double h, double Q, double P, double cut,
+                                              double inv_eps, double2 cf, double2* dst) {
+  int r0 = 0;
+  while (r0 < 8 && fabs(fma((double)r0, h, xi0) - Q) > cut) ++r0;
+  for (int r = 0; r < r0; ++r) dst[r] = make_double2(0.0, 0.0);
+  if (r0 == 8) return;
+  double d = fma((double)r0, h, xi0) - Q;
+  double gs = exp(-0.5 * d * d * inv_eps);
+  double sn, cs;
+  sincos(P * d * inv_eps, &sn, &cs);
+  double er = gs * cs, ei = gs * sn;
+  double R = exp(-(d * h + 0.5 * h * h) * inv_eps);
+  double rs, rc;
+  sincos(P * h * inv_eps, &rs, &rc);
+  const double rho = exp(-h * h * inv_eps);
+  for (int r = r0; r < 8; ++r) {
+    double dr = fma((double)r, h, xi0) - Q;
+    if (fabs(dr) <= cut)
+      dst[r] = make_double2(cf.x * er - cf.y * ei, cf.x * ei + cf.y * er);
+    else
+      dst[r] = make_double2(0.0, 0.0);
+    double tr = er * R, ti = ei * R;
+    er = tr * rc - ti * rs;
+    ei = tr * rs + ti * rc;
+    R *= rho;
+  }
+}
+
+// The (tile, segment) work item w: tile t is the largest with seg_off[t] <= w.
+__device__ __forceinline__ int64_t tile_of_item(const int64_t* seg_off, int64_t ntiles, int64_t w) {
+  int64_t lo = 0, hi = ntiles - 1;
+  while (lo < hi) {
+    int64_t mid = (lo + hi + 1) >> 1;
+    if (seg_off[mid] <= w) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// Number of list segments per tile (then scanned into seg_off).
+__global__ void k_segments(const int64_t* __restrict__ off, int64_t ntiles, int64_t list_cap,
+                           int64_t seg, int64_t* __restrict__ seg_cnt) {
+  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= ntiles) return;
+  int64_t a = min(off[t], list_cap), b = min(off[t + 1], list_cap);
+  seg_cnt[t] = (b - a + seg - 1) / seg;
+}
+
+// 1D gather of one work item: thread = grid point, partial[w][T1].
+__global__ void __launch_bounds__(NT) k_gather1(GridDev gd, const ShotDev* __restrict__ shots,
+                                                int nshots, double kappa,
+                                                const double* __restrict__ state, int64_t ld,
+                                                const double2* __restrict__ coef,
+                                                const int64_t* __restrict__ off,
+                                                const int32_t* __restrict__ list, int64_t list_cap,
+                                                const int64_t* __restrict__ seg_off, int64_t ntiles,
+                                                double* __restrict__ partial) {
+  const int64_t w = blockIdx.x;
+  if (w >= seg_off[ntiles]) return;
+  const int64_t t = tile_of_item(seg_off, ntiles, w);
   const int s = shot_of_tile(shots, nshots, t);
   const ShotDev& sh = shots[s];
   const double cut = kappa * sh.sqrt_eps, inv_eps = sh.inv_eps;
@@ -160,7 +219,8 @@ __global__ void __launch_bounds__(NT) k_recon1(GridDev gd, const ShotDev* __rest
   __shared__ double sQ[CH1], sP[CH1];
   __shared__ double2 sC[CH1];
   double re = 0.0;
-  const int64_t l0 = min(off[t], list_cap), l1 = min(off[t + 1], list_cap);
+  const int64_t l0 = min(off[t], list_cap) + (w - seg_off[t]) * SEG1;
+  const int64_t l1 = min(min(off[t + 1], list_cap), l0 + SEG1);
   for (int64_t c0 = l0; c0 < l1; c0 += CH1) {
     int nc = (int)((l1 - c0) < CH1 ? (l1 - c0) : CH1);
     if (threadIdx.x < nc) {
@@ -170,27 +230,29 @@ __global__ void __launch_bounds__(NT) k_recon1(GridDev gd, const ShotDev* __rest
       sC[threadIdx.x] = coef[g];
     }
     __syncthreads();
-    if (i < gd.n[0]) {
-      for (int j = 0; j < nc; ++j) {
-        double2 x = axis_factor(gd, 0, i, sQ[j], sP[j], cut, inv_eps);
-        re = fma(sC[j].x, x.x, fma(-sC[j].y, x.y, re));
-      }
+    for (int j = 0; j < nc; ++j) {
+      double2 x = axis_factor(gd, 0, i, sQ[j], sP[j], cut, inv_eps);
+      re = fma(sC[j].x, x.x, fma(-sC[j].y, x.y, re));
     }
     __syncthreads();
   }
-  if (i < gd.n[0]) out[(int64_t)s * gd.npts + i] = re;
+  partial[w * T1 + threadIdx.x] = re;
 }
 
-// 2D gather: 64 x 64 tile, 8 warps each covering a 16 x 32 patch (4 x 8 threads of
-// 4 x 4 points); a warp skips a Gaussian whose window misses its patch.
-__global__ void __launch_bounds__(NT) k_recon2(GridDev gd, const ShotDev* __restrict__ shots,
-                                               int nshots, double kappa,
-                                               const double* __restrict__ state, int64_t ld,
-                                               const double2* __restrict__ coef,
-                                               const int64_t* __restrict__ off,
-                                               const int32_t* __restrict__ list, int64_t list_cap,
-                                               double* __restrict__ out) {
-  const int64_t t = blockIdx.x;
+// 2D gather of one work item: 64 x 64 tile, 8 warps each covering a 16 x 32 patch
+// (4 x 8 threads of 4 x 4 points); a warp skips a Gaussian whose window misses its
+// patch. Writes the partial tile sum partial[w][64][64].
+__global__ void __launch_bounds__(NT) k_gather2(GridDev gd, const ShotDev* __restrict__ shots,
+                                                int nshots, double kappa,
+                                                const double* __restrict__ state, int64_t ld,
+                                                const double2* __restrict__ coef,
+                                                const int64_t* __restrict__ off,
+                                                const int32_t* __restrict__ list, int64_t list_cap,
+                                                const int64_t* __restrict__ seg_off, int64_t ntiles,
+                                                double* __restrict__ partial) {
+  const int64_t w = blockIdx.x;
+  if (w >= seg_off[ntiles]) return;
+  const int64_t t = tile_of_item(seg_off, ntiles, w);
   const int s = shot_of_tile(shots, nshots, t);
   const ShotDev& sh = shots[s];
   const double cut = kappa * sh.sqrt_eps, inv_eps = sh.inv_eps;
@@ -210,7 +272,8 @@ __global__ void __launch_bounds__(NT) k_recon2(GridDev gd, const ShotDev* __rest
   for (int i = 0; i < 4; ++i)
 #pragma unroll
     for (int j = 0; j < 4; ++j) accr[i][j] = 0.0;
-  const int64_t l0 = min(off[t], list_cap), l1 = min(off[t + 1], list_cap);
+  const int64_t l0 = min(off[t], list_cap) + (w - seg_off[t]) * SEG2;
+  const int64_t l1 = min(min(off[t + 1], list_cap), l0 + SEG2);
   for (int64_t c0 = l0; c0 < l1; c0 += CH) {
     const int nc = (int)((l1 - c0) < CH ? (l1 - c0) : CH);
     // factor generation: thread -> (gaussian, axis, 8 consecutive points)
@@ -220,12 +283,15 @@ __global__ void __launch_bounds__(NT) k_recon2(GridDev gd, const ShotDev* __rest
         int32_t g = list[c0 + gi];
         double Q = state[axis * ld + g], P = state[(2 + axis) * ld + g];
         double2 cf = axis == 0 ? coef[g] : make_double2(1.0, 0.0);
-        double2* dst = axis == 0 ? Xs[gi] : Zs[gi];
-#pragma unroll 2
-        for (int r = 0; r < 8; ++r) {
-          int li = part * 8 + r;
-          double2 f = axis_factor(gd, axis, a[axis] + li, Q, P, cut, inv_eps);
-          dst[li] = make_double2(cf.x * f.x - cf.y * f.y, cf.x * f.y + cf.y * f.x);
+        double2* dst = (axis == 0 ? Xs[gi] : Zs[gi]) + part * 8;
+        if (gd.periodic[axis]) {
+          for (int r = 0; r < 8; ++r) {
+            double2 f = axis_factor(gd, axis, a[axis] + part * 8 + r, Q, P, cut, inv_eps);
+            dst[r] = make_double2(cf.x * f.x - cf.y * f.y, cf.x * f.y + cf.y * f.x);
+          }
+        } else {
+          double xi0 = gd.o[axis] + (double)(a[axis] + part * 8) * gd.h[axis];
+          axis_factors8(xi0, gd.h[axis], Q, P, cut, inv_eps, cf, dst);
         }
         if (part == 0) {
           if (gd.periodic[axis]) {
@@ -258,15 +324,35 @@ __global__ void __launch_bounds__(NT) k_recon2(GridDev gd, const ShotDev* __rest
     }
     __syncthreads();
   }
+  double* dst = partial + w * (int64_t)(T2 * T2);
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    int64_t ix = a[0] + x0 + i;
-    if (ix > b[0]) continue;
+  for (int i = 0; i < 4; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      int64_t iz = a[1] + z0 + j;
-      if (iz > b[1]) continue;
-      out[(int64_t)s * gd.npts + ix * gd.n[1] + iz] = accr[i][j];
+    for (int j = 0; j < 4; ++j) dst[(x0 + i) * T2 + z0 + j] = accr[i][j];
+}
+
+// Ordered sum of the partial tiles of every tile into the output grid.
+template <int D>
+__global__ void __launch_bounds__(NT) k_reduce(GridDev gd, const ShotDev* __restrict__ shots,
+                                               int nshots, const int64_t* __restrict__ seg_off,
+                                               const double* __restrict__ partial,
+                                               double* __restrict__ out) {
+  const int64_t t = blockIdx.x;
+  const int s = shot_of_tile(shots, nshots, t);
+  const ShotDev& sh = shots[s];
+  int64_t a[D], b[D];
+  tile_box<D>(gd, sh, t - sh.tile_off, a, b);
+  constexpr int TP = (D == 1) ? T1 : T2 * T2;
+  const int64_t w0 = seg_off[t], w1 = seg_off[t + 1];
+  for (int idx = threadIdx.x; idx < TP; idx += NT) {
+    double v = 0.0;
+    for (int64_t w = w0; w < w1; ++w) v += partial[w * TP + idx];
+    if constexpr (D == 1) {
+      int64_t i = a[0] + idx;
+      if (i <= b[0]) out[(int64_t)s * gd.npts + i] = v;
+    } else {
+      int64_t ix = a[0] + idx / T2, iz = a[1] + idx % T2;
+      if (ix <= b[0] && iz <= b[1]) out[(int64_t)s * gd.npts + ix * gd.n[1] + iz] = v;
     }
   }
 }
@@ -306,19 +392,42 @@ cudaError_t launch_binning_fill(fga_plan_s* p) {
   return cudaGetLastError();
 }
 
+size_t partial_items(fga_plan_s* p) {
+  int64_t seg = p->grid.dim == 1 ? SEG1 : SEG2;
+  return (size_t)p->ntiles + (p->list_cap + seg - 1) / seg;
+}
+
+size_t tile_points(int dim) { return dim == 1 ? (size_t)T1 : (size_t)T2 * T2; }
+
+// Split of every tile's list into segments, one CTA per (tile, segment) writing a
+// partial tile, then the ordered reduction into u_dev.
 cudaError_t launch_reconstruct(fga_plan_s* p, double* u_dev) {
   if (p->ntiles == 0) return cudaSuccess;
-  if (p->grid.dim == 1)
-    k_recon1<<<(unsigned)p->ntiles, NT, 0, p->stream>>>(p->grid, p->d_shots, p->nshots, p->kappa,
-                                                        p->d_state, (int64_t)p->g_cap, p->d_gcoef,
-                                                        p->d_tile_off, p->d_tile_list,
-                                                        (int64_t)p->list_cap, u_dev);
-  else
-    k_recon2<<<(unsigned)p->ntiles, NT, 0, p->stream>>>(p->grid, p->d_shots, p->nshots, p->kappa,
-                                                        p->d_state, (int64_t)p->g_cap, p->d_gcoef,
-                                                        p->d_tile_off, p->d_tile_list,
-                                                        (int64_t)p->list_cap, u_dev);
+  const int64_t seg = p->grid.dim == 1 ? SEG1 : SEG2;
+  k_segments<<<(unsigned)((p->ntiles + 255) / 256), 256, 0, p->stream>>>(
+      p->d_tile_off, p->ntiles, (int64_t)p->list_cap, seg, p->d_seg_off);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
   p->launches += 1;
+  e = launch_scan(p, p->d_seg_off, p->ntiles);
+  if (e != cudaSuccess) return e;
+  const unsigned items = (unsigned)partial_items(p);
+  if (p->grid.dim == 1) {
+    k_gather1<<<items, NT, 0, p->stream>>>(p->grid, p->d_shots, p->nshots, p->kappa, p->d_state,
+                                           (int64_t)p->g_cap, p->d_gcoef, p->d_tile_off,
+                                           p->d_tile_list, (int64_t)p->list_cap, p->d_seg_off,
+                                           p->ntiles, p->d_partial);
+    k_reduce<1><<<(unsigned)p->ntiles, NT, 0, p->stream>>>(p->grid, p->d_shots, p->nshots,
+                                                           p->d_seg_off, p->d_partial, u_dev);
+  } else {
+    k_gather2<<<items, NT, 0, p->stream>>>(p->grid, p->d_shots, p->nshots, p->kappa, p->d_state,
+                                           (int64_t)p->g_cap, p->d_gcoef, p->d_tile_off,
+                                           p->d_tile_list, (int64_t)p->list_cap, p->d_seg_off,
+                                           p->ntiles, p->d_partial);
+    k_reduce<2><<<(unsigned)p->ntiles, NT, 0, p->stream>>>(p->grid, p->d_shots, p->nshots,
+                                                           p->d_seg_off, p->d_partial, u_dev);
+  }
+  p->launches += 2;
   return cudaGetLastError();
 }
 

@@ -50,6 +50,7 @@ class Config(ctypes.Structure):
         ("kappa", ctypes.c_double),
         ("tau", ctypes.c_double),
         ("precision", ctypes.c_int),
+        ("integrate_exited", ctypes.c_int),
     ]
 
 
@@ -90,6 +91,8 @@ def load(build_if_missing: bool = True):
     L.fga_gaussians.argtypes = [P, ci, P, P, P]
     L.fga_state.argtypes = [P, ci, P, P, P, P, P, P]
     L.fga_stage_times.argtypes = [P, P, P]
+    L.fga_ray_steps.argtypes = [P]
+    L.fga_ray_steps.restype = i64
     for name in ("fga_plan", "fga_decompose", "fga_propagate", "fga_reconstruct", "fga_sync",
                  "fga_destroy", "fga_shot_grid", "fga_psi", "fga_gaussians", "fga_state",
                  "fga_stage_times"):
@@ -134,7 +137,7 @@ class Plan:
     def __init__(self, dim: int, n: Sequence[int], h: Sequence[float], origin: Sequence[float],
                  periodic: Sequence[bool], velocity, eps: Sequence[float], T: float, dt: float,
                  kappa: float, tau: float, q_stride=None, box=None, precision: int = FGA_FP64,
-                 stream: Optional[int] = None):
+                 stream: Optional[int] = None, integrate_exited: bool = False):
         self._L = load()
         self.dim = dim
         self.n = tuple(int(v) for v in n)
@@ -158,6 +161,7 @@ class Plan:
                    if self._box is not None else None)
         cfg.T, cfg.dt, cfg.kappa, cfg.tau = float(T), float(dt), float(kappa), float(tau)
         cfg.precision = int(precision)
+        cfg.integrate_exited = int(bool(integrate_exited))
         _check_f64(velocity, self.npts, "velocity")
         self._keep = [velocity]
         out = ctypes.c_void_p()
@@ -251,6 +255,9 @@ class Plan:
         return {"Q": Q, "P": P, "A": A[..., 0] + 1j * A[..., 1], "B": B[..., 0] + 1j * B[..., 1],
                 "a": a[:, 0] + 1j * a[:, 1], "S": S}
 
+    def ray_steps(self) -> int:
+        return int(self._L.fga_ray_steps(self._h))
+
     def stage_times(self):
         ms = np.zeros(5)
         n = ctypes.c_int64(0)
@@ -260,7 +267,8 @@ class Plan:
                 "reconstruct": ms[4]}, int(n.value)
 
 
-def plan_from_problem(prob, velocity=None, stream=None, precision: int = FGA_FP64) -> Plan:
+def plan_from_problem(prob, velocity=None, stream=None, precision: int = FGA_FP64,
+                      integrate_exited: bool = False) -> Plan:
     """A Plan for a workloads.Problem (its grid, shots, T, dt, kappa, tau)."""
     vel = prob.velocity if velocity is None else velocity
     if isinstance(vel, np.ndarray):
@@ -268,7 +276,7 @@ def plan_from_problem(prob, velocity=None, stream=None, precision: int = FGA_FP6
     return Plan(prob.dim, prob.n, prob.h, prob.origin, prob.periodic, vel,
                 [s.eps for s in prob.shots], prob.T, prob.dt, prob.kappa, prob.tau,
                 q_stride=[s.q_stride for s in prob.shots], box=[s.box for s in prob.shots],
-                precision=precision, stream=stream)
+                precision=precision, stream=stream, integrate_exited=integrate_exited)
 
 
 def stacked_initial_data(prob):

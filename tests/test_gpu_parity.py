@@ -32,9 +32,12 @@ def _grid(prob):
     return O.Grid(prob.n, prob.h, prob.origin, prob.periodic)
 
 
-def run_gpu(prob, device=True):
+def run_gpu(prob, device=True, integrate_exited=True):
+    """Run the three steps through the C ABI. By default every ray is integrated to T so
+    that ray states can be compared with the oracle's."""
     torch = _torch()
-    plan = F.plan_from_problem(prob, stream=torch.cuda.current_stream().cuda_stream)
+    plan = F.plan_from_problem(prob, stream=torch.cuda.current_stream().cuda_stream,
+                               integrate_exited=integrate_exited)
     u0, u1 = F.stacked_initial_data(prob)
     if device:
         a, b = torch.from_numpy(u0).cuda(), torch.from_numpy(u1).cuda()
@@ -253,7 +256,10 @@ def test_layered_full_size_sampled_and_invariants():
     plus = np.flatnonzero(gs["sigma"] == 1)
     pick = np.random.default_rng(11).choice(plus, 96, replace=False)
     check_rays(plan, prob, 0, gs["qidx"][pick], gs["pidx"][pick], tol_q=1e-8, tol_a=1e-8)
-    # invariants for every GPU ray: c(Q)|P| = c(q)|p| and a^2/(c(Q)^2 det Z) = 1/c(q)^2
+    # invariants for every GPU ray: c(Q)|P| = c(q)|p| and a^2/(c(Q)^2 det Z) = 1/c(q)^2.
+    # Both drift only by the RK4 truncation error of 2000 steps of 1 ms through the
+    # spline medium (largest drift observed 2e-7: at the knots the Hessian of c has
+    # kinks, which lowers RK4's order); a wrong term on the GPU breaks them at O(1).
     st = plan.state(0)
     q = O.q_points(g, sh.q_stride)[qi]
     p = O.p_points(g, sh.eps, sh.box)[pi]
@@ -261,13 +267,36 @@ def test_layered_full_size_sampled_and_invariants():
     cQ = _bspline_c(prob, st["Q"])
     H0 = cq * np.linalg.norm(p, axis=1)
     H = cQ * np.linalg.norm(st["P"], axis=1)
-    assert np.max(np.abs(H - H0) / H0) <= 1e-8
+    assert np.max(np.abs(H - H0) / H0) <= 1e-6
     Z = st["A"] + 1j * st["B"]
     inv = st["a"] ** 2 / (cQ ** 2 * np.linalg.det(Z))
-    assert np.max(np.abs(inv * cq ** 2 - 1.0)) <= 1e-8
+    assert np.max(np.abs(inv * cq ** 2 - 1.0)) <= 1e-6
     assert np.max(np.abs(st["S"])) <= 1e-12
     assert np.all(np.isfinite(u))
     plan.close()
+
+
+def test_stopping_exited_rays_leaves_the_field_unchanged():
+    # rays whose window has left an open axis for good stop integrating (the default);
+    # their terms vanish on the grid either way, so the field is identical bit for bit
+    prob = WL.layered_single(T=1.0)
+    p_all, c_all, u_all = run_gpu(prob, integrate_exited=True)
+    p_cut, c_cut, u_cut = run_gpu(prob, integrate_exited=False)
+    assert np.array_equal(c_all, c_cut)
+    assert np.array_equal(u_all, u_cut)
+    st_all, st_cut = p_all.state(0), p_cut.state(0)
+    stopped = np.any(st_all["Q"] != st_cut["Q"], axis=1)
+    assert stopped.sum() > 0
+    # every stopped ray lies outside the grid by more than its window, moving away
+    sh = prob.shots[0]
+    reach = prob.kappa * math.sqrt(sh.eps) + 2 * np.array(prob.h)
+    lo = np.array(prob.origin) - reach
+    hi = np.array(prob.origin) + (np.array(prob.n) - 1) * np.array(prob.h) + reach
+    Q, P = st_cut["Q"][stopped], st_cut["P"][stopped]
+    away = ((Q < lo) & (P <= 0)) | ((Q > hi) & (P >= 0))
+    assert np.all(np.any(away, axis=1))
+    p_all.close()
+    p_cut.close()
 
 
 def test_layered_short_time_field_sampled():
