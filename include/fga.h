@@ -174,6 +174,44 @@ int64_t fga_ray_steps(fga_plan_t plan);
  * library since the plan was created. */
 fga_status fga_stage_times(fga_plan_t plan, double* ms5, int64_t* launches);
 
+/* ---- reconstruction without any device allocation ----
+ *
+ * The paper has no counterpart of this call; it exists for callers that cannot
+ * allocate device memory (code running where cudaMalloc is off limits, such as
+ * a host callback or a layer whose device memory is all owned by someone else,
+ * or a caller that has budgeted every byte of the device). It is fga_reconstruct
+ * for one set of propagated Gaussians given by the caller, with the scratch the
+ * plan would allocate (tile offsets and per-tile Gaussian lists, 8.3 MiB) held in
+ * one fixed file-scope device array instead. Every GPU that loads the library
+ * holds that array until the process exits.
+ *
+ *   u(x) = Re sum_g coef_g prod_k X_k,   X_k = exp(i P_k (x_k - Q_k)/eps
+ *                                                - (x_k - Q_k)^2/(2 eps))
+ * cut to |x_k - Q_k| <= kappa sqrt(eps) on each axis (all images on periodic
+ * axes). With coef_g = 2 W a_g psi_g (2 pi eps)^{-3d/2} exp(i S_g/eps) this is the
+ * field fga_reconstruct writes for one shot.
+ *
+ * dim, n, h, origin, periodic: the output grid (as in fga_config); eps, kappa > 0.
+ * qp: device, [2*dim][nG] FP64: rows Q_0..Q_{dim-1} then P_0..P_{dim-1}.
+ * coef: device, [nG][2] FP64 (re, im). u: device, [n...] FP64, overwritten.
+ * stream: a cudaStream_t (NULL = legacy default stream).
+ *
+ * Limits: the grid may have at most 16384 tiles (64 x 64 points in 2D, 256 in
+ * 1D); larger grids get FGA_ERR_CAPACITY. Any nG < 2^31 is accepted: the
+ * Gaussians are processed in chunks whose tile lists fit 2^21 entries.
+ * The call allocates nothing (no cudaMalloc, cudaFree or allocating library
+ * routine) and waits for its stream before returning (it reads a status word).
+ * Its first call on a device looks up the array's device address on that
+ * device; make that first call before any stream capture on the device.
+ * Every call uses the same array and leaves its contents behind (the call
+ * clears what must start at zero): calls that overlap on the GPU -- on two
+ * streams, or from two host threads -- race on it and must be serialised.
+ * Errors: FGA_ERR_INVALID (arguments, host pointers), FGA_ERR_CAPACITY,
+ * FGA_ERR_CUDA; the message is returned by fga_last_error(NULL). */
+fga_status fga_reconstruct_static(int dim, const int64_t* n, const double* h, const double* origin,
+                                  const int* periodic, double eps, double kappa, int64_t nG,
+                                  const double* qp, const double* coef, double* u, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

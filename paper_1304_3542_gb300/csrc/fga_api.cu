@@ -114,6 +114,10 @@ fga_status read_status(fga_plan_s* p) {
 
 }  // namespace
 
+namespace fga {
+void set_unbound_error(const std::string& msg) { g_plan_error = msg; }
+}  // namespace fga
+
 extern "C" {
 
 const char* fga_status_string(fga_status s) {

@@ -11,6 +11,11 @@
 // the per-axis factors of a chunk of Gaussians into shared memory and
 // accumulates the tile in registers, FP64 throughout. The scatter-free form
 // needs no atomics on the output and gives a deterministic summation order.
+#include <cmath>
+#include <cstring>
+#include <mutex>
+#include <string>
+
 #include "fga_internal.cuh"
 
 namespace fga {
@@ -434,3 +439,306 @@ cudaError_t launch_reconstruct(fga_plan_s* p, double* u_dev) {
 int tile_edge(int dim) { return dim == 1 ? T1 : T2; }
 
 }  // namespace fga
+
+// ---------------------------------------------------------------------------
+// Reconstruction that allocates nothing (fga_reconstruct_static in fga.h).
+//
+// For callers that cannot call cudaMalloc: code that runs where the allocator
+// is off limits (for instance inside a host callback or a driver layer that owns
+// all device memory), or a caller that has budgeted every byte of the device.
+// The scratch that the plan-based path allocates per plan -- the shot record,
+// the per-tile offsets and the per-tile Gaussian lists -- lives here in one
+// file-scope device array of fixed size, which every GPU that loads this
+// library holds until the process exits. The caller passes the inputs
+// (centres, momenta and coefficients of the Gaussians) and the output grid.
+// ---------------------------------------------------------------------------
+
+namespace fga {
+namespace {
+
+constexpr int64_t kStaticMaxTiles = 16384;     // 64x64 tiles (2D) or 256-point tiles (1D)
+constexpr int64_t kStaticMaxPairs = 1 << 21;   // (Gaussian, tile) list entries per chunk
+constexpr size_t align256(size_t b) { return (b + 255) / 256 * 256; }
+constexpr size_t kStOffShot = 0;
+constexpr size_t kStOffStatus = align256(sizeof(ShotDev));
+constexpr size_t kStOffTiles = kStOffStatus + 256;
+constexpr size_t kStOffList = kStOffTiles + align256(sizeof(int64_t) * (kStaticMaxTiles + 1));
+constexpr size_t kStaticBytes = kStOffList + align256(sizeof(int32_t) * kStaticMaxPairs);
+
+// Gather of one tile over its whole list, added to the output (chunks of Gaussians
+// are summed one after the other, so the order of summation is fixed).
+__global__ void __launch_bounds__(NT) k_gather2_tile_add(GridDev gd, const ShotDev* __restrict__ shots,
+                                                         double kappa,
+                                                         const double* __restrict__ state, int64_t ld,
+                                                         const double2* __restrict__ coef,
+                                                         const int64_t* __restrict__ off,
+                                                         const int32_t* __restrict__ list,
+                                                         int64_t list_cap, double* __restrict__ out) {
+  const int64_t t = blockIdx.x;
+  const ShotDev& sh = shots[0];
+  const double cut = kappa * sh.sqrt_eps, inv_eps = sh.inv_eps;
+  int64_t a[2], b[2];
+  tile_box<2>(gd, sh, t, a, b);
+  __shared__ double2 Xs[CH][T2];
+  __shared__ double2 Zs[CH][T2];
+  __shared__ int win[CH][4];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int wx = warp >> 1, wz = warp & 1;
+  const int lx = lane >> 3, lz = lane & 7;
+  const int x0 = wx * 16 + lx * 4, z0 = wz * 32 + lz * 4;
+  const int px0 = wx * 16, px1 = wx * 16 + 15, pz0 = wz * 32, pz1 = wz * 32 + 31;
+  double accr[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) accr[i][j] = 0.0;
+  const int64_t l0 = min(off[t], list_cap), l1 = min(off[t + 1], list_cap);
+  for (int64_t c0 = l0; c0 < l1; c0 += CH) {
+    const int nc = (int)((l1 - c0) < CH ? (l1 - c0) : CH);
+    {
+      const int gi = threadIdx.x >> 4, axis = (threadIdx.x >> 3) & 1, part = threadIdx.x & 7;
+      if (gi < nc) {
+        int32_t g = list[c0 + gi];
+        double Q = state[axis * ld + g], P = state[(2 + axis) * ld + g];
+        double2 cf = axis == 0 ? coef[g] : make_double2(1.0, 0.0);
+        double2* dst = (axis == 0 ? Xs[gi] : Zs[gi]) + part * 8;
+        if (gd.periodic[axis]) {
+          for (int r = 0; r < 8; ++r) {
+            double2 f = axis_factor(gd, axis, a[axis] + part * 8 + r, Q, P, cut, inv_eps);
+            dst[r] = make_double2(cf.x * f.x - cf.y * f.y, cf.x * f.y + cf.y * f.x);
+          }
+        } else {
+          double xi0 = gd.o[axis] + (double)(a[axis] + part * 8) * gd.h[axis];
+          axis_factors8(xi0, gd.h[axis], Q, P, cut, inv_eps, cf, dst);
+        }
+        if (part == 0) {
+          if (gd.periodic[axis]) {
+            win[gi][2 * axis] = 0;
+            win[gi][2 * axis + 1] = T2 - 1;
+          } else {
+            int64_t lo, hi;
+            window_range(gd, axis, Q, cut, lo, hi);
+            win[gi][2 * axis] = (int)((lo - a[axis]) > -1 ? (lo - a[axis]) : -1);
+            win[gi][2 * axis + 1] = (int)((hi - a[axis]) < T2 ? (hi - a[axis]) : T2);
+          }
+        }
+      }
+    }
+    __syncthreads();
+    for (int gi = 0; gi < nc; ++gi) {
+      if (win[gi][0] > px1 || win[gi][1] < px0 || win[gi][2] > pz1 || win[gi][3] < pz0) continue;
+      double2 xv[4], zv[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        xv[i] = Xs[gi][x0 + i];
+        zv[i] = Zs[gi][z0 + i];
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+          accr[i][j] = fma(xv[i].x, zv[j].x, fma(-xv[i].y, zv[j].y, accr[i][j]));
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    int64_t ix = a[0] + x0 + i;
+    if (ix > b[0]) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      int64_t iz = a[1] + z0 + j;
+      if (iz > b[1]) continue;
+      out[ix * gd.n[1] + iz] += accr[i][j];
+    }
+  }
+}
+
+__global__ void __launch_bounds__(NT) k_gather1_tile_add(GridDev gd, const ShotDev* __restrict__ shots,
+                                                         double kappa,
+                                                         const double* __restrict__ state, int64_t ld,
+                                                         const double2* __restrict__ coef,
+                                                         const int64_t* __restrict__ off,
+                                                         const int32_t* __restrict__ list,
+                                                         int64_t list_cap, double* __restrict__ out) {
+  const int64_t t = blockIdx.x;
+  const ShotDev& sh = shots[0];
+  const double cut = kappa * sh.sqrt_eps, inv_eps = sh.inv_eps;
+  const int64_t i = t * T1 + threadIdx.x;
+  __shared__ double sQ[CH1], sP[CH1];
+  __shared__ double2 sC[CH1];
+  double re = 0.0;
+  const int64_t l0 = min(off[t], list_cap), l1 = min(off[t + 1], list_cap);
+  for (int64_t c0 = l0; c0 < l1; c0 += CH1) {
+    int nc = (int)((l1 - c0) < CH1 ? (l1 - c0) : CH1);
+    if (threadIdx.x < nc) {
+      int32_t g = list[c0 + threadIdx.x];
+      sQ[threadIdx.x] = state[0 * ld + g];
+      sP[threadIdx.x] = state[1 * ld + g];
+      sC[threadIdx.x] = coef[g];
+    }
+    __syncthreads();
+    for (int j = 0; j < nc; ++j) {
+      double2 x = axis_factor(gd, 0, i, sQ[j], sP[j], cut, inv_eps);
+      re = fma(sC[j].x, x.x, fma(-sC[j].y, x.y, re));
+    }
+    __syncthreads();
+  }
+  if (i < gd.n[0]) out[i] += re;
+}
+
+}  // namespace
+}  // namespace fga
+
+// The scratch of fga_reconstruct_static: [shot record | status | tile offsets | lists].
+static __device__ __align__(256) unsigned char fga_static_scratch[fga::kStaticBytes];
+
+namespace {
+
+constexpr int kStaticMaxDevices = 64;
+std::mutex g_static_mu;
+void* g_static_addr[kStaticMaxDevices] = {};
+
+// Device address of the scratch on the current device, looked up once per device.
+cudaError_t static_scratch_address(void** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kStaticMaxDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_static_mu);
+  if (!g_static_addr[dev]) {
+    void* ptr = nullptr;
+    e = cudaGetSymbolAddress(&ptr, fga_static_scratch);
+    if (e != cudaSuccess) return e;
+    g_static_addr[dev] = ptr;
+  }
+  *out = g_static_addr[dev];
+  return cudaSuccess;
+}
+
+fga_status static_fail(fga_status st, const std::string& msg) {
+  fga::set_unbound_error(msg);
+  return st;
+}
+
+bool device_pointer(const void* ptr) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+}  // namespace
+
+extern "C" fga_status fga_reconstruct_static(int dim, const int64_t* n, const double* h,
+                                             const double* origin, const int* periodic, double eps,
+                                             double kappa, int64_t nG, const double* qp,
+                                             const double* coef, double* u, void* stream) {
+  using namespace fga;
+  if (dim < 1 || dim > 2) return static_fail(FGA_ERR_INVALID, "dim must be 1 or 2");
+  if (!n || !h || !origin || !periodic || !u)
+    return static_fail(FGA_ERR_INVALID, "grid description and u must not be NULL");
+  if (!(eps > 0.0) || !std::isfinite(eps) || !(kappa > 0.0) || !std::isfinite(kappa))
+    return static_fail(FGA_ERR_INVALID, "eps and kappa must be finite and > 0");
+  if (nG < 0 || nG > (((int64_t)1 << 31) - 1))
+    return static_fail(FGA_ERR_INVALID, "nG must be in [0, 2^31 - 1]");
+  if (nG > 0 && (!qp || !coef)) return static_fail(FGA_ERR_INVALID, "qp and coef must not be NULL");
+  if (!device_pointer(u) || (nG > 0 && (!device_pointer(qp) || !device_pointer(coef))))
+    return static_fail(FGA_ERR_INVALID, "qp, coef and u must be device pointers");
+  cudaStream_t st = (cudaStream_t)stream;
+  GridDev gd;
+  std::memset(&gd, 0, sizeof(gd));
+  gd.dim = dim;
+  gd.npts = 1;
+  ShotDev sh;
+  std::memset(&sh, 0, sizeof(sh));
+  sh.eps = eps;
+  sh.sqrt_eps = std::sqrt(eps);
+  sh.inv_eps = 1.0 / eps;
+  const int TS = tile_edge(dim);
+  int64_t ntiles = 1;
+  size_t per = 1;  // tiles one Gaussian can meet at most
+  for (int k = 0; k < dim; ++k) {
+    if (n[k] < 4 || n[k] > ((int64_t)1 << 30) || !(h[k] > 0.0) || !std::isfinite(h[k]) ||
+        !std::isfinite(origin[k]))
+      return static_fail(FGA_ERR_INVALID, "bad grid axis");
+    gd.n[k] = n[k];
+    gd.h[k] = h[k];
+    gd.o[k] = origin[k];
+    gd.inv_h[k] = 1.0 / h[k];
+    gd.periodic[k] = periodic[k] ? 1 : 0;
+    gd.L[k] = gd.periodic[k] ? (double)n[k] * h[k] : 0.0;
+    gd.npts *= n[k];
+    sh.ntile[k] = (int)((n[k] + TS - 1) / TS);
+    ntiles *= sh.ntile[k];
+    if (gd.periodic[k] && kappa * sh.sqrt_eps > 2.0 * gd.L[k])
+      return static_fail(FGA_ERR_INVALID, "kappa sqrt(eps) must not exceed two periods");
+    double wpts = 2.0 * kappa * sh.sqrt_eps * gd.inv_h[k] + 6.0;
+    size_t mk = (size_t)(wpts / TS) + 2;
+    if (gd.periodic[k]) mk *= 5;
+    per *= std::min<size_t>(mk, (size_t)sh.ntile[k]);
+  }
+  for (int k = dim; k < kMaxDim; ++k) {
+    gd.n[k] = 1;
+    gd.h[k] = gd.inv_h[k] = 1.0;
+  }
+  if (ntiles > kStaticMaxTiles)
+    return static_fail(FGA_ERR_CAPACITY,
+                       "the grid needs " + std::to_string(ntiles) + " tiles; the static scratch holds " +
+                           std::to_string(kStaticMaxTiles));
+  void* base = nullptr;
+  cudaError_t e = static_scratch_address(&base);
+  if (e != cudaSuccess)
+    return static_fail(FGA_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+  unsigned char* b8 = (unsigned char*)base;
+  ShotDev* d_shot = (ShotDev*)(b8 + kStOffShot);
+  int* d_status = (int*)(b8 + kStOffStatus);
+  int64_t* d_off = (int64_t*)(b8 + kStOffTiles);
+  int32_t* d_list = (int32_t*)(b8 + kStOffList);
+#define ST_CUDA(call)                                                                     \
+  do {                                                                                    \
+    cudaError_t e_ = (call);                                                              \
+    if (e_ != cudaSuccess)                                                                \
+      return static_fail(FGA_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+  ST_CUDA(cudaMemsetAsync(u, 0, sizeof(double) * gd.npts, st));
+  ST_CUDA(cudaMemsetAsync(d_status, 0, sizeof(int), st));
+  const int64_t chunk = std::max<int64_t>(1, kStaticMaxPairs / (int64_t)per);
+  const double2* cf = reinterpret_cast<const double2*>(coef);
+  for (int64_t g0 = 0; g0 < nG; g0 += chunk) {
+    sh.g_off = g0;
+    sh.g_cnt = std::min<int64_t>(chunk, nG - g0);
+    // pageable source: the copy is staged before cudaMemcpyAsync returns
+    ST_CUDA(cudaMemcpyAsync(d_shot, &sh, sizeof(ShotDev), cudaMemcpyHostToDevice, st));
+    if (dim == 1) {
+      k_bin<1, false><<<(unsigned)ntiles, NT, 0, st>>>(gd, d_shot, 1, kappa, qp, nG, d_off, nullptr,
+                                                       nullptr, 0, d_status);
+    } else {
+      k_bin<2, false><<<(unsigned)ntiles, NT, 0, st>>>(gd, d_shot, 1, kappa, qp, nG, d_off, nullptr,
+                                                       nullptr, 0, d_status);
+    }
+    ST_CUDA(cudaGetLastError());
+    ST_CUDA(launch_scan_on(st, d_off, ntiles));
+    if (dim == 1) {
+      k_bin<1, true><<<(unsigned)ntiles, NT, 0, st>>>(gd, d_shot, 1, kappa, qp, nG, nullptr, d_off,
+                                                      d_list, kStaticMaxPairs, d_status);
+      k_gather1_tile_add<<<(unsigned)ntiles, NT, 0, st>>>(gd, d_shot, kappa, qp, nG, cf, d_off,
+                                                          d_list, kStaticMaxPairs, u);
+    } else {
+      k_bin<2, true><<<(unsigned)ntiles, NT, 0, st>>>(gd, d_shot, 1, kappa, qp, nG, nullptr, d_off,
+                                                      d_list, kStaticMaxPairs, d_status);
+      k_gather2_tile_add<<<(unsigned)ntiles, NT, 0, st>>>(gd, d_shot, kappa, qp, nG, cf, d_off,
+                                                          d_list, kStaticMaxPairs, u);
+    }
+    ST_CUDA(cudaGetLastError());
+  }
+  int status = 0;
+  ST_CUDA(cudaMemcpyAsync(&status, d_status, sizeof(int), cudaMemcpyDeviceToHost, st));
+  ST_CUDA(cudaStreamSynchronize(st));
+#undef ST_CUDA
+  if (status & kStatusCapacity)
+    return static_fail(FGA_ERR_CAPACITY, "a chunk overflowed the static tile lists");
+  return FGA_OK;
+}

@@ -199,6 +199,11 @@ cudaError_t launch_select(fga_plan_s* p) {
   return cudaGetLastError();
 }
 
+cudaError_t launch_scan_on(cudaStream_t stream, int64_t* a, int64_t n) {
+  k_scan_exclusive<<<1, 1024, 0, stream>>>(a, n);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_scan(fga_plan_s* p, int64_t* a, int64_t n) {
   k_scan_exclusive<<<1, 1024, 0, p->stream>>>(a, n);
   p->launches += 1;

@@ -93,6 +93,9 @@ def load(build_if_missing: bool = True):
     L.fga_stage_times.argtypes = [P, P, P]
     L.fga_ray_steps.argtypes = [P]
     L.fga_ray_steps.restype = i64
+    L.fga_reconstruct_static.argtypes = [ci, P, P, P, P, ctypes.c_double, ctypes.c_double, i64,
+                                         P, P, P, P]
+    L.fga_reconstruct_static.restype = ci
     for name in ("fga_plan", "fga_decompose", "fga_propagate", "fga_reconstruct", "fga_sync",
                  "fga_destroy", "fga_shot_grid", "fga_psi", "fga_gaussians", "fga_state",
                  "fga_stage_times"):
@@ -265,6 +268,28 @@ class Plan:
                     "fga_stage_times")
         return {"fbi": ms[0], "select": ms[1], "rays": ms[2], "binning": ms[3],
                 "reconstruct": ms[4]}, int(n.value)
+
+
+def reconstruct_static(dim: int, n: Sequence[int], h: Sequence[float], origin: Sequence[float],
+                       periodic: Sequence[bool], eps: float, kappa: float, qp, coef, u,
+                       stream: Optional[int] = None):
+    """fga_reconstruct_static: the reconstruction without any device allocation.
+    qp: device float64 [2*dim][nG] (Q rows then P rows); coef: device float64 [nG][2];
+    u: device float64 grid, overwritten."""
+    L = load()
+    nG = 0
+    if qp is not None:
+        nG = (qp.numel() if hasattr(qp, "numel") else qp.size) // (2 * dim)
+    n_ = np.ascontiguousarray(n, dtype=np.int64)
+    h_ = np.ascontiguousarray(h, dtype=np.float64)
+    o_ = np.ascontiguousarray(origin, dtype=np.float64)
+    p_ = np.ascontiguousarray([1 if v else 0 for v in periodic], dtype=np.int32)
+    st = L.fga_reconstruct_static(dim, n_.ctypes.data, h_.ctypes.data, o_.ctypes.data,
+                                  p_.ctypes.data, float(eps), float(kappa), nG, _ptr(qp),
+                                  _ptr(coef), _ptr(u), stream)
+    if st != FGA_OK:
+        raise FGAError(st, "fga_reconstruct_static", L.fga_last_error(None).decode())
+    return u
 
 
 def plan_from_problem(prob, velocity=None, stream=None, precision: int = FGA_FP64,
