@@ -280,7 +280,7 @@ fga_status fga_plan(const fga_config* cfg, const double* velocity, void* stream,
   PLAN_CUDA(cudaMemcpyAsync(p->d_coef, velocity, sizeof(double) * gd.npts, cudaMemcpyDefault,
                             p->stream));
   PLAN_CUDA(cudaMalloc(&p->d_status, sizeof(int)));
-  PLAN_CUDA(cudaMalloc(&p->d_steps, sizeof(unsigned long long)));
+  PLAN_CUDA(cudaMalloc(&p->d_steps, 2 * sizeof(unsigned long long)));
   PLAN_CUDA(cudaMemsetAsync(p->d_status, 0, sizeof(int), p->stream));
   k_check_velocity<<<256, 256, 0, p->stream>>>(p->d_coef, gd.npts, p->d_status);
   p->launches += 1;

@@ -15,7 +15,11 @@
 // the state (structure of arrays, coalesced) and the complex coefficient of the
 // reconstruction sum, 2 W a psi (2 pi eps)^{-3d/2} e^{i S/eps} (the 2 accounts for the
 // conjugate - branch). Unless asked to integrate every ray to T, a ray stops once its
-// window has left an open axis for good (see fga_config.integrate_exited).
+// window has left an open axis for good (see fga_config.integrate_exited); the kernel
+// is persistent (one grid of resident blocks pulling Gaussians from a counter) so that
+// lanes whose ray stopped early pick up new work instead of idling in their warp.
+#include <algorithm>
+
 #include "fga_internal.cuh"
 #include "fga_medium.cuh"
 
@@ -119,27 +123,14 @@ __device__ __forceinline__ bool rhs(const GridDev& gd, const double* __restrict_
   return pn2 > 0.0 && dd > 0.0;
 }
 
+// Initial state of Gaussian (q index qf, p index pj): Q = q, P = p, A = I, B = -iI,
+// a = 2^{d/2}, S = 0.
 template <int D>
-__global__ void __launch_bounds__(128) k_rays(GridDev gd, const ShotDev* __restrict__ shots,
-                                              const double* __restrict__ C, int64_t G,
-                                              const int32_t* __restrict__ gshot,
-                                              const int64_t* __restrict__ gq,
-                                              const int32_t* __restrict__ gp,
-                                              const double2* __restrict__ gpsi, int64_t nsteps,
-                                              double dt, double kappa, int integrate_exited,
-                                              double* __restrict__ state, int64_t ld,
-                                              double2* __restrict__ coef, int* status,
-                                              unsigned long long* steps_done) {
+__device__ __forceinline__ void ray_init(const GridDev& gd, const ShotDev& sh, int64_t qf, int64_t pj,
+                                         double* y) {
   using Lo = Layout<D>;
-  constexpr int NF = Lo::NF;
-  int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (g >= G) return;
-  const int s = gshot[g];
-  const ShotDev& sh = shots[s];
-  double y[NF];
 #pragma unroll
-  for (int i = 0; i < NF; ++i) y[i] = 0.0;
-  int64_t qf = gq[g], pj = gp[g];
+  for (int i = 0; i < Lo::NF; ++i) y[i] = 0.0;
   int64_t qm[D], pm[D];
   if constexpr (D == 1) {
     qm[0] = qf;
@@ -159,71 +150,16 @@ __global__ void __launch_bounds__(128) k_rays(GridDev gd, const ShotDev* __restr
     y[Lo::BI + i * D + i] = -1.0;
   }
   y[Lo::aR] = (D == 1) ? 1.4142135623730951 : 2.0;
-  // exit box: beyond these bounds on an open axis the window misses the grid and the
-  // spline's taps are all clamped, so c does not depend on Q_k there
-  double lo[D], hi[D];
+}
+
+// Final state (structure of arrays) and coefficient 2 W a psi (2 pi eps)^{-3d/2} e^{iS/eps}.
+template <int D>
+__device__ __forceinline__ bool ray_store(const ShotDev& sh, int64_t g, const double* y,
+                                          const double2* __restrict__ gpsi, double* __restrict__ state,
+                                          int64_t ld, double2* __restrict__ coef) {
+  using Lo = Layout<D>;
 #pragma unroll
-  for (int i = 0; i < D; ++i) {
-    double reach = kappa * sh.sqrt_eps + 2.0 * gd.h[i];
-    lo[i] = gd.o[i] - reach;
-    hi[i] = gd.o[i] + (double)(gd.n[i] - 1) * gd.h[i] + reach;
-  }
-  bool ok = true;
-  const double h2 = 0.5 * dt, h6 = dt / 6.0, h3 = dt / 3.0;
-  int64_t step = 0;
-  for (; step < nsteps; ++step) {
-    if (!integrate_exited) {
-      bool gone = false;
-#pragma unroll
-      for (int i = 0; i < D; ++i)
-        gone = gone || (!gd.periodic[i] && ((y[Lo::Q + i] < lo[i] && y[Lo::P + i] <= 0.0) ||
-                                            (y[Lo::Q + i] > hi[i] && y[Lo::P + i] >= 0.0)));
-      if (gone) break;
-    }
-    double acc[NF], tmp[NF], k[NF];
-    ok &= rhs<D>(gd, C, y, k);
-#pragma unroll
-    for (int i = 0; i < NF; ++i) {
-      acc[i] = fma(h6, k[i], y[i]);
-      tmp[i] = fma(h2, k[i], y[i]);
-    }
-    ok &= rhs<D>(gd, C, tmp, k);
-#pragma unroll
-    for (int i = 0; i < NF; ++i) {
-      acc[i] = fma(h3, k[i], acc[i]);
-      tmp[i] = fma(h2, k[i], y[i]);
-    }
-    ok &= rhs<D>(gd, C, tmp, k);
-#pragma unroll
-    for (int i = 0; i < NF; ++i) {
-      acc[i] = fma(h3, k[i], acc[i]);
-      tmp[i] = fma(dt, k[i], y[i]);
-    }
-    ok &= rhs<D>(gd, C, tmp, k);
-#pragma unroll
-    for (int i = 0; i < NF; ++i) y[i] = fma(h6, k[i], acc[i]);
-#pragma unroll
-    for (int i = 0; i < D; ++i) {
-      if (gd.periodic[i]) {
-        double r = fmod(y[Lo::Q + i] - gd.o[i], gd.L[i]);
-        if (r < 0) r += gd.L[i];
-        y[Lo::Q + i] = gd.o[i] + r;
-      }
-    }
-  }
-  // count of the steps integrated, summed over the converged lanes of the warp
-  {
-    unsigned mask = __activemask();
-    unsigned tot = __reduce_add_sync(mask, (unsigned)step);
-    if ((int)(threadIdx.x & 31) == __ffs(mask) - 1) atomicAdd(steps_done, (unsigned long long)tot);
-  }
-  bool fin = isfinite(y[Lo::aR]) && isfinite(y[Lo::aI]) && isfinite(y[Lo::S]);
-#pragma unroll
-  for (int i = 0; i < D; ++i) fin = fin && isfinite(y[Lo::Q + i]) && isfinite(y[Lo::P + i]);
-  if (!(ok && fin)) atomicOr(status, kStatusNumeric);
-#pragma unroll
-  for (int i = 0; i < NF; ++i) state[i * ld + g] = y[i];
-  // coefficient 2 W a psi (2 pi eps)^{-3d/2} e^{i S/eps}
+  for (int i = 0; i < Lo::NF; ++i) state[i * ld + g] = y[i];
   double2 ps = gpsi[g];
   double sc = 2.0 * sh.W * sh.norm;
   double ar = y[Lo::aR], ai = y[Lo::aI];
@@ -231,25 +167,139 @@ __global__ void __launch_bounds__(128) k_rays(GridDev gd, const ShotDev* __restr
   double sn, cs;
   sincos(y[Lo::S] * sh.inv_eps, &sn, &cs);
   coef[g] = make_double2(pr * cs - pi * sn, pr * sn + pi * cs);
+  bool fin = isfinite(y[Lo::aR]) && isfinite(y[Lo::aI]) && isfinite(y[Lo::S]);
+#pragma unroll
+  for (int i = 0; i < D; ++i) fin = fin && isfinite(y[Lo::Q + i]) && isfinite(y[Lo::P + i]);
+  return fin;
+}
+
+// Persistent integrator: every lane takes the next Gaussian from a global counter as
+// soon as its ray has reached T (or left the grid for good), so the warps stay full
+// whatever the mix of ray lifetimes. Each ray's arithmetic does not depend on which
+// lane runs it, so the results are the same as with one thread per Gaussian.
+template <int D>
+__global__ void __launch_bounds__(128) k_rays(GridDev gd, const ShotDev* __restrict__ shots,
+                                              const double* __restrict__ C, int64_t G,
+                                              const int32_t* __restrict__ gshot,
+                                              const int64_t* __restrict__ gq,
+                                              const int32_t* __restrict__ gp,
+                                              const double2* __restrict__ gpsi, int64_t nsteps,
+                                              double dt, double kappa, int integrate_exited,
+                                              double* __restrict__ state, int64_t ld,
+                                              double2* __restrict__ coef, int* status,
+                                              unsigned long long* steps_done,
+                                              unsigned long long* next) {
+  using Lo = Layout<D>;
+  constexpr int NF = Lo::NF;
+  int64_t g = (int64_t)atomicAdd(next, 1ull);
+  unsigned long long my_steps = 0;
+  bool ok = true;
+  if (g < G) {
+    int s = gshot[g];
+    double y[NF];
+    ray_init<D>(gd, shots[s], gq[g], gp[g], y);
+    // exit box: beyond these bounds on an open axis the window misses the grid and the
+    // spline's taps are all clamped, so c does not depend on Q_k there
+    double lo[D], hi[D];
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+      double reach = kappa * shots[s].sqrt_eps + 2.0 * gd.h[i];
+      lo[i] = gd.o[i] - reach;
+      hi[i] = gd.o[i] + (double)(gd.n[i] - 1) * gd.h[i] + reach;
+    }
+    const double h2 = 0.5 * dt, h6 = dt / 6.0, h3 = dt / 3.0;
+    int64_t step = 0;
+    while (true) {
+      bool done = step >= nsteps;
+      if (!done && !integrate_exited) {
+#pragma unroll
+        for (int i = 0; i < D; ++i)
+          done = done || (!gd.periodic[i] && ((y[Lo::Q + i] < lo[i] && y[Lo::P + i] <= 0.0) ||
+                                              (y[Lo::Q + i] > hi[i] && y[Lo::P + i] >= 0.0)));
+      }
+      if (done) {
+        ok &= ray_store<D>(shots[s], g, y, gpsi, state, ld, coef);
+        my_steps += (unsigned long long)step;
+        g = (int64_t)atomicAdd(next, 1ull);
+        if (g >= G) break;
+        s = gshot[g];
+        ray_init<D>(gd, shots[s], gq[g], gp[g], y);
+#pragma unroll
+        for (int i = 0; i < D; ++i) {
+          double reach = kappa * shots[s].sqrt_eps + 2.0 * gd.h[i];
+          lo[i] = gd.o[i] - reach;
+          hi[i] = gd.o[i] + (double)(gd.n[i] - 1) * gd.h[i] + reach;
+        }
+        step = 0;
+        continue;
+      }
+      double acc[NF], tmp[NF], k[NF];
+      ok &= rhs<D>(gd, C, y, k);
+#pragma unroll
+      for (int i = 0; i < NF; ++i) {
+        acc[i] = fma(h6, k[i], y[i]);
+        tmp[i] = fma(h2, k[i], y[i]);
+      }
+      ok &= rhs<D>(gd, C, tmp, k);
+#pragma unroll
+      for (int i = 0; i < NF; ++i) {
+        acc[i] = fma(h3, k[i], acc[i]);
+        tmp[i] = fma(h2, k[i], y[i]);
+      }
+      ok &= rhs<D>(gd, C, tmp, k);
+#pragma unroll
+      for (int i = 0; i < NF; ++i) {
+        acc[i] = fma(h3, k[i], acc[i]);
+        tmp[i] = fma(dt, k[i], y[i]);
+      }
+      ok &= rhs<D>(gd, C, tmp, k);
+#pragma unroll
+      for (int i = 0; i < NF; ++i) y[i] = fma(h6, k[i], acc[i]);
+#pragma unroll
+      for (int i = 0; i < D; ++i) {
+        if (gd.periodic[i]) {
+          double r = fmod(y[Lo::Q + i] - gd.o[i], gd.L[i]);
+          if (r < 0) r += gd.L[i];
+          y[Lo::Q + i] = gd.o[i] + r;
+        }
+      }
+      ++step;
+    }
+  }
+  if (!ok) atomicOr(status, kStatusNumeric);
+  // steps integrated (one atomic per resident thread)
+  if (my_steps) atomicAdd(steps_done, my_steps);
 }
 
 }  // namespace
 
 cudaError_t launch_rays(fga_plan_s* p) {
-  cudaError_t e = cudaMemsetAsync(p->d_steps, 0, sizeof(unsigned long long), p->stream);
+  // d_steps[0]: steps integrated; d_steps[1]: the work counter of the persistent kernel
+  cudaError_t e = cudaMemsetAsync(p->d_steps, 0, 2 * sizeof(unsigned long long), p->stream);
   if (e != cudaSuccess) return e;
   if (p->G == 0) return cudaSuccess;
-  unsigned blocks = (unsigned)((p->G + 127) / 128);
+  if (p->ray_blocks == 0) {
+    int dev = 0, sms = 0, per_sm = 0;
+    e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess)
+      e = p->grid.dim == 1
+              ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rays<1>, 128, 0)
+              : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rays<2>, 128, 0);
+    if (e != cudaSuccess) return e;
+    p->ray_blocks = (int64_t)sms * (per_sm > 0 ? per_sm : 1);
+  }
+  unsigned blocks = (unsigned)std::min<int64_t>(p->ray_blocks, (p->G + 127) / 128);
   if (p->grid.dim == 1)
     k_rays<1><<<blocks, 128, 0, p->stream>>>(p->grid, p->d_shots, p->d_coef, p->G, p->d_gshot,
                                              p->d_gq, p->d_gp, p->d_gpsi, p->nsteps, p->dt, p->kappa,
                                              p->integrate_exited, p->d_state, (int64_t)p->g_cap,
-                                             p->d_gcoef, p->d_status, p->d_steps);
+                                             p->d_gcoef, p->d_status, p->d_steps, p->d_steps + 1);
   else
     k_rays<2><<<blocks, 128, 0, p->stream>>>(p->grid, p->d_shots, p->d_coef, p->G, p->d_gshot,
                                              p->d_gq, p->d_gp, p->d_gpsi, p->nsteps, p->dt, p->kappa,
                                              p->integrate_exited, p->d_state, (int64_t)p->g_cap,
-                                             p->d_gcoef, p->d_status, p->d_steps);
+                                             p->d_gcoef, p->d_status, p->d_steps, p->d_steps + 1);
   p->launches += 1;
   return cudaGetLastError();
 }
