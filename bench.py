@@ -165,7 +165,8 @@ def run_ours(args, rank, world, local_rank):
     dev = torch.device("cuda", local_rank)
     prob = workload()
     stream = torch.cuda.current_stream(dev)
-    plan = F.plan_from_problem(prob, stream=stream.cuda_stream)
+    precision = F.FGA_MIXED_TF32X3 if args.precision == "mixed" else F.FGA_FP64
+    plan = F.plan_from_problem(prob, stream=stream.cuda_stream, precision=precision)
     u0, u1 = F.stacked_initial_data(prob)
     d_u0 = torch.from_numpy(u0).to(dev)
     d_u1 = torch.from_numpy(u1).to(dev)
@@ -237,6 +238,31 @@ def run_ours(args, rank, world, local_rank):
     e2e_value = world * evals * args.steps / e2e_s
     npts = prob.npoints
 
+    rel_l2 = None
+    fp64_value = None
+    if precision != F.FGA_FP64:
+        # the FP64 path on the same input: the reference for the mixed path's error
+        ref = F.plan_from_problem(prob, stream=stream.cuda_stream, precision=F.FGA_FP64)
+        d_ref = torch.zeros_like(d_out)
+        ref.decompose(d_u0, d_u1)
+        ref.propagate()
+        ref.reconstruct(d_ref)
+        ref.sync()
+        rel_l2 = float((d_out - d_ref).norm() / d_ref.norm())
+        t64 = []
+        for i in range(max(1, args.steps)):
+            flush.fill_(float(i))
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ref.decompose(d_u0, d_u1)
+            ref.propagate()
+            ref.reconstruct(d_ref)
+            e1.record(stream)
+            e1.synchronize()
+            t64.append(e0.elapsed_time(e1) / 1e3)
+        fp64_value = evals / statistics.mean(t64)
+        ref.close()
     ray_s = statistics.mean(ray_ms) / 1e3
     steps_done = statistics.mean(ray_steps)
     ray_flops = FLOPS_PER_RAY_STEP_2D * steps_done
@@ -253,8 +279,9 @@ def run_ours(args, rank, world, local_rank):
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "f64",
+        "dtype": "f64" if precision == F.FGA_FP64 else "f64+tf32",
         "data": "synthetic (seeded layered model and Ricker ring; no dataset)",
+        "rel_l2_vs_fp64": rel_l2,
         "config": {
             "workload": workload_name(prob),
             "grid": list(prob.n),
@@ -267,7 +294,11 @@ def run_ours(args, rank, world, local_rank):
             "ray_steps_integrated": steps_done,
             "ray_steps_all_to_T": G * prob.nsteps,
             "evals_per_step_both_branches": evals,
-            "precision": "fp64",
+            "precision": ("fp64" if precision == F.FGA_FP64 else
+                          "mixed: FP64 FBI and rays; reconstruction on tensor cores "
+                          "(TF32 head/tail factors, 3 products, FP32 accumulate, FP64 phase "
+                          "anchors and segment sums)"),
+            "fp64_path_value": fp64_value,
             "stage_ms_mean": {"fbi": statistics.mean(fbi_ms), "rays": statistics.mean(ray_ms),
                               "binning+reconstruct": statistics.mean(recon_ms)},
             "l2": "256 MiB buffer written between timed steps",
@@ -381,6 +412,9 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=512)
+    ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed",
+                    help="mixed: tensor-core reconstruction (its rel-L2 against the FP64 "
+                         "path is measured in the same run); fp64: every step in FP64")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")

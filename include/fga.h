@@ -57,8 +57,11 @@ typedef enum {
 
 typedef enum {
   FGA_FP64 = 0,         /* every step in FP64 */
-  FGA_MIXED_TF32X2 = 1, /* reserved: split-TF32 contractions, FP32 accumulate */
-  FGA_MIXED_BF16X3 = 2  /* reserved: split-BF16 contractions, FP32 accumulate */
+  FGA_MIXED_TF32X3 = 1, /* reconstruction on the tensor cores: factors split into a TF32
+                           head and tail, hi*hi + hi*lo + lo*hi accumulated in FP32, phase
+                           anchored in FP64; FBI, rays and the final sum stay FP64.
+                           2D grids with open axes only. */
+  FGA_MIXED_BF16X3 = 2  /* reserved (rejected by fga_plan) */
 } fga_precision;
 
 typedef struct {

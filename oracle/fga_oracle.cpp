@@ -447,6 +447,44 @@ int orc_propagate(int dim, const int64_t* n, const double* h, const double* o, c
   return 0;
 }
 
+// One term of Eq. recons at the point xp (without the factor W a psi (2 pi eps)^{-3d/2}
+// e^{iS/eps}): the sum over the images inside the square window |x_k - Q_k| <= cut of
+// exp(i P.(x - Q)/eps - |x - Q|^2/(2 eps)); periodic axes have L[k] > 0.
+static cplx window_term(int d, const double* L, double eps, double cut, const double* Qg,
+                        const double* Pg, const double* xp) {
+  const cplx I(0.0, 1.0);
+  double img[3][5];
+  int nimg[3];
+  for (int k = 0; k < d; ++k) {
+    nimg[k] = 0;
+    double d0 = xp[k] - Qg[k];
+    if (L[k] > 0.0) {
+      for (int l = -2; l <= 2; ++l) {
+        double dk = d0 + l * L[k];
+        if (std::fabs(dk) <= cut) img[k][nimg[k]++] = dk;
+      }
+    } else if (std::fabs(d0) <= cut) {
+      img[k][nimg[k]++] = d0;
+    }
+    if (nimg[k] == 0) return 0.0;
+  }
+  cplx sum = 0.0;
+  int combos = 1;
+  for (int k = 0; k < d; ++k) combos *= nimg[k];
+  for (int cidx = 0; cidx < combos; ++cidx) {
+    int rem = cidx;
+    double phase = 0.0, r2 = 0.0;
+    for (int k = 0; k < d; ++k) {
+      double dk = img[k][rem % nimg[k]];
+      rem /= nimg[k];
+      phase += Pg[k] * dk;
+      r2 += dk * dk;
+    }
+    sum += std::exp(I * phase / eps - r2 / (2.0 * eps));
+  }
+  return sum;
+}
+
 // Reconstruction sum (Eq. recons) at npts points x[npts][dim]:
 //   u(x) = sum_g W a_g psi_g (2 pi eps)^{-3d/2} e^{i S_g/eps}
 //            e^{ i P_g.(x-Q_g)/eps - |x-Q_g|^2/(2 eps) }
@@ -562,6 +600,72 @@ int orc_fbi_direct(int dim, const int64_t* n, const double* h, const int* period
     for (int k = 0; k < d; ++k) hv *= h[k];
     out[2 * ip] = (hv * acc).real();
     out[2 * ip + 1] = (hv * acc).imag();
+  }
+  return 0;
+}
+
+// Traces: the field of Eq. recons at nrx receiver points x[nrx][dim] at the record
+// times t_m = m * record_every * dt, m = 0 .. nsteps/record_every, with every Gaussian
+// propagated by RK4 as in orc_propagate. out: [nrec][nrx][2] (re, im). The sum over
+// Gaussians is split over nthreads fixed blocks and added up in block order.
+int orc_traces(int dim, const int64_t* n, const double* h, const double* o, const int* periodic,
+               const double* C, int64_t nsteps, double dt, int64_t record_every, int64_t nG,
+               const int* sigma, const double* q, const double* p, const double* psi,
+               double eps, double kappa, double W, int64_t nrx, const double* xr, double* out,
+               int nthreads) {
+  if (dim < 1 || dim > 3 || record_every < 1 || nsteps % record_every != 0) return 1;
+  Grid g = make_grid(dim, n, h, o, periodic);
+  int d = dim;
+  double L[3] = {0, 0, 0};
+  for (int k = 0; k < d; ++k) L[k] = g.periodic[k] ? g.n[k] * g.h[k] : 0.0;
+  const int64_t nrec = nsteps / record_every + 1;
+  const double cut = kappa * std::sqrt(eps);
+  const double norm = std::pow(2.0 * kPi * eps, -1.5 * d);
+  const cplx I(0.0, 1.0);
+  int nt = nthreads > 0 ? nthreads : 1;
+  std::vector<cplx> part((size_t)nt * nrec * nrx, cplx(0.0, 0.0));
+  for (int64_t i = 0; i < nG; ++i) {
+    double pn = 0.0;
+    for (int k = 0; k < d; ++k) pn += p[i * d + k] * p[i * d + k];
+    if (!(pn > 0.0)) return 2;
+  }
+  set_threads(nt);
+#pragma omp parallel num_threads(nt)
+  {
+    int tid = 0;
+#ifdef _OPENMP
+    tid = omp_get_thread_num();
+#endif
+    int64_t lo = nG * tid / nt, hi = nG * (tid + 1) / nt;
+    cplx* acc = part.data() + (size_t)tid * nrec * nrx;
+    for (int64_t i = lo; i < hi; ++i) {
+      State y;
+      state_zero(y);
+      for (int k = 0; k < d; ++k) {
+        y.Q[k] = q[i * d + k];
+        y.P[k] = p[i * d + k];
+        y.A[k][k] = cplx(1.0, 0.0);
+        y.B[k][k] = cplx(0.0, -1.0);
+      }
+      y.a = cplx(std::pow(2.0, 0.5 * d), 0.0);
+      y.S = 0.0;
+      cplx ps(psi[2 * i], psi[2 * i + 1]);
+      for (int64_t s = 0; s <= nsteps; ++s) {
+        if (s % record_every == 0) {
+          cplx pref = W * y.a * ps * norm * std::exp(I * y.S / eps);
+          int64_t m = s / record_every;
+          for (int64_t r = 0; r < nrx; ++r)
+            acc[m * nrx + r] += pref * window_term(d, L, eps, cut, y.Q, y.P, xr + r * d);
+        }
+        if (s < nsteps) rk4_step(g, C, sigma[i], y, dt);
+      }
+    }
+  }
+  for (int64_t e = 0; e < nrec * nrx; ++e) {
+    cplx v = 0.0;
+    for (int t = 0; t < nt; ++t) v += part[(size_t)t * nrec * nrx + e];
+    out[2 * e] = v.real();
+    out[2 * e + 1] = v.imag();
   }
   return 0;
 }

@@ -76,6 +76,8 @@ def _load():
                                       ci]
         lib.orc_reconstruct.argtypes = [ci, P, d, d, d, i64, P, P, P, P, P, i64, P, P, P, ci]
         lib.orc_fbi_direct.argtypes = [ci, P, P, P, P, d, P, i64, P, P, P]
+        lib.orc_traces.argtypes = [ci, P, P, P, P, P, i64, d, i64, i64, P, P, P, P, d, d, d, i64,
+                                   P, P, ci]
         lib.orc_num_threads_available.restype = ci
         _lib = lib
     return _lib
@@ -396,6 +398,45 @@ def reconstruct(grid: Grid, eps: float, kappa: float, W: float, Q, P, a, psi, S,
                              _ptr(uim), int(nthreads or default_threads()))
     assert rc == 0
     return ure + 1j * uim
+
+
+def traces(grid: Grid, coef, nsteps: int, dt: float, record_every: int, sigma, q, p, psi,
+           eps: float, kappa: float, W: float, xr, nthreads: Optional[int] = None):
+    """Complex field at receivers xr[nrx][dim] at t_m = m*record_every*dt (m = 0..nsteps/
+    record_every), every Gaussian propagated by RK4. Returns [nrec][nrx] complex."""
+    lib = _load()
+    d = grid.dim
+    sigma = np.ascontiguousarray(sigma, dtype=np.int32)
+    q = _f64(q).reshape(-1, d)
+    p = _f64(p).reshape(-1, d)
+    nG = q.shape[0]
+    ps = _f64(np.stack([np.real(psi), np.imag(psi)], axis=1)) if nG else np.empty((0, 2))
+    xr = _f64(xr).reshape(-1, d)
+    nrec = nsteps // record_every + 1
+    out = np.empty((nrec, xr.shape[0], 2))
+    rc = lib.orc_traces(*grid.args(), _ptr(_f64(coef)), int(nsteps), float(dt), int(record_every),
+                        nG, _ptr(sigma), _ptr(q), _ptr(p), _ptr(ps), float(eps), float(kappa),
+                        float(W), xr.shape[0], _ptr(xr), _ptr(out), int(nthreads or default_threads()))
+    assert rc == 0, "orc_traces failed (%d)" % rc
+    return out[..., 0] + 1j * out[..., 1]
+
+
+def frozen_set_traces(grid: Grid, coef, f0, f1, eps, stride, box, keys, nsteps, dt, record_every,
+                      kappa, xr, nthreads=None):
+    """Traces for a fixed set of Gaussians keys = (sigma, q index, p index) arrays, with the
+    weights psi+- recomputed for the velocity coef (the FBI of the data does not depend on
+    c; the branch split does, through c(q)). Used for derivatives with the set frozen."""
+    sigma, qidx, pidx = keys
+    rows, inv = np.unique(qidx, return_inverse=True)
+    psi0 = fbi(grid, f0, eps, stride, box, q_subset=rows)
+    psi1 = fbi(grid, f1, eps, stride, box, q_subset=rows)
+    plus, minus, _ = branch_split(grid, coef, eps, stride, box, psi0, psi1, q_subset=rows)
+    psi = np.where(np.asarray(sigma) > 0, plus[inv, pidx], minus[inv, pidx])
+    qpts = q_points(grid, stride)[qidx]
+    ppts = p_points(grid, eps, box)[pidx]
+    W = quadrature_weight(grid, eps, stride, box)
+    return traces(grid, coef, nsteps, dt, record_every, sigma, qpts, ppts, psi, eps, kappa, W, xr,
+                  nthreads)
 
 
 # ---------------------------------------------------------------------------

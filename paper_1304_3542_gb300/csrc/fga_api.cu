@@ -109,6 +109,8 @@ fga_status read_status(fga_plan_s* p) {
   if (st & fga::kStatusNumeric)
     return fail(p, FGA_ERR_NUMERIC, "a ray met |P| = 0, det Z = 0 or a non-finite value", true);
   if (st & fga::kStatusCapacity) return fail(p, FGA_ERR_CAPACITY, "a plan capacity was exceeded", true);
+  if (st & fga::kStatusTimeout)
+    return fail(p, FGA_ERR_TIMEOUT, "a bounded tensor-core completion wait gave up", true);
   return FGA_OK;
 }
 
@@ -165,8 +167,13 @@ fga_status fga_plan(const fga_config* cfg, const double* velocity, void* stream,
   if (cfg->nshots < 1 || cfg->nshots > fga::kMaxShots)
     return fail(nullptr, FGA_ERR_INVALID, "nshots out of range");
   if (!cfg->eps) return fail(nullptr, FGA_ERR_INVALID, "eps is NULL");
-  if (cfg->precision != FGA_FP64)
-    return fail(nullptr, FGA_ERR_INVALID, "only FGA_FP64 is available in this build");
+  if (cfg->precision != FGA_FP64 && cfg->precision != FGA_MIXED_TF32X3)
+    return fail(nullptr, FGA_ERR_INVALID, "precision must be FGA_FP64 or FGA_MIXED_TF32X3");
+  if (cfg->precision == FGA_MIXED_TF32X3) {
+    if (d != 2) return fail(nullptr, FGA_ERR_INVALID, "FGA_MIXED_TF32X3 needs a 2D grid");
+    if (cfg->periodic[0] || cfg->periodic[1])
+      return fail(nullptr, FGA_ERR_INVALID, "FGA_MIXED_TF32X3 needs open (non-periodic) axes");
+  }
   if (!(cfg->dt > 0.0) || !(cfg->T >= 0.0) || !std::isfinite(cfg->T))
     return fail(nullptr, FGA_ERR_INVALID, "need T >= 0 and dt > 0");
   double steps = cfg->T / cfg->dt;
@@ -209,7 +216,8 @@ fga_status fga_plan(const fga_config* cfg, const double* velocity, void* stream,
   p->integrate_exited = cfg->integrate_exited ? 1 : 0;
   p->stream = (cudaStream_t)stream;
   p->nfields = fga::state_fields(d);
-  const int TS = fga::tile_edge(d);
+  const int TS = cfg->precision == FGA_MIXED_TF32X3 ? fga::tile_edge_tc() : fga::tile_edge(d);
+  for (int k = 0; k < fga::kMaxDim; ++k) p->grid.tile[k] = TS;
   int64_t tile_off = 0;
   p->shots.resize(cfg->nshots);
   for (int s = 0; s < cfg->nshots; ++s) {
@@ -257,7 +265,7 @@ fga_status fga_plan(const fga_config* cfg, const double* velocity, void* stream,
       sh.pscale[k] = 2.0 * kPi * eps / ((double)nbk * gd.h[k]);
       sh.W *= (double)sk * gd.h[k] * sh.pscale[k];
       sh.np *= nbk;
-      sh.ntile[k] = (int)((gd.n[k] + TS - 1) / TS);
+      sh.ntile[k] = (int)((gd.n[k] + p->grid.tile[k] - 1) / p->grid.tile[k]);
     }
     sh.tile_off = tile_off;
     int64_t nt = 1;
@@ -447,7 +455,6 @@ fga_status fga_reconstruct(fga_plan_t p, double* u_out) {
   if (!u_out) return fail(p, FGA_ERR_INVALID, "u_out must not be NULL");
   const GridDev& gd = p->grid;
   const int d = gd.dim;
-  const int TS = fga::tile_edge(d);
   // capacity of the tile lists: every Gaussian meets at most prod_k m_k tiles,
   // m_k = (floor(window points / tile) + 2) per image, times 5 images on periodic axes
   size_t pairs = 0;
@@ -455,7 +462,7 @@ fga_status fga_reconstruct(fga_plan_t p, double* u_out) {
     size_t per = 1;
     for (int k = 0; k < d; ++k) {
       double wpts = 2.0 * p->kappa * sh.sqrt_eps * gd.inv_h[k] + 6.0;
-      size_t mk = (size_t)(wpts / TS) + 2;
+      size_t mk = (size_t)(wpts / gd.tile[k]) + 2;
       if (gd.periodic[k]) mk *= 5;
       mk = std::min<size_t>(mk, (size_t)sh.ntile[k]);
       per *= mk;
@@ -463,8 +470,10 @@ fga_status fga_reconstruct(fga_plan_t p, double* u_out) {
     pairs += per * (size_t)sh.g_cnt;
   }
   CUDA_OR_FAIL(p, grow(&p->d_tile_list, &p->list_cap, pairs));
+  const bool tc = p->precision == FGA_MIXED_TF32X3;
   CUDA_OR_FAIL(p, grow(&p->d_partial, &p->partial_cap,
-                       fga::partial_items(p) * fga::tile_points(d)));
+                       tc ? (fga::partial_bytes_tc(p) + 7) / 8
+                          : fga::partial_items(p) * fga::tile_points(d)));
   CUDA_OR_FAIL(p, cudaEventRecord(p->ev[5], p->stream));
   CUDA_OR_FAIL(p, fga::launch_binning(p, nullptr));
   CUDA_OR_FAIL(p, fga::launch_binning_fill(p));
@@ -476,7 +485,7 @@ fga_status fga_reconstruct(fga_plan_t p, double* u_out) {
     CUDA_OR_FAIL(p, grow(&p->d_out, &p->out_cap, n_all));
     dst = p->d_out;
   }
-  CUDA_OR_FAIL(p, fga::launch_reconstruct(p, dst));
+  CUDA_OR_FAIL(p, tc ? fga::launch_reconstruct_tc(p, dst) : fga::launch_reconstruct(p, dst));
   CUDA_OR_FAIL(p, cudaEventRecord(p->ev[7], p->stream));
   if (host_out) {
     CUDA_OR_FAIL(p, cudaMemcpyAsync(u_out, dst, sizeof(double) * n_all, cudaMemcpyDeviceToHost,

@@ -17,6 +17,7 @@
 #include <string>
 
 #include "fga_internal.cuh"
+#include "fga_tiles.cuh"
 
 namespace fga {
 
@@ -29,59 +30,6 @@ constexpr int CH = 16;   // Gaussians per chunk (2D)
 constexpr int CH1 = 32;  // Gaussians per chunk (1D)
 constexpr int64_t SEG2 = 1024;  // Gaussians per work item (2D)
 constexpr int64_t SEG1 = 512;   // Gaussians per work item (1D)
-
-__device__ __forceinline__ int shot_of_tile(const ShotDev* shots, int nshots, int64_t t) {
-  int lo = 0, hi = nshots - 1;
-  while (lo < hi) {
-    int mid = (lo + hi + 1) >> 1;
-    if (shots[mid].tile_off <= t) lo = mid; else hi = mid - 1;
-  }
-  return lo;
-}
-
-// Window of Gaussian (Q, cut) along one axis as a conservative grid-index range,
-// for the image shifted by l periods.
-__device__ __forceinline__ void window_range(const GridDev& gd, int k, double Q, double cut,
-                                             int64_t& lo, int64_t& hi) {
-  lo = (int64_t)floor((Q - cut - gd.o[k]) * gd.inv_h[k]) - 1;
-  hi = (int64_t)ceil((Q + cut - gd.o[k]) * gd.inv_h[k]) + 1;
-}
-
-// Does the window of the Gaussian with centre Q meet the index box [a, b] on all axes?
-template <int D>
-__device__ __forceinline__ bool overlaps(const GridDev& gd, const double* Q, double cut,
-                                         const int64_t* a, const int64_t* b) {
-#pragma unroll
-  for (int k = 0; k < D; ++k) {
-    bool any = false;
-    int lmax = gd.periodic[k] ? 2 : 0;
-    for (int l = -lmax; l <= lmax; ++l) {
-      int64_t lo, hi;
-      window_range(gd, k, Q[k] + l * gd.L[k], cut, lo, hi);
-      any = any || (lo <= b[k] && hi >= a[k]);
-    }
-    if (!any) return false;
-  }
-  return true;
-}
-
-template <int D>
-__device__ __forceinline__ void tile_box(const GridDev& gd, const ShotDev& sh, int64_t tloc,
-                                         int64_t* a, int64_t* b) {
-  const int TS = (D == 1) ? T1 : T2;
-  int64_t t[D];
-  if constexpr (D == 1) {
-    t[0] = tloc;
-  } else {
-    t[0] = tloc / sh.ntile[1];
-    t[1] = tloc - t[0] * sh.ntile[1];
-  }
-#pragma unroll
-  for (int k = 0; k < D; ++k) {
-    a[k] = t[k] * TS;
-    b[k] = min(a[k] + TS - 1, gd.n[k] - 1);
-  }
-}
 
 // Pass 1 (FILL = false): number of Gaussians per tile. Pass 2 (FILL = true): the
 // ordered list, written at the tile's offset. One CTA per tile scans the shot's
@@ -184,16 +132,6 @@ __device__ __forceinline__ void axis_factors8(double xi0, double h, double Q, do
     ei = tr * rs + ti * rc;
     R *= rho;
   }
-}
-
-// The (tile, segment) work item w: tile t is the largest with seg_off[t] <= w.
-__device__ __forceinline__ int64_t tile_of_item(const int64_t* seg_off, int64_t ntiles, int64_t w) {
-  int64_t lo = 0, hi = ntiles - 1;
-  while (lo < hi) {
-    int64_t mid = (lo + hi + 1) >> 1;
-    if (seg_off[mid] <= w) lo = mid; else hi = mid - 1;
-  }
-  return lo;
 }
 
 // Number of list segments per tile (then scanned into seg_off).
@@ -660,6 +598,7 @@ extern "C" fga_status fga_reconstruct_static(int dim, const int64_t* n, const do
   const int TS = tile_edge(dim);
   int64_t ntiles = 1;
   size_t per = 1;  // tiles one Gaussian can meet at most
+  for (int k = 0; k < kMaxDim; ++k) gd.tile[k] = TS;
   for (int k = 0; k < dim; ++k) {
     if (n[k] < 4 || n[k] > ((int64_t)1 << 30) || !(h[k] > 0.0) || !std::isfinite(h[k]) ||
         !std::isfinite(origin[k]))

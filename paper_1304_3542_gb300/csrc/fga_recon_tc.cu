@@ -1,0 +1,259 @@
+// Mixed-precision reconstruction on the tensor cores (2D, open axes).
+//
+// For one output tile of 128 x 128 points and one segment of its Gaussian list, the
+// real part of the Gaussian sum (Eq. recons) is a real GEMM over the Gaussian index:
+//   u[x][z] = sum_g Re(X_g(x) Z_g(z)) = sum_k A[x][k] B[z][k],
+//   A[x][2g] = Re X_g(x), A[x][2g+1] = -Im X_g(x), B[z][2g] = Re Z_g(z), B[z][2g+1] = Im Z_g(z),
+// where X_g carries the Gaussian's coefficient. Each factor is split into a TF32 head
+// and an FP32 tail (v = hi + lo), and the three products hi*hi + hi*lo + lo*hi are
+// accumulated in FP32 in tensor memory by tcgen05.mma (kind::tf32, M = N = 128,
+// K = 8 per instruction), so each product carries about 21 significant bits.
+//
+// Precision policy: the phase P (x - Q)/eps is anchored in FP64 at the first point of
+// each 16-point run and carried as a 32-bit fixed-point fraction of a turn (exact
+// increments modulo 2 pi), so the FP32 sine/cosine see an argument in [-pi, pi) that is
+// accurate to about 1e-7 rad; the Gaussian envelope exp(-d^2/(2 eps)) is FP32. The
+// partial tile of each (tile, segment) work item is FP32 and the segments are summed in
+// FP64 in a fixed order.
+#include <algorithm>
+
+#include "fga_internal.cuh"
+#include "fga_tc.cuh"
+#include "fga_tiles.cuh"
+
+namespace fga {
+
+namespace {
+
+constexpr int TM = 128;       // tile edge (x = GEMM M, z = GEMM N)
+constexpr int CHG = 16;       // Gaussians per chunk -> K = 32
+constexpr int KC = 2 * CHG;   // GEMM K per chunk
+constexpr int KB = KC / 4;    // 16-byte core matrices along K (tf32: 4 per core row)
+constexpr int64_t SEGM = 2048;
+constexpr int NTC = 128;      // threads per CTA
+constexpr uint32_t kMaxTries = 1u << 22;
+// core-matrix (8 rows x 16 bytes) strides of the K-major operand tiles
+constexpr uint32_t kLBO = 128;       // next core matrix along K
+constexpr uint32_t kSBO = KB * 128;  // next 8-row group along M / N
+constexpr size_t kOperandBytes = (size_t)TM * KC * sizeof(float);  // 16 KiB
+constexpr size_t kSmemBytes = 4 * kOperandBytes + 64;
+
+__device__ __forceinline__ int core_offset(int row, int k) {
+  return (((row >> 3) * KB + (k >> 2)) * 8 + (row & 7)) * 4 + (k & 3);
+}
+
+__device__ __forceinline__ float tf32_head(float v) {
+  return __uint_as_float(__float_as_uint(v) & 0xFFFFE000u);
+}
+
+// Factors of one Gaussian at 16 consecutive points of one axis, written to the operand
+// tiles as (re, im) or (re, -im) at column pair k = 2 gi.
+__device__ __forceinline__ void factors16(double x0, double h, double Q, double P, double cut,
+                                          double inv_eps, float2 cf, bool conj_im, int row0, int k,
+                                          float* hi, float* lo) {
+  const double two_pi = 6.283185307179586;
+  double d0 = x0 - Q;
+  // phase at the run's first point and per step, as fractions of a turn (FP64)
+  double t0 = P * d0 * inv_eps / two_pi, td = P * h * inv_eps / two_pi;
+  t0 -= floor(t0);
+  td -= floor(td);
+  uint32_t u0 = (uint32_t)(long long)(t0 * 4294967296.0);
+  uint32_t ud = (uint32_t)(long long)(td * 4294967296.0);
+  const float fd0 = (float)d0, fh = (float)h, fcut = (float)cut, fie = (float)inv_eps;
+  const float ang_scale = 1.4629180792671596e-09f;  // 2 pi / 2^32
+#pragma unroll 4
+  for (int r = 0; r < 16; ++r) {
+    float d = fmaf((float)r, fh, fd0);
+    float re = 0.f, im = 0.f;
+    if (fabsf(d) <= fcut) {
+      float gs = __expf(-0.5f * d * d * fie);
+      float sn, cs;
+      __sincosf((float)(int32_t)(u0 + (uint32_t)r * ud) * ang_scale, &sn, &cs);
+      float fr = gs * cs, fi = gs * sn;
+      re = cf.x * fr - cf.y * fi;
+      im = cf.x * fi + cf.y * fr;
+    }
+    if (conj_im) im = -im;
+    float rh = tf32_head(re), ih = tf32_head(im);
+    int o = core_offset(row0 + r, k);
+    hi[o] = rh;
+    lo[o] = re - rh;
+    hi[o + 1] = ih;  // k + 1 stays in the same core row (k even)
+    lo[o + 1] = im - ih;
+  }
+}
+
+__global__ void __launch_bounds__(NTC) k_gather_tc(GridDev gd, const ShotDev* __restrict__ shots,
+                                                   int nshots, double kappa,
+                                                   const double* __restrict__ state, int64_t ld,
+                                                   const double2* __restrict__ coef,
+                                                   const int64_t* __restrict__ off,
+                                                   const int32_t* __restrict__ list, int64_t list_cap,
+                                                   const int64_t* __restrict__ seg_off, int64_t ntiles,
+                                                   float* __restrict__ partial, int* status) {
+  const int64_t w = blockIdx.x;
+  if (w >= seg_off[ntiles]) return;  // uniform over the CTA
+  extern __shared__ __align__(1024) unsigned char smem[];
+  float* Ahi = reinterpret_cast<float*>(smem);
+  float* Alo = Ahi + TM * KC;
+  float* Bhi = Alo + TM * KC;
+  float* Blo = Bhi + TM * KC;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + 4 * kOperandBytes);
+  uint32_t* tbase = reinterpret_cast<uint32_t*>(smem + 4 * kOperandBytes + 16);
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int64_t t = tile_of_item(seg_off, ntiles, w);
+  const int s = shot_of_tile(shots, nshots, t);
+  const ShotDev& sh = shots[s];
+  const double cut = kappa * sh.sqrt_eps, inv_eps = sh.inv_eps;
+  int64_t a[2], b[2];
+  tile_box<2>(gd, sh, t - sh.tile_off, a, b);
+  if (tid == 0) {
+    tc::mbar_init(bar, 1);
+    tc::fence_mbar_init();
+  }
+  if (warp == 0) {
+    tc::tmem_alloc(tbase, TM);
+    tc::tmem_relinquish();
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = *tbase;
+  const uint32_t idesc = tc::idesc_f32acc(tc::kFmtTF32, TM, TM);
+  const int64_t l0 = min(off[t], list_cap) + (w - seg_off[t]) * SEGM;
+  const int64_t l1 = min(min(off[t + 1], list_cap), l0 + SEGM);
+  const int gi = tid >> 3, part = tid & 7;
+  uint32_t chunks = 0;
+  bool ok = true;
+  for (int64_t c0 = l0; c0 < l1; c0 += CHG) {
+    if (chunks > 0) ok &= tc::mbar_wait_bounded(bar, (chunks - 1) & 1u, kMaxTries);
+    const int nc = (int)((l1 - c0) < CHG ? (l1 - c0) : CHG);
+    if (gi < nc) {
+      int32_t g = list[c0 + gi];
+      double Qx = state[0 * ld + g], Qz = state[1 * ld + g];
+      double Px = state[2 * ld + g], Pz = state[3 * ld + g];
+      double2 c = coef[g];
+      float2 cf = make_float2((float)c.x, (float)c.y);
+      factors16(gd.o[0] + (double)(a[0] + 16 * part) * gd.h[0], gd.h[0], Qx, Px, cut, inv_eps, cf,
+                true, 16 * part, 2 * gi, Ahi, Alo);
+      factors16(gd.o[1] + (double)(a[1] + 16 * part) * gd.h[1], gd.h[1], Qz, Pz, cut, inv_eps,
+                make_float2(1.f, 0.f), false, 16 * part, 2 * gi, Bhi, Blo);
+    } else {
+      for (int r = 0; r < 16; ++r) {
+        int o = core_offset(16 * part + r, 2 * gi);
+        Ahi[o] = Alo[o] = Ahi[o + 1] = Alo[o + 1] = 0.f;
+        Bhi[o] = Blo[o] = Bhi[o + 1] = Blo[o + 1] = 0.f;
+      }
+    }
+    tc::fence_proxy_async_smem();
+    __syncthreads();
+    if (tid == 0) {
+      tc::fence_after_sync();
+      const uint32_t ah = tc::smem_u32(Ahi), al = tc::smem_u32(Alo);
+      const uint32_t bh = tc::smem_u32(Bhi), bl = tc::smem_u32(Blo);
+#pragma unroll
+      for (int ks = 0; ks < KC / 8; ++ks) {
+        const uint32_t step = ks * 256;  // 8 tf32 of K = two core matrices
+        tc::mma_tf32(tmem, tc::smem_desc(ah + step, kLBO, kSBO), tc::smem_desc(bh + step, kLBO, kSBO),
+                     idesc, (chunks > 0 || ks > 0) ? 1u : 0u);
+        tc::mma_tf32(tmem, tc::smem_desc(ah + step, kLBO, kSBO), tc::smem_desc(bl + step, kLBO, kSBO),
+                     idesc, 1u);
+        tc::mma_tf32(tmem, tc::smem_desc(al + step, kLBO, kSBO), tc::smem_desc(bh + step, kLBO, kSBO),
+                     idesc, 1u);
+      }
+      tc::mma_commit(bar);
+    }
+    ++chunks;
+  }
+  if (chunks > 0) ok &= tc::mbar_wait_bounded(bar, (chunks - 1) & 1u, kMaxTries);
+  if (!ok) {
+    atomicOr(status, kStatusTimeout);
+    if (chunks > 0) tc::mbar_wait_bounded(bar, (chunks - 1) & 1u, kMaxTries);
+  }
+  tc::fence_after_sync();
+  // epilogue: warp w holds rows (x) 32w .. 32w+31, one row per thread, 128 columns (z)
+  float* dst = partial + (size_t)w * TM * TM + (size_t)(32 * warp + (tid & 31)) * TM;
+  float v[32];
+#pragma unroll 1
+  for (int col = 0; col < TM; col += 32) {
+    if (chunks > 0 && ok) {
+      tc::tmem_ld_32x32b_x32(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)col, v);
+    } else {
+#pragma unroll
+      for (int i = 0; i < 32; ++i) v[i] = 0.f;
+    }
+#pragma unroll
+    for (int i = 0; i < 32; i += 4)
+      *reinterpret_cast<float4*>(dst + col + i) = make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) tc::tmem_dealloc(tmem, TM);
+}
+
+// Ordered FP64 sum of the FP32 partial tiles of every tile into the output grid.
+__global__ void __launch_bounds__(256) k_reduce_tc(GridDev gd, const ShotDev* __restrict__ shots,
+                                                   int nshots, const int64_t* __restrict__ seg_off,
+                                                   const float* __restrict__ partial,
+                                                   double* __restrict__ out) {
+  const int64_t t = blockIdx.x;
+  const int s = shot_of_tile(shots, nshots, t);
+  const ShotDev& sh = shots[s];
+  int64_t a[2], b[2];
+  tile_box<2>(gd, sh, t - sh.tile_off, a, b);
+  const int64_t w0 = seg_off[t], w1 = seg_off[t + 1];
+  for (int idx = threadIdx.x; idx < TM * TM; idx += 256) {
+    double v = 0.0;
+    for (int64_t w = w0; w < w1; ++w) v += (double)partial[w * TM * TM + idx];
+    int64_t ix = a[0] + idx / TM, iz = a[1] + idx % TM;
+    if (ix <= b[0] && iz <= b[1]) out[(int64_t)s * gd.npts + ix * gd.n[1] + iz] = v;
+  }
+}
+
+__global__ void k_segments_tc(const int64_t* __restrict__ off, int64_t ntiles, int64_t list_cap,
+                              int64_t seg, int64_t* __restrict__ seg_cnt) {
+  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= ntiles) return;
+  int64_t a = min(off[t], list_cap), b = min(off[t + 1], list_cap);
+  seg_cnt[t] = (b - a + seg - 1) / seg;
+}
+
+}  // namespace
+
+int tile_edge_tc() { return TM; }
+
+size_t partial_items_tc(fga_plan_s* p) {
+  return (size_t)p->ntiles + (p->list_cap + SEGM - 1) / SEGM;
+}
+
+size_t partial_bytes_tc(fga_plan_s* p) { return partial_items_tc(p) * TM * TM * sizeof(float); }
+
+cudaError_t launch_reconstruct_tc(fga_plan_s* p, double* u_dev) {
+  if (p->ntiles == 0) return cudaSuccess;
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(k_gather_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)kSmemBytes);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  k_segments_tc<<<(unsigned)((p->ntiles + 255) / 256), 256, 0, p->stream>>>(
+      p->d_tile_off, p->ntiles, (int64_t)p->list_cap, SEGM, p->d_seg_off);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  e = launch_scan(p, p->d_seg_off, p->ntiles);
+  if (e != cudaSuccess) return e;
+  const unsigned items = (unsigned)partial_items_tc(p);
+  k_gather_tc<<<items, NTC, kSmemBytes, p->stream>>>(
+      p->grid, p->d_shots, p->nshots, p->kappa, p->d_state, (int64_t)p->g_cap, p->d_gcoef,
+      p->d_tile_off, p->d_tile_list, (int64_t)p->list_cap, p->d_seg_off, p->ntiles,
+      reinterpret_cast<float*>(p->d_partial), p->d_status);
+  k_reduce_tc<<<(unsigned)p->ntiles, 256, 0, p->stream>>>(p->grid, p->d_shots, p->nshots,
+                                                          p->d_seg_off,
+                                                          reinterpret_cast<float*>(p->d_partial),
+                                                          u_dev);
+  p->launches += 3;
+  return cudaGetLastError();
+}
+
+}  // namespace fga

@@ -21,7 +21,7 @@ from . import build as _build
 
 FGA_OK = 0
 FGA_FP64 = 0
-FGA_MIXED_TF32X2 = 1
+FGA_MIXED_TF32X3 = 1
 FGA_MIXED_BF16X3 = 2
 
 STATUS = {0: "FGA_OK", 1: "FGA_ERR_INVALID", 2: "FGA_ERR_OOM", 3: "FGA_ERR_CUDA",

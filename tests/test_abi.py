@@ -60,7 +60,11 @@ def _plan(**kw):
     (dict(n=(2, 16), velocity=np.ones(32)), "grid size"),
     (dict(box=[[7, 8]]), "box"),
     (dict(periodic=(True, False), box=[[8, 32]], q_stride=[[2, 2]]), "periodic"),
-    (dict(precision=F.FGA_MIXED_BF16X3), "FGA_FP64"),
+    (dict(precision=F.FGA_MIXED_BF16X3), "precision"),
+    (dict(precision=F.FGA_MIXED_TF32X3, periodic=(True, False), box=[[16, 32]], q_stride=[[2, 2]]),
+     "open"),
+    (dict(precision=F.FGA_MIXED_TF32X3, dim=1, n=(16,), h=(0.1,), origin=(0.0,), periodic=(False,),
+          velocity=np.ones(16)), "2D"),
 ])
 def test_invalid_configurations_are_rejected_on_the_host(kw, msg):
     with pytest.raises(F.FGAError) as ei:
