@@ -129,6 +129,45 @@ fga_status fga_propagate(fga_plan_t plan);
  * FGA_ERR_INVALID, FGA_ERR_OOM, FGA_ERR_CUDA, FGA_ERR_NUMERIC. */
 fga_status fga_reconstruct(fga_plan_t plan, double* u_out);
 
+/* Receivers for traces: the field of Eq. recons (Re u, as fga_reconstruct writes it)
+ * at the points xr (host or device, [nrx][dim] FP64, inside the grid, open axes only)
+ * at the record times t_m = m * record_every * dt, m = 0 .. T/(record_every dt)
+ * (record_every must divide T/dt). fga_propagate then accumulates the traces while it
+ * integrates the rays. nrx = 0 removes the receivers. Errors: FGA_ERR_INVALID,
+ * FGA_ERR_OOM, FGA_ERR_CUDA. */
+fga_status fga_set_receivers(fga_plan_t plan, int64_t nrx, const double* xr,
+                             int64_t record_every);
+
+/* Traces of the last fga_propagate: host or device [nshots][nrec][nrx] FP64,
+ * nrec = T/(record_every dt) + 1. Synchronises the plan's stream. The sum over
+ * Gaussians is accumulated with atomic additions, so the last bits may differ between
+ * runs. Errors: FGA_ERR_STATE (no receivers or no propagation since they were set). */
+fga_status fga_traces(fga_plan_t plan, double* traces);
+
+/* Adjoint (gradient with respect to the velocity samples). With the set of Gaussians
+ * of the last fga_decompose held fixed, computes
+ *   grad[i] = sum_{s,m,r} residual[s][m][r] * d traces[s][m][r] / d c_i
+ * for the traces of fga_traces (so for J = 1/2 sum (traces - data)^2 the residual is
+ * traces - data and grad = dJ/dc). c_i are the velocity samples, which are the spline
+ * coefficients of the medium; c enters through the rays (c, grad c, Hessian of c in
+ * Eqs. characline, dzQ, dzP, a_formu) and through c(q) in the branch split (Eq. psi).
+ * The derivative is that of the computed traces (discrete adjoint of the RK4 scheme,
+ * checkpoints every ceil(sqrt(T/dt)) steps, segments recomputed in the reverse sweep).
+ * residual: host or device [nshots][nrec][nrx]; grad: host or device [n...], overwritten.
+ * Rays that left the grid for good contribute nothing after they stop (as in the
+ * forward). Needs fga_set_receivers and fga_propagate. Synchronises the stream.
+ * Errors: FGA_ERR_STATE, FGA_ERR_INVALID, FGA_ERR_OOM, FGA_ERR_CUDA. */
+fga_status fga_grad(fga_plan_t plan, const double* residual, double* grad);
+
+/* fga_propagate followed by fga_reconstruct into device memory, replayed as one CUDA
+ * graph: the ray, binning and reconstruction launches are captured on the plan's stream
+ * (which must not be the legacy default stream) and replayed on later calls; the graph
+ * is captured again when the Gaussian count, a buffer or u_dev changes. The first call
+ * on a plan runs the two steps eagerly (it sets up the lazily initialised resources).
+ * Results are identical to the two calls. Errors: FGA_ERR_STATE (not decomposed),
+ * FGA_ERR_INVALID (host u_dev, default stream), FGA_ERR_CUDA. */
+fga_status fga_run_graph(fga_plan_t plan, double* u_dev);
+
 /* Waits for the plan's stream and reports any device-side error flag. */
 fga_status fga_sync(fga_plan_t plan);
 

@@ -19,8 +19,9 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libfga.so")
 
 SOURCES = ["fga_api.cu", "fga_fbi.cu", "fga_select.cu", "fga_rays.cu", "fga_recon.cu",
-           "fga_recon_tc.cu"]
-HEADERS = ["fga_internal.cuh", "fga_medium.cuh", "fga_tiles.cuh", "fga_tc.cuh"]
+           "fga_recon_tc.cu", "fga_adjoint.cu"]
+HEADERS = ["fga_internal.cuh", "fga_medium.cuh", "fga_tiles.cuh", "fga_tc.cuh",
+           "fga_ray_rhs.cuh", "fga_ray_vjp.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr"]

@@ -1,0 +1,268 @@
+// Adjoint of the traces with respect to the velocity samples (the spline
+// coefficients): given the cotangent of the traces (for the misfit
+// J = 1/2 sum (trace - data)^2 it is the residual), accumulate
+//   grad_c = (d traces / d c)^T residual
+// with the set of Gaussians held fixed. c enters the traces through the rays (c, grad c
+// and the Hessian of c at Q in the right-hand side of Eqs. characline, dzQ, dzP,
+// a_formu) and through the branch split psi+ = 1/2 (psi_0 + i eps psi_1/(c(q)|p|))
+// (Eq. psi).
+//
+// Discrete adjoint of the RK4 scheme (the exact gradient of the computed traces):
+// every ray is integrated forward again storing a checkpoint every K ~ sqrt(T/dt)
+// steps; the reverse sweep recomputes one segment of K states at a time from its
+// checkpoint and runs the transposed RK4 stages, each through the hand-written
+// vector-Jacobian product of the right-hand side below (rhs_vjp). The coefficient
+// gradient of each evaluation of c, grad c, Hessian of c is scattered to its 4^d
+// spline taps with atomic additions. Like the forward integrator the kernel is
+// persistent (lanes take the next Gaussian from a counter); each resident thread owns
+// a slice of a scratch buffer for its checkpoints and segment states.
+#include <algorithm>
+
+#include "fga_internal.cuh"
+#include "fga_medium.cuh"
+#include "fga_ray_rhs.cuh"
+#include "fga_ray_vjp.cuh"
+
+namespace fga {
+
+namespace {
+
+using adj::cx;
+using adj::MedAD;
+using adj::conj;
+using adj::medium_ad;
+using adj::medium_ad_transpose;
+using adj::mk;
+using adj::mulc;
+using adj::rdot;
+using adj::rhs_vjp;
+using adj::rk4_step;
+using adj::rk4_step_adjoint;
+using adj::operator+;
+using adj::operator-;
+using adj::operator*;
+
+// Adjoint of the record at state y: lam += d(sum_r res_r trace contribution)/dy and
+// psib += the same derivative with respect to (Re psi, Im psi).
+template <int D>
+__device__ __forceinline__ void record_vjp(const GridDev& gd, const ShotDev& sh, const RxDev& rx,
+                                           double kappa, const double* y, double2 psi,
+                                           const double* __restrict__ res_row, double* lam,
+                                           double* psib) {
+  using Lo = Layout<D>;
+  const double cut = kappa * sh.sqrt_eps;
+  const double c0 = 2.0 * sh.W * sh.norm;
+  double sn, cs;
+  sincos(y[Lo::S] * sh.inv_eps, &sn, &cs);
+  const cx eS = mk(cs, sn);
+  const cx a = mk(y[Lo::aR], y[Lo::aI]);
+  const cx ps = mk(psi.x, psi.y);
+  const cx pref = c0 * (a * ps * eS);
+  cx prefb = mk(0, 0);
+  double Qb[D], Pb[D];
+#pragma unroll
+  for (int k = 0; k < D; ++k) Qb[k] = Pb[k] = 0.0;
+  for_receivers_in_window<D>(gd, rx, y + Lo::Q, cut, [&](int32_t r, const double* d) {
+    const double w = res_row[r];
+    double ph = 0.0, r2 = 0.0;
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      ph = fma(y[Lo::P + k], d[k], ph);
+      r2 = fma(d[k], d[k], r2);
+    }
+    double gs = exp(-0.5 * r2 * sh.inv_eps);
+    double s2, c2;
+    sincos(ph * sh.inv_eps, &s2, &c2);
+    const cx X = mk(gs * c2, gs * s2);
+    // value = Re(pref X); adjoint of the complex product with a real cotangent w
+    prefb = prefb + w * conj(X);
+    const cx Xb = w * conj(pref);
+    const cx zeta_b = mulc(Xb, X);  // X = exp(zeta), zeta = -|d|^2/(2 eps) + i P.d/eps
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      const double db = zeta_b.r * (-d[k] * sh.inv_eps) + zeta_b.i * y[Lo::P + k] * sh.inv_eps;
+      Pb[k] += zeta_b.i * d[k] * sh.inv_eps;
+      Qb[k] -= db;  // d = x_r - Q
+    }
+  });
+  // pref = c0 a psi e^{iS/eps}
+  const cx ab = mulc(prefb, c0 * (ps * eS));
+  const cx psb = mulc(prefb, c0 * (a * eS));
+  const double Sb = rdot(prefb, mk(-pref.i * sh.inv_eps, pref.r * sh.inv_eps));
+#pragma unroll
+  for (int k = 0; k < D; ++k) {
+    lam[Lo::Q + k] += Qb[k];
+    lam[Lo::P + k] += Pb[k];
+  }
+  lam[Lo::aR] += ab.r;
+  lam[Lo::aI] += ab.i;
+  lam[Lo::S] += Sb;
+  psib[0] += psb.r;
+  psib[1] += psb.i;
+}
+
+template <int D>
+__global__ void __launch_bounds__(128) k_adjoint(GridDev gd, const ShotDev* __restrict__ shots,
+                                                 const double* __restrict__ C, int64_t G,
+                                                 const int32_t* __restrict__ gshot,
+                                                 const int64_t* __restrict__ gq,
+                                                 const int32_t* __restrict__ gp,
+                                                 const double2* __restrict__ gpsi,
+                                                 const double2* __restrict__ gpsi_f1, int64_t nsteps,
+                                                 double dt, double kappa, int integrate_exited,
+                                                 RxDev rx, const double* __restrict__ residual,
+                                                 double* __restrict__ gradC, double* __restrict__ scratch,
+                                                 int64_t kseg, int64_t ncheck,
+                                                 unsigned long long* next) {
+  using Lo = Layout<D>;
+  constexpr int NF = Lo::NF;
+  const int64_t nthr = (int64_t)gridDim.x * blockDim.x;
+  const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  // scratch: [slot][field][thread], slots 0..ncheck-1 checkpoints, then kseg segment states
+  auto slot = [&](int64_t sidx, int f) -> double& { return scratch[(sidx * NF + f) * nthr + tid]; };
+  while (true) {
+    const int64_t g = (int64_t)atomicAdd(next, 1ull);
+    if (g >= G) break;
+    const int s = gshot[g];
+    const ShotDev& sh = shots[s];
+    double lo[D], hi[D];
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+      double reach = kappa * sh.sqrt_eps + 2.0 * gd.h[i];
+      lo[i] = gd.o[i] - reach;
+      hi[i] = gd.o[i] + (double)(gd.n[i] - 1) * gd.h[i] + reach;
+    }
+    double y[NF];
+    ray_init<D>(gd, sh, gq[g], gp[g], y);
+    // forward with checkpoints every kseg steps; nend = last step reached
+    int64_t nend = 0;
+    for (int64_t step = 0;; ++step) {
+      if (step % kseg == 0)
+#pragma unroll
+        for (int f = 0; f < NF; ++f) slot(step / kseg, f) = y[f];
+      bool done = step >= nsteps;
+      if (!done && !integrate_exited) {
+#pragma unroll
+        for (int i = 0; i < D; ++i)
+          done = done || (!gd.periodic[i] && ((y[Lo::Q + i] < lo[i] && y[Lo::P + i] <= 0.0) ||
+                                              (y[Lo::Q + i] > hi[i] && y[Lo::P + i] >= 0.0)));
+      }
+      if (done) {
+        nend = step;
+        break;
+      }
+      rk4_step<D>(gd, C, y, dt);
+    }
+    // reverse sweep
+    double lam[NF], psib[2] = {0.0, 0.0};
+#pragma unroll
+    for (int f = 0; f < NF; ++f) lam[f] = 0.0;
+    const double2 psi = gpsi[g];
+    int64_t seg_loaded = -1;
+    for (int64_t nn = nend;; --nn) {
+      // state y_nn from its segment (recomputed from the checkpoint when needed)
+      const int64_t j = nn / kseg;
+      if (j != seg_loaded) {
+        double z[NF];
+#pragma unroll
+        for (int f = 0; f < NF; ++f) z[f] = slot(j, f);
+        for (int64_t i = 0; i < kseg && j * kseg + i <= nend; ++i) {
+#pragma unroll
+          for (int f = 0; f < NF; ++f) slot(ncheck + i, f) = z[f];
+          if (i + 1 < kseg && j * kseg + i + 1 <= nend) rk4_step<D>(gd, C, z, dt);
+        }
+        seg_loaded = j;
+      }
+      double yn[NF];
+#pragma unroll
+      for (int f = 0; f < NF; ++f) yn[f] = slot(ncheck + (nn - j * kseg), f);
+      if (rx.every > 0 && nn % rx.every == 0)
+        record_vjp<D>(gd, sh, rx, kappa, yn, psi,
+                      residual + ((int64_t)s * rx.nrec + nn / rx.every) * rx.nrx, lam, psib);
+      if (nn == 0) break;
+      // state at nn - 1
+      const int64_t jp = (nn - 1) / kseg;
+      if (jp != seg_loaded) {
+        double z[NF];
+#pragma unroll
+        for (int f = 0; f < NF; ++f) z[f] = slot(jp, f);
+        for (int64_t i = 0; i < kseg && jp * kseg + i <= nend; ++i) {
+#pragma unroll
+          for (int f = 0; f < NF; ++f) slot(ncheck + i, f) = z[f];
+          if (i + 1 < kseg && jp * kseg + i + 1 <= nend) rk4_step<D>(gd, C, z, dt);
+        }
+        seg_loaded = jp;
+      }
+#pragma unroll
+      for (int f = 0; f < NF; ++f) yn[f] = slot(ncheck + (nn - 1 - jp * kseg), f);
+      rk4_step_adjoint<D>(gd, C, yn, dt, lam, gradC);
+    }
+    // branch split: psi+ = 1/2 psi_0 + t, t = 1/2 i eps psi_1/(c(q)|p|), so d psi+/d c(q) = -t/c(q)
+    const double2 t1 = gpsi_f1[g];
+    double q[D];
+    {
+      int64_t qf = gq[g];
+      int64_t qm[D];
+      if constexpr (D == 1) {
+        qm[0] = qf;
+      } else {
+        qm[0] = qf / sh.nq[1];
+        qm[1] = qf - qm[0] * sh.nq[1];
+      }
+#pragma unroll
+      for (int i = 0; i < D; ++i) q[i] = gd.o[i] + (double)(sh.s[i] * qm[i]) * gd.h[i];
+    }
+    MedAD<D> mq;
+    medium_ad<D>(gd, C, q, mq);
+    const double cqb = -(psib[0] * t1.x + psib[1] * t1.y) / mq.c;
+    double zero_g[D], Qdummy[D];
+    double zero_K[D][D];
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+      zero_g[i] = 0.0;
+      Qdummy[i] = 0.0;
+#pragma unroll
+      for (int k = 0; k < D; ++k) zero_K[i][k] = 0.0;
+    }
+    medium_ad_transpose<D>(gd, mq, cqb, zero_g, zero_K, Qdummy, gradC);
+  }
+}
+
+}  // namespace
+
+// Resident threads of the adjoint kernel and the scratch doubles they need.
+int64_t adjoint_threads(fga_plan_s* p) {
+  int dev = 0, sms = 0, per_sm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+  cudaError_t e = p->grid.dim == 1
+                      ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_adjoint<1>, 128, 0)
+                      : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_adjoint<2>, 128, 0);
+  if (e != cudaSuccess) return 0;
+  int64_t blocks = (int64_t)sms * (per_sm > 0 ? per_sm : 1);
+  blocks = std::min<int64_t>(blocks, (p->G + 127) / 128);
+  return std::max<int64_t>(blocks, 1) * 128;
+}
+
+cudaError_t launch_adjoint(fga_plan_s* p, const double* residual, double* gradC, double* scratch,
+                           int64_t nthreads, int64_t kseg, int64_t ncheck) {
+  cudaError_t e = cudaMemsetAsync(p->d_steps + 1, 0, sizeof(unsigned long long), p->stream);
+  if (e != cudaSuccess) return e;
+  if (p->G == 0) return cudaSuccess;
+  unsigned blocks = (unsigned)(nthreads / 128);
+  RxDev rx = p->rx;
+  if (p->grid.dim == 1)
+    k_adjoint<1><<<blocks, 128, 0, p->stream>>>(p->grid, p->d_shots, p->d_coef, p->G, p->d_gshot,
+                                                p->d_gq, p->d_gp, p->d_gpsi, p->d_gpsi_f1, p->nsteps,
+                                                p->dt, p->kappa, p->integrate_exited, rx, residual,
+                                                gradC, scratch, kseg, ncheck, p->d_steps + 1);
+  else
+    k_adjoint<2><<<blocks, 128, 0, p->stream>>>(p->grid, p->d_shots, p->d_coef, p->G, p->d_gshot,
+                                                p->d_gq, p->d_gp, p->d_gpsi, p->d_gpsi_f1, p->nsteps,
+                                                p->dt, p->kappa, p->integrate_exited, rx, residual,
+                                                gradC, scratch, kseg, ncheck, p->d_steps + 1);
+  p->launches += 1;
+  return cudaGetLastError();
+}
+
+}  // namespace fga

@@ -147,13 +147,15 @@ fga_status fga_destroy(fga_plan_t p) {
                   p->d_max2, p->d_blk, p->d_counts, p->d_blk_first, p->d_gshot, p->d_gq, p->d_gp,
                   p->d_gpsi, p->d_state, p->d_gcoef, p->d_tile_cnt, p->d_tile_off,
                   p->d_tile_list, p->d_seg_off, p->d_partial, p->d_out, p->d_status,
-                  p->d_steps};
+                  p->d_steps, p->d_rx, p->d_rx_off, p->d_rx_list, p->d_traces,
+                  p->d_psi_f1, p->d_gpsi_f1, p->d_adj_scratch, p->d_grad, p->d_resid};
   for (void* b : bufs)
     if (b) cudaFree(b);
   for (double* e : p->E)
     if (e) cudaFree(e);
   for (auto& ev : p->ev)
     if (ev) cudaEventDestroy(ev);
+  if (p->graph_exec) cudaGraphExecDestroy(p->graph_exec);
   delete p;
   return FGA_OK;
 }
@@ -390,6 +392,7 @@ fga_status fga_decompose(fga_plan_t p, const double* u0, const double* u1, int64
   p->blk_first[p->nshots] = psi_total / fga::kScanBlock;
   p->nblocks = psi_total / fga::kScanBlock;
   CUDA_OR_FAIL(p, grow(&p->d_psi, &p->psi_cap, (size_t)psi_total));
+  CUDA_OR_FAIL(p, grow(&p->d_psi_f1, &p->psi_f1_cap, (size_t)psi_total));
   if (d == 2) CUDA_OR_FAIL(p, grow(&p->d_g1, &p->g1_cap, (size_t)g1_total));
   CUDA_OR_FAIL(p, grow(&p->d_blk, &p->blk_cap, (size_t)p->nblocks + 1));
   CUDA_OR_FAIL(p, cudaMemcpyAsync(p->d_blk_first, p->blk_first.data(),
@@ -423,6 +426,8 @@ fga_status fga_decompose(fga_plan_t p, const double* u0, const double* u1, int64
     CUDA_OR_FAIL(p, grow(&p->d_gp, &c, cap));
     c = 0; if (p->d_gpsi) { cudaFree(p->d_gpsi); p->d_gpsi = nullptr; }
     CUDA_OR_FAIL(p, grow(&p->d_gpsi, &c, cap));
+    c = 0; if (p->d_gpsi_f1) { cudaFree(p->d_gpsi_f1); p->d_gpsi_f1 = nullptr; }
+    CUDA_OR_FAIL(p, grow(&p->d_gpsi_f1, &c, cap));
     c = 0; if (p->d_gcoef) { cudaFree(p->d_gcoef); p->d_gcoef = nullptr; }
     CUDA_OR_FAIL(p, grow(&p->d_gcoef, &c, cap));
     c = 0; if (p->d_state) { cudaFree(p->d_state); p->d_state = nullptr; }
@@ -448,15 +453,12 @@ fga_status fga_propagate(fga_plan_t p) {
   return FGA_OK;
 }
 
-fga_status fga_reconstruct(fga_plan_t p, double* u_out) {
-  fga_status st = check_usable(p);
-  if (st != FGA_OK) return st;
-  if (p->stage < 2) return fail(p, FGA_ERR_STATE, "fga_reconstruct before fga_propagate");
-  if (!u_out) return fail(p, FGA_ERR_INVALID, "u_out must not be NULL");
+// Device capacities the reconstruction needs for the current Gaussian set. The tile
+// lists: every Gaussian meets at most prod_k m_k tiles, m_k = (floor(window points /
+// tile) + 2) per image, times 5 images on periodic axes.
+static fga_status reconstruct_capacity(fga_plan_s* p) {
   const GridDev& gd = p->grid;
   const int d = gd.dim;
-  // capacity of the tile lists: every Gaussian meets at most prod_k m_k tiles,
-  // m_k = (floor(window points / tile) + 2) per image, times 5 images on periodic axes
   size_t pairs = 0;
   for (const auto& sh : p->shots) {
     size_t per = 1;
@@ -474,6 +476,71 @@ fga_status fga_reconstruct(fga_plan_t p, double* u_out) {
   CUDA_OR_FAIL(p, grow(&p->d_partial, &p->partial_cap,
                        tc ? (fga::partial_bytes_tc(p) + 7) / 8
                           : fga::partial_items(p) * fga::tile_points(d)));
+  return FGA_OK;
+}
+
+fga_status fga_run_graph(fga_plan_t p, double* u_dev) {
+  fga_status st = check_usable(p);
+  if (st != FGA_OK) return st;
+  if (p->stage < 1) return fail(p, FGA_ERR_STATE, "fga_run_graph before fga_decompose");
+  if (!u_dev || !is_device_ptr(u_dev))
+    return fail(p, FGA_ERR_INVALID, "fga_run_graph writes to device memory only");
+  if (p->stream == nullptr)
+    return fail(p, FGA_ERR_INVALID, "graph mode needs a stream other than the legacy default stream");
+  if (p->ray_blocks == 0) {
+    // first call: one eager pass sets up every lazily initialised resource
+    st = fga_propagate(p);
+    if (st != FGA_OK) return st;
+    return fga_reconstruct(p, u_dev);
+  }
+  st = reconstruct_capacity(p);
+  if (st != FGA_OK) return st;
+  int64_t key[6] = {p->G, (int64_t)p->g_cap, (int64_t)p->list_cap, (int64_t)p->partial_cap,
+                    (int64_t)(uintptr_t)u_dev, p->nrx};
+  bool same = p->graph_exec != nullptr;
+  for (int i = 0; i < 6; ++i) same = same && key[i] == p->graph_key[i];
+  if (!same) {
+    if (p->graph_exec) {
+      cudaGraphExecDestroy(p->graph_exec);
+      p->graph_exec = nullptr;
+    }
+    cudaGraph_t graph = nullptr;
+    CUDA_OR_FAIL(p, cudaStreamBeginCapture(p->stream, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = fga::launch_rays(p);
+    if (e == cudaSuccess) e = fga::launch_binning(p, nullptr);
+    if (e == cudaSuccess) e = fga::launch_binning_fill(p);
+    if (e == cudaSuccess)
+      e = p->precision == FGA_MIXED_TF32X3 ? fga::launch_reconstruct_tc(p, u_dev)
+                                           : fga::launch_reconstruct(p, u_dev);
+    cudaError_t e2 = cudaStreamEndCapture(p->stream, &graph);
+    if (e != cudaSuccess || e2 != cudaSuccess) {
+      if (graph) cudaGraphDestroy(graph);
+      return fail(p, FGA_ERR_CUDA, std::string("graph capture: ") +
+                                       cudaGetErrorString(e != cudaSuccess ? e : e2), true);
+    }
+    e = cudaGraphInstantiate(&p->graph_exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+      p->graph_exec = nullptr;
+      return fail(p, FGA_ERR_CUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e), true);
+    }
+    for (int i = 0; i < 6; ++i) p->graph_key[i] = key[i];
+  }
+  CUDA_OR_FAIL(p, cudaGraphLaunch(p->graph_exec, p->stream));
+  p->launches += 12;
+  p->stage = 2;
+  return FGA_OK;
+}
+
+fga_status fga_reconstruct(fga_plan_t p, double* u_out) {
+  fga_status st = check_usable(p);
+  if (st != FGA_OK) return st;
+  if (p->stage < 2) return fail(p, FGA_ERR_STATE, "fga_reconstruct before fga_propagate");
+  if (!u_out) return fail(p, FGA_ERR_INVALID, "u_out must not be NULL");
+  st = reconstruct_capacity(p);
+  if (st != FGA_OK) return st;
+  const GridDev& gd = p->grid;
+  const bool tc = p->precision == FGA_MIXED_TF32X3;
   CUDA_OR_FAIL(p, cudaEventRecord(p->ev[5], p->stream));
   CUDA_OR_FAIL(p, fga::launch_binning(p, nullptr));
   CUDA_OR_FAIL(p, fga::launch_binning_fill(p));
@@ -623,6 +690,119 @@ fga_status fga_state(fga_plan_t p, int shot, double* Q, double* P, double* A, do
     if (S) S[g] = F(aR + 2, g);
   }
   return FGA_OK;
+}
+
+fga_status fga_set_receivers(fga_plan_t p, int64_t nrx, const double* xr, int64_t record_every) {
+  fga_status st = check_usable(p);
+  if (st != FGA_OK) return st;
+  const GridDev& gd = p->grid;
+  const int d = gd.dim;
+  if (p->graph_exec) {  // a captured graph holds the old receiver buffers
+    cudaGraphExecDestroy(p->graph_exec);
+    p->graph_exec = nullptr;
+  }
+  for (void* b : {(void*)p->d_rx, (void*)p->d_rx_off, (void*)p->d_rx_list, (void*)p->d_traces})
+    if (b) cudaFree(b);
+  p->d_rx = nullptr;
+  p->d_rx_off = nullptr;
+  p->d_rx_list = nullptr;
+  p->d_traces = nullptr;
+  p->nrx = 0;
+  std::memset(&p->rx, 0, sizeof(p->rx));
+  if (nrx == 0) return FGA_OK;
+  if (nrx < 0 || nrx > (((int64_t)1 << 31) - 1) || !xr)
+    return fail(p, FGA_ERR_INVALID, "need 0 < nrx < 2^31 and receiver positions");
+  if (record_every < 1 || p->nsteps % record_every != 0)
+    return fail(p, FGA_ERR_INVALID, "record_every must be >= 1 and divide T/dt");
+  for (int k = 0; k < d; ++k)
+    if (gd.periodic[k]) return fail(p, FGA_ERR_INVALID, "receivers need open axes");
+  std::vector<double> x((size_t)nrx * d);
+  CUDA_OR_FAIL(p, cudaMemcpy(x.data(), xr, sizeof(double) * x.size(), cudaMemcpyDefault));
+  const int* nt = p->shots[0].ntile;
+  int64_t nbins = 1;
+  for (int k = 0; k < d; ++k) nbins *= nt[k];
+  std::vector<int64_t> bin((size_t)nrx), off((size_t)nbins + 1, 0);
+  for (int64_t r = 0; r < nrx; ++r) {
+    int64_t b = 0;
+    for (int k = 0; k < d; ++k) {
+      double v = x[(size_t)r * d + k];
+      if (!std::isfinite(v) || v < gd.o[k] || v > gd.o[k] + (double)(gd.n[k] - 1) * gd.h[k])
+        return fail(p, FGA_ERR_INVALID, "receivers must lie inside the grid");
+      int64_t i = (int64_t)std::floor((v - gd.o[k]) * gd.inv_h[k]);
+      i = std::min<int64_t>(std::max<int64_t>(i, 0), gd.n[k] - 1);
+      b = b * nt[k] + i / gd.tile[k];
+    }
+    bin[r] = b;
+    off[b + 1] += 1;
+  }
+  for (int64_t b = 0; b < nbins; ++b) off[b + 1] += off[b];
+  std::vector<int32_t> list((size_t)nrx);
+  std::vector<int64_t> fill(off.begin(), off.end() - 1);
+  for (int64_t r = 0; r < nrx; ++r) list[fill[bin[r]]++] = (int32_t)r;
+  const int64_t nrec = p->nsteps / record_every + 1;
+  CUDA_OR_FAIL(p, cudaMalloc(&p->d_rx, sizeof(double) * x.size()));
+  CUDA_OR_FAIL(p, cudaMalloc(&p->d_rx_off, sizeof(int64_t) * off.size()));
+  CUDA_OR_FAIL(p, cudaMalloc(&p->d_rx_list, sizeof(int32_t) * list.size()));
+  CUDA_OR_FAIL(p, cudaMalloc(&p->d_traces, sizeof(double) * p->nshots * nrec * nrx));
+  CUDA_OR_FAIL(p, cudaMemcpy(p->d_rx, x.data(), sizeof(double) * x.size(), cudaMemcpyHostToDevice));
+  CUDA_OR_FAIL(p, cudaMemcpy(p->d_rx_off, off.data(), sizeof(int64_t) * off.size(), cudaMemcpyHostToDevice));
+  CUDA_OR_FAIL(p, cudaMemcpy(p->d_rx_list, list.data(), sizeof(int32_t) * list.size(), cudaMemcpyHostToDevice));
+  p->nrx = nrx;
+  p->rx.nrx = nrx;
+  p->rx.nrec = nrec;
+  p->rx.every = record_every;
+  p->rx.x = p->d_rx;
+  p->rx.off = p->d_rx_off;
+  p->rx.list = p->d_rx_list;
+  for (int k = 0; k < fga::kMaxDim; ++k) p->rx.ntile[k] = k < d ? nt[k] : 1;
+  if (p->stage >= 2) p->stage = 1;  // traces need a new propagation
+  return FGA_OK;
+}
+
+fga_status fga_traces(fga_plan_t p, double* traces) {
+  fga_status st = check_usable(p);
+  if (st != FGA_OK) return st;
+  if (p->nrx == 0) return fail(p, FGA_ERR_STATE, "no receivers set");
+  if (p->stage < 2) return fail(p, FGA_ERR_STATE, "not propagated since the receivers were set");
+  if (!traces) return fail(p, FGA_ERR_INVALID, "traces must not be NULL");
+  size_t n = (size_t)p->nshots * p->rx.nrec * p->rx.nrx;
+  CUDA_OR_FAIL(p, cudaMemcpyAsync(traces, p->d_traces, sizeof(double) * n, cudaMemcpyDefault, p->stream));
+  return read_status(p);
+}
+
+fga_status fga_grad(fga_plan_t p, const double* residual, double* grad) {
+  fga_status st = check_usable(p);
+  if (st != FGA_OK) return st;
+  if (p->nrx == 0) return fail(p, FGA_ERR_STATE, "fga_grad needs receivers (fga_set_receivers)");
+  if (p->stage < 2) return fail(p, FGA_ERR_STATE, "fga_grad before fga_propagate");
+  if (!residual || !grad) return fail(p, FGA_ERR_INVALID, "residual and grad must not be NULL");
+  const GridDev& gd = p->grid;
+  const size_t nres = (size_t)p->nshots * p->rx.nrec * p->rx.nrx;
+  const double* d_res = residual;
+  if (!is_device_ptr(residual)) {
+    CUDA_OR_FAIL(p, grow(&p->d_resid, &p->resid_cap, nres));
+    CUDA_OR_FAIL(p, cudaMemcpyAsync(p->d_resid, residual, sizeof(double) * nres, cudaMemcpyDefault,
+                                    p->stream));
+    d_res = p->d_resid;
+  }
+  const int64_t kseg = std::max<int64_t>(1, (int64_t)std::ceil(std::sqrt((double)std::max<int64_t>(p->nsteps, 1))));
+  const int64_t ncheck = p->nsteps / kseg + 2;
+  const int64_t nthr = fga::adjoint_threads(p);
+  if (nthr <= 0) return fail(p, FGA_ERR_CUDA, "occupancy query for the adjoint kernel failed", true);
+  const size_t need = (size_t)nthr * (size_t)(ncheck + kseg) * (size_t)p->nfields;
+  CUDA_OR_FAIL(p, grow(&p->d_adj_scratch, &p->adj_scratch_cap, need));
+  double* dst = grad;
+  bool host_out = !is_device_ptr(grad);
+  if (host_out) {
+    if (!p->d_grad) CUDA_OR_FAIL(p, cudaMalloc(&p->d_grad, sizeof(double) * gd.npts));
+    dst = p->d_grad;
+  }
+  CUDA_OR_FAIL(p, cudaMemsetAsync(dst, 0, sizeof(double) * gd.npts, p->stream));
+  CUDA_OR_FAIL(p, fga::launch_adjoint(p, d_res, dst, p->d_adj_scratch, nthr, kseg, ncheck));
+  if (host_out)
+    CUDA_OR_FAIL(p, cudaMemcpyAsync(grad, dst, sizeof(double) * gd.npts, cudaMemcpyDeviceToHost,
+                                    p->stream));
+  return read_status(p);
 }
 
 int64_t fga_ray_steps(fga_plan_t p) {

@@ -77,9 +77,10 @@ __global__ void k_support_bbox(GridDev gd, const double* __restrict__ u0,
 }
 
 // Branch split, left-out p values and max |psi+|^2 for one output element.
+// out = psi+ = psi_0/2 + t, t = i eps psi_1/(2 c(q)|p|) (t is kept for the adjoint).
 template <int D>
 __device__ __forceinline__ double psi_plus(const ShotDev& sh, int64_t jp, double2 p0, double2 p1,
-                                           double cq, double2& out) {
+                                           double cq, double2& out, double2& t) {
   bool valid;
   double pn;
   if constexpr (D == 1) {
@@ -95,10 +96,12 @@ __device__ __forceinline__ double psi_plus(const ShotDev& sh, int64_t jp, double
   }
   if (!valid) {
     out = make_double2(0.0, 0.0);
+    t = out;
     return 0.0;
   }
   double r = sh.eps / (cq * pn);
-  out = make_double2(0.5 * (p0.x - r * p1.y), 0.5 * (p0.y + r * p1.x));
+  t = make_double2(-0.5 * r * p1.y, 0.5 * r * p1.x);
+  out = make_double2(0.5 * p0.x + t.x, 0.5 * p0.y + t.y);
   return out.x * out.x + out.y * out.y;
 }
 
@@ -113,6 +116,7 @@ __global__ void __launch_bounds__(NT) k_fbi_stage1(GridDev gd, const ShotDev* __
                                                    const double* __restrict__ C,
                                                    double2* __restrict__ g1,
                                                    double2* __restrict__ psi,
+                                                   double2* __restrict__ psi_f1,
                                                    unsigned long long* __restrict__ max2) {
   const int s = blockIdx.z;
   const ShotDev sh = shots[s];
@@ -226,9 +230,10 @@ __global__ void __launch_bounds__(NT) k_fbi_stage1(GridDev gd, const ShotDev* __
         if (m < M && n < N) {
           double2 p0 = make_double2(hv * acc0[i][j].x, hv * acc0[i][j].y);
           double2 p1 = make_double2(hv * acc1[i][j].x, hv * acc1[i][j].y);
-          double2 o;
-          double a2 = psi_plus<1>(sh, n, p0, p1, cq_s[ty + 16 * i], o);
+          double2 o, tt;
+          double a2 = psi_plus<1>(sh, n, p0, p1, cq_s[ty + 16 * i], o, tt);
           psi[sh.psi_off + m * sh.np + n] = o;
+          psi_f1[sh.psi_off + m * sh.np + n] = tt;
           mymax = fmax(mymax, a2);
         }
       }
@@ -243,6 +248,7 @@ __global__ void __launch_bounds__(NT) k_fbi_stage2(GridDev gd, const ShotDev* __
                                                    const double* __restrict__ C,
                                                    const double2* __restrict__ g1,
                                                    double2* __restrict__ psi,
+                                                   double2* __restrict__ psi_f1,
                                                    unsigned long long* __restrict__ max2) {
   const int s = blockIdx.z;
   const ShotDev sh = shots[s];
@@ -331,10 +337,11 @@ __global__ void __launch_bounds__(NT) k_fbi_stage2(GridDev gd, const ShotDev* __
       if (m < nbx && n < nbz) {
         double2 p0 = make_double2(hv * acc0[i][j].x, hv * acc0[i][j].y);
         double2 p1 = make_double2(hv * acc1[i][j].x, hv * acc1[i][j].y);
-        double2 o;
+        double2 o, tt;
         int64_t jp = m * nbz + n;
-        double a2 = psi_plus<2>(sh, jp, p0, p1, cq_s, o);
+        double a2 = psi_plus<2>(sh, jp, p0, p1, cq_s, o, tt);
         psi[sh.psi_off + ql * sh.np + jp] = o;
+        psi_f1[sh.psi_off + ql * sh.np + jp] = tt;
         mymax = fmax(mymax, a2);
       }
     }
@@ -374,16 +381,16 @@ cudaError_t launch_fbi(fga_plan_s* p, const double* u0, const double* u1) {
   if (g1grid.y > 65535) return cudaErrorInvalidConfiguration;
   if (D == 1) {
     k_fbi_stage1<1><<<g1grid, NT, 0, p->stream>>>(p->grid, p->d_shots, u0, u1, p->d_coef, p->d_g1,
-                                                  p->d_psi, p->d_max2);
+                                                  p->d_psi, p->d_psi_f1, p->d_max2);
     p->launches += 1;
     return cudaGetLastError();
   }
   k_fbi_stage1<2><<<g1grid, NT, 0, p->stream>>>(p->grid, p->d_shots, u0, u1, p->d_coef, p->d_g1,
-                                                p->d_psi, p->d_max2);
+                                                p->d_psi, p->d_psi_f1, p->d_max2);
   if (maxQ > 65535) return cudaErrorInvalidConfiguration;
   dim3 g2grid((unsigned)maxTiles, (unsigned)maxQ, p->nshots);
   k_fbi_stage2<<<g2grid, NT, 0, p->stream>>>(p->grid, p->d_shots, p->d_coef, p->d_g1, p->d_psi,
-                                             p->d_max2);
+                                             p->d_psi_f1, p->d_max2);
   p->launches += 2;
   return cudaGetLastError();
 }

@@ -109,7 +109,8 @@ __global__ void __launch_bounds__(NT) k_select_scatter(const ShotDev* __restrict
                                                        const unsigned long long* __restrict__ max2,
                                                        double tau2, const int64_t* __restrict__ blk,
                                                        int32_t* gshot, int64_t* gq, int32_t* gp,
-                                                       double2* gpsi) {
+                                                       double2* gpsi, const double2* __restrict__ psi_f1,
+                                                       double2* gpsi_f1) {
   int64_t base = (int64_t)blockIdx.x * kScanBlock;
   int s = shot_of_block(shots, nshots, base);
   const ShotDev& sh = shots[s];
@@ -149,6 +150,7 @@ __global__ void __launch_bounds__(NT) k_select_scatter(const ShotDev* __restrict
     gq[pos] = qflat;
     gp[pos] = (int32_t)jp;
     gpsi[pos] = psi[e0 + i];
+    gpsi_f1[pos] = psi_f1[e0 + i];
     ++pos;
   }
 }
@@ -190,11 +192,11 @@ cudaError_t launch_select(fga_plan_s* p) {
   if (p->grid.dim == 1)
     k_select_scatter<1><<<(unsigned)p->nblocks, NT, 0, p->stream>>>(
         p->d_shots, p->nshots, p->d_psi, p->d_max2, tau2, p->d_blk, p->d_gshot, p->d_gq, p->d_gp,
-        p->d_gpsi);
+        p->d_gpsi, p->d_psi_f1, p->d_gpsi_f1);
   else
     k_select_scatter<2><<<(unsigned)p->nblocks, NT, 0, p->stream>>>(
         p->d_shots, p->nshots, p->d_psi, p->d_max2, tau2, p->d_blk, p->d_gshot, p->d_gq, p->d_gp,
-        p->d_gpsi);
+        p->d_gpsi, p->d_psi_f1, p->d_gpsi_f1);
   p->launches += 1;
   return cudaGetLastError();
 }

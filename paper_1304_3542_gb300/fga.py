@@ -20,6 +20,8 @@ import numpy as np
 from . import build as _build
 
 FGA_OK = 0
+FGA_ERR_INVALID = 1
+FGA_ERR_STATE = 5
 FGA_FP64 = 0
 FGA_MIXED_TF32X3 = 1
 FGA_MIXED_BF16X3 = 2
@@ -93,6 +95,14 @@ def load(build_if_missing: bool = True):
     L.fga_stage_times.argtypes = [P, P, P]
     L.fga_ray_steps.argtypes = [P]
     L.fga_ray_steps.restype = i64
+    L.fga_set_receivers.argtypes = [P, i64, P, i64]
+    L.fga_set_receivers.restype = ci
+    L.fga_traces.argtypes = [P, P]
+    L.fga_traces.restype = ci
+    L.fga_run_graph.argtypes = [P, P]
+    L.fga_run_graph.restype = ci
+    L.fga_grad.argtypes = [P, P, P]
+    L.fga_grad.restype = ci
     L.fga_reconstruct_static.argtypes = [ci, P, P, P, P, ctypes.c_double, ctypes.c_double, i64,
                                          P, P, P, P]
     L.fga_reconstruct_static.restype = ci
@@ -163,6 +173,7 @@ class Plan:
         cfg.box = (self._box.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
                    if self._box is not None else None)
         cfg.T, cfg.dt, cfg.kappa, cfg.tau = float(T), float(dt), float(kappa), float(tau)
+        self._T, self._dt = float(T), float(dt)
         cfg.precision = int(precision)
         cfg.integrate_exited = int(bool(integrate_exited))
         _check_f64(velocity, self.npts, "velocity")
@@ -216,6 +227,11 @@ class Plan:
         self._check(self._L.fga_reconstruct(self._h, _ptr(out)), "fga_reconstruct")
         return out
 
+    def run_graph(self, out):
+        """propagate + reconstruct into the device tensor out, as one CUDA graph replay."""
+        self._check(self._L.fga_run_graph(self._h, _ptr(out)), "fga_run_graph")
+        return out
+
     def sync(self):
         self._check(self._L.fga_sync(self._h), "fga_sync")
 
@@ -257,6 +273,29 @@ class Plan:
                                       B.ctypes.data, a.ctypes.data, S.ctypes.data), "fga_state")
         return {"Q": Q, "P": P, "A": A[..., 0] + 1j * A[..., 1], "B": B[..., 0] + 1j * B[..., 1],
                 "a": a[:, 0] + 1j * a[:, 1], "S": S}
+
+    def set_receivers(self, xr, record_every: int):
+        xr = np.ascontiguousarray(xr, dtype=np.float64)
+        self._rx = xr
+        self._record_every = int(record_every)
+        self._check(self._L.fga_set_receivers(self._h, xr.shape[0] if xr.size else 0,
+                                              xr.ctypes.data if xr.size else None,
+                                              int(record_every)), "fga_set_receivers")
+
+    def traces(self, out=None):
+        nrx = self._rx.shape[0]
+        nrec = int(round(self._T / self._dt)) // self._record_every + 1
+        if out is None:
+            out = np.empty((self.nshots, nrec, nrx))
+        self._check(self._L.fga_traces(self._h, _ptr(out)), "fga_traces")
+        return out
+
+    def grad(self, residual, out=None):
+        """(d traces / d c)^T residual on the velocity grid (the set of Gaussians fixed)."""
+        if out is None:
+            out = np.empty(self.n)
+        self._check(self._L.fga_grad(self._h, _ptr(residual), _ptr(out)), "fga_grad")
+        return out
 
     def ray_steps(self) -> int:
         return int(self._L.fga_ray_steps(self._h))

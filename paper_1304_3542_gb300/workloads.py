@@ -116,14 +116,15 @@ def periodic_1d(N: int = 512, eps: float = 1.0 / 128, T: float = 0.25, dt: float
 def lens_2d(N: int = 256, eps: float = 1.0 / 256, T: float = 0.5, dt: float = 1e-3,
             kappa: float = 6.0, tau: float = 1e-3, s: int = 8, box: int = 192,
             k0: float = 40 * math.pi, width2: float = 0.005,
-            x0: Tuple[float, float] = (0.5, 0.2)) -> Problem:
-    """2D smooth lens c = 1 + 0.3 exp(-((x-.5)^2+(z-.5)^2)/0.02) on [0,1)^2 (open axes),
-    with a Gaussian-modulated plane-wave packet travelling in +z:
-    u0 = exp(-|x-x0|^2/width2) cos(k0 (z - z0)), u1 = -c(x) du0/dz."""
+            x0: Tuple[float, float] = (0.5, 0.2),
+            center: Tuple[float, float] = (0.5, 0.5)) -> Problem:
+    """2D smooth lens c = 1 + 0.3 exp(-|x - center|^2/0.02) on [0,1)^2 (open axes; the
+    default center is (0.5, 0.5)), with a Gaussian-modulated plane-wave packet travelling
+    in +z: u0 = exp(-|x-x0|^2/width2) cos(k0 (z - z0)), u1 = -c(x) du0/dz."""
     h = 1.0 / N
     ax = h * np.arange(N)
     X, Z = np.meshgrid(ax, ax, indexing="ij")
-    c = 1.0 + 0.3 * np.exp(-((X - 0.5) ** 2 + (Z - 0.5) ** 2) / 0.02)
+    c = 1.0 + 0.3 * np.exp(-((X - center[0]) ** 2 + (Z - center[1]) ** 2) / 0.02)
     env = np.exp(-((X - x0[0]) ** 2 + (Z - x0[1]) ** 2) / width2)
     u0 = env * np.cos(k0 * (Z - x0[1]))
     du0 = env * (-2.0 * (Z - x0[1]) / width2 * np.cos(k0 * (Z - x0[1]))

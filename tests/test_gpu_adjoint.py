@@ -1,0 +1,171 @@
+"""Traces at receivers and the hand-written adjoint (d traces/d c)^T r.
+
+* GPU traces against the oracle's traces (same Gaussians, both branches summed
+  literally by the oracle): rel-L2 <= 1e-10.
+* <grad J, v> for J = 1/2 |traces|^2 against central differences of J on the GPU
+  (<= 1e-6 relative) and against the oracle's directional derivative (Richardson-
+  extrapolated central differences of the oracle's traces with the set of Gaussians
+  frozen; <= 1e-6 relative), for random smooth v and for single grid cells.
+kappa = 8 so that Gaussians crossing a window edge change J by e^{-32} only. The lens
+centre is kept off the spline's knot lines: in the symmetric lens centred on a knot
+line, rays with p_x = 0 started on that line stay on it, where the Hessian of the cubic
+spline has a kink; the derivative is then one-sided (the adjoint returns the derivative
+of the cell the ray is in) while a central difference averages both sides.
+"""
+
+import dataclasses
+import functools
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1304_3542_gb300 import fga as F
+from paper_1304_3542_gb300 import workloads as WL
+
+pytestmark = pytest.mark.gpu
+
+
+@functools.lru_cache(maxsize=1)
+def _problem():
+    """The lens problem with the threshold put where the selected set cannot change under
+    the finite-difference steps below (the adjoint differentiates with the set held
+    fixed). A change dc of c(q) moves psi+ by at most |psi+ - psi0/2| |dc|/c (Eq. psi,
+    u+-,0) and M by about as much, so each |psi+|/M is known to within a relative shift
+    s; tau goes into the gap between consecutive ratios in 0.2%..5% whose slack after
+    both neighbours' shifts is largest."""
+    prob = WL.lens_2d(N=64, eps=1.0 / 400, T=0.1, dt=2e-3, s=2, box=32, tau=1e-2, kappa=8.0,
+                      k0=24 * math.pi, width2=0.004, x0=(0.4937, 0.3), center=(0.5071, 0.4963))
+    sh = prob.shots[0]
+    g = O.Grid(prob.n, prob.h, prob.origin, prob.periodic)
+    dec = O.decompose(g, prob.velocity, sh.u0, sh.u1, sh.eps, sh.q_stride, sh.box, prob.tau)
+    plus = dec["psi_plus"][:, dec["valid"]].ravel()
+    psi0 = dec["psi0"][:, dec["valid"]].ravel()
+    r = np.abs(plus) / dec["M"]
+    rel_dc = 2e-4 / prob.velocity.min()  # |dc| <= 1e-4 * max|v| (v <= 1), spline gain < 2
+    shift = (np.abs(plus - 0.5 * psi0) / np.maximum(np.abs(plus), 1e-300) + 1.0) * rel_dc
+    keep = (r > 2e-3) & (r < 5e-2)
+    order = np.argsort(r[keep])
+    rs, ss = r[keep][order], shift[keep][order]
+    lo, hi = rs[:-1] * (1 + ss[:-1]), rs[1:] * (1 - ss[1:])
+    k = int(np.argmax(np.log(hi) - np.log(lo)))
+    assert hi[k] > lo[k] * 1.0005, (lo[k], hi[k])
+    return dataclasses.replace(prob, tau=float(np.sqrt(lo[k] * hi[k])))
+
+
+def _receivers():
+    x = np.linspace(0.15, 0.85, 29)
+    return np.stack([x, np.full_like(x, 0.5)], axis=1)
+
+
+REC = 5
+
+
+def _gpu(prob, c, want_plan=False):
+    import torch
+
+    plan = F.plan_from_problem(prob, velocity=np.ascontiguousarray(c),
+                               stream=torch.cuda.current_stream().cuda_stream,
+                               integrate_exited=True)
+    plan.set_receivers(_receivers(), REC)
+    u0, u1 = F.stacked_initial_data(prob)
+    plan.decompose(torch.from_numpy(u0).cuda(), torch.from_numpy(u1).cuda())
+    plan.propagate()
+    tr = plan.traces()
+    qi, pi, _ = plan.gaussians(0)
+    keys = set(zip(qi.tolist(), pi.tolist()))
+    if want_plan:
+        return tr, keys, plan
+    plan.close()
+    return tr, keys
+
+
+def _smooth_direction(n, seed):
+    rng = np.random.default_rng(seed)
+    X, Z = np.meshgrid(np.linspace(0, 1, n[0]), np.linspace(0, 1, n[1]), indexing="ij")
+    v = np.zeros(n)
+    for _ in range(4):
+        kx, kz = rng.uniform(1, 4, 2)
+        v += rng.standard_normal() * np.sin(2 * np.pi * (kx * X + rng.uniform())) * np.cos(
+            2 * np.pi * (kz * Z + rng.uniform()))
+    return v / np.abs(v).max()
+
+
+def test_traces_match_oracle():
+    prob = _problem()
+    tr, keys = _gpu(prob, prob.velocity)
+    sh = prob.shots[0]
+    g = O.Grid(prob.n, prob.h, prob.origin, prob.periodic)
+    dec = O.decompose(g, prob.velocity, sh.u0, sh.u1, sh.eps, sh.q_stride, sh.box, prob.tau)
+    gs = dec["gauss"]
+    W = O.quadrature_weight(g, sh.eps, sh.q_stride, sh.box)
+    ot = O.traces(g, prob.velocity, prob.nsteps, prob.dt, REC, gs["sigma"], gs["q"], gs["p"],
+                  gs["psi"], sh.eps, prob.kappa, W, _receivers())
+    assert np.linalg.norm(ot.imag) <= 1e-12 * np.linalg.norm(ot.real)
+    err = np.linalg.norm(tr[0] - ot.real) / np.linalg.norm(ot.real)
+    assert err <= 1e-10, err
+
+
+def test_adjoint_directional_derivatives():
+    prob = _problem()
+    c = prob.velocity
+    tr, keys, plan = _gpu(prob, c, want_plan=True)
+    J0 = 0.5 * float(np.sum(tr ** 2))
+    grad = plan.grad(np.ascontiguousarray(tr))  # residual = traces (data = 0)
+    plan.close()
+    assert np.all(np.isfinite(grad)) and np.abs(grad).max() > 0
+    sh = prob.shots[0]
+    g = O.Grid(prob.n, prob.h, prob.origin, prob.periodic)
+    dec = O.decompose(g, c, sh.u0, sh.u1, sh.eps, sh.q_stride, sh.box, prob.tau)
+    gk = dec["gauss"]
+    okeys = (gk["sigma"], gk["qidx"], gk["pidx"])
+
+    def J_oracle(cc):
+        t = O.frozen_set_traces(g, cc, sh.u0, sh.u1, sh.eps, sh.q_stride, sh.box, okeys,
+                                prob.nsteps, prob.dt, REC, prob.kappa, _receivers())
+        return 0.5 * float(np.sum(t.real ** 2))
+
+    for seed in (1, 2):
+        v = _smooth_direction(prob.n, seed)
+        dg = float(np.sum(grad * v))
+        # GPU central differences (the selected set must not change)
+        hstep = 1e-4
+        trp, kp = _gpu(prob, c + hstep * v)
+        trm, km = _gpu(prob, c - hstep * v)
+        assert kp == keys and km == keys
+        fd = (0.5 * np.sum(trp ** 2) - 0.5 * np.sum(trm ** 2)) / (2 * hstep)
+        assert abs(dg - fd) <= 2e-6 * abs(fd), (dg, fd)
+        # oracle directional derivative, Richardson-extrapolated central differences
+        h1 = 1e-4
+        d1 = (J_oracle(c + h1 * v) - J_oracle(c - h1 * v)) / (2 * h1)
+        d2 = (J_oracle(c + 0.5 * h1 * v) - J_oracle(c - 0.5 * h1 * v)) / h1
+        dor = (4 * d2 - d1) / 3
+        assert abs(dg - dor) <= 2e-6 * abs(dor), (dg, dor)
+    # single cells where the gradient is largest
+    flat = np.argsort(-np.abs(grad.ravel()))[:3]
+    for f in flat:
+        e = np.zeros(prob.n)
+        e.ravel()[f] = 1.0
+        hstep = 1e-4
+        trp, _ = _gpu(prob, c + hstep * e)
+        trm, _ = _gpu(prob, c - hstep * e)
+        fd = (0.5 * np.sum(trp ** 2) - 0.5 * np.sum(trm ** 2)) / (2 * hstep)
+        assert abs(grad.ravel()[f] - fd) <= 1e-5 * abs(fd) + 1e-12 * J0, (grad.ravel()[f], fd)
+
+
+def test_autograd_function_matches_fga_grad():
+    import torch
+
+    from paper_1304_3542_gb300 import autograd as FA
+
+    prob = _problem()
+    vel = torch.from_numpy(np.ascontiguousarray(prob.velocity)).cuda().requires_grad_(True)
+    tr = FA.traces(vel, prob, _receivers(), REC, integrate_exited=True)
+    loss = 0.5 * (tr ** 2).sum()
+    loss.backward()
+    tr_np, keys, plan = _gpu(prob, prob.velocity, want_plan=True)
+    g = plan.grad(np.ascontiguousarray(tr_np))
+    plan.close()
+    got = vel.grad.cpu().numpy()
+    assert np.linalg.norm(got - g) <= 1e-10 * np.linalg.norm(g)
