@@ -43,11 +43,11 @@ METRIC = "FGA Gaussian·gridpoint evals/s and rel-L2 err; mixed-prec vs FP64, 1 
 UNIT = "evals/s"
 L2_FLUSH_BYTES = 256 << 20
 # FP64 operations of one RK4 ray step in 2D, counted from the source of the ray
-# kernel (add/sub/mul/div/rsqrt = 1, fma = 2): 4 right-hand sides of 460 (spline
-# weights 76, 4x4 tap contraction 144, derivative scaling 8, ray and dynamic-ray
-# algebra 145, tr(Z^-1 dZ/dt) with da/dt 81, dS/dt 6) plus 322 for the stage
-# combinations of the 23 state values.
-FLOPS_PER_RAY_STEP_2D = 2162
+# kernel (add/sub/mul/div/rsqrt/floor = 1, fma = 2): 4 right-hand sides of 322
+# (medium from the per-cell polynomial table 90: cell and offsets 10, four rows in z
+# 48, combination in x 32; ray and dynamic-ray algebra 145, tr(Z^-1 dZ/dt) with
+# da/dt 81, dS/dt 6) plus 322 for the stage combinations of the 23 state values.
+FLOPS_PER_RAY_STEP_2D = 1610
 # FP64 peak from the unit counts and clocks: 152 SMs x 2 DFMA/clk/SM x 2 flop x 2.07 GHz
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 
@@ -178,7 +178,10 @@ def run_ours(args, rank, world, local_rank):
         plan.propagate()
         plan.reconstruct(out)
 
-    # first pass: Gaussian count and algorithmic evaluation count of the workload
+    # first pass: the autotuner picks the ray launch shape and the gather's segment
+    # length on this workload; then the Gaussian count and evaluation count
+    plan.decompose(d_u0, d_u1)
+    tuning = plan.autotune(d_out)
     step(d_u0, d_u1, d_out)
     plan.sync()
     G = plan.count(0)
@@ -245,8 +248,7 @@ def run_ours(args, rank, world, local_rank):
         ref = F.plan_from_problem(prob, stream=stream.cuda_stream, precision=F.FGA_FP64)
         d_ref = torch.zeros_like(d_out)
         ref.decompose(d_u0, d_u1)
-        ref.propagate()
-        ref.reconstruct(d_ref)
+        ref.autotune(d_ref)
         ref.sync()
         rel_l2 = float((d_out - d_ref).norm() / d_ref.norm())
         t64 = []
@@ -299,6 +301,8 @@ def run_ours(args, rank, world, local_rank):
                           "(TF32 head/tail factors, 3 products, FP32 accumulate, FP64 phase "
                           "anchors and segment sums)"),
             "fp64_path_value": fp64_value,
+            "tuning": {"ray_blocks_per_sm": tuning[0], "gather_segment": tuning[1],
+                       "by": "fga_autotune on this workload before the warm-up"},
             "stage_ms_mean": {"fbi": statistics.mean(fbi_ms), "rays": statistics.mean(ray_ms),
                               "binning+reconstruct": statistics.mean(recon_ms)},
             "l2": "256 MiB buffer written between timed steps",
@@ -371,6 +375,132 @@ def oracle_sample(prob, n_sample, nthreads):
     return est, desc, evals, t_dec + t_prop + t_rec
 
 
+def run_batch(args, rank, world, local_rank):
+    """The batched-shots workload (64 shots on the layered model, per-shot frequency and
+    eps): this rank's shots (contiguous block, no collective) as one plan per stage in the
+    mixed precision with the CUDA-graph replay, against the same shots run in FP64 in one
+    batched plan and in FP64 one plan per shot. One untimed pass, then args.steps timed
+    passes of each form; the speedups of batching and of precision are reported apart."""
+    import dataclasses
+
+    import torch
+
+    from paper_1304_3542_gb300 import fga as F
+    from paper_1304_3542_gb300 import workloads as WL
+    from paper_1304_3542_gb300.shards import max_over_ranks, shard_shots
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    full = WL.layered_batch()
+    mine = shard_shots(len(full.shots), rank, world)
+    prob = dataclasses.replace(full, shots=[full.shots[i] for i in mine])
+    stream = torch.cuda.Stream(dev)
+    u0, u1 = F.stacked_initial_data(prob)
+    d_u0, d_u1 = torch.from_numpy(u0).to(dev), torch.from_numpy(u1).to(dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def timed(fn, reps):
+        out = []
+        for i in range(reps):
+            flush.fill_(float(i))
+            torch.cuda.synchronize(dev)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            e1.synchronize()
+            out.append(e0.elapsed_time(e1) / 1e3)
+        return statistics.mean(out)
+
+    with torch.cuda.stream(stream):
+        # mixed, batched, graph replay of propagate + reconstruct
+        mixed = F.plan_from_problem(prob, stream=stream.cuda_stream, precision=F.FGA_MIXED_TF32X3)
+        d_mx = torch.zeros((len(prob.shots),) + prob.n, dtype=torch.float64, device=dev)
+        mixed.decompose(d_u0, d_u1)
+        tuning = mixed.autotune(d_mx)
+        counts = [mixed.count(s) for s in range(len(prob.shots))]
+        evals = 0.0
+        for s in range(len(prob.shots)):
+            evals += 2.0 * window_evals(prob, mixed.state(s)["Q"], prob.shots[s].eps)
+
+        def mixed_step():
+            mixed.decompose(d_u0, d_u1)
+            mixed.run_graph(d_mx)
+
+        mixed_step()
+        t_mixed = timed(mixed_step, args.steps)
+        # FP64, batched
+        b64 = F.plan_from_problem(prob, stream=stream.cuda_stream, precision=F.FGA_FP64)
+        d_64 = torch.zeros_like(d_mx)
+        b64.decompose(d_u0, d_u1)
+        b64.autotune(d_64)
+
+        def b64_step():
+            b64.decompose(d_u0, d_u1)
+            b64.propagate()
+            b64.reconstruct(d_64)
+
+        t_b64 = timed(b64_step, args.steps)
+        rel = float((d_mx - d_64).norm() / d_64.norm())
+        b64.close()
+        # FP64, one plan per shot, shots in turn
+        singles = []
+        for s in range(len(prob.shots)):
+            one = dataclasses.replace(prob, shots=[prob.shots[s]])
+            pl = F.plan_from_problem(one, stream=stream.cuda_stream, precision=F.FGA_FP64)
+            singles.append(pl)
+
+        def per_shot_step():
+            for s, pl in enumerate(singles):
+                pl.decompose(d_u0[s:s + 1], d_u1[s:s + 1])
+                pl.propagate()
+                pl.reconstruct(d_64[s:s + 1])
+
+        per_shot_step()
+        t_single = timed(per_shot_step, args.steps)
+        for pl in singles:
+            pl.close()
+        mixed.close()
+    t_mixed_all = max_over_ranks(t_mixed)
+    evals_all = evals
+    if world > 1:
+        t = torch.tensor([evals], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t)
+        evals_all = float(t.item())
+    return {
+        "metric": METRIC,
+        "value": evals_all / t_mixed_all,
+        "unit": UNIT,
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": 1,
+        "ms_per_step": t_mixed_all * 1e3,
+        "higher_is_better": True,
+        "scaling": "strong",
+        "vs_baseline": None,
+        "dtype": "f64+tf32",
+        "data": "synthetic (seeded layered model, 64 Ricker-ring shots; no dataset)",
+        "rel_l2_vs_fp64": rel,
+        "config": {
+            "workload": "layered model 737x241 at 12.5 m, 64 shots (x ~ U(1.0, 8.2) km, depth ~ "
+                        "U(0.01, 0.5) km, f ~ U(8, 25) Hz, per-shot eps), T=2 s, dt=1 ms",
+            "shots_this_rank": len(mine),
+            "gaussians_per_shot": {"min": min(counts), "median": statistics.median(counts),
+                                   "max": max(counts)},
+            "tuning": {"ray_blocks_per_sm": tuning[0], "gather_segment": tuning[1]},
+            "form": "mixed precision, all shots of the rank in one plan, propagate + "
+                    "reconstruct replayed as one CUDA graph",
+            "seconds_per_pass": {"mixed_batched_graph": t_mixed, "fp64_batched": t_b64,
+                                 "fp64_one_plan_per_shot": t_single},
+            "speedup_batching_fp64": t_single / t_b64,
+            "speedup_precision_batched": t_b64 / t_mixed,
+            "speedup_total_vs_fp64_per_shot": t_single / t_mixed,
+            "l2": "256 MiB buffer written between timed passes",
+            "parallelism": "shot-parallel, %d rank(s), no collective" % world,
+        },
+    }
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return None
@@ -412,6 +542,10 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=512)
+    ap.add_argument("--workload", choices=["layered_single", "layered_batch"],
+                    default="layered_single",
+                    help="layered_batch: the 64-shot batched form against FP64 batched and "
+                         "FP64 one plan per shot (one timed pass each by default)")
     ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed",
                     help="mixed: tensor-core reconstruction (its rel-L2 against the FP64 "
                          "path is measured in the same run); fp64: every step in FP64")
@@ -437,6 +571,16 @@ def main():
         if world > 1:
             import torch.distributed as dist
 
+            dist.destroy_process_group()
+        return
+    if args.workload == "layered_batch":
+        line = run_batch(args, rank, world, local_rank)
+        if rank == 0:
+            print(json.dumps(line), flush=True)
+        if world > 1:
+            import torch.distributed as dist
+
+            dist.barrier()
             dist.destroy_process_group()
         return
     line, prob, evals = run_ours(args, rank, world, local_rank)

@@ -168,6 +168,26 @@ fga_status fga_grad(fga_plan_t plan, const double* residual, double* grad);
  * FGA_ERR_INVALID (host u_dev, default stream), FGA_ERR_CUDA. */
 fga_status fga_run_graph(fga_plan_t plan, double* u_dev);
 
+/* Autotuner (batching). Picks, by timing on this plan's own decomposed data, (0) the
+ * number of resident blocks per SM of the persistent ray kernel (from the occupancy
+ * maximum down, on a short integration of at most 64 steps) and (1) the split-K segment
+ * length of the reconstruction gather (Gaussians per (tile, segment) work item; 5
+ * powers of two), then runs the full fga_propagate and fga_reconstruct with them into
+ * the device buffer u_dev. Blocks the host until done. The choice stays with the plan
+ * and is written to choice[2] when choice is not NULL. Ray states are identical for
+ * every choice; the field changes only by the order of the FP64 (or FP32 tensor-core)
+ * partial sums. Errors: FGA_ERR_STATE (not decomposed), FGA_ERR_INVALID (host u_dev),
+ * FGA_ERR_OOM, FGA_ERR_CUDA. */
+fga_status fga_autotune(fga_plan_t plan, double* u_dev, int64_t* choice);
+
+/* The plan's current tuning, choice[2] as written by fga_autotune (blocks per SM, 0 =
+ * occupancy maximum; segment length in Gaussians). */
+fga_status fga_tuning(fga_plan_t plan, int64_t* choice);
+
+/* Sets the tuning (e.g. one found earlier for the same workload): 0 <= choice[0] <= 64,
+ * 0 <= choice[1] <= 2^20, 0 meaning the default. FGA_ERR_INVALID otherwise. */
+fga_status fga_set_tuning(fga_plan_t plan, const int64_t* choice);
+
 /* Waits for the plan's stream and reports any device-side error flag. */
 fga_status fga_sync(fga_plan_t plan);
 

@@ -62,18 +62,10 @@ __device__ __forceinline__ void record_vjp(const GridDev& gd, const ShotDev& sh,
   double Qb[D], Pb[D];
 #pragma unroll
   for (int k = 0; k < D; ++k) Qb[k] = Pb[k] = 0.0;
-  for_receivers_in_window<D>(gd, rx, y + Lo::Q, cut, [&](int32_t r, const double* d) {
+  for_receivers_X<D>(gd, rx, y + Lo::Q, y + Lo::P, cut, sh.inv_eps,
+                     [&](int64_t r, const double* d, double2 Xv) {
     const double w = res_row[r];
-    double ph = 0.0, r2 = 0.0;
-#pragma unroll
-    for (int k = 0; k < D; ++k) {
-      ph = fma(y[Lo::P + k], d[k], ph);
-      r2 = fma(d[k], d[k], r2);
-    }
-    double gs = exp(-0.5 * r2 * sh.inv_eps);
-    double s2, c2;
-    sincos(ph * sh.inv_eps, &s2, &c2);
-    const cx X = mk(gs * c2, gs * s2);
+    const cx X = mk(Xv.x, Xv.y);
     // value = Re(pref X); adjoint of the complex product with a real cotangent w
     prefb = prefb + w * conj(X);
     const cx Xb = w * conj(pref);
@@ -111,18 +103,22 @@ __global__ void __launch_bounds__(128) k_adjoint(GridDev gd, const ShotDev* __re
                                                  const double2* __restrict__ gpsi_f1, int64_t nsteps,
                                                  double dt, double kappa, int integrate_exited,
                                                  RxDev rx, const double* __restrict__ residual,
-                                                 double* __restrict__ gradC, double* __restrict__ scratch,
+                                                 double* __restrict__ grad_part, int64_t grad_len,
+                                                 int slices, double* __restrict__ scratch,
                                                  int64_t kseg, int64_t ncheck,
-                                                 unsigned long long* next) {
+                                                 unsigned long long* next, unsigned long long mult) {
   using Lo = Layout<D>;
   constexpr int NF = Lo::NF;
+  // this block's private slice of dJ/dc (no other block adds into it)
+  double* gradC = grad_part + (int64_t)(blockIdx.x % slices) * grad_len;
   const int64_t nthr = (int64_t)gridDim.x * blockDim.x;
   const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   // scratch: [slot][field][thread], slots 0..ncheck-1 checkpoints, then kseg segment states
   auto slot = [&](int64_t sidx, int f) -> double& { return scratch[(sidx * NF + f) * nthr + tid]; };
   while (true) {
-    const int64_t g = (int64_t)atomicAdd(next, 1ull);
-    if (g >= G) break;
+    const unsigned long long w = atomicAdd(next, 1ull);
+    if (w >= (unsigned long long)G) break;
+    const int64_t g = work_order(w, G, mult);
     const int s = gshot[g];
     const ShotDev& sh = shots[s];
     double lo[D], hi[D];
@@ -244,25 +240,41 @@ int64_t adjoint_threads(fga_plan_s* p) {
   return std::max<int64_t>(blocks, 1) * 128;
 }
 
+// dJ/dc into gradC (device, npts): the kernel adds into block-private slices of
+// p->d_part (sized by the caller for adjoint_slices(p, nthreads)), then the slices are
+// summed in order into gradC.
+int64_t adjoint_slices(fga_plan_s* p, int64_t nthreads) {
+  return part_slices(std::max<int64_t>(nthreads / 128, 1), p->grid.npts);
+}
+
 cudaError_t launch_adjoint(fga_plan_s* p, const double* residual, double* gradC, double* scratch,
                            int64_t nthreads, int64_t kseg, int64_t ncheck) {
   cudaError_t e = cudaMemsetAsync(p->d_steps + 1, 0, sizeof(unsigned long long), p->stream);
   if (e != cudaSuccess) return e;
-  if (p->G == 0) return cudaSuccess;
-  unsigned blocks = (unsigned)(nthreads / 128);
+  const int64_t len = p->grid.npts;
+  if (p->G == 0) return cudaMemsetAsync(gradC, 0, sizeof(double) * len, p->stream);
+  const unsigned blocks = (unsigned)(nthreads / 128);
+  const int64_t slices = adjoint_slices(p, nthreads);
+  if (p->part_cap < (size_t)(slices * len)) return cudaErrorInvalidValue;
+  e = cudaMemsetAsync(p->d_part, 0, sizeof(double) * slices * len, p->stream);
+  if (e != cudaSuccess) return e;
   RxDev rx = p->rx;
   if (p->grid.dim == 1)
     k_adjoint<1><<<blocks, 128, 0, p->stream>>>(p->grid, p->d_shots, p->d_coef, p->G, p->d_gshot,
                                                 p->d_gq, p->d_gp, p->d_gpsi, p->d_gpsi_f1, p->nsteps,
                                                 p->dt, p->kappa, p->integrate_exited, rx, residual,
-                                                gradC, scratch, kseg, ncheck, p->d_steps + 1);
+                                                p->d_part, len, (int)slices, scratch, kseg, ncheck,
+                                                p->d_steps + 1, work_order_mult(p->G));
   else
     k_adjoint<2><<<blocks, 128, 0, p->stream>>>(p->grid, p->d_shots, p->d_coef, p->G, p->d_gshot,
                                                 p->d_gq, p->d_gp, p->d_gpsi, p->d_gpsi_f1, p->nsteps,
                                                 p->dt, p->kappa, p->integrate_exited, rx, residual,
-                                                gradC, scratch, kseg, ncheck, p->d_steps + 1);
+                                                p->d_part, len, (int)slices, scratch, kseg, ncheck,
+                                                p->d_steps + 1, work_order_mult(p->G));
   p->launches += 1;
-  return cudaGetLastError();
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return launch_slice_sum(p, p->d_part, slices, len, gradC);
 }
 
 }  // namespace fga

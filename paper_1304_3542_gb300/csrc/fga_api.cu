@@ -4,6 +4,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <string>
 #include <vector>
 
@@ -143,12 +144,14 @@ const char* fga_last_error(fga_plan_t plan) {
 fga_status fga_destroy(fga_plan_t p) {
   if (!p) return FGA_OK;
   cudaStreamSynchronize(p->stream);
-  void* bufs[] = {p->d_coef, p->d_shots, p->d_in0, p->d_bbox, p->d_psi, p->d_g1,
+  void* bufs[] = {p->d_coef, p->d_medtab, p->d_shots, p->d_in0, p->d_bbox, p->d_psi, p->d_g1,
                   p->d_max2, p->d_blk, p->d_counts, p->d_blk_first, p->d_gshot, p->d_gq, p->d_gp,
                   p->d_gpsi, p->d_state, p->d_gcoef, p->d_tile_cnt, p->d_tile_off,
                   p->d_tile_list, p->d_seg_off, p->d_partial, p->d_out, p->d_status,
-                  p->d_steps, p->d_rx, p->d_rx_off, p->d_rx_list, p->d_traces,
-                  p->d_psi_f1, p->d_gpsi_f1, p->d_adj_scratch, p->d_grad, p->d_resid};
+                  p->d_steps, p->d_rx, p->d_rx_off, p->d_rx_perm, p->d_traces,
+                  p->d_run_geo, p->d_run_axis, p->d_run_off, p->d_resid_int,
+                  p->d_psi_f1, p->d_gpsi_f1, p->d_adj_scratch, p->d_grad, p->d_resid,
+                  p->d_part};
   for (void* b : bufs)
     if (b) cudaFree(b);
   for (double* e : p->E)
@@ -301,6 +304,9 @@ fga_status fga_plan(const fga_config* cfg, const double* velocity, void* stream,
     fga_destroy(p);
     return fail(nullptr, FGA_ERR_INVALID, "velocity must be finite and > 0 everywhere");
   }
+  PLAN_CUDA(cudaMalloc(&p->d_medtab, sizeof(double) * fga::medium_table_doubles(p->grid)));
+  p->grid.tab = p->d_medtab;
+  PLAN_CUDA(fga::launch_medium_table(p));
   PLAN_CUDA(cudaMemsetAsync(p->d_status, 0, sizeof(int), p->stream));
   p->E.assign((size_t)cfg->nshots * d, nullptr);
   for (int s = 0; s < cfg->nshots; ++s) {
@@ -442,10 +448,21 @@ fga_status fga_decompose(fga_plan_t p, const double* u0, const double* u1, int64
   return FGA_OK;
 }
 
+// Device capacity of the block-private trace slices of the next ray launch.
+static fga_status trace_capacity(fga_plan_s* p) {
+  if (p->nrx == 0 || p->G == 0) return FGA_OK;
+  CUDA_OR_FAIL(p, fga::ensure_ray_blocks(p));
+  const size_t need = (size_t)(fga::trace_slices(p) * p->nshots * p->rx.nrec * p->rx.nrx);
+  CUDA_OR_FAIL(p, grow(&p->d_part, &p->part_cap, need));
+  return FGA_OK;
+}
+
 fga_status fga_propagate(fga_plan_t p) {
   fga_status st = check_usable(p);
   if (st != FGA_OK) return st;
   if (p->stage < 1) return fail(p, FGA_ERR_STATE, "fga_propagate before fga_decompose");
+  st = trace_capacity(p);
+  if (st != FGA_OK) return st;
   CUDA_OR_FAIL(p, cudaEventRecord(p->ev[3], p->stream));
   CUDA_OR_FAIL(p, fga::launch_rays(p));
   CUDA_OR_FAIL(p, cudaEventRecord(p->ev[4], p->stream));
@@ -495,10 +512,13 @@ fga_status fga_run_graph(fga_plan_t p, double* u_dev) {
   }
   st = reconstruct_capacity(p);
   if (st != FGA_OK) return st;
-  int64_t key[6] = {p->G, (int64_t)p->g_cap, (int64_t)p->list_cap, (int64_t)p->partial_cap,
-                    (int64_t)(uintptr_t)u_dev, p->nrx};
+  st = trace_capacity(p);
+  if (st != FGA_OK) return st;
+  int64_t key[9] = {p->G, (int64_t)p->g_cap, (int64_t)p->list_cap, (int64_t)p->partial_cap,
+                    (int64_t)(uintptr_t)u_dev, p->nrx, p->seg, p->ray_blocks,
+                    (int64_t)(uintptr_t)p->d_part};
   bool same = p->graph_exec != nullptr;
-  for (int i = 0; i < 6; ++i) same = same && key[i] == p->graph_key[i];
+  for (int i = 0; i < 9; ++i) same = same && key[i] == p->graph_key[i];
   if (!same) {
     if (p->graph_exec) {
       cudaGraphExecDestroy(p->graph_exec);
@@ -524,11 +544,111 @@ fga_status fga_run_graph(fga_plan_t p, double* u_dev) {
       p->graph_exec = nullptr;
       return fail(p, FGA_ERR_CUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e), true);
     }
-    for (int i = 0; i < 6; ++i) p->graph_key[i] = key[i];
+    for (int i = 0; i < 9; ++i) p->graph_key[i] = key[i];
   }
   CUDA_OR_FAIL(p, cudaGraphLaunch(p->graph_exec, p->stream));
   p->launches += 12;
   p->stage = 2;
+  return FGA_OK;
+}
+
+// Milliseconds between two events recorded around `launch` on the plan's stream (the
+// best of `reps` runs after one untimed run).
+extern "C++" template <class F>
+cudaError_t time_best(fga_plan_s* p, int reps, F launch, float* best_ms) {
+  cudaError_t e = launch();
+  *best_ms = 3.0e38f;
+  for (int r = 0; r < reps && e == cudaSuccess; ++r) {
+    e = cudaEventRecord(p->ev[8], p->stream);
+    if (e == cudaSuccess) e = launch();
+    if (e == cudaSuccess) e = cudaEventRecord(p->ev[9], p->stream);
+    if (e == cudaSuccess) e = cudaEventSynchronize(p->ev[9]);
+    float ms = 0.0f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, p->ev[8], p->ev[9]);
+    if (e == cudaSuccess && ms < *best_ms) *best_ms = ms;
+  }
+  return e;
+}
+
+fga_status fga_autotune(fga_plan_t p, double* u_dev, int64_t* choice) {
+  fga_status st = check_usable(p);
+  if (st != FGA_OK) return st;
+  if (p->stage < 1) return fail(p, FGA_ERR_STATE, "fga_autotune before fga_decompose");
+  if (!u_dev || !is_device_ptr(u_dev))
+    return fail(p, FGA_ERR_INVALID, "fga_autotune writes to device memory only");
+  // 1. blocks per SM of the persistent ray kernel, timed on a short integration
+  const int max_sm = fga::ray_max_per_sm(p);
+  const int64_t probe = std::min<int64_t>(p->nsteps, 64);
+  int best_sm = max_sm;
+  float best = 3.0e38f;
+  if (p->G > 0 && probe > 0) {
+    for (int per_sm = max_sm; per_sm >= 1 && per_sm >= max_sm - 3; --per_sm) {
+      p->ray_per_sm = per_sm;
+      p->ray_blocks = 0;
+      float ms = 0.0f;
+      CUDA_OR_FAIL(p, time_best(p, 2, [&] { return fga::launch_rays_steps(p, probe, false); }, &ms));
+      if (ms < best * 0.98f) {  // prefer more resident blocks unless clearly slower
+        best = ms;
+        best_sm = per_sm;
+      }
+    }
+  }
+  p->ray_per_sm = best_sm;
+  p->ray_blocks = 0;
+  // 2. the full integration with the chosen launch shape
+  st = fga_propagate(p);
+  if (st != FGA_OK) return st;
+  // 3. split-K segment length of the gather, timed on the real Gaussian set
+  const bool tc = p->precision == FGA_MIXED_TF32X3;
+  const int d = p->grid.dim;
+  const int64_t base = tc ? 512 : (d == 1 ? 128 : 256);
+  int64_t best_seg = 0;
+  best = 3.0e38f;
+  for (int k = 0; k < 5; ++k) {
+    p->seg = base << k;
+    st = reconstruct_capacity(p);
+    if (st != FGA_OK) return st;
+    float ms = 0.0f;
+    CUDA_OR_FAIL(p, time_best(p, 2, [&] {
+      cudaError_t e = fga::launch_binning(p, nullptr);
+      if (e == cudaSuccess) e = fga::launch_binning_fill(p);
+      if (e == cudaSuccess)
+        e = tc ? fga::launch_reconstruct_tc(p, u_dev) : fga::launch_reconstruct(p, u_dev);
+      return e;
+    }, &ms));
+    if (ms < best) {
+      best = ms;
+      best_seg = p->seg;
+    }
+  }
+  p->seg = best_seg;
+  // 4. the field with the chosen segment length
+  st = fga_reconstruct(p, u_dev);
+  if (st != FGA_OK) return st;
+  if (choice) {
+    choice[0] = p->ray_per_sm;
+    choice[1] = p->seg;
+  }
+  return read_status(p);
+}
+
+fga_status fga_tuning(fga_plan_t p, int64_t* choice) {
+  if (!p || !choice) return fail(p, FGA_ERR_INVALID, "NULL plan or output");
+  choice[0] = p->ray_per_sm;
+  choice[1] = p->seg > 0 ? p->seg
+                         : (p->precision == FGA_MIXED_TF32X3 ? fga::segment_len_tc(p)
+                                                              : fga::segment_len(p));
+  return FGA_OK;
+}
+
+fga_status fga_set_tuning(fga_plan_t p, const int64_t* choice) {
+  fga_status st = check_usable(p);
+  if (st != FGA_OK) return st;
+  if (!choice || choice[0] < 0 || choice[0] > 64 || choice[1] < 0 || choice[1] > ((int64_t)1 << 20))
+    return fail(p, FGA_ERR_INVALID, "tuning values out of range (0 <= blocks/SM <= 64, 0 <= segment <= 2^20)");
+  p->ray_per_sm = (int)choice[0];
+  p->ray_blocks = 0;
+  p->seg = choice[1];
   return FGA_OK;
 }
 
@@ -701,12 +821,16 @@ fga_status fga_set_receivers(fga_plan_t p, int64_t nrx, const double* xr, int64_
     cudaGraphExecDestroy(p->graph_exec);
     p->graph_exec = nullptr;
   }
-  for (void* b : {(void*)p->d_rx, (void*)p->d_rx_off, (void*)p->d_rx_list, (void*)p->d_traces})
+  for (void* b : {(void*)p->d_rx, (void*)p->d_rx_off, (void*)p->d_rx_perm, (void*)p->d_traces,
+                  (void*)p->d_run_geo, (void*)p->d_run_axis, (void*)p->d_run_off})
     if (b) cudaFree(b);
   p->d_rx = nullptr;
   p->d_rx_off = nullptr;
-  p->d_rx_list = nullptr;
+  p->d_rx_perm = nullptr;
   p->d_traces = nullptr;
+  p->d_run_geo = nullptr;
+  p->d_run_axis = nullptr;
+  p->d_run_off = nullptr;
   p->nrx = 0;
   std::memset(&p->rx, 0, sizeof(p->rx));
   if (nrx == 0) return FGA_OK;
@@ -718,16 +842,80 @@ fga_status fga_set_receivers(fga_plan_t p, int64_t nrx, const double* xr, int64_
     if (gd.periodic[k]) return fail(p, FGA_ERR_INVALID, "receivers need open axes");
   std::vector<double> x((size_t)nrx * d);
   CUDA_OR_FAIL(p, cudaMemcpy(x.data(), xr, sizeof(double) * x.size(), cudaMemcpyDefault));
-  const int* nt = p->shots[0].ntile;
-  int64_t nbins = 1;
-  for (int k = 0; k < d; ++k) nbins *= nt[k];
-  std::vector<int64_t> bin((size_t)nrx), off((size_t)nbins + 1, 0);
-  for (int64_t r = 0; r < nrx; ++r) {
-    int64_t b = 0;
+  for (int64_t r = 0; r < nrx; ++r)
     for (int k = 0; k < d; ++k) {
       double v = x[(size_t)r * d + k];
       if (!std::isfinite(v) || v < gd.o[k] || v > gd.o[k] + (double)(gd.n[k] - 1) * gd.h[k])
         return fail(p, FGA_ERR_INVALID, "receivers must lie inside the grid");
+    }
+  // runs: receivers sharing the coordinate across an axis, equally spaced along it
+  std::vector<double> run_geo;
+  std::vector<int32_t> run_axis, run_rx;
+  std::vector<int64_t> run_off(1, 0);
+  std::vector<char> in_run((size_t)nrx, 0);
+  const int64_t kMinRun = 4;
+  for (int a = 0; a < d; ++a) {
+    std::map<uint64_t, std::vector<int32_t>> groups;  // by the exact coordinate across axis a
+    for (int64_t r = 0; r < nrx; ++r) {
+      if (in_run[r]) continue;
+      uint64_t key = 0;
+      if (d == 2) std::memcpy(&key, &x[(size_t)r * d + (1 - a)], sizeof(double));
+      groups[key].push_back((int32_t)r);
+    }
+    for (auto& kv : groups) {
+      std::vector<int32_t>& g = kv.second;
+      if ((int64_t)g.size() < kMinRun) continue;
+      std::stable_sort(g.begin(), g.end(), [&](int32_t u, int32_t v) {
+        return x[(size_t)u * d + a] < x[(size_t)v * d + a];
+      });
+      size_t i = 0;
+      while (i + 1 < g.size()) {
+        const double x0 = x[(size_t)g[i] * d + a];
+        const double dl = x[(size_t)g[i + 1] * d + a] - x0;
+        size_t j = i + 1;
+        if (dl > 0.0)
+          while (j + 1 < g.size() &&
+                 std::fabs((x[(size_t)g[j + 1] * d + a] - x[(size_t)g[j] * d + a]) - dl) <= 1e-9 * dl)
+            ++j;
+        bool ok = dl > 0.0 && (int64_t)(j - i + 1) >= kMinRun;
+        // spacing from the end points; every position of the run x0 + m * step must be
+        // within a few ulps of the given coordinate (the kernels use the former)
+        const double step = ok ? (x[(size_t)g[j] * d + a] - x0) / (double)(j - i) : 0.0;
+        if (ok) {
+          const double tol = 8.0 * 2.220446049250313e-16 *
+                             std::max(std::fabs(x0), std::fabs(x[(size_t)g[j] * d + a]));
+          for (size_t m = i; m <= j && ok; ++m)
+            ok = std::fabs(std::fma((double)(m - i), step, x0) - x[(size_t)g[m] * d + a]) <= tol;
+        }
+        if (ok) {
+          run_geo.push_back(x0);
+          run_geo.push_back(step);
+          run_geo.push_back(d == 2 ? x[(size_t)g[i] * d + (1 - a)] : 0.0);
+          run_axis.push_back(a);
+          for (size_t m = i; m <= j; ++m) {
+            run_rx.push_back(g[m]);
+            in_run[g[m]] = 1;
+          }
+          run_off.push_back((int64_t)run_rx.size());
+          i = j + 1;
+        } else {
+          ++i;
+        }
+      }
+    }
+  }
+  const int64_t nruns = (int64_t)run_axis.size();
+  const int64_t nin_runs = (int64_t)run_rx.size();
+  // the other receivers, grouped by output tile, after the runs in the internal order
+  const int* nt = p->shots[0].ntile;
+  int64_t nbins = 1;
+  for (int k = 0; k < d; ++k) nbins *= nt[k];
+  std::vector<int64_t> bin((size_t)nrx, -1), off((size_t)nbins + 1, 0);
+  for (int64_t r = 0; r < nrx; ++r) {
+    if (in_run[r]) continue;
+    int64_t b = 0;
+    for (int k = 0; k < d; ++k) {
+      double v = x[(size_t)r * d + k];
       int64_t i = (int64_t)std::floor((v - gd.o[k]) * gd.inv_h[k]);
       i = std::min<int64_t>(std::max<int64_t>(i, 0), gd.n[k] - 1);
       b = b * nt[k] + i / gd.tile[k];
@@ -735,25 +923,45 @@ fga_status fga_set_receivers(fga_plan_t p, int64_t nrx, const double* xr, int64_
     bin[r] = b;
     off[b + 1] += 1;
   }
+  off[0] = nin_runs;
   for (int64_t b = 0; b < nbins; ++b) off[b + 1] += off[b];
-  std::vector<int32_t> list((size_t)nrx);
+  std::vector<int32_t> perm(run_rx);  // internal index -> caller's index
+  perm.resize((size_t)nrx);
   std::vector<int64_t> fill(off.begin(), off.end() - 1);
-  for (int64_t r = 0; r < nrx; ++r) list[fill[bin[r]]++] = (int32_t)r;
+  for (int64_t r = 0; r < nrx; ++r)
+    if (bin[r] >= 0) perm[fill[bin[r]]++] = (int32_t)r;
+  std::vector<double> xi((size_t)nrx * d);
+  for (int64_t i = 0; i < nrx; ++i)
+    for (int k = 0; k < d; ++k) xi[(size_t)i * d + k] = x[(size_t)perm[i] * d + k];
   const int64_t nrec = p->nsteps / record_every + 1;
-  CUDA_OR_FAIL(p, cudaMalloc(&p->d_rx, sizeof(double) * x.size()));
+  CUDA_OR_FAIL(p, cudaMalloc(&p->d_rx, sizeof(double) * xi.size()));
   CUDA_OR_FAIL(p, cudaMalloc(&p->d_rx_off, sizeof(int64_t) * off.size()));
-  CUDA_OR_FAIL(p, cudaMalloc(&p->d_rx_list, sizeof(int32_t) * list.size()));
+  CUDA_OR_FAIL(p, cudaMalloc(&p->d_rx_perm, sizeof(int32_t) * perm.size()));
   CUDA_OR_FAIL(p, cudaMalloc(&p->d_traces, sizeof(double) * p->nshots * nrec * nrx));
-  CUDA_OR_FAIL(p, cudaMemcpy(p->d_rx, x.data(), sizeof(double) * x.size(), cudaMemcpyHostToDevice));
+  CUDA_OR_FAIL(p, cudaMemcpy(p->d_rx, xi.data(), sizeof(double) * xi.size(), cudaMemcpyHostToDevice));
   CUDA_OR_FAIL(p, cudaMemcpy(p->d_rx_off, off.data(), sizeof(int64_t) * off.size(), cudaMemcpyHostToDevice));
-  CUDA_OR_FAIL(p, cudaMemcpy(p->d_rx_list, list.data(), sizeof(int32_t) * list.size(), cudaMemcpyHostToDevice));
+  CUDA_OR_FAIL(p, cudaMemcpy(p->d_rx_perm, perm.data(), sizeof(int32_t) * perm.size(), cudaMemcpyHostToDevice));
+  if (nruns > 0) {
+    CUDA_OR_FAIL(p, cudaMalloc(&p->d_run_geo, sizeof(double) * run_geo.size()));
+    CUDA_OR_FAIL(p, cudaMalloc(&p->d_run_axis, sizeof(int32_t) * run_axis.size()));
+    CUDA_OR_FAIL(p, cudaMalloc(&p->d_run_off, sizeof(int64_t) * run_off.size()));
+    CUDA_OR_FAIL(p, cudaMemcpy(p->d_run_geo, run_geo.data(), sizeof(double) * run_geo.size(),
+                               cudaMemcpyHostToDevice));
+    CUDA_OR_FAIL(p, cudaMemcpy(p->d_run_axis, run_axis.data(), sizeof(int32_t) * run_axis.size(),
+                               cudaMemcpyHostToDevice));
+    CUDA_OR_FAIL(p, cudaMemcpy(p->d_run_off, run_off.data(), sizeof(int64_t) * run_off.size(),
+                               cudaMemcpyHostToDevice));
+  }
   p->nrx = nrx;
   p->rx.nrx = nrx;
   p->rx.nrec = nrec;
   p->rx.every = record_every;
   p->rx.x = p->d_rx;
   p->rx.off = p->d_rx_off;
-  p->rx.list = p->d_rx_list;
+  p->rx.nruns = nruns;
+  p->rx.run_geo = p->d_run_geo;
+  p->rx.run_axis = p->d_run_axis;
+  p->rx.run_off = p->d_run_off;
   for (int k = 0; k < fga::kMaxDim; ++k) p->rx.ntile[k] = k < d ? nt[k] : 1;
   if (p->stage >= 2) p->stage = 1;  // traces need a new propagation
   return FGA_OK;
@@ -785,6 +993,11 @@ fga_status fga_grad(fga_plan_t p, const double* residual, double* grad) {
                                     p->stream));
     d_res = p->d_resid;
   }
+  // to the internal receiver order of the kernels
+  CUDA_OR_FAIL(p, grow(&p->d_resid_int, &p->resid_int_cap, nres));
+  CUDA_OR_FAIL(p, fga::launch_gather_rows(p, d_res, p->d_rx_perm, (int64_t)p->nshots * p->rx.nrec,
+                                          p->rx.nrx, p->d_resid_int));
+  d_res = p->d_resid_int;
   const int64_t kseg = std::max<int64_t>(1, (int64_t)std::ceil(std::sqrt((double)std::max<int64_t>(p->nsteps, 1))));
   const int64_t ncheck = p->nsteps / kseg + 2;
   const int64_t nthr = fga::adjoint_threads(p);
@@ -797,7 +1010,8 @@ fga_status fga_grad(fga_plan_t p, const double* residual, double* grad) {
     if (!p->d_grad) CUDA_OR_FAIL(p, cudaMalloc(&p->d_grad, sizeof(double) * gd.npts));
     dst = p->d_grad;
   }
-  CUDA_OR_FAIL(p, cudaMemsetAsync(dst, 0, sizeof(double) * gd.npts, p->stream));
+  CUDA_OR_FAIL(p, grow(&p->d_part, &p->part_cap,
+                       (size_t)(fga::adjoint_slices(p, nthr) * gd.npts)));
   CUDA_OR_FAIL(p, fga::launch_adjoint(p, d_res, dst, p->d_adj_scratch, nthr, kseg, ncheck));
   if (host_out)
     CUDA_OR_FAIL(p, cudaMemcpyAsync(grad, dst, sizeof(double) * gd.npts, cudaMemcpyDeviceToHost,

@@ -11,12 +11,14 @@
 // contraction along the first axis is a dense complex GEMM per q (stage 2).
 // Both stages are FP64 tiled GEMMs; the stage that yields psi fuses the branch
 // split psi+ = 1/2 (psi_0 + i eps psi_1/(c(q)|p|)), the removal of the left-out
-// p values and the running max of |psi+|^2 per shot.
+// p values and the running max of |psi+|^2 per shot. In the mixed precision the
+// per-q GEMM of stage 2 (2D) runs on the tensor cores instead (k_fbi_stage2_tc).
 #include <algorithm>
 #include <climits>
 
 #include "fga_internal.cuh"
 #include "fga_medium.cuh"
+#include "fga_tc.cuh"
 
 namespace fga {
 
@@ -349,6 +351,187 @@ __global__ void __launch_bounds__(NT) k_fbi_stage2(GridDev gd, const ShotDev* __
   if ((t & 31) == 0) atomic_max_nonneg(max2 + s, mymax);
 }
 
+// ---------------------------------------------------------------------------
+// Stage 2 on the tensor cores (mixed precision, 2D). For one q and one 128 x 128 tile
+// of (p_x, p_z), the complex GEMM psi_f[px][pz] = sum_jx E_x[px][jx] G1_f[jx][pz] is
+// written as real GEMMs over K = 2 jx:
+//   Re psi_f = A_re B_f^T,  Im psi_f = A_im B_f^T,
+//   A_re[px][2j] = Re E, A_re[px][2j+1] = -Im E,  A_im[px][2j] = Im E, A_im[px][2j+1] = Re E,
+//   B_f[pz][2j] = Re G1_f, B_f[pz][2j+1] = Im G1_f,
+// with every operand split into a TF32 head and an FP32 tail and the three products
+// hi*hi + hi*lo + lo*hi accumulated in FP32 in tensor memory (four accumulators of 128
+// columns: field 0 re/im, field 1 re/im). The epilogue forms psi+ in FP64 as the FP64
+// stage does. Operands are K-major in shared memory without swizzle (8-row x 16-byte
+// core matrices), one CTA per SM (128 KiB of operands, all 512 TMEM columns).
+constexpr int FT = 128;        // tile edge in p_x (GEMM M) and p_z (GEMM N)
+constexpr int FJ = 16;         // complex jx per chunk -> K = 32
+constexpr int FKC = 2 * FJ;
+constexpr int FKB = FKC / 4;   // core matrices along K
+constexpr int FNT = 128;
+constexpr uint32_t kFbiLBO = 128, kFbiSBO = FKB * 128;
+constexpr size_t kFbiOperand = (size_t)FT * FKC * sizeof(float);  // 16 KiB
+constexpr size_t kFbiSmem = 8 * kFbiOperand + 64;
+constexpr uint32_t kFbiTries = 1u << 22;
+
+__device__ __forceinline__ int fbi_core_offset(int row, int k) {
+  return (((row >> 3) * FKB + (k >> 2)) * 8 + (row & 7)) * 4 + (k & 3);
+}
+
+__device__ __forceinline__ void split_store(float* hi, float* lo, int o, double v) {
+  const float f = (float)v;
+  const float h = __uint_as_float(__float_as_uint(f) & 0xFFFFE000u);
+  hi[o] = h;
+  lo[o] = (float)(v - (double)h);
+}
+
+__global__ void __launch_bounds__(FNT) k_fbi_stage2_tc(GridDev gd, const ShotDev* __restrict__ shots,
+                                                      const double* __restrict__ C,
+                                                      const double2* __restrict__ g1,
+                                                      double2* __restrict__ psi,
+                                                      double2* __restrict__ psi_f1,
+                                                      unsigned long long* __restrict__ max2,
+                                                      int* status) {
+  const int s = blockIdx.z;
+  const ShotDev& sh = shots[s];
+  const int64_t qtot = sh.qn[0] * sh.qn[1];
+  const int64_t ql = blockIdx.y;
+  const int64_t nbx = sh.nb[0], nbz = sh.nb[1];
+  const int64_t tiles_z = (nbz + FT - 1) / FT;
+  const int64_t m0 = (blockIdx.x / tiles_z) * FT, n0 = (blockIdx.x % tiles_z) * FT;
+  if (ql >= qtot || m0 >= nbx) return;  // uniform over the CTA
+  extern __shared__ __align__(1024) unsigned char smem[];
+  float* op = reinterpret_cast<float*>(smem);
+  float *Arh = op, *Arl = op + FT * FKC, *Aih = op + 2 * FT * FKC, *Ail = op + 3 * FT * FKC;
+  float *B0h = op + 4 * FT * FKC, *B0l = op + 5 * FT * FKC, *B1h = op + 6 * FT * FKC,
+        *B1l = op + 7 * FT * FKC;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + 8 * kFbiOperand);
+  uint32_t* tbase = reinterpret_cast<uint32_t*>(smem + 8 * kFbiOperand + 16);
+  __shared__ double cq_s;
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int64_t mxl = ql / sh.qn[1], mzl = ql - mxl * sh.qn[1];
+  if (tid == 0) {
+    double q[2] = {gd.o[0] + (double)(sh.s[0] * (sh.qlo[0] + mxl)) * gd.h[0],
+                   gd.o[1] + (double)(sh.s[1] * (sh.qlo[1] + mzl)) * gd.h[1]};
+    cq_s = medium_value<2>(gd, C, q);
+    tc::mbar_init(bar, 1);
+    tc::fence_mbar_init();
+  }
+  if (warp == 0) {
+    tc::tmem_alloc(tbase, 4 * FT);
+    tc::tmem_relinquish();
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = *tbase;
+  const uint32_t idesc = tc::idesc_f32acc(tc::kFmtTF32, FT, FT);
+  const int64_t M1 = sh.nrows * sh.qn[1];
+  const double2* G0 = g1 + sh.g1_off;
+  const double2* G1p = G0 + M1 * nbz;
+  const double2* Ex = sh.E[0];
+  const int64_t row0 = sh.s[0] * mxl;
+  uint32_t chunks = 0;
+  bool ok = true;
+  for (int64_t k0 = 0; k0 < nbx; k0 += FJ) {
+    if (chunks > 0) ok &= tc::mbar_wait_bounded(bar, (chunks - 1) & 1u, kFbiTries);
+    // A: E_x rows m0 .. m0+127, columns k0 .. k0+15 (16 threads per row, coalesced)
+    for (int e = tid; e < FT * FJ; e += FNT) {
+      const int r = e / FJ, j = e % FJ;
+      const int64_t m = m0 + r, k = k0 + j;
+      const double2 v = (m < nbx && k < nbx) ? __ldg(Ex + m * nbx + k) : make_double2(0.0, 0.0);
+      const int o = fbi_core_offset(r, 2 * j);
+      split_store(Arh, Arl, o, v.x);
+      split_store(Arh, Arl, o + 1, -v.y);
+      split_store(Aih, Ail, o, v.y);
+      split_store(Aih, Ail, o + 1, v.x);
+    }
+    // B: stage-1 rows row0 + k0 .. + 15 of this q column, p_z n0 .. n0+127 (coalesced)
+    for (int e = tid; e < FT * FJ; e += FNT) {
+      const int j = e / FT, r = e % FT;
+      const int64_t k = k0 + j, n = n0 + r;
+      double2 v0 = make_double2(0.0, 0.0), v1 = v0;
+      if (k < nbx && n < nbz) {
+        const int64_t off = ((row0 + k) * sh.qn[1] + mzl) * nbz + n;
+        v0 = __ldg(G0 + off);
+        v1 = __ldg(G1p + off);
+      }
+      const int o = fbi_core_offset(r, 2 * j);
+      split_store(B0h, B0l, o, v0.x);
+      split_store(B0h, B0l, o + 1, v0.y);
+      split_store(B1h, B1l, o, v1.x);
+      split_store(B1h, B1l, o + 1, v1.y);
+    }
+    tc::fence_proxy_async_smem();
+    __syncthreads();
+    if (tid == 0) {
+      tc::fence_after_sync();
+      const uint32_t arh = tc::smem_u32(Arh), arl = tc::smem_u32(Arl);
+      const uint32_t aih = tc::smem_u32(Aih), ail = tc::smem_u32(Ail);
+      const uint32_t b0h = tc::smem_u32(B0h), b0l = tc::smem_u32(B0l);
+      const uint32_t b1h = tc::smem_u32(B1h), b1l = tc::smem_u32(B1l);
+#pragma unroll
+      for (int ks = 0; ks < FKC / 8; ++ks) {
+        const uint32_t st = ks * 256;
+        const uint32_t acc = (chunks > 0 || ks > 0) ? 1u : 0u;
+        const uint32_t ah[2] = {arh, aih}, al[2] = {arl, ail};
+        const uint32_t bh[2] = {b0h, b1h}, bl[2] = {b0l, b1l};
+#pragma unroll
+        for (int f = 0; f < 2; ++f)
+#pragma unroll
+          for (int c = 0; c < 2; ++c) {
+            const uint32_t d = tmem + (uint32_t)((2 * f + c) * FT);
+            tc::mma_tf32(d, tc::smem_desc(ah[c] + st, kFbiLBO, kFbiSBO),
+                         tc::smem_desc(bh[f] + st, kFbiLBO, kFbiSBO), idesc, acc);
+            tc::mma_tf32(d, tc::smem_desc(ah[c] + st, kFbiLBO, kFbiSBO),
+                         tc::smem_desc(bl[f] + st, kFbiLBO, kFbiSBO), idesc, 1u);
+            tc::mma_tf32(d, tc::smem_desc(al[c] + st, kFbiLBO, kFbiSBO),
+                         tc::smem_desc(bh[f] + st, kFbiLBO, kFbiSBO), idesc, 1u);
+          }
+      }
+      tc::mma_commit(bar);
+    }
+    ++chunks;
+  }
+  if (chunks > 0) ok &= tc::mbar_wait_bounded(bar, (chunks - 1) & 1u, kFbiTries);
+  if (!ok) {
+    atomicOr(status, kStatusTimeout);
+    if (chunks > 0) tc::mbar_wait_bounded(bar, (chunks - 1) & 1u, kFbiTries);
+  }
+  tc::fence_after_sync();
+  // epilogue: thread = p_x row (TMEM lane 32 w + lane), 32 p_z columns at a time
+  const double hv = gd.h[0] * gd.h[1];
+  const int64_t m = m0 + 32 * warp + (tid & 31);
+  double mymax = 0.0;
+  float a0r[32], a0i[32], a1r[32], a1i[32];
+#pragma unroll 1
+  for (int cb = 0; cb < FT; cb += 32) {
+    const uint32_t lane_base = tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)cb;
+    tc::tmem_ld_32x32b_x32(lane_base, a0r);
+    tc::tmem_ld_32x32b_x32(lane_base + FT, a0i);
+    tc::tmem_ld_32x32b_x32(lane_base + 2 * FT, a1r);
+    tc::tmem_ld_32x32b_x32(lane_base + 3 * FT, a1i);
+    if (!ok || m >= nbx) continue;
+#pragma unroll
+    for (int i = 0; i < 32; ++i) {
+      const int64_t n = n0 + cb + i;
+      if (n >= nbz) continue;
+      const double2 p0 = make_double2(hv * (double)a0r[i], hv * (double)a0i[i]);
+      const double2 p1 = make_double2(hv * (double)a1r[i], hv * (double)a1i[i]);
+      double2 o, tt;
+      const int64_t jp = m * nbz + n;
+      const double a2 = psi_plus<2>(sh, jp, p0, p1, cq_s, o, tt);
+      psi[sh.psi_off + ql * sh.np + jp] = o;
+      psi_f1[sh.psi_off + ql * sh.np + jp] = tt;
+      mymax = fmax(mymax, a2);
+    }
+  }
+  for (int off = 16; off > 0; off >>= 1) mymax = fmax(mymax, __shfl_xor_sync(0xffffffffu, mymax, off));
+  if ((tid & 31) == 0) atomic_max_nonneg(max2 + s, mymax);
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) tc::tmem_dealloc(tmem, 4 * FT);
+}
+
 }  // namespace
 
 cudaError_t launch_support_bbox(fga_plan_s* p, const double* u0, const double* u1) {
@@ -388,10 +571,27 @@ cudaError_t launch_fbi(fga_plan_s* p, const double* u0, const double* u1) {
   k_fbi_stage1<2><<<g1grid, NT, 0, p->stream>>>(p->grid, p->d_shots, u0, u1, p->d_coef, p->d_g1,
                                                 p->d_psi, p->d_psi_f1, p->d_max2);
   if (maxQ > 65535) return cudaErrorInvalidConfiguration;
+  p->launches += 2;
+  if (p->precision == FGA_MIXED_TF32X3) {
+    static bool attr_set = false;
+    if (!attr_set) {
+      cudaError_t e = cudaFuncSetAttribute(k_fbi_stage2_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)kFbiSmem);
+      if (e != cudaSuccess) return e;
+      attr_set = true;
+    }
+    int64_t tiles = 0;
+    for (const auto& sh : p->shots)
+      tiles = std::max<int64_t>(tiles, ((sh.nb[0] + FT - 1) / FT) * ((sh.nb[1] + FT - 1) / FT));
+    dim3 tgrid((unsigned)tiles, (unsigned)maxQ, p->nshots);
+    k_fbi_stage2_tc<<<tgrid, FNT, kFbiSmem, p->stream>>>(p->grid, p->d_shots, p->d_coef, p->d_g1,
+                                                        p->d_psi, p->d_psi_f1, p->d_max2,
+                                                        p->d_status);
+    return cudaGetLastError();
+  }
   dim3 g2grid((unsigned)maxTiles, (unsigned)maxQ, p->nshots);
   k_fbi_stage2<<<g2grid, NT, 0, p->stream>>>(p->grid, p->d_shots, p->d_coef, p->d_g1, p->d_psi,
                                              p->d_psi_f1, p->d_max2);
-  p->launches += 2;
   return cudaGetLastError();
 }
 

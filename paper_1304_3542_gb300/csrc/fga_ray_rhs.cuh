@@ -15,12 +15,21 @@ struct Layout {
                        BI = 2 * D + 3 * D * D, aR = 2 * D + 4 * D * D, aI = aR + 1, S = aR + 2;
 };
 
+// Order in which the persistent ray kernels take Gaussians: work item w -> Gaussian
+// (w * mult) mod G, mult coprime with G and near G/golden ratio. Consecutive Gaussians
+// share q (and so, early on, position and receivers); spreading them over the list keeps
+// the threads running at the same time from adding into the same few trace or
+// gradient entries at once.
+__device__ __forceinline__ int64_t work_order(unsigned long long w, int64_t G, unsigned long long mult) {
+  return (int64_t)((w * mult) % (unsigned long long)G);
+}
+
+// The medium comes from the per-cell polynomial table gd.tab.
 template <int D>
-__device__ __forceinline__ bool rhs(const GridDev& gd, const double* __restrict__ C, const double* y,
-                                    double* k) {
+__device__ __forceinline__ bool rhs(const GridDev& gd, const double* y, double* k) {
   using Lo = Layout<D>;
   Med m;
-  medium_eval<D>(gd, C, y + Lo::Q, m);
+  medium_eval_tab<D>(gd, y + Lo::Q, m);
   double pn2 = 0;
 #pragma unroll
   for (int i = 0; i < D; ++i) pn2 = fma(y[Lo::P + i], y[Lo::P + i], pn2);
@@ -152,11 +161,63 @@ __device__ __forceinline__ bool ray_store(const ShotDev& sh, int64_t g, const do
   return fin;
 }
 
-// Calls fn(r, d[]) for every receiver r inside the window |x_r,k - Q_k| <= cut of the
-// Gaussian with centre Q (open axes), d = x_r - Q.
+// Calls fn(r, d[], X) for every receiver r (internal index) inside the window
+// |x_r,k - Q_k| <= cut of the Gaussian with centre Q and momentum P (open axes), with
+// d = x_r - Q and X = exp(i P.d/eps - |d|^2/(2 eps)) (complex, as double2). Receivers on
+// runs get X by the recurrence X_{k+1} = X_k R_k, R_{k+1} = R_k exp(-dl^2/eps) along the
+// run (dl the spacing: two exponentials and two sine/cosine pairs per run instead of one
+// pair per receiver) and their positions from the run's geometry (within a few ulps of
+// the given coordinates, checked when the runs are formed); the other receivers are
+// evaluated one by one from their coordinates.
 template <int D, typename Fn>
-__device__ __forceinline__ void for_receivers_in_window(const GridDev& gd, const RxDev& rx,
-                                                        const double* Q, double cut, Fn fn) {
+__device__ __forceinline__ void for_receivers_X(const GridDev& gd, const RxDev& rx, const double* Q,
+                                                const double* P, double cut, double inv_eps, Fn fn) {
+  for (int64_t j = 0; j < rx.nruns; ++j) {
+    const int a = rx.run_axis[j];
+    const double x0 = rx.run_geo[3 * j], dl = rx.run_geo[3 * j + 1];
+    double fr = 1.0, fi = 0.0;  // factor of the coordinate across the run
+    double e = 0.0;
+    if constexpr (D == 2) {
+      e = rx.run_geo[3 * j + 2] - Q[1 - a];
+      if (fabs(e) > cut) continue;
+      double s, c;
+      sincos(P[1 - a] * e * inv_eps, &s, &c);
+      const double g = exp(-0.5 * e * e * inv_eps);
+      fr = g * c;
+      fi = g * s;
+    }
+    const int64_t r0 = rx.run_off[j], n = rx.run_off[j + 1] - r0;
+    // candidates, one beyond each end of the window
+    int64_t k0 = (int64_t)ceil((Q[a] - cut - x0) / dl) - 1;
+    int64_t k1 = (int64_t)floor((Q[a] + cut - x0) / dl) + 1;
+    k0 = k0 < 0 ? 0 : k0;
+    k1 = k1 > n - 1 ? n - 1 : k1;
+    if (k0 > k1) continue;
+    double u = fma((double)k0, dl, x0) - Q[a];
+    double s, c;
+    sincos(P[a] * u * inv_eps, &s, &c);
+    double g = exp(-0.5 * u * u * inv_eps);
+    double xr = g * c * fr - g * s * fi, xi = g * c * fi + g * s * fr;
+    sincos(P[a] * dl * inv_eps, &s, &c);
+    g = exp(-(u * dl + 0.5 * dl * dl) * inv_eps);
+    double rr = g * c, ri = g * s;
+    const double rho = exp(-dl * dl * inv_eps);
+    for (int64_t k = k0; k <= k1; ++k) {
+      u = fma((double)k, dl, x0) - Q[a];
+      if (fabs(u) <= cut) {
+        double d[D];
+        d[a] = u;
+        if constexpr (D == 2) d[1 - a] = e;
+        fn(r0 + k, d, make_double2(xr, xi));
+      }
+      const double nr = xr * rr - xi * ri, ni = xr * ri + xi * rr;
+      xr = nr;
+      xi = ni;
+      rr *= rho;
+      ri *= rho;
+    }
+  }
+  // the other receivers, by output tile
   int64_t tlo[D], thi[D];
 #pragma unroll
   for (int k = 0; k < D; ++k) {
@@ -168,22 +229,30 @@ __device__ __forceinline__ void for_receivers_in_window(const GridDev& gd, const
     tlo[k] = lo / gd.tile[k];
     thi[k] = hi / gd.tile[k];
   }
+  auto direct = [&](int64_t r) {
+    double d[D], ph = 0.0, r2 = 0.0;
+    bool in = true;
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      d[k] = rx.x[r * D + k] - Q[k];
+      in = in && fabs(d[k]) <= cut;
+      ph = fma(P[k], d[k], ph);
+      r2 = fma(d[k], d[k], r2);
+    }
+    if (!in) return;
+    const double g = exp(-0.5 * r2 * inv_eps);
+    double s, c;
+    sincos(ph * inv_eps, &s, &c);
+    fn(r, d, make_double2(g * c, g * s));
+  };
   if constexpr (D == 1) {
     for (int64_t t0 = tlo[0]; t0 <= thi[0]; ++t0)
-      for (int64_t e = rx.off[t0]; e < rx.off[t0 + 1]; ++e) {
-        int32_t r = rx.list[e];
-        double d[1] = {rx.x[r] - Q[0]};
-        if (fabs(d[0]) <= cut) fn(r, d);
-      }
+      for (int64_t r = rx.off[t0]; r < rx.off[t0 + 1]; ++r) direct(r);
   } else {
     for (int64_t t0 = tlo[0]; t0 <= thi[0]; ++t0)
       for (int64_t t1 = tlo[1]; t1 <= thi[1]; ++t1) {
-        int64_t bin = t0 * rx.ntile[1] + t1;
-        for (int64_t e = rx.off[bin]; e < rx.off[bin + 1]; ++e) {
-          int32_t r = rx.list[e];
-          double d[2] = {rx.x[2 * r] - Q[0], rx.x[2 * r + 1] - Q[1]};
-          if (fabs(d[0]) <= cut && fabs(d[1]) <= cut) fn(r, d);
-        }
+        const int64_t bin = t0 * rx.ntile[1] + t1;
+        for (int64_t r = rx.off[bin]; r < rx.off[bin + 1]; ++r) direct(r);
       }
   }
 }
@@ -203,18 +272,10 @@ __device__ __forceinline__ void record_traces(const GridDev& gd, const ShotDev& 
   sincos(y[Lo::S] * sh.inv_eps, &sn, &cs);
   const double er = pr * cs - pi * sn, ei = pr * sn + pi * cs;
   double* tr = traces + ((int64_t)s * rx.nrec + m) * rx.nrx;
-  for_receivers_in_window<D>(gd, rx, y + Lo::Q, cut, [&](int32_t r, const double* d) {
-    double ph = 0.0, r2 = 0.0;
-#pragma unroll
-    for (int k = 0; k < D; ++k) {
-      ph = fma(y[Lo::P + k], d[k], ph);
-      r2 = fma(d[k], d[k], r2);
-    }
-    double gs = exp(-0.5 * r2 * sh.inv_eps);
-    double s2, c2;
-    sincos(ph * sh.inv_eps, &s2, &c2);
-    atomicAdd(tr + r, gs * (er * c2 - ei * s2));
-  });
+  for_receivers_X<D>(gd, rx, y + Lo::Q, y + Lo::P, cut, sh.inv_eps,
+                     [&](int64_t r, const double*, double2 X) {
+                       atomicAdd(tr + r, er * X.x - ei * X.y);
+                     });
 }
 
 }  // namespace fga

@@ -378,25 +378,25 @@ __device__ __forceinline__ void rk4_step(const GridDev& gd, const double* __rest
   constexpr int NF = Lo::NF;
   double acc[NF], tmp[NF], k[NF];
   const double h2 = 0.5 * dt, h6 = dt / 6.0, h3 = dt / 3.0;
-  rhs<D>(gd, C, y, k);
+  rhs<D>(gd, y, k);
 #pragma unroll
   for (int i = 0; i < NF; ++i) {
     acc[i] = fma(h6, k[i], y[i]);
     tmp[i] = fma(h2, k[i], y[i]);
   }
-  rhs<D>(gd, C, tmp, k);
+  rhs<D>(gd, tmp, k);
 #pragma unroll
   for (int i = 0; i < NF; ++i) {
     acc[i] = fma(h3, k[i], acc[i]);
     tmp[i] = fma(h2, k[i], y[i]);
   }
-  rhs<D>(gd, C, tmp, k);
+  rhs<D>(gd, tmp, k);
 #pragma unroll
   for (int i = 0; i < NF; ++i) {
     acc[i] = fma(h3, k[i], acc[i]);
     tmp[i] = fma(dt, k[i], y[i]);
   }
-  rhs<D>(gd, C, tmp, k);
+  rhs<D>(gd, tmp, k);
 #pragma unroll
   for (int i = 0; i < NF; ++i) y[i] = fma(h6, k[i], acc[i]);
 #pragma unroll
@@ -417,13 +417,13 @@ __device__ void rk4_step_adjoint(const GridDev& gd, const double* __restrict__ C
   constexpr int NF = Lo::NF;
   double k[NF], z2[NF], z3[NF], z4[NF];
   const double h2 = 0.5 * dt;
-  rhs<D>(gd, C, y, k);
+  rhs<D>(gd, y, k);
 #pragma unroll
   for (int i = 0; i < NF; ++i) z2[i] = fma(h2, k[i], y[i]);
-  rhs<D>(gd, C, z2, k);
+  rhs<D>(gd, z2, k);
 #pragma unroll
   for (int i = 0; i < NF; ++i) z3[i] = fma(h2, k[i], y[i]);
-  rhs<D>(gd, C, z3, k);
+  rhs<D>(gd, z3, k);
 #pragma unroll
   for (int i = 0; i < NF; ++i) z4[i] = fma(dt, k[i], y[i]);
   double kb[NF], zb[NF], k1b[NF], k2b[NF], k3b[NF];

@@ -46,10 +46,14 @@ __global__ void __launch_bounds__(128) k_rays(GridDev gd, const ShotDev* __restr
                                               double2* __restrict__ coef, int* status,
                                               unsigned long long* steps_done,
                                               unsigned long long* next, RxDev rx,
-                                              double* __restrict__ traces) {
+                                              double* __restrict__ trace_part, int64_t slice_len,
+                                              int slices, unsigned long long mult) {
   using Lo = Layout<D>;
   constexpr int NF = Lo::NF;
-  int64_t g = (int64_t)atomicAdd(next, 1ull);
+  // this block's private slice of the trace sums (no other block adds into it)
+  double* traces = rx.every > 0 ? trace_part + (int64_t)(blockIdx.x % slices) * slice_len : nullptr;
+  unsigned long long w = atomicAdd(next, 1ull);
+  int64_t g = w < (unsigned long long)G ? work_order(w, G, mult) : G;
   unsigned long long my_steps = 0;
   bool ok = true;
   if (g < G) {
@@ -67,8 +71,17 @@ __global__ void __launch_bounds__(128) k_rays(GridDev gd, const ShotDev* __restr
     }
     const double h2 = 0.5 * dt, h6 = dt / 6.0, h3 = dt / 3.0;
     int64_t step = 0;
+    // With receivers, every ray's step 0 falls on a loop trip that is a multiple of the
+    // record interval, so all lanes of a warp record on the same trips (a lane that
+    // picks up a new ray idles until then, at most every - 1 trips).
+    int64_t trip = 0, wait = 0;
     double2 psi = rx.every > 0 ? gpsi[g] : make_double2(0.0, 0.0);
     while (true) {
+      if (wait > 0) {
+        --wait;
+        ++trip;
+        continue;
+      }
       if (rx.every > 0 && step % rx.every == 0)
         record_traces<D>(gd, shots[s], rx, kappa, y, psi, s, step / rx.every, traces);
       bool done = step >= nsteps;
@@ -81,8 +94,9 @@ __global__ void __launch_bounds__(128) k_rays(GridDev gd, const ShotDev* __restr
       if (done) {
         ok &= ray_store<D>(shots[s], g, y, gpsi, state, ld, coef);
         my_steps += (unsigned long long)step;
-        g = (int64_t)atomicAdd(next, 1ull);
-        if (g >= G) break;
+        w = atomicAdd(next, 1ull);
+        if (w >= (unsigned long long)G) break;
+        g = work_order(w, G, mult);
         s = gshot[g];
         ray_init<D>(gd, shots[s], gq[g], gp[g], y);
         if (rx.every > 0) psi = gpsi[g];
@@ -93,28 +107,30 @@ __global__ void __launch_bounds__(128) k_rays(GridDev gd, const ShotDev* __restr
           hi[i] = gd.o[i] + (double)(gd.n[i] - 1) * gd.h[i] + reach;
         }
         step = 0;
+        if (rx.every > 0) wait = (rx.every - (trip + 1) % rx.every) % rx.every;
+        ++trip;
         continue;
       }
       double acc[NF], tmp[NF], k[NF];
-      ok &= rhs<D>(gd, C, y, k);
+      ok &= rhs<D>(gd, y, k);
 #pragma unroll
       for (int i = 0; i < NF; ++i) {
         acc[i] = fma(h6, k[i], y[i]);
         tmp[i] = fma(h2, k[i], y[i]);
       }
-      ok &= rhs<D>(gd, C, tmp, k);
+      ok &= rhs<D>(gd, tmp, k);
 #pragma unroll
       for (int i = 0; i < NF; ++i) {
         acc[i] = fma(h3, k[i], acc[i]);
         tmp[i] = fma(h2, k[i], y[i]);
       }
-      ok &= rhs<D>(gd, C, tmp, k);
+      ok &= rhs<D>(gd, tmp, k);
 #pragma unroll
       for (int i = 0; i < NF; ++i) {
         acc[i] = fma(h3, k[i], acc[i]);
         tmp[i] = fma(dt, k[i], y[i]);
       }
-      ok &= rhs<D>(gd, C, tmp, k);
+      ok &= rhs<D>(gd, tmp, k);
 #pragma unroll
       for (int i = 0; i < NF; ++i) y[i] = fma(h6, k[i], acc[i]);
 #pragma unroll
@@ -126,6 +142,7 @@ __global__ void __launch_bounds__(128) k_rays(GridDev gd, const ShotDev* __restr
         }
       }
       ++step;
+      ++trip;
     }
   }
   if (!ok) atomicOr(status, kStatusNumeric);
@@ -135,44 +152,170 @@ __global__ void __launch_bounds__(128) k_rays(GridDev gd, const ShotDev* __restr
 
 }  // namespace
 
-cudaError_t launch_rays(fga_plan_s* p) {
+namespace {
+
+// One thread per table cell (cells -1 .. n per axis, stored at index + 1).
+template <int D>
+__global__ void k_medium_table(GridDev gd, const double* __restrict__ C, double* __restrict__ tab) {
+  const int64_t n1 = D == 1 ? 1 : gd.n[1] + 2;
+  const int64_t cells = (gd.n[0] + 2) * n1;
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < cells;
+       c += (int64_t)gridDim.x * blockDim.x) {
+    int64_t ci[2] = {D == 1 ? c : c / n1, D == 1 ? 0 : c % n1};
+    double a[D == 1 ? 4 : 16];
+    medium_cell<D>(gd, C, ci, a);
+#pragma unroll
+    for (int k = 0; k < (D == 1 ? 4 : 16); ++k) tab[c * (D == 1 ? 4 : 16) + k] = a[k];
+  }
+}
+
+// out[j] = sum_s part[s * len + i] in slice order (j: see launch_slice_sum).
+__global__ void k_slice_sum(const double* __restrict__ part, int64_t slices, int64_t len,
+                            double* __restrict__ out, const int32_t* __restrict__ perm,
+                            int64_t row) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < len;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    double v = 0.0;
+    for (int64_t s = 0; s < slices; ++s) v += part[s * len + i];
+    const int64_t j = perm ? (i / row) * row + perm[i % row] : i;
+    out[j] = v;
+  }
+}
+
+__global__ void k_gather_rows(const double* __restrict__ in, const int32_t* __restrict__ perm,
+                              int64_t len, int64_t row, double* __restrict__ out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < len;
+       i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = in[(i / row) * row + perm[i % row]];
+}
+
+}  // namespace
+
+size_t medium_table_doubles(const GridDev& gd) {
+  return gd.dim == 1 ? (size_t)(gd.n[0] + 2) * 4 : (size_t)(gd.n[0] + 2) * (gd.n[1] + 2) * 16;
+}
+
+cudaError_t launch_medium_table(fga_plan_s* p) {
+  const size_t cells = medium_table_doubles(p->grid) / (p->grid.dim == 1 ? 4 : 16);
+  const unsigned blocks = (unsigned)std::min<size_t>((cells + 255) / 256, 4096);
+  if (p->grid.dim == 1)
+    k_medium_table<1><<<blocks, 256, 0, p->stream>>>(p->grid, p->d_coef, p->d_medtab);
+  else
+    k_medium_table<2><<<blocks, 256, 0, p->stream>>>(p->grid, p->d_coef, p->d_medtab);
+  p->launches += 1;
+  return cudaGetLastError();
+}
+
+unsigned long long work_order_mult(int64_t G) {
+  if (G < 3 || G >= ((int64_t)1 << 32)) return 1;  // (w * mult) must not overflow 64 bits
+  unsigned long long m = (unsigned long long)((double)G * 0.6180339887498949) | 1ull;
+  auto gcd = [](unsigned long long a, unsigned long long b) {
+    while (b) {
+      unsigned long long r = a % b;
+      a = b;
+      b = r;
+    }
+    return a;
+  };
+  while (gcd(m, (unsigned long long)G) != 1) m += 2;
+  return m % (unsigned long long)G;
+}
+
+int ray_max_per_sm(fga_plan_s* p) {
+  int per_sm = 0;
+  cudaError_t e = p->grid.dim == 1
+                      ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rays<1>, 128, 0)
+                      : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rays<2>, 128, 0);
+  return (e == cudaSuccess && per_sm > 0) ? per_sm : 1;
+}
+
+cudaError_t ensure_ray_blocks(fga_plan_s* p) {
+  if (p->ray_blocks > 0) return cudaSuccess;
+  int dev = 0, sms = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  const int max_sm = ray_max_per_sm(p);
+  const int per_sm = p->ray_per_sm > 0 && p->ray_per_sm < max_sm ? p->ray_per_sm : max_sm;
+  p->ray_blocks = (int64_t)sms * per_sm;
+  return cudaSuccess;
+}
+
+int64_t ray_launch_blocks(fga_plan_s* p) {
+  return std::max<int64_t>(1, std::min<int64_t>(p->ray_blocks, (p->G + 127) / 128));
+}
+
+int64_t part_slices(int64_t blocks, int64_t len) {
+  const int64_t budget = ((int64_t)4 << 30) / 8;
+  return std::max<int64_t>(1, std::min<int64_t>(blocks, budget / std::max<int64_t>(len, 1)));
+}
+
+int64_t trace_slices(fga_plan_s* p) {
+  return part_slices(ray_launch_blocks(p), p->nshots * p->rx.nrec * p->rx.nrx);
+}
+
+cudaError_t launch_slice_sum(fga_plan_s* p, const double* part, int64_t slices, int64_t len,
+                             double* out, const int32_t* perm, int64_t row) {
+  const unsigned blocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>((len + 255) / 256, 8192));
+  k_slice_sum<<<blocks, 256, 0, p->stream>>>(part, slices, len, out, perm, row);
+  p->launches += 1;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gather_rows(fga_plan_s* p, const double* in, const int32_t* perm, int64_t rows,
+                               int64_t row, double* out) {
+  const int64_t len = rows * row;
+  const unsigned blocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>((len + 255) / 256, 8192));
+  k_gather_rows<<<blocks, 256, 0, p->stream>>>(in, perm, len, row, out);
+  p->launches += 1;
+  return cudaGetLastError();
+}
+
+// The caller has sized p->d_part for the trace slices when record is set and there
+// are receivers.
+cudaError_t launch_rays_steps(fga_plan_s* p, int64_t nsteps, bool record) {
   // d_steps[0]: steps integrated; d_steps[1]: the work counter of the persistent kernel
   cudaError_t e = cudaMemsetAsync(p->d_steps, 0, 2 * sizeof(unsigned long long), p->stream);
   if (e != cudaSuccess) return e;
-  if (p->G == 0) return cudaSuccess;
-  if (p->ray_blocks == 0) {
-    int dev = 0, sms = 0, per_sm = 0;
-    e = cudaGetDevice(&dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e == cudaSuccess)
-      e = p->grid.dim == 1
-              ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rays<1>, 128, 0)
-              : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rays<2>, 128, 0);
-    if (e != cudaSuccess) return e;
-    p->ray_blocks = (int64_t)sms * (per_sm > 0 ? per_sm : 1);
+  if (p->G == 0) {
+    if (record && p->nrx > 0)
+      return cudaMemsetAsync(p->d_traces, 0, sizeof(double) * p->nshots * p->rx.nrec * p->rx.nrx,
+                             p->stream);
+    return cudaSuccess;
   }
-  unsigned blocks = (unsigned)std::min<int64_t>(p->ray_blocks, (p->G + 127) / 128);
+  e = ensure_ray_blocks(p);
+  if (e != cudaSuccess) return e;
+  const unsigned blocks = (unsigned)ray_launch_blocks(p);
   RxDev rx = p->rx;
-  if (p->nrx > 0) {
-    e = cudaMemsetAsync(p->d_traces, 0, sizeof(double) * p->nshots * rx.nrec * rx.nrx, p->stream);
+  int64_t len = 0, slices = 1;
+  if (record && p->nrx > 0) {
+    len = p->nshots * rx.nrec * rx.nrx;
+    slices = trace_slices(p);
+    if (p->part_cap < (size_t)(slices * len)) return cudaErrorInvalidValue;
+    e = cudaMemsetAsync(p->d_part, 0, sizeof(double) * slices * len, p->stream);
     if (e != cudaSuccess) return e;
   } else {
     rx.every = 0;
   }
+  const unsigned long long mult = work_order_mult(p->G);
   if (p->grid.dim == 1)
     k_rays<1><<<blocks, 128, 0, p->stream>>>(p->grid, p->d_shots, p->d_coef, p->G, p->d_gshot,
-                                             p->d_gq, p->d_gp, p->d_gpsi, p->nsteps, p->dt, p->kappa,
+                                             p->d_gq, p->d_gp, p->d_gpsi, nsteps, p->dt, p->kappa,
                                              p->integrate_exited, p->d_state, (int64_t)p->g_cap,
                                              p->d_gcoef, p->d_status, p->d_steps, p->d_steps + 1,
-                                             rx, p->d_traces);
+                                             rx, p->d_part, len, (int)slices, mult);
   else
     k_rays<2><<<blocks, 128, 0, p->stream>>>(p->grid, p->d_shots, p->d_coef, p->G, p->d_gshot,
-                                             p->d_gq, p->d_gp, p->d_gpsi, p->nsteps, p->dt, p->kappa,
+                                             p->d_gq, p->d_gp, p->d_gpsi, nsteps, p->dt, p->kappa,
                                              p->integrate_exited, p->d_state, (int64_t)p->g_cap,
                                              p->d_gcoef, p->d_status, p->d_steps, p->d_steps + 1,
-                                             rx, p->d_traces);
+                                             rx, p->d_part, len, (int)slices, mult);
   p->launches += 1;
-  return cudaGetLastError();
+  e = cudaGetLastError();
+  if (e != cudaSuccess || len == 0) return e;
+  return launch_slice_sum(p, p->d_part, slices, len, p->d_traces, p->d_rx_perm, rx.nrx);
 }
+
+cudaError_t launch_rays(fga_plan_s* p) { return launch_rays_steps(p, p->nsteps, true); }
 
 }  // namespace fga

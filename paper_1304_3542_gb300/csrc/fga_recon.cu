@@ -28,8 +28,8 @@ constexpr int T2 = 64;   // 2D tile edge (points)
 constexpr int T1 = 256;  // 1D tile length
 constexpr int CH = 16;   // Gaussians per chunk (2D)
 constexpr int CH1 = 32;  // Gaussians per chunk (1D)
-constexpr int64_t SEG2 = 1024;  // Gaussians per work item (2D)
-constexpr int64_t SEG1 = 512;   // Gaussians per work item (1D)
+constexpr int64_t SEG2 = 1024;  // default Gaussians per work item (2D)
+constexpr int64_t SEG1 = 512;   // default Gaussians per work item (1D)
 
 // Pass 1 (FILL = false): number of Gaussians per tile. Pass 2 (FILL = true): the
 // ordered list, written at the tile's offset. One CTA per tile scans the shot's
@@ -151,7 +151,7 @@ __global__ void __launch_bounds__(NT) k_gather1(GridDev gd, const ShotDev* __res
                                                 const int64_t* __restrict__ off,
                                                 const int32_t* __restrict__ list, int64_t list_cap,
                                                 const int64_t* __restrict__ seg_off, int64_t ntiles,
-                                                double* __restrict__ partial) {
+                                                int64_t seg, double* __restrict__ partial) {
   const int64_t w = blockIdx.x;
   if (w >= seg_off[ntiles]) return;
   const int64_t t = tile_of_item(seg_off, ntiles, w);
@@ -162,8 +162,8 @@ __global__ void __launch_bounds__(NT) k_gather1(GridDev gd, const ShotDev* __res
   __shared__ double sQ[CH1], sP[CH1];
   __shared__ double2 sC[CH1];
   double re = 0.0;
-  const int64_t l0 = min(off[t], list_cap) + (w - seg_off[t]) * SEG1;
-  const int64_t l1 = min(min(off[t + 1], list_cap), l0 + SEG1);
+  const int64_t l0 = min(off[t], list_cap) + (w - seg_off[t]) * seg;
+  const int64_t l1 = min(min(off[t + 1], list_cap), l0 + seg);
   for (int64_t c0 = l0; c0 < l1; c0 += CH1) {
     int nc = (int)((l1 - c0) < CH1 ? (l1 - c0) : CH1);
     if (threadIdx.x < nc) {
@@ -192,7 +192,7 @@ __global__ void __launch_bounds__(NT) k_gather2(GridDev gd, const ShotDev* __res
                                                 const int64_t* __restrict__ off,
                                                 const int32_t* __restrict__ list, int64_t list_cap,
                                                 const int64_t* __restrict__ seg_off, int64_t ntiles,
-                                                double* __restrict__ partial) {
+                                                int64_t seg, double* __restrict__ partial) {
   const int64_t w = blockIdx.x;
   if (w >= seg_off[ntiles]) return;
   const int64_t t = tile_of_item(seg_off, ntiles, w);
@@ -215,8 +215,8 @@ __global__ void __launch_bounds__(NT) k_gather2(GridDev gd, const ShotDev* __res
   for (int i = 0; i < 4; ++i)
 #pragma unroll
     for (int j = 0; j < 4; ++j) accr[i][j] = 0.0;
-  const int64_t l0 = min(off[t], list_cap) + (w - seg_off[t]) * SEG2;
-  const int64_t l1 = min(min(off[t + 1], list_cap), l0 + SEG2);
+  const int64_t l0 = min(off[t], list_cap) + (w - seg_off[t]) * seg;
+  const int64_t l1 = min(min(off[t + 1], list_cap), l0 + seg);
   for (int64_t c0 = l0; c0 < l1; c0 += CH) {
     const int nc = (int)((l1 - c0) < CH ? (l1 - c0) : CH);
     // factor generation: thread -> (gaussian, axis, 8 consecutive points)
@@ -335,8 +335,12 @@ cudaError_t launch_binning_fill(fga_plan_s* p) {
   return cudaGetLastError();
 }
 
+int64_t segment_len(fga_plan_s* p) {
+  return p->seg > 0 ? p->seg : (p->grid.dim == 1 ? SEG1 : SEG2);
+}
+
 size_t partial_items(fga_plan_s* p) {
-  int64_t seg = p->grid.dim == 1 ? SEG1 : SEG2;
+  const int64_t seg = segment_len(p);
   return (size_t)p->ntiles + (p->list_cap + seg - 1) / seg;
 }
 
@@ -346,7 +350,7 @@ size_t tile_points(int dim) { return dim == 1 ? (size_t)T1 : (size_t)T2 * T2; }
 // partial tile, then the ordered reduction into u_dev.
 cudaError_t launch_reconstruct(fga_plan_s* p, double* u_dev) {
   if (p->ntiles == 0) return cudaSuccess;
-  const int64_t seg = p->grid.dim == 1 ? SEG1 : SEG2;
+  const int64_t seg = segment_len(p);
   k_segments<<<(unsigned)((p->ntiles + 255) / 256), 256, 0, p->stream>>>(
       p->d_tile_off, p->ntiles, (int64_t)p->list_cap, seg, p->d_seg_off);
   cudaError_t e = cudaGetLastError();
@@ -359,14 +363,14 @@ cudaError_t launch_reconstruct(fga_plan_s* p, double* u_dev) {
     k_gather1<<<items, NT, 0, p->stream>>>(p->grid, p->d_shots, p->nshots, p->kappa, p->d_state,
                                            (int64_t)p->g_cap, p->d_gcoef, p->d_tile_off,
                                            p->d_tile_list, (int64_t)p->list_cap, p->d_seg_off,
-                                           p->ntiles, p->d_partial);
+                                           p->ntiles, seg, p->d_partial);
     k_reduce<1><<<(unsigned)p->ntiles, NT, 0, p->stream>>>(p->grid, p->d_shots, p->nshots,
                                                            p->d_seg_off, p->d_partial, u_dev);
   } else {
     k_gather2<<<items, NT, 0, p->stream>>>(p->grid, p->d_shots, p->nshots, p->kappa, p->d_state,
                                            (int64_t)p->g_cap, p->d_gcoef, p->d_tile_off,
                                            p->d_tile_list, (int64_t)p->list_cap, p->d_seg_off,
-                                           p->ntiles, p->d_partial);
+                                           p->ntiles, seg, p->d_partial);
     k_reduce<2><<<(unsigned)p->ntiles, NT, 0, p->stream>>>(p->grid, p->d_shots, p->nshots,
                                                            p->d_seg_off, p->d_partial, u_dev);
   }

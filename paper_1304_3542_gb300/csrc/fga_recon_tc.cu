@@ -29,7 +29,7 @@ constexpr int TM = 128;       // tile edge (x = GEMM M, z = GEMM N)
 constexpr int CHG = 16;       // Gaussians per chunk -> K = 32
 constexpr int KC = 2 * CHG;   // GEMM K per chunk
 constexpr int KB = KC / 4;    // 16-byte core matrices along K (tf32: 4 per core row)
-constexpr int64_t SEGM = 2048;
+constexpr int64_t SEGM = 2048;  // default Gaussians per work item
 constexpr int NTC = 128;      // threads per CTA
 constexpr uint32_t kMaxTries = 1u << 22;
 // core-matrix (8 rows x 16 bytes) strides of the K-major operand tiles
@@ -90,7 +90,8 @@ __global__ void __launch_bounds__(NTC) k_gather_tc(GridDev gd, const ShotDev* __
                                                    const int64_t* __restrict__ off,
                                                    const int32_t* __restrict__ list, int64_t list_cap,
                                                    const int64_t* __restrict__ seg_off, int64_t ntiles,
-                                                   float* __restrict__ partial, int* status) {
+                                                   int64_t seg, float* __restrict__ partial,
+                                                   int* status) {
   const int64_t w = blockIdx.x;
   if (w >= seg_off[ntiles]) return;  // uniform over the CTA
   extern __shared__ __align__(1024) unsigned char smem[];
@@ -120,8 +121,8 @@ __global__ void __launch_bounds__(NTC) k_gather_tc(GridDev gd, const ShotDev* __
   tc::fence_after_sync();
   const uint32_t tmem = *tbase;
   const uint32_t idesc = tc::idesc_f32acc(tc::kFmtTF32, TM, TM);
-  const int64_t l0 = min(off[t], list_cap) + (w - seg_off[t]) * SEGM;
-  const int64_t l1 = min(min(off[t + 1], list_cap), l0 + SEGM);
+  const int64_t l0 = min(off[t], list_cap) + (w - seg_off[t]) * seg;
+  const int64_t l1 = min(min(off[t + 1], list_cap), l0 + seg);
   const int gi = tid >> 3, part = tid & 7;
   uint32_t chunks = 0;
   bool ok = true;
@@ -222,8 +223,11 @@ __global__ void k_segments_tc(const int64_t* __restrict__ off, int64_t ntiles, i
 
 int tile_edge_tc() { return TM; }
 
+int64_t segment_len_tc(fga_plan_s* p) { return p->seg > 0 ? p->seg : SEGM; }
+
 size_t partial_items_tc(fga_plan_s* p) {
-  return (size_t)p->ntiles + (p->list_cap + SEGM - 1) / SEGM;
+  const int64_t seg = segment_len_tc(p);
+  return (size_t)p->ntiles + (p->list_cap + seg - 1) / seg;
 }
 
 size_t partial_bytes_tc(fga_plan_s* p) { return partial_items_tc(p) * TM * TM * sizeof(float); }
@@ -238,7 +242,7 @@ cudaError_t launch_reconstruct_tc(fga_plan_s* p, double* u_dev) {
     attr_set = true;
   }
   k_segments_tc<<<(unsigned)((p->ntiles + 255) / 256), 256, 0, p->stream>>>(
-      p->d_tile_off, p->ntiles, (int64_t)p->list_cap, SEGM, p->d_seg_off);
+      p->d_tile_off, p->ntiles, (int64_t)p->list_cap, segment_len_tc(p), p->d_seg_off);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   e = launch_scan(p, p->d_seg_off, p->ntiles);
@@ -247,7 +251,7 @@ cudaError_t launch_reconstruct_tc(fga_plan_s* p, double* u_dev) {
   k_gather_tc<<<items, NTC, kSmemBytes, p->stream>>>(
       p->grid, p->d_shots, p->nshots, p->kappa, p->d_state, (int64_t)p->g_cap, p->d_gcoef,
       p->d_tile_off, p->d_tile_list, (int64_t)p->list_cap, p->d_seg_off, p->ntiles,
-      reinterpret_cast<float*>(p->d_partial), p->d_status);
+      segment_len_tc(p), reinterpret_cast<float*>(p->d_partial), p->d_status);
   k_reduce_tc<<<(unsigned)p->ntiles, 256, 0, p->stream>>>(p->grid, p->d_shots, p->nshots,
                                                           p->d_seg_off,
                                                           reinterpret_cast<float*>(p->d_partial),

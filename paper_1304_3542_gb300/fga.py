@@ -99,6 +99,12 @@ def load(build_if_missing: bool = True):
     L.fga_set_receivers.restype = ci
     L.fga_traces.argtypes = [P, P]
     L.fga_traces.restype = ci
+    L.fga_autotune.argtypes = [P, P, P]
+    L.fga_autotune.restype = ci
+    L.fga_tuning.argtypes = [P, P]
+    L.fga_tuning.restype = ci
+    L.fga_set_tuning.argtypes = [P, P]
+    L.fga_set_tuning.restype = ci
     L.fga_run_graph.argtypes = [P, P]
     L.fga_run_graph.restype = ci
     L.fga_grad.argtypes = [P, P, P]
@@ -231,6 +237,23 @@ class Plan:
         """propagate + reconstruct into the device tensor out, as one CUDA graph replay."""
         self._check(self._L.fga_run_graph(self._h, _ptr(out)), "fga_run_graph")
         return out
+
+    def autotune(self, out):
+        """Tune the ray launch shape and the gather's segment length on this plan's data,
+        then propagate and reconstruct into the device tensor out. Returns the choice
+        (blocks per SM, segment length)."""
+        ch = np.zeros(2, dtype=np.int64)
+        self._check(self._L.fga_autotune(self._h, _ptr(out), ch.ctypes.data), "fga_autotune")
+        return int(ch[0]), int(ch[1])
+
+    def tuning(self):
+        ch = np.zeros(2, dtype=np.int64)
+        self._check(self._L.fga_tuning(self._h, ch.ctypes.data), "fga_tuning")
+        return int(ch[0]), int(ch[1])
+
+    def set_tuning(self, blocks_per_sm: int, segment: int):
+        ch = np.array([blocks_per_sm, segment], dtype=np.int64)
+        self._check(self._L.fga_set_tuning(self._h, ch.ctypes.data), "fga_set_tuning")
 
     def sync(self):
         self._check(self._L.fga_sync(self._h), "fga_sync")

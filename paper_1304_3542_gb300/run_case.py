@@ -2,6 +2,7 @@
 
   python -m paper_1304_3542_gb300.run_case [--workload layered_single] [--T 0.1]
                                            [--tau 1e-3] [--repeat 1] [--nshots 4]
+                                           [--precision fp64|mixed] [--receivers]
 
 A small driver for trying the library on the seeded workloads (and the command
 the kernel profiles are taken with).
@@ -28,6 +29,9 @@ def main():
     ap.add_argument("--tau", type=float, default=None)
     ap.add_argument("--nshots", type=int, default=4)
     ap.add_argument("--repeat", type=int, default=1)
+    ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64")
+    ap.add_argument("--receivers", action="store_true",
+                    help="record traces at 368 surface receivers every 4 ms (layered model)")
     args = ap.parse_args()
     kw = {}
     if args.T is not None:
@@ -37,7 +41,12 @@ def main():
     if args.workload == "layered_batch":
         kw["nshots"] = args.nshots
     prob = WL.by_name(args.workload, **kw)
-    plan = F.plan_from_problem(prob, stream=torch.cuda.current_stream().cuda_stream)
+    precision = F.FGA_MIXED_TF32X3 if args.precision == "mixed" else F.FGA_FP64
+    plan = F.plan_from_problem(prob, stream=torch.cuda.current_stream().cuda_stream,
+                               precision=precision)
+    if args.receivers:
+        xr = np.stack([0.025 * np.arange(368), np.zeros(368)], axis=1)
+        plan.set_receivers(xr, int(round(0.004 / prob.dt)))
     u0, u1 = F.stacked_initial_data(prob)
     a, b = torch.from_numpy(u0).cuda(), torch.from_numpy(u1).cuda()
     out = torch.zeros((len(prob.shots),) + prob.n, dtype=torch.float64, device="cuda")

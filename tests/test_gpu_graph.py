@@ -2,7 +2,8 @@
 
 The replay runs the same kernels on the same buffers, and the field reduction has a
 fixed order, so every replay must give the eager result bit for bit; receiver traces
-are summed with atomics and agree to rounding. The graph is captured again when the
+are summed with atomics (in an order that changes from run to run), so they agree to
+rounding of sums with cancellation: 1e-11 of the largest trace value. The graph is captured again when the
 receivers or the output buffer change."""
 
 import numpy as np
@@ -82,7 +83,7 @@ def test_replay_traces_and_receiver_change():
             tr = plan.traces()
             scale = np.abs(tr_eager).max()
             assert scale > 0
-            assert np.abs(tr - tr_eager).max() <= 1e-13 * scale
+            assert np.abs(tr - tr_eager).max() <= 1e-11 * scale
         # new receivers: the graph must be captured again around the new buffers
         plan.set_receivers(xr[::2], 1)
         plan.run_graph(out)
@@ -92,7 +93,7 @@ def test_replay_traces_and_receiver_change():
         plan.sync()
         tr2_eager = plan.traces()
     assert tr2.shape == tr2_eager.shape and tr2.shape != tr_eager.shape
-    assert np.abs(tr2 - tr2_eager).max() <= 1e-13 * np.abs(tr2_eager).max()
+    assert np.abs(tr2 - tr2_eager).max() <= 1e-11 * np.abs(tr2_eager).max()
 
 
 def test_default_stream_rejected():
@@ -108,3 +109,56 @@ def test_default_stream_rejected():
     assert ei.value.status == F.FGA_ERR_INVALID
     with pytest.raises(F.FGAError):
         plan.run_graph(np.zeros((1,) + prob.n))
+
+
+@pytest.mark.parametrize("precision", [F.FGA_FP64, F.FGA_MIXED_TF32X3])
+def test_autotune_choice_and_results(precision):
+    """The autotuner's choice is one of its candidates, leaves every ray state unchanged
+    (bit for bit) and the field unchanged up to the order of the partial sums; a plan
+    given the same choice reproduces the tuned field bit for bit."""
+    import torch
+
+    prob = _problem(N=128, T=0.05)
+    stream = torch.cuda.Stream()
+    u0, u1 = F.stacked_initial_data(prob)
+    shape = (len(prob.shots),) + prob.n
+
+    def fresh():
+        plan = F.plan_from_problem(prob, stream=stream.cuda_stream, precision=precision)
+        with torch.cuda.stream(stream):
+            plan.decompose(torch.from_numpy(u0).cuda(), torch.from_numpy(u1).cuda())
+        return plan
+
+    with torch.cuda.stream(stream):
+        ref_plan = fresh()
+        ref = torch.zeros(shape, dtype=torch.float64, device="cuda")
+        ref_plan.propagate()
+        ref_plan.reconstruct(ref)
+        ref_plan.sync()
+        ref_state = ref_plan.state(0)
+        tuned_plan = fresh()
+        out = torch.zeros(shape, dtype=torch.float64, device="cuda")
+        per_sm, seg = tuned_plan.autotune(out)
+        tuned_plan.sync()
+    assert tuned_plan.tuning() == (per_sm, seg)
+    assert 1 <= per_sm <= 64
+    base = 512 if precision == F.FGA_MIXED_TF32X3 else 256
+    assert seg in [base << k for k in range(5)]
+    st = tuned_plan.state(0)
+    for k in ref_state:
+        assert np.array_equal(st[k], ref_state[k]), k
+    u_ref, u_tuned = ref.cpu().numpy(), out.cpu().numpy()
+    tol = 1e-13 if precision == F.FGA_FP64 else 1e-6
+    assert np.linalg.norm(u_tuned - u_ref) <= tol * np.linalg.norm(u_ref)
+    with torch.cuda.stream(stream):
+        again = fresh()
+        again.set_tuning(per_sm, seg)
+        out2 = torch.zeros(shape, dtype=torch.float64, device="cuda")
+        again.propagate()
+        again.reconstruct(out2)
+        again.sync()
+    assert np.array_equal(out2.cpu().numpy(), u_tuned)
+    with pytest.raises(F.FGAError):
+        again.set_tuning(-1, 0)
+    with pytest.raises(F.FGAError):
+        again.set_tuning(2, 1 << 21)
