@@ -302,6 +302,7 @@ def run_ours(args, rank, world, local_rank):
                           "anchors and segment sums)"),
             "fp64_path_value": fp64_value,
             "tuning": {"ray_blocks_per_sm": tuning[0], "gather_segment": tuning[1],
+                       "ray_register_variant": tuning[2],
                        "by": "fga_autotune on this workload before the warm-up"},
             "stage_ms_mean": {"fbi": statistics.mean(fbi_ms), "rays": statistics.mean(ray_ms),
                               "binning+reconstruct": statistics.mean(recon_ms)},
@@ -429,6 +430,7 @@ def run_batch(args, rank, world, local_rank):
 
         mixed_step()
         t_mixed = timed(mixed_step, args.steps)
+        mixed.close()  # free its buffers before the FP64 forms
         # FP64, batched
         b64 = F.plan_from_problem(prob, stream=stream.cuda_stream, precision=F.FGA_FP64)
         d_64 = torch.zeros_like(d_mx)
@@ -447,8 +449,8 @@ def run_batch(args, rank, world, local_rank):
         singles = []
         for s in range(len(prob.shots)):
             one = dataclasses.replace(prob, shots=[prob.shots[s]])
-            pl = F.plan_from_problem(one, stream=stream.cuda_stream, precision=F.FGA_FP64)
-            singles.append(pl)
+            singles.append(F.plan_from_problem(one, stream=stream.cuda_stream,
+                                               precision=F.FGA_FP64))
 
         def per_shot_step():
             for s, pl in enumerate(singles):
@@ -460,7 +462,6 @@ def run_batch(args, rank, world, local_rank):
         t_single = timed(per_shot_step, args.steps)
         for pl in singles:
             pl.close()
-        mixed.close()
     t_mixed_all = max_over_ranks(t_mixed)
     evals_all = evals
     if world > 1:
@@ -487,7 +488,8 @@ def run_batch(args, rank, world, local_rank):
             "shots_this_rank": len(mine),
             "gaussians_per_shot": {"min": min(counts), "median": statistics.median(counts),
                                    "max": max(counts)},
-            "tuning": {"ray_blocks_per_sm": tuning[0], "gather_segment": tuning[1]},
+            "tuning": {"ray_blocks_per_sm": tuning[0], "gather_segment": tuning[1],
+                       "ray_register_variant": tuning[2]},
             "form": "mixed precision, all shots of the rank in one plan, propagate + "
                     "reconstruct replayed as one CUDA graph",
             "seconds_per_pass": {"mixed_batched_graph": t_mixed, "fp64_batched": t_b64,

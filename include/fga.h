@@ -78,7 +78,7 @@ typedef struct {
                          ceil(12 sqrt(eps)/h) rounded up to a multiple of 32; n on
                          periodic axes (where any given value must equal n) */
   double T;           /* final time >= 0 */
-  double dt;          /* RK4 step; T/dt must be an integer to within 1e-9 */
+  double dt;          /* RK4 step; T/dt must be an integer (to within 1e-9) below 2^31 */
   double kappa;       /* reconstruction window half-width in units of sqrt(eps) */
   double tau;         /* relative threshold: keep |psi+| >= tau * max|psi+-| */
   int precision;      /* fga_precision */
@@ -169,23 +169,27 @@ fga_status fga_grad(fga_plan_t plan, const double* residual, double* grad);
 fga_status fga_run_graph(fga_plan_t plan, double* u_dev);
 
 /* Autotuner (batching). Picks, by timing on this plan's own decomposed data, (0) the
- * number of resident blocks per SM of the persistent ray kernel (from the occupancy
- * maximum down, on a short integration of at most 64 steps) and (1) the split-K segment
- * length of the reconstruction gather (Gaussians per (tile, segment) work item; 5
- * powers of two), then runs the full fga_propagate and fga_reconstruct with them into
+ * number of resident blocks per SM of the persistent ray kernel and (2) its register
+ * budget (variant 0: up to 255 registers per thread; 1: 168, so that 3 blocks of 128
+ * fit an SM), both on a short integration of at most 64 steps, and (1) the split-K
+ * segment length of the reconstruction gather (Gaussians per (tile, segment) work item;
+ * 5 powers of two), then runs the full fga_propagate and fga_reconstruct with them into
  * the device buffer u_dev. Blocks the host until done. The choice stays with the plan
- * and is written to choice[2] when choice is not NULL. Ray states are identical for
+ * and is written to choice[3] when choice is not NULL. Ray states are identical for
  * every choice; the field changes only by the order of the FP64 (or FP32 tensor-core)
  * partial sums. Errors: FGA_ERR_STATE (not decomposed), FGA_ERR_INVALID (host u_dev),
  * FGA_ERR_OOM, FGA_ERR_CUDA. */
 fga_status fga_autotune(fga_plan_t plan, double* u_dev, int64_t* choice);
 
-/* The plan's current tuning, choice[2] as written by fga_autotune (blocks per SM, 0 =
- * occupancy maximum; segment length in Gaussians). */
+/* The plan's current tuning, choice[3] as written by fga_autotune (blocks per SM, 0 =
+ * occupancy maximum; segment length in Gaussians actually used, which is raised above
+ * the set one when the partial tiles of a large batch would exceed 4 GiB; ray kernel
+ * variant). */
 fga_status fga_tuning(fga_plan_t plan, int64_t* choice);
 
 /* Sets the tuning (e.g. one found earlier for the same workload): 0 <= choice[0] <= 64,
- * 0 <= choice[1] <= 2^20, 0 meaning the default. FGA_ERR_INVALID otherwise. */
+ * 0 <= choice[1] <= 2^20 (0 meaning the default for both), choice[2] in {0, 1}.
+ * FGA_ERR_INVALID otherwise. */
 fga_status fga_set_tuning(fga_plan_t plan, const int64_t* choice);
 
 /* Waits for the plan's stream and reports any device-side error flag. */

@@ -93,6 +93,30 @@ __device__ __forceinline__ void record_vjp(const GridDev& gd, const ShotDev& sh,
   psib[1] += psb.i;
 }
 
+// Gaussians in order of decreasing stop step (counting sort by stop-step bucket), so
+// that the 32 rays of a warp, which the adjoint runs in lockstep, have nearly the same
+// length.
+__global__ void k_order_count(const int32_t* __restrict__ gsteps, int64_t G, int64_t nsteps,
+                              int64_t width, int64_t* __restrict__ cnt) {
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < G;
+       g += (int64_t)gridDim.x * blockDim.x)
+    atomicAdd(reinterpret_cast<unsigned long long*>(cnt + (nsteps - gsteps[g]) / width), 1ull);
+}
+
+__global__ void k_order_scatter(const int32_t* __restrict__ gsteps, int64_t G, int64_t nsteps,
+                                int64_t width, int64_t* __restrict__ fill, int32_t* __restrict__ order) {
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < G;
+       g += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t pos = (int64_t)atomicAdd(
+        reinterpret_cast<unsigned long long*>(fill + (nsteps - gsteps[g]) / width), 1ull);
+    order[pos] = (int32_t)g;
+  }
+}
+
+// One warp runs 32 Gaussians in lockstep: the forward pass with checkpoints until the
+// last of them stops, then the reverse sweep from the warp's longest ray down to step 0,
+// each lane working only on steps its own ray reached (the others wait); so the segment
+// recomputations of all lanes fall on the same trips.
 template <int D>
 __global__ void __launch_bounds__(128) k_adjoint(GridDev gd, const ShotDev* __restrict__ shots,
                                                  const double* __restrict__ C, int64_t G,
@@ -106,20 +130,27 @@ __global__ void __launch_bounds__(128) k_adjoint(GridDev gd, const ShotDev* __re
                                                  double* __restrict__ grad_part, int64_t grad_len,
                                                  int slices, double* __restrict__ scratch,
                                                  int64_t kseg, int64_t ncheck,
-                                                 unsigned long long* next, unsigned long long mult) {
+                                                 unsigned long long* next,
+                                                 const int32_t* __restrict__ order) {
   using Lo = Layout<D>;
   constexpr int NF = Lo::NF;
+  constexpr unsigned kFull = 0xffffffffu;
   // this block's private slice of dJ/dc (no other block adds into it)
   double* gradC = grad_part + (int64_t)(blockIdx.x % slices) * grad_len;
   const int64_t nthr = (int64_t)gridDim.x * blockDim.x;
   const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int lane = threadIdx.x & 31;
   // scratch: [slot][field][thread], slots 0..ncheck-1 checkpoints, then kseg segment states
   auto slot = [&](int64_t sidx, int f) -> double& { return scratch[(sidx * NF + f) * nthr + tid]; };
   while (true) {
-    const unsigned long long w = atomicAdd(next, 1ull);
-    if (w >= (unsigned long long)G) break;
-    const int64_t g = work_order(w, G, mult);
-    const int s = gshot[g];
+    unsigned long long base = 0;
+    if (lane == 0) base = atomicAdd(next, 32ull);
+    base = __shfl_sync(kFull, base, 0);
+    const unsigned long long w = base + (unsigned long long)lane;
+    const bool has = w < (unsigned long long)G;
+    if (!__any_sync(kFull, has)) break;
+    const int64_t g = has ? (int64_t)order[w] : 0;
+    const int s = has ? gshot[g] : 0;
     const ShotDev& sh = shots[s];
     double lo[D], hi[D];
 #pragma unroll
@@ -129,10 +160,12 @@ __global__ void __launch_bounds__(128) k_adjoint(GridDev gd, const ShotDev* __re
       hi[i] = gd.o[i] + (double)(gd.n[i] - 1) * gd.h[i] + reach;
     }
     double y[NF];
-    ray_init<D>(gd, sh, gq[g], gp[g], y);
-    // forward with checkpoints every kseg steps; nend = last step reached
+    ray_init<D>(gd, sh, has ? gq[g] : 0, has ? gp[g] : 0, y);
+    // forward with checkpoints every kseg steps; nend = the step the ray stopped at
     int64_t nend = 0;
-    for (int64_t step = 0;; ++step) {
+    bool run = has;
+    for (int64_t step = 0; __any_sync(kFull, run); ++step) {
+      if (!run) continue;
       if (step % kseg == 0)
 #pragma unroll
         for (int f = 0; f < NF; ++f) slot(step / kseg, f) = y[f];
@@ -145,54 +178,64 @@ __global__ void __launch_bounds__(128) k_adjoint(GridDev gd, const ShotDev* __re
       }
       if (done) {
         nend = step;
-        break;
+        run = false;
+      } else {
+        rk4_step<D>(gd, C, y, dt);
       }
-      rk4_step<D>(gd, C, y, dt);
+    }
+    int64_t nend_w = nend;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      const int64_t o = __shfl_xor_sync(kFull, nend_w, off);
+      nend_w = o > nend_w ? o : nend_w;
     }
     // reverse sweep
     double lam[NF], psib[2] = {0.0, 0.0};
 #pragma unroll
     for (int f = 0; f < NF; ++f) lam[f] = 0.0;
-    const double2 psi = gpsi[g];
+    const double2 psi = has ? gpsi[g] : make_double2(0.0, 0.0);
+    // states j*kseg .. of segment j into the segment slots (lanes whose ray reached them)
+    auto load_segment = [&](int64_t j) {
+      const bool mine = has && j * kseg <= nend;
+      double z[NF];
+#pragma unroll
+      for (int f = 0; f < NF; ++f) z[f] = mine ? slot(j, f) : 0.0;
+      for (int64_t i = 0; i < kseg && j * kseg + i <= nend_w; ++i) {
+        if (!mine || j * kseg + i > nend) continue;
+#pragma unroll
+        for (int f = 0; f < NF; ++f) slot(ncheck + i, f) = z[f];
+        if (i + 1 < kseg && j * kseg + i + 1 <= nend) rk4_step<D>(gd, C, z, dt);
+      }
+    };
     int64_t seg_loaded = -1;
-    for (int64_t nn = nend;; --nn) {
-      // state y_nn from its segment (recomputed from the checkpoint when needed)
+    for (int64_t nn = nend_w;; --nn) {
+      const bool act = has && nn <= nend;
       const int64_t j = nn / kseg;
       if (j != seg_loaded) {
-        double z[NF];
-#pragma unroll
-        for (int f = 0; f < NF; ++f) z[f] = slot(j, f);
-        for (int64_t i = 0; i < kseg && j * kseg + i <= nend; ++i) {
-#pragma unroll
-          for (int f = 0; f < NF; ++f) slot(ncheck + i, f) = z[f];
-          if (i + 1 < kseg && j * kseg + i + 1 <= nend) rk4_step<D>(gd, C, z, dt);
-        }
+        load_segment(j);
         seg_loaded = j;
       }
       double yn[NF];
+      if (act && rx.every > 0 && nn % rx.every == 0) {
 #pragma unroll
-      for (int f = 0; f < NF; ++f) yn[f] = slot(ncheck + (nn - j * kseg), f);
-      if (rx.every > 0 && nn % rx.every == 0)
+        for (int f = 0; f < NF; ++f) yn[f] = slot(ncheck + (nn - j * kseg), f);
         record_vjp<D>(gd, sh, rx, kappa, yn, psi,
                       residual + ((int64_t)s * rx.nrec + nn / rx.every) * rx.nrx, lam, psib);
+      }
       if (nn == 0) break;
       // state at nn - 1
       const int64_t jp = (nn - 1) / kseg;
       if (jp != seg_loaded) {
-        double z[NF];
-#pragma unroll
-        for (int f = 0; f < NF; ++f) z[f] = slot(jp, f);
-        for (int64_t i = 0; i < kseg && jp * kseg + i <= nend; ++i) {
-#pragma unroll
-          for (int f = 0; f < NF; ++f) slot(ncheck + i, f) = z[f];
-          if (i + 1 < kseg && jp * kseg + i + 1 <= nend) rk4_step<D>(gd, C, z, dt);
-        }
+        load_segment(jp);
         seg_loaded = jp;
       }
+      if (act) {
 #pragma unroll
-      for (int f = 0; f < NF; ++f) yn[f] = slot(ncheck + (nn - 1 - jp * kseg), f);
-      rk4_step_adjoint<D>(gd, C, yn, dt, lam, gradC);
+        for (int f = 0; f < NF; ++f) yn[f] = slot(ncheck + (nn - 1 - jp * kseg), f);
+        rk4_step_adjoint<D>(gd, C, yn, dt, lam, gradC);
+      }
     }
+    if (!has) continue;
     // branch split: psi+ = 1/2 psi_0 + t, t = 1/2 i eps psi_1/(c(q)|p|), so d psi+/d c(q) = -t/c(q)
     const double2 t1 = gpsi_f1[g];
     double q[D];
@@ -256,6 +299,18 @@ cudaError_t launch_adjoint(fga_plan_s* p, const double* residual, double* gradC,
   const unsigned blocks = (unsigned)(nthreads / 128);
   const int64_t slices = adjoint_slices(p, nthreads);
   if (p->part_cap < (size_t)(slices * len)) return cudaErrorInvalidValue;
+  // Gaussians by decreasing stop step
+  const int64_t width = kseg, nb = p->nsteps / width + 1;
+  if (p->adj_bucket_cap < (size_t)(nb + 1)) return cudaErrorInvalidValue;
+  e = cudaMemsetAsync(p->d_adj_bucket, 0, sizeof(int64_t) * (nb + 1), p->stream);
+  if (e != cudaSuccess) return e;
+  const unsigned gb = (unsigned)std::max<int64_t>(1, std::min<int64_t>((p->G + 255) / 256, 4096));
+  k_order_count<<<gb, 256, 0, p->stream>>>(p->d_gsteps, p->G, p->nsteps, width, p->d_adj_bucket);
+  e = launch_scan(p, p->d_adj_bucket, nb);
+  if (e != cudaSuccess) return e;
+  k_order_scatter<<<gb, 256, 0, p->stream>>>(p->d_gsteps, p->G, p->nsteps, width, p->d_adj_bucket,
+                                             p->d_adj_order);
+  p->launches += 2;
   e = cudaMemsetAsync(p->d_part, 0, sizeof(double) * slices * len, p->stream);
   if (e != cudaSuccess) return e;
   RxDev rx = p->rx;
@@ -264,13 +319,13 @@ cudaError_t launch_adjoint(fga_plan_s* p, const double* residual, double* gradC,
                                                 p->d_gq, p->d_gp, p->d_gpsi, p->d_gpsi_f1, p->nsteps,
                                                 p->dt, p->kappa, p->integrate_exited, rx, residual,
                                                 p->d_part, len, (int)slices, scratch, kseg, ncheck,
-                                                p->d_steps + 1, work_order_mult(p->G));
+                                                p->d_steps + 1, p->d_adj_order);
   else
     k_adjoint<2><<<blocks, 128, 0, p->stream>>>(p->grid, p->d_shots, p->d_coef, p->G, p->d_gshot,
                                                 p->d_gq, p->d_gp, p->d_gpsi, p->d_gpsi_f1, p->nsteps,
                                                 p->dt, p->kappa, p->integrate_exited, rx, residual,
                                                 p->d_part, len, (int)slices, scratch, kseg, ncheck,
-                                                p->d_steps + 1, work_order_mult(p->G));
+                                                p->d_steps + 1, p->d_adj_order);
   p->launches += 1;
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;

@@ -148,7 +148,8 @@ fga_status fga_destroy(fga_plan_t p) {
                   p->d_max2, p->d_blk, p->d_counts, p->d_blk_first, p->d_gshot, p->d_gq, p->d_gp,
                   p->d_gpsi, p->d_state, p->d_gcoef, p->d_tile_cnt, p->d_tile_off,
                   p->d_tile_list, p->d_seg_off, p->d_partial, p->d_out, p->d_status,
-                  p->d_steps, p->d_rx, p->d_rx_off, p->d_rx_perm, p->d_traces,
+                  p->d_steps, p->d_rx, p->d_rx_off, p->d_rx_perm, p->d_traces, p->d_gsteps,
+                  p->d_adj_order, p->d_adj_bucket,
                   p->d_run_geo, p->d_run_axis, p->d_run_off, p->d_resid_int,
                   p->d_psi_f1, p->d_gpsi_f1, p->d_adj_scratch, p->d_grad, p->d_resid,
                   p->d_part};
@@ -184,6 +185,7 @@ fga_status fga_plan(const fga_config* cfg, const double* velocity, void* stream,
   double steps = cfg->T / cfg->dt;
   if (std::fabs(steps - std::round(steps)) > 1e-9 * std::max(1.0, steps))
     return fail(nullptr, FGA_ERR_INVALID, "T/dt must be an integer");
+  if (steps > 2147483647.0) return fail(nullptr, FGA_ERR_INVALID, "T/dt must be below 2^31");
   if (!(cfg->kappa > 0.0) || !std::isfinite(cfg->kappa))
     return fail(nullptr, FGA_ERR_INVALID, "kappa must be > 0");
   if (!(cfg->tau >= 0.0) || !std::isfinite(cfg->tau))
@@ -438,6 +440,10 @@ fga_status fga_decompose(fga_plan_t p, const double* u0, const double* u1, int64
     CUDA_OR_FAIL(p, grow(&p->d_gcoef, &c, cap));
     c = 0; if (p->d_state) { cudaFree(p->d_state); p->d_state = nullptr; }
     CUDA_OR_FAIL(p, grow(&p->d_state, &c, cap * p->nfields));
+    c = 0; if (p->d_gsteps) { cudaFree(p->d_gsteps); p->d_gsteps = nullptr; }
+    CUDA_OR_FAIL(p, grow(&p->d_gsteps, &c, cap));
+    c = 0; if (p->d_adj_order) { cudaFree(p->d_adj_order); p->d_adj_order = nullptr; }
+    CUDA_OR_FAIL(p, grow(&p->d_adj_order, &c, cap));
     p->g_cap = cap;
   }
   CUDA_OR_FAIL(p, fga::launch_select(p));
@@ -514,11 +520,11 @@ fga_status fga_run_graph(fga_plan_t p, double* u_dev) {
   if (st != FGA_OK) return st;
   st = trace_capacity(p);
   if (st != FGA_OK) return st;
-  int64_t key[9] = {p->G, (int64_t)p->g_cap, (int64_t)p->list_cap, (int64_t)p->partial_cap,
+  int64_t key[10] = {p->G, (int64_t)p->g_cap, (int64_t)p->list_cap, (int64_t)p->partial_cap,
                     (int64_t)(uintptr_t)u_dev, p->nrx, p->seg, p->ray_blocks,
-                    (int64_t)(uintptr_t)p->d_part};
+                    (int64_t)(uintptr_t)p->d_part, p->ray_variant};
   bool same = p->graph_exec != nullptr;
-  for (int i = 0; i < 9; ++i) same = same && key[i] == p->graph_key[i];
+  for (int i = 0; i < 10; ++i) same = same && key[i] == p->graph_key[i];
   if (!same) {
     if (p->graph_exec) {
       cudaGraphExecDestroy(p->graph_exec);
@@ -544,7 +550,7 @@ fga_status fga_run_graph(fga_plan_t p, double* u_dev) {
       p->graph_exec = nullptr;
       return fail(p, FGA_ERR_CUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e), true);
     }
-    for (int i = 0; i < 9; ++i) p->graph_key[i] = key[i];
+    for (int i = 0; i < 10; ++i) p->graph_key[i] = key[i];
   }
   CUDA_OR_FAIL(p, cudaGraphLaunch(p->graph_exec, p->stream));
   p->launches += 12;
@@ -576,23 +582,29 @@ fga_status fga_autotune(fga_plan_t p, double* u_dev, int64_t* choice) {
   if (p->stage < 1) return fail(p, FGA_ERR_STATE, "fga_autotune before fga_decompose");
   if (!u_dev || !is_device_ptr(u_dev))
     return fail(p, FGA_ERR_INVALID, "fga_autotune writes to device memory only");
-  // 1. blocks per SM of the persistent ray kernel, timed on a short integration
-  const int max_sm = fga::ray_max_per_sm(p);
+  // 1. register budget and blocks per SM of the persistent ray kernel, timed on a short
+  //    integration
   const int64_t probe = std::min<int64_t>(p->nsteps, 64);
-  int best_sm = max_sm;
+  int best_variant = 0, best_sm = 0;
   float best = 3.0e38f;
   if (p->G > 0 && probe > 0) {
-    for (int per_sm = max_sm; per_sm >= 1 && per_sm >= max_sm - 3; --per_sm) {
-      p->ray_per_sm = per_sm;
-      p->ray_blocks = 0;
-      float ms = 0.0f;
-      CUDA_OR_FAIL(p, time_best(p, 2, [&] { return fga::launch_rays_steps(p, probe, false); }, &ms));
-      if (ms < best * 0.98f) {  // prefer more resident blocks unless clearly slower
-        best = ms;
-        best_sm = per_sm;
+    for (int variant = 0; variant < 2; ++variant) {
+      p->ray_variant = variant;
+      const int max_sm = fga::ray_max_per_sm(p);
+      for (int per_sm = max_sm; per_sm >= 1 && per_sm >= max_sm - 3; --per_sm) {
+        p->ray_per_sm = per_sm;
+        p->ray_blocks = 0;
+        float ms = 0.0f;
+        CUDA_OR_FAIL(p, time_best(p, 2, [&] { return fga::launch_rays_steps(p, probe, false); }, &ms));
+        if (ms < best * 0.98f) {  // prefer the earlier candidate unless clearly slower
+          best = ms;
+          best_sm = per_sm;
+          best_variant = variant;
+        }
       }
     }
   }
+  p->ray_variant = best_variant;
   p->ray_per_sm = best_sm;
   p->ray_blocks = 0;
   // 2. the full integration with the chosen launch shape
@@ -627,7 +639,8 @@ fga_status fga_autotune(fga_plan_t p, double* u_dev, int64_t* choice) {
   if (st != FGA_OK) return st;
   if (choice) {
     choice[0] = p->ray_per_sm;
-    choice[1] = p->seg;
+    choice[1] = p->precision == FGA_MIXED_TF32X3 ? fga::segment_len_tc(p) : fga::segment_len(p);
+    choice[2] = p->ray_variant;
   }
   return read_status(p);
 }
@@ -635,20 +648,22 @@ fga_status fga_autotune(fga_plan_t p, double* u_dev, int64_t* choice) {
 fga_status fga_tuning(fga_plan_t p, int64_t* choice) {
   if (!p || !choice) return fail(p, FGA_ERR_INVALID, "NULL plan or output");
   choice[0] = p->ray_per_sm;
-  choice[1] = p->seg > 0 ? p->seg
-                         : (p->precision == FGA_MIXED_TF32X3 ? fga::segment_len_tc(p)
-                                                              : fga::segment_len(p));
+  choice[1] = p->precision == FGA_MIXED_TF32X3 ? fga::segment_len_tc(p) : fga::segment_len(p);
+  choice[2] = p->ray_variant;
   return FGA_OK;
 }
 
 fga_status fga_set_tuning(fga_plan_t p, const int64_t* choice) {
   fga_status st = check_usable(p);
   if (st != FGA_OK) return st;
-  if (!choice || choice[0] < 0 || choice[0] > 64 || choice[1] < 0 || choice[1] > ((int64_t)1 << 20))
-    return fail(p, FGA_ERR_INVALID, "tuning values out of range (0 <= blocks/SM <= 64, 0 <= segment <= 2^20)");
+  if (!choice || choice[0] < 0 || choice[0] > 64 || choice[1] < 0 || choice[1] > ((int64_t)1 << 20) ||
+      choice[2] < 0 || choice[2] > 1)
+    return fail(p, FGA_ERR_INVALID,
+                "tuning values out of range (0 <= blocks/SM <= 64, 0 <= segment <= 2^20, variant 0 or 1)");
   p->ray_per_sm = (int)choice[0];
   p->ray_blocks = 0;
   p->seg = choice[1];
+  p->ray_variant = (int)choice[2];
   return FGA_OK;
 }
 
@@ -1012,6 +1027,7 @@ fga_status fga_grad(fga_plan_t p, const double* residual, double* grad) {
   }
   CUDA_OR_FAIL(p, grow(&p->d_part, &p->part_cap,
                        (size_t)(fga::adjoint_slices(p, nthr) * gd.npts)));
+  CUDA_OR_FAIL(p, grow(&p->d_adj_bucket, &p->adj_bucket_cap, (size_t)(p->nsteps / kseg + 2)));
   CUDA_OR_FAIL(p, fga::launch_adjoint(p, d_res, dst, p->d_adj_scratch, nthr, kseg, ncheck));
   if (host_out)
     CUDA_OR_FAIL(p, cudaMemcpyAsync(grad, dst, sizeof(double) * gd.npts, cudaMemcpyDeviceToHost,

@@ -173,41 +173,49 @@ template <int D, typename Fn>
 __device__ __forceinline__ void for_receivers_X(const GridDev& gd, const RxDev& rx, const double* Q,
                                                 const double* P, double cut, double inv_eps, Fn fn) {
   for (int64_t j = 0; j < rx.nruns; ++j) {
-    const int a = rx.run_axis[j];
+    // the run's axis is a runtime value: select with conditionals rather than index Q
+    // and P with it (a runtime index would move the ray state to local memory)
+    const bool a1 = D == 2 && rx.run_axis[j] == 1;
+    const double qa = a1 ? Q[D - 1] : Q[0], pa = a1 ? P[D - 1] : P[0];
     const double x0 = rx.run_geo[3 * j], dl = rx.run_geo[3 * j + 1];
     double fr = 1.0, fi = 0.0;  // factor of the coordinate across the run
     double e = 0.0;
     if constexpr (D == 2) {
-      e = rx.run_geo[3 * j + 2] - Q[1 - a];
+      const double qb = a1 ? Q[0] : Q[1], pb = a1 ? P[0] : P[1];
+      e = rx.run_geo[3 * j + 2] - qb;
       if (fabs(e) > cut) continue;
       double s, c;
-      sincos(P[1 - a] * e * inv_eps, &s, &c);
+      sincos(pb * e * inv_eps, &s, &c);
       const double g = exp(-0.5 * e * e * inv_eps);
       fr = g * c;
       fi = g * s;
     }
     const int64_t r0 = rx.run_off[j], n = rx.run_off[j + 1] - r0;
     // candidates, one beyond each end of the window
-    int64_t k0 = (int64_t)ceil((Q[a] - cut - x0) / dl) - 1;
-    int64_t k1 = (int64_t)floor((Q[a] + cut - x0) / dl) + 1;
+    int64_t k0 = (int64_t)ceil((qa - cut - x0) / dl) - 1;
+    int64_t k1 = (int64_t)floor((qa + cut - x0) / dl) + 1;
     k0 = k0 < 0 ? 0 : k0;
     k1 = k1 > n - 1 ? n - 1 : k1;
     if (k0 > k1) continue;
-    double u = fma((double)k0, dl, x0) - Q[a];
+    double u = fma((double)k0, dl, x0) - qa;
     double s, c;
-    sincos(P[a] * u * inv_eps, &s, &c);
+    sincos(pa * u * inv_eps, &s, &c);
     double g = exp(-0.5 * u * u * inv_eps);
     double xr = g * c * fr - g * s * fi, xi = g * c * fi + g * s * fr;
-    sincos(P[a] * dl * inv_eps, &s, &c);
+    sincos(pa * dl * inv_eps, &s, &c);
     g = exp(-(u * dl + 0.5 * dl * dl) * inv_eps);
     double rr = g * c, ri = g * s;
     const double rho = exp(-dl * dl * inv_eps);
     for (int64_t k = k0; k <= k1; ++k) {
-      u = fma((double)k, dl, x0) - Q[a];
+      u = fma((double)k, dl, x0) - qa;
       if (fabs(u) <= cut) {
         double d[D];
-        d[a] = u;
-        if constexpr (D == 2) d[1 - a] = e;
+        if constexpr (D == 2) {
+          d[0] = a1 ? e : u;
+          d[1] = a1 ? u : e;
+        } else {
+          d[0] = u;
+        }
         fn(r0 + k, d, make_double2(xr, xi));
       }
       const double nr = xr * rr - xi * ri, ni = xr * ri + xi * rr;
@@ -257,6 +265,19 @@ __device__ __forceinline__ void for_receivers_X(const GridDev& gd, const RxDev& 
   }
 }
 
+// Adds Re(e X(x_r)) to tr[r] for the receivers in the window of the Gaussian at (Q, P),
+// with reductions the thread does not wait for (an atomic add whose result is awaited
+// made trace recording about 8x slower).
+template <int D>
+__device__ __forceinline__ void add_traces(const GridDev& gd, const RxDev& rx, double cut, double inv_eps,
+                                        double q0, double q1, double p0, double p1, double er,
+                                        double ei, double* __restrict__ tr) {
+  const double Q[2] = {q0, q1}, P[2] = {p0, p1};
+  for_receivers_X<D>(gd, rx, Q, P, cut, inv_eps, [&](int64_t r, const double*, double2 X) {
+    red_add_f64(tr + r, er * X.x - ei * X.y);
+  });
+}
+
 // Contribution of one Gaussian (state y, weight psi) to the traces at record m:
 // Re(2 W a psi (2 pi eps)^{-3d/2} e^{iS/eps} exp(i P.d/eps - |d|^2/(2 eps))).
 template <int D>
@@ -272,10 +293,8 @@ __device__ __forceinline__ void record_traces(const GridDev& gd, const ShotDev& 
   sincos(y[Lo::S] * sh.inv_eps, &sn, &cs);
   const double er = pr * cs - pi * sn, ei = pr * sn + pi * cs;
   double* tr = traces + ((int64_t)s * rx.nrec + m) * rx.nrx;
-  for_receivers_X<D>(gd, rx, y + Lo::Q, y + Lo::P, cut, sh.inv_eps,
-                     [&](int64_t r, const double*, double2 X) {
-                       atomicAdd(tr + r, er * X.x - ei * X.y);
-                     });
+  add_traces<D>(gd, rx, cut, sh.inv_eps, y[Lo::Q], D == 2 ? y[Lo::Q + D - 1] : 0.0, y[Lo::P],
+                D == 2 ? y[Lo::P + D - 1] : 0.0, er, ei, tr);
 }
 
 }  // namespace fga

@@ -114,7 +114,7 @@ __device__ __forceinline__ void medium_ad(const GridDev& gd, const double* __res
 }
 
 // Transposed spline: adjoints (cb, gb, Kb) of (c, grad c, Hessian) at a point -> the
-// coefficient gradient (atomic) and the point's adjoint Qb.
+// coefficient gradient (added without waiting for the result) and the point's adjoint Qb.
 template <int D>
 __device__ __forceinline__ void medium_ad_transpose(const GridDev& gd, const MedAD<D>& m, double cb,
                                                     const double* gb, const double (*Kb)[D],
@@ -123,10 +123,9 @@ __device__ __forceinline__ void medium_ad_transpose(const GridDev& gd, const Med
     Qb[0] += cb * m.g[0] + gb[0] * m.K[0][0] + Kb[0][0] * m.T3[0];
     double ih = gd.inv_h[0];
 #pragma unroll
-    for (int a = 0; a < 4; ++a) {
-      double v = cb * m.w[0][a] + gb[0] * m.dw[0][a] * ih + Kb[0][0] * m.ddw[0][a] * ih * ih;
-      atomicAdd(gradC + m.idx[0][a], v);
-    }
+    for (int a = 0; a < 4; ++a)
+      red_add_f64(gradC + m.idx[0][a],
+                  cb * m.w[0][a] + gb[0] * m.dw[0][a] * ih + Kb[0][0] * m.ddw[0][a] * ih * ih);
   } else {
     const double kxz = Kb[0][1] + Kb[1][0];
     Qb[0] += cb * m.g[0] + gb[0] * m.K[0][0] + gb[1] * m.K[0][1] + Kb[0][0] * m.T3[0] +
@@ -140,9 +139,9 @@ __device__ __forceinline__ void medium_ad_transpose(const GridDev& gd, const Med
 #pragma unroll
       for (int b = 0; b < 4; ++b) {
         const double wb = m.w[1][b], db = m.dw[1][b] * iz, ddb = m.ddw[1][b] * iz * iz;
-        double v = cb * wa * wb + gb[0] * da * wb + gb[1] * wa * db + Kb[0][0] * dda * wb +
-                   kxz * da * db + Kb[1][1] * wa * ddb;
-        atomicAdd(gradC + m.idx[0][a] * gd.n[1] + m.idx[1][b], v);
+        red_add_f64(gradC + m.idx[0][a] * gd.n[1] + m.idx[1][b],
+                    cb * wa * wb + gb[0] * da * wb + gb[1] * wa * db + Kb[0][0] * dda * wb +
+                        kxz * da * db + Kb[1][1] * wa * ddb);
       }
     }
   }

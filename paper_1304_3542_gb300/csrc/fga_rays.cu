@@ -34,8 +34,11 @@ namespace {
 // soon as its ray has reached T (or left the grid for good), so the warps stay full
 // whatever the mix of ray lifetimes. Each ray's arithmetic does not depend on which
 // lane runs it, so the results are the same as with one thread per Gaussian.
-template <int D>
-__global__ void __launch_bounds__(128) k_rays(GridDev gd, const ShotDev* __restrict__ shots,
+// MINB = 1 lets the compiler use up to 255 registers per thread (2 blocks of 128 per SM
+// for the 2D kernel); MINB = 3 caps them at 168 for 3 resident blocks (a few spills).
+// The autotuner picks one.
+template <int D, int MINB>
+__global__ void __launch_bounds__(128, MINB) k_rays(GridDev gd, const ShotDev* __restrict__ shots,
                                               const double* __restrict__ C, int64_t G,
                                               const int32_t* __restrict__ gshot,
                                               const int64_t* __restrict__ gq,
@@ -47,7 +50,8 @@ __global__ void __launch_bounds__(128) k_rays(GridDev gd, const ShotDev* __restr
                                               unsigned long long* steps_done,
                                               unsigned long long* next, RxDev rx,
                                               double* __restrict__ trace_part, int64_t slice_len,
-                                              int slices, unsigned long long mult) {
+                                              int slices, unsigned long long mult,
+                                              int32_t* __restrict__ gsteps) {
   using Lo = Layout<D>;
   constexpr int NF = Lo::NF;
   // this block's private slice of the trace sums (no other block adds into it)
@@ -93,6 +97,7 @@ __global__ void __launch_bounds__(128) k_rays(GridDev gd, const ShotDev* __restr
       }
       if (done) {
         ok &= ray_store<D>(shots[s], g, y, gpsi, state, ld, coef);
+        gsteps[g] = (int32_t)step;
         my_steps += (unsigned long long)step;
         w = atomicAdd(next, 1ull);
         if (w >= (unsigned long long)G) break;
@@ -223,9 +228,11 @@ unsigned long long work_order_mult(int64_t G) {
 
 int ray_max_per_sm(fga_plan_s* p) {
   int per_sm = 0;
-  cudaError_t e = p->grid.dim == 1
-                      ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rays<1>, 128, 0)
-                      : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rays<2>, 128, 0);
+  const bool v3 = p->ray_variant == 1;
+  cudaError_t e =
+      p->grid.dim == 1
+          ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, v3 ? k_rays<1, 3> : k_rays<1, 1>, 128, 0)
+          : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, v3 ? k_rays<2, 3> : k_rays<2, 1>, 128, 0);
   return (e == cudaSuccess && per_sm > 0) ? per_sm : 1;
 }
 
@@ -298,18 +305,13 @@ cudaError_t launch_rays_steps(fga_plan_s* p, int64_t nsteps, bool record) {
     rx.every = 0;
   }
   const unsigned long long mult = work_order_mult(p->G);
-  if (p->grid.dim == 1)
-    k_rays<1><<<blocks, 128, 0, p->stream>>>(p->grid, p->d_shots, p->d_coef, p->G, p->d_gshot,
-                                             p->d_gq, p->d_gp, p->d_gpsi, nsteps, p->dt, p->kappa,
-                                             p->integrate_exited, p->d_state, (int64_t)p->g_cap,
-                                             p->d_gcoef, p->d_status, p->d_steps, p->d_steps + 1,
-                                             rx, p->d_part, len, (int)slices, mult);
-  else
-    k_rays<2><<<blocks, 128, 0, p->stream>>>(p->grid, p->d_shots, p->d_coef, p->G, p->d_gshot,
-                                             p->d_gq, p->d_gp, p->d_gpsi, nsteps, p->dt, p->kappa,
-                                             p->integrate_exited, p->d_state, (int64_t)p->g_cap,
-                                             p->d_gcoef, p->d_status, p->d_steps, p->d_steps + 1,
-                                             rx, p->d_part, len, (int)slices, mult);
+  auto kern = p->grid.dim == 1 ? (p->ray_variant == 1 ? k_rays<1, 3> : k_rays<1, 1>)
+                               : (p->ray_variant == 1 ? k_rays<2, 3> : k_rays<2, 1>);
+  kern<<<blocks, 128, 0, p->stream>>>(p->grid, p->d_shots, p->d_coef, p->G, p->d_gshot, p->d_gq,
+                                      p->d_gp, p->d_gpsi, nsteps, p->dt, p->kappa,
+                                      p->integrate_exited, p->d_state, (int64_t)p->g_cap,
+                                      p->d_gcoef, p->d_status, p->d_steps, p->d_steps + 1, rx,
+                                      p->d_part, len, (int)slices, mult, p->d_gsteps);
   p->launches += 1;
   e = cudaGetLastError();
   if (e != cudaSuccess || len == 0) return e;

@@ -30,6 +30,7 @@ constexpr int CH = 16;   // Gaussians per chunk (2D)
 constexpr int CH1 = 32;  // Gaussians per chunk (1D)
 constexpr int64_t SEG2 = 1024;  // default Gaussians per work item (2D)
 constexpr int64_t SEG1 = 512;   // default Gaussians per work item (1D)
+constexpr int64_t kPartialBudget = (int64_t)4 << 30;  // bytes of partial tiles at most
 
 // Pass 1 (FILL = false): number of Gaussians per tile. Pass 2 (FILL = true): the
 // ordered list, written at the tile's offset. One CTA per tile scans the shot's
@@ -82,13 +83,13 @@ __global__ void __launch_bounds__(NT) k_bin(GridDev gd, const ShotDev* __restric
 }
 
 // Per-axis factor of one Gaussian at grid index i (all images inside the window).
-__device__ __forceinline__ double2 axis_factor(const GridDev& gd, int k, int64_t i, double Q, double P,
+__device__ __forceinline__ double2 axis_factor(const Axis& ax, int64_t i, double Q, double P,
                                                double cut, double inv_eps) {
-  double x = gd.o[k] + (double)i * gd.h[k];
+  double x = ax.o + (double)i * ax.h;
   double re = 0.0, im = 0.0;
-  int lmax = gd.periodic[k] ? 2 : 0;
+  int lmax = ax.periodic ? 2 : 0;
   for (int l = -lmax; l <= lmax; ++l) {
-    double d = x - Q + l * gd.L[k];
+    double d = x - Q + l * ax.L;
     if (fabs(d) <= cut) {
       double gs = exp(-0.5 * d * d * inv_eps);
       double sn, cs;
@@ -174,7 +175,7 @@ __global__ void __launch_bounds__(NT) k_gather1(GridDev gd, const ShotDev* __res
     }
     __syncthreads();
     for (int j = 0; j < nc; ++j) {
-      double2 x = axis_factor(gd, 0, i, sQ[j], sP[j], cut, inv_eps);
+      double2 x = axis_factor(grid_axis(gd, 0), i, sQ[j], sP[j], cut, inv_eps);
       re = fma(sC[j].x, x.x, fma(-sC[j].y, x.y, re));
     }
     __syncthreads();
@@ -227,24 +228,26 @@ __global__ void __launch_bounds__(NT) k_gather2(GridDev gd, const ShotDev* __res
         double Q = state[axis * ld + g], P = state[(2 + axis) * ld + g];
         double2 cf = axis == 0 ? coef[g] : make_double2(1.0, 0.0);
         double2* dst = (axis == 0 ? Xs[gi] : Zs[gi]) + part * 8;
-        if (gd.periodic[axis]) {
+        const Axis ax = grid_axis(gd, axis);
+        const int64_t a_ax = axis == 0 ? a[0] : a[1];
+        if (ax.periodic) {
           for (int r = 0; r < 8; ++r) {
-            double2 f = axis_factor(gd, axis, a[axis] + part * 8 + r, Q, P, cut, inv_eps);
+            double2 f = axis_factor(ax, a_ax + part * 8 + r, Q, P, cut, inv_eps);
             dst[r] = make_double2(cf.x * f.x - cf.y * f.y, cf.x * f.y + cf.y * f.x);
           }
         } else {
-          double xi0 = gd.o[axis] + (double)(a[axis] + part * 8) * gd.h[axis];
-          axis_factors8(xi0, gd.h[axis], Q, P, cut, inv_eps, cf, dst);
+          double xi0 = ax.o + (double)(a_ax + part * 8) * ax.h;
+          axis_factors8(xi0, ax.h, Q, P, cut, inv_eps, cf, dst);
         }
         if (part == 0) {
-          if (gd.periodic[axis]) {
+          if (ax.periodic) {
             win[gi][2 * axis] = 0;
             win[gi][2 * axis + 1] = T2 - 1;
           } else {
             int64_t lo, hi;
-            window_range(gd, axis, Q, cut, lo, hi);
-            win[gi][2 * axis] = (int)((lo - a[axis]) > -1 ? (lo - a[axis]) : -1);
-            win[gi][2 * axis + 1] = (int)((hi - a[axis]) < T2 ? (hi - a[axis]) : T2);
+            window_range_ax(ax, Q, cut, lo, hi);
+            win[gi][2 * axis] = (int)((lo - a_ax) > -1 ? (lo - a_ax) : -1);
+            win[gi][2 * axis + 1] = (int)((hi - a_ax) < T2 ? (hi - a_ax) : T2);
           }
         }
       }
@@ -335,8 +338,15 @@ cudaError_t launch_binning_fill(fga_plan_s* p) {
   return cudaGetLastError();
 }
 
+// Gaussians per work item: the tuned or default length, raised when needed so that the
+// partial tiles (one per work item, sized for the tile lists' capacity) stay within
+// kPartialBudget bytes.
 int64_t segment_len(fga_plan_s* p) {
-  return p->seg > 0 ? p->seg : (p->grid.dim == 1 ? SEG1 : SEG2);
+  const int64_t want = p->seg > 0 ? p->seg : (p->grid.dim == 1 ? SEG1 : SEG2);
+  const int64_t tile_bytes = (int64_t)tile_points(p->grid.dim) * (int64_t)sizeof(double);
+  const int64_t items = std::max<int64_t>(kPartialBudget / tile_bytes - p->ntiles, 1);
+  const int64_t floor_len = ((int64_t)p->list_cap + items - 1) / items;
+  return std::max<int64_t>(want, floor_len);
 }
 
 size_t partial_items(fga_plan_s* p) {
@@ -444,24 +454,26 @@ __global__ void __launch_bounds__(NT) k_gather2_tile_add(GridDev gd, const ShotD
         double Q = state[axis * ld + g], P = state[(2 + axis) * ld + g];
         double2 cf = axis == 0 ? coef[g] : make_double2(1.0, 0.0);
         double2* dst = (axis == 0 ? Xs[gi] : Zs[gi]) + part * 8;
-        if (gd.periodic[axis]) {
+        const Axis ax = grid_axis(gd, axis);
+        const int64_t a_ax = axis == 0 ? a[0] : a[1];
+        if (ax.periodic) {
           for (int r = 0; r < 8; ++r) {
-            double2 f = axis_factor(gd, axis, a[axis] + part * 8 + r, Q, P, cut, inv_eps);
+            double2 f = axis_factor(ax, a_ax + part * 8 + r, Q, P, cut, inv_eps);
             dst[r] = make_double2(cf.x * f.x - cf.y * f.y, cf.x * f.y + cf.y * f.x);
           }
         } else {
-          double xi0 = gd.o[axis] + (double)(a[axis] + part * 8) * gd.h[axis];
-          axis_factors8(xi0, gd.h[axis], Q, P, cut, inv_eps, cf, dst);
+          double xi0 = ax.o + (double)(a_ax + part * 8) * ax.h;
+          axis_factors8(xi0, ax.h, Q, P, cut, inv_eps, cf, dst);
         }
         if (part == 0) {
-          if (gd.periodic[axis]) {
+          if (ax.periodic) {
             win[gi][2 * axis] = 0;
             win[gi][2 * axis + 1] = T2 - 1;
           } else {
             int64_t lo, hi;
-            window_range(gd, axis, Q, cut, lo, hi);
-            win[gi][2 * axis] = (int)((lo - a[axis]) > -1 ? (lo - a[axis]) : -1);
-            win[gi][2 * axis + 1] = (int)((hi - a[axis]) < T2 ? (hi - a[axis]) : T2);
+            window_range_ax(ax, Q, cut, lo, hi);
+            win[gi][2 * axis] = (int)((lo - a_ax) > -1 ? (lo - a_ax) : -1);
+            win[gi][2 * axis + 1] = (int)((hi - a_ax) < T2 ? (hi - a_ax) : T2);
           }
         }
       }
@@ -521,7 +533,7 @@ __global__ void __launch_bounds__(NT) k_gather1_tile_add(GridDev gd, const ShotD
     }
     __syncthreads();
     for (int j = 0; j < nc; ++j) {
-      double2 x = axis_factor(gd, 0, i, sQ[j], sP[j], cut, inv_eps);
+      double2 x = axis_factor(grid_axis(gd, 0), i, sQ[j], sP[j], cut, inv_eps);
       re = fma(sC[j].x, x.x, fma(-sC[j].y, x.y, re));
     }
     __syncthreads();

@@ -46,41 +46,65 @@ __device__ __forceinline__ float tf32_head(float v) {
   return __uint_as_float(__float_as_uint(v) & 0xFFFFE000u);
 }
 
-// Factors of one Gaussian at 16 consecutive points of one axis, written to the operand
-// tiles as (re, im) or (re, -im) at column pair k = 2 gi.
-__device__ __forceinline__ void factors16(double x0, double h, double Q, double P, double cut,
-                                          double inv_eps, float2 cf, bool conj_im, int row0, int k,
-                                          float* hi, float* lo) {
-  const double two_pi = 6.283185307179586;
-  double d0 = x0 - Q;
-  // phase at the run's first point and per step, as fractions of a turn (FP64)
-  double t0 = P * d0 * inv_eps / two_pi, td = P * h * inv_eps / two_pi;
+// Per (Gaussian, axis) of a chunk: what every thread needs to make that Gaussian's
+// factor at its own row of the tile.
+struct Anchor {
+  uint32_t u0, ud;  // phase at the tile's first point and per point, as fractions of a turn
+  float d0, h;      // offset of the first point from Q, and the spacing
+  int lo, hi;       // rows inside the window |d| <= cut (empty when lo > hi)
+  float2 cf;        // coefficient (x axis) or 1 (z axis)
+};
+
+// The anchor of one Gaussian on one axis of the tile starting at x0 (FP64: the phase
+// P (x0 - Q)/eps and its per-point step P h/eps as 32-bit fractions of a turn, so that
+// the phase at row r is the exact wrap-around sum u0 + r ud).
+__device__ __forceinline__ Anchor make_anchor(double x0, double h, double Q, double P, double cut,
+                                              double inv_eps, float2 cf) {
+  const double inv_two_pi = 0.15915494309189535;
+  const double d0 = x0 - Q;
+  double t0 = P * d0 * inv_eps * inv_two_pi, td = P * h * inv_eps * inv_two_pi;
   t0 -= floor(t0);
   td -= floor(td);
-  uint32_t u0 = (uint32_t)(long long)(t0 * 4294967296.0);
-  uint32_t ud = (uint32_t)(long long)(td * 4294967296.0);
-  const float fd0 = (float)d0, fh = (float)h, fcut = (float)cut, fie = (float)inv_eps;
+  Anchor an;
+  an.u0 = (uint32_t)(unsigned long long)floor(t0 * 4294967296.0 + 0.5);
+  an.ud = (uint32_t)(unsigned long long)floor(td * 4294967296.0 + 0.5);
+  an.d0 = (float)d0;
+  an.h = (float)h;
+  double lo = ceil((-cut - d0) / h), hi = floor((cut - d0) / h);
+  lo = lo < 0.0 ? 0.0 : lo;
+  hi = hi > (double)(TM - 1) ? (double)(TM - 1) : hi;
+  an.lo = (int)lo;
+  an.hi = (int)hi;
+  an.cf = cf;
+  return an;
+}
+
+__device__ __forceinline__ Anchor make_empty_anchor() {
+  Anchor an;
+  an.u0 = an.ud = 0u;
+  an.d0 = an.h = 0.f;
+  an.lo = 1;
+  an.hi = 0;
+  an.cf = make_float2(0.f, 0.f);
+  return an;
+}
+
+// Factor of a Gaussian at row r: cf * exp(i phase - d^2/(2 eps)) (0 outside the window).
+__device__ __forceinline__ float2 row_factor(const Anchor& an, int r, float inv_eps) {
+  if (r < an.lo || r > an.hi) return make_float2(0.f, 0.f);
   const float ang_scale = 1.4629180792671596e-09f;  // 2 pi / 2^32
-#pragma unroll 4
-  for (int r = 0; r < 16; ++r) {
-    float d = fmaf((float)r, fh, fd0);
-    float re = 0.f, im = 0.f;
-    if (fabsf(d) <= fcut) {
-      float gs = __expf(-0.5f * d * d * fie);
-      float sn, cs;
-      __sincosf((float)(int32_t)(u0 + (uint32_t)r * ud) * ang_scale, &sn, &cs);
-      float fr = gs * cs, fi = gs * sn;
-      re = cf.x * fr - cf.y * fi;
-      im = cf.x * fi + cf.y * fr;
-    }
-    if (conj_im) im = -im;
-    float rh = tf32_head(re), ih = tf32_head(im);
-    int o = core_offset(row0 + r, k);
-    hi[o] = rh;
-    lo[o] = re - rh;
-    hi[o + 1] = ih;  // k + 1 stays in the same core row (k even)
-    lo[o + 1] = im - ih;
-  }
+  const float d = fmaf((float)r, an.h, an.d0);
+  const float gs = __expf(-0.5f * d * d * inv_eps);
+  float sn, cs;
+  __sincosf((float)(int32_t)(an.u0 + (uint32_t)r * an.ud) * ang_scale, &sn, &cs);
+  const float fr = gs * cs, fi = gs * sn;
+  return make_float2(an.cf.x * fr - an.cf.y * fi, an.cf.x * fi + an.cf.y * fr);
+}
+
+__device__ __forceinline__ void store_split4(float* hi, float* lo, int o, float4 v) {
+  const float4 h = make_float4(tf32_head(v.x), tf32_head(v.y), tf32_head(v.z), tf32_head(v.w));
+  *reinterpret_cast<float4*>(hi + o) = h;
+  *reinterpret_cast<float4*>(lo + o) = make_float4(v.x - h.x, v.y - h.y, v.z - h.z, v.w - h.w);
 }
 
 __global__ void __launch_bounds__(NTC) k_gather_tc(GridDev gd, const ShotDev* __restrict__ shots,
@@ -123,28 +147,44 @@ __global__ void __launch_bounds__(NTC) k_gather_tc(GridDev gd, const ShotDev* __
   const uint32_t idesc = tc::idesc_f32acc(tc::kFmtTF32, TM, TM);
   const int64_t l0 = min(off[t], list_cap) + (w - seg_off[t]) * seg;
   const int64_t l1 = min(min(off[t + 1], list_cap), l0 + seg);
-  const int gi = tid >> 3, part = tid & 7;
+  __shared__ Anchor anc[2][CHG];  // [axis][Gaussian of the chunk]
+  const float inv_eps_f = (float)inv_eps;
   uint32_t chunks = 0;
   bool ok = true;
   for (int64_t c0 = l0; c0 < l1; c0 += CHG) {
-    if (chunks > 0) ok &= tc::mbar_wait_bounded(bar, (chunks - 1) & 1u, kMaxTries);
     const int nc = (int)((l1 - c0) < CHG ? (l1 - c0) : CHG);
-    if (gi < nc) {
-      int32_t g = list[c0 + gi];
-      double Qx = state[0 * ld + g], Qz = state[1 * ld + g];
-      double Px = state[2 * ld + g], Pz = state[3 * ld + g];
-      double2 c = coef[g];
-      float2 cf = make_float2((float)c.x, (float)c.y);
-      factors16(gd.o[0] + (double)(a[0] + 16 * part) * gd.h[0], gd.h[0], Qx, Px, cut, inv_eps, cf,
-                true, 16 * part, 2 * gi, Ahi, Alo);
-      factors16(gd.o[1] + (double)(a[1] + 16 * part) * gd.h[1], gd.h[1], Qz, Pz, cut, inv_eps,
-                make_float2(1.f, 0.f), false, 16 * part, 2 * gi, Bhi, Blo);
-    } else {
-      for (int r = 0; r < 16; ++r) {
-        int o = core_offset(16 * part + r, 2 * gi);
-        Ahi[o] = Alo[o] = Ahi[o + 1] = Alo[o + 1] = 0.f;
-        Bhi[o] = Blo[o] = Bhi[o + 1] = Blo[o + 1] = 0.f;
+    // anchors: thread 2 gi + axis (the previous chunk's MMAs read only the operands)
+    if (tid < 2 * CHG) {
+      const int gi = tid >> 1, axis = tid & 1;
+      Anchor an = make_empty_anchor();
+      if (gi < nc) {
+        const int32_t g = list[c0 + gi];
+        const double Q = state[axis * ld + g], P = state[(2 + axis) * ld + g];
+        float2 cf = make_float2(1.f, 0.f);
+        if (axis == 0) {
+          const double2 c = coef[g];
+          cf = make_float2((float)c.x, (float)c.y);
+        }
+        const double x0 = axis == 0 ? gd.o[0] + (double)a[0] * gd.h[0] : gd.o[1] + (double)a[1] * gd.h[1];
+        an = make_anchor(x0, axis == 0 ? gd.h[0] : gd.h[1], Q, P, cut, inv_eps, cf);
       }
+      if (chunks > 0) ok &= tc::mbar_wait_bounded(bar, (chunks - 1) & 1u, kMaxTries);
+      anc[axis][gi] = an;
+    } else if (chunks > 0) {
+      ok &= tc::mbar_wait_bounded(bar, (chunks - 1) & 1u, kMaxTries);
+    }
+    __syncthreads();
+    // operands: thread = row of the tile (x for A, z for B), four K values per store
+    // A[x][2g] = Re X_g, A[x][2g+1] = -Im X_g; B[z][2g] = Re Z_g, B[z][2g+1] = Im Z_g
+#pragma unroll
+    for (int gp = 0; gp < CHG / 2; ++gp) {
+      const float2 x0 = row_factor(anc[0][2 * gp], tid, inv_eps_f);
+      const float2 x1 = row_factor(anc[0][2 * gp + 1], tid, inv_eps_f);
+      const float2 z0 = row_factor(anc[1][2 * gp], tid, inv_eps_f);
+      const float2 z1 = row_factor(anc[1][2 * gp + 1], tid, inv_eps_f);
+      const int o = core_offset(tid, 4 * gp);
+      store_split4(Ahi, Alo, o, make_float4(x0.x, -x0.y, x1.x, -x1.y));
+      store_split4(Bhi, Blo, o, make_float4(z0.x, z0.y, z1.x, z1.y));
     }
     tc::fence_proxy_async_smem();
     __syncthreads();
@@ -223,7 +263,15 @@ __global__ void k_segments_tc(const int64_t* __restrict__ off, int64_t ntiles, i
 
 int tile_edge_tc() { return TM; }
 
-int64_t segment_len_tc(fga_plan_s* p) { return p->seg > 0 ? p->seg : SEGM; }
+// Gaussians per work item, raised when needed to keep the FP32 partial tiles within
+// 4 GiB (see segment_len).
+int64_t segment_len_tc(fga_plan_s* p) {
+  const int64_t want = p->seg > 0 ? p->seg : SEGM;
+  const int64_t tile_bytes = (int64_t)TM * TM * (int64_t)sizeof(float);
+  const int64_t items = std::max<int64_t>((((int64_t)4 << 30) / tile_bytes) - p->ntiles, 1);
+  const int64_t floor_len = ((int64_t)p->list_cap + items - 1) / items;
+  return std::max<int64_t>(want, floor_len);
+}
 
 size_t partial_items_tc(fga_plan_s* p) {
   const int64_t seg = segment_len_tc(p);

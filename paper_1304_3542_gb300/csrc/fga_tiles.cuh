@@ -18,6 +18,32 @@ __device__ __forceinline__ int shot_of_tile(const ShotDev* shots, int nshots, in
 
 // Window of Gaussian (Q, cut) along one axis as a conservative grid-index range,
 // for the image shifted by l periods.
+// One axis of the grid picked by a runtime index with conditionals (indexing the grid's
+// arrays with a runtime value would put the kernel parameter block in local memory).
+struct Axis {
+  double o, h, inv_h, L;
+  int64_t n;
+  int periodic;
+};
+
+__device__ __forceinline__ Axis grid_axis(const GridDev& gd, int k) {
+  const bool k1 = k == 1 && kMaxDim > 1;
+  Axis ax;
+  ax.o = k1 ? gd.o[kMaxDim - 1] : gd.o[0];
+  ax.h = k1 ? gd.h[kMaxDim - 1] : gd.h[0];
+  ax.inv_h = k1 ? gd.inv_h[kMaxDim - 1] : gd.inv_h[0];
+  ax.L = k1 ? gd.L[kMaxDim - 1] : gd.L[0];
+  ax.n = k1 ? gd.n[kMaxDim - 1] : gd.n[0];
+  ax.periodic = k1 ? gd.periodic[kMaxDim - 1] : gd.periodic[0];
+  return ax;
+}
+
+__device__ __forceinline__ void window_range_ax(const Axis& ax, double Q, double cut, int64_t& lo,
+                                                int64_t& hi) {
+  lo = (int64_t)floor((Q - cut - ax.o) * ax.inv_h) - 1;
+  hi = (int64_t)ceil((Q + cut - ax.o) * ax.inv_h) + 1;
+}
+
 __device__ __forceinline__ void window_range(const GridDev& gd, int k, double Q, double cut,
                                              int64_t& lo, int64_t& hi) {
   lo = (int64_t)floor((Q - cut - gd.o[k]) * gd.inv_h[k]) - 1;

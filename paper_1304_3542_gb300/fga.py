@@ -239,20 +239,20 @@ class Plan:
         return out
 
     def autotune(self, out):
-        """Tune the ray launch shape and the gather's segment length on this plan's data,
-        then propagate and reconstruct into the device tensor out. Returns the choice
-        (blocks per SM, segment length)."""
-        ch = np.zeros(2, dtype=np.int64)
+        """Tune the ray kernel (blocks per SM, register budget) and the gather's segment
+        length on this plan's data, then propagate and reconstruct into the device tensor
+        out. Returns the choice (blocks per SM, segment length, ray kernel variant)."""
+        ch = np.zeros(3, dtype=np.int64)
         self._check(self._L.fga_autotune(self._h, _ptr(out), ch.ctypes.data), "fga_autotune")
-        return int(ch[0]), int(ch[1])
+        return tuple(int(v) for v in ch)
 
     def tuning(self):
-        ch = np.zeros(2, dtype=np.int64)
+        ch = np.zeros(3, dtype=np.int64)
         self._check(self._L.fga_tuning(self._h, ch.ctypes.data), "fga_tuning")
-        return int(ch[0]), int(ch[1])
+        return tuple(int(v) for v in ch)
 
-    def set_tuning(self, blocks_per_sm: int, segment: int):
-        ch = np.array([blocks_per_sm, segment], dtype=np.int64)
+    def set_tuning(self, blocks_per_sm: int, segment: int, variant: int = 0):
+        ch = np.array([blocks_per_sm, segment, variant], dtype=np.int64)
         self._check(self._L.fga_set_tuning(self._h, ch.ctypes.data), "fga_set_tuning")
 
     def sync(self):

@@ -2,7 +2,7 @@
 
   python -m paper_1304_3542_gb300.run_case [--workload layered_single] [--T 0.1]
                                            [--tau 1e-3] [--repeat 1] [--nshots 4]
-                                           [--precision fp64|mixed] [--receivers]
+                                           [--precision fp64|mixed] [--receivers] [--grad]
 
 A small driver for trying the library on the seeded workloads (and the command
 the kernel profiles are taken with).
@@ -32,6 +32,8 @@ def main():
     ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64")
     ap.add_argument("--receivers", action="store_true",
                     help="record traces at 368 surface receivers every 4 ms (layered model)")
+    ap.add_argument("--grad", action="store_true",
+                    help="with --receivers: also the adjoint dJ/dc for J = 1/2 |traces|^2")
     args = ap.parse_args()
     kw = {}
     if args.T is not None:
@@ -55,10 +57,15 @@ def main():
         plan.propagate()
         plan.reconstruct(out)
         plan.sync()
+    extra = {}
+    if args.receivers and args.grad:
+        tr = plan.traces()
+        g = plan.grad(np.ascontiguousarray(tr))
+        extra = {"grad_max": float(np.abs(g).max())}
     times, launches = plan.stage_times()
     print(json.dumps({"workload": args.workload, "counts": counts.tolist(),
                       "stage_ms": {k: float(v) for k, v in times.items()},
-                      "launches": launches, "field_norm": float(out.norm())}))
+                      "launches": launches, "field_norm": float(out.norm()), **extra}))
     plan.close()
 
 

@@ -138,12 +138,12 @@ def test_autotune_choice_and_results(precision):
         ref_state = ref_plan.state(0)
         tuned_plan = fresh()
         out = torch.zeros(shape, dtype=torch.float64, device="cuda")
-        per_sm, seg = tuned_plan.autotune(out)
+        per_sm, seg, variant = tuned_plan.autotune(out)
         tuned_plan.sync()
-    assert tuned_plan.tuning() == (per_sm, seg)
-    assert 1 <= per_sm <= 64
+    assert tuned_plan.tuning() == (per_sm, seg, variant)
+    assert 1 <= per_sm <= 64 and variant in (0, 1)
     base = 512 if precision == F.FGA_MIXED_TF32X3 else 256
-    assert seg in [base << k for k in range(5)]
+    assert seg in [base << k for k in range(5)]  # a small case: no raise for memory
     st = tuned_plan.state(0)
     for k in ref_state:
         assert np.array_equal(st[k], ref_state[k]), k
@@ -152,7 +152,7 @@ def test_autotune_choice_and_results(precision):
     assert np.linalg.norm(u_tuned - u_ref) <= tol * np.linalg.norm(u_ref)
     with torch.cuda.stream(stream):
         again = fresh()
-        again.set_tuning(per_sm, seg)
+        again.set_tuning(per_sm, seg, variant)
         out2 = torch.zeros(shape, dtype=torch.float64, device="cuda")
         again.propagate()
         again.reconstruct(out2)
@@ -162,3 +162,5 @@ def test_autotune_choice_and_results(precision):
         again.set_tuning(-1, 0)
     with pytest.raises(F.FGAError):
         again.set_tuning(2, 1 << 21)
+    with pytest.raises(F.FGAError):
+        again.set_tuning(2, 1024, 2)
