@@ -65,7 +65,8 @@ typedef enum {
 } fga_precision;
 
 typedef struct {
-  int dim;            /* 1 or 2 */
+  int dim;            /* 1, 2 or 3 (3: FP64 only, boxes of at most 64 points per axis,
+                         no receivers) */
   int64_t n[3];       /* grid points per axis (>= 4) */
   double h[3];        /* grid spacing per axis (> 0) */
   double origin[3];   /* first grid point per axis */
@@ -130,7 +131,8 @@ fga_status fga_propagate(fga_plan_t plan);
 fga_status fga_reconstruct(fga_plan_t plan, double* u_out);
 
 /* Receivers for traces: the field of Eq. recons (Re u, as fga_reconstruct writes it)
- * at the points xr (host or device, [nrx][dim] FP64, inside the grid, open axes only)
+ * at the points xr (host or device, [nrx][dim] FP64, inside the grid, open axes only;
+ * 1D and 2D)
  * at the record times t_m = m * record_every * dt, m = 0 .. T/(record_every dt)
  * (record_every must divide T/dt). fga_propagate then accumulates the traces while it
  * integrates the rays. nrx = 0 removes the receivers. Errors: FGA_ERR_INVALID,
@@ -257,7 +259,7 @@ fga_status fga_stage_times(fga_plan_t plan, double* ms5, int64_t* launches);
  * axes). With coef_g = 2 W a_g psi_g (2 pi eps)^{-3d/2} exp(i S_g/eps) this is the
  * field fga_reconstruct writes for one shot.
  *
- * dim, n, h, origin, periodic: the output grid (as in fga_config); eps, kappa > 0.
+ * dim (1 or 2), n, h, origin, periodic: the output grid (as in fga_config); eps, kappa > 0.
  * qp: device, [2*dim][nG] FP64: rows Q_0..Q_{dim-1} then P_0..P_{dim-1}.
  * coef: device, [nG][2] FP64 (re, im). u: device, [n...] FP64, overwritten.
  * stream: a cudaStream_t (NULL = legacy default stream).

@@ -148,7 +148,7 @@ fga_status fga_destroy(fga_plan_t p) {
                   p->d_max2, p->d_blk, p->d_counts, p->d_blk_first, p->d_gshot, p->d_gq, p->d_gp,
                   p->d_gpsi, p->d_state, p->d_gcoef, p->d_tile_cnt, p->d_tile_off,
                   p->d_tile_list, p->d_seg_off, p->d_partial, p->d_out, p->d_status,
-                  p->d_steps, p->d_rx, p->d_rx_off, p->d_rx_perm, p->d_traces, p->d_gsteps,
+                  p->d_steps, p->d_rx, p->d_rx_off, p->d_rx_perm, p->d_traces, p->d_gsteps, p->d_g2,
                   p->d_adj_order, p->d_adj_bucket,
                   p->d_run_geo, p->d_run_axis, p->d_run_off, p->d_resid_int,
                   p->d_psi_f1, p->d_gpsi_f1, p->d_adj_scratch, p->d_grad, p->d_resid,
@@ -169,7 +169,7 @@ fga_status fga_plan(const fga_config* cfg, const double* velocity, void* stream,
   *out = nullptr;
   if (!cfg || !velocity) return fail(nullptr, FGA_ERR_INVALID, "cfg or velocity is NULL");
   const int d = cfg->dim;
-  if (d < 1 || d > fga::kMaxDim) return fail(nullptr, FGA_ERR_INVALID, "dim must be 1 or 2");
+  if (d < 1 || d > fga::kMaxDim) return fail(nullptr, FGA_ERR_INVALID, "dim must be 1, 2 or 3");
   if (cfg->nshots < 1 || cfg->nshots > fga::kMaxShots)
     return fail(nullptr, FGA_ERR_INVALID, "nshots out of range");
   if (!cfg->eps) return fail(nullptr, FGA_ERR_INVALID, "eps is NULL");
@@ -266,6 +266,10 @@ fga_status fga_plan(const fga_config* cfg, const double* velocity, void* stream,
         delete p;
         return fail(nullptr, FGA_ERR_INVALID, "box must be even, >= 2 and <= 4096");
       }
+      if (d == 3 && nbk > 64) {
+        delete p;
+        return fail(nullptr, FGA_ERR_INVALID, "in 3D the box must be at most 64 points per axis");
+      }
       sh.s[k] = sk;
       sh.nb[k] = nbk;
       sh.nq[k] = gd.periodic[k] ? gd.n[k] / sk : (gd.n[k] - 1) / sk + 1;
@@ -306,9 +310,13 @@ fga_status fga_plan(const fga_config* cfg, const double* velocity, void* stream,
     fga_destroy(p);
     return fail(nullptr, FGA_ERR_INVALID, "velocity must be finite and > 0 everywhere");
   }
-  PLAN_CUDA(cudaMalloc(&p->d_medtab, sizeof(double) * fga::medium_table_doubles(p->grid)));
-  p->grid.tab = p->d_medtab;
-  PLAN_CUDA(fga::launch_medium_table(p));
+  if (d == 3) {
+    p->grid.tab = p->d_coef;  // 3D: the ray kernels read the samples (64-tap form)
+  } else {
+    PLAN_CUDA(cudaMalloc(&p->d_medtab, sizeof(double) * fga::medium_table_doubles(p->grid)));
+    p->grid.tab = p->d_medtab;
+    PLAN_CUDA(fga::launch_medium_table(p));
+  }
   PLAN_CUDA(cudaMemsetAsync(p->d_status, 0, sizeof(int), p->stream));
   p->E.assign((size_t)cfg->nshots * d, nullptr);
   for (int s = 0; s < cfg->nshots; ++s) {
@@ -360,7 +368,7 @@ fga_status fga_decompose(fga_plan_t p, const double* u0, const double* u1, int64
                                   cudaMemcpyDeviceToHost, p->stream));
   CUDA_OR_FAIL(p, cudaStreamSynchronize(p->stream));
   // active q rectangle per shot: q whose box meets the data's bounding box
-  int64_t psi_total = 0, g1_total = 0;
+  int64_t psi_total = 0, g1_total = 0, g2_total = 0;
   p->blk_first.assign(p->nshots + 1, 0);
   for (int s = 0; s < p->nshots; ++s) {
     ShotDev& sh = p->shots[s];
@@ -389,11 +397,19 @@ fga_status fga_decompose(fga_plan_t p, const double* u0, const double* u1, int64
     sh.psi_len = qt * sh.np;
     psi_total += ((sh.psi_len + fga::kScanBlock - 1) / fga::kScanBlock) * fga::kScanBlock;
     p->blk_first[s] = sh.psi_off / fga::kScanBlock;
-    if (d == 2) {
+    if (d >= 2) {
       sh.row_lo = (int64_t)sh.s[0] * sh.qlo[0] - sh.nb[0] / 2;
       sh.nrows = sh.qn[0] > 0 ? (int64_t)sh.s[0] * (sh.qn[0] - 1) + sh.nb[0] : 0;
       sh.g1_off = g1_total;
-      g1_total += 2 * sh.nrows * sh.qn[1] * sh.nb[1];
+    }
+    if (d == 2) g1_total += 2 * sh.nrows * sh.qn[1] * sh.nb[1];
+    if (d == 3) {
+      sh.row_lo1 = (int64_t)sh.s[1] * sh.qlo[1] - sh.nb[1] / 2;
+      sh.nrows1 = sh.qn[1] > 0 ? (int64_t)sh.s[1] * (sh.qn[1] - 1) + sh.nb[1] : 0;
+      // stage 1: [field][x row][y row][q_z][p_z]; stage 2: [field][x row][q_y][q_z][p_y][p_z]
+      g1_total += 2 * sh.nrows * sh.nrows1 * sh.qn[2] * sh.nb[2];
+      sh.g2_off = g2_total;
+      g2_total += 2 * sh.nrows * sh.qn[1] * sh.qn[2] * sh.nb[1] * sh.nb[2];
     }
     sh.g_off = sh.g_cnt = 0;
   }
@@ -401,7 +417,8 @@ fga_status fga_decompose(fga_plan_t p, const double* u0, const double* u1, int64
   p->nblocks = psi_total / fga::kScanBlock;
   CUDA_OR_FAIL(p, grow(&p->d_psi, &p->psi_cap, (size_t)psi_total));
   CUDA_OR_FAIL(p, grow(&p->d_psi_f1, &p->psi_f1_cap, (size_t)psi_total));
-  if (d == 2) CUDA_OR_FAIL(p, grow(&p->d_g1, &p->g1_cap, (size_t)g1_total));
+  if (d >= 2) CUDA_OR_FAIL(p, grow(&p->d_g1, &p->g1_cap, (size_t)g1_total));
+  if (d == 3) CUDA_OR_FAIL(p, grow(&p->d_g2, &p->g2_cap, (size_t)g2_total));
   CUDA_OR_FAIL(p, grow(&p->d_blk, &p->blk_cap, (size_t)p->nblocks + 1));
   CUDA_OR_FAIL(p, cudaMemcpyAsync(p->d_blk_first, p->blk_first.data(),
                                   sizeof(int64_t) * (p->nshots + 1), cudaMemcpyHostToDevice, p->stream));
@@ -741,9 +758,13 @@ fga_status fga_psi(fga_plan_t p, int shot, double* psi_host, double* max_abs) {
       int64_t qf;
       if (d == 1) {
         qf = sh.qlo[0] + ql;
-      } else {
+      } else if (d == 2) {
         int64_t mx = ql / sh.qn[1], mz = ql % sh.qn[1];
         qf = (sh.qlo[0] + mx) * sh.nq[1] + sh.qlo[1] + mz;
+      } else {
+        const int64_t qn12 = sh.qn[1] * sh.qn[2];
+        int64_t mx = ql / qn12, my = (ql % qn12) / sh.qn[2], mz = ql % sh.qn[2];
+        qf = ((sh.qlo[0] + mx) * sh.nq[1] + sh.qlo[1] + my) * sh.nq[2] + sh.qlo[2] + mz;
       }
       std::memcpy(psi_host + 2 * qf * sh.np, seg.data() + 2 * ql * sh.np, sizeof(double) * 2 * sh.np);
     }
@@ -853,6 +874,7 @@ fga_status fga_set_receivers(fga_plan_t p, int64_t nrx, const double* xr, int64_
     return fail(p, FGA_ERR_INVALID, "need 0 < nrx < 2^31 and receiver positions");
   if (record_every < 1 || p->nsteps % record_every != 0)
     return fail(p, FGA_ERR_INVALID, "record_every must be >= 1 and divide T/dt");
+  if (d == 3) return fail(p, FGA_ERR_INVALID, "receivers (traces, fga_grad) are supported in 1D and 2D");
   for (int k = 0; k < d; ++k)
     if (gd.periodic[k]) return fail(p, FGA_ERR_INVALID, "receivers need open axes");
   std::vector<double> x((size_t)nrx * d);

@@ -89,6 +89,13 @@ __device__ __forceinline__ double psi_plus(const ShotDev& sh, int64_t jp, double
     int64_t m = jp - sh.nb[0] / 2;
     valid = (jp != 0) && (m != 0);
     pn = fabs((double)m) * sh.pscale[0];
+  } else if constexpr (D == 3) {
+    const int64_t nb12 = (int64_t)sh.nb[1] * sh.nb[2];
+    const int64_t j0 = jp / nb12, j1 = (jp - j0 * nb12) / sh.nb[2], j2 = jp - j0 * nb12 - j1 * sh.nb[2];
+    const int64_t m0 = j0 - sh.nb[0] / 2, m1 = j1 - sh.nb[1] / 2, m2 = j2 - sh.nb[2] / 2;
+    valid = j0 != 0 && j1 != 0 && j2 != 0 && !(m0 == 0 && m1 == 0 && m2 == 0);
+    const double a = (double)m0 * sh.pscale[0], b = (double)m1 * sh.pscale[1], c = (double)m2 * sh.pscale[2];
+    pn = sqrt(a * a + b * b + c * c);
   } else {
     int64_t j0 = jp / sh.nb[1], j1 = jp - j0 * sh.nb[1];
     int64_t m0 = j0 - sh.nb[0] / 2, m1 = j1 - sh.nb[1] / 2;
@@ -352,6 +359,132 @@ __global__ void __launch_bounds__(NT) k_fbi_stage2(GridDev gd, const ShotDev* __
 }
 
 // ---------------------------------------------------------------------------
+// 3D: three separable stages over all active q of a shot, one thread per output
+// entry (FP64; boxes of at most 64 points per axis):
+//   stage 1 (z): G1_f[x][y][q_z][p_z]     = sum_jz f(x, y, z(q_z, jz)) E_z[p_z][jz]
+//   stage 2 (y): G2_f[x][q_y][q_z][p_y][p_z] = sum_jy E_y[p_y][jy] G1_f[x][y(q_y, jy)][q_z][p_z]
+//   stage 3 (x): psi_f[q][p_x][p_y][p_z]   = h^3 sum_jx E_x[p_x][jx] G2_f[x(q_x, jx)][q_y][q_z][p_y][p_z]
+// with the branch split of Eq. psi in the last stage. x and y run over the data rows the
+// active q's boxes touch (wrapped on periodic axes, zero outside an open axis).
+__global__ void k_fbi3_stage1(GridDev gd, const ShotDev* __restrict__ shots,
+                              const double* __restrict__ u0, const double* __restrict__ u1,
+                              double2* __restrict__ g1) {
+  const int s = blockIdx.y;
+  const ShotDev& sh = shots[s];
+  const int64_t nbz = sh.nb[2];
+  const int64_t plane = sh.nrows * sh.nrows1 * sh.qn[2] * nbz;
+  const double* f0 = u0 + (int64_t)s * gd.npts;
+  const double* f1 = u1 + (int64_t)s * gd.npts;
+  const double2* Ez = sh.E[2];
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < plane;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t pz = e % nbz;
+    int64_t r = e / nbz;
+    const int64_t qz = r % sh.qn[2];
+    r /= sh.qn[2];
+    const int64_t yr = r % sh.nrows1, xr = r / sh.nrows1;
+    const int64_t ix = wrap_or_invalid(sh.row_lo + xr, gd.n[0], gd.periodic[0]);
+    const int64_t iy = wrap_or_invalid(sh.row_lo1 + yr, gd.n[1], gd.periodic[1]);
+    double2 a0 = make_double2(0.0, 0.0), a1 = a0;
+    if (ix >= 0 && iy >= 0) {
+      const int64_t base = (ix * gd.n[1] + iy) * gd.n[2];
+      const int64_t z0 = (int64_t)sh.s[2] * (sh.qlo[2] + qz) - nbz / 2;
+      for (int64_t jz = 0; jz < nbz; ++jz) {
+        const int64_t iz = wrap_or_invalid(z0 + jz, gd.n[2], gd.periodic[2]);
+        if (iz < 0) continue;
+        const double v0 = __ldg(f0 + base + iz), v1 = __ldg(f1 + base + iz);
+        const double2 E = __ldg(Ez + pz * nbz + jz);
+        a0.x = fma(v0, E.x, a0.x);
+        a0.y = fma(v0, E.y, a0.y);
+        a1.x = fma(v1, E.x, a1.x);
+        a1.y = fma(v1, E.y, a1.y);
+      }
+    }
+    g1[sh.g1_off + e] = a0;
+    g1[sh.g1_off + plane + e] = a1;
+  }
+}
+
+__global__ void k_fbi3_stage2(const ShotDev* __restrict__ shots, const double2* __restrict__ g1,
+                              double2* __restrict__ g2) {
+  const int s = blockIdx.y;
+  const ShotDev& sh = shots[s];
+  const int64_t nby = sh.nb[1], nbz = sh.nb[2];
+  const int64_t plane1 = sh.nrows * sh.nrows1 * sh.qn[2] * nbz;
+  const int64_t plane2 = sh.nrows * sh.qn[1] * sh.qn[2] * nby * nbz;
+  const double2* Ey = sh.E[1];
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < plane2;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t pz = e % nbz;
+    int64_t r = e / nbz;
+    const int64_t py = r % nby;
+    r /= nby;
+    const int64_t qz = r % sh.qn[2];
+    r /= sh.qn[2];
+    const int64_t qy = r % sh.qn[1], xr = r / sh.qn[1];
+    const int64_t y0 = (int64_t)sh.s[1] * qy;  // y row of jy = 0 relative to row_lo1
+    double2 a0 = make_double2(0.0, 0.0), a1 = a0;
+    for (int64_t jy = 0; jy < nby; ++jy) {
+      const int64_t off = ((xr * sh.nrows1 + y0 + jy) * sh.qn[2] + qz) * nbz + pz;
+      const double2 b0 = g1[sh.g1_off + off], b1 = g1[sh.g1_off + plane1 + off];
+      const double2 E = __ldg(Ey + py * nby + jy);
+      a0.x = fma(E.x, b0.x, fma(-E.y, b0.y, a0.x));
+      a0.y = fma(E.x, b0.y, fma(E.y, b0.x, a0.y));
+      a1.x = fma(E.x, b1.x, fma(-E.y, b1.y, a1.x));
+      a1.y = fma(E.x, b1.y, fma(E.y, b1.x, a1.y));
+    }
+    g2[sh.g2_off + e] = a0;
+    g2[sh.g2_off + plane2 + e] = a1;
+  }
+}
+
+__global__ void k_fbi3_stage3(GridDev gd, const ShotDev* __restrict__ shots,
+                              const double* __restrict__ C, const double2* __restrict__ g2,
+                              double2* __restrict__ psi, double2* __restrict__ psi_f1,
+                              unsigned long long* __restrict__ max2) {
+  const int s = blockIdx.y;
+  const ShotDev& sh = shots[s];
+  const int64_t nbx = sh.nb[0], nby = sh.nb[1], nbz = sh.nb[2];
+  const int64_t plane2 = sh.nrows * sh.qn[1] * sh.qn[2] * nby * nbz;
+  const int64_t qtot = sh.qn[0] * sh.qn[1] * sh.qn[2];
+  const int64_t total = qtot * sh.np;
+  const double2* Ex = sh.E[0];
+  const double hv = gd.h[0] * gd.h[1] * gd.h[2];
+  double mymax = 0.0;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t ql = e / sh.np, jp = e - ql * sh.np;
+    const int64_t qn12 = sh.qn[1] * sh.qn[2];
+    const int64_t mx = ql / qn12, myz = ql - mx * qn12;  // myz = q_y * qn_z + q_z
+    const int64_t px = jp / (nby * nbz), pyz = jp - px * nby * nbz;
+    double2 a0 = make_double2(0.0, 0.0), a1 = a0;
+    for (int64_t jx = 0; jx < nbx; ++jx) {
+      const int64_t xr = (int64_t)sh.s[0] * mx + jx;
+      const int64_t off = (xr * qn12 + myz) * nby * nbz + pyz;
+      const double2 b0 = g2[sh.g2_off + off], b1 = g2[sh.g2_off + plane2 + off];
+      const double2 E = __ldg(Ex + px * nbx + jx);
+      a0.x = fma(E.x, b0.x, fma(-E.y, b0.y, a0.x));
+      a0.y = fma(E.x, b0.y, fma(E.y, b0.x, a0.y));
+      a1.x = fma(E.x, b1.x, fma(-E.y, b1.y, a1.x));
+      a1.y = fma(E.x, b1.y, fma(E.y, b1.x, a1.y));
+    }
+    const int64_t my = myz / sh.qn[2], mz = myz - my * sh.qn[2];
+    const double q[3] = {gd.o[0] + (double)(sh.s[0] * (sh.qlo[0] + mx)) * gd.h[0],
+                         gd.o[1] + (double)(sh.s[1] * (sh.qlo[1] + my)) * gd.h[1],
+                         gd.o[2] + (double)(sh.s[2] * (sh.qlo[2] + mz)) * gd.h[2]};
+    const double cq = medium_value<3>(gd, C, q);
+    double2 o, tt;
+    const double a2 = psi_plus<3>(sh, jp, make_double2(hv * a0.x, hv * a0.y),
+                                  make_double2(hv * a1.x, hv * a1.y), cq, o, tt);
+    psi[sh.psi_off + e] = o;
+    psi_f1[sh.psi_off + e] = tt;
+    mymax = fmax(mymax, a2);
+  }
+  for (int off = 16; off > 0; off >>= 1) mymax = fmax(mymax, __shfl_xor_sync(0xffffffffu, mymax, off));
+  if ((threadIdx.x & 31) == 0) atomic_max_nonneg(max2 + s, mymax);
+}
+
+// ---------------------------------------------------------------------------
 // Stage 2 on the tensor cores (mixed precision, 2D). For one q and one 128 x 128 tile
 // of (p_x, p_z), the complex GEMM psi_f[px][pz] = sum_jx E_x[px][jx] G1_f[jx][pz] is
 // written as real GEMMs over K = 2 jx:
@@ -558,6 +691,19 @@ cudaError_t launch_fbi(fga_plan_s* p, const double* u0, const double* u1) {
       maxQ = std::max(maxQ, sh.qn[0] * sh.qn[1]);
       maxTiles = std::max<int64_t>(maxTiles, ((sh.nb[0] + BM - 1) / BM) * ((sh.nb[1] + BN - 1) / BN));
     }
+  }
+  if (D == 3) {
+    bool any = false;
+    for (const auto& sh : p->shots) any = any || sh.qn[0] * sh.qn[1] * sh.qn[2] > 0;
+    if (!any) return cudaSuccess;
+    const unsigned blocks = 1024;
+    k_fbi3_stage1<<<dim3(blocks, p->nshots), 256, 0, p->stream>>>(p->grid, p->d_shots, u0, u1, p->d_g1);
+    k_fbi3_stage2<<<dim3(blocks, p->nshots), 256, 0, p->stream>>>(p->d_shots, p->d_g1, p->d_g2);
+    k_fbi3_stage3<<<dim3(blocks, p->nshots), 256, 0, p->stream>>>(p->grid, p->d_shots, p->d_coef,
+                                                                 p->d_g2, p->d_psi, p->d_psi_f1,
+                                                                 p->d_max2);
+    p->launches += 3;
+    return cudaGetLastError();
   }
   if (maxM == 0) return cudaSuccess;
   dim3 g1grid((unsigned)((maxN + BN - 1) / BN), (unsigned)((maxM + BM - 1) / BM), p->nshots);

@@ -80,6 +80,51 @@ __device__ __forceinline__ void medium_eval(const GridDev& gd, const double* __r
     m.c = c;
     m.g[0] = c1 * gd.inv_h[0];
     m.K[0][0] = c2 * gd.inv_h[0] * gd.inv_h[0];
+  } else if constexpr (D == 3) {
+    // contract z, then y, then x; s[ordz][ordy] after the first two, ord = derivative order
+    double c = 0, cg[3] = {0, 0, 0}, ck[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      double y0 = 0, yz = 0, yzz = 0, yy = 0, yyz = 0, yyy = 0;  // sums over (b, c)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) {
+        const double* row = C + (idx[0][a] * gd.n[1] + idx[1][b]) * gd.n[2];
+        double s0 = 0, s1 = 0, s2 = 0;
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          double v = __ldg(row + idx[2][e]);
+          s0 += w[2][e] * v;
+          s1 += dw[2][e] * v;
+          s2 += ddw[2][e] * v;
+        }
+        y0 += w[1][b] * s0;
+        yz += w[1][b] * s1;
+        yzz += w[1][b] * s2;
+        yy += dw[1][b] * s0;
+        yyz += dw[1][b] * s1;
+        yyy += ddw[1][b] * s0;
+      }
+      c += w[0][a] * y0;
+      cg[0] += dw[0][a] * y0;
+      cg[1] += w[0][a] * yy;
+      cg[2] += w[0][a] * yz;
+      ck[0][0] += ddw[0][a] * y0;
+      ck[0][1] += dw[0][a] * yy;
+      ck[0][2] += dw[0][a] * yz;
+      ck[1][1] += w[0][a] * yyy;
+      ck[1][2] += w[0][a] * yyz;
+      ck[2][2] += w[0][a] * yzz;
+    }
+    m.c = c;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) m.g[k] = cg[k] * gd.inv_h[k];
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+#pragma unroll
+      for (int l = k; l < 3; ++l) {
+        m.K[k][l] = ck[k][l] * gd.inv_h[k] * gd.inv_h[l];
+        m.K[l][k] = m.K[k][l];
+      }
   } else {
     double r[4], rz[4], rzz[4];
 #pragma unroll
@@ -213,7 +258,9 @@ __device__ __forceinline__ int64_t medium_cell_of(const GridDev& gd, int k, doub
 // c, grad c, Hessian of c at x from the table gd.tab.
 template <int D>
 __device__ __forceinline__ void medium_eval_tab(const GridDev& gd, const double* x, Med& m) {
-  if constexpr (D == 1) {
+  if constexpr (D == 3) {
+    medium_eval<3>(gd, gd.tab, x, m);  // 3D: gd.tab holds the samples (tap form)
+  } else if constexpr (D == 1) {
     double t;
     const int64_t c0 = medium_cell_of(gd, 0, x[0], t);
     const double2* cell = reinterpret_cast<const double2*>(gd.tab) + c0 * 2;
@@ -269,6 +316,17 @@ __device__ __forceinline__ double medium_value(const GridDev& gd, const double* 
   if constexpr (D == 1) {
 #pragma unroll
     for (int a = 0; a < 4; ++a) c += w[0][a] * __ldg(C + idx[0][a]);
+  } else if constexpr (D == 3) {
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) {
+        const double* row = C + (idx[0][a] * gd.n[1] + idx[1][b]) * gd.n[2];
+        double s0 = 0;
+#pragma unroll
+        for (int e = 0; e < 4; ++e) s0 += w[2][e] * __ldg(row + idx[2][e]);
+        c += w[0][a] * w[1][b] * s0;
+      }
   } else {
 #pragma unroll
     for (int a = 0; a < 4; ++a) {

@@ -80,6 +80,44 @@ __device__ __forceinline__ bool rhs(const GridDev& gd, const double* y, double* 
     tri = dzi;
     detr = zr;
     deti = zi;
+  } else if constexpr (D == 3) {
+    // Z = A + iB and dZ/dt (3 x 3 complex); tr(adj(Z) dZ) and det Z by cofactors
+    double zr[9], zi[9], dzr[9], dzi[9];
+#pragma unroll
+    for (int e = 0; e < 9; ++e) {
+      zr[e] = y[Lo::AR + e] - y[Lo::BI + e];
+      zi[e] = y[Lo::AI + e] + y[Lo::BR + e];
+      dzr[e] = k[Lo::AR + e] - k[Lo::BI + e];
+      dzi[e] = k[Lo::AI + e] + k[Lo::BR + e];
+    }
+    // cofactor C[i][j] = (-1)^{i+j} det(minor ij); adj(Z)[j][i] = C[i][j]
+    double cr[9], ci[9];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        const int r0 = (i + 1) % 3, r1 = (i + 2) % 3, c0 = (j + 1) % 3, c1 = (j + 2) % 3;
+        // cyclic minors carry the sign (-1)^{i+j} already
+        const double ar = zr[r0 * 3 + c0], ai = zi[r0 * 3 + c0], br = zr[r1 * 3 + c1], bi = zi[r1 * 3 + c1];
+        const double er = zr[r0 * 3 + c1], ei = zi[r0 * 3 + c1], fr = zr[r1 * 3 + c0], fi = zi[r1 * 3 + c0];
+        cr[i * 3 + j] = (ar * br - ai * bi) - (er * fr - ei * fi);
+        ci[i * 3 + j] = (ar * bi + ai * br) - (er * fi + ei * fr);
+      }
+    // tr(adj(Z) dZ) = sum_{i,j} C[i][j] dZ[i][j];  det Z = sum_j Z[0][j] C[0][j]
+    trr = 0.0;
+    tri = 0.0;
+#pragma unroll
+    for (int e = 0; e < 9; ++e) {
+      trr += cr[e] * dzr[e] - ci[e] * dzi[e];
+      tri += cr[e] * dzi[e] + ci[e] * dzr[e];
+    }
+    detr = 0.0;
+    deti = 0.0;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      detr += zr[j] * cr[j] - zi[j] * ci[j];
+      deti += zr[j] * ci[j] + zi[j] * cr[j];
+    }
   } else {
     double zr[4], zi[4], dzr[4], dzi[4];
 #pragma unroll
@@ -123,6 +161,16 @@ __device__ __forceinline__ void ray_init(const GridDev& gd, const ShotDev& sh, i
   if constexpr (D == 1) {
     qm[0] = qf;
     pm[0] = pj - sh.nb[0] / 2;
+  } else if constexpr (D == 3) {
+    const int64_t nq12 = sh.nq[1] * sh.nq[2];
+    qm[0] = qf / nq12;
+    qm[1] = (qf - qm[0] * nq12) / sh.nq[2];
+    qm[2] = qf - qm[0] * nq12 - qm[1] * sh.nq[2];
+    const int64_t nb12 = (int64_t)sh.nb[1] * sh.nb[2];
+    const int64_t j0 = pj / nb12, j1 = (pj - j0 * nb12) / sh.nb[2], j2 = pj - j0 * nb12 - j1 * sh.nb[2];
+    pm[0] = j0 - sh.nb[0] / 2;
+    pm[1] = j1 - sh.nb[1] / 2;
+    pm[2] = j2 - sh.nb[2] / 2;
   } else {
     qm[0] = qf / sh.nq[1];
     qm[1] = qf - qm[0] * sh.nq[1];
@@ -137,7 +185,7 @@ __device__ __forceinline__ void ray_init(const GridDev& gd, const ShotDev& sh, i
     y[Lo::AR + i * D + i] = 1.0;
     y[Lo::BI + i * D + i] = -1.0;
   }
-  y[Lo::aR] = (D == 1) ? 1.4142135623730951 : 2.0;
+  y[Lo::aR] = D == 1 ? 1.4142135623730951 : (D == 2 ? 2.0 : 2.8284271247461903);  // 2^{d/2}
 }
 
 // Final state (structure of arrays) and coefficient 2 W a psi (2 pi eps)^{-3d/2} e^{iS/eps}.
@@ -285,6 +333,7 @@ __device__ __forceinline__ void record_traces(const GridDev& gd, const ShotDev& 
                                               double kappa, const double* y, double2 psi, int s,
                                               int64_t m, double* __restrict__ traces) {
   using Lo = Layout<D>;
+  if constexpr (D == 3) return;  // receivers are not supported in 3D (rejected at the boundary)
   const double cut = kappa * sh.sqrt_eps;
   double sc = 2.0 * sh.W * sh.norm;
   double ar = y[Lo::aR], ai = y[Lo::aI];

@@ -196,7 +196,9 @@ __global__ void k_gather_rows(const double* __restrict__ in, const int32_t* __re
 
 }  // namespace
 
+// 0 in 3D: the ray kernels evaluate the 64 taps of the samples there.
 size_t medium_table_doubles(const GridDev& gd) {
+  if (gd.dim == 3) return 0;
   return gd.dim == 1 ? (size_t)(gd.n[0] + 2) * 4 : (size_t)(gd.n[0] + 2) * (gd.n[1] + 2) * 16;
 }
 
@@ -226,13 +228,19 @@ unsigned long long work_order_mult(int64_t G) {
   return m % (unsigned long long)G;
 }
 
+namespace {
+using RayKernel = decltype(&k_rays<2, 1>);
+RayKernel ray_kernel(const fga_plan_s* p) {
+  const bool v3 = p->ray_variant == 1;
+  if (p->grid.dim == 1) return v3 ? k_rays<1, 3> : k_rays<1, 1>;
+  if (p->grid.dim == 2) return v3 ? k_rays<2, 3> : k_rays<2, 1>;
+  return v3 ? k_rays<3, 3> : k_rays<3, 1>;
+}
+}  // namespace
+
 int ray_max_per_sm(fga_plan_s* p) {
   int per_sm = 0;
-  const bool v3 = p->ray_variant == 1;
-  cudaError_t e =
-      p->grid.dim == 1
-          ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, v3 ? k_rays<1, 3> : k_rays<1, 1>, 128, 0)
-          : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, v3 ? k_rays<2, 3> : k_rays<2, 1>, 128, 0);
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ray_kernel(p), 128, 0);
   return (e == cudaSuccess && per_sm > 0) ? per_sm : 1;
 }
 
@@ -305,8 +313,7 @@ cudaError_t launch_rays_steps(fga_plan_s* p, int64_t nsteps, bool record) {
     rx.every = 0;
   }
   const unsigned long long mult = work_order_mult(p->G);
-  auto kern = p->grid.dim == 1 ? (p->ray_variant == 1 ? k_rays<1, 3> : k_rays<1, 1>)
-                               : (p->ray_variant == 1 ? k_rays<2, 3> : k_rays<2, 1>);
+  auto kern = ray_kernel(p);
   kern<<<blocks, 128, 0, p->stream>>>(p->grid, p->d_shots, p->d_coef, p->G, p->d_gshot, p->d_gq,
                                       p->d_gp, p->d_gpsi, nsteps, p->dt, p->kappa,
                                       p->integrate_exited, p->d_state, (int64_t)p->g_cap,

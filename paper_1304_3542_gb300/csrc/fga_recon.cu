@@ -25,6 +25,9 @@ namespace {
 
 constexpr int NT = 256;
 constexpr int T2 = 64;   // 2D tile edge (points)
+constexpr int T3 = 16;   // 3D tile edge (points)
+constexpr int CH3 = 16;  // Gaussians per chunk (3D)
+constexpr int64_t SEG3 = 512;  // default Gaussians per work item (3D)
 constexpr int T1 = 256;  // 1D tile length
 constexpr int CH = 16;   // Gaussians per chunk (2D)
 constexpr int CH1 = 32;  // Gaussians per chunk (1D)
@@ -278,6 +281,75 @@ __global__ void __launch_bounds__(NT) k_gather2(GridDev gd, const ShotDev* __res
 }
 
 // Ordered sum of the partial tiles of every tile into the output grid.
+// 3D gather of one work item: a 16^3 tile, thread = (x, y) column of 16 points along z;
+// per chunk of 16 Gaussians the per-axis factors (16 points each, the x factor carrying
+// the coefficient) are made in shared memory, then every thread adds
+// Re(X_g(x) Y_g(y) Z_g(z)) to its 16 points. Writes partial[w][16][16][16].
+__global__ void __launch_bounds__(NT) k_gather3(GridDev gd, const ShotDev* __restrict__ shots,
+                                                int nshots, double kappa,
+                                                const double* __restrict__ state, int64_t ld,
+                                                const double2* __restrict__ coef,
+                                                const int64_t* __restrict__ off,
+                                                const int32_t* __restrict__ list, int64_t list_cap,
+                                                const int64_t* __restrict__ seg_off, int64_t ntiles,
+                                                int64_t seg, double* __restrict__ partial) {
+  const int64_t w = blockIdx.x;
+  if (w >= seg_off[ntiles]) return;
+  const int64_t t = tile_of_item(seg_off, ntiles, w);
+  const int s = shot_of_tile(shots, nshots, t);
+  const ShotDev& sh = shots[s];
+  const double cut = kappa * sh.sqrt_eps, inv_eps = sh.inv_eps;
+  int64_t a[3], b[3];
+  tile_box<3>(gd, sh, t - sh.tile_off, a, b);
+  __shared__ double2 F[3][CH3][T3];  // [axis][gaussian][point]
+  const int ix = threadIdx.x / T3, iy = threadIdx.x % T3;
+  double acc[T3];
+#pragma unroll
+  for (int i = 0; i < T3; ++i) acc[i] = 0.0;
+  const int64_t l0 = min(off[t], list_cap) + (w - seg_off[t]) * seg;
+  const int64_t l1 = min(min(off[t + 1], list_cap), l0 + seg);
+  for (int64_t c0 = l0; c0 < l1; c0 += CH3) {
+    const int nc = (int)((l1 - c0) < CH3 ? (l1 - c0) : CH3);
+    if (threadIdx.x < 3 * CH3) {
+      const int gi = threadIdx.x / 3, axis = threadIdx.x % 3;
+      double2* dst = F[axis][gi];
+      if (gi < nc) {
+        const int32_t g = list[c0 + gi];
+        const double Q = state[axis * ld + g], P = state[(3 + axis) * ld + g];
+        const double2 cf = axis == 0 ? coef[g] : make_double2(1.0, 0.0);
+        const Axis ax = grid_axis(gd, axis);
+        const int64_t a_ax = axis == 0 ? a[0] : (axis == 1 ? a[1] : a[2]);
+        if (ax.periodic) {
+          for (int r = 0; r < T3; ++r) {
+            const double2 f = axis_factor(ax, a_ax + r, Q, P, cut, inv_eps);
+            dst[r] = make_double2(cf.x * f.x - cf.y * f.y, cf.x * f.y + cf.y * f.x);
+          }
+        } else {
+          axis_factors8(ax.o + (double)a_ax * ax.h, ax.h, Q, P, cut, inv_eps, cf, dst);
+          axis_factors8(ax.o + (double)(a_ax + 8) * ax.h, ax.h, Q, P, cut, inv_eps, cf, dst + 8);
+        }
+      } else {
+        for (int r = 0; r < T3; ++r) dst[r] = make_double2(0.0, 0.0);
+      }
+    }
+    __syncthreads();
+    for (int gi = 0; gi < nc; ++gi) {
+      const double2 X = F[0][gi][ix], Y = F[1][gi][iy];
+      const double xr = X.x * Y.x - X.y * Y.y, xi = X.x * Y.y + X.y * Y.x;
+      if (xr == 0.0 && xi == 0.0) continue;
+#pragma unroll
+      for (int i = 0; i < T3; ++i) {
+        const double2 Z = F[2][gi][i];
+        acc[i] = fma(xr, Z.x, fma(-xi, Z.y, acc[i]));
+      }
+    }
+    __syncthreads();
+  }
+  double* dst = partial + w * (int64_t)(T3 * T3 * T3) + (int64_t)(ix * T3 + iy) * T3;
+#pragma unroll
+  for (int i = 0; i < T3; ++i) dst[i] = acc[i];
+}
+
 template <int D>
 __global__ void __launch_bounds__(NT) k_reduce(GridDev gd, const ShotDev* __restrict__ shots,
                                                int nshots, const int64_t* __restrict__ seg_off,
@@ -288,7 +360,7 @@ __global__ void __launch_bounds__(NT) k_reduce(GridDev gd, const ShotDev* __rest
   const ShotDev& sh = shots[s];
   int64_t a[D], b[D];
   tile_box<D>(gd, sh, t - sh.tile_off, a, b);
-  constexpr int TP = (D == 1) ? T1 : T2 * T2;
+  constexpr int TP = (D == 1) ? T1 : (D == 2 ? T2 * T2 : T3 * T3 * T3);
   const int64_t w0 = seg_off[t], w1 = seg_off[t + 1];
   for (int idx = threadIdx.x; idx < TP; idx += NT) {
     double v = 0.0;
@@ -296,9 +368,13 @@ __global__ void __launch_bounds__(NT) k_reduce(GridDev gd, const ShotDev* __rest
     if constexpr (D == 1) {
       int64_t i = a[0] + idx;
       if (i <= b[0]) out[(int64_t)s * gd.npts + i] = v;
-    } else {
+    } else if constexpr (D == 2) {
       int64_t ix = a[0] + idx / T2, iz = a[1] + idx % T2;
       if (ix <= b[0] && iz <= b[1]) out[(int64_t)s * gd.npts + ix * gd.n[1] + iz] = v;
+    } else {
+      int64_t ix = a[0] + idx / (T3 * T3), iy = a[1] + (idx / T3) % T3, iz = a[2] + idx % T3;
+      if (ix <= b[0] && iy <= b[1] && iz <= b[2])
+        out[(int64_t)s * gd.npts + (ix * gd.n[1] + iy) * gd.n[2] + iz] = v;
     }
   }
 }
@@ -310,14 +386,10 @@ __global__ void __launch_bounds__(NT) k_reduce(GridDev gd, const ShotDev* __rest
 cudaError_t launch_binning(fga_plan_s* p, size_t* needed_pairs) {
   (void)needed_pairs;
   if (p->ntiles == 0) return cudaSuccess;
-  if (p->grid.dim == 1)
-    k_bin<1, false><<<(unsigned)p->ntiles, NT, 0, p->stream>>>(
-        p->grid, p->d_shots, p->nshots, p->kappa, p->d_state, (int64_t)p->g_cap, p->d_tile_off,
-        nullptr, nullptr, 0, p->d_status);
-  else
-    k_bin<2, false><<<(unsigned)p->ntiles, NT, 0, p->stream>>>(
-        p->grid, p->d_shots, p->nshots, p->kappa, p->d_state, (int64_t)p->g_cap, p->d_tile_off,
-        nullptr, nullptr, 0, p->d_status);
+  auto bin = p->grid.dim == 1 ? k_bin<1, false> : (p->grid.dim == 2 ? k_bin<2, false> : k_bin<3, false>);
+  bin<<<(unsigned)p->ntiles, NT, 0, p->stream>>>(p->grid, p->d_shots, p->nshots, p->kappa, p->d_state,
+                                                 (int64_t)p->g_cap, p->d_tile_off, nullptr, nullptr,
+                                                 0, p->d_status);
   p->launches += 1;
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
@@ -326,14 +398,10 @@ cudaError_t launch_binning(fga_plan_s* p, size_t* needed_pairs) {
 
 cudaError_t launch_binning_fill(fga_plan_s* p) {
   if (p->ntiles == 0) return cudaSuccess;
-  if (p->grid.dim == 1)
-    k_bin<1, true><<<(unsigned)p->ntiles, NT, 0, p->stream>>>(
-        p->grid, p->d_shots, p->nshots, p->kappa, p->d_state, (int64_t)p->g_cap, nullptr,
-        p->d_tile_off, p->d_tile_list, (int64_t)p->list_cap, p->d_status);
-  else
-    k_bin<2, true><<<(unsigned)p->ntiles, NT, 0, p->stream>>>(
-        p->grid, p->d_shots, p->nshots, p->kappa, p->d_state, (int64_t)p->g_cap, nullptr,
-        p->d_tile_off, p->d_tile_list, (int64_t)p->list_cap, p->d_status);
+  auto fill = p->grid.dim == 1 ? k_bin<1, true> : (p->grid.dim == 2 ? k_bin<2, true> : k_bin<3, true>);
+  fill<<<(unsigned)p->ntiles, NT, 0, p->stream>>>(p->grid, p->d_shots, p->nshots, p->kappa, p->d_state,
+                                                  (int64_t)p->g_cap, nullptr, p->d_tile_off,
+                                                  p->d_tile_list, (int64_t)p->list_cap, p->d_status);
   p->launches += 1;
   return cudaGetLastError();
 }
@@ -342,7 +410,7 @@ cudaError_t launch_binning_fill(fga_plan_s* p) {
 // partial tiles (one per work item, sized for the tile lists' capacity) stay within
 // kPartialBudget bytes.
 int64_t segment_len(fga_plan_s* p) {
-  const int64_t want = p->seg > 0 ? p->seg : (p->grid.dim == 1 ? SEG1 : SEG2);
+  const int64_t want = p->seg > 0 ? p->seg : (p->grid.dim == 1 ? SEG1 : (p->grid.dim == 2 ? SEG2 : SEG3));
   const int64_t tile_bytes = (int64_t)tile_points(p->grid.dim) * (int64_t)sizeof(double);
   const int64_t items = std::max<int64_t>(kPartialBudget / tile_bytes - p->ntiles, 1);
   const int64_t floor_len = ((int64_t)p->list_cap + items - 1) / items;
@@ -354,7 +422,9 @@ size_t partial_items(fga_plan_s* p) {
   return (size_t)p->ntiles + (p->list_cap + seg - 1) / seg;
 }
 
-size_t tile_points(int dim) { return dim == 1 ? (size_t)T1 : (size_t)T2 * T2; }
+size_t tile_points(int dim) {
+  return dim == 1 ? (size_t)T1 : (dim == 2 ? (size_t)T2 * T2 : (size_t)T3 * T3 * T3);
+}
 
 // Split of every tile's list into segments, one CTA per (tile, segment) writing a
 // partial tile, then the ordered reduction into u_dev.
@@ -376,19 +446,26 @@ cudaError_t launch_reconstruct(fga_plan_s* p, double* u_dev) {
                                            p->ntiles, seg, p->d_partial);
     k_reduce<1><<<(unsigned)p->ntiles, NT, 0, p->stream>>>(p->grid, p->d_shots, p->nshots,
                                                            p->d_seg_off, p->d_partial, u_dev);
-  } else {
+  } else if (p->grid.dim == 2) {
     k_gather2<<<items, NT, 0, p->stream>>>(p->grid, p->d_shots, p->nshots, p->kappa, p->d_state,
                                            (int64_t)p->g_cap, p->d_gcoef, p->d_tile_off,
                                            p->d_tile_list, (int64_t)p->list_cap, p->d_seg_off,
                                            p->ntiles, seg, p->d_partial);
     k_reduce<2><<<(unsigned)p->ntiles, NT, 0, p->stream>>>(p->grid, p->d_shots, p->nshots,
                                                            p->d_seg_off, p->d_partial, u_dev);
+  } else {
+    k_gather3<<<items, NT, 0, p->stream>>>(p->grid, p->d_shots, p->nshots, p->kappa, p->d_state,
+                                           (int64_t)p->g_cap, p->d_gcoef, p->d_tile_off,
+                                           p->d_tile_list, (int64_t)p->list_cap, p->d_seg_off,
+                                           p->ntiles, seg, p->d_partial);
+    k_reduce<3><<<(unsigned)p->ntiles, NT, 0, p->stream>>>(p->grid, p->d_shots, p->nshots,
+                                                           p->d_seg_off, p->d_partial, u_dev);
   }
   p->launches += 2;
   return cudaGetLastError();
 }
 
-int tile_edge(int dim) { return dim == 1 ? T1 : T2; }
+int tile_edge(int dim) { return dim == 1 ? T1 : (dim == 2 ? T2 : T3); }
 
 }  // namespace fga
 

@@ -30,6 +30,11 @@ template <int D>
 __device__ __forceinline__ bool p_valid(const ShotDev& sh, int64_t jp) {
   if constexpr (D == 1) {
     return jp != 0 && jp != sh.nb[0] / 2;
+  } else if constexpr (D == 3) {
+    const int64_t nb12 = (int64_t)sh.nb[1] * sh.nb[2];
+    const int64_t j0 = jp / nb12, j1 = (jp - j0 * nb12) / sh.nb[2], j2 = jp - j0 * nb12 - j1 * sh.nb[2];
+    return j0 != 0 && j1 != 0 && j2 != 0 &&
+           !(j0 == sh.nb[0] / 2 && j1 == sh.nb[1] / 2 && j2 == sh.nb[2] / 2);
   } else {
     int64_t j0 = jp / sh.nb[1], j1 = jp - j0 * sh.nb[1];
     return j0 != 0 && j1 != 0 && !(j0 == sh.nb[0] / 2 && j1 == sh.nb[1] / 2);
@@ -142,6 +147,10 @@ __global__ void __launch_bounds__(NT) k_select_scatter(const ShotDev* __restrict
     int64_t qflat;
     if constexpr (D == 1) {
       qflat = sh.qlo[0] + ql;
+    } else if constexpr (D == 3) {
+      const int64_t qn12 = sh.qn[1] * sh.qn[2];
+      const int64_t m0 = ql / qn12, m1 = (ql - m0 * qn12) / sh.qn[2], m2 = ql - m0 * qn12 - m1 * sh.qn[2];
+      qflat = ((sh.qlo[0] + m0) * sh.nq[1] + (sh.qlo[1] + m1)) * sh.nq[2] + (sh.qlo[2] + m2);
     } else {
       int64_t mxl = ql / sh.qn[1], mzl = ql - mxl * sh.qn[1];
       qflat = (sh.qlo[0] + mxl) * sh.nq[1] + (sh.qlo[1] + mzl);
@@ -173,12 +182,10 @@ cudaError_t launch_select_count(fga_plan_s* p) {
   const int64_t* d_blk_first = p->d_blk_first;
   double tau2 = p->tau * p->tau;
   if (p->nblocks == 0) return cudaSuccess;
-  if (p->grid.dim == 1)
-    k_select_count<1><<<(unsigned)p->nblocks, NT, 0, p->stream>>>(p->d_shots, p->nshots, p->d_psi,
-                                                                   p->d_max2, tau2, p->d_blk);
-  else
-    k_select_count<2><<<(unsigned)p->nblocks, NT, 0, p->stream>>>(p->d_shots, p->nshots, p->d_psi,
-                                                                   p->d_max2, tau2, p->d_blk);
+  auto count = p->grid.dim == 1 ? k_select_count<1> : (p->grid.dim == 2 ? k_select_count<2>
+                                                                         : k_select_count<3>);
+  count<<<(unsigned)p->nblocks, NT, 0, p->stream>>>(p->d_shots, p->nshots, p->d_psi, p->d_max2, tau2,
+                                                    p->d_blk);
   k_scan_exclusive<<<1, 1024, 0, p->stream>>>(p->d_blk, p->nblocks);
   k_select_counts<<<(p->nshots + 127) / 128, 128, 0, p->stream>>>(p->d_shots, p->nshots, p->d_blk,
                                                                   d_blk_first, p->d_counts);
@@ -189,14 +196,11 @@ cudaError_t launch_select_count(fga_plan_s* p) {
 cudaError_t launch_select(fga_plan_s* p) {
   double tau2 = p->tau * p->tau;
   if (p->nblocks == 0) return cudaSuccess;
-  if (p->grid.dim == 1)
-    k_select_scatter<1><<<(unsigned)p->nblocks, NT, 0, p->stream>>>(
-        p->d_shots, p->nshots, p->d_psi, p->d_max2, tau2, p->d_blk, p->d_gshot, p->d_gq, p->d_gp,
-        p->d_gpsi, p->d_psi_f1, p->d_gpsi_f1);
-  else
-    k_select_scatter<2><<<(unsigned)p->nblocks, NT, 0, p->stream>>>(
-        p->d_shots, p->nshots, p->d_psi, p->d_max2, tau2, p->d_blk, p->d_gshot, p->d_gq, p->d_gp,
-        p->d_gpsi, p->d_psi_f1, p->d_gpsi_f1);
+  auto scatter = p->grid.dim == 1 ? k_select_scatter<1>
+                                   : (p->grid.dim == 2 ? k_select_scatter<2> : k_select_scatter<3>);
+  scatter<<<(unsigned)p->nblocks, NT, 0, p->stream>>>(p->d_shots, p->nshots, p->d_psi, p->d_max2,
+                                                      tau2, p->d_blk, p->d_gshot, p->d_gq, p->d_gp,
+                                                      p->d_gpsi, p->d_psi_f1, p->d_gpsi_f1);
   p->launches += 1;
   return cudaGetLastError();
 }

@@ -16,8 +16,6 @@ __device__ __forceinline__ int shot_of_tile(const ShotDev* shots, int nshots, in
   return lo;
 }
 
-// Window of Gaussian (Q, cut) along one axis as a conservative grid-index range,
-// for the image shifted by l periods.
 // One axis of the grid picked by a runtime index with conditionals (indexing the grid's
 // arrays with a runtime value would put the kernel parameter block in local memory).
 struct Axis {
@@ -27,14 +25,13 @@ struct Axis {
 };
 
 __device__ __forceinline__ Axis grid_axis(const GridDev& gd, int k) {
-  const bool k1 = k == 1 && kMaxDim > 1;
   Axis ax;
-  ax.o = k1 ? gd.o[kMaxDim - 1] : gd.o[0];
-  ax.h = k1 ? gd.h[kMaxDim - 1] : gd.h[0];
-  ax.inv_h = k1 ? gd.inv_h[kMaxDim - 1] : gd.inv_h[0];
-  ax.L = k1 ? gd.L[kMaxDim - 1] : gd.L[0];
-  ax.n = k1 ? gd.n[kMaxDim - 1] : gd.n[0];
-  ax.periodic = k1 ? gd.periodic[kMaxDim - 1] : gd.periodic[0];
+  ax.o = k == 0 ? gd.o[0] : (k == 1 ? gd.o[1] : gd.o[2]);
+  ax.h = k == 0 ? gd.h[0] : (k == 1 ? gd.h[1] : gd.h[2]);
+  ax.inv_h = k == 0 ? gd.inv_h[0] : (k == 1 ? gd.inv_h[1] : gd.inv_h[2]);
+  ax.L = k == 0 ? gd.L[0] : (k == 1 ? gd.L[1] : gd.L[2]);
+  ax.n = k == 0 ? gd.n[0] : (k == 1 ? gd.n[1] : gd.n[2]);
+  ax.periodic = k == 0 ? gd.periodic[0] : (k == 1 ? gd.periodic[1] : gd.periodic[2]);
   return ax;
 }
 
@@ -44,6 +41,7 @@ __device__ __forceinline__ void window_range_ax(const Axis& ax, double Q, double
   hi = (int64_t)ceil((Q + cut - ax.o) * ax.inv_h) + 1;
 }
 
+// Window of Gaussian (Q, cut) along one axis as a conservative grid-index range.
 __device__ __forceinline__ void window_range(const GridDev& gd, int k, double Q, double cut,
                                              int64_t& lo, int64_t& hi) {
   lo = (int64_t)floor((Q - cut - gd.o[k]) * gd.inv_h[k]) - 1;
@@ -74,9 +72,15 @@ __device__ __forceinline__ void tile_box(const GridDev& gd, const ShotDev& sh, i
   int64_t t[D];
   if constexpr (D == 1) {
     t[0] = tloc;
-  } else {
+  } else if constexpr (D == 2) {
     t[0] = tloc / sh.ntile[1];
     t[1] = tloc - t[0] * sh.ntile[1];
+  } else {
+    const int64_t yz = (int64_t)sh.ntile[1] * sh.ntile[2];
+    t[0] = tloc / yz;
+    const int64_t r = tloc - t[0] * yz;
+    t[1] = r / sh.ntile[2];
+    t[2] = r - t[1] * sh.ntile[2];
   }
 #pragma unroll
   for (int k = 0; k < D; ++k) {
@@ -85,7 +89,6 @@ __device__ __forceinline__ void tile_box(const GridDev& gd, const ShotDev& sh, i
   }
 }
 
-// The (tile, segment) work item w: tile t is the largest with seg_off[t] <= w.
 __device__ __forceinline__ int64_t tile_of_item(const int64_t* seg_off, int64_t ntiles, int64_t w) {
   int64_t lo = 0, hi = ntiles - 1;
   while (lo < hi) {

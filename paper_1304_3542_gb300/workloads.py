@@ -136,6 +136,30 @@ def lens_2d(N: int = 256, eps: float = 1.0 / 256, T: float = 0.5, dt: float = 1e
                    kappa=kappa, tau=tau)
 
 
+def lens_3d(N: int = 20, eps: float = 0.003, T: float = 0.05, dt: float = 1e-3,
+            kappa: float = 6.0, tau: float = 1e-2, s: int = 2, box: int = 16,
+            k0: float = 6 * math.pi, width2: float = 0.01,
+            x0: Tuple[float, float, float] = (0.5, 0.5, 0.35),
+            center: Tuple[float, float, float] = (0.52, 0.48, 0.55)) -> Problem:
+    """3D smooth lens c = 1 + 0.3 exp(-|x - center|^2/0.02) on [0,1)^3 (open axes; center
+    off the grid's knot planes), with a Gaussian-modulated plane-wave packet travelling
+    in +z: u0 = exp(-|x-x0|^2/width2) cos(k0 (z - z0)), u1 = -c(x) du0/dz."""
+    h = 1.0 / N
+    ax = h * np.arange(N)
+    X, Y, Z = np.meshgrid(ax, ax, ax, indexing="ij")
+    c = 1.0 + 0.3 * np.exp(-((X - center[0]) ** 2 + (Y - center[1]) ** 2 + (Z - center[2]) ** 2)
+                           / 0.02)
+    env = np.exp(-((X - x0[0]) ** 2 + (Y - x0[1]) ** 2 + (Z - x0[2]) ** 2) / width2)
+    u0 = env * np.cos(k0 * (Z - x0[2]))
+    du0 = env * (-2.0 * (Z - x0[2]) / width2 * np.cos(k0 * (Z - x0[2]))
+                 - k0 * np.sin(k0 * (Z - x0[2])))
+    u1 = -c * du0
+    shot = Shot(eps=eps, u0=u0, u1=u1, q_stride=(s, s, s), box=(box, box, box))
+    return Problem(name="lens_3d", dim=3, n=(N, N, N), h=(h, h, h), origin=(0.0, 0.0, 0.0),
+                   periodic=(False, False, False), velocity=c, shots=[shot], T=T, dt=dt,
+                   kappa=kappa, tau=tau)
+
+
 def periodic_2d(N: int = 64, eps: float = 1.0 / 128, T: float = 0.0, dt: float = 1e-2,
                 s: int = 2, kappa: float = 8.0, tau: float = 0.0, c: float = 1.0,
                 k0: Tuple[float, float] = (8 * math.pi, 12 * math.pi), width2: float = 0.01,
@@ -286,6 +310,7 @@ def by_name(name: str, **kw) -> Problem:
     table = {
         "periodic_1d": periodic_1d,
         "lens_2d": lens_2d,
+        "lens_3d": lens_3d,
         "periodic_2d": periodic_2d,
         "layered_single": layered_single,
         "layered_batch": layered_batch,

@@ -24,6 +24,8 @@ def _rand_data(shape, seed):
     dict(n=(24,), h=(1.0 / 24,), per=(True,), eps=0.004, s=(4,), box=(24,)),
     dict(n=(18, 14), h=(0.1, 0.08), per=(False, False), eps=0.02, s=(4, 3), box=(8, 10)),
     dict(n=(16, 12), h=(1.0 / 16, 0.1), per=(True, False), eps=0.01, s=(4, 3), box=(16, 8)),
+    dict(n=(9, 8, 7), h=(0.1, 0.125, 0.11), per=(False, True, False), eps=0.02, s=(3, 2, 3),
+         box=(6, 8, 4)),
 ])
 def test_fft_route_matches_direct_sum(case):
     g = O.Grid(case["n"], case["h"], (0.0,) * len(case["n"]), case["per"])
@@ -74,6 +76,39 @@ def test_gaussian_data_closed_form_2d():
                         + 1j * p * q / eps))
     got = psi[near]
     assert np.max(np.abs(got - ex)) <= 1e-12 * np.max(np.abs(ex))
+
+
+def test_gaussian_data_closed_form_3d():
+    # the 3D transform of a Gaussian is the product of three 1D Gaussian integrals
+    # (the closed form of the 2D test per axis); only q near the data (q_subset). The
+    # data sit 8 sg from the grid's edges, the box (+-8 sqrt(eps)) cuts the window at
+    # e^{-32}, and the integrand's spectrum at the grid Nyquist is below e^{-24}.
+    n = (80, 76, 72)
+    h = (0.0125, 0.0125, 0.0125)
+    g = O.Grid(n, h, (0.0, 0.0, 0.0), (False, False, False))
+    eps = 0.001
+    sg = 0.06
+    y0 = (0.5, 0.47, 0.45)
+    xs = [h[k] * np.arange(n[k]) for k in range(3)]
+    X, Y, Z = np.meshgrid(*xs, indexing="ij")
+    f = np.exp(-((X - y0[0]) ** 2 + (Y - y0[1]) ** 2 + (Z - y0[2]) ** 2) / (2 * sg ** 2))
+    s = (4, 4, 4)
+    box = (40, 40, 40)
+    qp_all = O.q_points(g, s)
+    near = np.where(np.max(np.abs(qp_all - np.array(y0)[None, :]), axis=1) < 0.05)[0]
+    assert near.size >= 8
+    psi = O.fbi(g, f, eps, s, box, q_subset=near)
+    pp = O.p_points(g, eps, box)
+    ex = np.ones((near.size, pp.shape[0]), dtype=complex)
+    for k in range(3):
+        q = qp_all[near, k][:, None]
+        p = pp[:, k][None, :]
+        alpha = 1.0 / sg ** 2 + 1.0 / eps
+        beta = y0[k] / sg ** 2 + (q - 1j * p) / eps
+        ex *= (math.sqrt(2 * math.pi / alpha)
+               * np.exp(beta ** 2 / (2 * alpha) - y0[k] ** 2 / (2 * sg ** 2) - q ** 2 / (2 * eps)
+                        + 1j * p * q / eps))
+    assert np.max(np.abs(psi - ex)) <= 1e-10 * np.max(np.abs(ex))
 
 
 def test_p_grid_is_symmetric_and_excludes_zero():
