@@ -142,6 +142,7 @@ __global__ void __launch_bounds__(128) k_adjoint(GridDev gd, const ShotDev* __re
   const int lane = threadIdx.x & 31;
   // scratch: [slot][field][thread], slots 0..ncheck-1 checkpoints, then kseg segment states
   auto slot = [&](int64_t sidx, int f) -> double& { return scratch[(sidx * NF + f) * nthr + tid]; };
+  extern __shared__ double zs[];  // [4][NF][blockDim.x]: RK4 stage states and lambda in
   while (true) {
     unsigned long long base = 0;
     if (lane == 0) base = atomicAdd(next, 32ull);
@@ -232,7 +233,7 @@ __global__ void __launch_bounds__(128) k_adjoint(GridDev gd, const ShotDev* __re
       if (act) {
 #pragma unroll
         for (int f = 0; f < NF; ++f) yn[f] = slot(ncheck + (nn - 1 - jp * kseg), f);
-        rk4_step_adjoint<D>(gd, C, yn, dt, lam, gradC);
+        rk4_step_adjoint<D>(gd, C, yn, dt, lam, gradC, zs, blockDim.x, threadIdx.x);
       }
     }
     if (!has) continue;
@@ -269,14 +270,27 @@ __global__ void __launch_bounds__(128) k_adjoint(GridDev gd, const ShotDev* __re
 
 }  // namespace
 
+// Dynamic shared memory of the adjoint kernel: 4 * NF doubles per thread of 128.
+size_t adjoint_smem(int dim) { return (size_t)4 * state_fields(dim) * 128 * sizeof(double); }
+
+cudaError_t set_adjoint_smem(int dim) {
+  return dim == 1 ? cudaFuncSetAttribute(k_adjoint<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)adjoint_smem(1))
+                  : cudaFuncSetAttribute(k_adjoint<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)adjoint_smem(2));
+}
+
 // Resident threads of the adjoint kernel and the scratch doubles they need.
 int64_t adjoint_threads(fga_plan_s* p) {
   int dev = 0, sms = 0, per_sm = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return 0;
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+  if (set_adjoint_smem(p->grid.dim) != cudaSuccess) return 0;
   cudaError_t e = p->grid.dim == 1
-                      ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_adjoint<1>, 128, 0)
-                      : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_adjoint<2>, 128, 0);
+                      ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_adjoint<1>, 128,
+                                                                      adjoint_smem(1))
+                      : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_adjoint<2>, 128,
+                                                                      adjoint_smem(2));
   if (e != cudaSuccess) return 0;
   int64_t blocks = (int64_t)sms * (per_sm > 0 ? per_sm : 1);
   blocks = std::min<int64_t>(blocks, (p->G + 127) / 128);
@@ -315,13 +329,13 @@ cudaError_t launch_adjoint(fga_plan_s* p, const double* residual, double* gradC,
   if (e != cudaSuccess) return e;
   RxDev rx = p->rx;
   if (p->grid.dim == 1)
-    k_adjoint<1><<<blocks, 128, 0, p->stream>>>(p->grid, p->d_shots, p->d_coef, p->G, p->d_gshot,
+    k_adjoint<1><<<blocks, 128, adjoint_smem(1), p->stream>>>(p->grid, p->d_shots, p->d_coef, p->G, p->d_gshot,
                                                 p->d_gq, p->d_gp, p->d_gpsi, p->d_gpsi_f1, p->nsteps,
                                                 p->dt, p->kappa, p->integrate_exited, rx, residual,
                                                 p->d_part, len, (int)slices, scratch, kseg, ncheck,
                                                 p->d_steps + 1, p->d_adj_order);
   else
-    k_adjoint<2><<<blocks, 128, 0, p->stream>>>(p->grid, p->d_shots, p->d_coef, p->G, p->d_gshot,
+    k_adjoint<2><<<blocks, 128, adjoint_smem(2), p->stream>>>(p->grid, p->d_shots, p->d_coef, p->G, p->d_gshot,
                                                 p->d_gq, p->d_gp, p->d_gpsi, p->d_gpsi_f1, p->nsteps,
                                                 p->dt, p->kappa, p->integrate_exited, rx, residual,
                                                 p->d_part, len, (int)slices, scratch, kseg, ncheck,

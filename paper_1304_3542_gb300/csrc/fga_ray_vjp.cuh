@@ -409,53 +409,65 @@ __device__ __forceinline__ void rk4_step(const GridDev& gd, const double* __rest
 }
 
 // lambda <- (d step/d y)^T lambda at the state y (start of the step), gradC accumulated.
+// The three stage states and the incoming lambda live in the caller's shared-memory
+// slots zs[(slot * NF + field) * nt + lane] (4 * NF values per thread) rather than in
+// registers, which the vector-Jacobian products need.
 template <int D>
 __device__ void rk4_step_adjoint(const GridDev& gd, const double* __restrict__ C, const double* y,
-                                 double dt, double* lam, double* __restrict__ gradC) {
+                                 double dt, double* lam, double* __restrict__ gradC, double* zs,
+                                 int nt, int lane) {
   using Lo = Layout<D>;
   constexpr int NF = Lo::NF;
-  double k[NF], z2[NF], z3[NF], z4[NF];
-  const double h2 = 0.5 * dt;
-  rhs<D>(gd, y, k);
+  auto Z = [&](int s, int f) -> double& { return zs[(s * NF + f) * nt + lane]; };
+  const double h2 = 0.5 * dt, h6 = dt / 6.0, h3 = dt / 3.0;
+  {
+    double k[NF], t[NF];
+    rhs<D>(gd, y, k);
 #pragma unroll
-  for (int i = 0; i < NF; ++i) z2[i] = fma(h2, k[i], y[i]);
-  rhs<D>(gd, z2, k);
+    for (int i = 0; i < NF; ++i) Z(0, i) = t[i] = fma(h2, k[i], y[i]);  // z2
+    rhs<D>(gd, t, k);
 #pragma unroll
-  for (int i = 0; i < NF; ++i) z3[i] = fma(h2, k[i], y[i]);
-  rhs<D>(gd, z3, k);
+    for (int i = 0; i < NF; ++i) Z(1, i) = t[i] = fma(h2, k[i], y[i]);  // z3
+    rhs<D>(gd, t, k);
 #pragma unroll
-  for (int i = 0; i < NF; ++i) z4[i] = fma(dt, k[i], y[i]);
-  double kb[NF], zb[NF], k1b[NF], k2b[NF], k3b[NF];
-  const double h6 = dt / 6.0, h3 = dt / 3.0;
+    for (int i = 0; i < NF; ++i) Z(2, i) = fma(dt, k[i], y[i]);  // z4
+  }
+#pragma unroll
+  for (int i = 0; i < NF; ++i) Z(3, i) = lam[i];  // lambda in
+  double kb[NF], zb[NF], z[NF];
+  // stage 4: k4 bar = h/6 lambda
 #pragma unroll
   for (int i = 0; i < NF; ++i) {
-    kb[i] = h6 * lam[i];  // k4 bar
-    k3b[i] = h3 * lam[i];
-    k2b[i] = h3 * lam[i];
-    k1b[i] = h6 * lam[i];
+    kb[i] = h6 * Z(3, i);
     zb[i] = 0.0;
+    z[i] = Z(2, i);
   }
-  rhs_vjp<D>(gd, C, z4, kb, zb, gradC);
+  rhs_vjp<D>(gd, C, z, kb, zb, gradC);
+  // stage 3: k3 bar = h/3 lambda + h z4 bar
 #pragma unroll
   for (int i = 0; i < NF; ++i) {
     lam[i] += zb[i];
-    k3b[i] = fma(dt, zb[i], k3b[i]);
+    kb[i] = fma(dt, zb[i], h3 * Z(3, i));
     zb[i] = 0.0;
+    z[i] = Z(1, i);
   }
-  rhs_vjp<D>(gd, C, z3, k3b, zb, gradC);
+  rhs_vjp<D>(gd, C, z, kb, zb, gradC);
+  // stage 2: k2 bar = h/3 lambda + h/2 z3 bar
 #pragma unroll
   for (int i = 0; i < NF; ++i) {
     lam[i] += zb[i];
-    k2b[i] = fma(h2, zb[i], k2b[i]);
+    kb[i] = fma(h2, zb[i], h3 * Z(3, i));
     zb[i] = 0.0;
+    z[i] = Z(0, i);
   }
-  rhs_vjp<D>(gd, C, z2, k2b, zb, gradC);
+  rhs_vjp<D>(gd, C, z, kb, zb, gradC);
+  // stage 1: k1 bar = h/6 lambda + h/2 z2 bar, at y itself
 #pragma unroll
   for (int i = 0; i < NF; ++i) {
     lam[i] += zb[i];
-    k1b[i] = fma(h2, zb[i], k1b[i]);
+    kb[i] = fma(h2, zb[i], h6 * Z(3, i));
   }
-  rhs_vjp<D>(gd, C, y, k1b, lam, gradC);
+  rhs_vjp<D>(gd, C, y, kb, lam, gradC);
 }
 
 }  // namespace adj
