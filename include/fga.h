@@ -90,6 +90,10 @@ typedef struct {
                            and the Gaussian never touches the grid again: the field is
                            unchanged, its stored state is the state at exit).
                            1: every ray is integrated to T. */
+  int64_t keep_n;     /* 0: select by tau. > 0: keep, per shot, the keep_n largest |psi+|
+                         over the valid (q, p) instead (ties by q index, then p index);
+                         the - branch holds the mirror set, so each branch has keep_n
+                         Gaussians (the N-largest selection of the paper's experiment) */
 } fga_config;
 
 /* Create a plan: validate cfg, copy the velocity (host or device, [n...] FP64,

@@ -149,6 +149,7 @@ fga_status fga_destroy(fga_plan_t p) {
                   p->d_gpsi, p->d_state, p->d_gcoef, p->d_tile_cnt, p->d_tile_off,
                   p->d_tile_list, p->d_seg_off, p->d_partial, p->d_out, p->d_status,
                   p->d_steps, p->d_rx, p->d_rx_off, p->d_rx_perm, p->d_traces, p->d_gsteps, p->d_g2,
+                  p->d_topk, p->d_topk_hist, p->d_blk_eq,
                   p->d_adj_order, p->d_adj_bucket,
                   p->d_run_geo, p->d_run_axis, p->d_run_off, p->d_resid_int,
                   p->d_psi_f1, p->d_gpsi_f1, p->d_adj_scratch, p->d_grad, p->d_resid,
@@ -190,6 +191,7 @@ fga_status fga_plan(const fga_config* cfg, const double* velocity, void* stream,
     return fail(nullptr, FGA_ERR_INVALID, "kappa must be > 0");
   if (!(cfg->tau >= 0.0) || !std::isfinite(cfg->tau))
     return fail(nullptr, FGA_ERR_INVALID, "tau must be >= 0");
+  if (cfg->keep_n < 0) return fail(nullptr, FGA_ERR_INVALID, "keep_n must be >= 0");
   GridDev gd;
   std::memset(&gd, 0, sizeof(gd));
   gd.dim = d;
@@ -221,6 +223,7 @@ fga_status fga_plan(const fga_config* cfg, const double* velocity, void* stream,
   p->tau = cfg->tau;
   p->precision = cfg->precision;
   p->integrate_exited = cfg->integrate_exited ? 1 : 0;
+  p->keep_n = cfg->keep_n;
   p->stream = (cudaStream_t)stream;
   p->nfields = fga::state_fields(d);
   const int TS = cfg->precision == FGA_MIXED_TF32X3 ? fga::tile_edge_tc() : fga::tile_edge(d);
@@ -426,6 +429,13 @@ fga_status fga_decompose(fga_plan_t p, const double* u0, const double* u1, int64
                                   cudaMemcpyHostToDevice, p->stream));
   CUDA_OR_FAIL(p, fga::launch_fbi(p, du0, du1));
   CUDA_OR_FAIL(p, cudaEventRecord(p->ev[1], p->stream));
+  if (p->keep_n > 0) {
+    if (!p->d_topk) {
+      CUDA_OR_FAIL(p, cudaMalloc(&p->d_topk, sizeof(unsigned long long) * 4 * p->nshots));
+      CUDA_OR_FAIL(p, cudaMalloc(&p->d_topk_hist, sizeof(unsigned long long) * 256 * p->nshots));
+    }
+    CUDA_OR_FAIL(p, grow(&p->d_blk_eq, &p->blk_eq_cap, (size_t)p->nblocks + 1));
+  }
   CUDA_OR_FAIL(p, fga::launch_select_count(p));
   std::vector<int64_t> counts(p->nshots, 0);
   if (p->nblocks > 0)

@@ -53,6 +53,7 @@ class Config(ctypes.Structure):
         ("tau", ctypes.c_double),
         ("precision", ctypes.c_int),
         ("integrate_exited", ctypes.c_int),
+        ("keep_n", ctypes.c_int64),
     ]
 
 
@@ -156,7 +157,8 @@ class Plan:
     def __init__(self, dim: int, n: Sequence[int], h: Sequence[float], origin: Sequence[float],
                  periodic: Sequence[bool], velocity, eps: Sequence[float], T: float, dt: float,
                  kappa: float, tau: float, q_stride=None, box=None, precision: int = FGA_FP64,
-                 stream: Optional[int] = None, integrate_exited: bool = False):
+                 stream: Optional[int] = None, integrate_exited: bool = False,
+                 keep_n: int = 0):
         self._L = load()
         self.dim = dim
         self.n = tuple(int(v) for v in n)
@@ -182,6 +184,7 @@ class Plan:
         self._T, self._dt = float(T), float(dt)
         cfg.precision = int(precision)
         cfg.integrate_exited = int(bool(integrate_exited))
+        cfg.keep_n = int(keep_n)
         _check_f64(velocity, self.npts, "velocity")
         self._keep = [velocity]
         out = ctypes.c_void_p()
@@ -363,7 +366,8 @@ def plan_from_problem(prob, velocity=None, stream=None, precision: int = FGA_FP6
     return Plan(prob.dim, prob.n, prob.h, prob.origin, prob.periodic, vel,
                 [s.eps for s in prob.shots], prob.T, prob.dt, prob.kappa, prob.tau,
                 q_stride=[s.q_stride for s in prob.shots], box=[s.box for s in prob.shots],
-                precision=precision, stream=stream, integrate_exited=integrate_exited)
+                precision=precision, stream=stream, integrate_exited=integrate_exited,
+                keep_n=getattr(prob, "keep_n", 0))
 
 
 def stacked_initial_data(prob):

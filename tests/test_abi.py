@@ -58,6 +58,7 @@ def _plan(**kw):
     (dict(eps=[-1.0]), "eps"),
     (dict(eps=[float("nan")]), "eps"),
     (dict(kappa=0.0), "kappa"),
+    (dict(keep_n=-1), "keep_n"),
     (dict(tau=-1.0), "tau"),
     (dict(h=(0.0, 0.1)), "spacing"),
     (dict(n=(2, 16), velocity=np.ones(32)), "grid size"),
