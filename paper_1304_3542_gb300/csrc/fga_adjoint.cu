@@ -9,8 +9,8 @@
 //
 // Discrete adjoint of the RK4 scheme (the exact gradient of the computed traces):
 // every ray is integrated forward again storing a checkpoint every K ~ sqrt(T/dt)
-// steps; the reverse sweep recomputes one segment of K states at a time from its
-// checkpoint and runs the transposed RK4 stages, each through the hand-written
+// steps; the reverse sweep recomputes one segment of K states (and the RK4 stage states
+// of its steps) at a time from its checkpoint and runs the transposed RK4 stages, each through the hand-written
 // vector-Jacobian product of the right-hand side below (rhs_vjp). The coefficient
 // gradient of each evaluation of c, grad c, Hessian of c is scattered to its 4^d
 // spline taps with atomic additions. Like the forward integrator the kernel is
@@ -38,6 +38,7 @@ using adj::rdot;
 using adj::rhs_vjp;
 using adj::rk4_step;
 using adj::rk4_step_adjoint;
+using adj::rk4_step_record;
 using adj::operator+;
 using adj::operator-;
 using adj::operator*;
@@ -140,7 +141,8 @@ __global__ void __launch_bounds__(128) k_adjoint(GridDev gd, const ShotDev* __re
   const int64_t nthr = (int64_t)gridDim.x * blockDim.x;
   const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int lane = threadIdx.x & 31;
-  // scratch: [slot][field][thread], slots 0..ncheck-1 checkpoints, then kseg segment states
+  // scratch: [slot][field][thread], slots 0..ncheck-1 checkpoints, then kseg segment states,
+  // then 3 kseg stage states
   auto slot = [&](int64_t sidx, int f) -> double& { return scratch[(sidx * NF + f) * nthr + tid]; };
   extern __shared__ double zs[];  // [4][NF][blockDim.x]: RK4 stage states and lambda in
   while (true) {
@@ -196,6 +198,7 @@ __global__ void __launch_bounds__(128) k_adjoint(GridDev gd, const ShotDev* __re
     for (int f = 0; f < NF; ++f) lam[f] = 0.0;
     const double2 psi = has ? gpsi[g] : make_double2(0.0, 0.0);
     // states j*kseg .. of segment j into the segment slots (lanes whose ray reached them)
+    // stage states of the step from segment state i: slots ncheck + kseg + 3 i + (0, 1, 2)
     auto load_segment = [&](int64_t j) {
       const bool mine = has && j * kseg <= nend;
       double z[NF];
@@ -205,7 +208,11 @@ __global__ void __launch_bounds__(128) k_adjoint(GridDev gd, const ShotDev* __re
         if (!mine || j * kseg + i > nend) continue;
 #pragma unroll
         for (int f = 0; f < NF; ++f) slot(ncheck + i, f) = z[f];
-        if (i + 1 < kseg && j * kseg + i + 1 <= nend) rk4_step<D>(gd, C, z, dt);
+        if (j * kseg + i + 1 <= nend)
+          rk4_step_record<D>(gd, z, dt, [&](int s, const double* zz) {
+#pragma unroll
+            for (int f = 0; f < NF; ++f) slot(ncheck + kseg + 3 * i + s, f) = zz[f];
+          });
       }
     };
     int64_t seg_loaded = -1;
@@ -233,7 +240,9 @@ __global__ void __launch_bounds__(128) k_adjoint(GridDev gd, const ShotDev* __re
       if (act) {
 #pragma unroll
         for (int f = 0; f < NF; ++f) yn[f] = slot(ncheck + (nn - 1 - jp * kseg), f);
-        rk4_step_adjoint<D>(gd, C, yn, dt, lam, gradC, zs, blockDim.x, threadIdx.x);
+        const int64_t i = nn - 1 - jp * kseg;
+        rk4_step_adjoint<D>(gd, C, yn, dt, lam, gradC, zs, blockDim.x, threadIdx.x,
+                            [&](int s, int f) { return slot(ncheck + kseg + 3 * i + s, f); });
       }
     }
     if (!has) continue;

@@ -158,6 +158,8 @@ fga_status fga_destroy(fga_plan_t p) {
     if (b) cudaFree(b);
   for (double* e : p->E)
     if (e) cudaFree(e);
+  for (void* e : p->mixed_tabs)
+    if (e) cudaFree(e);
   for (auto& ev : p->ev)
     if (ev) cudaEventDestroy(ev);
   if (p->graph_exec) cudaGraphExecDestroy(p->graph_exec);
@@ -331,6 +333,54 @@ fga_status fga_plan(const fga_config* cfg, const double* velocity, void* stream,
       p->E[(size_t)s * d + k] = dE;
       PLAN_CUDA(cudaMemcpy(dE, E.data(), sizeof(double) * E.size(), cudaMemcpyHostToDevice));
       sh.E[k] = reinterpret_cast<const double2*>(dE);
+      if (k == 0 && cfg->precision == FGA_MIXED_TF32X3) {
+        // A operands of the tensor-core stage 2: Re-part rows (Re E, -Im E) and Im-part rows
+        // (Im E, Re E) over K = 2 jx, each split into a TF32 head and an FP32 tail
+        const int nb = sh.nb[0];
+        std::vector<float> A((size_t)4 * nb * 2 * nb);
+        auto split = [](double v, float& hi, float& lo) {
+          float f = (float)v;
+          uint32_t bits;
+          std::memcpy(&bits, &f, sizeof(bits));
+          bits &= 0xFFFFE000u;
+          std::memcpy(&hi, &bits, sizeof(hi));
+          lo = (float)(v - (double)hi);
+        };
+        for (int px = 0; px < nb; ++px)
+          for (int jx = 0; jx < nb; ++jx) {
+            const double er = E[((size_t)px * nb + jx) * 2], ei = E[((size_t)px * nb + jx) * 2 + 1];
+            const double vals[2][2] = {{er, -ei}, {ei, er}};
+            for (int part = 0; part < 2; ++part)
+              for (int c = 0; c < 2; ++c) {
+                float hi, lo;
+                split(vals[part][c], hi, lo);
+                const size_t at = (size_t)px * 2 * nb + 2 * jx + c;
+                A[(size_t)(2 * part) * nb * 2 * nb + at] = hi;
+                A[(size_t)(2 * part + 1) * nb * 2 * nb + at] = lo;
+              }
+          }
+        float* dA = nullptr;
+        PLAN_CUDA(cudaMalloc(&dA, sizeof(float) * A.size()));
+        p->mixed_tabs.push_back(dA);
+        PLAN_CUDA(cudaMemcpy(dA, A.data(), sizeof(float) * A.size(), cudaMemcpyHostToDevice));
+        sh.Etc = dA;
+      }
+    }
+    if (cfg->precision == FGA_MIXED_TF32X3) {
+      ShotDev& sh = p->shots[s];
+      std::vector<double> inv((size_t)sh.np, 0.0);
+      for (int64_t jp = 0; jp < sh.np; ++jp) {
+        const int64_t j0 = jp / sh.nb[1], j1 = jp - j0 * sh.nb[1];
+        const int64_t m0 = j0 - sh.nb[0] / 2, m1 = j1 - sh.nb[1] / 2;
+        if (j0 == 0 || j1 == 0 || (m0 == 0 && m1 == 0)) continue;  // left-out p
+        const double a = (double)m0 * sh.pscale[0], b = (double)m1 * sh.pscale[1];
+        inv[(size_t)jp] = 1.0 / std::sqrt(a * a + b * b);
+      }
+      double* dI = nullptr;
+      PLAN_CUDA(cudaMalloc(&dI, sizeof(double) * inv.size()));
+      p->mixed_tabs.push_back(dI);
+      PLAN_CUDA(cudaMemcpy(dI, inv.data(), sizeof(double) * inv.size(), cudaMemcpyHostToDevice));
+      sh.inv_pn = dI;
     }
   }
   PLAN_CUDA(cudaMalloc(&p->d_shots, sizeof(ShotDev) * cfg->nshots));
@@ -1049,7 +1099,8 @@ fga_status fga_grad(fga_plan_t p, const double* residual, double* grad) {
   const int64_t ncheck = p->nsteps / kseg + 2;
   const int64_t nthr = fga::adjoint_threads(p);
   if (nthr <= 0) return fail(p, FGA_ERR_CUDA, "occupancy query for the adjoint kernel failed", true);
-  const size_t need = (size_t)nthr * (size_t)(ncheck + kseg) * (size_t)p->nfields;
+  // checkpoints, the segment's states and the stage states of its steps
+  const size_t need = (size_t)nthr * (size_t)(ncheck + 4 * kseg) * (size_t)p->nfields;
   CUDA_OR_FAIL(p, grow(&p->d_adj_scratch, &p->adj_scratch_cap, need));
   double* dst = grad;
   bool host_out = !is_device_ptr(grad);

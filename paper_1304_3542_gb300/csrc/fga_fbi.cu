@@ -114,6 +114,14 @@ __device__ __forceinline__ double psi_plus(const ShotDev& sh, int64_t jp, double
   return out.x * out.x + out.y * out.y;
 }
 
+// TF32 head and FP32 tail of a complex value: (Re head, Re tail, Im head, Im tail).
+__device__ __forceinline__ float4 split4(double2 v) {
+  const float xr = (float)v.x, xi = (float)v.y;
+  const float hr = __uint_as_float(__float_as_uint(xr) & 0xFFFFE000u);
+  const float hi = __uint_as_float(__float_as_uint(xi) & 0xFFFFE000u);
+  return make_float4(hr, (float)(v.x - (double)hr), hi, (float)(v.y - (double)hi));
+}
+
 // Stage 1: C_f[m][n] = sum_k data_f(m, k) * E_last[n][k], f = 0, 1.
 // D == 2: m = (row r, q_z local), k runs along the last axis of the box; the
 //         result goes to the stage-1 buffer.
@@ -126,7 +134,8 @@ __global__ void __launch_bounds__(NT) k_fbi_stage1(GridDev gd, const ShotDev* __
                                                    double2* __restrict__ g1,
                                                    double2* __restrict__ psi,
                                                    double2* __restrict__ psi_f1,
-                                                   unsigned long long* __restrict__ max2) {
+                                                   unsigned long long* __restrict__ max2,
+                                                   int split_out) {
   const int s = blockIdx.z;
   const ShotDev sh = shots[s];
   constexpr int L = D - 1;  // last axis
@@ -217,8 +226,15 @@ __global__ void __launch_bounds__(NT) k_fbi_stage1(GridDev gd, const ShotDev* __
       for (int j = 0; j < 2; ++j) {
         int64_t m = m0 + ty + 16 * i, n = n0 + tx + 16 * j;
         if (m < M && n < N) {
-          g1[sh.g1_off + m * N + n] = acc0[i][j];
-          g1[sh.g1_off + plane + m * N + n] = acc1[i][j];
+          if (split_out) {
+            // mixed precision: the tensor-core stage 2 reads TF32 head/tail splits
+            float4* f = reinterpret_cast<float4*>(g1);
+            f[sh.g1_off + m * N + n] = split4(acc0[i][j]);
+            f[sh.g1_off + plane + m * N + n] = split4(acc1[i][j]);
+          } else {
+            g1[sh.g1_off + m * N + n] = acc0[i][j];
+            g1[sh.g1_off + plane + m * N + n] = acc1[i][j];
+          }
         }
       }
   } else {
@@ -559,40 +575,40 @@ __global__ void __launch_bounds__(FNT) k_fbi_stage2_tc(GridDev gd, const ShotDev
   const uint32_t tmem = *tbase;
   const uint32_t idesc = tc::idesc_f32acc(tc::kFmtTF32, FT, FT);
   const int64_t M1 = sh.nrows * sh.qn[1];
-  const double2* G0 = g1 + sh.g1_off;
-  const double2* G1p = G0 + M1 * nbz;
-  const double2* Ex = sh.E[0];
+  // the stage-1 output of the mixed precision holds (Re head, Re tail, Im head, Im tail)
+  const float4* G0s = reinterpret_cast<const float4*>(g1) + sh.g1_off;
+  const float4* G1s = G0s + M1 * nbz;
   const int64_t row0 = sh.s[0] * mxl;
   uint32_t chunks = 0;
   bool ok = true;
   for (int64_t k0 = 0; k0 < nbx; k0 += FJ) {
     if (chunks > 0) ok &= tc::mbar_wait_bounded(bar, (chunks - 1) & 1u, kFbiTries);
-    // A: E_x rows m0 .. m0+127, columns k0 .. k0+15 (16 threads per row, coalesced)
-    for (int e = tid; e < FT * FJ; e += FNT) {
-      const int r = e / FJ, j = e % FJ;
-      const int64_t m = m0 + r, k = k0 + j;
-      const double2 v = (m < nbx && k < nbx) ? __ldg(Ex + m * nbx + k) : make_double2(0.0, 0.0);
-      const int o = fbi_core_offset(r, 2 * j);
-      split_store(Arh, Arl, o, v.x);
-      split_store(Arh, Arl, o + 1, -v.y);
-      split_store(Aih, Ail, o, v.y);
-      split_store(Aih, Ail, o + 1, v.x);
+    // A: the pre-split rows m0 .. m0+127 of E_x, K = 2 k0 .. 2 k0 + 31, four floats per copy
+    for (int e = tid; e < 4 * FT * (FKC / 4); e += FNT) {
+      const int part = e / (FT * (FKC / 4)), rem = e % (FT * (FKC / 4));
+      const int r = rem / (FKC / 4), c = rem % (FKC / 4);
+      const int64_t m = m0 + r, kk = 2 * k0 + 4 * c;
+      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (m < nbx && kk < 2 * nbx)
+        v = __ldg(reinterpret_cast<const float4*>(sh.Etc + ((int64_t)part * nbx + m) * 2 * nbx + kk));
+      float* dst = part == 0 ? Arh : (part == 1 ? Arl : (part == 2 ? Aih : Ail));
+      *reinterpret_cast<float4*>(dst + fbi_core_offset(r, 4 * c)) = v;
     }
-    // B: stage-1 rows row0 + k0 .. + 15 of this q column, p_z n0 .. n0+127 (coalesced)
+    // B: the split stage-1 rows row0 + k0 .. + 15 of this q column, p_z n0 .. n0+127
     for (int e = tid; e < FT * FJ; e += FNT) {
       const int j = e / FT, r = e % FT;
       const int64_t k = k0 + j, n = n0 + r;
-      double2 v0 = make_double2(0.0, 0.0), v1 = v0;
+      float4 v0 = make_float4(0.f, 0.f, 0.f, 0.f), v1 = v0;
       if (k < nbx && n < nbz) {
         const int64_t off = ((row0 + k) * sh.qn[1] + mzl) * nbz + n;
-        v0 = __ldg(G0 + off);
-        v1 = __ldg(G1p + off);
+        v0 = __ldg(G0s + off);
+        v1 = __ldg(G1s + off);
       }
       const int o = fbi_core_offset(r, 2 * j);
-      split_store(B0h, B0l, o, v0.x);
-      split_store(B0h, B0l, o + 1, v0.y);
-      split_store(B1h, B1l, o, v1.x);
-      split_store(B1h, B1l, o + 1, v1.y);
+      *reinterpret_cast<float2*>(B0h + o) = make_float2(v0.x, v0.z);
+      *reinterpret_cast<float2*>(B0l + o) = make_float2(v0.y, v0.w);
+      *reinterpret_cast<float2*>(B1h + o) = make_float2(v1.x, v1.z);
+      *reinterpret_cast<float2*>(B1l + o) = make_float2(v1.y, v1.w);
     }
     tc::fence_proxy_async_smem();
     __syncthreads();
@@ -633,6 +649,7 @@ __global__ void __launch_bounds__(FNT) k_fbi_stage2_tc(GridDev gd, const ShotDev
   tc::fence_after_sync();
   // epilogue: thread = p_x row (TMEM lane 32 w + lane), 32 p_z columns at a time
   const double hv = gd.h[0] * gd.h[1];
+  const double inv_cq = 1.0 / cq_s;
   const int64_t m = m0 + 32 * warp + (tid & 31);
   double mymax = 0.0;
   float a0r[32], a0i[32], a1r[32], a1i[32];
@@ -650,12 +667,15 @@ __global__ void __launch_bounds__(FNT) k_fbi_stage2_tc(GridDev gd, const ShotDev
       if (n >= nbz) continue;
       const double2 p0 = make_double2(hv * (double)a0r[i], hv * (double)a0i[i]);
       const double2 p1 = make_double2(hv * (double)a1r[i], hv * (double)a1i[i]);
-      double2 o, tt;
       const int64_t jp = m * nbz + n;
-      const double a2 = psi_plus<2>(sh, jp, p0, p1, cq_s, o, tt);
+      // branch split with the tabulated 1/|p| (0 on the left-out p)
+      const double r = sh.eps * __ldg(sh.inv_pn + jp) * inv_cq;
+      const double2 tt = make_double2(-0.5 * r * p1.y, 0.5 * r * p1.x);
+      const double2 o = r > 0.0 ? make_double2(0.5 * p0.x + tt.x, 0.5 * p0.y + tt.y)
+                                : make_double2(0.0, 0.0);
       psi[sh.psi_off + ql * sh.np + jp] = o;
-      psi_f1[sh.psi_off + ql * sh.np + jp] = tt;
-      mymax = fmax(mymax, a2);
+      psi_f1[sh.psi_off + ql * sh.np + jp] = r > 0.0 ? tt : make_double2(0.0, 0.0);
+      mymax = fmax(mymax, o.x * o.x + o.y * o.y);
     }
   }
   for (int off = 16; off > 0; off >>= 1) mymax = fmax(mymax, __shfl_xor_sync(0xffffffffu, mymax, off));
@@ -710,12 +730,13 @@ cudaError_t launch_fbi(fga_plan_s* p, const double* u0, const double* u1) {
   if (g1grid.y > 65535) return cudaErrorInvalidConfiguration;
   if (D == 1) {
     k_fbi_stage1<1><<<g1grid, NT, 0, p->stream>>>(p->grid, p->d_shots, u0, u1, p->d_coef, p->d_g1,
-                                                  p->d_psi, p->d_psi_f1, p->d_max2);
+                                                  p->d_psi, p->d_psi_f1, p->d_max2, 0);
     p->launches += 1;
     return cudaGetLastError();
   }
   k_fbi_stage1<2><<<g1grid, NT, 0, p->stream>>>(p->grid, p->d_shots, u0, u1, p->d_coef, p->d_g1,
-                                                p->d_psi, p->d_psi_f1, p->d_max2);
+                                                p->d_psi, p->d_psi_f1, p->d_max2,
+                                                p->precision == FGA_MIXED_TF32X3 ? 1 : 0);
   if (maxQ > 65535) return cudaErrorInvalidConfiguration;
   p->launches += 2;
   if (p->precision == FGA_MIXED_TF32X3) {

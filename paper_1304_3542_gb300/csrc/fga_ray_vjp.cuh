@@ -369,6 +369,48 @@ __device__ void rhs_vjp(const GridDev& gd, const double* __restrict__ C, const d
   // S does not enter f
 }
 
+// One RK4 step that also hands its stage states z2 = y + h/2 k1, z3 = y + h/2 k2,
+// z4 = y + h k3 to put(stage, z) (the same arithmetic as rk4_step).
+template <int D, typename Put>
+__device__ __forceinline__ void rk4_step_record(const GridDev& gd, double* y, double dt, Put put) {
+  using Lo = Layout<D>;
+  constexpr int NF = Lo::NF;
+  double acc[NF], tmp[NF], k[NF];
+  const double h2 = 0.5 * dt, h6 = dt / 6.0, h3 = dt / 3.0;
+  rhs<D>(gd, y, k);
+#pragma unroll
+  for (int i = 0; i < NF; ++i) {
+    acc[i] = fma(h6, k[i], y[i]);
+    tmp[i] = fma(h2, k[i], y[i]);
+  }
+  put(0, tmp);
+  rhs<D>(gd, tmp, k);
+#pragma unroll
+  for (int i = 0; i < NF; ++i) {
+    acc[i] = fma(h3, k[i], acc[i]);
+    tmp[i] = fma(h2, k[i], y[i]);
+  }
+  put(1, tmp);
+  rhs<D>(gd, tmp, k);
+#pragma unroll
+  for (int i = 0; i < NF; ++i) {
+    acc[i] = fma(h3, k[i], acc[i]);
+    tmp[i] = fma(dt, k[i], y[i]);
+  }
+  put(2, tmp);
+  rhs<D>(gd, tmp, k);
+#pragma unroll
+  for (int i = 0; i < NF; ++i) y[i] = fma(h6, k[i], acc[i]);
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+    if (gd.periodic[i]) {
+      double r = fmod(y[Lo::Q + i] - gd.o[i], gd.L[i]);
+      if (r < 0) r += gd.L[i];
+      y[Lo::Q + i] = gd.o[i] + r;
+    }
+  }
+}
+
 // One RK4 step y -> y + dt/6 (k1 + 2 k2 + 2 k3 + k4) (the periodic wrap is a shift).
 template <int D>
 __device__ __forceinline__ void rk4_step(const GridDev& gd, const double* __restrict__ C, double* y,
@@ -412,26 +454,20 @@ __device__ __forceinline__ void rk4_step(const GridDev& gd, const double* __rest
 // The three stage states and the incoming lambda live in the caller's shared-memory
 // slots zs[(slot * NF + field) * nt + lane] (4 * NF values per thread) rather than in
 // registers, which the vector-Jacobian products need.
-template <int D>
+// The step's stage states z2, z3, z4 come from stage(s, f) (recorded by rk4_step_record
+// when the segment was recomputed).
+template <int D, typename Stage>
 __device__ void rk4_step_adjoint(const GridDev& gd, const double* __restrict__ C, const double* y,
                                  double dt, double* lam, double* __restrict__ gradC, double* zs,
-                                 int nt, int lane) {
+                                 int nt, int lane, Stage stage) {
   using Lo = Layout<D>;
   constexpr int NF = Lo::NF;
   auto Z = [&](int s, int f) -> double& { return zs[(s * NF + f) * nt + lane]; };
   const double h2 = 0.5 * dt, h6 = dt / 6.0, h3 = dt / 3.0;
-  {
-    double k[NF], t[NF];
-    rhs<D>(gd, y, k);
 #pragma unroll
-    for (int i = 0; i < NF; ++i) Z(0, i) = t[i] = fma(h2, k[i], y[i]);  // z2
-    rhs<D>(gd, t, k);
+  for (int s = 0; s < 3; ++s)
 #pragma unroll
-    for (int i = 0; i < NF; ++i) Z(1, i) = t[i] = fma(h2, k[i], y[i]);  // z3
-    rhs<D>(gd, t, k);
-#pragma unroll
-    for (int i = 0; i < NF; ++i) Z(2, i) = fma(dt, k[i], y[i]);  // z4
-  }
+    for (int i = 0; i < NF; ++i) Z(s, i) = stage(s, i);
 #pragma unroll
   for (int i = 0; i < NF; ++i) Z(3, i) = lam[i];  // lambda in
   double kb[NF], zb[NF], z[NF];
