@@ -526,13 +526,6 @@ __device__ __forceinline__ int fbi_core_offset(int row, int k) {
   return (((row >> 3) * FKB + (k >> 2)) * 8 + (row & 7)) * 4 + (k & 3);
 }
 
-__device__ __forceinline__ void split_store(float* hi, float* lo, int o, double v) {
-  const float f = (float)v;
-  const float h = __uint_as_float(__float_as_uint(f) & 0xFFFFE000u);
-  hi[o] = h;
-  lo[o] = (float)(v - (double)h);
-}
-
 __global__ void __launch_bounds__(FNT) k_fbi_stage2_tc(GridDev gd, const ShotDev* __restrict__ shots,
                                                       const double* __restrict__ C,
                                                       const double2* __restrict__ g1,
