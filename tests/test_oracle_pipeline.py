@@ -6,7 +6,7 @@
   periodic axis of length L, the overlap 2 exp(-L^2/(4 eps)) of neighbouring
   images of the periodised window (1e-14 at eps = 1/128, L = 1). This pins the
   FBI/reconstruction pair, the quadrature weight and the prefactors 2^{d/2} and
-  (2 pi eps)^{-3d/2} of Eqs. recons and a_formu.
+  (2 pi eps)^{-3d/2} of Eqs. recons and a_formu (d = 1, 2, 3).
 * Constant speed: the semi-analytic Fourier-space prediction derived from the
   exact rays and amplitude (the method, not the PDE) pins the whole pipeline,
   including the branch split of Eq. psi, in 1D and in 2D.
@@ -75,6 +75,21 @@ def test_frame_identity_random_data_2d_open():
                                                 indexing="ij")], axis=1)
     u = _all_p_frame(g, f, eps, s, box, 6.0, x)
     assert np.linalg.norm(u - f.ravel()) <= 1e-10 * np.linalg.norm(f)
+
+
+def test_frame_identity_random_data_3d_periodic():
+    # n = 12 per axis, q-stride 1, eps = 1.9 h^2, kappa = 4.3: the Poisson error
+    # exp(-pi^2 eps/h^2) = 7e-9, the image overlap 2 exp(-L^2/(4 eps)) = 1.2e-8 and the
+    # window cut exp(-kappa^2) = 9e-9 bound the identity at about 3e-8 (3M Gaussians)
+    n = 12
+    h = 1.0 / n
+    g = O.Grid((n,) * 3, (h,) * 3, (0.0,) * 3, (True,) * 3)
+    f = np.random.default_rng(7).standard_normal((n,) * 3)
+    axes = np.meshgrid(*(np.arange(n) / n,) * 3, indexing="ij")
+    pick = np.random.default_rng(8).choice(n ** 3, size=32, replace=False)
+    x = np.stack([a.ravel() for a in axes], axis=1)[pick]
+    u = _all_p_frame(g, f, 1.9 * h * h, (1, 1, 1), (n,) * 3, 4.3, x)
+    assert np.linalg.norm(u - f.ravel()[pick]) <= 2e-7 * np.linalg.norm(f.ravel()[pick])
 
 
 def test_frame_identity_pipeline_1d():
