@@ -92,3 +92,21 @@ def test_wrong_dtype_and_size_rejected_in_binding():
         _plan(velocity=np.ones(256, dtype=np.float32))
     with pytest.raises(ValueError):
         _plan(velocity=np.ones(255))
+
+
+def test_grid_receivers_cover_the_grid_inside_its_bounds():
+    import math
+
+    from paper_1304_3542_gb300 import autograd as FA
+    from paper_1304_3542_gb300 import workloads as WL
+
+    prob = WL.lens_2d(N=64, eps=1.0 / 400, T=0.1, dt=2e-3, s=2, box=32, tau=1e-2, kappa=8.0,
+                      k0=24 * math.pi, width2=0.004)
+    xr = FA.grid_receivers(prob)
+    assert xr.shape == (64 * 64, 2) and xr.flags["C_CONTIGUOUS"]
+    for k in range(2):
+        hi = prob.origin[k] + (prob.n[k] - 1) * prob.h[k]
+        assert xr[:, k].min() == prob.origin[k]
+        assert hi - 4 * np.spacing(hi) <= xr[:, k].max() < hi
+    # C order: the last axis runs fastest
+    assert xr[1, 1] - xr[0, 1] == prob.h[1] and xr[1, 0] == xr[0, 0]
