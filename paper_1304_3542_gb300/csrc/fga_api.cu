@@ -146,8 +146,8 @@ fga_status fga_destroy(fga_plan_t p) {
   cudaStreamSynchronize(p->stream);
   void* bufs[] = {p->d_coef, p->d_medtab, p->d_shots, p->d_in0, p->d_bbox, p->d_psi, p->d_g1,
                   p->d_max2, p->d_blk, p->d_counts, p->d_blk_first, p->d_gshot, p->d_gq, p->d_gp,
-                  p->d_gpsi, p->d_state, p->d_gcoef, p->d_tile_cnt, p->d_tile_off,
-                  p->d_tile_list, p->d_seg_off, p->d_partial, p->d_out, p->d_status,
+                  p->d_gpsi, p->d_state, p->d_gcoef, p->d_tile_off,
+                  p->d_tile_list, p->d_bin_off, p->d_seg_off, p->d_partial, p->d_out, p->d_status,
                   p->d_steps, p->d_rx, p->d_rx_off, p->d_rx_perm, p->d_traces, p->d_gsteps, p->d_g2,
                   p->d_topk, p->d_topk_hist, p->d_blk_eq,
                   p->d_adj_order, p->d_adj_bucket,
@@ -366,22 +366,6 @@ fga_status fga_plan(const fga_config* cfg, const double* velocity, void* stream,
         sh.Etc = dA;
       }
     }
-    if (cfg->precision == FGA_MIXED_TF32X3) {
-      ShotDev& sh = p->shots[s];
-      std::vector<double> inv((size_t)sh.np, 0.0);
-      for (int64_t jp = 0; jp < sh.np; ++jp) {
-        const int64_t j0 = jp / sh.nb[1], j1 = jp - j0 * sh.nb[1];
-        const int64_t m0 = j0 - sh.nb[0] / 2, m1 = j1 - sh.nb[1] / 2;
-        if (j0 == 0 || j1 == 0 || (m0 == 0 && m1 == 0)) continue;  // left-out p
-        const double a = (double)m0 * sh.pscale[0], b = (double)m1 * sh.pscale[1];
-        inv[(size_t)jp] = 1.0 / std::sqrt(a * a + b * b);
-      }
-      double* dI = nullptr;
-      PLAN_CUDA(cudaMalloc(&dI, sizeof(double) * inv.size()));
-      p->mixed_tabs.push_back(dI);
-      PLAN_CUDA(cudaMemcpy(dI, inv.data(), sizeof(double) * inv.size(), cudaMemcpyHostToDevice));
-      sh.inv_pn = dI;
-    }
   }
   PLAN_CUDA(cudaMalloc(&p->d_shots, sizeof(ShotDev) * cfg->nshots));
   PLAN_CUDA(cudaMalloc(&p->d_bbox, sizeof(int) * cfg->nshots * d * 2));
@@ -572,6 +556,10 @@ static fga_status reconstruct_capacity(fga_plan_s* p) {
     pairs += per * (size_t)sh.g_cnt;
   }
   CUDA_OR_FAIL(p, grow(&p->d_tile_list, &p->list_cap, pairs));
+  int nsplit;
+  int64_t chunk;
+  fga::bin_splits(p, &nsplit, &chunk);
+  CUDA_OR_FAIL(p, grow(&p->d_bin_off, &p->bin_cap, (size_t)p->ntiles * nsplit + 1));
   const bool tc = p->precision == FGA_MIXED_TF32X3;
   CUDA_OR_FAIL(p, grow(&p->d_partial, &p->partial_cap,
                        tc ? (fga::partial_bytes_tc(p) + 7) / 8
@@ -597,11 +585,15 @@ fga_status fga_run_graph(fga_plan_t p, double* u_dev) {
   if (st != FGA_OK) return st;
   st = trace_capacity(p);
   if (st != FGA_OK) return st;
-  int64_t key[10] = {p->G, (int64_t)p->g_cap, (int64_t)p->list_cap, (int64_t)p->partial_cap,
+  int nsplit;
+  int64_t chunk;
+  fga::bin_splits(p, &nsplit, &chunk);
+  int64_t key[13] = {p->G, (int64_t)p->g_cap, (int64_t)p->list_cap, (int64_t)p->partial_cap,
                     (int64_t)(uintptr_t)u_dev, p->nrx, p->seg, p->ray_blocks,
-                    (int64_t)(uintptr_t)p->d_part, p->ray_variant};
+                    (int64_t)(uintptr_t)p->d_part, p->ray_variant, nsplit, chunk,
+                    (int64_t)(uintptr_t)p->d_bin_off};
   bool same = p->graph_exec != nullptr;
-  for (int i = 0; i < 10; ++i) same = same && key[i] == p->graph_key[i];
+  for (int i = 0; i < 13; ++i) same = same && key[i] == p->graph_key[i];
   if (!same) {
     if (p->graph_exec) {
       cudaGraphExecDestroy(p->graph_exec);
@@ -610,7 +602,7 @@ fga_status fga_run_graph(fga_plan_t p, double* u_dev) {
     cudaGraph_t graph = nullptr;
     CUDA_OR_FAIL(p, cudaStreamBeginCapture(p->stream, cudaStreamCaptureModeThreadLocal));
     cudaError_t e = fga::launch_rays(p);
-    if (e == cudaSuccess) e = fga::launch_binning(p, nullptr);
+    if (e == cudaSuccess) e = fga::launch_binning(p);
     if (e == cudaSuccess) e = fga::launch_binning_fill(p);
     if (e == cudaSuccess)
       e = p->precision == FGA_MIXED_TF32X3 ? fga::launch_reconstruct_tc(p, u_dev)
@@ -627,7 +619,7 @@ fga_status fga_run_graph(fga_plan_t p, double* u_dev) {
       p->graph_exec = nullptr;
       return fail(p, FGA_ERR_CUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e), true);
     }
-    for (int i = 0; i < 10; ++i) p->graph_key[i] = key[i];
+    for (int i = 0; i < 13; ++i) p->graph_key[i] = key[i];
   }
   CUDA_OR_FAIL(p, cudaGraphLaunch(p->graph_exec, p->stream));
   p->launches += 12;
@@ -699,7 +691,7 @@ fga_status fga_autotune(fga_plan_t p, double* u_dev, int64_t* choice) {
     if (st != FGA_OK) return st;
     float ms = 0.0f;
     CUDA_OR_FAIL(p, time_best(p, 2, [&] {
-      cudaError_t e = fga::launch_binning(p, nullptr);
+      cudaError_t e = fga::launch_binning(p);
       if (e == cudaSuccess) e = fga::launch_binning_fill(p);
       if (e == cudaSuccess)
         e = tc ? fga::launch_reconstruct_tc(p, u_dev) : fga::launch_reconstruct(p, u_dev);
@@ -754,7 +746,7 @@ fga_status fga_reconstruct(fga_plan_t p, double* u_out) {
   const GridDev& gd = p->grid;
   const bool tc = p->precision == FGA_MIXED_TF32X3;
   CUDA_OR_FAIL(p, cudaEventRecord(p->ev[5], p->stream));
-  CUDA_OR_FAIL(p, fga::launch_binning(p, nullptr));
+  CUDA_OR_FAIL(p, fga::launch_binning(p));
   CUDA_OR_FAIL(p, fga::launch_binning_fill(p));
   CUDA_OR_FAIL(p, cudaEventRecord(p->ev[6], p->stream));
   const size_t n_all = (size_t)p->nshots * gd.npts;

@@ -509,9 +509,14 @@ __global__ void k_fbi3_stage3(GridDev gd, const ShotDev* __restrict__ shots,
 //   B_f[pz][2j] = Re G1_f, B_f[pz][2j+1] = Im G1_f,
 // with every operand split into a TF32 head and an FP32 tail and the three products
 // hi*hi + hi*lo + lo*hi accumulated in FP32 in tensor memory (four accumulators of 128
-// columns: field 0 re/im, field 1 re/im). The epilogue forms psi+ in FP64 as the FP64
-// stage does. Operands are K-major in shared memory without swizzle (8-row x 16-byte
-// core matrices), one CTA per SM (128 KiB of operands, all 512 TMEM columns).
+// columns: field 0 re/im, field 1 re/im). Operands are K-major in shared memory without
+// swizzle (8-row x 16-byte core matrices), one CTA per SM (128 KiB of operands, all 512
+// TMEM columns). Epilogue: each warp moves its 32 accumulator rows through shared memory
+// (a 32 x 32 block at a time) so that the branch split runs with lane = p_z column and
+// every store of the warp is one contiguous row segment; the split is FP32 arithmetic on
+// the FP32 accumulations (with 1/|p| from rsqrtf), stored as FP64, and the maximum of
+// |psi+|^2 is taken in FP64 over the stored values (squares of FP32 values are exact in
+// FP64, so it equals the selection's own |psi+|^2).
 constexpr int FT = 128;        // tile edge in p_x (GEMM M) and p_z (GEMM N)
 constexpr int FJ = 16;         // complex jx per chunk -> K = 32
 constexpr int FKC = 2 * FJ;
@@ -519,8 +524,30 @@ constexpr int FKB = FKC / 4;   // core matrices along K
 constexpr int FNT = 128;
 constexpr uint32_t kFbiLBO = 128, kFbiSBO = FKB * 128;
 constexpr size_t kFbiOperand = (size_t)FT * FKC * sizeof(float);  // 16 KiB
-constexpr size_t kFbiSmem = 8 * kFbiOperand + 64;
+constexpr int kStageLd = 33;  // float4 per staged row: 32 columns + 1 of padding (no bank conflicts)
+constexpr size_t kFbiStageOff = 8 * kFbiOperand + 128;
+constexpr size_t kFbiSmem = kFbiStageOff + (size_t)4 * 32 * kStageLd * sizeof(float4);
 constexpr uint32_t kFbiTries = 1u << 22;
+
+// IEEE binary32 -> binary64 in integer arithmetic (exact, keeps the FP64 pipe free):
+// re-bias the exponent and widen the significand; a subnormal m 2^-149 is normalised at
+// its leading bit b (value 1.f 2^(b-149)); infinities and NaNs keep exponent 0x7ff.
+__device__ __forceinline__ double widen_f32(float f) {
+  const uint32_t u = __float_as_uint(f);
+  const uint64_t sign = (uint64_t)(u >> 31) << 63;
+  const uint32_t e = (u >> 23) & 0xffu, m = u & 0x7fffffu;
+  uint64_t bits;
+  if (e != 0u) {
+    const uint64_t ed = e == 0xffu ? 0x7ffull : (uint64_t)(e + 896u);
+    bits = sign | (ed << 52) | ((uint64_t)m << 29);
+  } else if (m != 0u) {
+    const int b = 31 - __clz(m);
+    bits = sign | ((uint64_t)(b + 874) << 52) | (((uint64_t)m << (52 - b)) & 0xfffffffffffffull);
+  } else {
+    bits = sign;
+  }
+  return __longlong_as_double((long long)bits);
+}
 
 __device__ __forceinline__ int fbi_core_offset(int row, int k) {
   return (((row >> 3) * FKB + (k >> 2)) * 8 + (row & 7)) * 4 + (k & 3);
@@ -640,11 +667,17 @@ __global__ void __launch_bounds__(FNT) k_fbi_stage2_tc(GridDev gd, const ShotDev
     if (chunks > 0) tc::mbar_wait_bounded(bar, (chunks - 1) & 1u, kFbiTries);
   }
   tc::fence_after_sync();
-  // epilogue: thread = p_x row (TMEM lane 32 w + lane), 32 p_z columns at a time
+  // epilogue: TMEM lane 32 w + l holds p_x row m0 + 32 w + l; a warp stages 32 rows x 32
+  // p_z columns, then sweeps them row by row with lane = column
+  const int lane = tid & 31;
+  float4* stage = reinterpret_cast<float4*>(smem + kFbiStageOff) + warp * 32 * kStageLd;
   const double hv = gd.h[0] * gd.h[1];
-  const double inv_cq = 1.0 / cq_s;
-  const int64_t m = m0 + 32 * warp + (tid & 31);
-  double mymax = 0.0;
+  const float h2 = (float)(0.5 * hv);                    // psi_f = hv * acc; psi+ = psi0/2 + ...
+  const float c1 = (float)(0.5 * hv * sh.eps / cq_s);    // ... i (eps/(2 c(q) |p|)) hv acc1
+  const float psx = (float)sh.pscale[0], psz = (float)sh.pscale[1];
+  double2* out0 = psi + sh.psi_off + ql * sh.np;
+  double2* out1 = psi_f1 + sh.psi_off + ql * sh.np;
+  unsigned long long mymax = 0ull;  // bits of the largest |psi+|^2 (non-negative doubles order as integers)
   float a0r[32], a0i[32], a1r[32], a1i[32];
 #pragma unroll 1
   for (int cb = 0; cb < FT; cb += 32) {
@@ -653,26 +686,41 @@ __global__ void __launch_bounds__(FNT) k_fbi_stage2_tc(GridDev gd, const ShotDev
     tc::tmem_ld_32x32b_x32(lane_base + FT, a0i);
     tc::tmem_ld_32x32b_x32(lane_base + 2 * FT, a1r);
     tc::tmem_ld_32x32b_x32(lane_base + 3 * FT, a1i);
-    if (!ok || m >= nbx) continue;
 #pragma unroll
-    for (int i = 0; i < 32; ++i) {
-      const int64_t n = n0 + cb + i;
-      if (n >= nbz) continue;
-      const double2 p0 = make_double2(hv * (double)a0r[i], hv * (double)a0i[i]);
-      const double2 p1 = make_double2(hv * (double)a1r[i], hv * (double)a1i[i]);
-      const int64_t jp = m * nbz + n;
-      // branch split with the tabulated 1/|p| (0 on the left-out p)
-      const double r = sh.eps * __ldg(sh.inv_pn + jp) * inv_cq;
-      const double2 tt = make_double2(-0.5 * r * p1.y, 0.5 * r * p1.x);
-      const double2 o = r > 0.0 ? make_double2(0.5 * p0.x + tt.x, 0.5 * p0.y + tt.y)
-                                : make_double2(0.0, 0.0);
-      psi[sh.psi_off + ql * sh.np + jp] = o;
-      psi_f1[sh.psi_off + ql * sh.np + jp] = r > 0.0 ? tt : make_double2(0.0, 0.0);
-      mymax = fmax(mymax, o.x * o.x + o.y * o.y);
+    for (int i = 0; i < 32; ++i) stage[lane * kStageLd + i] = make_float4(a0r[i], a0i[i], a1r[i], a1i[i]);
+    __syncwarp();
+    const int64_t n = n0 + cb + lane;
+    const int mz = (int)(n - nbz / 2);
+    const float pz = (float)mz * psz;
+    if (ok) {
+#pragma unroll 2
+      for (int rr = 0; rr < 32; ++rr) {
+        const int64_t m = m0 + 32 * warp + rr;  // uniform over the warp
+        if (m >= nbx) break;
+        if (n >= nbz) continue;
+        const float4 v = stage[rr * kStageLd + lane];
+        const int mx = (int)(m - nbx / 2);
+        const float px = (float)mx * psx;
+        // left-out p: the Nyquist index of either axis and p = 0 (as psi_plus<2>)
+        const bool valid = m != 0 && n != 0 && !(mx == 0 && mz == 0);
+        const float r = valid ? c1 * rsqrtf(fmaf(px, px, pz * pz)) : 0.0f;
+        const float tx = valid ? -r * v.w : 0.0f, ty = valid ? r * v.z : 0.0f;
+        const float ox = valid ? fmaf(h2, v.x, tx) : 0.0f, oy = valid ? fmaf(h2, v.y, ty) : 0.0f;
+        const double2 o = make_double2(widen_f32(ox), widen_f32(oy));
+        const int64_t jp = m * nbz + n;
+        out0[jp] = o;
+        out1[jp] = make_double2(widen_f32(tx), widen_f32(ty));
+        const unsigned long long a2 = (unsigned long long)__double_as_longlong(o.x * o.x + o.y * o.y);
+        if (a2 <= 0x7ff0000000000000ull && a2 > mymax) mymax = a2;  // NaN left out, as fmax does
+      }
     }
+    __syncwarp();
   }
-  for (int off = 16; off > 0; off >>= 1) mymax = fmax(mymax, __shfl_xor_sync(0xffffffffu, mymax, off));
-  if ((tid & 31) == 0) atomic_max_nonneg(max2 + s, mymax);
+  for (int off = 16; off > 0; off >>= 1) {
+    const unsigned long long o = __shfl_xor_sync(0xffffffffu, mymax, off);
+    mymax = o > mymax ? o : mymax;
+  }
+  if ((tid & 31) == 0) atomic_max_nonneg(max2 + s, __longlong_as_double((long long)mymax));
   tc::fence_before_sync();
   __syncthreads();
   if (warp == 0) tc::tmem_dealloc(tmem, 4 * FT);

@@ -34,18 +34,23 @@ constexpr int CH1 = 32;  // Gaussians per chunk (1D)
 constexpr int64_t SEG2 = 1024;  // default Gaussians per work item (2D)
 constexpr int64_t SEG1 = 512;   // default Gaussians per work item (1D)
 constexpr int64_t kPartialBudget = (int64_t)4 << 30;  // bytes of partial tiles at most
+constexpr int64_t kBinChunk = 8192;  // Gaussians per binning split (at least)
 
-// Pass 1 (FILL = false): number of Gaussians per tile. Pass 2 (FILL = true): the
-// ordered list, written at the tile's offset. One CTA per tile scans the shot's
-// Gaussians in order (block-wide ordered compaction per chunk of NT).
+// Pass 1 (FILL = false): number of Gaussians of each (tile, split), a split being a run
+// of `chunk` consecutive Gaussians of the tile's shot. Pass 2 (FILL = true): the ordered
+// list, each (tile, split) written at its own offset. One CTA per (tile, split),
+// blockIdx.x = tile * nsplit + split, scans its run in order (block-wide ordered
+// compaction per chunk of NT); with the splits' offsets in tile-major order every tile's
+// list is ordered by Gaussian index, whatever nsplit is.
 template <int D, bool FILL>
 __global__ void __launch_bounds__(NT) k_bin(GridDev gd, const ShotDev* __restrict__ shots, int nshots,
                                             double kappa, const double* __restrict__ state,
                                             int64_t ld, int64_t* __restrict__ cnt,
                                             const int64_t* __restrict__ off,
                                             int32_t* __restrict__ list, int64_t list_cap,
-                                            int* __restrict__ status) {
-  const int64_t t = blockIdx.x;
+                                            int nsplit, int64_t chunk, int* __restrict__ status) {
+  const int64_t t = blockIdx.x / nsplit;
+  const int64_t split = blockIdx.x - t * nsplit;
   const int s = shot_of_tile(shots, nshots, t);
   const ShotDev& sh = shots[s];
   int64_t a[D], b[D];
@@ -53,12 +58,15 @@ __global__ void __launch_bounds__(NT) k_bin(GridDev gd, const ShotDev* __restric
   const double cut = kappa * sh.sqrt_eps;
   __shared__ int warp_tot[NT / 32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  int64_t base = FILL ? off[t] : 0;
+  const int64_t gend = sh.g_off + sh.g_cnt;
+  const int64_t gb = sh.g_off + split * chunk;
+  const int64_t ge = gb < gend && gend - gb > chunk ? gb + chunk : gend;
+  int64_t base = FILL ? off[blockIdx.x] : 0;
   int64_t total = 0;
-  for (int64_t g0 = sh.g_off; g0 < sh.g_off + sh.g_cnt; g0 += NT) {
+  for (int64_t g0 = gb; g0 < ge; g0 += NT) {
     int64_t g = g0 + threadIdx.x;
     bool f = false;
-    if (g < sh.g_off + sh.g_cnt) {
+    if (g < ge) {
       double Q[D];
 #pragma unroll
       for (int k = 0; k < D; ++k) Q[k] = state[k * ld + g];
@@ -82,7 +90,15 @@ __global__ void __launch_bounds__(NT) k_bin(GridDev gd, const ShotDev* __restric
     total += all;
     __syncthreads();
   }
-  if (!FILL && threadIdx.x == 0) cnt[t] = total;
+  if (!FILL && threadIdx.x == 0) cnt[blockIdx.x] = total;
+}
+
+// Offsets of the tiles' lists from the scanned (tile, split) offsets (entry ntiles: the
+// total).
+__global__ void k_tile_offsets(const int64_t* __restrict__ split_off, int nsplit, int64_t ntiles,
+                               int64_t* __restrict__ tile_off) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t <= ntiles) tile_off[t] = split_off[t * nsplit];
 }
 
 // Per-axis factor of one Gaussian at grid index i (all images inside the window).
@@ -381,27 +397,53 @@ __global__ void __launch_bounds__(NT) k_reduce(GridDev gd, const ShotDev* __rest
 
 }  // namespace
 
-// Counts per tile, then the exclusive scan; *needed_pairs is not known until the
-// caller reads d_tile_off[ntiles] back.
-cudaError_t launch_binning(fga_plan_s* p, size_t* needed_pairs) {
-  (void)needed_pairs;
+// Splits of the binning: runs of at least kBinChunk Gaussians, so that tiles x splits
+// CTAs fill the GPU even when a shot has few tiles; at most 2^30 CTAs.
+void bin_splits(const fga_plan_s* p, int* nsplit, int64_t* chunk) {
+  int64_t gmax = 1;
+  for (const auto& sh : p->shots) gmax = std::max<int64_t>(gmax, sh.g_cnt);
+  int64_t ns = (gmax + kBinChunk - 1) / kBinChunk;
+  ns = std::max<int64_t>(1, std::min<int64_t>(ns, ((int64_t)1 << 30) / std::max<int64_t>(p->ntiles, 1)));
+  *nsplit = (int)ns;
+  *chunk = (gmax + ns - 1) / ns;
+}
+
+// Counts per (tile, split), their exclusive scan in tile-major order, and the tiles'
+// list offsets d_tile_off (the total at d_tile_off[ntiles]).
+cudaError_t launch_binning(fga_plan_s* p) {
   if (p->ntiles == 0) return cudaSuccess;
+  int nsplit;
+  int64_t chunk;
+  bin_splits(p, &nsplit, &chunk);
+  const int64_t items = p->ntiles * nsplit;
+  if ((size_t)items + 1 > p->bin_cap) return cudaErrorInvalidValue;  // capacity not set up
   auto bin = p->grid.dim == 1 ? k_bin<1, false> : (p->grid.dim == 2 ? k_bin<2, false> : k_bin<3, false>);
-  bin<<<(unsigned)p->ntiles, NT, 0, p->stream>>>(p->grid, p->d_shots, p->nshots, p->kappa, p->d_state,
-                                                 (int64_t)p->g_cap, p->d_tile_off, nullptr, nullptr,
-                                                 0, p->d_status);
+  bin<<<(unsigned)items, NT, 0, p->stream>>>(p->grid, p->d_shots, p->nshots, p->kappa, p->d_state,
+                                             (int64_t)p->g_cap, p->d_bin_off, nullptr, nullptr, 0,
+                                             nsplit, chunk, p->d_status);
   p->launches += 1;
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  return launch_scan(p, p->d_tile_off, p->ntiles);
+  e = launch_scan(p, p->d_bin_off, items);
+  if (e != cudaSuccess) return e;
+  k_tile_offsets<<<(unsigned)((p->ntiles + 256) / 256), 256, 0, p->stream>>>(p->d_bin_off, nsplit,
+                                                                            p->ntiles, p->d_tile_off);
+  p->launches += 1;
+  return cudaGetLastError();
 }
 
 cudaError_t launch_binning_fill(fga_plan_s* p) {
   if (p->ntiles == 0) return cudaSuccess;
+  int nsplit;
+  int64_t chunk;
+  bin_splits(p, &nsplit, &chunk);
+  const int64_t items = p->ntiles * nsplit;
+  if ((size_t)items + 1 > p->bin_cap) return cudaErrorInvalidValue;
   auto fill = p->grid.dim == 1 ? k_bin<1, true> : (p->grid.dim == 2 ? k_bin<2, true> : k_bin<3, true>);
-  fill<<<(unsigned)p->ntiles, NT, 0, p->stream>>>(p->grid, p->d_shots, p->nshots, p->kappa, p->d_state,
-                                                  (int64_t)p->g_cap, nullptr, p->d_tile_off,
-                                                  p->d_tile_list, (int64_t)p->list_cap, p->d_status);
+  fill<<<(unsigned)items, NT, 0, p->stream>>>(p->grid, p->d_shots, p->nshots, p->kappa, p->d_state,
+                                              (int64_t)p->g_cap, nullptr, p->d_bin_off,
+                                              p->d_tile_list, (int64_t)p->list_cap, nsplit, chunk,
+                                              p->d_status);
   p->launches += 1;
   return cudaGetLastError();
 }
@@ -746,21 +788,21 @@ extern "C" fga_status fga_reconstruct_static(int dim, const int64_t* n, const do
     ST_CUDA(cudaMemcpyAsync(d_shot, &sh, sizeof(ShotDev), cudaMemcpyHostToDevice, st));
     if (dim == 1) {
       k_bin<1, false><<<(unsigned)ntiles, NT, 0, st>>>(gd, d_shot, 1, kappa, qp, nG, d_off, nullptr,
-                                                       nullptr, 0, d_status);
+                                                       nullptr, 0, 1, sh.g_cnt, d_status);
     } else {
       k_bin<2, false><<<(unsigned)ntiles, NT, 0, st>>>(gd, d_shot, 1, kappa, qp, nG, d_off, nullptr,
-                                                       nullptr, 0, d_status);
+                                                       nullptr, 0, 1, sh.g_cnt, d_status);
     }
     ST_CUDA(cudaGetLastError());
     ST_CUDA(launch_scan_on(st, d_off, ntiles));
     if (dim == 1) {
       k_bin<1, true><<<(unsigned)ntiles, NT, 0, st>>>(gd, d_shot, 1, kappa, qp, nG, nullptr, d_off,
-                                                      d_list, kStaticMaxPairs, d_status);
+                                                      d_list, kStaticMaxPairs, 1, sh.g_cnt, d_status);
       k_gather1_tile_add<<<(unsigned)ntiles, NT, 0, st>>>(gd, d_shot, kappa, qp, nG, cf, d_off,
                                                           d_list, kStaticMaxPairs, u);
     } else {
       k_bin<2, true><<<(unsigned)ntiles, NT, 0, st>>>(gd, d_shot, 1, kappa, qp, nG, nullptr, d_off,
-                                                      d_list, kStaticMaxPairs, d_status);
+                                                      d_list, kStaticMaxPairs, 1, sh.g_cnt, d_status);
       k_gather2_tile_add<<<(unsigned)ntiles, NT, 0, st>>>(gd, d_shot, kappa, qp, nG, cf, d_off,
                                                           d_list, kStaticMaxPairs, u);
     }
