@@ -2,7 +2,8 @@
 
 Not the method: the accuracy-versus-N sweep of the paper's numerical section compares
 FGA fields with a fine-grid solve of the PDE, and this is that solve (test
-infrastructure, plain numpy/scipy; shares nothing with the CUDA path).
+infrastructure: numpy/scipy set-up, the time loop in plain PyTorch CPU tensor operations
+so that it uses the host's cores; shares nothing with the CUDA path).
 
 * Space: 8th-order central second differences on a grid refined `refine` times.
 * Time: fourth-order two-step scheme (leapfrog with the modified-equation correction),
@@ -20,6 +21,7 @@ from __future__ import annotations
 import math
 
 import numpy as np
+import torch
 from scipy import ndimage
 
 # 8th-order central weights of the second derivative: w0, w1..w4 (times 1/h^2)
@@ -33,16 +35,16 @@ def spline_velocity(coef: np.ndarray, h, x: np.ndarray, z: np.ndarray) -> np.nda
                                    prefilter=False)
 
 
-def laplacian8(u: np.ndarray, inv_h2: float, out: np.ndarray) -> np.ndarray:
+def laplacian8(u: torch.Tensor, inv_h2: float, out: torch.Tensor) -> torch.Tensor:
     """8th-order Laplacian of u with u = 0 beyond the array (Dirichlet)."""
-    out[...] = 2.0 * W8[0] * u
+    torch.mul(u, 2.0 * W8[0], out=out)
     for k in range(1, 5):
         w = W8[k]
-        out[k:, :] += w * u[:-k, :]
-        out[:-k, :] += w * u[k:, :]
-        out[:, k:] += w * u[:, :-k]
-        out[:, :-k] += w * u[:, k:]
-    out *= inv_h2
+        out[k:, :].add_(u[:-k, :], alpha=w)
+        out[:-k, :].add_(u[k:, :], alpha=w)
+        out[:, k:].add_(u[:, :-k], alpha=w)
+        out[:, :-k].add_(u[:, k:], alpha=w)
+    out.mul_(inv_h2)
     return out
 
 
@@ -80,11 +82,11 @@ def solve(coef: np.ndarray, h, n, f0, f1, T: float, refine: int = 2, pad: float 
     half = 0.5 * hf
     inside = ((X >= -half) & (X <= (n[0] - 1) * h[0] + half) & (Z >= -half)
               & (Z <= (n[1] - 1) * h[1] + half))
-    u0 = np.where(inside, f0(X, Z), 0.0)
-    u1 = np.where(inside, f1(X, Z), 0.0)
-    c2 = c * c
+    u0 = torch.from_numpy(np.where(inside, f0(X, Z), 0.0))
+    u1 = torch.from_numpy(np.where(inside, f1(X, Z), 0.0))
+    c2 = torch.from_numpy(c * c)
     inv_h2 = 1.0 / (hf * hf)
-    lap = np.empty_like(u0)
+    lap = torch.empty_like(u0)
 
     def M(u):
         return c2 * laplacian8(u, inv_h2, lap)
@@ -98,5 +100,6 @@ def solve(coef: np.ndarray, h, n, f0, f1, T: float, refine: int = 2, pad: float 
         Mc = M(cur)
         nxt = 2.0 * cur - prev + a2 * Mc + a4 * M(Mc)
         prev, cur = cur, nxt
+    cur = cur.numpy()
     uc = cur[npad:npad + (n[0] - 1) * refine + 1:refine, npad:npad + (n[1] - 1) * refine + 1:refine]
     return np.ascontiguousarray(uc), {"fine_shape": nf, "dt": dt, "steps": nsteps, "cmax": cmax}

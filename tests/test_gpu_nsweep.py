@@ -1,0 +1,83 @@
+"""Accuracy against the number of Gaussians: the N-sweep of the paper's numerical section
+(N = 6, 48, 521, 5650 largest |psi| per branch), continued by decades to 56500 and
+565000, and the threshold set |psi+| >= 1e-3 max, on the layered model with a 15 Hz
+Ricker ring at (4.6, 1.5) km, T = 0.25 s, each field against a finite-difference solve
+of the wave equation in the same medium (`fd_reference.py`, 8th order in space on a
+grid refined twice, 4th order in time).
+
+Checks: the error falls at every step of N, and the threshold set reaches the method's
+own accuracy at this eps. Run with -s to see the table.
+"""
+
+import math
+
+import numpy as np
+import pytest
+
+import fd_reference as FD
+from paper_1304_3542_gb300 import fga as F
+from paper_1304_3542_gb300 import workloads as WL
+
+pytestmark = pytest.mark.gpu
+
+SRC = (4.6, 1.5)
+FREQ = 15.0
+T = 0.25
+NS = (6, 48, 521, 5650, 56500, 565000)
+
+
+def _problem():
+    return WL.layered_single(T=T, src=SRC, f=FREQ)
+
+
+def _fd_field(prob):
+    cs = float(prob.velocity[int(round(SRC[0] / prob.h[0])), int(round(SRC[1] / prob.h[1]))])
+    t0 = 1.0 / FREQ
+
+    def f0(X, Z):
+        return WL.ricker(t0 - np.hypot(X - SRC[0], Z - SRC[1]) / cs, FREQ)
+
+    def f1(X, Z):
+        return WL.ricker_dt(t0 - np.hypot(X - SRC[0], Z - SRC[1]) / cs, FREQ)
+
+    # the grid data of the shot are these functions at the grid points
+    X, Z = np.meshgrid(prob.h[0] * np.arange(prob.n[0]), prob.h[1] * np.arange(prob.n[1]),
+                       indexing="ij")
+    sh = prob.shots[0]
+    assert np.abs(f0(X, Z) - sh.u0).max() <= 1e-12 and np.abs(f1(X, Z) - sh.u1).max() <= 1e-9
+    u, _ = FD.solve(prob.velocity, prob.h, prob.n, f0, f1, T, refine=2, pad=0.75)
+    return u
+
+
+def _fga_field(prob, keep_n):
+    import torch
+
+    plan = F.plan_from_problem(prob.with_(keep_n=keep_n),
+                               stream=torch.cuda.current_stream().cuda_stream)
+    u0, u1 = F.stacked_initial_data(prob)
+    counts = plan.decompose(torch.from_numpy(u0).cuda(), torch.from_numpy(u1).cuda())
+    plan.propagate()
+    u = plan.reconstruct()[0]
+    plan.close()
+    return u, int(np.asarray(counts).ravel()[0])
+
+
+def test_error_falls_with_the_number_of_gaussians():
+    prob = _problem()
+    ufd = _fd_field(prob)
+    nrm = np.linalg.norm(ufd)
+    rows = []
+    for n in NS:
+        u, cnt = _fga_field(prob, n)
+        assert cnt == n
+        rows.append((n, np.linalg.norm(u - ufd) / nrm))
+    u, cnt = _fga_field(prob, 0)
+    err_tau = np.linalg.norm(u - ufd) / nrm
+    print("\nN per branch | rel-L2 error vs FD")
+    for n, e in rows:
+        print("%12d | %.4f" % (n, e))
+    print("%12d | %.4f  (threshold 1e-3: all |psi+| >= 1e-3 max)" % (cnt, err_tau))
+    errs = [e for _, e in rows]
+    assert all(b < a for a, b in zip(errs, errs[1:])), errs
+    assert err_tau <= errs[-1] * 1.05
+    assert err_tau <= 0.07, err_tau  # measured 0.0558: the method's O(eps) error at eps = 0.024 km
