@@ -9,7 +9,7 @@ Checks: the error falls at every step of N, and the threshold set reaches the me
 own accuracy at this eps. Run with -s to see the table.
 """
 
-import math
+import os
 
 import numpy as np
 import pytest
@@ -20,14 +20,27 @@ from paper_1304_3542_gb300 import workloads as WL
 
 pytestmark = pytest.mark.gpu
 
+
+
+def _paper_sweep():
+    """N values, T and dt of the paper's experiment (tests/golden/nsweep_paper.txt)."""
+    vals = {}
+    with open(os.path.join(os.path.dirname(__file__), "golden", "nsweep_paper.txt")) as f:
+        for line in f:
+            if line.strip() and not line.startswith("#"):
+                key, *rest = line.split()
+                vals[key] = rest
+    return [int(v) for v in vals["N"]], float(vals["T_s"][0]), float(vals["dt_s"][0])
+
+
+PAPER_N, T, DT = _paper_sweep()
 SRC = (4.6, 1.5)
 FREQ = 15.0
-T = 0.25
-NS = (6, 48, 521, 5650, 56500, 565000)
+NS = tuple(PAPER_N) + (56500, 565000)  # the paper's values, then on by decades
 
 
 def _problem():
-    return WL.layered_single(T=T, src=SRC, f=FREQ)
+    return WL.layered_single(T=T, dt=DT, src=SRC, f=FREQ)
 
 
 def _fd_field(prob):
