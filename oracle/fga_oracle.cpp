@@ -17,6 +17,9 @@
 //     dzP), the amplitude equation (Eq. a_formu with Z from Eq. op_zZ) and the
 //     action S, integrated with classical fourth-order Runge-Kutta (Numerical
 //     test section);
+//   * the divided-difference alternative for d_z Q and d_z P (the passage after
+//     Eq. op_zZ): auxiliary rays from (q +- dq_j e_j, p) and (q, p +- dp_j e_j)
+//     integrated with the ray, Z and dZ/dt from central differences across them;
 //   * the reconstruction sum (Eq. recons), evaluated term by term with
 //     std::exp of the full complex exponent;
 //   * a brute-force FBI direct sum (Eq. psi) used only to pin the FFT route.
@@ -319,6 +322,115 @@ void rk4_step(const Grid& g, const double* C, int sigma, State& y, double dt) {
   y = out;
 }
 
+// ---------------------------------------------------------------------------
+// Divided-difference form of Z (the alternative to Eqs. dzQ, dzP named after Eq.
+// op_zZ). Besides its own ray the Gaussian carries 4d auxiliary rays, r = 4j + m:
+// m = 0, 1 start at q +- dq_j e_j (p unchanged), m = 2, 3 at p +- dp_j e_j (q
+// unchanged); all follow Eq. characline. With d_z = d_q - i d_p (Eq. op_zZ) and
+// central differences,
+//   Z_jk = d_{z_j}(Q_k + i P_k) = (Dq_j Q_k + Dp_j P_k) + i (Dq_j P_k - Dp_j Q_k),
+//   Dq_j X = (X[4j] - X[4j+1])/(2 dq_j),  Dp_j X = (X[4j+2] - X[4j+3])/(2 dp_j),
+// and dZ/dt the same differences of the auxiliary rays' right-hand sides; the
+// amplitude and the action then follow Eq. a_formu and dS/dt = P.dQ/dt - H.
+// ---------------------------------------------------------------------------
+struct DDState {
+  double Q[3], P[3];          // the Gaussian's own ray
+  double Qa[12][3], Pa[12][3];  // the auxiliary rays
+  cplx a;
+  double S;
+};
+
+void dd_axpy(int d, const DDState& y, double h, const DDState& k, DDState& out) {
+  for (int i = 0; i < d; ++i) {
+    out.Q[i] = y.Q[i] + h * k.Q[i];
+    out.P[i] = y.P[i] + h * k.P[i];
+  }
+  for (int r = 0; r < 4 * d; ++r)
+    for (int i = 0; i < d; ++i) {
+      out.Qa[r][i] = y.Qa[r][i] + h * k.Qa[r][i];
+      out.Pa[r][i] = y.Pa[r][i] + h * k.Pa[r][i];
+    }
+  out.a = y.a + h * k.a;
+  out.S = y.S + h * k.S;
+}
+
+// Z (or dZ/dt, from the auxiliary rays' rates) by central differences.
+void dd_matrix(int d, const double Qa[12][3], const double Pa[12][3], const double* dq,
+               const double* dp, cplx Z[3][3]) {
+  const cplx I(0.0, 1.0);
+  for (int j = 0; j < d; ++j)
+    for (int k = 0; k < d; ++k) {
+      double DqQ = (Qa[4 * j][k] - Qa[4 * j + 1][k]) / (2.0 * dq[j]);
+      double DqP = (Pa[4 * j][k] - Pa[4 * j + 1][k]) / (2.0 * dq[j]);
+      double DpQ = (Qa[4 * j + 2][k] - Qa[4 * j + 3][k]) / (2.0 * dp[j]);
+      double DpP = (Pa[4 * j + 2][k] - Pa[4 * j + 3][k]) / (2.0 * dp[j]);
+      Z[j][k] = (DqQ + DpP) + I * (DqP - DpQ);
+    }
+}
+
+void dd_rhs(const Grid& g, const double* C, int sigma, const double* dq, const double* dp,
+            const DDState& y, DDState& dy) {
+  int d = g.dim;
+  std::memset(&dy, 0, sizeof(DDState));
+  HamDerivs hd = hamiltonian(g, C, sigma, y.Q, y.P);
+  for (int k = 0; k < d; ++k) {
+    dy.Q[k] = hd.dHdP[k];
+    dy.P[k] = -hd.dHdQ[k];
+  }
+  for (int r = 0; r < 4 * d; ++r) {
+    HamDerivs ha = hamiltonian(g, C, sigma, y.Qa[r], y.Pa[r]);
+    for (int k = 0; k < d; ++k) {
+      dy.Qa[r][k] = ha.dHdP[k];
+      dy.Pa[r][k] = -ha.dHdQ[k];
+    }
+  }
+  cplx Z[3][3], dZ[3][3];
+  dd_matrix(d, y.Qa, y.Pa, dq, dp, Z);
+  dd_matrix(d, dy.Qa, dy.Pa, dq, dp, dZ);
+  double dot = 0.0;
+  for (int k = 0; k < d; ++k) dot += hd.dHdP[k] * hd.dHdQ[k];
+  dy.a = y.a * (dot / hd.H) + 0.5 * y.a * trace_solve(d, Z, dZ);
+  double pq = 0.0;
+  for (int k = 0; k < d; ++k) pq += y.P[k] * dy.Q[k];
+  dy.S = pq - hd.H;
+}
+
+// The auxiliary rays are not wrapped on periodic axes (the medium is periodic, and
+// their differences must not jump by a period); the Gaussian's own ray is.
+void dd_rk4_step(const Grid& g, const double* C, int sigma, const double* dq, const double* dp,
+                 DDState& y, double dt) {
+  int d = g.dim;
+  DDState k1, k2, k3, k4, tmp;
+  std::memset(&tmp, 0, sizeof(DDState));
+  dd_rhs(g, C, sigma, dq, dp, y, k1);
+  dd_axpy(d, y, 0.5 * dt, k1, tmp);
+  dd_rhs(g, C, sigma, dq, dp, tmp, k2);
+  dd_axpy(d, y, 0.5 * dt, k2, tmp);
+  dd_rhs(g, C, sigma, dq, dp, tmp, k3);
+  dd_axpy(d, y, dt, k3, tmp);
+  dd_rhs(g, C, sigma, dq, dp, tmp, k4);
+  DDState out = y;
+  for (int i = 0; i < d; ++i) {
+    out.Q[i] = y.Q[i] + dt / 6.0 * (k1.Q[i] + 2.0 * k2.Q[i] + 2.0 * k3.Q[i] + k4.Q[i]);
+    out.P[i] = y.P[i] + dt / 6.0 * (k1.P[i] + 2.0 * k2.P[i] + 2.0 * k3.P[i] + k4.P[i]);
+  }
+  for (int r = 0; r < 4 * d; ++r)
+    for (int i = 0; i < d; ++i) {
+      out.Qa[r][i] = y.Qa[r][i] + dt / 6.0 * (k1.Qa[r][i] + 2.0 * k2.Qa[r][i] + 2.0 * k3.Qa[r][i] + k4.Qa[r][i]);
+      out.Pa[r][i] = y.Pa[r][i] + dt / 6.0 * (k1.Pa[r][i] + 2.0 * k2.Pa[r][i] + 2.0 * k3.Pa[r][i] + k4.Pa[r][i]);
+    }
+  out.a = y.a + dt / 6.0 * (k1.a + 2.0 * k2.a + 2.0 * k3.a + k4.a);
+  out.S = y.S + dt / 6.0 * (k1.S + 2.0 * k2.S + 2.0 * k3.S + k4.S);
+  for (int k = 0; k < d; ++k) {
+    if (!g.periodic[k]) continue;
+    double L = g.n[k] * g.h[k];
+    double r = std::fmod(out.Q[k] - g.o[k], L);
+    if (r < 0) r += L;
+    out.Q[k] = g.o[k] + r;
+  }
+  y = out;
+}
+
 void set_threads(int nthreads) {
 #ifdef _OPENMP
   if (nthreads > 0) omp_set_num_threads(nthreads);
@@ -440,6 +552,71 @@ int orc_propagate(int dim, const int64_t* n, const double* h, const double* o, c
         Bout[((i * d + k) * d + l) * 2 + 1] = y.B[k][l].imag();
       }
     }
+    aout[2 * i + 0] = y.a.real();
+    aout[2 * i + 1] = y.a.imag();
+    Sout[i] = y.S;
+  }
+  return 0;
+}
+
+// orc_propagate with d_z Q, d_z P from divided differences (offsets dq[d], dp[d] > 0)
+// instead of the dynamic ray equations; same outputs, A = d_z Q and B = d_z P being the
+// central differences at the final time.
+int orc_propagate_dd(int dim, const int64_t* n, const double* h, const double* o,
+                     const int* periodic, const double* C, int64_t nsteps, double dt, int64_t nG,
+                     const int* sigma, const double* q, const double* p, const double* dq,
+                     const double* dp, double* Qout, double* Pout, double* Aout, double* Bout,
+                     double* aout, double* Sout, int nthreads) {
+  if (dim < 1 || dim > 3) return 1;
+  Grid g = make_grid(dim, n, h, o, periodic);
+  int d = dim;
+  for (int k = 0; k < d; ++k)
+    if (!(dq[k] > 0.0) || !(dp[k] > 0.0)) return 3;
+  for (int64_t i = 0; i < nG; ++i) {
+    double pn = 0.0;
+    for (int k = 0; k < d; ++k) pn += p[i * d + k] * p[i * d + k];
+    if (!(pn > 0.0)) return 2;
+  }
+  set_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 16)
+  for (int64_t i = 0; i < nG; ++i) {
+    DDState y;
+    std::memset(&y, 0, sizeof(DDState));
+    for (int k = 0; k < d; ++k) {
+      y.Q[k] = q[i * d + k];
+      y.P[k] = p[i * d + k];
+    }
+    for (int j = 0; j < d; ++j)
+      for (int m = 0; m < 4; ++m) {
+        int r = 4 * j + m;
+        for (int k = 0; k < d; ++k) {
+          y.Qa[r][k] = y.Q[k];
+          y.Pa[r][k] = y.P[k];
+        }
+        if (m == 0) y.Qa[r][j] += dq[j];
+        if (m == 1) y.Qa[r][j] -= dq[j];
+        if (m == 2) y.Pa[r][j] += dp[j];
+        if (m == 3) y.Pa[r][j] -= dp[j];
+      }
+    y.a = cplx(std::pow(2.0, 0.5 * d), 0.0);
+    y.S = 0.0;
+    for (int64_t s = 0; s < nsteps; ++s) dd_rk4_step(g, C, sigma[i], dq, dp, y, dt);
+    for (int k = 0; k < d; ++k) {
+      Qout[i * d + k] = y.Q[k];
+      Pout[i * d + k] = y.P[k];
+    }
+    // A = d_z Q = Dq Q - i Dp Q, B = d_z P = Dq P - i Dp P
+    for (int j = 0; j < d; ++j)
+      for (int k = 0; k < d; ++k) {
+        double DqQ = (y.Qa[4 * j][k] - y.Qa[4 * j + 1][k]) / (2.0 * dq[j]);
+        double DqP = (y.Pa[4 * j][k] - y.Pa[4 * j + 1][k]) / (2.0 * dq[j]);
+        double DpQ = (y.Qa[4 * j + 2][k] - y.Qa[4 * j + 3][k]) / (2.0 * dp[j]);
+        double DpP = (y.Pa[4 * j + 2][k] - y.Pa[4 * j + 3][k]) / (2.0 * dp[j]);
+        Aout[((i * d + j) * d + k) * 2 + 0] = DqQ;
+        Aout[((i * d + j) * d + k) * 2 + 1] = -DpQ;
+        Bout[((i * d + j) * d + k) * 2 + 0] = DqP;
+        Bout[((i * d + j) * d + k) * 2 + 1] = -DpP;
+      }
     aout[2 * i + 0] = y.a.real();
     aout[2 * i + 1] = y.a.imag();
     Sout[i] = y.S;

@@ -12,7 +12,9 @@ The three steps of the paper's algorithm (Algorithm section):
      (numpy.fft is the library step); the branch split of Eq. psi; selection
      of the sets G+- by thresholding |psi+-};
   2. propagate: RK4 on the ray, dynamic-ray, amplitude and action equations
-     (C++ part, fga_oracle.cpp);
+     (C++ part, fga_oracle.cpp); propagate_dd takes d_z Q, d_z P from divided
+     differences across auxiliary rays instead (the alternative named after
+     Eq. op_zZ);
   3. reconstruct: the sum of Eq. recons (C++ part), term by term.
 
 Discretisation (the paper leaves these open; each is a reading):
@@ -74,6 +76,8 @@ def _load():
         lib.orc_hamiltonian.argtypes = [ci, P, P, P, P, P, ci, P, P, P]
         lib.orc_propagate.argtypes = [ci, P, P, P, P, P, i64, d, i64, P, P, P, P, P, P, P, P, P,
                                       ci]
+        lib.orc_propagate_dd.argtypes = [ci, P, P, P, P, P, i64, d, i64, P, P, P, P, P, P, P,
+                                         P, P, P, P, ci]
         lib.orc_reconstruct.argtypes = [ci, P, d, d, d, i64, P, P, P, P, P, i64, P, P, P, ci]
         lib.orc_fbi_direct.argtypes = [ci, P, P, P, P, d, P, i64, P, P, P]
         lib.orc_traces.argtypes = [ci, P, P, P, P, P, i64, d, i64, i64, P, P, P, P, d, d, d, i64,
@@ -374,6 +378,29 @@ def propagate(grid: Grid, coef: np.ndarray, nsteps: int, dt: float, sigma: np.nd
                            _ptr(sigma), _ptr(q), _ptr(p), _ptr(Q), _ptr(P), _ptr(A), _ptr(B),
                            _ptr(a), _ptr(S), int(nthreads or default_threads()))
     assert rc == 0, "orc_propagate failed (%d)" % rc
+    return {"Q": Q, "P": P, "A": A[..., 0] + 1j * A[..., 1], "B": B[..., 0] + 1j * B[..., 1],
+            "a": a[:, 0] + 1j * a[:, 1], "S": S}
+
+
+def propagate_dd(grid: Grid, coef: np.ndarray, nsteps: int, dt: float, sigma: np.ndarray,
+                 q: np.ndarray, p: np.ndarray, dq, dp, nthreads: Optional[int] = None):
+    """propagate() with d_z Q, d_z P from central divided differences across auxiliary rays
+    offset by dq[k] in q and dp[k] in p (the alternative named after Eq. op_zZ)."""
+    lib = _load()
+    d = grid.dim
+    sigma = np.ascontiguousarray(sigma, dtype=np.int32)
+    q = _f64(q).reshape(-1, d)
+    p = _f64(p).reshape(-1, d)
+    dq = _f64(np.broadcast_to(np.asarray(dq, dtype=np.float64), (d,)))
+    dp = _f64(np.broadcast_to(np.asarray(dp, dtype=np.float64), (d,)))
+    nG = q.shape[0]
+    Q = np.empty((nG, d)); P = np.empty((nG, d))
+    A = np.empty((nG, d, d, 2)); B = np.empty((nG, d, d, 2))
+    a = np.empty((nG, 2)); S = np.empty(nG)
+    rc = lib.orc_propagate_dd(*grid.args(), _ptr(_f64(coef)), int(nsteps), float(dt), nG,
+                              _ptr(sigma), _ptr(q), _ptr(p), _ptr(dq), _ptr(dp), _ptr(Q), _ptr(P),
+                              _ptr(A), _ptr(B), _ptr(a), _ptr(S), int(nthreads or default_threads()))
+    assert rc == 0, "orc_propagate_dd failed (%d)" % rc
     return {"Q": Q, "P": P, "A": A[..., 0] + 1j * A[..., 1], "B": B[..., 0] + 1j * B[..., 1],
             "a": a[:, 0] + 1j * a[:, 1], "S": S}
 

@@ -9,7 +9,10 @@ Facts used (none of them is the oracle's own formula):
     a = c(Q)/c(q) sqrt(det Z) with a continuously chosen branch; the flow map is
     symplectic; A = d_z Q and B = d_z P agree with finite differences of whole
     rays in q and p (Eq. op_zZ); the action S stays zero (H is homogeneous of
-    degree one in P); RK4 converges at fourth order.
+    degree one in P); RK4 converges at fourth order;
+  * the divided-difference form of Z (auxiliary rays offset by delta in q and p)
+    is exact where the flow is affine and approaches the dynamic-ray Z at second
+    order in delta.
 """
 
 import cmath
@@ -160,3 +163,57 @@ def test_periodic_wrap_of_centres():
     st = O.propagate(g, coef, 200, 1e-3, np.array([1]), q, p, nthreads=1)
     exp = np.mod(q + 0.2 * p / np.linalg.norm(p), 1.0)
     np.testing.assert_allclose(st["Q"], exp, atol=1e-13)
+
+
+# ---------------------------------------------------------------------------
+# The divided-difference alternative for d_z Q, d_z P (the passage after Eq. op_zZ)
+# ---------------------------------------------------------------------------
+
+def test_divided_differences_homogeneous_closed_form():
+    # constant c: Q = q + c t p/|p| is linear in q, and in p up to the curvature of p/|p|,
+    # so the central differences are exact in q (and in 1D) and carry an O(delta^2) error
+    # in p: the amplitude error must fall by 4 when delta halves, against the closed form
+    for dim in (1, 2):
+        g = _open_grid(dim)
+        c0 = 1.7
+        coef = np.full((40,) * dim, c0)
+        rng = np.random.default_rng(3)
+        q = rng.uniform(4.0, 6.0, (6, dim))
+        p = rng.uniform(-1.5, 1.5, (6, dim))
+        T, dt = 0.6, 1e-3
+        sig = np.ones(6, np.int32)
+        pn = np.linalg.norm(p, axis=1)
+        aex = math.sqrt(2.0) * (2.0 - 1j * c0 * T / pn) ** ((dim - 1) / 2.0)
+        dyn = O.propagate(g, coef, 600, dt, sig, q, p, nthreads=2)
+        errs = []
+        for delta in (1e-2, 5e-3, 2.5e-3):
+            st = O.propagate_dd(g, coef, 600, dt, sig, q, p, delta, delta, nthreads=2)
+            assert np.array_equal(st["Q"], dyn["Q"]) and np.array_equal(st["P"], dyn["P"])
+            np.testing.assert_allclose(st["B"], np.broadcast_to(-1j * np.eye(dim), st["B"].shape),
+                                       atol=1e-13)
+            errs.append(np.max(np.abs(st["a"] - aex)))
+        if dim == 1:
+            assert max(errs) <= 1e-14
+        else:
+            assert errs[0] <= 1.1e-3
+            for e0, e1 in zip(errs, errs[1:]):
+                assert 3.9 <= e0 / e1 <= 4.1, errs
+
+
+def test_divided_differences_converge_to_dynamic_rays():
+    # variable medium: Z from differences of the discrete flow tends to the dynamic-ray Z
+    # (the Jacobian of the same RK4 flow) at second order in delta; the spline's third
+    # derivative jumps at knots, so the observed ratio per halving sits a little under 4
+    g, c = _lens_medium(64, 1.0 / 64)
+    q = np.array([[0.351, 0.203], [0.507, 0.253], [0.622, 0.301], [0.451, 0.803]])
+    p = np.array([[0.1, 1.0], [0.0, 0.7], [-0.2, 0.9], [0.3, -1.1]])
+    sig = np.ones(4, np.int32)
+    dyn = O.propagate(g, c, 400, 1e-3, sig, q, p, nthreads=2)
+    diffs = []
+    for delta in (2e-3, 1e-3, 5e-4):
+        st = O.propagate_dd(g, c, 400, 1e-3, sig, q, p, delta, delta, nthreads=2)
+        diffs.append(np.max(np.abs(st["a"] - dyn["a"])))
+        np.testing.assert_allclose(st["A"], dyn["A"], atol=100 * delta ** 2)
+    assert diffs[-1] <= 1e-4
+    for e0, e1 in zip(diffs, diffs[1:]):
+        assert 2.8 <= e0 / e1 <= 4.2, diffs
