@@ -94,7 +94,23 @@ typedef struct {
                          over the valid (q, p) instead (ties by q index, then p index);
                          the - branch holds the mirror set, so each branch has keep_n
                          Gaussians (the N-largest selection of the paper's experiment) */
+  int z_method;       /* how d_zQ and d_zP (Z of Eq. op_zZ) are obtained (fga_z_method):
+                         FGA_Z_DYNAMIC (0): the dynamic ray equations (Eqs. dzQ, dzP);
+                         FGA_Z_DIVIDED (1): central divided differences across 4d auxiliary
+                         rays started at (q +- dq_k e_k, p) and (q, p +- dp_k e_k), integrated
+                         with the ray by the same RK4 (the alternative named after Eq.
+                         op_zZ); dq_k = dz_eta s_k h_k and dp_k = dz_eta times the p-grid
+                         spacing of the shot. 1D and 2D; no receivers (so no fga_grad) */
+  double dz_eta;      /* FGA_Z_DIVIDED: offsets as a fraction of the q- and p-grid spacings,
+                         0 < dz_eta < 1 (at 1 the auxiliary rays would start at the
+                         neighbouring grid points, which for p one step from 0 include
+                         the left-out p = 0 where H = c|P| is singular). Ignored otherwise */
 } fga_config;
+
+typedef enum {
+  FGA_Z_DYNAMIC = 0,
+  FGA_Z_DIVIDED = 1
+} fga_z_method;
 
 /* Create a plan: validate cfg, copy the velocity (host or device, [n...] FP64,
  * every value finite and > 0) to the device as the cubic B-spline coefficients
@@ -119,7 +135,9 @@ fga_status fga_decompose(fga_plan_t plan, const double* u0, const double* u1,
                          int64_t* counts_host);
 
 /* Step 2. Integrates every kept Gaussian from (Q,P) = (q,p), d_zQ = I,
- * d_zP = -iI, a = 2^{d/2}, S = 0 to time T with T/dt classical RK4 steps.
+ * d_zP = -iI, a = 2^{d/2}, S = 0 to time T with T/dt classical RK4 steps (with
+ * FGA_Z_DIVIDED: (Q,P), its auxiliary rays, a and S; the stored d_zQ, d_zP are then
+ * the divided differences at the final time).
  * Errors: FGA_ERR_STATE (no decomposition yet), FGA_ERR_CUDA. A ray that meets
  * |P| = 0, det Z = 0 or a non-finite value is reported as FGA_ERR_NUMERIC by
  * the next call that synchronises (fga_reconstruct, fga_sync). */
@@ -136,7 +154,7 @@ fga_status fga_reconstruct(fga_plan_t plan, double* u_out);
 
 /* Receivers for traces: the field of Eq. recons (Re u, as fga_reconstruct writes it)
  * at the points xr (host or device, [nrx][dim] FP64, inside the grid, open axes only;
- * 1D and 2D)
+ * 1D and 2D; not with FGA_Z_DIVIDED)
  * at the record times t_m = m * record_every * dt, m = 0 .. T/(record_every dt)
  * (record_every must divide T/dt). fga_propagate then accumulates the traces while it
  * integrates the rays. nrx = 0 removes the receivers. Errors: FGA_ERR_INVALID,

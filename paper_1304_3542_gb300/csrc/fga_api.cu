@@ -194,6 +194,13 @@ fga_status fga_plan(const fga_config* cfg, const double* velocity, void* stream,
   if (!(cfg->tau >= 0.0) || !std::isfinite(cfg->tau))
     return fail(nullptr, FGA_ERR_INVALID, "tau must be >= 0");
   if (cfg->keep_n < 0) return fail(nullptr, FGA_ERR_INVALID, "keep_n must be >= 0");
+  if (cfg->z_method != FGA_Z_DYNAMIC && cfg->z_method != FGA_Z_DIVIDED)
+    return fail(nullptr, FGA_ERR_INVALID, "z_method must be FGA_Z_DYNAMIC or FGA_Z_DIVIDED");
+  if (cfg->z_method == FGA_Z_DIVIDED) {
+    if (d > 2) return fail(nullptr, FGA_ERR_INVALID, "FGA_Z_DIVIDED is supported in 1D and 2D");
+    if (!(cfg->dz_eta > 0.0 && cfg->dz_eta < 1.0))
+      return fail(nullptr, FGA_ERR_INVALID, "FGA_Z_DIVIDED needs 0 < dz_eta < 1");
+  }
   GridDev gd;
   std::memset(&gd, 0, sizeof(gd));
   gd.dim = d;
@@ -226,6 +233,8 @@ fga_status fga_plan(const fga_config* cfg, const double* velocity, void* stream,
   p->precision = cfg->precision;
   p->integrate_exited = cfg->integrate_exited ? 1 : 0;
   p->keep_n = cfg->keep_n;
+  p->z_method = cfg->z_method;
+  p->dz_eta = cfg->z_method == FGA_Z_DIVIDED ? cfg->dz_eta : 0.0;
   p->stream = (cudaStream_t)stream;
   p->nfields = fga::state_fields(d);
   const int TS = cfg->precision == FGA_MIXED_TF32X3 ? fga::tile_edge_tc() : fga::tile_edge(d);
@@ -927,6 +936,8 @@ fga_status fga_set_receivers(fga_plan_t p, int64_t nrx, const double* xr, int64_
   if (record_every < 1 || p->nsteps % record_every != 0)
     return fail(p, FGA_ERR_INVALID, "record_every must be >= 1 and divide T/dt");
   if (d == 3) return fail(p, FGA_ERR_INVALID, "receivers (traces, fga_grad) are supported in 1D and 2D");
+  if (p->z_method != FGA_Z_DYNAMIC)
+    return fail(p, FGA_ERR_INVALID, "receivers (traces, fga_grad) need z_method FGA_Z_DYNAMIC");
   for (int k = 0; k < d; ++k)
     if (gd.periodic[k]) return fail(p, FGA_ERR_INVALID, "receivers need open axes");
   std::vector<double> x((size_t)nrx * d);

@@ -25,6 +25,8 @@ FGA_ERR_STATE = 5
 FGA_FP64 = 0
 FGA_MIXED_TF32X3 = 1
 FGA_MIXED_BF16X3 = 2
+FGA_Z_DYNAMIC = 0
+FGA_Z_DIVIDED = 1
 
 STATUS = {0: "FGA_OK", 1: "FGA_ERR_INVALID", 2: "FGA_ERR_OOM", 3: "FGA_ERR_CUDA",
           4: "FGA_ERR_TIMEOUT", 5: "FGA_ERR_STATE", 6: "FGA_ERR_NUMERIC", 7: "FGA_ERR_CAPACITY"}
@@ -54,6 +56,8 @@ class Config(ctypes.Structure):
         ("precision", ctypes.c_int),
         ("integrate_exited", ctypes.c_int),
         ("keep_n", ctypes.c_int64),
+        ("z_method", ctypes.c_int),
+        ("dz_eta", ctypes.c_double),
     ]
 
 
@@ -158,7 +162,7 @@ class Plan:
                  periodic: Sequence[bool], velocity, eps: Sequence[float], T: float, dt: float,
                  kappa: float, tau: float, q_stride=None, box=None, precision: int = FGA_FP64,
                  stream: Optional[int] = None, integrate_exited: bool = False,
-                 keep_n: int = 0):
+                 keep_n: int = 0, z_method: int = 0, dz_eta: float = 0.0):
         self._L = load()
         self.dim = dim
         self.n = tuple(int(v) for v in n)
@@ -185,6 +189,8 @@ class Plan:
         cfg.precision = int(precision)
         cfg.integrate_exited = int(bool(integrate_exited))
         cfg.keep_n = int(keep_n)
+        cfg.z_method = int(z_method)
+        cfg.dz_eta = float(dz_eta)
         _check_f64(velocity, self.npts, "velocity")
         self._keep = [velocity]
         out = ctypes.c_void_p()
@@ -358,8 +364,9 @@ def reconstruct_static(dim: int, n: Sequence[int], h: Sequence[float], origin: S
 
 
 def plan_from_problem(prob, velocity=None, stream=None, precision: int = FGA_FP64,
-                      integrate_exited: bool = False) -> Plan:
-    """A Plan for a workloads.Problem (its grid, shots, T, dt, kappa, tau)."""
+                      integrate_exited: bool = False, z_method: int = 0,
+                      dz_eta: float = 0.0) -> Plan:
+    """A Plan for a workloads.Problem (its grid, shots, T, dt, kappa, tau, keep_n)."""
     vel = prob.velocity if velocity is None else velocity
     if isinstance(vel, np.ndarray):
         vel = np.ascontiguousarray(vel, dtype=np.float64)
@@ -367,7 +374,7 @@ def plan_from_problem(prob, velocity=None, stream=None, precision: int = FGA_FP6
                 [s.eps for s in prob.shots], prob.T, prob.dt, prob.kappa, prob.tau,
                 q_stride=[s.q_stride for s in prob.shots], box=[s.box for s in prob.shots],
                 precision=precision, stream=stream, integrate_exited=integrate_exited,
-                keep_n=getattr(prob, "keep_n", 0))
+                keep_n=getattr(prob, "keep_n", 0), z_method=z_method, dz_eta=dz_eta)
 
 
 def stacked_initial_data(prob):

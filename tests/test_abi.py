@@ -59,6 +59,12 @@ def _plan(**kw):
     (dict(eps=[float("nan")]), "eps"),
     (dict(kappa=0.0), "kappa"),
     (dict(keep_n=-1), "keep_n"),
+    (dict(z_method=2), "z_method"),
+    (dict(z_method=F.FGA_Z_DIVIDED), "dz_eta"),
+    (dict(z_method=F.FGA_Z_DIVIDED, dz_eta=1.0), "dz_eta"),
+    (dict(z_method=F.FGA_Z_DIVIDED, dz_eta=float("nan")), "dz_eta"),
+    (dict(dim=3, n=(8, 8, 8), h=(1, 1, 1), origin=(0, 0, 0), periodic=(0, 0, 0),
+          velocity=np.ones(512), z_method=F.FGA_Z_DIVIDED, dz_eta=0.5), "1D and 2D"),
     (dict(tau=-1.0), "tau"),
     (dict(h=(0.0, 0.1)), "spacing"),
     (dict(n=(2, 16), velocity=np.ones(32)), "grid size"),

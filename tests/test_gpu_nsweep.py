@@ -6,9 +6,12 @@ of the wave equation in the same medium (`fd_reference.py`, 8th order in space o
 grid refined twice, 4th order in time).
 
 Checks: the error falls at every step of N, and the threshold set reaches the method's
-own accuracy at this eps. Run with -s to see the table.
+own accuracy at this eps. On the same case, the divided-difference form of Z
+(FGA_Z_DIVIDED) is set against the dynamic rays for accuracy and cost. Run with -s to see
+the tables.
 """
 
+import functools
 import os
 
 import numpy as np
@@ -43,6 +46,11 @@ def _problem():
     return WL.layered_single(T=T, dt=DT, src=SRC, f=FREQ)
 
 
+@functools.lru_cache(maxsize=1)
+def _fd_reference():
+    return _fd_field(_problem())
+
+
 def _fd_field(prob):
     cs = float(prob.velocity[int(round(SRC[0] / prob.h[0])), int(round(SRC[1] / prob.h[1]))])
     t0 = 1.0 / FREQ
@@ -62,22 +70,28 @@ def _fd_field(prob):
     return u
 
 
-def _fga_field(prob, keep_n):
+def _fga_field(prob, keep_n, z_method=F.FGA_Z_DYNAMIC, dz_eta=0.0, timed=False):
     import torch
 
     plan = F.plan_from_problem(prob.with_(keep_n=keep_n),
-                               stream=torch.cuda.current_stream().cuda_stream)
+                               stream=torch.cuda.current_stream().cuda_stream,
+                               z_method=z_method, dz_eta=dz_eta)
     u0, u1 = F.stacked_initial_data(prob)
     counts = plan.decompose(torch.from_numpy(u0).cuda(), torch.from_numpy(u1).cuda())
     plan.propagate()
+    if timed:  # time a second integration (the first one sets up the launch shape)
+        plan.propagate()
     u = plan.reconstruct()[0]
+    ms = plan.stage_times()[0]["rays"]
     plan.close()
+    if timed:
+        return u, int(np.asarray(counts).ravel()[0]), ms
     return u, int(np.asarray(counts).ravel()[0])
 
 
 def test_error_falls_with_the_number_of_gaussians():
     prob = _problem()
-    ufd = _fd_field(prob)
+    ufd = _fd_reference()
     nrm = np.linalg.norm(ufd)
     rows = []
     for n in NS:
@@ -94,3 +108,23 @@ def test_error_falls_with_the_number_of_gaussians():
     assert all(b < a for a, b in zip(errs, errs[1:])), errs
     assert err_tau <= errs[-1] * 1.05
     assert err_tau <= 0.07, err_tau  # measured 0.0558: the method's O(eps) error at eps = 0.024 km
+
+
+def test_divided_difference_form_accuracy_and_cost():
+    """The threshold set with Z from the dynamic rays and from divided differences across
+    auxiliary rays offset by half and by a tenth of the phase-space grid spacings: error
+    against the FD solve and ray-kernel time."""
+    prob = _problem()
+    ufd = _fd_reference()
+    nrm = np.linalg.norm(ufd)
+    rows = []
+    for label, z, eta in (("dynamic rays (Eqs. dzQ, dzP)", F.FGA_Z_DYNAMIC, 0.0),
+                          ("divided differences, dz_eta = 0.5", F.FGA_Z_DIVIDED, 0.5),
+                          ("divided differences, dz_eta = 0.1", F.FGA_Z_DIVIDED, 0.1)):
+        u, cnt, ms = _fga_field(prob, 0, z, eta, timed=True)
+        rows.append((label, np.linalg.norm(u - ufd) / nrm, ms))
+    print("\nZ from | rel-L2 error vs FD | ray kernel ms (%d Gaussians, %d steps)"
+          % (cnt, prob.nsteps))
+    for label, e, ms in rows:
+        print("%s | %.4f | %.1f" % (label, e, ms))
+    assert abs(rows[2][1] - rows[0][1]) <= 0.02 * rows[0][1], rows
