@@ -540,7 +540,7 @@ fga_status fga_propagate(fga_plan_t p) {
   st = trace_capacity(p);
   if (st != FGA_OK) return st;
   CUDA_OR_FAIL(p, cudaEventRecord(p->ev[3], p->stream));
-  CUDA_OR_FAIL(p, fga::launch_rays(p));
+  CUDA_OR_FAIL(p, p->z_method == FGA_Z_DIVIDED ? fga::launch_rays_dd(p, p->nsteps) : fga::launch_rays(p));
   CUDA_OR_FAIL(p, cudaEventRecord(p->ev[4], p->stream));
   p->stage = 2;
   return FGA_OK;
@@ -610,7 +610,7 @@ fga_status fga_run_graph(fga_plan_t p, double* u_dev) {
     }
     cudaGraph_t graph = nullptr;
     CUDA_OR_FAIL(p, cudaStreamBeginCapture(p->stream, cudaStreamCaptureModeThreadLocal));
-    cudaError_t e = fga::launch_rays(p);
+    cudaError_t e = p->z_method == FGA_Z_DIVIDED ? fga::launch_rays_dd(p, p->nsteps) : fga::launch_rays(p);
     if (e == cudaSuccess) e = fga::launch_binning(p);
     if (e == cudaSuccess) e = fga::launch_binning_fill(p);
     if (e == cudaSuccess)
@@ -665,7 +665,7 @@ fga_status fga_autotune(fga_plan_t p, double* u_dev, int64_t* choice) {
   const int64_t probe = std::min<int64_t>(p->nsteps, 64);
   int best_variant = 0, best_sm = 0;
   float best = 3.0e38f;
-  if (p->G > 0 && probe > 0) {
+  if (p->G > 0 && probe > 0 && p->z_method == FGA_Z_DYNAMIC) {  // the divided-difference kernel has no variants
     for (int variant = 0; variant < 2; ++variant) {
       p->ray_variant = variant;
       const int max_sm = fga::ray_max_per_sm(p);
