@@ -7,10 +7,11 @@
 // so the sum over the Gaussians that touch an output tile is a complex
 // contraction U = X^T diag(coef) Z over the Gaussian index (a GEMM of rank one
 // terms). Binning (K4) builds, per (shot, tile), the ordered list of Gaussians
-// whose window meets the tile; the gather (K5) runs one CTA per tile, generates
-// the per-axis factors of a chunk of Gaussians into shared memory and
-// accumulates the tile in registers, FP64 throughout. The scatter-free form
-// needs no atomics on the output and gives a deterministic summation order.
+// whose window meets the tile; the gather (K5) runs one CTA per (tile, segment of
+// its list), generates the per-axis factors of a chunk of Gaussians into shared
+// memory and accumulates a partial tile in registers, FP64 throughout; the
+// partial tiles are then summed in a fixed order. The scatter-free form needs no
+// atomics on the output and gives a deterministic summation order.
 #include <cmath>
 #include <cstring>
 #include <mutex>
