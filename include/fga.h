@@ -105,6 +105,13 @@ typedef struct {
                          0 < dz_eta < 1 (at 1 the auxiliary rays would start at the
                          neighbouring grid points, which for p one step from 0 include
                          the left-out p = 0 where H = c|P| is singular). Ignored otherwise */
+  int interp;         /* fga_interp: FGA_BSPLINE_APPROX (0): the velocity samples are the
+                         spline coefficients (c(x) smooths them; the default).
+                         FGA_BSPLINE_INTERP (1): the coefficients are the samples passed
+                         through fga_spline_prefilter, so that c(x_i) = c_i at every grid
+                         point (between the points the interpolant can undershoot where the
+                         samples jump; the samples must be > 0, the rays need c > 0 where
+                         they go); fga_grad then returns dJ/dc with respect to the samples */
 } fga_config;
 
 typedef enum {
@@ -112,10 +119,16 @@ typedef enum {
   FGA_Z_DIVIDED = 1
 } fga_z_method;
 
+typedef enum {
+  FGA_BSPLINE_APPROX = 0,
+  FGA_BSPLINE_INTERP = 1
+} fga_interp;
+
 /* Create a plan: validate cfg, copy the velocity (host or device, [n...] FP64,
  * every value finite and > 0) to the device as the cubic B-spline coefficients
  * of the medium c(x) = sum_i c_i prod_k beta3((x_k - origin_k)/h_k - i_k) (indices
- * clamped on open axes, wrapped on periodic ones), and bind the CUDA stream
+ * clamped on open axes, wrapped on periodic ones; with FGA_BSPLINE_INTERP the
+ * coefficients are fga_spline_prefilter of the samples), and bind the CUDA stream
  * (a cudaStream_t; NULL = the legacy default stream).
  * Errors: FGA_ERR_INVALID (cfg, velocity <= 0 or NaN), FGA_ERR_OOM, FGA_ERR_CUDA. */
 fga_status fga_plan(const fga_config* cfg, const double* velocity, void* stream,
@@ -301,6 +314,20 @@ fga_status fga_stage_times(fga_plan_t plan, double* ms5, int64_t* launches);
 fga_status fga_reconstruct_static(int dim, const int64_t* n, const double* h, const double* origin,
                                   const int* periodic, double eps, double kappa, int64_t nG,
                                   const double* qp, const double* coef, double* u, void* stream);
+
+/* The interpolating prefilter of the medium (host only; no CUDA call). Given samples
+ * c_i on the grid (host, [n...] FP64, C order), writes the coefficients C (host, may be
+ * the same array) of the clamped / wrapped cubic B-spline of fga_plan that interpolates
+ * them: along every axis, one tridiagonal system per grid line,
+ *   (C_{i-1} + 4 C_i + C_{i+1})/6 = c_i,
+ * whose end rows on an open axis are those of the clamped spline itself,
+ * (5 C_0 + C_1)/6 = c_0 and (C_{n-2} + 5 C_{n-1})/6 = c_{n-1}, and which wraps on a
+ * periodic axis (solved by the Thomas algorithm, with the Sherman-Morrison correction
+ * on periodic axes). Every such system is symmetric, so the map is its own adjoint
+ * (fga_grad uses it to turn dJ/dC into dJ/dc).
+ * dim 1..3, n[k] >= 4. Errors: FGA_ERR_INVALID (message via fga_last_error(NULL)). */
+fga_status fga_spline_prefilter(int dim, const int64_t* n, const int* periodic,
+                                const double* samples, double* coef);
 
 #ifdef __cplusplus
 }

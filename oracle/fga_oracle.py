@@ -141,6 +141,27 @@ def medium_eval(grid: Grid, coef: np.ndarray, x: np.ndarray, order: int = 2):
     return c, g, hs, d3
 
 
+def interp_coefficients(grid: Grid, samples: np.ndarray) -> np.ndarray:
+    """Coefficients C of the medium's spline (clamped indices on open axes, wrapped on
+    periodic ones) that interpolate the samples: c(x_i) = c_i at every grid point. The
+    tensor-product spline samples separably, so along each axis the grid values are
+    B_k C with B_k[i][j] = sum of beta3(i - t) over the taps t = i-1, i, i+1 whose
+    clamped (or wrapped) index is j; each B_k is solved densely (numpy.linalg.solve)."""
+    c = _f64(samples).reshape(tuple(int(v) for v in grid.n))
+    w = {-1: 1.0 / 6.0, 0: 2.0 / 3.0, 1: 1.0 / 6.0}  # beta3 at the integer offsets
+    for k in range(grid.dim):
+        n = int(grid.n[k])
+        B = np.zeros((n, n))
+        for i in range(n):
+            for off, wt in w.items():
+                t = i + off
+                j = t % n if grid.periodic[k] else min(max(t, 0), n - 1)
+                B[i, j] += wt
+        c = np.moveaxis(np.linalg.solve(B, np.moveaxis(c, k, 0).reshape(n, -1)).reshape(
+            np.moveaxis(c, k, 0).shape), 0, k)
+    return np.ascontiguousarray(c)
+
+
 def hamiltonian(grid: Grid, coef: np.ndarray, sigma: int, Q, P) -> Dict[str, np.ndarray]:
     lib = _load()
     d = grid.dim

@@ -115,6 +115,68 @@ fga_status read_status(fga_plan_s* p) {
   return FGA_OK;
 }
 
+// One grid line of the interpolating prefilter, v[i * stride], i < n, in place: the
+// tridiagonal system (C_{i-1} + 4 C_i + C_{i+1})/6 = c_i with the clamped spline's end
+// rows (5 C_0 + C_1)/6, (C_{n-2} + 5 C_{n-1})/6 on an open axis (Thomas algorithm), or
+// wrapped indices on a periodic axis (Thomas on the matrix with its corners removed and
+// the Sherman-Morrison correction for them). w, x, z: scratch of n values.
+void prefilter_line(double* v, int64_t n, int64_t stride, bool periodic, std::vector<double>& w,
+                    std::vector<double>& x, std::vector<double>& z) {
+  // rows scaled by 6: sub- and super-diagonal 1, diagonal 4 (5 at the ends of an open axis)
+  if (!periodic) {
+    double m = 5.0;
+    w[0] = 1.0 / m;
+    x[0] = 6.0 * v[0] / m;
+    for (int64_t i = 1; i < n; ++i) {
+      m = (i == n - 1 ? 5.0 : 4.0) - w[i - 1];
+      w[i] = 1.0 / m;
+      x[i] = (6.0 * v[i * stride] - x[i - 1]) / m;
+    }
+    for (int64_t i = n - 2; i >= 0; --i) x[i] -= w[i] * x[i + 1];
+    for (int64_t i = 0; i < n; ++i) v[i * stride] = x[i];
+    return;
+  }
+  // Sherman-Morrison: A = T + u v^T, u = (gamma, 0, ..., 0, 1), v = (1, 0, ..., 0, 1/gamma),
+  // gamma = -4, so that T (tridiagonal, diagonal entries 4 - gamma first and 4 - 1/gamma
+  // last) holds no corners; solve T x = rhs and T z = u, then
+  // x -= z (x_0 + x_{n-1}/gamma)/(1 + z_0 + z_{n-1}/gamma)
+  const double gamma = -4.0;
+  auto solve_t = [&](const double* rhs, int64_t rstride, std::vector<double>& out) {
+    double m = 4.0 - gamma;
+    w[0] = 1.0 / m;
+    out[0] = rhs[0] / m;
+    for (int64_t i = 1; i < n; ++i) {
+      m = (i == n - 1 ? 4.0 - 1.0 / gamma : 4.0) - w[i - 1];
+      w[i] = 1.0 / m;
+      out[i] = (rhs[i * rstride] - out[i - 1]) / m;
+    }
+    for (int64_t i = n - 2; i >= 0; --i) out[i] -= w[i] * out[i + 1];
+  };
+  std::vector<double> rhs((size_t)n), u((size_t)n, 0.0);
+  for (int64_t i = 0; i < n; ++i) rhs[i] = 6.0 * v[i * stride];
+  u[0] = gamma;
+  u[n - 1] = 1.0;
+  solve_t(rhs.data(), 1, x);
+  solve_t(u.data(), 1, z);
+  const double f = (x[0] + x[n - 1] / gamma) / (1.0 + z[0] + z[n - 1] / gamma);
+  for (int64_t i = 0; i < n; ++i) v[i * stride] = x[i] - f * z[i];
+}
+
+// The prefilter on a whole C-order grid, axis by axis.
+void prefilter_grid(int d, const int64_t* n, const int* periodic, double* c) {
+  int64_t total = 1;
+  for (int k = 0; k < d; ++k) total *= n[k];
+  for (int k = 0; k < d; ++k) {
+    int64_t stride = 1;
+    for (int j = k + 1; j < d; ++j) stride *= n[j];
+    std::vector<double> w((size_t)n[k]), x((size_t)n[k]), z((size_t)n[k]);
+    const int64_t outer = total / (n[k] * stride);
+    for (int64_t o = 0; o < outer; ++o)
+      for (int64_t in = 0; in < stride; ++in)
+        prefilter_line(c + o * n[k] * stride + in, n[k], stride, periodic[k] != 0, w, x, z);
+  }
+}
+
 }  // namespace
 
 namespace fga {
@@ -194,6 +256,8 @@ fga_status fga_plan(const fga_config* cfg, const double* velocity, void* stream,
   if (!(cfg->tau >= 0.0) || !std::isfinite(cfg->tau))
     return fail(nullptr, FGA_ERR_INVALID, "tau must be >= 0");
   if (cfg->keep_n < 0) return fail(nullptr, FGA_ERR_INVALID, "keep_n must be >= 0");
+  if (cfg->interp != FGA_BSPLINE_APPROX && cfg->interp != FGA_BSPLINE_INTERP)
+    return fail(nullptr, FGA_ERR_INVALID, "interp must be FGA_BSPLINE_APPROX or FGA_BSPLINE_INTERP");
   if (cfg->z_method != FGA_Z_DYNAMIC && cfg->z_method != FGA_Z_DIVIDED)
     return fail(nullptr, FGA_ERR_INVALID, "z_method must be FGA_Z_DYNAMIC or FGA_Z_DIVIDED");
   if (cfg->z_method == FGA_Z_DIVIDED) {
@@ -234,6 +298,7 @@ fga_status fga_plan(const fga_config* cfg, const double* velocity, void* stream,
   p->integrate_exited = cfg->integrate_exited ? 1 : 0;
   p->keep_n = cfg->keep_n;
   p->z_method = cfg->z_method;
+  p->interp = cfg->interp;
   p->dz_eta = cfg->z_method == FGA_Z_DIVIDED ? cfg->dz_eta : 0.0;
   p->stream = (cudaStream_t)stream;
   p->nfields = fga::state_fields(d);
@@ -323,6 +388,17 @@ fga_status fga_plan(const fga_config* cfg, const double* velocity, void* stream,
   if (bad) {
     fga_destroy(p);
     return fail(nullptr, FGA_ERR_INVALID, "velocity must be finite and > 0 everywhere");
+  }
+  if (p->interp == FGA_BSPLINE_INTERP) {
+    // the samples were checked; the coefficients are their interpolating prefilter
+    std::vector<double> hc((size_t)gd.npts);
+    PLAN_CUDA(cudaMemcpyAsync(hc.data(), p->d_coef, sizeof(double) * gd.npts,
+                              cudaMemcpyDeviceToHost, p->stream));
+    PLAN_CUDA(cudaStreamSynchronize(p->stream));
+    prefilter_grid(d, gd.n, gd.periodic, hc.data());
+    PLAN_CUDA(cudaMemcpyAsync(p->d_coef, hc.data(), sizeof(double) * gd.npts,
+                              cudaMemcpyHostToDevice, p->stream));
+    PLAN_CUDA(cudaStreamSynchronize(p->stream));
   }
   if (d == 3) {
     p->grid.tab = p->d_coef;  // 3D: the ray kernels read the samples (64-tap form)
@@ -1115,6 +1191,22 @@ fga_status fga_grad(fga_plan_t p, const double* residual, double* grad) {
                        (size_t)(fga::adjoint_slices(p, nthr) * gd.npts)));
   CUDA_OR_FAIL(p, grow(&p->d_adj_bucket, &p->adj_bucket_cap, (size_t)(p->nsteps / kseg + 2)));
   CUDA_OR_FAIL(p, fga::launch_adjoint(p, d_res, dst, p->d_adj_scratch, nthr, kseg, ncheck));
+  if (p->interp == FGA_BSPLINE_INTERP) {
+    // dJ/dc = B^{-T} dJ/dC for C = B^{-1} c; B is symmetric, so this is the prefilter again
+    std::vector<double> hg((size_t)gd.npts);
+    CUDA_OR_FAIL(p, cudaMemcpyAsync(hg.data(), dst, sizeof(double) * gd.npts, cudaMemcpyDeviceToHost,
+                                    p->stream));
+    CUDA_OR_FAIL(p, cudaStreamSynchronize(p->stream));
+    prefilter_grid(gd.dim, gd.n, gd.periodic, hg.data());
+    if (host_out) {
+      std::memcpy(grad, hg.data(), sizeof(double) * gd.npts);
+    } else {
+      CUDA_OR_FAIL(p, cudaMemcpyAsync(grad, hg.data(), sizeof(double) * gd.npts,
+                                      cudaMemcpyHostToDevice, p->stream));
+      CUDA_OR_FAIL(p, cudaStreamSynchronize(p->stream));
+    }
+    return read_status(p);
+  }
   if (host_out)
     CUDA_OR_FAIL(p, cudaMemcpyAsync(grad, dst, sizeof(double) * gd.npts, cudaMemcpyDeviceToHost,
                                     p->stream));
@@ -1147,6 +1239,21 @@ fga_status fga_stage_times(fga_plan_t p, double* ms5, int64_t* launches) {
     }
   }
   if (launches) *launches = p->launches;
+  return FGA_OK;
+}
+
+fga_status fga_spline_prefilter(int dim, const int64_t* n, const int* periodic,
+                                const double* samples, double* coef) {
+  if (dim < 1 || dim > fga::kMaxDim || !n || !periodic || !samples || !coef)
+    return fail(nullptr, FGA_ERR_INVALID, "fga_spline_prefilter: bad arguments");
+  int64_t total = 1;
+  for (int k = 0; k < dim; ++k) {
+    if (n[k] < 4 || n[k] > ((int64_t)1 << 30))
+      return fail(nullptr, FGA_ERR_INVALID, "fga_spline_prefilter: grid size out of range");
+    total *= n[k];
+  }
+  if (coef != samples) std::memmove(coef, samples, sizeof(double) * total);
+  prefilter_grid(dim, n, periodic, coef);
   return FGA_OK;
 }
 

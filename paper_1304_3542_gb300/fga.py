@@ -27,6 +27,8 @@ FGA_MIXED_TF32X3 = 1
 FGA_MIXED_BF16X3 = 2
 FGA_Z_DYNAMIC = 0
 FGA_Z_DIVIDED = 1
+FGA_BSPLINE_APPROX = 0
+FGA_BSPLINE_INTERP = 1
 
 STATUS = {0: "FGA_OK", 1: "FGA_ERR_INVALID", 2: "FGA_ERR_OOM", 3: "FGA_ERR_CUDA",
           4: "FGA_ERR_TIMEOUT", 5: "FGA_ERR_STATE", 6: "FGA_ERR_NUMERIC", 7: "FGA_ERR_CAPACITY"}
@@ -58,6 +60,7 @@ class Config(ctypes.Structure):
         ("keep_n", ctypes.c_int64),
         ("z_method", ctypes.c_int),
         ("dz_eta", ctypes.c_double),
+        ("interp", ctypes.c_int),
     ]
 
 
@@ -117,6 +120,8 @@ def load(build_if_missing: bool = True):
     L.fga_reconstruct_static.argtypes = [ci, P, P, P, P, ctypes.c_double, ctypes.c_double, i64,
                                          P, P, P, P]
     L.fga_reconstruct_static.restype = ci
+    L.fga_spline_prefilter.argtypes = [ci, P, P, P, P]
+    L.fga_spline_prefilter.restype = ci
     for name in ("fga_plan", "fga_decompose", "fga_propagate", "fga_reconstruct", "fga_sync",
                  "fga_destroy", "fga_shot_grid", "fga_psi", "fga_gaussians", "fga_state",
                  "fga_stage_times"):
@@ -162,7 +167,8 @@ class Plan:
                  periodic: Sequence[bool], velocity, eps: Sequence[float], T: float, dt: float,
                  kappa: float, tau: float, q_stride=None, box=None, precision: int = FGA_FP64,
                  stream: Optional[int] = None, integrate_exited: bool = False,
-                 keep_n: int = 0, z_method: int = 0, dz_eta: float = 0.0):
+                 keep_n: int = 0, z_method: int = 0, dz_eta: float = 0.0,
+                 interp: int = FGA_BSPLINE_APPROX):
         self._L = load()
         self.dim = dim
         self.n = tuple(int(v) for v in n)
@@ -191,6 +197,7 @@ class Plan:
         cfg.keep_n = int(keep_n)
         cfg.z_method = int(z_method)
         cfg.dz_eta = float(dz_eta)
+        cfg.interp = int(interp)
         _check_f64(velocity, self.npts, "velocity")
         self._keep = [velocity]
         out = ctypes.c_void_p()
@@ -363,9 +370,24 @@ def reconstruct_static(dim: int, n: Sequence[int], h: Sequence[float], origin: S
     return u
 
 
+def spline_prefilter(samples: np.ndarray, periodic: Sequence[bool]) -> np.ndarray:
+    """fga_spline_prefilter on the host: the coefficients of the clamped / wrapped cubic
+    B-spline that interpolates the samples (C-order float64 grid, 1 to 3 axes)."""
+    L = load()
+    a = np.ascontiguousarray(samples, dtype=np.float64)
+    out = np.empty_like(a)
+    n = np.ascontiguousarray(a.shape, dtype=np.int64)
+    per = np.ascontiguousarray([int(bool(v)) for v in periodic], dtype=np.int32)
+    st = L.fga_spline_prefilter(a.ndim, n.ctypes.data, per.ctypes.data, a.ctypes.data,
+                                out.ctypes.data)
+    if st != FGA_OK:
+        raise FGAError(st, "fga_spline_prefilter", L.fga_last_error(None).decode())
+    return out
+
+
 def plan_from_problem(prob, velocity=None, stream=None, precision: int = FGA_FP64,
                       integrate_exited: bool = False, z_method: int = 0,
-                      dz_eta: float = 0.0) -> Plan:
+                      dz_eta: float = 0.0, interp: int = FGA_BSPLINE_APPROX) -> Plan:
     """A Plan for a workloads.Problem (its grid, shots, T, dt, kappa, tau, keep_n)."""
     vel = prob.velocity if velocity is None else velocity
     if isinstance(vel, np.ndarray):
@@ -374,7 +396,8 @@ def plan_from_problem(prob, velocity=None, stream=None, precision: int = FGA_FP6
                 [s.eps for s in prob.shots], prob.T, prob.dt, prob.kappa, prob.tau,
                 q_stride=[s.q_stride for s in prob.shots], box=[s.box for s in prob.shots],
                 precision=precision, stream=stream, integrate_exited=integrate_exited,
-                keep_n=getattr(prob, "keep_n", 0), z_method=z_method, dz_eta=dz_eta)
+                keep_n=getattr(prob, "keep_n", 0), z_method=z_method, dz_eta=dz_eta,
+                interp=interp)
 
 
 def stacked_initial_data(prob):

@@ -60,6 +60,7 @@ def _plan(**kw):
     (dict(kappa=0.0), "kappa"),
     (dict(keep_n=-1), "keep_n"),
     (dict(z_method=2), "z_method"),
+    (dict(interp=2), "interp"),
     (dict(z_method=F.FGA_Z_DIVIDED), "dz_eta"),
     (dict(z_method=F.FGA_Z_DIVIDED, dz_eta=1.0), "dz_eta"),
     (dict(z_method=F.FGA_Z_DIVIDED, dz_eta=float("nan")), "dz_eta"),
@@ -116,3 +117,36 @@ def test_grid_receivers_cover_the_grid_inside_its_bounds():
         assert hi - 4 * np.spacing(hi) <= xr[:, k].max() < hi
     # C order: the last axis runs fastest
     assert xr[1, 1] - xr[0, 1] == prob.h[1] and xr[1, 0] == xr[0, 0]
+
+
+@pytest.mark.parametrize("shape, periodic", [((9,), (False,)), ((8,), (True,)),
+                                             ((13, 11), (False, False)), ((12, 7), (True, False)),
+                                             ((6, 5, 7), (False, True, False))])
+def test_spline_prefilter_matches_the_oracle_and_is_symmetric(shape, periodic):
+    import oracle as O
+
+    rng = np.random.default_rng(31)
+    c = 1.0 + rng.uniform(0.0, 1.0, shape)
+    g = O.Grid(shape, (1.0,) * len(shape), (0.0,) * len(shape), periodic)
+    got = F.spline_prefilter(c, periodic)
+    np.testing.assert_allclose(got, O.interp_coefficients(g, c), rtol=0, atol=1e-12)
+    # the map is symmetric (fga_grad applies it as its own adjoint)
+    x, y = rng.standard_normal(shape), rng.standard_normal(shape)
+    lhs = float(np.sum(F.spline_prefilter(x, periodic) * y))
+    rhs = float(np.sum(x * F.spline_prefilter(y, periodic)))
+    assert abs(lhs - rhs) <= 1e-12 * max(abs(lhs), 1.0)
+
+
+def test_spline_prefilter_in_place_and_errors():
+    L = F.load()
+    c = np.random.default_rng(32).uniform(1.0, 2.0, (10, 9))
+    ref = F.spline_prefilter(c, (False, False))
+    n = np.ascontiguousarray(c.shape, dtype=np.int64)
+    per = np.zeros(2, dtype=np.int32)
+    a = c.copy()
+    assert L.fga_spline_prefilter(2, n.ctypes.data, per.ctypes.data, a.ctypes.data, a.ctypes.data) == 0
+    np.testing.assert_array_equal(a, ref)
+    with pytest.raises(F.FGAError) as ei:
+        F.spline_prefilter(np.ones(3), (False,))
+    assert ei.value.status == 1 and "grid size" in str(ei.value)
+    assert L.fga_spline_prefilter(4, n.ctypes.data, per.ctypes.data, a.ctypes.data, a.ctypes.data) == 1

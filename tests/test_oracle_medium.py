@@ -144,3 +144,32 @@ def test_hamiltonian_derivatives_match_finite_differences(sigma):
         np.testing.assert_allclose((qp["dHdP"] - qm["dHdP"]) / (2 * step), ref["HQP"][k], atol=1e-6)
         np.testing.assert_allclose((pp["dHdP"] - pm["dHdP"]) / (2 * step), ref["HPP"][k], atol=1e-6)
         np.testing.assert_allclose((pp["dHdQ"] - pm["dHdQ"]) / (2 * step), ref["HPQ"][k], atol=1e-6)
+
+
+# ---------------------------------------------------------------------------
+# The interpolating prefilter (FGA_BSPLINE_INTERP)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("periodic", [(False, False), (True, False), (True, True)])
+def test_interp_coefficients_interpolate_the_samples(periodic):
+    # the oracle's own spline evaluation (pinned above) at the grid points gives the samples
+    n = (13, 11)
+    g = O.Grid(n, (0.1, 0.2), (0.3, -0.4), periodic)
+    rng = np.random.default_rng(21)
+    c = 1.0 + rng.uniform(0.0, 1.0, n)
+    C = O.interp_coefficients(g, c)
+    axes = [g.o[k] + g.h[k] * np.arange(n[k]) for k in range(2)]
+    X = np.stack([a.ravel() for a in np.meshgrid(*axes, indexing="ij")], axis=1)
+    val, _, _, _ = O.medium_eval(g, C, X, order=0)
+    np.testing.assert_allclose(val, c.ravel(), rtol=0, atol=1e-13)
+    assert np.max(np.abs(C - c)) > 1e-3  # the prefilter does change the values
+
+
+def test_interp_coefficients_periodic_equal_scipy_wrap_filter():
+    from scipy import ndimage
+
+    n = (16, 12)
+    g = O.Grid(n, (1.0, 1.0), (0.0, 0.0), (True, True))
+    c = np.random.default_rng(22).standard_normal(n)
+    ref = ndimage.spline_filter(c, order=3, mode="grid-wrap")
+    np.testing.assert_allclose(O.interp_coefficients(g, c), ref, atol=1e-12)
