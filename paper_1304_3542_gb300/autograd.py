@@ -26,10 +26,11 @@ from . import fga as F
 class FGATraces(torch.autograd.Function):
     @staticmethod
     def forward(ctx, velocity, prob, receivers, record_every, precision=F.FGA_FP64,
-                integrate_exited=False):
+                integrate_exited=False, interp=F.FGA_BSPLINE_APPROX):
         plan = F.plan_from_problem(prob, velocity=velocity.detach().contiguous(),
                                    stream=torch.cuda.current_stream().cuda_stream,
-                                   precision=precision, integrate_exited=integrate_exited)
+                                   precision=precision, integrate_exited=integrate_exited,
+                                   interp=interp)
         plan.set_receivers(receivers, record_every)
         u0, u1 = F.stacked_initial_data(prob)
         plan.decompose(torch.from_numpy(u0).to(velocity.device),
@@ -48,12 +49,13 @@ class FGATraces(torch.autograd.Function):
         grad = torch.empty(ctx.shape, dtype=torch.float64, device=grad_out.device)
         ctx.plan.grad(grad_out.contiguous(), grad)
         ctx.plan.close()
-        return grad, None, None, None, None, None
+        return grad, None, None, None, None, None, None
 
 
 def traces(velocity, prob, receivers, record_every, **kw):
     return FGATraces.apply(velocity, prob, receivers, record_every,
-                           kw.get("precision", F.FGA_FP64), kw.get("integrate_exited", False))
+                           kw.get("precision", F.FGA_FP64), kw.get("integrate_exited", False),
+                           kw.get("interp", F.FGA_BSPLINE_APPROX))
 
 
 def grid_receivers(prob):
@@ -71,10 +73,12 @@ def grid_receivers(prob):
 
 class FGAField(torch.autograd.Function):
     @staticmethod
-    def forward(ctx, velocity, prob, precision=F.FGA_FP64, integrate_exited=False):
+    def forward(ctx, velocity, prob, precision=F.FGA_FP64, integrate_exited=False,
+                interp=F.FGA_BSPLINE_APPROX):
         plan = F.plan_from_problem(prob, velocity=velocity.detach().contiguous(),
                                    stream=torch.cuda.current_stream().cuda_stream,
-                                   precision=precision, integrate_exited=integrate_exited)
+                                   precision=precision, integrate_exited=integrate_exited,
+                                   interp=interp)
         xr = grid_receivers(prob)
         plan.set_receivers(xr, prob.nsteps)  # records at t = 0 and t = T
         u0, u1 = F.stacked_initial_data(prob)
@@ -96,11 +100,12 @@ class FGAField(torch.autograd.Function):
         grad = torch.empty(ctx.shape, dtype=torch.float64, device=grad_out.device)
         ctx.plan.grad(res, grad)
         ctx.plan.close()
-        return grad, None, None, None
+        return grad, None, None, None, None
 
 
 def field(velocity, prob, **kw):
     """u(T) on the grid [nshots][n...], differentiable in the velocity (1D and 2D, open
     axes)."""
     return FGAField.apply(velocity, prob, kw.get("precision", F.FGA_FP64),
-                          kw.get("integrate_exited", False))
+                          kw.get("integrate_exited", False),
+                          kw.get("interp", F.FGA_BSPLINE_APPROX))
