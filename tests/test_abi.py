@@ -150,3 +150,26 @@ def test_spline_prefilter_in_place_and_errors():
         F.spline_prefilter(np.ones(3), (False,))
     assert ei.value.status == 1 and "grid size" in str(ei.value)
     assert L.fga_spline_prefilter(4, n.ctypes.data, per.ctypes.data, a.ctypes.data, a.ctypes.data) == 1
+
+
+def test_config_layout_matches_the_header(tmp_path):
+    # the ctypes mirror of fga_config must have the C compiler's offsets and size
+    import shutil
+    import subprocess
+
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    names = [f[0] for f in F.Config._fields_]
+    src = tmp_path / "layout.c"
+    body = "".join('  printf("%%s %%zu\\n", "%s", offsetof(fga_config, %s));\n' % (n, n) for n in names)
+    src.write_text('#include <stddef.h>\n#include <stdio.h>\n#include "fga.h"\nint main(void) {\n'
+                   + body + '  printf("sizeof %zu\\n", sizeof(fga_config));\n  return 0;\n}\n')
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.join(root, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = dict(line.split() for line in out if line.strip())
+    for n in names:
+        assert int(got[n]) == getattr(F.Config, n).offset, n
+    assert int(got["sizeof"]) == ctypes.sizeof(F.Config)
