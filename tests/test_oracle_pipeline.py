@@ -278,3 +278,24 @@ def test_order_eps_convergence_variable_medium_1d():
         epss.append(eps)
     slope = np.polyfit(np.log(epss), np.log(errs), 1)[0]
     assert 0.8 <= slope <= 1.2, (errs, slope)
+
+
+def test_traces_equal_the_reconstruction_at_every_record():
+    # the oracle's receiver traces (rays and the sum at the receivers in one pass) against
+    # the separate propagate + reconstruct of the same Gaussians stopped at each record time
+    pr = WL.lens_2d(N=64, eps=1.0 / 256, T=0.04, dt=5e-3, s=2, box=48, tau=1e-2,
+                    k0=24 * math.pi, width2=0.01, x0=(0.5, 0.4))
+    sh = pr.shots[0]
+    g = _grid(pr)
+    dec = O.decompose(g, pr.velocity, sh.u0, sh.u1, sh.eps, sh.q_stride, sh.box, pr.tau)
+    gs = dec["gauss"]
+    W = O.quadrature_weight(g, sh.eps, sh.q_stride, sh.box)
+    xr = np.stack([np.linspace(0.2, 0.8, 9), np.full(9, 0.45)], axis=1)
+    every = 2
+    tr = O.traces(g, pr.velocity, pr.nsteps, pr.dt, every, gs["sigma"], gs["q"], gs["p"], gs["psi"],
+                  sh.eps, pr.kappa, W, xr)
+    assert tr.shape == (pr.nsteps // every + 1, len(xr))
+    for m in range(tr.shape[0]):
+        st = O.propagate(g, pr.velocity, m * every, pr.dt, gs["sigma"], gs["q"], gs["p"])
+        u = O.reconstruct(g, sh.eps, pr.kappa, W, st["Q"], st["P"], st["a"], gs["psi"], st["S"], xr)
+        np.testing.assert_allclose(tr[m], u, rtol=0, atol=1e-12 * max(1.0, np.abs(u).max()))
