@@ -16,7 +16,7 @@ def test_layered_model_is_seeded_and_in_range():
     assert not np.array_equal(a, WL.gen_layered(1305))
     assert a.min() >= 1.5 - 1e-5 and a.max() <= 5.5 + 1e-5
     assert float(np.median(a[:, 0])) < 1.55  # the top layer is 1.5 km/s
-    assert float(a[:, -1].mean()) > 3.5              # faster at depth
+    assert float(a[:, -1].mean()) > 3.5  # faster at depth
 
 
 def test_ricker_dt_is_the_derivative_of_ricker():
