@@ -3,6 +3,8 @@
   python -m paper_1304_3542_gb300.run_case [--workload layered_single] [--T 0.1]
                                            [--tau 1e-3] [--repeat 1] [--nshots 4]
                                            [--precision fp64|mixed] [--receivers] [--grad]
+                                           [--z-method dynamic|divided] [--dz-eta 0.1]
+                                           [--interp approx|interp] [--keep-n N]
 
 A small driver for trying the library on the seeded workloads (and the command
 the kernel profiles are taken with).
@@ -34,6 +36,10 @@ def main():
                     help="record traces at 368 surface receivers every 4 ms (layered model)")
     ap.add_argument("--grad", action="store_true",
                     help="with --receivers: also the adjoint dJ/dc for J = 1/2 |traces|^2")
+    ap.add_argument("--z-method", choices=["dynamic", "divided"], default="dynamic")
+    ap.add_argument("--dz-eta", type=float, default=0.1)
+    ap.add_argument("--interp", choices=["approx", "interp"], default="approx")
+    ap.add_argument("--keep-n", type=int, default=0)
     args = ap.parse_args()
     kw = {}
     if args.T is not None:
@@ -43,9 +49,16 @@ def main():
     if args.workload == "layered_batch":
         kw["nshots"] = args.nshots
     prob = WL.by_name(args.workload, **kw)
+    if args.keep_n > 0:
+        prob = prob.with_(keep_n=args.keep_n)
     precision = F.FGA_MIXED_TF32X3 if args.precision == "mixed" else F.FGA_FP64
+    divided = args.z_method == "divided"
     plan = F.plan_from_problem(prob, stream=torch.cuda.current_stream().cuda_stream,
-                               precision=precision)
+                               precision=precision,
+                               z_method=F.FGA_Z_DIVIDED if divided else F.FGA_Z_DYNAMIC,
+                               dz_eta=args.dz_eta if divided else 0.0,
+                               interp=F.FGA_BSPLINE_INTERP if args.interp == "interp"
+                               else F.FGA_BSPLINE_APPROX)
     if args.receivers:
         xr = np.stack([0.025 * np.arange(368), np.zeros(368)], axis=1)
         plan.set_receivers(xr, int(round(0.004 / prob.dt)))
