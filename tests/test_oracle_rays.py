@@ -173,7 +173,7 @@ def test_divided_differences_homogeneous_closed_form():
     # constant c: Q = q + c t p/|p| is linear in q, and in p up to the curvature of p/|p|,
     # so the central differences are exact in q (and in 1D) and carry an O(delta^2) error
     # in p: the amplitude error must fall by 4 when delta halves, against the closed form
-    for dim in (1, 2):
+    for dim in (1, 2, 3):
         g = _open_grid(dim)
         c0 = 1.7
         coef = np.full((40,) * dim, c0)
