@@ -299,3 +299,16 @@ def test_traces_equal_the_reconstruction_at_every_record():
         st = O.propagate(g, pr.velocity, m * every, pr.dt, gs["sigma"], gs["q"], gs["p"])
         u = O.reconstruct(g, sh.eps, pr.kappa, W, st["Q"], st["P"], st["a"], gs["psi"], st["S"], xr)
         np.testing.assert_allclose(tr[m], u, rtol=0, atol=1e-12 * max(1.0, np.abs(u).max()))
+
+
+def test_keep_n_ties_go_to_the_lower_q_then_p_index():
+    # equal |psi| everywhere but one entry: the N - 1 remaining picks are the first valid
+    # (q, p) in q-major, p-minor order
+    plus = np.full((4, 10), 1.0 + 0j)
+    plus[2, 5] = 3.0
+    valid = np.ones(10, dtype=bool)
+    valid[[0, 3]] = False
+    sp, _, _ = O.select(plus, plus.copy(), valid, 0.0, keep_n=5)
+    flat_valid = [q * 10 + p for q in range(4) for p in range(10) if valid[p]]
+    expect = sorted([2 * 10 + 5] + [f for f in flat_valid if f != 25][:4])
+    assert sp.tolist() == expect
