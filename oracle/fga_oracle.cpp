@@ -62,26 +62,118 @@ Grid make_grid(int dim, const int64_t* n, const double* h, const double* o, cons
 }
 
 // ---------------------------------------------------------------------------
+// Scalars. The ray system below is written once for a real scalar type R and its
+// complex partner: R = double is the oracle itself; R = Dual carries, next to every
+// value, its derivative along one direction V of the velocity coefficients (forward
+// mode: a dual number x + x' e with e^2 = 0, so every operation applies the chain
+// rule to the derivative part and leaves the value part exactly as in plain FP64).
+// Branch decisions (the spline cell, the window cut, pivoting) follow the value, so
+// the derivative is that of the piece the value lies on.
+// ---------------------------------------------------------------------------
+struct Dual {
+  double v, d;
+  Dual() : v(0.0), d(0.0) {}
+  Dual(double x) : v(x), d(0.0) {}
+  Dual(double x, double dx) : v(x), d(dx) {}
+};
+
+inline Dual operator+(const Dual& a, const Dual& b) { return Dual(a.v + b.v, a.d + b.d); }
+inline Dual operator-(const Dual& a, const Dual& b) { return Dual(a.v - b.v, a.d - b.d); }
+inline Dual operator-(const Dual& a) { return Dual(-a.v, -a.d); }
+inline Dual operator*(const Dual& a, const Dual& b) { return Dual(a.v * b.v, a.d * b.v + a.v * b.d); }
+inline Dual operator/(const Dual& a, const Dual& b) {
+  return Dual(a.v / b.v, (a.d * b.v - a.v * b.d) / (b.v * b.v));
+}
+inline Dual operator+(const Dual& a, double b) { return Dual(a.v + b, a.d); }
+inline Dual operator+(double a, const Dual& b) { return Dual(a + b.v, b.d); }
+inline Dual operator-(const Dual& a, double b) { return Dual(a.v - b, a.d); }
+inline Dual operator-(double a, const Dual& b) { return Dual(a - b.v, -b.d); }
+inline Dual operator*(const Dual& a, double b) { return Dual(a.v * b, a.d * b); }
+inline Dual operator*(double a, const Dual& b) { return Dual(a * b.v, a * b.d); }
+inline Dual operator/(const Dual& a, double b) { return Dual(a.v / b, a.d / b); }
+inline Dual operator/(double a, const Dual& b) { return Dual(a / b.v, -a * b.d / (b.v * b.v)); }
+inline Dual& operator+=(Dual& a, const Dual& b) { a = a + b; return a; }
+inline Dual& operator-=(Dual& a, const Dual& b) { a = a - b; return a; }
+inline bool operator<(const Dual& a, double b) { return a.v < b; }
+inline Dual sqrt(const Dual& a) {
+  double s = std::sqrt(a.v);
+  return Dual(s, a.d / (2.0 * s));
+}
+inline Dual fabs(const Dual& a) { return a.v < 0 ? -a : a; }
+
+// Complex partner of Dual: complex value and complex derivative.
+struct DualC {
+  cplx v, d;
+  DualC() : v(0.0), d(0.0) {}
+  DualC(double re, double im) : v(re, im), d(0.0) {}
+  DualC(const cplx& x) : v(x), d(0.0) {}
+  DualC(const cplx& x, const cplx& dx) : v(x), d(dx) {}
+  DualC(const Dual& re) : v(re.v), d(re.d) {}
+};
+
+inline DualC operator+(const DualC& a, const DualC& b) { return DualC(a.v + b.v, a.d + b.d); }
+inline DualC operator-(const DualC& a, const DualC& b) { return DualC(a.v - b.v, a.d - b.d); }
+inline DualC operator-(const DualC& a) { return DualC(-a.v, -a.d); }
+inline DualC operator*(const DualC& a, const DualC& b) { return DualC(a.v * b.v, a.d * b.v + a.v * b.d); }
+inline DualC operator/(const DualC& a, const DualC& b) {
+  return DualC(a.v / b.v, (a.d * b.v - a.v * b.d) / (b.v * b.v));
+}
+inline DualC operator*(const DualC& a, const Dual& b) { return DualC(a.v * b.v, a.d * b.v + a.v * b.d); }
+inline DualC operator*(const Dual& a, const DualC& b) { return b * a; }
+inline DualC operator*(const DualC& a, double b) { return DualC(a.v * b, a.d * b); }
+inline DualC operator*(double a, const DualC& b) { return DualC(a * b.v, a * b.d); }
+inline DualC operator/(const DualC& a, double b) { return DualC(a.v / b, a.d / b); }
+inline DualC operator-(const DualC& a, const Dual& b) { return DualC(a.v - b.v, a.d - b.d); }
+inline DualC& operator+=(DualC& a, const DualC& b) { a = a + b; return a; }
+inline DualC& operator-=(DualC& a, const DualC& b) { a = a - b; return a; }
+inline DualC exp(const DualC& a) {
+  cplx e = std::exp(a.v);
+  return DualC(e, a.d * e);
+}
+
+template <class R> struct Num;
+template <> struct Num<double> { typedef cplx C; };
+template <> struct Num<Dual> { typedef DualC C; };
+
+inline double val(double x) { return x; }
+inline double val(const Dual& x) { return x.v; }
+inline double mag(const cplx& z) { return std::abs(z); }
+inline double mag(const DualC& z) { return std::abs(z.v); }
+inline double fmod_val(double x, double L) { return std::fmod(x, L); }
+inline Dual fmod_val(const Dual& x, double L) { return Dual(std::fmod(x.v, L), x.d); }
+
+// The spline coefficients C and, for the derivative, the direction V (a grid-shaped
+// change of the coefficients; NULL = 0).
+struct Coefs {
+  const double* C;
+  const double* V;
+};
+inline void coef_at(const Coefs& cf, int64_t i, double& out) { out = cf.C[i]; }
+inline void coef_at(const Coefs& cf, int64_t i, Dual& out) { out = Dual(cf.C[i], cf.V ? cf.V[i] : 0.0); }
+
+// ---------------------------------------------------------------------------
 // Cubic B-spline beta_3 and its derivatives (order 0..3), piecewise by |t|.
 // ---------------------------------------------------------------------------
-double beta3(double t, int order) {
-  double at = std::fabs(t);
-  double sg = t < 0 ? -1.0 : 1.0;
-  if (at >= 2.0) return 0.0;
-  if (at < 1.0) {
+template <class R>
+R beta3(const R& t, int order) {
+  using std::fabs;
+  R at = fabs(t);
+  double sg = val(t) < 0 ? -1.0 : 1.0;
+  if (val(at) >= 2.0) return R(0.0);
+  if (val(at) < 1.0) {
     switch (order) {
       case 0: return 2.0 / 3.0 - t * t + 0.5 * at * at * at;
       case 1: return -2.0 * t + 1.5 * t * at;
       case 2: return -2.0 + 3.0 * at;
-      default: return 3.0 * sg;
+      default: return R(3.0 * sg);
     }
   }
-  double u = 2.0 - at;
+  R u = 2.0 - at;
   switch (order) {
     case 0: return u * u * u / 6.0;
     case 1: return -sg * u * u / 2.0;
     case 2: return u;
-    default: return -sg;
+    default: return R(-sg);
   }
 }
 
@@ -99,51 +191,56 @@ int64_t coef_index(const Grid& g, int k, int64_t i) {
 
 // c(x) = sum_i C_i prod_k beta3((x_k - o_k)/h_k - i_k), and its derivatives.
 // deriv[k] is the derivative order taken along axis k.
-double spline_value(const Grid& g, const double* C, const double* x, const int* deriv) {
+template <class R>
+R spline_value(const Grid& g, const Coefs& cf, const R* x, const int* deriv) {
   int64_t base[3];
-  double u[3];
+  R u[3];
   for (int k = 0; k < g.dim; ++k) {
     u[k] = (x[k] - g.o[k]) / g.h[k];
-    base[k] = (int64_t)std::floor(u[k]) - 1;
+    base[k] = (int64_t)std::floor(val(u[k])) - 1;
   }
-  double total = 0.0;
+  R total(0.0);
   int ntaps = 1;
   for (int k = 0; k < g.dim; ++k) ntaps *= 4;
   for (int t = 0; t < ntaps; ++t) {
     int rem = t;
     int64_t flat = 0;
-    double w = 1.0;
+    R w(1.0);
     for (int k = 0; k < g.dim; ++k) {
       int tk = rem % 4;
       rem /= 4;
       int64_t i = base[k] + tk;
-      w *= beta3(u[k] - (double)i, deriv[k]) / std::pow(g.h[k], deriv[k]);
+      w = w * (beta3(u[k] - (double)i, deriv[k]) / std::pow(g.h[k], deriv[k]));
       flat = flat * g.n[k] + coef_index(g, k, i);
     }
-    total += C[flat] * w;
+    R ci;
+    coef_at(cf, flat, ci);
+    total += ci * w;
   }
   return total;
 }
 
+template <class R>
 struct Medium {
-  double c;
-  double grad[3];
-  double hess[3][3];
+  R c;
+  R grad[3];
+  R hess[3][3];
 };
 
-Medium medium_at(const Grid& g, const double* C, const double* x) {
-  Medium m;
+template <class R>
+Medium<R> medium_at(const Grid& g, const Coefs& cf, const R* x) {
+  Medium<R> m;
   int d0[3] = {0, 0, 0};
-  m.c = spline_value(g, C, x, d0);
+  m.c = spline_value(g, cf, x, d0);
   for (int k = 0; k < g.dim; ++k) {
     int d1[3] = {0, 0, 0};
     d1[k] = 1;
-    m.grad[k] = spline_value(g, C, x, d1);
+    m.grad[k] = spline_value(g, cf, x, d1);
     for (int l = 0; l < g.dim; ++l) {
       int d2[3] = {0, 0, 0};
       d2[k] += 1;
       d2[l] += 1;
-      m.hess[k][l] = spline_value(g, C, x, d2);
+      m.hess[k][l] = spline_value(g, cf, x, d2);
     }
   }
   return m;
@@ -152,20 +249,23 @@ Medium medium_at(const Grid& g, const double* C, const double* x) {
 // ---------------------------------------------------------------------------
 // Hamiltonian H = sigma c(Q) |P| (Eq. hamiltonian) and its derivatives.
 // ---------------------------------------------------------------------------
+template <class R>
 struct HamDerivs {
-  double H;
-  double dHdQ[3], dHdP[3];
-  double HQQ[3][3], HQP[3][3], HPP[3][3], HPQ[3][3];  // HQP[l][k] = d2H/dQ_l dP_k
+  R H;
+  R dHdQ[3], dHdP[3];
+  R HQQ[3][3], HQP[3][3], HPP[3][3], HPQ[3][3];  // HQP[l][k] = d2H/dQ_l dP_k
 };
 
-HamDerivs hamiltonian(const Grid& g, const double* C, int sigma, const double* Q, const double* P) {
-  HamDerivs r;
+template <class R>
+HamDerivs<R> hamiltonian(const Grid& g, const Coefs& cf, int sigma, const R* Q, const R* P) {
+  using std::sqrt;
+  HamDerivs<R> r;
   int d = g.dim;
-  Medium m = medium_at(g, C, Q);
-  double pn = 0.0;
+  Medium<R> m = medium_at(g, cf, Q);
+  R pn(0.0);
   for (int k = 0; k < d; ++k) pn += P[k] * P[k];
-  pn = std::sqrt(pn);
-  double nh[3];
+  pn = sqrt(pn);
+  R nh[3];
   for (int k = 0; k < d; ++k) nh[k] = P[k] / pn;
   double s = (double)sigma;
   r.H = s * m.c * pn;
@@ -187,19 +287,32 @@ HamDerivs hamiltonian(const Grid& g, const double* C, int sigma, const double* Q
 // Per-Gaussian state and the right-hand side of the FGA ODE system.
 // A = d_z Q and B = d_z P with (j,k) entry d_{z_j} Q_k (resp. P_k).
 // ---------------------------------------------------------------------------
+template <class R>
 struct State {
-  double Q[3], P[3];
-  cplx A[3][3], B[3][3];
-  cplx a;
-  double S;
+  typedef typename Num<R>::C C;
+  R Q[3], P[3];
+  C A[3][3], B[3][3];
+  C a;
+  R S;
 };
 
-void state_zero(State& s) {
-  std::memset(&s, 0, sizeof(State));
+template <class R>
+void state_zero(State<R>& s) {
+  for (int i = 0; i < 3; ++i) {
+    s.Q[i] = R(0.0);
+    s.P[i] = R(0.0);
+    for (int j = 0; j < 3; ++j) {
+      s.A[i][j] = typename Num<R>::C(0.0, 0.0);
+      s.B[i][j] = typename Num<R>::C(0.0, 0.0);
+    }
+  }
+  s.a = typename Num<R>::C(0.0, 0.0);
+  s.S = R(0.0);
 }
 
 // out = y + h * k
-void state_axpy(int d, const State& y, double h, const State& k, State& out) {
+template <class R>
+void state_axpy(int d, const State<R>& y, double h, const State<R>& k, State<R>& out) {
   for (int i = 0; i < d; ++i) {
     out.Q[i] = y.Q[i] + h * k.Q[i];
     out.P[i] = y.P[i] + h * k.P[i];
@@ -213,8 +326,9 @@ void state_axpy(int d, const State& y, double h, const State& k, State& out) {
 }
 
 // tr(Z^{-1} W) by solving Z X = W with Gaussian elimination (partial pivoting).
-cplx trace_solve(int d, const cplx Zin[3][3], const cplx Win[3][3]) {
-  cplx Z[3][3], W[3][3];
+template <class C>
+C trace_solve(int d, const C Zin[3][3], const C Win[3][3]) {
+  C Z[3][3], W[3][3];
   for (int i = 0; i < d; ++i)
     for (int j = 0; j < d; ++j) {
       Z[i][j] = Zin[i][j];
@@ -223,36 +337,38 @@ cplx trace_solve(int d, const cplx Zin[3][3], const cplx Win[3][3]) {
   for (int col = 0; col < d; ++col) {
     int piv = col;
     for (int r = col + 1; r < d; ++r)
-      if (std::abs(Z[r][col]) > std::abs(Z[piv][col])) piv = r;
+      if (mag(Z[r][col]) > mag(Z[piv][col])) piv = r;
     if (piv != col)
       for (int j = 0; j < d; ++j) {
         std::swap(Z[col][j], Z[piv][j]);
         std::swap(W[col][j], W[piv][j]);
       }
     for (int r = col + 1; r < d; ++r) {
-      cplx f = Z[r][col] / Z[col][col];
+      C f = Z[r][col] / Z[col][col];
       for (int j = 0; j < d; ++j) {
         Z[r][j] -= f * Z[col][j];
         W[r][j] -= f * W[col][j];
       }
     }
   }
-  cplx X[3][3];
+  C X[3][3];
   for (int j = 0; j < d; ++j)
     for (int r = d - 1; r >= 0; --r) {
-      cplx acc = W[r][j];
+      C acc = W[r][j];
       for (int c = r + 1; c < d; ++c) acc -= Z[r][c] * X[c][j];
       X[r][j] = acc / Z[r][r];
     }
-  cplx tr = 0.0;
+  C tr(0.0, 0.0);
   for (int i = 0; i < d; ++i) tr += X[i][i];
   return tr;
 }
 
-void rhs(const Grid& g, const double* C, int sigma, const State& y, State& dy) {
+template <class R>
+void rhs(const Grid& g, const Coefs& cf, int sigma, const State<R>& y, State<R>& dy) {
+  typedef typename Num<R>::C C;
   int d = g.dim;
   state_zero(dy);
-  HamDerivs hd = hamiltonian(g, C, sigma, y.Q, y.P);
+  HamDerivs<R> hd = hamiltonian(g, cf, sigma, y.Q, y.P);
   // Eq. characline
   for (int k = 0; k < d; ++k) {
     dy.Q[k] = hd.dHdP[k];
@@ -261,7 +377,7 @@ void rhs(const Grid& g, const double* C, int sigma, const State& y, State& dy) {
   // Eqs. dzQ, dzP (componentwise form, summation over l)
   for (int j = 0; j < d; ++j)
     for (int k = 0; k < d; ++k) {
-      cplx dA = 0.0, dB = 0.0;
+      C dA(0.0, 0.0), dB(0.0, 0.0);
       for (int l = 0; l < d; ++l) {
         dA += y.A[j][l] * hd.HQP[l][k] + y.B[j][l] * hd.HPP[l][k];
         dB += -y.A[j][l] * hd.HQQ[l][k] - y.B[j][l] * hd.HPQ[l][k];
@@ -270,44 +386,46 @@ void rhs(const Grid& g, const double* C, int sigma, const State& y, State& dy) {
       dy.B[j][k] = dB;
     }
   // Eq. a_formu with Z = d_z(Q + iP) = A + iB (Eq. op_zZ)
-  const cplx I(0.0, 1.0);
-  cplx Z[3][3], dZ[3][3];
+  const C I(0.0, 1.0);
+  C Z[3][3], dZ[3][3];
   for (int j = 0; j < d; ++j)
     for (int k = 0; k < d; ++k) {
       Z[j][k] = y.A[j][k] + I * y.B[j][k];
       dZ[j][k] = dy.A[j][k] + I * dy.B[j][k];
     }
-  double dot = 0.0;
+  R dot(0.0);
   for (int k = 0; k < d; ++k) dot += hd.dHdP[k] * hd.dHdQ[k];
   dy.a = y.a * (dot / hd.H) + 0.5 * y.a * trace_solve(d, Z, dZ);
   // action: dS/dt = P . dQ/dt - H
-  double pq = 0.0;
+  R pq(0.0);
   for (int k = 0; k < d; ++k) pq += y.P[k] * dy.Q[k];
   dy.S = pq - hd.H;
 }
 
-void wrap_periodic(const Grid& g, State& y) {
+template <class R>
+void wrap_periodic(const Grid& g, State<R>& y) {
   for (int k = 0; k < g.dim; ++k) {
     if (!g.periodic[k]) continue;
     double L = g.n[k] * g.h[k];
-    double r = std::fmod(y.Q[k] - g.o[k], L);
-    if (r < 0) r += L;
+    R r = fmod_val(y.Q[k] - g.o[k], L);
+    if (val(r) < 0) r = r + L;
     y.Q[k] = g.o[k] + r;
   }
 }
 
-void rk4_step(const Grid& g, const double* C, int sigma, State& y, double dt) {
+template <class R>
+void rk4_step(const Grid& g, const Coefs& cf, int sigma, State<R>& y, double dt) {
   int d = g.dim;
-  State k1, k2, k3, k4, tmp;
+  State<R> k1, k2, k3, k4, tmp;
   state_zero(tmp);
-  rhs(g, C, sigma, y, k1);
+  rhs(g, cf, sigma, y, k1);
   state_axpy(d, y, 0.5 * dt, k1, tmp);
-  rhs(g, C, sigma, tmp, k2);
+  rhs(g, cf, sigma, tmp, k2);
   state_axpy(d, y, 0.5 * dt, k2, tmp);
-  rhs(g, C, sigma, tmp, k3);
+  rhs(g, cf, sigma, tmp, k3);
   state_axpy(d, y, dt, k3, tmp);
-  rhs(g, C, sigma, tmp, k4);
-  State out = y;
+  rhs(g, cf, sigma, tmp, k4);
+  State<R> out = y;
   for (int i = 0; i < d; ++i) {
     out.Q[i] = y.Q[i] + dt / 6.0 * (k1.Q[i] + 2.0 * k2.Q[i] + 2.0 * k3.Q[i] + k4.Q[i]);
     out.P[i] = y.P[i] + dt / 6.0 * (k1.P[i] + 2.0 * k2.P[i] + 2.0 * k3.P[i] + k4.P[i]);
@@ -320,6 +438,21 @@ void rk4_step(const Grid& g, const double* C, int sigma, State& y, double dt) {
   out.S = y.S + dt / 6.0 * (k1.S + 2.0 * k2.S + 2.0 * k3.S + k4.S);
   wrap_periodic(g, out);
   y = out;
+}
+
+// Initial values Q = q, P = p, A = I, B = -iI, a = 2^{d/2}, S = 0.
+template <class R>
+void state_init(int d, const double* q, const double* p, State<R>& y) {
+  typedef typename Num<R>::C C;
+  state_zero(y);
+  for (int k = 0; k < d; ++k) {
+    y.Q[k] = R(q[k]);
+    y.P[k] = R(p[k]);
+    y.A[k][k] = C(1.0, 0.0);
+    y.B[k][k] = C(0.0, -1.0);
+  }
+  y.a = C(std::pow(2.0, 0.5 * d), 0.0);
+  y.S = R(0.0);
 }
 
 // ---------------------------------------------------------------------------
@@ -372,13 +505,14 @@ void dd_rhs(const Grid& g, const double* C, int sigma, const double* dq, const d
             const DDState& y, DDState& dy) {
   int d = g.dim;
   std::memset(&dy, 0, sizeof(DDState));
-  HamDerivs hd = hamiltonian(g, C, sigma, y.Q, y.P);
+  const Coefs cf = {C, nullptr};
+  HamDerivs<double> hd = hamiltonian<double>(g, cf, sigma, y.Q, y.P);
   for (int k = 0; k < d; ++k) {
     dy.Q[k] = hd.dHdP[k];
     dy.P[k] = -hd.dHdQ[k];
   }
   for (int r = 0; r < 4 * d; ++r) {
-    HamDerivs ha = hamiltonian(g, C, sigma, y.Qa[r], y.Pa[r]);
+    HamDerivs<double> ha = hamiltonian<double>(g, cf, sigma, y.Qa[r], y.Pa[r]);
     for (int k = 0; k < d; ++k) {
       dy.Qa[r][k] = ha.dHdP[k];
       dy.Pa[r][k] = -ha.dHdQ[k];
@@ -439,6 +573,160 @@ void set_threads(int nthreads) {
 #endif
 }
 
+// Output of a propagation: the values and, for R = Dual, their derivatives.
+struct StateOut {
+  double *Q, *P, *A, *B, *a, *S;
+};
+
+inline void put(double x, int64_t i, double* v, double*) { v[i] = x; }
+inline void put(const Dual& x, int64_t i, double* v, double* dv) {
+  v[i] = x.v;
+  if (dv) dv[i] = x.d;
+}
+inline void put_c(const cplx& z, int64_t i, double* v, double*) {
+  v[2 * i] = z.real();
+  v[2 * i + 1] = z.imag();
+}
+inline void put_c(const DualC& z, int64_t i, double* v, double* dv) {
+  v[2 * i] = z.v.real();
+  v[2 * i + 1] = z.v.imag();
+  if (dv) {
+    dv[2 * i] = z.d.real();
+    dv[2 * i + 1] = z.d.imag();
+  }
+}
+
+template <class R>
+int propagate_impl(const Grid& g, const Coefs& cf, int64_t nsteps, double dt, int64_t nG,
+                   const int* sigma, const double* q, const double* p, const StateOut& out,
+                   const StateOut& dout, int nthreads) {
+  int d = g.dim;
+  for (int64_t i = 0; i < nG; ++i) {
+    double pn = 0.0;
+    for (int k = 0; k < d; ++k) pn += p[i * d + k] * p[i * d + k];
+    if (!(pn > 0.0)) return 2;
+  }
+  set_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 16)
+  for (int64_t i = 0; i < nG; ++i) {
+    State<R> y;
+    state_init(d, q + i * d, p + i * d, y);
+    for (int64_t s = 0; s < nsteps; ++s) rk4_step(g, cf, sigma[i], y, dt);
+    for (int k = 0; k < d; ++k) {
+      put(y.Q[k], i * d + k, out.Q, dout.Q);
+      put(y.P[k], i * d + k, out.P, dout.P);
+      for (int l = 0; l < d; ++l) {
+        put_c(y.A[k][l], (i * d + k) * d + l, out.A, dout.A);
+        put_c(y.B[k][l], (i * d + k) * d + l, out.B, dout.B);
+      }
+    }
+    put_c(y.a, i, out.a, dout.a);
+    put(y.S, i, out.S, dout.S);
+  }
+  return 0;
+}
+
+// One term of Eq. recons at the point xp (without the factor W a psi (2 pi eps)^{-3d/2}
+// e^{iS/eps}): the sum over the images inside the square window |x_k - Q_k| <= cut of
+// exp(i P.(x - Q)/eps - |x - Q|^2/(2 eps)); periodic axes have L[k] > 0.
+template <class R>
+typename Num<R>::C window_term(int d, const double* L, double eps, double cut, const R* Qg,
+                               const R* Pg, const double* xp) {
+  typedef typename Num<R>::C C;
+  const C I(0.0, 1.0);
+  R img[3][5];
+  int nimg[3];
+  for (int k = 0; k < d; ++k) {
+    nimg[k] = 0;
+    R d0 = xp[k] - Qg[k];
+    if (L[k] > 0.0) {
+      for (int l = -2; l <= 2; ++l) {
+        R dk = d0 + l * L[k];
+        if (std::fabs(val(dk)) <= cut) img[k][nimg[k]++] = dk;
+      }
+    } else if (std::fabs(val(d0)) <= cut) {
+      img[k][nimg[k]++] = d0;
+    }
+    if (nimg[k] == 0) return C(0.0, 0.0);
+  }
+  C sum(0.0, 0.0);
+  int combos = 1;
+  for (int k = 0; k < d; ++k) combos *= nimg[k];
+  for (int cidx = 0; cidx < combos; ++cidx) {
+    int rem = cidx;
+    R phase(0.0), r2(0.0);
+    for (int k = 0; k < d; ++k) {
+      R dk = img[k][rem % nimg[k]];
+      rem /= nimg[k];
+      phase += Pg[k] * dk;
+      r2 += dk * dk;
+    }
+    sum += exp(I * phase / eps - r2 / (2.0 * eps));
+  }
+  return sum;
+}
+
+inline void make_psi(const double* psi, const double*, int64_t i, cplx& out) {
+  out = cplx(psi[2 * i], psi[2 * i + 1]);
+}
+inline void make_psi(const double* psi, const double* dpsi, int64_t i, DualC& out) {
+  out = DualC(cplx(psi[2 * i], psi[2 * i + 1]),
+              dpsi ? cplx(dpsi[2 * i], dpsi[2 * i + 1]) : cplx(0.0, 0.0));
+}
+
+template <class R>
+int traces_impl(const Grid& g, const Coefs& cf, int64_t nsteps, double dt, int64_t record_every,
+                int64_t nG, const int* sigma, const double* q, const double* p, const double* psi,
+                const double* dpsi, double eps, double kappa, double W, int64_t nrx,
+                const double* xr, double* out, double* dout, int nthreads) {
+  typedef typename Num<R>::C C;
+  int d = g.dim;
+  double L[3] = {0, 0, 0};
+  for (int k = 0; k < d; ++k) L[k] = g.periodic[k] ? g.n[k] * g.h[k] : 0.0;
+  const int64_t nrec = nsteps / record_every + 1;
+  const double cut = kappa * std::sqrt(eps);
+  const double norm = std::pow(2.0 * kPi * eps, -1.5 * d);
+  const C I(0.0, 1.0);
+  int nt = nthreads > 0 ? nthreads : 1;
+  std::vector<C> part((size_t)nt * nrec * nrx, C(0.0, 0.0));
+  for (int64_t i = 0; i < nG; ++i) {
+    double pn = 0.0;
+    for (int k = 0; k < d; ++k) pn += p[i * d + k] * p[i * d + k];
+    if (!(pn > 0.0)) return 2;
+  }
+  set_threads(nt);
+#pragma omp parallel num_threads(nt)
+  {
+    int tid = 0;
+#ifdef _OPENMP
+    tid = omp_get_thread_num();
+#endif
+    int64_t lo = nG * tid / nt, hi = nG * (tid + 1) / nt;
+    C* acc = part.data() + (size_t)tid * nrec * nrx;
+    for (int64_t i = lo; i < hi; ++i) {
+      State<R> y;
+      state_init(d, q + i * d, p + i * d, y);
+      C ps;
+      make_psi(psi, dpsi, i, ps);
+      for (int64_t s = 0; s <= nsteps; ++s) {
+        if (s % record_every == 0) {
+          C pref = W * y.a * ps * norm * exp(I * y.S / eps);
+          int64_t m = s / record_every;
+          for (int64_t r = 0; r < nrx; ++r)
+            acc[m * nrx + r] += pref * window_term(d, L, eps, cut, y.Q, y.P, xr + r * d);
+        }
+        if (s < nsteps) rk4_step(g, cf, sigma[i], y, dt);
+      }
+    }
+  }
+  for (int64_t e = 0; e < nrec * nrx; ++e) {
+    C v(0.0, 0.0);
+    for (int t = 0; t < nt; ++t) v += part[(size_t)t * nrec * nrx + e];
+    put_c(v, e, out, dout);
+  }
+  return 0;
+}
+
 }  // namespace
 
 extern "C" {
@@ -458,22 +746,23 @@ int orc_medium_eval(int dim, const int64_t* n, const double* h, const double* o,
                     double* hess, double* d3) {
   if (dim < 1 || dim > 3) return 1;
   Grid g = make_grid(dim, n, h, o, periodic);
+  const Coefs cf = {C, nullptr};
   for (int64_t ip = 0; ip < npts; ++ip) {
     const double* xp = x + ip * dim;
     int d0[3] = {0, 0, 0};
-    c[ip] = spline_value(g, C, xp, d0);
+    c[ip] = spline_value<double>(g, cf, xp, d0);
     for (int k = 0; k < dim; ++k) {
       if (grad) {
         int d1[3] = {0, 0, 0};
         d1[k] = 1;
-        grad[ip * dim + k] = spline_value(g, C, xp, d1);
+        grad[ip * dim + k] = spline_value<double>(g, cf, xp, d1);
       }
       for (int l = 0; l < dim; ++l) {
         if (hess) {
           int d2[3] = {0, 0, 0};
           d2[k] += 1;
           d2[l] += 1;
-          hess[(ip * dim + k) * dim + l] = spline_value(g, C, xp, d2);
+          hess[(ip * dim + k) * dim + l] = spline_value<double>(g, cf, xp, d2);
         }
         if (d3)
           for (int m = 0; m < dim; ++m) {
@@ -481,7 +770,7 @@ int orc_medium_eval(int dim, const int64_t* n, const double* h, const double* o,
             dd[k] += 1;
             dd[l] += 1;
             dd[m] += 1;
-            d3[((ip * dim + k) * dim + l) * dim + m] = spline_value(g, C, xp, dd);
+            d3[((ip * dim + k) * dim + l) * dim + m] = spline_value<double>(g, cf, xp, dd);
           }
       }
     }
@@ -496,7 +785,8 @@ int orc_hamiltonian(int dim, const int64_t* n, const double* h, const double* o,
                     const double* C, int sigma, const double* Q, const double* P, double* out) {
   if (dim < 1 || dim > 3) return 1;
   Grid g = make_grid(dim, n, h, o, periodic);
-  HamDerivs r = hamiltonian(g, C, sigma, Q, P);
+  const Coefs cf = {C, nullptr};
+  HamDerivs<double> r = hamiltonian<double>(g, cf, sigma, Q, P);
   int d = dim, at = 0;
   out[at++] = r.H;
   for (int k = 0; k < d; ++k) out[at++] = r.dHdQ[k];
@@ -522,41 +812,27 @@ int orc_propagate(int dim, const int64_t* n, const double* h, const double* o, c
                   double* Bout, double* aout, double* Sout, int nthreads) {
   if (dim < 1 || dim > 3) return 1;
   Grid g = make_grid(dim, n, h, o, periodic);
-  int d = dim;
-  for (int64_t i = 0; i < nG; ++i) {
-    double pn = 0.0;
-    for (int k = 0; k < d; ++k) pn += p[i * d + k] * p[i * d + k];
-    if (!(pn > 0.0)) return 2;
-  }
-  set_threads(nthreads);
-#pragma omp parallel for schedule(dynamic, 16)
-  for (int64_t i = 0; i < nG; ++i) {
-    State y;
-    state_zero(y);
-    for (int k = 0; k < d; ++k) {
-      y.Q[k] = q[i * d + k];
-      y.P[k] = p[i * d + k];
-      y.A[k][k] = cplx(1.0, 0.0);
-      y.B[k][k] = cplx(0.0, -1.0);
-    }
-    y.a = cplx(std::pow(2.0, 0.5 * d), 0.0);
-    y.S = 0.0;
-    for (int64_t s = 0; s < nsteps; ++s) rk4_step(g, C, sigma[i], y, dt);
-    for (int k = 0; k < d; ++k) {
-      Qout[i * d + k] = y.Q[k];
-      Pout[i * d + k] = y.P[k];
-      for (int l = 0; l < d; ++l) {
-        Aout[((i * d + k) * d + l) * 2 + 0] = y.A[k][l].real();
-        Aout[((i * d + k) * d + l) * 2 + 1] = y.A[k][l].imag();
-        Bout[((i * d + k) * d + l) * 2 + 0] = y.B[k][l].real();
-        Bout[((i * d + k) * d + l) * 2 + 1] = y.B[k][l].imag();
-      }
-    }
-    aout[2 * i + 0] = y.a.real();
-    aout[2 * i + 1] = y.a.imag();
-    Sout[i] = y.S;
-  }
-  return 0;
+  const Coefs cf = {C, nullptr};
+  const StateOut out = {Qout, Pout, Aout, Bout, aout, Sout};
+  const StateOut none = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  return propagate_impl<double>(g, cf, nsteps, dt, nG, sigma, q, p, out, none, nthreads);
+}
+
+// Tangent-linear propagation: orc_propagate of the coefficients C + e V to first order in
+// e. The values (Qout .. Sout) equal orc_propagate's; dQ .. dS (same layouts) are their
+// derivatives along V, d/de at e = 0, from the dual-number evaluation of the same RK4.
+int orc_propagate_tangent(int dim, const int64_t* n, const double* h, const double* o,
+                          const int* periodic, const double* C, const double* V, int64_t nsteps,
+                          double dt, int64_t nG, const int* sigma, const double* q,
+                          const double* p, double* Qout, double* Pout, double* Aout,
+                          double* Bout, double* aout, double* Sout, double* dQ, double* dP,
+                          double* dA, double* dB, double* da, double* dS, int nthreads) {
+  if (dim < 1 || dim > 3) return 1;
+  Grid g = make_grid(dim, n, h, o, periodic);
+  const Coefs cf = {C, V};
+  const StateOut out = {Qout, Pout, Aout, Bout, aout, Sout};
+  const StateOut dout = {dQ, dP, dA, dB, da, dS};
+  return propagate_impl<Dual>(g, cf, nsteps, dt, nG, sigma, q, p, out, dout, nthreads);
 }
 
 // orc_propagate with d_z Q, d_z P from divided differences (offsets dq[d], dp[d] > 0)
@@ -622,44 +898,6 @@ int orc_propagate_dd(int dim, const int64_t* n, const double* h, const double* o
     Sout[i] = y.S;
   }
   return 0;
-}
-
-// One term of Eq. recons at the point xp (without the factor W a psi (2 pi eps)^{-3d/2}
-// e^{iS/eps}): the sum over the images inside the square window |x_k - Q_k| <= cut of
-// exp(i P.(x - Q)/eps - |x - Q|^2/(2 eps)); periodic axes have L[k] > 0.
-static cplx window_term(int d, const double* L, double eps, double cut, const double* Qg,
-                        const double* Pg, const double* xp) {
-  const cplx I(0.0, 1.0);
-  double img[3][5];
-  int nimg[3];
-  for (int k = 0; k < d; ++k) {
-    nimg[k] = 0;
-    double d0 = xp[k] - Qg[k];
-    if (L[k] > 0.0) {
-      for (int l = -2; l <= 2; ++l) {
-        double dk = d0 + l * L[k];
-        if (std::fabs(dk) <= cut) img[k][nimg[k]++] = dk;
-      }
-    } else if (std::fabs(d0) <= cut) {
-      img[k][nimg[k]++] = d0;
-    }
-    if (nimg[k] == 0) return 0.0;
-  }
-  cplx sum = 0.0;
-  int combos = 1;
-  for (int k = 0; k < d; ++k) combos *= nimg[k];
-  for (int cidx = 0; cidx < combos; ++cidx) {
-    int rem = cidx;
-    double phase = 0.0, r2 = 0.0;
-    for (int k = 0; k < d; ++k) {
-      double dk = img[k][rem % nimg[k]];
-      rem /= nimg[k];
-      phase += Pg[k] * dk;
-      r2 += dk * dk;
-    }
-    sum += std::exp(I * phase / eps - r2 / (2.0 * eps));
-  }
-  return sum;
 }
 
 // Reconstruction sum (Eq. recons) at npts points x[npts][dim]:
@@ -792,59 +1030,27 @@ int orc_traces(int dim, const int64_t* n, const double* h, const double* o, cons
                int nthreads) {
   if (dim < 1 || dim > 3 || record_every < 1 || nsteps % record_every != 0) return 1;
   Grid g = make_grid(dim, n, h, o, periodic);
-  int d = dim;
-  double L[3] = {0, 0, 0};
-  for (int k = 0; k < d; ++k) L[k] = g.periodic[k] ? g.n[k] * g.h[k] : 0.0;
-  const int64_t nrec = nsteps / record_every + 1;
-  const double cut = kappa * std::sqrt(eps);
-  const double norm = std::pow(2.0 * kPi * eps, -1.5 * d);
-  const cplx I(0.0, 1.0);
-  int nt = nthreads > 0 ? nthreads : 1;
-  std::vector<cplx> part((size_t)nt * nrec * nrx, cplx(0.0, 0.0));
-  for (int64_t i = 0; i < nG; ++i) {
-    double pn = 0.0;
-    for (int k = 0; k < d; ++k) pn += p[i * d + k] * p[i * d + k];
-    if (!(pn > 0.0)) return 2;
-  }
-  set_threads(nt);
-#pragma omp parallel num_threads(nt)
-  {
-    int tid = 0;
-#ifdef _OPENMP
-    tid = omp_get_thread_num();
-#endif
-    int64_t lo = nG * tid / nt, hi = nG * (tid + 1) / nt;
-    cplx* acc = part.data() + (size_t)tid * nrec * nrx;
-    for (int64_t i = lo; i < hi; ++i) {
-      State y;
-      state_zero(y);
-      for (int k = 0; k < d; ++k) {
-        y.Q[k] = q[i * d + k];
-        y.P[k] = p[i * d + k];
-        y.A[k][k] = cplx(1.0, 0.0);
-        y.B[k][k] = cplx(0.0, -1.0);
-      }
-      y.a = cplx(std::pow(2.0, 0.5 * d), 0.0);
-      y.S = 0.0;
-      cplx ps(psi[2 * i], psi[2 * i + 1]);
-      for (int64_t s = 0; s <= nsteps; ++s) {
-        if (s % record_every == 0) {
-          cplx pref = W * y.a * ps * norm * std::exp(I * y.S / eps);
-          int64_t m = s / record_every;
-          for (int64_t r = 0; r < nrx; ++r)
-            acc[m * nrx + r] += pref * window_term(d, L, eps, cut, y.Q, y.P, xr + r * d);
-        }
-        if (s < nsteps) rk4_step(g, C, sigma[i], y, dt);
-      }
-    }
-  }
-  for (int64_t e = 0; e < nrec * nrx; ++e) {
-    cplx v = 0.0;
-    for (int t = 0; t < nt; ++t) v += part[(size_t)t * nrec * nrx + e];
-    out[2 * e] = v.real();
-    out[2 * e + 1] = v.imag();
-  }
-  return 0;
+  const Coefs cf = {C, nullptr};
+  return traces_impl<double>(g, cf, nsteps, dt, record_every, nG, sigma, q, p, psi, nullptr,
+                             eps, kappa, W, nrx, xr, out, nullptr, nthreads);
+}
+
+// Tangent-linear traces: orc_traces for the coefficients C + e V and the weights
+// psi + e dpsi, to first order in e (the set of Gaussians and their (q, p) held fixed).
+// out equals orc_traces; dout ([nrec][nrx][2]) is d/de at e = 0 through the rays, the
+// amplitude and the action (dual-number RK4) and through psi. The window cut
+// |x_k - Q_k| <= kappa sqrt(eps) is decided on the value of Q.
+int orc_traces_tangent(int dim, const int64_t* n, const double* h, const double* o,
+                       const int* periodic, const double* C, const double* V, int64_t nsteps,
+                       double dt, int64_t record_every, int64_t nG, const int* sigma,
+                       const double* q, const double* p, const double* psi, const double* dpsi,
+                       double eps, double kappa, double W, int64_t nrx, const double* xr,
+                       double* out, double* dout, int nthreads) {
+  if (dim < 1 || dim > 3 || record_every < 1 || nsteps % record_every != 0) return 1;
+  Grid g = make_grid(dim, n, h, o, periodic);
+  const Coefs cf = {C, V};
+  return traces_impl<Dual>(g, cf, nsteps, dt, record_every, nG, sigma, q, p, psi, dpsi, eps,
+                           kappa, W, nrx, xr, out, dout, nthreads);
 }
 
 }  // extern "C"

@@ -82,6 +82,10 @@ def _load():
         lib.orc_fbi_direct.argtypes = [ci, P, P, P, P, d, P, i64, P, P, P]
         lib.orc_traces.argtypes = [ci, P, P, P, P, P, i64, d, i64, i64, P, P, P, P, d, d, d, i64,
                                    P, P, ci]
+        lib.orc_propagate_tangent.argtypes = [ci, P, P, P, P, P, P, i64, d, i64, P, P, P, P, P,
+                                              P, P, P, P, P, P, P, P, P, P, ci]
+        lib.orc_traces_tangent.argtypes = [ci, P, P, P, P, P, P, i64, d, i64, i64, P, P, P, P,
+                                           P, d, d, d, i64, P, P, P, ci]
         lib.orc_num_threads_available.restype = ci
         _lib = lib
     return _lib
@@ -485,6 +489,116 @@ def frozen_set_traces(grid: Grid, coef, f0, f1, eps, stride, box, keys, nsteps, 
     W = quadrature_weight(grid, eps, stride, box)
     return traces(grid, coef, nsteps, dt, record_every, sigma, qpts, ppts, psi, eps, kappa, W, xr,
                   nthreads)
+
+
+# ---------------------------------------------------------------------------
+# Forward-mode (tangent-linear) derivatives along a change V of the velocity
+# coefficients, with the set of Gaussians held fixed. The C++ part evaluates the same
+# RK4 and reconstruction sum on dual numbers (value + derivative); the branch split's
+# derivative through c(q) is written out here.
+# ---------------------------------------------------------------------------
+
+def propagate_tangent(grid: Grid, coef: np.ndarray, dcoef: np.ndarray, nsteps: int, dt: float,
+                      sigma: np.ndarray, q: np.ndarray, p: np.ndarray,
+                      nthreads: Optional[int] = None):
+    """propagate() and the derivative of its outputs along dcoef: returns (state, dstate),
+    dstate[k] = d state[k](coef + e dcoef)/de at e = 0 (q, p fixed)."""
+    lib = _load()
+    d = grid.dim
+    sigma = np.ascontiguousarray(sigma, dtype=np.int32)
+    q = _f64(q).reshape(-1, d)
+    p = _f64(p).reshape(-1, d)
+    nG = q.shape[0]
+    bufs = [np.empty((nG, d)), np.empty((nG, d)), np.empty((nG, d, d, 2)), np.empty((nG, d, d, 2)),
+            np.empty((nG, 2)), np.empty(nG)]
+    dbufs = [np.empty_like(b) for b in bufs]
+    rc = lib.orc_propagate_tangent(*grid.args(), _ptr(_f64(coef)), _ptr(_f64(dcoef)), int(nsteps),
+                                   float(dt), nG, _ptr(sigma), _ptr(q), _ptr(p),
+                                   *[_ptr(b) for b in bufs], *[_ptr(b) for b in dbufs],
+                                   int(nthreads or default_threads()))
+    assert rc == 0, "orc_propagate_tangent failed (%d)" % rc
+
+    def pack(b):
+        return {"Q": b[0], "P": b[1], "A": b[2][..., 0] + 1j * b[2][..., 1],
+                "B": b[3][..., 0] + 1j * b[3][..., 1], "a": b[4][:, 0] + 1j * b[4][:, 1],
+                "S": b[5]}
+
+    return pack(bufs), pack(dbufs)
+
+
+def branch_split_tangent(grid: Grid, coef: np.ndarray, dcoef: np.ndarray, eps: float, stride, box,
+                         psi1: np.ndarray, q_subset: Optional[np.ndarray] = None):
+    """Derivative of psi+- = 1/2 (psi0 +- i eps psi1/(c(q)|p|)) (Eq. psi, u+-,0) along
+    dcoef: psi0 and psi1 do not depend on c, and the spline is linear in its
+    coefficients, so d c(q) is the spline of dcoef at q and
+        d psi+- = -+ 1/2 i eps psi1 d c(q)/(c(q)^2 |p|).
+    Zero on the left-out p values. Returns (d psi_plus, d psi_minus)."""
+    qpts = q_points(grid, stride)
+    if q_subset is not None:
+        qpts = qpts[np.asarray(q_subset, dtype=np.int64)]
+    cq, _, _, _ = medium_eval(grid, coef, qpts, order=0)
+    dcq, _, _, _ = medium_eval(grid, dcoef, qpts, order=0)
+    pp = p_points(grid, eps, box)
+    pn = np.sqrt(np.sum(pp * pp, axis=1))
+    valid = p_valid(box)
+    inv = np.zeros_like(pn)
+    inv[valid] = 1.0 / pn[valid]
+    dratio = -1j * eps * inv[None, :] * (dcq / (cq * cq))[:, None]
+    dplus = 0.5 * dratio * psi1
+    dminus = -0.5 * dratio * psi1
+    dplus[:, ~valid] = 0.0
+    dminus[:, ~valid] = 0.0
+    return dplus, dminus
+
+
+def traces_tangent(grid: Grid, coef, dcoef, nsteps: int, dt: float, record_every: int, sigma, q, p,
+                   psi, dpsi, eps: float, kappa: float, W: float, xr, nthreads: Optional[int] = None):
+    """traces() and its derivative along (dcoef, dpsi): returns two [nrec][nrx] complex
+    arrays, the traces (equal to traces()) and d traces(coef + e dcoef, psi + e dpsi)/de."""
+    lib = _load()
+    d = grid.dim
+    sigma = np.ascontiguousarray(sigma, dtype=np.int32)
+    q = _f64(q).reshape(-1, d)
+    p = _f64(p).reshape(-1, d)
+    nG = q.shape[0]
+
+    def c2(z):
+        return _f64(np.stack([np.real(z), np.imag(z)], axis=1)) if nG else np.empty((0, 2))
+
+    ps, dps = c2(psi), c2(dpsi)
+    xr = _f64(xr).reshape(-1, d)
+    nrec = nsteps // record_every + 1
+    out = np.empty((nrec, xr.shape[0], 2))
+    dout = np.empty_like(out)
+    rc = lib.orc_traces_tangent(*grid.args(), _ptr(_f64(coef)), _ptr(_f64(dcoef)), int(nsteps),
+                                float(dt), int(record_every), nG, _ptr(sigma), _ptr(q), _ptr(p),
+                                _ptr(ps), _ptr(dps), float(eps), float(kappa), float(W),
+                                xr.shape[0], _ptr(xr), _ptr(out), _ptr(dout),
+                                int(nthreads or default_threads()))
+    assert rc == 0, "orc_traces_tangent failed (%d)" % rc
+    return out[..., 0] + 1j * out[..., 1], dout[..., 0] + 1j * dout[..., 1]
+
+
+def frozen_set_traces_tangent(grid: Grid, coef, dcoef, f0, f1, eps, stride, box, keys, nsteps, dt,
+                              record_every, kappa, xr, nthreads=None):
+    """frozen_set_traces() and its directional derivative along dcoef (a change of the
+    velocity coefficients): the rays and amplitudes through the dual-number RK4, the
+    weights psi+- through c(q) in the branch split. Returns (traces, d traces), complex
+    [nrec][nrx] each; the real parts are the recorded field and its derivative."""
+    sigma, qidx, pidx = keys
+    rows, inv = np.unique(qidx, return_inverse=True)
+    psi0 = fbi(grid, f0, eps, stride, box, q_subset=rows)
+    psi1 = fbi(grid, f1, eps, stride, box, q_subset=rows)
+    plus, minus, _ = branch_split(grid, coef, eps, stride, box, psi0, psi1, q_subset=rows)
+    dplus, dminus = branch_split_tangent(grid, coef, dcoef, eps, stride, box, psi1, q_subset=rows)
+    pos = np.asarray(sigma) > 0
+    psi = np.where(pos, plus[inv, pidx], minus[inv, pidx])
+    dpsi = np.where(pos, dplus[inv, pidx], dminus[inv, pidx])
+    qpts = q_points(grid, stride)[qidx]
+    ppts = p_points(grid, eps, box)[pidx]
+    W = quadrature_weight(grid, eps, stride, box)
+    return traces_tangent(grid, coef, dcoef, nsteps, dt, record_every, sigma, qpts, ppts, psi, dpsi,
+                          eps, kappa, W, xr, nthreads)
 
 
 # ---------------------------------------------------------------------------
