@@ -13,6 +13,11 @@ and of the rays behind it).
 The set of Gaussians is the one selected by the forward call (held fixed for the
 derivative). Velocity and outputs are float64 CUDA tensors; PyTorch only supplies memory
 and the stream.
+
+The forward's plan (its device memory holds the checkpoints the backward needs) lives
+until the backward has run, or until the autograd graph that holds it is freed (the
+plan's finaliser destroys it); a forward that cannot be differentiated (grad mode off,
+or a velocity that does not require grad) destroys it at once.
 """
 
 from __future__ import annotations
@@ -26,7 +31,7 @@ from . import fga as F
 class FGATraces(torch.autograd.Function):
     @staticmethod
     def forward(ctx, velocity, prob, receivers, record_every, precision=F.FGA_FP64,
-                integrate_exited=False, interp=F.FGA_BSPLINE_APPROX):
+                integrate_exited=False, interp=F.FGA_BSPLINE_APPROX, keep_plan=True):
         plan = F.plan_from_problem(prob, velocity=velocity.detach().contiguous(),
                                    stream=torch.cuda.current_stream().cuda_stream,
                                    precision=precision, integrate_exited=integrate_exited,
@@ -40,6 +45,9 @@ class FGATraces(torch.autograd.Function):
         out = torch.empty((len(prob.shots), nrec, len(receivers)), dtype=torch.float64,
                           device=velocity.device)
         plan.traces(out)
+        if not keep_plan:
+            plan.close()
+            plan = None
         ctx.plan = plan
         ctx.shape = velocity.shape
         return out
@@ -49,13 +57,18 @@ class FGATraces(torch.autograd.Function):
         grad = torch.empty(ctx.shape, dtype=torch.float64, device=grad_out.device)
         ctx.plan.grad(grad_out.contiguous(), grad)
         ctx.plan.close()
-        return grad, None, None, None, None, None, None
+        ctx.plan = None
+        return grad, None, None, None, None, None, None, None
+
+
+def _differentiable(velocity):
+    return torch.is_grad_enabled() and velocity.requires_grad
 
 
 def traces(velocity, prob, receivers, record_every, **kw):
     return FGATraces.apply(velocity, prob, receivers, record_every,
                            kw.get("precision", F.FGA_FP64), kw.get("integrate_exited", False),
-                           kw.get("interp", F.FGA_BSPLINE_APPROX))
+                           kw.get("interp", F.FGA_BSPLINE_APPROX), _differentiable(velocity))
 
 
 def grid_receivers(prob):
@@ -74,7 +87,7 @@ def grid_receivers(prob):
 class FGAField(torch.autograd.Function):
     @staticmethod
     def forward(ctx, velocity, prob, precision=F.FGA_FP64, integrate_exited=False,
-                interp=F.FGA_BSPLINE_APPROX):
+                interp=F.FGA_BSPLINE_APPROX, keep_plan=True):
         plan = F.plan_from_problem(prob, velocity=velocity.detach().contiguous(),
                                    stream=torch.cuda.current_stream().cuda_stream,
                                    precision=precision, integrate_exited=integrate_exited,
@@ -88,6 +101,9 @@ class FGAField(torch.autograd.Function):
         ns = len(prob.shots)
         tr = torch.empty((ns, 2, xr.shape[0]), dtype=torch.float64, device=velocity.device)
         plan.traces(tr)
+        if not keep_plan:
+            plan.close()
+            plan = None
         ctx.plan = plan
         ctx.shape = velocity.shape
         ctx.ns, ctx.npts = ns, xr.shape[0]
@@ -100,7 +116,8 @@ class FGAField(torch.autograd.Function):
         grad = torch.empty(ctx.shape, dtype=torch.float64, device=grad_out.device)
         ctx.plan.grad(res, grad)
         ctx.plan.close()
-        return grad, None, None, None, None
+        ctx.plan = None
+        return grad, None, None, None, None, None
 
 
 def field(velocity, prob, **kw):
@@ -108,4 +125,4 @@ def field(velocity, prob, **kw):
     axes)."""
     return FGAField.apply(velocity, prob, kw.get("precision", F.FGA_FP64),
                           kw.get("integrate_exited", False),
-                          kw.get("interp", F.FGA_BSPLINE_APPROX))
+                          kw.get("interp", F.FGA_BSPLINE_APPROX), _differentiable(velocity))
