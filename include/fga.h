@@ -57,10 +57,12 @@ typedef enum {
 
 typedef enum {
   FGA_FP64 = 0,         /* every step in FP64 */
-  FGA_MIXED_TF32X3 = 1, /* reconstruction on the tensor cores: factors split into a TF32
-                           head and tail, hi*hi + hi*lo + lo*hi accumulated in FP32, phase
-                           anchored in FP64; FBI, rays and the final sum stay FP64.
-                           2D grids with open axes only. */
+  FGA_MIXED_TF32X3 = 1, /* the two contractions on the tensor cores, operands split into a
+                           TF32 head and tail, hi*hi + hi*lo + lo*hi accumulated in FP32:
+                           stage 2 of the FBI (the branch split in FP32 on its
+                           accumulators) and the reconstruction (phase anchored in FP64).
+                           Stage 1 of the FBI, the selection, the rays and the final sum
+                           over segments stay FP64. 2D grids with open axes only. */
   FGA_MIXED_BF16X3 = 2  /* reserved (rejected by fga_plan) */
 } fga_precision;
 
@@ -305,11 +307,15 @@ fga_status fga_stage_times(fga_plan_t plan, double* ms5, int64_t* launches);
  * The call allocates nothing (no cudaMalloc, cudaFree or allocating library
  * routine) and waits for its stream before returning (it reads a status word).
  * Its first call on a device looks up the array's device address on that
- * device; make that first call before any stream capture on the device.
+ * device; make that first call before any stream capture on the device. The
+ * address is kept for the life of the process: after a cudaDeviceReset of that
+ * device the kept address is stale, so do not call this entry point again in a
+ * process that has reset the device.
  * Every call uses the same array and leaves its contents behind (the call
  * clears what must start at zero): calls that overlap on the GPU -- on two
  * streams, or from two host threads -- race on it and must be serialised.
- * Errors: FGA_ERR_INVALID (arguments, host pointers), FGA_ERR_CAPACITY,
+ * Errors: FGA_ERR_INVALID (arguments, host pointers, pointers to another GPU's
+ * memory), FGA_ERR_CAPACITY,
  * FGA_ERR_CUDA; the message is returned by fga_last_error(NULL). */
 fga_status fga_reconstruct_static(int dim, const int64_t* n, const double* h, const double* origin,
                                   const int* periodic, double eps, double kappa, int64_t nG,
@@ -328,6 +334,16 @@ fga_status fga_reconstruct_static(int dim, const int64_t* n, const double* h, co
  * dim 1..3, n[k] >= 4. Errors: FGA_ERR_INVALID (message via fga_last_error(NULL)). */
 fga_status fga_spline_prefilter(int dim, const int64_t* n, const int* periodic,
                                 const double* samples, double* coef);
+
+/* Measured fused multiply-add throughput of the current GPU (no counterpart in the
+ * paper: the roofline denominator of the FP64-bound kernels). bits = 64 (DFMA) or 32
+ * (FFMA); each of 8 blocks of 256 threads per SM runs 8 independent FMA chains for
+ * iters x 16 rounds, timed with CUDA events on the legacy default stream after one
+ * warm-up launch (the call synchronises the device's default stream and allocates
+ * 64 KiB for the duration of the call). tflops (host) = 2 flop per FMA / time;
+ * ms (host) = the timed launch. Errors: FGA_ERR_INVALID, FGA_ERR_CUDA (message via
+ * fga_last_error(NULL)). */
+fga_status fga_fma_peak(int bits, int iters, double* tflops, double* ms);
 
 #ifdef __cplusplus
 }

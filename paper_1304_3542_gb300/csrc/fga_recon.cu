@@ -695,13 +695,21 @@ fga_status static_fail(fga_status st, const std::string& msg) {
   return st;
 }
 
+// True for managed memory and for device memory of the current device (memory of
+// another GPU would be reached without peer access by the kernels launched here).
 bool device_pointer(const void* ptr) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
   cudaPointerAttributes a;
   if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) {
     cudaGetLastError();
     return false;
   }
-  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+  if (a.type == cudaMemoryTypeManaged) return true;
+  return a.type == cudaMemoryTypeDevice && a.device == dev;
 }
 
 }  // namespace
@@ -720,7 +728,7 @@ extern "C" fga_status fga_reconstruct_static(int dim, const int64_t* n, const do
     return static_fail(FGA_ERR_INVALID, "nG must be in [0, 2^31 - 1]");
   if (nG > 0 && (!qp || !coef)) return static_fail(FGA_ERR_INVALID, "qp and coef must not be NULL");
   if (!device_pointer(u) || (nG > 0 && (!device_pointer(qp) || !device_pointer(coef))))
-    return static_fail(FGA_ERR_INVALID, "qp, coef and u must be device pointers");
+    return static_fail(FGA_ERR_INVALID, "qp, coef and u must be device pointers of the current device");
   cudaStream_t st = (cudaStream_t)stream;
   GridDev gd;
   std::memset(&gd, 0, sizeof(gd));

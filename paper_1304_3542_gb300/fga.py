@@ -122,6 +122,8 @@ def load(build_if_missing: bool = True):
     L.fga_reconstruct_static.restype = ci
     L.fga_spline_prefilter.argtypes = [ci, P, P, P, P]
     L.fga_spline_prefilter.restype = ci
+    L.fga_fma_peak.argtypes = [ci, ci, P, P]
+    L.fga_fma_peak.restype = ci
     for name in ("fga_plan", "fga_decompose", "fga_propagate", "fga_reconstruct", "fga_sync",
                  "fga_destroy", "fga_shot_grid", "fga_psi", "fga_gaussians", "fga_state",
                  "fga_stage_times"):
@@ -353,11 +355,19 @@ def reconstruct_static(dim: int, n: Sequence[int], h: Sequence[float], origin: S
                        stream: Optional[int] = None):
     """fga_reconstruct_static: the reconstruction without any device allocation.
     qp: device float64 [2*dim][nG] (Q rows then P rows); coef: device float64 [nG][2];
-    u: device float64 grid, overwritten."""
+    u: device float64 grid, overwritten. The C side cannot see buffer sizes, so every
+    size is checked here before the call."""
     L = load()
+    npts = int(np.prod(np.asarray(n, dtype=np.int64)))
     nG = 0
     if qp is not None:
-        nG = (qp.numel() if hasattr(qp, "numel") else qp.size) // (2 * dim)
+        nq = qp.numel() if hasattr(qp, "numel") else qp.size
+        if nq % (2 * dim) != 0:
+            raise ValueError("qp has %d values, not a multiple of 2*dim = %d" % (nq, 2 * dim))
+        nG = nq // (2 * dim)
+        _check_f64(qp, 2 * dim * nG, "qp")
+        _check_f64(coef, 2 * nG, "coef")
+    _check_f64(u, npts, "u")
     n_ = np.ascontiguousarray(n, dtype=np.int64)
     h_ = np.ascontiguousarray(h, dtype=np.float64)
     o_ = np.ascontiguousarray(origin, dtype=np.float64)
@@ -383,6 +393,17 @@ def spline_prefilter(samples: np.ndarray, periodic: Sequence[bool]) -> np.ndarra
     if st != FGA_OK:
         raise FGAError(st, "fga_spline_prefilter", L.fga_last_error(None).decode())
     return out
+
+
+def fma_peak(bits: int = 64, iters: int = 4096):
+    """fga_fma_peak: measured FMA throughput of the current GPU, (TFLOP/s, ms)."""
+    L = load()
+    tf = ctypes.c_double(0.0)
+    ms = ctypes.c_double(0.0)
+    st = L.fga_fma_peak(int(bits), int(iters), ctypes.addressof(tf), ctypes.addressof(ms))
+    if st != FGA_OK:
+        raise FGAError(st, "fga_fma_peak", L.fga_last_error(None).decode())
+    return tf.value, ms.value
 
 
 def plan_from_problem(prob, velocity=None, stream=None, precision: int = FGA_FP64,

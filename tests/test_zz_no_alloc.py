@@ -84,10 +84,34 @@ def test_static_reconstruction_rejects_oversized_grids():
     import torch
 
     n = (64 * 129, 64 * 128)  # 16512 tiles of 64 x 64: more than the fixed array holds
-    u = torch.zeros(1, dtype=torch.float64, device="cuda")
+    # a buffer of the grid's full size (541 MB), so that no order of the checks in the
+    # library can make the call touch memory outside it
+    u = torch.zeros(n, dtype=torch.float64, device="cuda")
     qp = torch.zeros((4, 1), dtype=torch.float64, device="cuda")
     cf = torch.zeros((1, 2), dtype=torch.float64, device="cuda")
     with pytest.raises(F.FGAError) as ei:
         F.reconstruct_static(2, n, (0.01, 0.01), (0.0, 0.0), (False, False), 1e-3, 6.0, qp, cf, u)
     assert ei.value.status == 7  # FGA_ERR_CAPACITY
     assert "tiles" in str(ei.value)
+    del u
+    torch.cuda.empty_cache()
+
+
+def test_static_reconstruction_wrapper_checks_buffer_sizes():
+    """The Python binding refuses buffers whose sizes do not match (the C entry point
+    cannot see sizes); nothing is launched."""
+    import torch
+
+    n = (64, 64)
+    qp = torch.zeros((4, 3), dtype=torch.float64, device="cuda")
+    cf = torch.zeros((3, 2), dtype=torch.float64, device="cuda")
+    with pytest.raises(ValueError):
+        F.reconstruct_static(2, n, (0.01, 0.01), (0.0, 0.0), (False, False), 1e-3, 6.0, qp, cf,
+                             torch.zeros(64 * 63, dtype=torch.float64, device="cuda"))
+    with pytest.raises(ValueError):
+        F.reconstruct_static(2, n, (0.01, 0.01), (0.0, 0.0), (False, False), 1e-3, 6.0, qp,
+                             cf[:2], torch.zeros(n, dtype=torch.float64, device="cuda"))
+    with pytest.raises(ValueError):
+        F.reconstruct_static(2, n, (0.01, 0.01), (0.0, 0.0), (False, False), 1e-3, 6.0,
+                             qp.reshape(-1)[:11], cf, torch.zeros(n, dtype=torch.float64,
+                                                                  device="cuda"))
