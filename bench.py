@@ -265,6 +265,9 @@ def run_ours(args, rank, world, local_rank):
             t64.append(e0.elapsed_time(e1) / 1e3)
         fp64_value = evals / statistics.mean(t64)
         ref.close()
+    # the FMA pipes measured on this GPU in this run (roofline denominators' check)
+    fp64_meas, _ = F.fma_peak(64, 4096)
+    fp32_meas, _ = F.fma_peak(32, 65536)
     ray_s = statistics.mean(ray_ms) / 1e3
     steps_done = statistics.mean(ray_steps)
     ray_flops = FLOPS_PER_RAY_STEP_2D * steps_done
@@ -297,9 +300,9 @@ def run_ours(args, rank, world, local_rank):
             "ray_steps_all_to_T": G * prob.nsteps,
             "evals_per_step_both_branches": evals,
             "precision": ("fp64" if precision == F.FGA_FP64 else
-                          "mixed: FP64 FBI and rays; reconstruction on tensor cores "
-                          "(TF32 head/tail factors, 3 products, FP32 accumulate, FP64 phase "
-                          "anchors and segment sums)"),
+                          "mixed: FBI stage 2 and the reconstruction on tensor cores "
+                          "(TF32 head/tail operands, 3 products, FP32 accumulate; FP64 phase "
+                          "anchors and segment sums); FBI stage 1, selection and rays FP64"),
             "fp64_path_value": fp64_value,
             "tuning": {"ray_blocks_per_sm": tuning[0], "gather_segment": tuning[1],
                        "ray_register_variant": tuning[2],
@@ -320,6 +323,10 @@ def run_ours(args, rank, world, local_rank):
             "traffic": ncu_traffic(),
             "flops_per_launch": ray_flops,
             "peak_source": "FP64 from unit counts and clock (152 SM x 2 DFMA/clk x 2.07 GHz)",
+            "peak_measured": {"fp64_tflops": fp64_meas, "fp32_tflops": fp32_meas,
+                              "frac_of_measured_fp64": achieved / fp64_meas,
+                              "by": "fga_fma_peak (csrc/fga_peaks.cu): 8 FMA chains per "
+                                    "thread, 8 x 256 threads per SM, CUDA events, this run"},
         },
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 2 * 8 * npts,
                 "d2h_bytes_per_step": 8 * npts},

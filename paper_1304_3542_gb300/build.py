@@ -19,7 +19,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libfga.so")
 
 SOURCES = ["fga_api.cu", "fga_fbi.cu", "fga_select.cu", "fga_rays.cu", "fga_rays_dd.cu",
-           "fga_recon.cu", "fga_recon_tc.cu", "fga_adjoint.cu"]
+           "fga_recon.cu", "fga_recon_tc.cu", "fga_adjoint.cu", "fga_peaks.cu"]
 HEADERS = ["fga_internal.cuh", "fga_medium.cuh", "fga_tiles.cuh", "fga_tc.cuh",
            "fga_ray_rhs.cuh", "fga_ray_vjp.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
