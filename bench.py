@@ -43,11 +43,13 @@ METRIC = "FGA Gaussian·gridpoint evals/s and rel-L2 err; mixed-prec vs FP64, 1 
 UNIT = "evals/s"
 L2_FLUSH_BYTES = 256 << 20
 # FP64 operations of one RK4 ray step in 2D, counted from the source of the ray
-# kernel (add/sub/mul/div/rsqrt/floor = 1, fma = 2): 4 right-hand sides of 322
-# (medium from the per-cell polynomial table 90: cell and offsets 10, four rows in z
-# 48, combination in x 32; ray and dynamic-ray algebra 145, tr(Z^-1 dZ/dt) with
-# da/dt 81, dS/dt 6) plus 322 for the stage combinations of the 23 state values.
-FLOPS_PER_RAY_STEP_2D = 1610
+# kernel (add/sub/mul/rsqrt/reciprocal = 1, fma = 2; conversions and compares not
+# counted): 4 right-hand sides of 285 (medium from the per-cell polynomial table 86:
+# cell offsets 8, four rows in z by Horner with derivatives 48, combination in x 30;
+# |P|, n, dQ/dt, dP/dt and -|P| K 18; dynamic rays 96; Z, dZ/dt and tr(adj Z dZ/dt),
+# det Z 60; da/dt 20; dS/dt 5) plus 322 for the stage combinations of the 23 state
+# values (7 fma each).
+FLOPS_PER_RAY_STEP_2D = 1462
 # FP64 peak from the unit counts and clocks: 152 SMs x 2 DFMA/clk/SM x 2 flop x 2.07 GHz
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 

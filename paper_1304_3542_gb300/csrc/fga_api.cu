@@ -278,6 +278,7 @@ fga_status fga_plan(const fga_config* cfg, const double* velocity, void* stream,
     gd.h[k] = cfg->h[k];
     gd.o[k] = cfg->origin[k];
     gd.inv_h[k] = 1.0 / cfg->h[k];
+    gd.mo[k] = -cfg->origin[k] * gd.inv_h[k];
     gd.periodic[k] = cfg->periodic[k] ? 1 : 0;
     gd.L[k] = gd.periodic[k] ? (double)cfg->n[k] * cfg->h[k] : 0.0;
     gd.npts *= cfg->n[k];

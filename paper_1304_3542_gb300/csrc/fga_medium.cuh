@@ -235,24 +235,41 @@ __device__ __forceinline__ void medium_cell(const GridDev& gd, const double* __r
   }
 }
 
-// Table cell (index + 1) and physical offset of x along axis k.
+// Table cell (index + 1) and physical offset of x along axis k. On an open axis the
+// cell index is one rounding-down conversion of u = (x - o)/h, clamped to the table's
+// cells -1 .. n in integer arithmetic; where it was clamped the offset is 0 (below cell
+// -1 the spline is constant along the axis and cell -1 is evaluated at its left edge;
+// cell n is constant, all its derivative coefficients being exact zeros). A position a
+// rounding error below a cell boundary evaluates the neighbouring cell's polynomial at
+// offset h: the spline is C2 there, so the two agree to within rounding.
 __device__ __forceinline__ int64_t medium_cell_of(const GridDev& gd, int k, double x, double& off) {
-  const double u = (x - gd.o[k]) * gd.inv_h[k];
-  double fl = floor(u);
-  off = (u - fl) * gd.h[k];
   if (gd.periodic[k]) {
+    const double u = (x - gd.o[k]) * gd.inv_h[k];
+    double fl = floor(u);
+    off = (u - fl) * gd.h[k];
     int64_t i = (int64_t)fl % gd.n[k];
     return (i < 0 ? i + gd.n[k] : i) + 1;
   }
-  if (fl < -1.0) {
-    off = 0.0;
-    return 0;
-  }
-  if (fl > (double)gd.n[k] - 1.0) {
-    off = 0.0;
-    return gd.n[k] + 1;
-  }
-  return (int64_t)fl + 1;
+  const double u = fma(x, gd.inv_h[k], gd.mo[k]);
+  const int i = __double2int_rd(u);
+  const int ic = min(max(i, -1), (int)gd.n[k]);
+  off = (u - (double)ic) * gd.h[k];
+  if (i != ic) off = 0.0;
+  return (int64_t)ic + 1;
+}
+
+// Value, first derivative and half the second derivative of the cubic
+// a0 + a1 t + a2 t^2 + a3 t^3 at t by Horner's scheme with derivatives (six fused
+// multiply-adds).
+__device__ __forceinline__ void horner3(double a0, double a1, double a2, double a3, double t,
+                                        double& v, double& d1, double& d2h) {
+  double w = fma(a3, t, a2);
+  double d = fma(a3, t, w);
+  w = fma(w, t, a1);
+  d2h = fma(a3, t, d);
+  d = fma(d, t, w);
+  v = fma(w, t, a0);
+  d1 = d;
 }
 
 // c, grad c, Hessian of c at x from the table gd.tab.
@@ -265,35 +282,34 @@ __device__ __forceinline__ void medium_eval_tab(const GridDev& gd, const double*
     const int64_t c0 = medium_cell_of(gd, 0, x[0], t);
     const double2* cell = reinterpret_cast<const double2*>(gd.tab) + c0 * 2;
     const double2 p01 = __ldg(cell), p23 = __ldg(cell + 1);
-    const double t3 = 3.0 * p23.y;
-    const double hh = fma(t3, t, p23.x);  // c''/2
-    m.c = fma(fma(fma(p23.y, t, p23.x), t, p01.y), t, p01.x);
-    m.g[0] = fma(t, hh + p23.x, p01.y);
+    double hh;
+    horner3(p01.x, p01.y, p23.x, p23.y, t, m.c, m.g[0], hh);
     m.K[0][0] = 2.0 * hh;
   } else {
     double tx, tz;
     const int64_t cx = medium_cell_of(gd, 0, x[0], tx);
     const int64_t cz = medium_cell_of(gd, 1, x[1], tz);
     const double2* cell = reinterpret_cast<const double2*>(gd.tab) + (cx * (gd.n[1] + 2) + cz) * 8;
+    // row k (power k of tx): its cubic in tz, with d/dz and (d2/dz2)/2
     double r[4], rz[4], hz[4];
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
       const double2 a01 = __ldg(cell + 2 * k), a23 = __ldg(cell + 2 * k + 1);
-      const double t3 = 3.0 * a23.y;
-      r[k] = fma(fma(fma(a23.y, tz, a23.x), tz, a01.y), tz, a01.x);
-      hz[k] = fma(t3, tz, a23.x);           // (d2/dz2)/2 of row k
-      rz[k] = fma(tz, hz[k] + a23.x, a01.y);  // d/dz of row k
+      horner3(a01.x, a01.y, a23.x, a23.y, tz, r[k], rz[k], hz[k]);
     }
-    const double T3 = 3.0 * r[3], U3 = 3.0 * rz[3];
-    const double hx = fma(T3, tx, r[2]);
-    const double hxz = fma(U3, tx, rz[2]);
-    m.c = fma(fma(fma(r[3], tx, r[2]), tx, r[1]), tx, r[0]);
-    m.g[0] = fma(tx, hx + r[2], r[1]);
-    m.g[1] = fma(fma(fma(rz[3], tx, rz[2]), tx, rz[1]), tx, rz[0]);
-    m.K[0][0] = 2.0 * hx;
-    m.K[0][1] = fma(tx, hxz + rz[2], rz[1]);
-    m.K[1][0] = m.K[0][1];
-    m.K[1][1] = 2.0 * fma(fma(fma(hz[3], tx, hz[2]), tx, hz[1]), tx, hz[0]);
+    double cxx_h, czz_h;
+    horner3(r[0], r[1], r[2], r[3], tx, m.c, m.g[0], cxx_h);
+    // d/dz and d2/dxdz: value and derivative in tx of the rz cubic
+    double w = fma(rz[3], tx, rz[2]);
+    double d = fma(rz[3], tx, w);
+    w = fma(w, tx, rz[1]);
+    d = fma(d, tx, w);
+    m.g[1] = fma(w, tx, rz[0]);
+    m.K[0][1] = d;
+    m.K[1][0] = d;
+    czz_h = fma(fma(fma(hz[3], tx, hz[2]), tx, hz[1]), tx, hz[0]);
+    m.K[0][0] = 2.0 * cxx_h;
+    m.K[1][1] = 2.0 * czz_h;
   }
 }
 

@@ -24,9 +24,101 @@ __device__ __forceinline__ int64_t work_order(unsigned long long w, int64_t G, u
   return (int64_t)((w * mult) % (unsigned long long)G);
 }
 
+// 1/x for x > 0: the hardware's approximate reciprocal (PTX rcp.approx.ftz.f64) refined
+// by two Newton-Raphson steps r <- r + r (1 - x r), each doubling the correct bits; the
+// result is within a few ulps of 1/x (not correctly rounded, which nothing here needs).
+__device__ __forceinline__ double rcp_nr(double x) {
+  double r;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(x));
+  double e = fma(-x, r, 1.0);
+  r = fma(r, e, r);
+  e = fma(-x, r, 1.0);
+  return fma(r, e, r);
+}
+
+// The right-hand side in 2D with the algebra arranged for fused multiply-adds (the same
+// equations as the generic form below; only the rounding differs):
+//   dQ/dt = (c/|P|) P,  dP/dt = -|P| g,
+//   dA_jk/dt = ((A g)_j - (c/|P|)(B n)_j) n_k + (c/|P|) B_jk,
+//   dB_jk/dt = (A Km)_jk - (B n)_j g_k,  Km = -|P| K  (H_QQ = |P| K),
+//   da/dt = a (n.g + tr(adj(Z) dZ/dt) conj(det Z)/(2 |det Z|^2)),  dS/dt = P.dQ/dt - c|P|.
+__device__ __forceinline__ bool rhs2(const GridDev& gd, const double* y, double* k) {
+  using Lo = Layout<2>;
+  Med m;
+  medium_eval_tab<2>(gd, y + Lo::Q, m);
+  const double p0 = y[Lo::P], p1 = y[Lo::P + 1];
+  const double pn2 = fma(p0, p0, p1 * p1);
+  const double rinv = rsqrt(pn2);
+  const double pn = pn2 * rinv;
+  const double n0 = p0 * rinv, n1 = p1 * rinv;
+  const double cop = m.c * rinv;  // c/|P|
+  const double g0 = m.g[0], g1 = m.g[1];
+  k[Lo::Q] = cop * p0;
+  k[Lo::Q + 1] = cop * p1;
+  k[Lo::P] = -pn * g0;
+  k[Lo::P + 1] = -pn * g1;
+  const double ng = fma(n0, g0, n1 * g1);
+  const double km00 = -pn * m.K[0][0], km01 = -pn * m.K[0][1], km11 = -pn * m.K[1][1];
+#pragma unroll
+  for (int j = 0; j < 2; ++j) {
+    const double ar0 = y[Lo::AR + 2 * j], ar1 = y[Lo::AR + 2 * j + 1];
+    const double ai0 = y[Lo::AI + 2 * j], ai1 = y[Lo::AI + 2 * j + 1];
+    const double br0 = y[Lo::BR + 2 * j], br1 = y[Lo::BR + 2 * j + 1];
+    const double bi0 = y[Lo::BI + 2 * j], bi1 = y[Lo::BI + 2 * j + 1];
+    const double bnr = fma(br0, n0, br1 * n1), bni = fma(bi0, n0, bi1 * n1);
+    const double ur = fma(-cop, bnr, fma(ar0, g0, ar1 * g1));
+    const double ui = fma(-cop, bni, fma(ai0, g0, ai1 * g1));
+    k[Lo::AR + 2 * j] = fma(ur, n0, cop * br0);
+    k[Lo::AR + 2 * j + 1] = fma(ur, n1, cop * br1);
+    k[Lo::AI + 2 * j] = fma(ui, n0, cop * bi0);
+    k[Lo::AI + 2 * j + 1] = fma(ui, n1, cop * bi1);
+    k[Lo::BR + 2 * j] = fma(ar0, km00, fma(ar1, km01, -bnr * g0));
+    k[Lo::BR + 2 * j + 1] = fma(ar0, km01, fma(ar1, km11, -bnr * g1));
+    k[Lo::BI + 2 * j] = fma(ai0, km00, fma(ai1, km01, -bni * g0));
+    k[Lo::BI + 2 * j + 1] = fma(ai0, km01, fma(ai1, km11, -bni * g1));
+  }
+  // Z = A + iB, dZ/dt; tr(adj(Z) dZ) = Z11 dZ00 - Z01 dZ10 - Z10 dZ01 + Z00 dZ11
+  double zr[4], zi[4], dzr[4], dzi[4];
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    zr[e] = y[Lo::AR + e] - y[Lo::BI + e];
+    zi[e] = y[Lo::AI + e] + y[Lo::BR + e];
+    dzr[e] = k[Lo::AR + e] - k[Lo::BI + e];
+    dzi[e] = k[Lo::AI + e] + k[Lo::BR + e];
+  }
+  double trr = zr[3] * dzr[0];
+  trr = fma(-zi[3], dzi[0], trr);
+  trr = fma(-zr[1], dzr[2], trr);
+  trr = fma(zi[1], dzi[2], trr);
+  trr = fma(-zr[2], dzr[1], trr);
+  trr = fma(zi[2], dzi[1], trr);
+  trr = fma(zr[0], dzr[3], trr);
+  trr = fma(-zi[0], dzi[3], trr);
+  double tri = zr[3] * dzi[0];
+  tri = fma(zi[3], dzr[0], tri);
+  tri = fma(-zr[1], dzi[2], tri);
+  tri = fma(-zi[1], dzr[2], tri);
+  tri = fma(-zr[2], dzi[1], tri);
+  tri = fma(-zi[2], dzr[1], tri);
+  tri = fma(zr[0], dzi[3], tri);
+  tri = fma(zi[0], dzr[3], tri);
+  const double detr = fma(zr[0], zr[3], fma(-zi[0], zi[3], fma(-zr[1], zr[2], zi[1] * zi[2])));
+  const double deti = fma(zr[0], zi[3], fma(zi[0], zr[3], fma(-zr[1], zi[2], -zi[1] * zr[2])));
+  const double dd = fma(detr, detr, deti * deti);
+  const double ih = 0.5 * rcp_nr(dd);  // 1/(2 |det Z|^2)
+  const double qr = fma(trr, detr, tri * deti) * ih, qi = fma(tri, detr, -trr * deti) * ih;
+  const double fr = ng + qr;
+  const double ar = y[Lo::aR], ai = y[Lo::aI];
+  k[Lo::aR] = fma(ar, fr, -ai * qi);
+  k[Lo::aI] = fma(ar, qi, ai * fr);
+  k[Lo::S] = fma(-m.c, pn, fma(p0, k[Lo::Q], p1 * k[Lo::Q + 1]));
+  return pn2 > 0.0 && dd > 0.0;
+}
+
 // The medium comes from the per-cell polynomial table gd.tab.
 template <int D>
 __device__ __forceinline__ bool rhs(const GridDev& gd, const double* y, double* k) {
+  if constexpr (D == 2) return rhs2(gd, y, k);
   using Lo = Layout<D>;
   Med m;
   medium_eval_tab<D>(gd, y + Lo::Q, m);
