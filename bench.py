@@ -43,12 +43,12 @@ METRIC = "FGA Gaussian·gridpoint evals/s and rel-L2 err; mixed-prec vs FP64, 1 
 UNIT = "evals/s"
 L2_FLUSH_BYTES = 256 << 20
 # FP64 operations of one RK4 ray step in 2D, counted from the source of the ray
-# kernel (add/sub/mul/rsqrt/reciprocal = 1, fma = 2; conversions and compares not
-# counted): 4 right-hand sides of 285 (medium from the per-cell polynomial table 86:
-# cell offsets 8, four rows in z by Horner with derivatives 48, combination in x 30;
-# |P|, n, dQ/dt, dP/dt and -|P| K 18; dynamic rays 96; Z, dZ/dt and tr(adj Z dZ/dt),
-# det Z 60; da/dt 20; dS/dt 5) plus 322 for the stage combinations of the 23 state
-# values (7 fma each).
+# kernel (add/sub/mul/rsqrt/reciprocal = 1, fma = 2; conversions, compares and the
+# Newton steps that refine the hardware's rsqrt and reciprocal not counted): 4
+# right-hand sides of 285 (medium from the per-cell polynomial table 86: cell offsets 8,
+# four rows in z by Horner with derivatives 48, combination in x 30; |P|, n, dQ/dt,
+# dP/dt and -|P| K 18; dynamic rays 96; Z, dZ/dt, tr(adj Z dZ/dt) and det Z 60; da/dt
+# 20; dS/dt 5) plus 322 for the stage combinations of the 23 state values (7 fma each).
 FLOPS_PER_RAY_STEP_2D = 1462
 # FP64 peak from the unit counts and clocks: 152 SMs x 2 DFMA/clk/SM x 2 flop x 2.07 GHz
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
@@ -385,31 +385,24 @@ def oracle_sample(prob, n_sample, nthreads):
     return est, desc, evals, t_dec + t_prop + t_rec
 
 
-def run_batch(args, rank, world, local_rank):
-    """The batched-shots workload (64 shots on the layered model, per-shot frequency and
-    eps): this rank's shots (contiguous block, no collective) as one plan per stage in the
-    mixed precision with the CUDA-graph replay, against the same shots run in FP64 in one
-    batched plan and in FP64 one plan per shot. One untimed pass, then args.steps timed
-    passes of each form; the speedups of batching and of precision are reported apart."""
+def measure_batch(prob, dev, reps):
+    """The batched forms on the shots of prob: mixed precision with all shots in one plan
+    and decompose + propagate + reconstruct replayed as one CUDA graph (fga_run_pipeline),
+    against FP64 with all shots in one plan (eager) and FP64 one plan per shot. One
+    untimed pass of each form (it captures the graph), then reps timed passes; CUDA
+    events on the plans' stream, a 256 MiB L2 flush between passes."""
     import dataclasses
 
     import torch
 
     from paper_1304_3542_gb300 import fga as F
-    from paper_1304_3542_gb300 import workloads as WL
-    from paper_1304_3542_gb300.shards import max_over_ranks, shard_shots
 
-    torch.cuda.set_device(local_rank)
-    dev = torch.device("cuda", local_rank)
-    full = WL.layered_batch()
-    mine = shard_shots(len(full.shots), rank, world)
-    prob = dataclasses.replace(full, shots=[full.shots[i] for i in mine])
     stream = torch.cuda.Stream(dev)
     u0, u1 = F.stacked_initial_data(prob)
     d_u0, d_u1 = torch.from_numpy(u0).to(dev), torch.from_numpy(u1).to(dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
 
-    def timed(fn, reps):
+    def timed(fn):
         out = []
         for i in range(reps):
             flush.fill_(float(i))
@@ -422,25 +415,23 @@ def run_batch(args, rank, world, local_rank):
             out.append(e0.elapsed_time(e1) / 1e3)
         return statistics.mean(out)
 
+    ns = len(prob.shots)
     with torch.cuda.stream(stream):
-        # mixed, batched, graph replay of propagate + reconstruct
         mixed = F.plan_from_problem(prob, stream=stream.cuda_stream, precision=F.FGA_MIXED_TF32X3)
-        d_mx = torch.zeros((len(prob.shots),) + prob.n, dtype=torch.float64, device=dev)
+        d_mx = torch.zeros((ns,) + prob.n, dtype=torch.float64, device=dev)
         mixed.decompose(d_u0, d_u1)
         tuning = mixed.autotune(d_mx)
-        counts = [mixed.count(s) for s in range(len(prob.shots))]
+        mixed.run_pipeline(d_u0, d_u1, d_mx)  # eager sizing pass and capture
+        mixed.sync()
+        counts = [mixed.count(s) for s in range(ns)]
         evals = 0.0
-        for s in range(len(prob.shots)):
+        for s in range(ns):
             evals += 2.0 * window_evals(prob, mixed.state(s)["Q"], prob.shots[s].eps)
-
-        def mixed_step():
-            mixed.decompose(d_u0, d_u1)
-            mixed.run_graph(d_mx)
-
-        mixed_step()
-        t_mixed = timed(mixed_step, args.steps)
+        _, l0 = mixed.stage_times()
+        t_mixed = timed(lambda: mixed.run_pipeline(d_u0, d_u1, d_mx))
+        mixed.sync()
+        _, l1 = mixed.stage_times()
         mixed.close()  # free its buffers before the FP64 forms
-        # FP64, batched
         b64 = F.plan_from_problem(prob, stream=stream.cuda_stream, precision=F.FGA_FP64)
         d_64 = torch.zeros_like(d_mx)
         b64.decompose(d_u0, d_u1)
@@ -451,12 +442,11 @@ def run_batch(args, rank, world, local_rank):
             b64.propagate()
             b64.reconstruct(d_64)
 
-        t_b64 = timed(b64_step, args.steps)
+        t_b64 = timed(b64_step)
         rel = float((d_mx - d_64).norm() / d_64.norm())
         b64.close()
-        # FP64, one plan per shot, shots in turn
         singles = []
-        for s in range(len(prob.shots)):
+        for s in range(ns):
             one = dataclasses.replace(prob, shots=[prob.shots[s]])
             singles.append(F.plan_from_problem(one, stream=stream.cuda_stream,
                                                precision=F.FGA_FP64))
@@ -468,15 +458,57 @@ def run_batch(args, rank, world, local_rank):
                 pl.reconstruct(d_64[s:s + 1])
 
         per_shot_step()
-        t_single = timed(per_shot_step, args.steps)
+        t_single = timed(per_shot_step)
         for pl in singles:
             pl.close()
-    t_mixed_all = max_over_ranks(t_mixed)
-    evals_all = evals
+    return {
+        "evals": evals, "t_mixed": t_mixed, "rel_l2_mixed_vs_fp64": rel,
+        "gaussians_per_shot": {"min": min(counts), "median": statistics.median(counts),
+                               "max": max(counts)},
+        "tuning": {"ray_blocks_per_sm": tuning[0], "gather_segment": tuning[1],
+                   "ray_register_variant": tuning[2]},
+        "kernel_launches_per_replay": int((l1 - l0) // max(reps, 1)),
+        "seconds_per_pass": {"mixed_batched_pipeline_graph": t_mixed, "fp64_batched": t_b64,
+                             "fp64_one_plan_per_shot": t_single},
+        "speedup_batching_fp64": t_single / t_b64,
+        "speedup_precision_batched": t_b64 / t_mixed,
+        "speedup_total_vs_fp64_per_shot": t_single / t_mixed,
+    }
+
+
+def run_batch(args, rank, world, local_rank):
+    """The batched-shots workload (64 shots on the layered model, per-shot frequency and
+    eps): this rank's shots (contiguous block, no collective) in the three forms of
+    measure_batch; value is the mixed pipeline-graph form's evaluations per second."""
+    import dataclasses
+
+    import torch
+
+    from paper_1304_3542_gb300 import workloads as WL
+    from paper_1304_3542_gb300.shards import max_over_ranks, shard_shots
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    full = WL.layered_batch()
+    mine = shard_shots(len(full.shots), rank, world)
+    prob = dataclasses.replace(full, shots=[full.shots[i] for i in mine])
+    m = measure_batch(prob, dev, args.steps)
+    t_mixed_all = max_over_ranks(m["t_mixed"])
+    evals_all = m["evals"]
     if world > 1:
-        t = torch.tensor([evals], dtype=torch.float64, device=dev)
+        t = torch.tensor([m["evals"]], dtype=torch.float64, device=dev)
         torch.distributed.all_reduce(t)
         evals_all = float(t.item())
+    cfg = {
+        "workload": "layered model 737x241 at 12.5 m, 64 shots (x ~ U(1.0, 8.2) km, depth ~ "
+                    "U(0.01, 0.5) km, f ~ U(8, 25) Hz, per-shot eps), T=2 s, dt=1 ms",
+        "shots_this_rank": len(mine),
+        "form": "mixed precision, all shots of the rank in one plan, decompose + propagate + "
+                "reconstruct replayed as one CUDA graph with the counts on the device",
+        "l2": "256 MiB buffer written between timed passes",
+        "parallelism": "shot-parallel, %d rank(s), no collective" % world,
+    }
+    cfg.update({k: v for k, v in m.items() if k not in ("evals", "t_mixed", "rel_l2_mixed_vs_fp64")})
     return {
         "metric": METRIC,
         "value": evals_all / t_mixed_all,
@@ -490,25 +522,8 @@ def run_batch(args, rank, world, local_rank):
         "vs_baseline": None,
         "dtype": "f64+tf32",
         "data": "synthetic (seeded layered model, 64 Ricker-ring shots; no dataset)",
-        "rel_l2_vs_fp64": rel,
-        "config": {
-            "workload": "layered model 737x241 at 12.5 m, 64 shots (x ~ U(1.0, 8.2) km, depth ~ "
-                        "U(0.01, 0.5) km, f ~ U(8, 25) Hz, per-shot eps), T=2 s, dt=1 ms",
-            "shots_this_rank": len(mine),
-            "gaussians_per_shot": {"min": min(counts), "median": statistics.median(counts),
-                                   "max": max(counts)},
-            "tuning": {"ray_blocks_per_sm": tuning[0], "gather_segment": tuning[1],
-                       "ray_register_variant": tuning[2]},
-            "form": "mixed precision, all shots of the rank in one plan, propagate + "
-                    "reconstruct replayed as one CUDA graph",
-            "seconds_per_pass": {"mixed_batched_graph": t_mixed, "fp64_batched": t_b64,
-                                 "fp64_one_plan_per_shot": t_single},
-            "speedup_batching_fp64": t_single / t_b64,
-            "speedup_precision_batched": t_b64 / t_mixed,
-            "speedup_total_vs_fp64_per_shot": t_single / t_mixed,
-            "l2": "256 MiB buffer written between timed passes",
-            "parallelism": "shot-parallel, %d rank(s), no collective" % world,
-        },
+        "rel_l2_vs_fp64": m["rel_l2_mixed_vs_fp64"],
+        "config": cfg,
     }
 
 
@@ -555,6 +570,9 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=512)
+    ap.add_argument("--batch-shots", type=int, default=8,
+                    help="shots of the batched workload timed in the three batched forms "
+                         "for the line's batch sub-record (0: none; N = 1 only)")
     ap.add_argument("--workload", choices=["layered_single", "layered_batch"],
                     default="layered_single",
                     help="layered_batch: the 64-shot batched form against FP64 batched and "
@@ -597,6 +615,20 @@ def main():
             dist.destroy_process_group()
         return
     line, prob, evals = run_ours(args, rank, world, local_rank)
+    if world == 1 and args.batch_shots > 0:
+        import torch
+
+        from paper_1304_3542_gb300 import workloads as WL
+
+        full = WL.layered_batch()
+        sub = full.with_(shots=full.shots[:args.batch_shots])
+        m = measure_batch(sub, torch.device("cuda", local_rank), 1)
+        m["value"] = m.pop("evals") / m["t_mixed"]
+        m["unit"] = UNIT
+        m["shots"] = "the first %d of the 64 shots of the batched workload (layered model, "\
+                     "x ~ U(1.0, 8.2) km, depth ~ U(0.01, 0.5) km, f ~ U(8, 25) Hz, T = 2 s); "\
+                     "one timed pass per form" % args.batch_shots
+        line["batch"] = m
     if rank == 0:
         if world == 1 and not args.no_cpu_baseline:
             cores = os.cpu_count() or 1

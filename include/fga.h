@@ -335,7 +335,51 @@ fga_status fga_reconstruct_static(int dim, const int64_t* n, const double* h, co
 fga_status fga_spline_prefilter(int dim, const int64_t* n, const int* periodic,
                                 const double* samples, double* coef);
 
-/* Measured fused multiply-add throughput of the current GPU (no counterpart in the
+/* The whole method -- fga_decompose, fga_propagate and fga_reconstruct of every shot
+ * -- as one CUDA graph (batching of the Algorithm section's three steps: a captured
+ * sequence of launches, each over all shots, with no host synchronisation and the
+ * Gaussian counts kept on the device). u0, u1: device [nshots][grid] (as
+ * fga_decompose); u_dev: device [nshots][grid], overwritten with Re u (as
+ * fga_reconstruct).
+ * The first call (and any call after an eager fga_decompose, or with other buffers)
+ * runs the three steps eagerly -- that is its result -- to learn each shot's active q
+ * rectangle and counts, sizes the Gaussian list, the tile lists and the binning for
+ * 1.25 x those counts, and captures the graph; later calls replay it and return at
+ * once. In the replay the counts, segment offsets and the total G are computed on the
+ * device and every launch sizes itself from them within those capacities. If later
+ * data need more (more Gaussians, longer tile lists) or give other active q
+ * rectangles (a different support), the replay stays within its buffers, and the next
+ * call that reads the device status (fga_sync, or one with a host output) fails with
+ * FGA_ERR_CAPACITY and marks the plan failed. After a replay fga_count and the other
+ * inspection calls report the replay's counts (they read them back, which waits for
+ * the stream).
+ * Needs a stream other than the legacy default stream, the dynamic-ray Z and no
+ * receivers (FGA_ERR_INVALID otherwise); FGA_ERR_CUDA on a capture failure. */
+fga_status fga_run_pipeline(fga_plan_t plan, const double* u0, const double* u1, double* u_dev);
+
+/* Budget of the bounded waits in the tensor-core kernels (FGA_MIXED_TF32X3: FBI stage 2
+ * and the reconstruction), as polls of the completion barrier of the previous chunk of
+ * MMAs before the CTA gives up (no counterpart in the paper: failure detection of the
+ * library). tries < 0 restores the defaults (2^22 polls, seconds); 0 makes every such
+ * wait give up at once, which exercises the give-up path. A CTA that gives up issues no
+ * further MMA, waits for its one outstanding commit with the default budget, releases
+ * its tensor memory and sets the plan's status word; the next fga_sync (or call with a
+ * host output) returns FGA_ERR_TIMEOUT and marks the plan failed.
+ * Errors: FGA_ERR_INVALID (tries >= 2^32), FGA_ERR_STATE. */
+fga_status fga_set_wait_budget(fga_plan_t plan, int64_t tries);
+
+/* Measured fused multiply-add throughput of the current GPU/* Measured fused multiply-add throughput of the current GPU/* Budget of the bounded waits in the tensor-core kernels (FGA_MIXED_TF32X3: FBI stage 2
+ * and the reconstruction), as polls of the completion barrier of the previous chunk of
+ * MMAs before the CTA gives up (no counterpart in the paper: failure detection of the
+ * library). tries < 0 restores the defaults (2^22 polls, seconds); 0 makes every such
+ * wait give up at once, which exercises the give-up path. A CTA that gives up issues no
+ * further MMA, waits for its one outstanding commit with the default budget, releases
+ * its tensor memory and sets the plan's status word; the next fga_sync (or call with a
+ * host output) returns FGA_ERR_TIMEOUT and marks the plan failed.
+ * Errors: FGA_ERR_INVALID (tries >= 2^32), FGA_ERR_STATE. */
+fga_status fga_set_wait_budget(fga_plan_t plan, int64_t tries);
+
+/* Measured fused multiply-add throughput of the current GPU/* Measured fused multiply-add throughput of the current GPU (no counterpart in the
  * paper: the roofline denominator of the FP64-bound kernels). bits = 64 (DFMA) or 32
  * (FFMA); each of 8 blocks of 256 threads per SM runs 8 independent FMA chains for
  * iters x 16 rounds, timed with CUDA events on the legacy default stream after one

@@ -1,6 +1,7 @@
 // C ABI of libfga (declared in include/fga.h): plan set-up, validation, device
 // memory, and the order of the three steps of the Algorithm section.
 #include <algorithm>
+#include <cstdint>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -97,10 +98,31 @@ std::vector<double> window_dft(int nb, double h, double eps, bool periodic, doub
   return E;
 }
 
+fga_status check_usable(fga_plan_s* p);
+
+// After a replay of the pipeline graph the counts live on the device: bring the host's
+// copies (per-shot segments, G) up to date before anything else reads them.
+fga_status refresh_host_counts(fga_plan_s* p) {
+  if (!p->pipe_host_stale) return FGA_OK;
+  p->pipe_host_stale = false;
+  std::vector<fga::ShotDev> dev(p->nshots);
+  int64_t gm[2] = {0, 0};
+  CUDA_OR_FAIL(p, cudaMemcpyAsync(dev.data(), p->d_shots, sizeof(fga::ShotDev) * p->nshots,
+                                  cudaMemcpyDeviceToHost, p->stream));
+  CUDA_OR_FAIL(p, cudaMemcpyAsync(gm, p->d_gm, sizeof(gm), cudaMemcpyDeviceToHost, p->stream));
+  CUDA_OR_FAIL(p, cudaStreamSynchronize(p->stream));
+  for (int s = 0; s < p->nshots; ++s) {
+    p->shots[s].g_off = dev[s].g_off;
+    p->shots[s].g_cnt = dev[s].g_cnt;
+  }
+  p->G = gm[0];
+  return FGA_OK;
+}
+
 fga_status check_usable(fga_plan_s* p) {
   if (!p) return fail(nullptr, FGA_ERR_INVALID, "plan is NULL");
   if (p->failed) return FGA_ERR_STATE;
-  return FGA_OK;
+  return refresh_host_counts(p);
 }
 
 fga_status read_status(fga_plan_s* p) {
@@ -109,6 +131,10 @@ fga_status read_status(fga_plan_s* p) {
   CUDA_OR_FAIL(p, cudaStreamSynchronize(p->stream));
   if (st & fga::kStatusNumeric)
     return fail(p, FGA_ERR_NUMERIC, "a ray met |P| = 0, det Z = 0 or a non-finite value", true);
+  if (st & fga::kStatusShape)
+    return fail(p, FGA_ERR_CAPACITY,
+                "the data's support gives other active q rectangles than the pipeline graph was "
+                "captured for (run fga_run_pipeline on a new plan)", true);
   if (st & fga::kStatusCapacity) return fail(p, FGA_ERR_CAPACITY, "a plan capacity was exceeded", true);
   if (st & fga::kStatusTimeout)
     return fail(p, FGA_ERR_TIMEOUT, "a bounded tensor-core completion wait gave up", true);
@@ -215,7 +241,7 @@ fga_status fga_destroy(fga_plan_t p) {
                   p->d_adj_order, p->d_adj_bucket,
                   p->d_run_geo, p->d_run_axis, p->d_run_off, p->d_resid_int,
                   p->d_psi_f1, p->d_gpsi_f1, p->d_adj_scratch, p->d_grad, p->d_resid,
-                  p->d_part};
+                  p->d_part, p->d_gm};
   for (void* b : bufs)
     if (b) cudaFree(b);
   for (double* e : p->E)
@@ -225,6 +251,7 @@ fga_status fga_destroy(fga_plan_t p) {
   for (auto& ev : p->ev)
     if (ev) cudaEventDestroy(ev);
   if (p->graph_exec) cudaGraphExecDestroy(p->graph_exec);
+  if (p->pipe_exec) cudaGraphExecDestroy(p->pipe_exec);
   delete p;
   return FGA_OK;
 }
@@ -350,6 +377,11 @@ fga_status fga_plan(const fga_config* cfg, const double* velocity, void* stream,
         delete p;
         return fail(nullptr, FGA_ERR_INVALID, "in 3D the box must be at most 64 points per axis");
       }
+      if (cfg->precision == FGA_MIXED_TF32X3 && k == 0 && nbk % 8 != 0) {
+        delete p;
+        return fail(nullptr, FGA_ERR_INVALID,
+                    "FGA_MIXED_TF32X3 needs boxes of a multiple of 8 points along the first axis");
+      }
       sh.s[k] = sk;
       sh.nb[k] = nbk;
       sh.nq[k] = gd.periodic[k] ? gd.n[k] / sk : (gd.n[k] - 1) / sk + 1;
@@ -421,9 +453,13 @@ fga_status fga_plan(const fga_config* cfg, const double* velocity, void* stream,
       sh.E[k] = reinterpret_cast<const double2*>(dE);
       if (k == 0 && cfg->precision == FGA_MIXED_TF32X3) {
         // A operands of the tensor-core stage 2: Re-part rows (Re E, -Im E) and Im-part rows
-        // (Im E, Re E) over K = 2 jx, each split into a TF32 head and an FP32 tail
+        // (Im E, Re E) over K = 2 jx, each split into a TF32 head and an FP32 tail, laid
+        // out as the shared-memory image one bulk copy fills per K chunk of 8 complex jx:
+        // [m tile of 128 p_x][chunk][part: Re head, Re tail, Im head, Im tail][K quad 4]
+        // [8-row group 16][row 8][4 floats], rows past n_b zero (fga::fbi_a_image_floats)
         const int nb = sh.nb[0];
-        std::vector<float> A((size_t)4 * nb * 2 * nb);
+        const int mtiles = (nb + 127) / 128, nchunk = nb / 8;
+        std::vector<float> A((size_t)mtiles * nchunk * 4 * 4 * 512, 0.0f);
         auto split = [](double v, float& hi, float& lo) {
           float f = (float)v;
           uint32_t bits;
@@ -436,13 +472,17 @@ fga_status fga_plan(const fga_config* cfg, const double* velocity, void* stream,
           for (int jx = 0; jx < nb; ++jx) {
             const double er = E[((size_t)px * nb + jx) * 2], ei = E[((size_t)px * nb + jx) * 2 + 1];
             const double vals[2][2] = {{er, -ei}, {ei, er}};
+            const int mt = px / 128, row = px % 128, chunk = jx / 8, quad = (jx % 8) / 2, slot = jx % 2;
             for (int part = 0; part < 2; ++part)
               for (int c = 0; c < 2; ++c) {
                 float hi, lo;
                 split(vals[part][c], hi, lo);
-                const size_t at = (size_t)px * 2 * nb + 2 * jx + c;
-                A[(size_t)(2 * part) * nb * 2 * nb + at] = hi;
-                A[(size_t)(2 * part + 1) * nb * 2 * nb + at] = lo;
+                for (int hl = 0; hl < 2; ++hl) {
+                  const size_t at =
+                      ((((((size_t)mt * nchunk + chunk) * 4 + (2 * part + hl)) * 4 + quad) * 16 +
+                        row / 8) * 8 + row % 8) * 4 + 2 * slot + c;
+                  A[at] = hl == 0 ? hi : lo;
+                }
               }
           }
         float* dA = nullptr;
@@ -463,6 +503,33 @@ fga_status fga_plan(const fga_config* cfg, const double* velocity, void* stream,
   for (auto& ev : p->ev) PLAN_CUDA(cudaEventCreate(&ev));
 #undef PLAN_CUDA
   *out = p;
+  return FGA_OK;
+}
+
+// Device arrays of the Gaussian list and the ray state for at least cap Gaussians.
+static fga_status alloc_gaussians(fga_plan_s* p, size_t need) {
+  if (need <= p->g_cap && p->d_gshot) return FGA_OK;
+  const size_t cap = std::max<size_t>(need, 1);
+  size_t c;
+  c = 0; if (p->d_gshot) { cudaFree(p->d_gshot); p->d_gshot = nullptr; }
+  CUDA_OR_FAIL(p, grow(&p->d_gshot, &c, cap));
+  c = 0; if (p->d_gq) { cudaFree(p->d_gq); p->d_gq = nullptr; }
+  CUDA_OR_FAIL(p, grow(&p->d_gq, &c, cap));
+  c = 0; if (p->d_gp) { cudaFree(p->d_gp); p->d_gp = nullptr; }
+  CUDA_OR_FAIL(p, grow(&p->d_gp, &c, cap));
+  c = 0; if (p->d_gpsi) { cudaFree(p->d_gpsi); p->d_gpsi = nullptr; }
+  CUDA_OR_FAIL(p, grow(&p->d_gpsi, &c, cap));
+  c = 0; if (p->d_gpsi_f1) { cudaFree(p->d_gpsi_f1); p->d_gpsi_f1 = nullptr; }
+  CUDA_OR_FAIL(p, grow(&p->d_gpsi_f1, &c, cap));
+  c = 0; if (p->d_gcoef) { cudaFree(p->d_gcoef); p->d_gcoef = nullptr; }
+  CUDA_OR_FAIL(p, grow(&p->d_gcoef, &c, cap));
+  c = 0; if (p->d_state) { cudaFree(p->d_state); p->d_state = nullptr; }
+  CUDA_OR_FAIL(p, grow(&p->d_state, &c, cap * p->nfields));
+  c = 0; if (p->d_gsteps) { cudaFree(p->d_gsteps); p->d_gsteps = nullptr; }
+  CUDA_OR_FAIL(p, grow(&p->d_gsteps, &c, cap));
+  c = 0; if (p->d_adj_order) { cudaFree(p->d_adj_order); p->d_adj_order = nullptr; }
+  CUDA_OR_FAIL(p, grow(&p->d_adj_order, &c, cap));
+  p->g_cap = cap;
   return FGA_OK;
 }
 
@@ -525,7 +592,10 @@ fga_status fga_decompose(fga_plan_t p, const double* u0, const double* u1, int64
       sh.nrows = sh.qn[0] > 0 ? (int64_t)sh.s[0] * (sh.qn[0] - 1) + sh.nb[0] : 0;
       sh.g1_off = g1_total;
     }
-    if (d == 2) g1_total += 2 * sh.nrows * sh.qn[1] * sh.nb[1];
+    if (d == 2)
+      g1_total += p->precision == FGA_MIXED_TF32X3
+                      ? (int64_t)(fga::fbi_b_image_floats(sh) / 4)  // float image, in double2
+                      : 2 * sh.nrows * sh.qn[1] * sh.nb[1];
     if (d == 3) {
       sh.row_lo1 = (int64_t)sh.s[1] * sh.qlo[1] - sh.nb[1] / 2;
       sh.nrows1 = sh.qn[1] > 0 ? (int64_t)sh.s[1] * (sh.qn[1] - 1) + sh.nb[1] : 0;
@@ -570,29 +640,9 @@ fga_status fga_decompose(fga_plan_t p, const double* u0, const double* u1, int64
   }
   if (G > ((int64_t)1 << 31) - 1) return fail(p, FGA_ERR_CAPACITY, "more than 2^31-1 Gaussians", true);
   p->G = G;
-  if ((size_t)G > p->g_cap || !p->d_gshot) {
-    size_t cap = std::max<size_t>((size_t)G, 1);
-    size_t c;
-    c = 0; if (p->d_gshot) { cudaFree(p->d_gshot); p->d_gshot = nullptr; }
-    CUDA_OR_FAIL(p, grow(&p->d_gshot, &c, cap));
-    c = 0; if (p->d_gq) { cudaFree(p->d_gq); p->d_gq = nullptr; }
-    CUDA_OR_FAIL(p, grow(&p->d_gq, &c, cap));
-    c = 0; if (p->d_gp) { cudaFree(p->d_gp); p->d_gp = nullptr; }
-    CUDA_OR_FAIL(p, grow(&p->d_gp, &c, cap));
-    c = 0; if (p->d_gpsi) { cudaFree(p->d_gpsi); p->d_gpsi = nullptr; }
-    CUDA_OR_FAIL(p, grow(&p->d_gpsi, &c, cap));
-    c = 0; if (p->d_gpsi_f1) { cudaFree(p->d_gpsi_f1); p->d_gpsi_f1 = nullptr; }
-    CUDA_OR_FAIL(p, grow(&p->d_gpsi_f1, &c, cap));
-    c = 0; if (p->d_gcoef) { cudaFree(p->d_gcoef); p->d_gcoef = nullptr; }
-    CUDA_OR_FAIL(p, grow(&p->d_gcoef, &c, cap));
-    c = 0; if (p->d_state) { cudaFree(p->d_state); p->d_state = nullptr; }
-    CUDA_OR_FAIL(p, grow(&p->d_state, &c, cap * p->nfields));
-    c = 0; if (p->d_gsteps) { cudaFree(p->d_gsteps); p->d_gsteps = nullptr; }
-    CUDA_OR_FAIL(p, grow(&p->d_gsteps, &c, cap));
-    c = 0; if (p->d_adj_order) { cudaFree(p->d_adj_order); p->d_adj_order = nullptr; }
-    CUDA_OR_FAIL(p, grow(&p->d_adj_order, &c, cap));
-    p->g_cap = cap;
-  }
+  p->shape_gen += 1;
+  st = alloc_gaussians(p, (size_t)G);
+  if (st != FGA_OK) return st;
   CUDA_OR_FAIL(p, fga::launch_select(p));
   CUDA_OR_FAIL(p, cudaEventRecord(p->ev[2], p->stream));
   if (counts_host)
@@ -626,7 +676,7 @@ fga_status fga_propagate(fga_plan_t p) {
 // Device capacities the reconstruction needs for the current Gaussian set. The tile
 // lists: every Gaussian meets at most prod_k m_k tiles, m_k = (floor(window points /
 // tile) + 2) per image, times 5 images on periodic axes.
-static fga_status reconstruct_capacity(fga_plan_s* p) {
+static fga_status reconstruct_capacity(fga_plan_s* p, double headroom = 1.0) {
   const GridDev& gd = p->grid;
   const int d = gd.dim;
   size_t pairs = 0;
@@ -639,7 +689,7 @@ static fga_status reconstruct_capacity(fga_plan_s* p) {
       mk = std::min<size_t>(mk, (size_t)sh.ntile[k]);
       per *= mk;
     }
-    pairs += per * (size_t)sh.g_cnt;
+    pairs += per * (size_t)std::ceil(headroom * (double)sh.g_cnt);
   }
   CUDA_OR_FAIL(p, grow(&p->d_tile_list, &p->list_cap, pairs));
   int nsplit;
@@ -710,6 +760,108 @@ fga_status fga_run_graph(fga_plan_t p, double* u_dev) {
   CUDA_OR_FAIL(p, cudaGraphLaunch(p->graph_exec, p->stream));
   p->launches += 12;
   p->stage = 2;
+  return FGA_OK;
+}
+
+// Headroom of the pipeline graph's capacities over the counts of its sizing pass.
+constexpr double kPipeHeadroom = 1.25;
+
+fga_status fga_run_pipeline(fga_plan_t p, const double* u0, const double* u1, double* u_dev) {
+  // no refresh of the host's counts here: a replay needs none, and reading them back
+  // would wait for the stream
+  if (!p) return fail(nullptr, FGA_ERR_INVALID, "plan is NULL");
+  if (p->failed) return FGA_ERR_STATE;
+  fga_status st = FGA_OK;
+  if (!u0 || !u1 || !u_dev || !is_device_ptr(u0) || !is_device_ptr(u1) || !is_device_ptr(u_dev))
+    return fail(p, FGA_ERR_INVALID, "fga_run_pipeline takes device pointers only");
+  if (p->stream == nullptr)
+    return fail(p, FGA_ERR_INVALID, "graph mode needs a stream other than the legacy default stream");
+  if (p->nrx > 0) return fail(p, FGA_ERR_INVALID, "fga_run_pipeline records no traces: the plan has receivers");
+  if (p->z_method != FGA_Z_DYNAMIC)
+    return fail(p, FGA_ERR_INVALID, "fga_run_pipeline needs the dynamic-ray Z (FGA_Z_DYNAMIC)");
+  auto key_now = [&]() {
+    return std::vector<int64_t>{
+        (int64_t)(uintptr_t)u0, (int64_t)(uintptr_t)u1, (int64_t)(uintptr_t)u_dev, p->shape_gen,
+        (int64_t)p->g_cap, (int64_t)p->list_cap, (int64_t)p->partial_cap, (int64_t)p->bin_cap,
+        (int64_t)(uintptr_t)p->d_gshot, (int64_t)(uintptr_t)p->d_state,
+        (int64_t)(uintptr_t)p->d_tile_list, (int64_t)(uintptr_t)p->d_partial,
+        (int64_t)(uintptr_t)p->d_bin_off, (int64_t)(uintptr_t)p->d_psi, (int64_t)(uintptr_t)p->d_g1,
+        p->seg, p->ray_blocks, p->ray_variant};
+  };
+  if (p->pipe_exec && key_now() == p->pipe_key) {
+    CUDA_OR_FAIL(p, cudaGraphLaunch(p->pipe_exec, p->stream));
+    p->launches += p->pipe_kernels;
+    p->pipe_host_stale = true;
+    p->stage = 2;
+    return FGA_OK;
+  }
+  if (p->pipe_exec) {
+    cudaGraphExecDestroy(p->pipe_exec);
+    p->pipe_exec = nullptr;
+  }
+  // sizing pass (eager; its result is this call's result): the data's active q
+  // rectangles and counts, then capacities with headroom for the counts of later data
+  st = fga_decompose(p, u0, u1, nullptr);
+  if (st != FGA_OK) return st;
+  const size_t want = (size_t)std::ceil(kPipeHeadroom * (double)p->G) + 1024;
+  if (want > p->g_cap) {
+    st = alloc_gaussians(p, want);  // the new arrays are empty: select into them again
+    if (st != FGA_OK) return st;
+    st = fga_decompose(p, u0, u1, nullptr);
+    if (st != FGA_OK) return st;
+  }
+  if (!p->d_gm) CUDA_OR_FAIL(p, cudaMalloc(&p->d_gm, 2 * sizeof(int64_t)));
+  st = fga_propagate(p);
+  if (st != FGA_OK) return st;
+  p->dev_counts = true;  // binning splits over the whole capacity
+  st = reconstruct_capacity(p, kPipeHeadroom);
+  p->dev_counts = false;
+  if (st != FGA_OK) return st;
+  st = fga_reconstruct(p, u_dev);
+  if (st != FGA_OK) return st;
+  // capture: every launch sizes itself from the device-side counts
+  cudaGraph_t graph = nullptr;
+  CUDA_OR_FAIL(p, cudaStreamBeginCapture(p->stream, cudaStreamCaptureModeThreadLocal));
+  p->dev_counts = true;
+  const int64_t launches0 = p->launches;
+  cudaError_t e = fga::launch_support_bbox(p, u0, u1);
+  if (e == cudaSuccess) e = fga::launch_check_shapes(p);
+  if (e == cudaSuccess) e = fga::launch_fbi(p, u0, u1);
+  if (e == cudaSuccess) e = fga::launch_select_count(p);
+  if (e == cudaSuccess) e = fga::launch_counts_finish(p);
+  if (e == cudaSuccess) e = fga::launch_select(p);
+  if (e == cudaSuccess) e = fga::launch_rays(p);
+  if (e == cudaSuccess) e = fga::launch_binning(p);
+  if (e == cudaSuccess) e = fga::launch_binning_fill(p);
+  if (e == cudaSuccess)
+    e = p->precision == FGA_MIXED_TF32X3 ? fga::launch_reconstruct_tc(p, u_dev)
+                                         : fga::launch_reconstruct(p, u_dev);
+  p->dev_counts = false;
+  cudaError_t e2 = cudaStreamEndCapture(p->stream, &graph);
+  p->launches = launches0;
+  if (e != cudaSuccess || e2 != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    return fail(p, FGA_ERR_CUDA, std::string("pipeline graph capture: ") +
+                                     cudaGetErrorString(e != cudaSuccess ? e : e2), true);
+  }
+  size_t nnodes = 0;
+  p->pipe_kernels = 0;
+  if (cudaGraphGetNodes(graph, nullptr, &nnodes) == cudaSuccess && nnodes > 0) {
+    std::vector<cudaGraphNode_t> nodes(nnodes);
+    if (cudaGraphGetNodes(graph, nodes.data(), &nnodes) == cudaSuccess)
+      for (size_t i = 0; i < nnodes; ++i) {
+        cudaGraphNodeType t;
+        if (cudaGraphNodeGetType(nodes[i], &t) == cudaSuccess && t == cudaGraphNodeTypeKernel)
+          p->pipe_kernels += 1;
+      }
+  }
+  e = cudaGraphInstantiate(&p->pipe_exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) {
+    p->pipe_exec = nullptr;
+    return fail(p, FGA_ERR_CUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e), true);
+  }
+  p->pipe_key = key_now();
   return FGA_OK;
 }
 
@@ -849,6 +1001,14 @@ fga_status fga_reconstruct(fga_plan_t p, double* u_out) {
                                     p->stream));
     return read_status(p);
   }
+  return FGA_OK;
+}
+
+fga_status fga_set_wait_budget(fga_plan_t p, int64_t tries) {
+  fga_status st = check_usable(p);
+  if (st != FGA_OK) return st;
+  if (tries > (int64_t)UINT32_MAX) return fail(p, FGA_ERR_INVALID, "tries must be below 2^32");
+  p->wait_tries = tries < 0 ? -1 : tries;
   return FGA_OK;
 }
 

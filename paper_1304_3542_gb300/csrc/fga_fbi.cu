@@ -227,10 +227,26 @@ __global__ void __launch_bounds__(NT) k_fbi_stage1(GridDev gd, const ShotDev* __
         int64_t m = m0 + ty + 16 * i, n = n0 + tx + 16 * j;
         if (m < M && n < N) {
           if (split_out) {
-            // mixed precision: the tensor-core stage 2 reads TF32 head/tail splits
-            float4* f = reinterpret_cast<float4*>(g1);
-            f[sh.g1_off + m * N + n] = split4(acc0[i][j]);
-            f[sh.g1_off + plane + m * N + n] = split4(acc1[i][j]);
+            // mixed precision: TF32 head/tail splits, written straight into the B operand
+            // image of the tensor-core stage 2 (every row is the first row of a pair of
+            // its own parity and the second of a pair of the other parity)
+            const int64_t r = m / sh.qn[1], mzl = m - r * sh.qn[1];
+            float* img = reinterpret_cast<float*>(g1 + sh.g1_off);
+            const int64_t nt = n / 128, w = n % 128, npair = fbi_b_pairs(sh), ntile = fbi_b_ntile(sh);
+#pragma unroll
+            for (int f = 0; f < 2; ++f) {
+              const float4 v = split4(f == 0 ? acc0[i][j] : acc1[i][j]);
+#pragma unroll
+              for (int slot = 0; slot < 2; ++slot) {
+                const int64_t rr = r - slot;
+                if (rr < 0) continue;
+                const int64_t par = rr & 1, t = rr >> 1;
+                const int64_t b = ((((((int64_t)f * sh.qn[1] + mzl) * 2 + par) * ntile + nt) * 2) * npair + t) * 512 +
+                                  w * 4 + 2 * slot;
+                *reinterpret_cast<float2*>(img + b) = make_float2(v.x, v.z);                 // head
+                *reinterpret_cast<float2*>(img + b + npair * 512) = make_float2(v.y, v.w);   // tail
+              }
+            }
           } else {
             g1[sh.g1_off + m * N + n] = acc0[i][j];
             g1[sh.g1_off + plane + m * N + n] = acc1[i][j];
@@ -509,24 +525,44 @@ __global__ void k_fbi3_stage3(GridDev gd, const ShotDev* __restrict__ shots,
 //   B_f[pz][2j] = Re G1_f, B_f[pz][2j+1] = Im G1_f,
 // with every operand split into a TF32 head and an FP32 tail and the three products
 // hi*hi + hi*lo + lo*hi accumulated in FP32 in tensor memory (four accumulators of 128
-// columns: field 0 re/im, field 1 re/im). Operands are K-major in shared memory without
-// swizzle (8-row x 16-byte core matrices), one CTA per SM (128 KiB of operands, all 512
-// TMEM columns). Epilogue: each warp moves its 32 accumulator rows through shared memory
-// (a 32 x 32 block at a time) so that the branch split runs with lane = p_z column and
-// every store of the warp is one contiguous row segment; the split is FP32 arithmetic on
-// the FP32 accumulations (with 1/|p| from rsqrtf), stored as FP64, and the maximum of
-// |psi+|^2 is taken in FP64 over the stored values (squares of FP32 values are exact in
-// FP64, so it equals the selection's own |psi+|^2).
+// columns: field 0 re/im, field 1 re/im).
+//
+// Operands: both live in global memory as the shared-memory image of a K chunk of 8
+// complex jx (K = 16): the A image is built at plan time (E_x is the same for every q),
+// the B image is what stage 1 writes (for each q column the pairs of stage-1 rows of
+// either parity, so that every q's box, whatever the parity of its first row, reads its
+// chunk as one contiguous block). K-major without swizzle: the core matrices (8 rows x
+// 16 bytes) of one K quad lie for all sixteen 8-row groups in a row (SBO = 128 B), the
+// four K quads of a chunk 2 KiB apart (LBO). One thread runs a 3-stage pipeline: bulk
+// copies (TMA, cp.async.bulk) of a chunk's A (32 KiB) and B (4 x 8 KiB) into a stage
+// complete on the stage's "full" mbarrier; the chunk's 24 MMAs are committed to its
+// "empty" mbarrier, after which the stage is refilled three chunks ahead; the last
+// commit goes to "done", which the whole CTA waits on before the epilogue. Every wait
+// is bounded; a thread that gives up issues nothing more and waits for what it has in
+// flight (one phase per barrier at most) with the full budget before the tensor memory
+// is released.
+//
+// Epilogue (8 warps, two per TMEM lane quarter, each taking half of the 128 columns):
+// each warp moves its 32 accumulator rows through shared memory (a 32 x 32 block at a
+// time, reusing the stage buffers) so that the branch split runs with lane = p_z column
+// and every store of the warp is one contiguous row segment; the split is FP32
+// arithmetic on the FP32 accumulations (with 1/|p| from rsqrtf), stored as FP64. The
+// maximum of |psi+|^2 is the selection's own FP64 |psi+|^2 of the stored values: a thread
+// screens its values by their FP32 square (relative error below 2^-21) and evaluates the
+// FP64 square only of those within 1e-6 of its running FP32 maximum, which any value
+// whose FP64 square could be the largest is.
 constexpr int FT = 128;        // tile edge in p_x (GEMM M) and p_z (GEMM N)
-constexpr int FJ = 16;         // complex jx per chunk -> K = 32
-constexpr int FKC = 2 * FJ;
-constexpr int FKB = FKC / 4;   // core matrices along K
-constexpr int FNT = 128;
-constexpr uint32_t kFbiLBO = 128, kFbiSBO = FKB * 128;
-constexpr size_t kFbiOperand = (size_t)FT * FKC * sizeof(float);  // 16 KiB
+constexpr int FJ = 8;          // complex jx per chunk -> K = 16
+constexpr int FNT = 256;       // 8 warps: warp w reads TMEM lanes 32 (w % 4) .., columns half w / 4
+constexpr int FSTAGES = 3;
+constexpr uint32_t kFbiOp = FT * 2 * FJ * sizeof(float);   // one operand part of a chunk: 8 KiB
+constexpr uint32_t kFbiStage = 8 * kFbiOp;                  // A: 4 parts, B: 2 fields x 2 parts
+constexpr uint32_t kFbiLBO = 2048, kFbiSBO = 128;
+constexpr size_t kFbiBarOff = (size_t)FSTAGES * kFbiStage;
+constexpr size_t kFbiSmem = kFbiBarOff + 128;
 constexpr int kStageLd = 33;  // float4 per staged row: 32 columns + 1 of padding (no bank conflicts)
-constexpr size_t kFbiStageOff = 8 * kFbiOperand + 128;
-constexpr size_t kFbiSmem = kFbiStageOff + (size_t)4 * 32 * kStageLd * sizeof(float4);
+static_assert((size_t)(FNT / 32) * 32 * kStageLd * sizeof(float4) <= kFbiBarOff,
+              "epilogue staging fits the stages");
 constexpr uint32_t kFbiTries = 1u << 22;
 
 // IEEE binary32 -> binary64 in integer arithmetic (exact, keeps the FP64 pipe free):
@@ -549,41 +585,42 @@ __device__ __forceinline__ double widen_f32(float f) {
   return __longlong_as_double((long long)bits);
 }
 
-__device__ __forceinline__ int fbi_core_offset(int row, int k) {
-  return (((row >> 3) * FKB + (k >> 2)) * 8 + (row & 7)) * 4 + (k & 3);
-}
-
 __global__ void __launch_bounds__(FNT) k_fbi_stage2_tc(GridDev gd, const ShotDev* __restrict__ shots,
                                                       const double* __restrict__ C,
                                                       const double2* __restrict__ g1,
                                                       double2* __restrict__ psi,
                                                       double2* __restrict__ psi_f1,
                                                       unsigned long long* __restrict__ max2,
-                                                      int* status) {
+                                                      int* status, uint32_t tries) {
   const int s = blockIdx.z;
   const ShotDev& sh = shots[s];
   const int64_t qtot = sh.qn[0] * sh.qn[1];
   const int64_t ql = blockIdx.y;
   const int64_t nbx = sh.nb[0], nbz = sh.nb[1];
   const int64_t tiles_z = (nbz + FT - 1) / FT;
-  const int64_t m0 = (blockIdx.x / tiles_z) * FT, n0 = (blockIdx.x % tiles_z) * FT;
+  const int64_t mt = blockIdx.x / tiles_z, nt = blockIdx.x % tiles_z;
+  const int64_t m0 = mt * FT, n0 = nt * FT;
   if (ql >= qtot || m0 >= nbx) return;  // uniform over the CTA
   extern __shared__ __align__(1024) unsigned char smem[];
-  float* op = reinterpret_cast<float*>(smem);
-  float *Arh = op, *Arl = op + FT * FKC, *Aih = op + 2 * FT * FKC, *Ail = op + 3 * FT * FKC;
-  float *B0h = op + 4 * FT * FKC, *B0l = op + 5 * FT * FKC, *B1h = op + 6 * FT * FKC,
-        *B1l = op + 7 * FT * FKC;
-  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + 8 * kFbiOperand);
-  uint32_t* tbase = reinterpret_cast<uint32_t*>(smem + 8 * kFbiOperand + 16);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + kFbiBarOff);
+  uint64_t* empty = full + FSTAGES;
+  uint64_t* done = empty + FSTAGES;
+  uint32_t* tbase = reinterpret_cast<uint32_t*>(done + 1);
   __shared__ double cq_s;
+  __shared__ int aborted_s;
   const int tid = threadIdx.x, warp = tid >> 5;
   const int64_t mxl = ql / sh.qn[1], mzl = ql - mxl * sh.qn[1];
   if (tid == 0) {
     double q[2] = {gd.o[0] + (double)(sh.s[0] * (sh.qlo[0] + mxl)) * gd.h[0],
                    gd.o[1] + (double)(sh.s[1] * (sh.qlo[1] + mzl)) * gd.h[1]};
     cq_s = medium_value<2>(gd, C, q);
-    tc::mbar_init(bar, 1);
+    for (int i = 0; i < FSTAGES; ++i) {
+      tc::mbar_init(&full[i], 1);
+      tc::mbar_init(&empty[i], 1);
+    }
+    tc::mbar_init(done, 1);
     tc::fence_mbar_init();
+    aborted_s = 0;
   }
   if (warp == 0) {
     tc::tmem_alloc(tbase, 4 * FT);
@@ -593,84 +630,91 @@ __global__ void __launch_bounds__(FNT) k_fbi_stage2_tc(GridDev gd, const ShotDev
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t tmem = *tbase;
-  const uint32_t idesc = tc::idesc_f32acc(tc::kFmtTF32, FT, FT);
-  const int64_t M1 = sh.nrows * sh.qn[1];
-  // the stage-1 output of the mixed precision holds (Re head, Re tail, Im head, Im tail)
-  const float4* G0s = reinterpret_cast<const float4*>(g1) + sh.g1_off;
-  const float4* G1s = G0s + M1 * nbz;
-  const int64_t row0 = sh.s[0] * mxl;
-  uint32_t chunks = 0;
-  bool ok = true;
-  for (int64_t k0 = 0; k0 < nbx; k0 += FJ) {
-    if (chunks > 0) ok &= tc::mbar_wait_bounded(bar, (chunks - 1) & 1u, kFbiTries);
-    // A: the pre-split rows m0 .. m0+127 of E_x, K = 2 k0 .. 2 k0 + 31, four floats per copy
-    for (int e = tid; e < 4 * FT * (FKC / 4); e += FNT) {
-      const int part = e / (FT * (FKC / 4)), rem = e % (FT * (FKC / 4));
-      const int r = rem / (FKC / 4), c = rem % (FKC / 4);
-      const int64_t m = m0 + r, kk = 2 * k0 + 4 * c;
-      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (m < nbx && kk < 2 * nbx)
-        v = __ldg(reinterpret_cast<const float4*>(sh.Etc + ((int64_t)part * nbx + m) * 2 * nbx + kk));
-      float* dst = part == 0 ? Arh : (part == 1 ? Arl : (part == 2 ? Aih : Ail));
-      *reinterpret_cast<float4*>(dst + fbi_core_offset(r, 4 * c)) = v;
-    }
-    // B: the split stage-1 rows row0 + k0 .. + 15 of this q column, p_z n0 .. n0+127
-    for (int e = tid; e < FT * FJ; e += FNT) {
-      const int j = e / FT, r = e % FT;
-      const int64_t k = k0 + j, n = n0 + r;
-      float4 v0 = make_float4(0.f, 0.f, 0.f, 0.f), v1 = v0;
-      if (k < nbx && n < nbz) {
-        const int64_t off = ((row0 + k) * sh.qn[1] + mzl) * nbz + n;
-        v0 = __ldg(G0s + off);
-        v1 = __ldg(G1s + off);
-      }
-      const int o = fbi_core_offset(r, 2 * j);
-      *reinterpret_cast<float2*>(B0h + o) = make_float2(v0.x, v0.z);
-      *reinterpret_cast<float2*>(B0l + o) = make_float2(v0.y, v0.w);
-      *reinterpret_cast<float2*>(B1h + o) = make_float2(v1.x, v1.z);
-      *reinterpret_cast<float2*>(B1l + o) = make_float2(v1.y, v1.w);
-    }
-    tc::fence_proxy_async_smem();
-    __syncthreads();
-    if (tid == 0) {
-      tc::fence_after_sync();
-      const uint32_t arh = tc::smem_u32(Arh), arl = tc::smem_u32(Arl);
-      const uint32_t aih = tc::smem_u32(Aih), ail = tc::smem_u32(Ail);
-      const uint32_t b0h = tc::smem_u32(B0h), b0l = tc::smem_u32(B0l);
-      const uint32_t b1h = tc::smem_u32(B1h), b1l = tc::smem_u32(B1l);
+  if (tid == 0) {
+    const int nchunk = (int)(nbx / FJ);
+    const float* Aimg = sh.Etc + (size_t)mt * nchunk * 4 * (kFbiOp / sizeof(float));
+    const int64_t row0 = (int64_t)sh.s[0] * mxl;  // first stage-1 row of this q's box
+    const int64_t par = row0 & 1, t0 = row0 >> 1;
+    const float* Bimg = reinterpret_cast<const float*>(g1 + sh.g1_off);
+    const int64_t npair = fbi_b_pairs(sh), ntile = fbi_b_ntile(sh);
+    auto load = [&](int c) {
+      const int st = c % FSTAGES;
+      unsigned char* base = smem + (size_t)st * kFbiStage;
+      tc::mbar_arrive_expect_tx(&full[st], kFbiStage);
+      tc::bulk_g2s(base, Aimg + (size_t)c * 4 * (kFbiOp / sizeof(float)), 4 * kFbiOp, &full[st]);
 #pragma unroll
-      for (int ks = 0; ks < FKC / 8; ++ks) {
-        const uint32_t st = ks * 256;
-        const uint32_t acc = (chunks > 0 || ks > 0) ? 1u : 0u;
-        const uint32_t ah[2] = {arh, aih}, al[2] = {arl, ail};
-        const uint32_t bh[2] = {b0h, b1h}, bl[2] = {b0l, b1l};
+      for (int f = 0; f < 2; ++f)
+#pragma unroll
+        for (int part = 0; part < 2; ++part) {
+          const float* src =
+              Bimg + (((((f * sh.qn[1] + mzl) * 2 + par) * ntile + nt) * 2 + part) * npair + t0 + 4 * c) * 512;
+          tc::bulk_g2s(base + (4 + 2 * f + part) * kFbiOp, src, kFbiOp, &full[st]);
+        }
+    };
+    const uint32_t idesc = tc::idesc_f32acc(tc::kFmtTF32, FT, FT);
+    int loaded = 0, fulled = 0, committed = 0, emptied = 0;  // chunks issued / observed
+    bool ok = true;
+    for (; loaded < FSTAGES && loaded < nchunk; ++loaded) load(loaded);
+    for (int c = 0; c < nchunk && ok; ++c) {
+      const int st = c % FSTAGES;
+      if (!tc::mbar_wait_bounded(&full[st], (uint32_t)(c / FSTAGES) & 1u, tries)) {
+        ok = false;
+        break;
+      }
+      ++fulled;
+      tc::fence_after_sync();
+      const uint32_t base = tc::smem_u32(smem + (size_t)st * kFbiStage);
+#pragma unroll
+      for (int ks = 0; ks < 2; ++ks) {
+        const uint32_t step = ks * 2 * kFbiLBO;  // two K quads = 8 tf32
 #pragma unroll
         for (int f = 0; f < 2; ++f)
 #pragma unroll
-          for (int c = 0; c < 2; ++c) {
-            const uint32_t d = tmem + (uint32_t)((2 * f + c) * FT);
-            tc::mma_tf32(d, tc::smem_desc(ah[c] + st, kFbiLBO, kFbiSBO),
-                         tc::smem_desc(bh[f] + st, kFbiLBO, kFbiSBO), idesc, acc);
-            tc::mma_tf32(d, tc::smem_desc(ah[c] + st, kFbiLBO, kFbiSBO),
-                         tc::smem_desc(bl[f] + st, kFbiLBO, kFbiSBO), idesc, 1u);
-            tc::mma_tf32(d, tc::smem_desc(al[c] + st, kFbiLBO, kFbiSBO),
-                         tc::smem_desc(bh[f] + st, kFbiLBO, kFbiSBO), idesc, 1u);
+          for (int cc = 0; cc < 2; ++cc) {
+            const uint32_t d = tmem + (uint32_t)((2 * f + cc) * FT);
+            const uint32_t ah = base + (2 * cc) * kFbiOp + step, al = ah + kFbiOp;
+            const uint32_t bh = base + (4 + 2 * f) * kFbiOp + step, bl = bh + kFbiOp;
+            tc::mma_tf32(d, tc::smem_desc(ah, kFbiLBO, kFbiSBO), tc::smem_desc(bh, kFbiLBO, kFbiSBO), idesc,
+                         (c > 0 || ks > 0) ? 1u : 0u);
+            tc::mma_tf32(d, tc::smem_desc(ah, kFbiLBO, kFbiSBO), tc::smem_desc(bl, kFbiLBO, kFbiSBO), idesc, 1u);
+            tc::mma_tf32(d, tc::smem_desc(al, kFbiLBO, kFbiSBO), tc::smem_desc(bh, kFbiLBO, kFbiSBO), idesc, 1u);
           }
       }
-      tc::mma_commit(bar);
+      tc::mma_commit(&empty[st]);
+      ++committed;
+      // refill the stage of the previous chunk once its MMAs are done
+      if (c >= 1 && loaded < nchunk) {
+        const int pc = c - 1;
+        if (!tc::mbar_wait_bounded(&empty[pc % FSTAGES], (uint32_t)(pc / FSTAGES) & 1u, tries)) {
+          ok = false;
+          break;
+        }
+        emptied = pc + 1;
+        load(loaded++);
+      }
     }
-    ++chunks;
+    if (ok) {
+      tc::mma_commit(done);  // arrives once every MMA of the CTA is complete
+    } else {
+      aborted_s = 1;
+      atomicOr(status, kStatusTimeout);
+      // nothing more is issued; wait, in order and with the full budget, for the copies and
+      // the MMAs in flight (each barrier has at most one phase outstanding)
+      for (int x = fulled; x < loaded; ++x)
+        tc::mbar_wait_bounded(&full[x % FSTAGES], (uint32_t)(x / FSTAGES) & 1u, kFbiTries);
+      for (int x = emptied; x < committed; ++x)
+        tc::mbar_wait_bounded(&empty[x % FSTAGES], (uint32_t)(x / FSTAGES) & 1u, kFbiTries);
+      tc::mbar_arrive(done);
+    }
   }
-  if (chunks > 0) ok &= tc::mbar_wait_bounded(bar, (chunks - 1) & 1u, kFbiTries);
-  if (!ok) {
-    atomicOr(status, kStatusTimeout);
-    if (chunks > 0) tc::mbar_wait_bounded(bar, (chunks - 1) & 1u, kFbiTries);
-  }
+  const bool finished = tc::mbar_wait_bounded(done, 0u, tid == 0 ? kFbiTries : (tries > 0 ? tries : 1u));
+  const bool ok = __syncthreads_and(finished) && aborted_s == 0;
+  if (!ok && tid == 0 && aborted_s == 0) atomicOr(status, kStatusTimeout);
   tc::fence_after_sync();
   // epilogue: TMEM lane 32 w + l holds p_x row m0 + 32 w + l; a warp stages 32 rows x 32
   // p_z columns, then sweeps them row by row with lane = column
-  const int lane = tid & 31;
-  float4* stage = reinterpret_cast<float4*>(smem + kFbiStageOff) + warp * 32 * kStageLd;
+  const int lane = tid & 31, quarter = warp & 3, half = warp >> 2;
+  float4* stage = reinterpret_cast<float4*>(smem) + warp * 32 * kStageLd;
   const double hv = gd.h[0] * gd.h[1];
   const float h2 = (float)(0.5 * hv);                    // psi_f = hv * acc; psi+ = psi0/2 + ...
   const float c1 = (float)(0.5 * hv * sh.eps / cq_s);    // ... i (eps/(2 c(q) |p|)) hv acc1
@@ -678,24 +722,25 @@ __global__ void __launch_bounds__(FNT) k_fbi_stage2_tc(GridDev gd, const ShotDev
   double2* out0 = psi + sh.psi_off + ql * sh.np;
   double2* out1 = psi_f1 + sh.psi_off + ql * sh.np;
   unsigned long long mymax = 0ull;  // bits of the largest |psi+|^2 (non-negative doubles order as integers)
+  float fmax32 = 0.0f;              // running maximum of the FP32 squares (screen)
   float a0r[32], a0i[32], a1r[32], a1i[32];
+  if (ok) {
 #pragma unroll 1
-  for (int cb = 0; cb < FT; cb += 32) {
-    const uint32_t lane_base = tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)cb;
-    tc::tmem_ld_32x32b_x32(lane_base, a0r);
-    tc::tmem_ld_32x32b_x32(lane_base + FT, a0i);
-    tc::tmem_ld_32x32b_x32(lane_base + 2 * FT, a1r);
-    tc::tmem_ld_32x32b_x32(lane_base + 3 * FT, a1i);
+    for (int cb = 64 * half; cb < 64 * half + 64; cb += 32) {
+      const uint32_t lane_base = tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)cb;
+      tc::tmem_ld_32x32b_x32(lane_base, a0r);
+      tc::tmem_ld_32x32b_x32(lane_base + FT, a0i);
+      tc::tmem_ld_32x32b_x32(lane_base + 2 * FT, a1r);
+      tc::tmem_ld_32x32b_x32(lane_base + 3 * FT, a1i);
 #pragma unroll
-    for (int i = 0; i < 32; ++i) stage[lane * kStageLd + i] = make_float4(a0r[i], a0i[i], a1r[i], a1i[i]);
-    __syncwarp();
-    const int64_t n = n0 + cb + lane;
-    const int mz = (int)(n - nbz / 2);
-    const float pz = (float)mz * psz;
-    if (ok) {
+      for (int i = 0; i < 32; ++i) stage[lane * kStageLd + i] = make_float4(a0r[i], a0i[i], a1r[i], a1i[i]);
+      __syncwarp();
+      const int64_t n = n0 + cb + lane;
+      const int mz = (int)(n - nbz / 2);
+      const float pz = (float)mz * psz;
 #pragma unroll 2
       for (int rr = 0; rr < 32; ++rr) {
-        const int64_t m = m0 + 32 * warp + rr;  // uniform over the warp
+        const int64_t m = m0 + 32 * quarter + rr;  // uniform over the warp
         if (m >= nbx) break;
         if (n >= nbz) continue;
         const float4 v = stage[rr * kStageLd + lane];
@@ -710,11 +755,15 @@ __global__ void __launch_bounds__(FNT) k_fbi_stage2_tc(GridDev gd, const ShotDev
         const int64_t jp = m * nbz + n;
         out0[jp] = o;
         out1[jp] = make_double2(widen_f32(tx), widen_f32(ty));
-        const unsigned long long a2 = (unsigned long long)__double_as_longlong(o.x * o.x + o.y * o.y);
-        if (a2 <= 0x7ff0000000000000ull && a2 > mymax) mymax = a2;  // NaN left out, as fmax does
+        const float f2 = fmaf(ox, ox, oy * oy);
+        if (f2 >= 0.999999f * fmax32) {  // false for NaN
+          fmax32 = fmaxf(fmax32, f2);
+          const unsigned long long a2 = (unsigned long long)__double_as_longlong(o.x * o.x + o.y * o.y);
+          if (a2 <= 0x7ff0000000000000ull && a2 > mymax) mymax = a2;  // NaN left out, as fmax does
+        }
       }
+      __syncwarp();
     }
-    __syncwarp();
   }
   for (int off = 16; off > 0; off >>= 1) {
     const unsigned long long o = __shfl_xor_sync(0xffffffffu, mymax, off);
@@ -736,6 +785,49 @@ cudaError_t launch_support_bbox(fga_plan_s* p, const double* u0, const double* u
   k_support_bbox<<<dim3((unsigned)blocks, p->nshots), 256, 0, p->stream>>>(p->grid, u0, u1,
                                                                           p->d_bbox);
   p->launches += 2;
+  return cudaGetLastError();
+}
+
+namespace {
+// One thread per shot: the active q rectangle of the support in bbox, computed as
+// fga_decompose computes it on the host, against the one the plan holds.
+__global__ void k_check_shapes(GridDev gd, const ShotDev* __restrict__ shots, int nshots,
+                               const int* __restrict__ bbox, int* status) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= nshots) return;
+  const ShotDev& sh = shots[s];
+  const int d = gd.dim;
+  bool empty = false;
+  int64_t qlo[kMaxDim] = {0, 0, 0}, qn[kMaxDim] = {0, 0, 0};
+  for (int k = 0; k < d; ++k) {
+    const int lo = bbox[(s * d + k) * 2], hi = bbox[(s * d + k) * 2 + 1];
+    if (hi < 0) empty = true;
+    if (gd.periodic[k]) {
+      qlo[k] = 0;
+      qn[k] = sh.nq[k];
+    } else {
+      const int64_t half = sh.nb[k] / 2;
+      int64_t mlo = (int64_t)ceil((double)(lo - half + 1) / sh.s[k]);
+      int64_t mhi = (int64_t)floor((double)(hi + half) / sh.s[k]);
+      mlo = mlo > 0 ? mlo : 0;
+      mhi = mhi < sh.nq[k] - 1 ? mhi : sh.nq[k] - 1;
+      qlo[k] = mlo;
+      qn[k] = mhi - mlo + 1 > 0 ? mhi - mlo + 1 : 0;
+    }
+  }
+  bool same = true;
+  for (int k = 0; k < d; ++k) {
+    if (empty) qn[k] = 0;
+    same = same && qn[k] == sh.qn[k] && (qn[k] == 0 || qlo[k] == sh.qlo[k]);
+  }
+  if (!same) atomicOr(status, kStatusShape);
+}
+}  // namespace
+
+cudaError_t launch_check_shapes(fga_plan_s* p) {
+  k_check_shapes<<<(p->nshots + 127) / 128, 128, 0, p->stream>>>(p->grid, p->d_shots, p->nshots,
+                                                                 p->d_bbox, p->d_status);
+  p->launches += 1;
   return cudaGetLastError();
 }
 
@@ -794,7 +886,9 @@ cudaError_t launch_fbi(fga_plan_s* p, const double* u0, const double* u1) {
     dim3 tgrid((unsigned)tiles, (unsigned)maxQ, p->nshots);
     k_fbi_stage2_tc<<<tgrid, FNT, kFbiSmem, p->stream>>>(p->grid, p->d_shots, p->d_coef, p->d_g1,
                                                         p->d_psi, p->d_psi_f1, p->d_max2,
-                                                        p->d_status);
+                                                        p->d_status,
+                                                        p->wait_tries >= 0 ? (uint32_t)p->wait_tries
+                                                                           : kFbiTries);
     return cudaGetLastError();
   }
   dim3 g2grid((unsigned)maxTiles, (unsigned)maxQ, p->nshots);

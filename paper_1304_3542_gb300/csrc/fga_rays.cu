@@ -51,9 +51,14 @@ __global__ void __launch_bounds__(128, MINB) k_rays(GridDev gd, const ShotDev* _
                                               unsigned long long* next, RxDev rx,
                                               double* __restrict__ trace_part, int64_t slice_len,
                                               int slices, unsigned long long mult,
-                                              int32_t* __restrict__ gsteps) {
+                                              int32_t* __restrict__ gsteps,
+                                              const int64_t* __restrict__ gm) {
   using Lo = Layout<D>;
   constexpr int NF = Lo::NF;
+  if (gm) {  // counts kept on the device (pipeline graph)
+    G = gm[0];
+    mult = (unsigned long long)gm[1];
+  }
   // this block's private slice of the trace sums (no other block adds into it)
   double* traces = rx.every > 0 ? trace_part + (int64_t)(blockIdx.x % slices) * slice_len : nullptr;
   unsigned long long w = atomicAdd(next, 1ull);
@@ -213,20 +218,7 @@ cudaError_t launch_medium_table(fga_plan_s* p) {
   return cudaGetLastError();
 }
 
-unsigned long long work_order_mult(int64_t G) {
-  if (G < 3 || G >= ((int64_t)1 << 32)) return 1;  // (w * mult) must not overflow 64 bits
-  unsigned long long m = (unsigned long long)((double)G * 0.6180339887498949) | 1ull;
-  auto gcd = [](unsigned long long a, unsigned long long b) {
-    while (b) {
-      unsigned long long r = a % b;
-      a = b;
-      b = r;
-    }
-    return a;
-  };
-  while (gcd(m, (unsigned long long)G) != 1) m += 2;
-  return m % (unsigned long long)G;
-}
+unsigned long long work_order_mult(int64_t G) { return work_order_mult_of(G); }
 
 namespace {
 using RayKernel = decltype(&k_rays<2, 1>);
@@ -292,7 +284,7 @@ cudaError_t launch_rays_steps(fga_plan_s* p, int64_t nsteps, bool record) {
   // d_steps[0]: steps integrated; d_steps[1]: the work counter of the persistent kernel
   cudaError_t e = cudaMemsetAsync(p->d_steps, 0, 2 * sizeof(unsigned long long), p->stream);
   if (e != cudaSuccess) return e;
-  if (p->G == 0) {
+  if (p->G == 0 && !p->dev_counts) {
     if (record && p->nrx > 0)
       return cudaMemsetAsync(p->d_traces, 0, sizeof(double) * p->nshots * p->rx.nrec * p->rx.nrx,
                              p->stream);
@@ -300,7 +292,7 @@ cudaError_t launch_rays_steps(fga_plan_s* p, int64_t nsteps, bool record) {
   }
   e = ensure_ray_blocks(p);
   if (e != cudaSuccess) return e;
-  const unsigned blocks = (unsigned)ray_launch_blocks(p);
+  const unsigned blocks = (unsigned)(p->dev_counts ? p->ray_blocks : ray_launch_blocks(p));
   RxDev rx = p->rx;
   int64_t len = 0, slices = 1;
   if (record && p->nrx > 0) {
@@ -318,7 +310,8 @@ cudaError_t launch_rays_steps(fga_plan_s* p, int64_t nsteps, bool record) {
                                       p->d_gp, p->d_gpsi, nsteps, p->dt, p->kappa,
                                       p->integrate_exited, p->d_state, (int64_t)p->g_cap,
                                       p->d_gcoef, p->d_status, p->d_steps, p->d_steps + 1, rx,
-                                      p->d_part, len, (int)slices, mult, p->d_gsteps);
+                                      p->d_part, len, (int)slices, mult, p->d_gsteps,
+                                      p->dev_counts ? p->d_gm : nullptr);
   p->launches += 1;
   e = cudaGetLastError();
   if (e != cudaSuccess || len == 0) return e;

@@ -400,9 +400,14 @@ __global__ void __launch_bounds__(NT) k_reduce(GridDev gd, const ShotDev* __rest
 
 // Splits of the binning: runs of at least kBinChunk Gaussians, so that tiles x splits
 // CTAs fill the GPU even when a shot has few tiles; at most 2^30 CTAs.
+// With the counts on the device (pipeline graph) the splits cover the plan's whole
+// Gaussian capacity.
 void bin_splits(const fga_plan_s* p, int* nsplit, int64_t* chunk) {
   int64_t gmax = 1;
-  for (const auto& sh : p->shots) gmax = std::max<int64_t>(gmax, sh.g_cnt);
+  if (p->dev_counts)
+    gmax = std::max<int64_t>(gmax, (int64_t)p->g_cap);
+  else
+    for (const auto& sh : p->shots) gmax = std::max<int64_t>(gmax, sh.g_cnt);
   int64_t ns = (gmax + kBinChunk - 1) / kBinChunk;
   ns = std::max<int64_t>(1, std::min<int64_t>(ns, ((int64_t)1 << 30) / std::max<int64_t>(p->ntiles, 1)));
   *nsplit = (int)ns;

@@ -26,7 +26,7 @@ namespace fga {
 namespace {
 
 constexpr int TM = 128;       // tile edge (x = GEMM M, z = GEMM N)
-constexpr int CHG = 16;       // Gaussians per chunk -> K = 32
+constexpr int CHG = 8;        // Gaussians per chunk -> K = 16
 constexpr int KC = 2 * CHG;   // GEMM K per chunk
 constexpr int KB = KC / 4;    // 16-byte core matrices along K (tf32: 4 per core row)
 constexpr int64_t SEGM = 2048;  // default Gaussians per work item
@@ -35,8 +35,9 @@ constexpr uint32_t kMaxTries = 1u << 22;
 // core-matrix (8 rows x 16 bytes) strides of the K-major operand tiles
 constexpr uint32_t kLBO = 128;       // next core matrix along K
 constexpr uint32_t kSBO = KB * 128;  // next 8-row group along M / N
-constexpr size_t kOperandBytes = (size_t)TM * KC * sizeof(float);  // 16 KiB
-constexpr size_t kSmemBytes = 4 * kOperandBytes + 64;
+constexpr size_t kOperandBytes = (size_t)TM * KC * sizeof(float);  // 8 KiB
+constexpr size_t kBufBytes = 4 * kOperandBytes;                     // A, B heads and tails
+constexpr size_t kSmemBytes = 2 * kBufBytes + 64;                   // two buffers, barriers
 
 __device__ __forceinline__ int core_offset(int row, int k) {
   return (((row >> 3) * KB + (k >> 2)) * 8 + (row & 7)) * 4 + (k & 3);
@@ -58,8 +59,8 @@ struct Anchor {
 // The anchor of one Gaussian on one axis of the tile starting at x0 (FP64: the phase
 // P (x0 - Q)/eps and its per-point step P h/eps as 32-bit fractions of a turn, so that
 // the phase at row r is the exact wrap-around sum u0 + r ud).
-__device__ __forceinline__ Anchor make_anchor(double x0, double h, double Q, double P, double cut,
-                                              double inv_eps, float2 cf) {
+__device__ __forceinline__ Anchor make_anchor(double x0, double h, double inv_h, double Q, double P,
+                                              double cut, double inv_eps, float2 cf) {
   const double inv_two_pi = 0.15915494309189535;
   const double d0 = x0 - Q;
   double t0 = P * d0 * inv_eps * inv_two_pi, td = P * h * inv_eps * inv_two_pi;
@@ -70,7 +71,7 @@ __device__ __forceinline__ Anchor make_anchor(double x0, double h, double Q, dou
   an.ud = (uint32_t)(unsigned long long)floor(td * 4294967296.0 + 0.5);
   an.d0 = (float)d0;
   an.h = (float)h;
-  double lo = ceil((-cut - d0) / h), hi = floor((cut - d0) / h);
+  double lo = ceil((-cut - d0) * inv_h), hi = floor((cut - d0) * inv_h);
   lo = lo < 0.0 ? 0.0 : lo;
   hi = hi > (double)(TM - 1) ? (double)(TM - 1) : hi;
   an.lo = (int)lo;
@@ -115,16 +116,12 @@ __global__ void __launch_bounds__(NTC) k_gather_tc(GridDev gd, const ShotDev* __
                                                    const int32_t* __restrict__ list, int64_t list_cap,
                                                    const int64_t* __restrict__ seg_off, int64_t ntiles,
                                                    int64_t seg, float* __restrict__ partial,
-                                                   int* status) {
+                                                   int* status, uint32_t tries) {
   const int64_t w = blockIdx.x;
   if (w >= seg_off[ntiles]) return;  // uniform over the CTA
   extern __shared__ __align__(1024) unsigned char smem[];
-  float* Ahi = reinterpret_cast<float*>(smem);
-  float* Alo = Ahi + TM * KC;
-  float* Bhi = Alo + TM * KC;
-  float* Blo = Bhi + TM * KC;
-  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + 4 * kOperandBytes);
-  uint32_t* tbase = reinterpret_cast<uint32_t*>(smem + 4 * kOperandBytes + 16);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + 2 * kBufBytes);  // one per buffer
+  uint32_t* tbase = reinterpret_cast<uint32_t*>(smem + 2 * kBufBytes + 16);
   const int tid = threadIdx.x, warp = tid >> 5;
   const int64_t t = tile_of_item(seg_off, ntiles, w);
   const int s = shot_of_tile(shots, nshots, t);
@@ -133,7 +130,8 @@ __global__ void __launch_bounds__(NTC) k_gather_tc(GridDev gd, const ShotDev* __
   int64_t a[2], b[2];
   tile_box<2>(gd, sh, t - sh.tile_off, a, b);
   if (tid == 0) {
-    tc::mbar_init(bar, 1);
+    tc::mbar_init(&bar[0], 1);
+    tc::mbar_init(&bar[1], 1);
     tc::fence_mbar_init();
   }
   if (warp == 0) {
@@ -149,30 +147,41 @@ __global__ void __launch_bounds__(NTC) k_gather_tc(GridDev gd, const ShotDev* __
   const int64_t l1 = min(min(off[t + 1], list_cap), l0 + seg);
   __shared__ Anchor anc[2][CHG];  // [axis][Gaussian of the chunk]
   const float inv_eps_f = (float)inv_eps;
+  // Chunks alternate between two operand buffers: while the MMAs of chunk c - 1 run, the
+  // factors of chunk c are made in the other buffer; before a buffer is overwritten the
+  // MMAs of chunk c - 2 (committed to that buffer's barrier) must be done.
   uint32_t chunks = 0;
-  bool ok = true;
+  bool gave_up = false;
   for (int64_t c0 = l0; c0 < l1; c0 += CHG) {
     const int nc = (int)((l1 - c0) < CHG ? (l1 - c0) : CHG);
-    // anchors: thread 2 gi + axis (the previous chunk's MMAs read only the operands)
-    if (tid < 2 * CHG) {
-      const int gi = tid >> 1, axis = tid & 1;
-      Anchor an = make_empty_anchor();
-      if (gi < nc) {
-        const int32_t g = list[c0 + gi];
-        const double Q = state[axis * ld + g], P = state[(2 + axis) * ld + g];
-        float2 cf = make_float2(1.f, 0.f);
-        if (axis == 0) {
-          const double2 c = coef[g];
-          cf = make_float2((float)c.x, (float)c.y);
-        }
-        const double x0 = axis == 0 ? gd.o[0] + (double)a[0] * gd.h[0] : gd.o[1] + (double)a[1] * gd.h[1];
-        an = make_anchor(x0, axis == 0 ? gd.h[0] : gd.h[1], Q, P, cut, inv_eps, cf);
+    const uint32_t buf = chunks & 1u;
+    float* Ahi = reinterpret_cast<float*>(smem + buf * kBufBytes);
+    float* Alo = Ahi + TM * KC;
+    float* Bhi = Alo + TM * KC;
+    float* Blo = Bhi + TM * KC;
+    // anchors: thread 2 gi + axis (the factors of the previous chunk are already made)
+    Anchor an = make_empty_anchor();
+    const int gi = tid >> 1, axis = tid & 1;
+    if (tid < 2 * CHG && gi < nc) {
+      const int32_t g = list[c0 + gi];
+      const double Q = state[axis * ld + g], P = state[(2 + axis) * ld + g];
+      float2 cf = make_float2(1.f, 0.f);
+      if (axis == 0) {
+        const double2 c = coef[g];
+        cf = make_float2((float)c.x, (float)c.y);
       }
-      if (chunks > 0) ok &= tc::mbar_wait_bounded(bar, (chunks - 1) & 1u, kMaxTries);
-      anc[axis][gi] = an;
-    } else if (chunks > 0) {
-      ok &= tc::mbar_wait_bounded(bar, (chunks - 1) & 1u, kMaxTries);
+      const double x0 = axis == 0 ? gd.o[0] + (double)a[0] * gd.h[0] : gd.o[1] + (double)a[1] * gd.h[1];
+      an = make_anchor(x0, gd.h[axis], gd.inv_h[axis], Q, P, cut, inv_eps, cf);
     }
+    // the CTA gives up as a whole; the two buffers' barriers then have at most one
+    // phase outstanding each
+    bool waited = true;
+    if (chunks >= 2) waited = tc::mbar_wait_bounded(&bar[buf], ((chunks - 2) >> 1) & 1u, tries);
+    if (!__syncthreads_and(waited)) {
+      gave_up = true;
+      break;
+    }
+    if (tid < 2 * CHG) anc[axis][gi] = an;
     __syncthreads();
     // operands: thread = row of the tile (x for A, z for B), four K values per store
     // A[x][2g] = Re X_g, A[x][2g+1] = -Im X_g; B[z][2g] = Re Z_g, B[z][2g+1] = Im Z_g
@@ -202,14 +211,23 @@ __global__ void __launch_bounds__(NTC) k_gather_tc(GridDev gd, const ShotDev* __
         tc::mma_tf32(tmem, tc::smem_desc(al + step, kLBO, kSBO), tc::smem_desc(bh + step, kLBO, kSBO),
                      idesc, 1u);
       }
-      tc::mma_commit(bar);
+      tc::mma_commit(&bar[buf]);
     }
     ++chunks;
   }
-  if (chunks > 0) ok &= tc::mbar_wait_bounded(bar, (chunks - 1) & 1u, kMaxTries);
+  // the last chunk's commit (and the one before it) may be outstanding
+  bool done = true;
+  if (!gave_up && chunks > 0) {
+    const uint32_t last = chunks - 1;
+    done = tc::mbar_wait_bounded(&bar[last & 1u], (last >> 1) & 1u, tries);
+  }
+  const bool ok = __syncthreads_and(done) && !gave_up;
   if (!ok) {
-    atomicOr(status, kStatusTimeout);
-    if (chunks > 0) tc::mbar_wait_bounded(bar, (chunks - 1) & 1u, kMaxTries);
+    if (tid == 0) atomicOr(status, kStatusTimeout);
+    // each barrier has at most one phase outstanding (chunks - 2 and chunks - 1): wait for
+    // both, in order, with the full budget before the accumulator's columns are released
+    for (uint32_t x = chunks >= 2 ? chunks - 2 : 0; x < chunks; ++x)
+      tc::mbar_wait_bounded(&bar[x & 1u], (x >> 1) & 1u, kMaxTries);
   }
   tc::fence_after_sync();
   // epilogue: warp w holds rows (x) 32w .. 32w+31, one row per thread, 128 columns (z)
@@ -299,7 +317,8 @@ cudaError_t launch_reconstruct_tc(fga_plan_s* p, double* u_dev) {
   k_gather_tc<<<items, NTC, kSmemBytes, p->stream>>>(
       p->grid, p->d_shots, p->nshots, p->kappa, p->d_state, (int64_t)p->g_cap, p->d_gcoef,
       p->d_tile_off, p->d_tile_list, (int64_t)p->list_cap, p->d_seg_off, p->ntiles,
-      segment_len_tc(p), reinterpret_cast<float*>(p->d_partial), p->d_status);
+      segment_len_tc(p), reinterpret_cast<float*>(p->d_partial), p->d_status,
+      p->wait_tries >= 0 ? (uint32_t)p->wait_tries : kMaxTries);
   k_reduce_tc<<<(unsigned)p->ntiles, 256, 0, p->stream>>>(p->grid, p->d_shots, p->nshots,
                                                           p->d_seg_off,
                                                           reinterpret_cast<float*>(p->d_partial),

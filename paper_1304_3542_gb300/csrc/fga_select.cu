@@ -130,7 +130,7 @@ __global__ void __launch_bounds__(NT) k_select_scatter(const ShotDev* __restrict
                                                        double tau2, const int64_t* __restrict__ blk,
                                                        int32_t* gshot, int64_t* gq, int32_t* gp,
                                                        double2* gpsi, const double2* __restrict__ psi_f1,
-                                                       double2* gpsi_f1) {
+                                                       double2* gpsi_f1, int64_t cap) {
   int64_t base = (int64_t)blockIdx.x * kScanBlock;
   int s = shot_of_block(shots, nshots, base);
   const ShotDev& sh = shots[s];
@@ -156,7 +156,7 @@ __global__ void __launch_bounds__(NT) k_select_scatter(const ShotDev* __restrict
   for (int w = 0; w < warp; ++w) wbase += warp_tot[w];
   int64_t pos = blk[blockIdx.x] + wbase + (x - c);
   for (int i = 0; i < PER; ++i) {
-    if (!f[i]) continue;
+    if (!f[i] || pos >= cap) continue;  // beyond the capacity: k_counts_finish flags it
     int64_t loc = e0 + i - sh.psi_off;
     int64_t ql = loc / sh.np, jp = loc - ql * sh.np;
     const int64_t qflat = q_flat<D>(sh, ql);
@@ -320,7 +320,7 @@ __global__ void __launch_bounds__(NT) k_topk_scatter(const ShotDev* __restrict__
                                                      const int64_t* __restrict__ blk_first,
                                                      int32_t* gshot, int64_t* gq, int32_t* gp,
                                                      double2* gpsi, const double2* __restrict__ psi_f1,
-                                                     double2* gpsi_f1) {
+                                                     double2* gpsi_f1, int64_t cap) {
   const int64_t base = (int64_t)blockIdx.x * kScanBlock;
   const int s = shot_of_block(shots, nshots, base);
   const ShotDev& sh = shots[s];
@@ -360,8 +360,8 @@ __global__ void __launch_bounds__(NT) k_topk_scatter(const ShotDev* __restrict__
   for (int i = 0; i < PER; ++i) {
     bool keep = g[i];
     if (q[i]) keep = eq_before < take;
-    if (keep) {
-      const int64_t pos = sh.g_off + gt_before + (eq_before < take ? eq_before : take);
+    const int64_t pos = sh.g_off + gt_before + (eq_before < take ? eq_before : take);
+    if (keep && pos < cap) {
       const int64_t loc = e0 + i - sh.psi_off;
       const int64_t ql = loc / sh.np, jp = loc - ql * sh.np;
       gshot[pos] = s;
@@ -373,6 +373,26 @@ __global__ void __launch_bounds__(NT) k_topk_scatter(const ShotDev* __restrict__
     if (g[i]) ++gt_before;
     if (q[i]) ++eq_before;
   }
+}
+
+// Pipeline graph (one thread): clamp every shot's segment to the Gaussian capacity
+// (flagging kStatusCapacity if it had to), and write the total G and the work-order
+// multiplier for the ray kernel.
+__global__ void k_counts_finish(ShotDev* shots, int nshots, int64_t cap, int64_t* gm, int* status) {
+  if (blockIdx.x != 0 || threadIdx.x != 0) return;
+  int64_t G = 0;
+  bool clamped = false;
+  for (int s = 0; s < nshots; ++s) {
+    const int64_t off = shots[s].g_off, cnt = shots[s].g_cnt;
+    const int64_t room = cap - off > 0 ? cap - off : 0;
+    const int64_t c = cnt < room ? cnt : room;
+    clamped = clamped || c != cnt;
+    shots[s].g_cnt = c;
+    G = off + c > G ? off + c : G;
+  }
+  if (clamped) atomicOr(status, kStatusCapacity);
+  gm[0] = G;
+  gm[1] = (int64_t)work_order_mult_of(G);
 }
 
 // Per-shot Gaussian segment [g_off, g_off + g_cnt) from the scanned block offsets.
@@ -441,7 +461,7 @@ cudaError_t launch_select(fga_plan_s* p) {
     scatter<<<(unsigned)p->nblocks, NT, 0, p->stream>>>(p->d_shots, p->nshots, p->d_psi, p->d_topk,
                                                         p->d_blk, p->d_blk_eq, p->d_blk_first,
                                                         p->d_gshot, p->d_gq, p->d_gp, p->d_gpsi,
-                                                        p->d_psi_f1, p->d_gpsi_f1);
+                                                        p->d_psi_f1, p->d_gpsi_f1, (int64_t)p->g_cap);
     p->launches += 1;
     return cudaGetLastError();
   }
@@ -449,7 +469,15 @@ cudaError_t launch_select(fga_plan_s* p) {
                                    : (p->grid.dim == 2 ? k_select_scatter<2> : k_select_scatter<3>);
   scatter<<<(unsigned)p->nblocks, NT, 0, p->stream>>>(p->d_shots, p->nshots, p->d_psi, p->d_max2,
                                                       tau2, p->d_blk, p->d_gshot, p->d_gq, p->d_gp,
-                                                      p->d_gpsi, p->d_psi_f1, p->d_gpsi_f1);
+                                                      p->d_gpsi, p->d_psi_f1, p->d_gpsi_f1,
+                                                      (int64_t)p->g_cap);
+  p->launches += 1;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_counts_finish(fga_plan_s* p) {
+  k_counts_finish<<<1, 1, 0, p->stream>>>(p->d_shots, p->nshots, (int64_t)p->g_cap, p->d_gm,
+                                          p->d_status);
   p->launches += 1;
   return cudaGetLastError();
 }

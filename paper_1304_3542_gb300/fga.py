@@ -21,7 +21,12 @@ from . import build as _build
 
 FGA_OK = 0
 FGA_ERR_INVALID = 1
+FGA_ERR_OOM = 2
+FGA_ERR_CUDA = 3
+FGA_ERR_TIMEOUT = 4
 FGA_ERR_STATE = 5
+FGA_ERR_NUMERIC = 6
+FGA_ERR_CAPACITY = 7
 FGA_FP64 = 0
 FGA_MIXED_TF32X3 = 1
 FGA_MIXED_BF16X3 = 2
@@ -115,6 +120,10 @@ def load(build_if_missing: bool = True):
     L.fga_set_tuning.restype = ci
     L.fga_run_graph.argtypes = [P, P]
     L.fga_run_graph.restype = ci
+    L.fga_run_pipeline.argtypes = [P, P, P, P]
+    L.fga_run_pipeline.restype = ci
+    L.fga_set_wait_budget.argtypes = [P, i64]
+    L.fga_set_wait_budget.restype = ci
     L.fga_grad.argtypes = [P, P, P]
     L.fga_grad.restype = ci
     L.fga_reconstruct_static.argtypes = [ci, P, P, P, P, ctypes.c_double, ctypes.c_double, i64,
@@ -254,6 +263,22 @@ class Plan:
     def run_graph(self, out):
         """propagate + reconstruct into the device tensor out, as one CUDA graph replay."""
         self._check(self._L.fga_run_graph(self._h, _ptr(out)), "fga_run_graph")
+        return out
+
+    def set_wait_budget(self, tries: int):
+        """fga_set_wait_budget: polls of a tensor-core completion wait before giving up
+        (< 0: defaults; 0: give up at once)."""
+        self._check(self._L.fga_set_wait_budget(self._h, int(tries)), "fga_set_wait_budget")
+
+    def run_pipeline(self, u0, u1, out):
+        """decompose + propagate + reconstruct of every shot as one CUDA graph replay
+        (fga_run_pipeline): device tensors u0, u1 in, out overwritten."""
+        n = self.nshots * self.npts
+        _check_f64(u0, n, "u0")
+        _check_f64(u1, n, "u1")
+        _check_f64(out, n, "out")
+        self._check(self._L.fga_run_pipeline(self._h, _ptr(u0), _ptr(u1), _ptr(out)),
+                    "fga_run_pipeline")
         return out
 
     def autotune(self, out):

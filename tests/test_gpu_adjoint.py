@@ -12,7 +12,7 @@
   the action, and the derivative of the branch split through c(q)) for the same
   frozen set. This is the dot-product test of the GPU's reverse mode against the
   oracle's forward mode: w = traces (so <w, J v> = <grad J, v>) and random w, smooth
-  v and single cells, <= 1e-10 relative; also at the shape of the layered adjoint
+  v and single cells, <= 1e-12 relative; also at the shape of the layered adjoint
   workload (T = 2 s, 368 receivers, 501 samples) with the N largest Gaussians.
 kappa = 8 so that Gaussians crossing a window edge change J by e^{-32} only. The lens
 centre is kept off the spline's knot lines: in the symmetric lens centred on a knot
@@ -145,7 +145,7 @@ def test_adjoint_directional_derivatives():
         assert abs(grad.ravel()[f] - fd) <= 1e-5 * abs(fd) + 1e-12 * J0, (grad.ravel()[f], fd)
 
 
-DOT_TOL = 1e-10
+DOT_TOL = 1e-12
 
 
 def _oracle_keys(prob, c, shot=0, rows=None):
