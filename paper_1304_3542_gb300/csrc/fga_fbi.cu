@@ -111,7 +111,7 @@ __device__ __forceinline__ double psi_plus(const ShotDev& sh, int64_t jp, double
   double r = sh.eps / (cq * pn);
   t = make_double2(-0.5 * r * p1.y, 0.5 * r * p1.x);
   out = make_double2(0.5 * p0.x + t.x, 0.5 * p0.y + t.y);
-  return out.x * out.x + out.y * out.y;
+  return abs2_rn(out);
 }
 
 // TF32 head and FP32 tail of a complex value: (Re head, Re tail, Im head, Im tail).
@@ -758,7 +758,7 @@ __global__ void __launch_bounds__(FNT) k_fbi_stage2_tc(GridDev gd, const ShotDev
         const float f2 = fmaf(ox, ox, oy * oy);
         if (f2 >= 0.999999f * fmax32) {  // false for NaN
           fmax32 = fmaxf(fmax32, f2);
-          const unsigned long long a2 = (unsigned long long)__double_as_longlong(o.x * o.x + o.y * o.y);
+          const unsigned long long a2 = (unsigned long long)__double_as_longlong(abs2_rn(o));
           if (a2 <= 0x7ff0000000000000ull && a2 > mymax) mymax = a2;  // NaN left out, as fmax does
         }
       }

@@ -26,7 +26,7 @@ namespace fga {
 namespace {
 
 constexpr int TM = 128;       // tile edge (x = GEMM M, z = GEMM N)
-constexpr int CHG = 8;        // Gaussians per chunk -> K = 16
+constexpr int CHG = 16;       // Gaussians per chunk -> K = 32
 constexpr int KC = 2 * CHG;   // GEMM K per chunk
 constexpr int KB = KC / 4;    // 16-byte core matrices along K (tf32: 4 per core row)
 constexpr int64_t SEGM = 2048;  // default Gaussians per work item
@@ -35,9 +35,9 @@ constexpr uint32_t kMaxTries = 1u << 22;
 // core-matrix (8 rows x 16 bytes) strides of the K-major operand tiles
 constexpr uint32_t kLBO = 128;       // next core matrix along K
 constexpr uint32_t kSBO = KB * 128;  // next 8-row group along M / N
-constexpr size_t kOperandBytes = (size_t)TM * KC * sizeof(float);  // 8 KiB
+constexpr size_t kOperandBytes = (size_t)TM * KC * sizeof(float);  // 16 KiB
 constexpr size_t kBufBytes = 4 * kOperandBytes;                     // A, B heads and tails
-constexpr size_t kSmemBytes = 2 * kBufBytes + 64;                   // two buffers, barriers
+constexpr size_t kSmemBytes = kBufBytes + 64;                       // operands, barrier
 
 __device__ __forceinline__ int core_offset(int row, int k) {
   return (((row >> 3) * KB + (k >> 2)) * 8 + (row & 7)) * 4 + (k & 3);
@@ -120,8 +120,8 @@ __global__ void __launch_bounds__(NTC) k_gather_tc(GridDev gd, const ShotDev* __
   const int64_t w = blockIdx.x;
   if (w >= seg_off[ntiles]) return;  // uniform over the CTA
   extern __shared__ __align__(1024) unsigned char smem[];
-  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + 2 * kBufBytes);  // one per buffer
-  uint32_t* tbase = reinterpret_cast<uint32_t*>(smem + 2 * kBufBytes + 16);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + kBufBytes);
+  uint32_t* tbase = reinterpret_cast<uint32_t*>(smem + kBufBytes + 16);
   const int tid = threadIdx.x, warp = tid >> 5;
   const int64_t t = tile_of_item(seg_off, ntiles, w);
   const int s = shot_of_tile(shots, nshots, t);
@@ -130,8 +130,7 @@ __global__ void __launch_bounds__(NTC) k_gather_tc(GridDev gd, const ShotDev* __
   int64_t a[2], b[2];
   tile_box<2>(gd, sh, t - sh.tile_off, a, b);
   if (tid == 0) {
-    tc::mbar_init(&bar[0], 1);
-    tc::mbar_init(&bar[1], 1);
+    tc::mbar_init(bar, 1);
     tc::fence_mbar_init();
   }
   if (warp == 0) {
@@ -147,18 +146,16 @@ __global__ void __launch_bounds__(NTC) k_gather_tc(GridDev gd, const ShotDev* __
   const int64_t l1 = min(min(off[t + 1], list_cap), l0 + seg);
   __shared__ Anchor anc[2][CHG];  // [axis][Gaussian of the chunk]
   const float inv_eps_f = (float)inv_eps;
-  // Chunks alternate between two operand buffers: while the MMAs of chunk c - 1 run, the
-  // factors of chunk c are made in the other buffer; before a buffer is overwritten the
-  // MMAs of chunk c - 2 (committed to that buffer's barrier) must be done.
+  // One operand buffer (three CTAs share an SM, so one CTA's factors are made while
+  // another's MMAs run); before it is overwritten the previous chunk's MMAs must be done.
+  float* Ahi = reinterpret_cast<float*>(smem);
+  float* Alo = Ahi + TM * KC;
+  float* Bhi = Alo + TM * KC;
+  float* Blo = Bhi + TM * KC;
   uint32_t chunks = 0;
   bool gave_up = false;
   for (int64_t c0 = l0; c0 < l1; c0 += CHG) {
     const int nc = (int)((l1 - c0) < CHG ? (l1 - c0) : CHG);
-    const uint32_t buf = chunks & 1u;
-    float* Ahi = reinterpret_cast<float*>(smem + buf * kBufBytes);
-    float* Alo = Ahi + TM * KC;
-    float* Bhi = Alo + TM * KC;
-    float* Blo = Bhi + TM * KC;
     // anchors: thread 2 gi + axis (the factors of the previous chunk are already made)
     Anchor an = make_empty_anchor();
     const int gi = tid >> 1, axis = tid & 1;
@@ -173,10 +170,9 @@ __global__ void __launch_bounds__(NTC) k_gather_tc(GridDev gd, const ShotDev* __
       const double x0 = axis == 0 ? gd.o[0] + (double)a[0] * gd.h[0] : gd.o[1] + (double)a[1] * gd.h[1];
       an = make_anchor(x0, gd.h[axis], gd.inv_h[axis], Q, P, cut, inv_eps, cf);
     }
-    // the CTA gives up as a whole; the two buffers' barriers then have at most one
-    // phase outstanding each
+    // the CTA gives up as a whole, with at most the previous commit outstanding
     bool waited = true;
-    if (chunks >= 2) waited = tc::mbar_wait_bounded(&bar[buf], ((chunks - 2) >> 1) & 1u, tries);
+    if (chunks > 0) waited = tc::mbar_wait_bounded(bar, (chunks - 1) & 1u, tries);
     if (!__syncthreads_and(waited)) {
       gave_up = true;
       break;
@@ -211,23 +207,18 @@ __global__ void __launch_bounds__(NTC) k_gather_tc(GridDev gd, const ShotDev* __
         tc::mma_tf32(tmem, tc::smem_desc(al + step, kLBO, kSBO), tc::smem_desc(bh + step, kLBO, kSBO),
                      idesc, 1u);
       }
-      tc::mma_commit(&bar[buf]);
+      tc::mma_commit(bar);
     }
     ++chunks;
   }
-  // the last chunk's commit (and the one before it) may be outstanding
   bool done = true;
-  if (!gave_up && chunks > 0) {
-    const uint32_t last = chunks - 1;
-    done = tc::mbar_wait_bounded(&bar[last & 1u], (last >> 1) & 1u, tries);
-  }
+  if (!gave_up && chunks > 0) done = tc::mbar_wait_bounded(bar, (chunks - 1) & 1u, tries);
   const bool ok = __syncthreads_and(done) && !gave_up;
   if (!ok) {
     if (tid == 0) atomicOr(status, kStatusTimeout);
-    // each barrier has at most one phase outstanding (chunks - 2 and chunks - 1): wait for
-    // both, in order, with the full budget before the accumulator's columns are released
-    for (uint32_t x = chunks >= 2 ? chunks - 2 : 0; x < chunks; ++x)
-      tc::mbar_wait_bounded(&bar[x & 1u], (x >> 1) & 1u, kMaxTries);
+    // every earlier phase was observed, so only the last commit can be outstanding: wait
+    // for it with the full budget before the accumulator's columns are released
+    tc::mbar_wait_bounded(bar, (chunks - 1) & 1u, kMaxTries);
   }
   tc::fence_after_sync();
   // epilogue: warp w holds rows (x) 32w .. 32w+31, one row per thread, 128 columns (z)

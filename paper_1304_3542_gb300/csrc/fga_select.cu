@@ -63,7 +63,7 @@ __device__ __forceinline__ bool keep(const ShotDev& sh, const double2* psi, int6
   int64_t jp = loc % sh.np;
   if (!p_valid<D>(sh, jp)) return false;
   double2 v = psi[e];
-  return v.x * v.x + v.y * v.y >= thr2;
+  return abs2_rn(v) >= thr2;
 }
 
 template <int D>
@@ -182,7 +182,7 @@ __device__ __forceinline__ unsigned long long topk_key(const ShotDev& sh, const 
   if (loc < 0 || loc >= sh.psi_len) return 0ull;
   if (!p_valid<D>(sh, loc % sh.np)) return 0ull;
   const double2 v = psi[e];
-  return (unsigned long long)__double_as_longlong(v.x * v.x + v.y * v.y) + 1ull;
+  return (unsigned long long)__double_as_longlong(abs2_rn(v)) + 1ull;
 }
 
 // topk[s] = {prefix, mask, to_take, take_all}
