@@ -534,7 +534,8 @@ def run_reference(args, rank, world):
     cores = os.cpu_count() or 1
     vals, ests = [], []
     for i in range(args.warmup + args.steps):
-        est, desc, evals, spent = oracle_sample(prob, 256, cores)
+        # the same sample (size and seed) as the cpu_baseline leg of the GPU line
+        est, desc, evals, spent = oracle_sample(prob, args.cpu_sample, cores)
         if i >= args.warmup:
             vals.append(evals / est)
             ests.append(est)
@@ -554,7 +555,10 @@ def run_reference(args, rank, world):
         "vs_baseline": None,
         "dtype": "f64",
         "data": "synthetic (seeded layered model and Ricker ring; no dataset)",
-        "config": {"workload": workload_name(prob), "precision": "fp64",
+        "config": {"workload": workload_name(prob), "grid": list(prob.n),
+                   "eps_km": prob.shots[0].eps, "q_stride": list(prob.shots[0].q_stride),
+                   "box": list(prob.shots[0].box), "tau": prob.tau, "kappa": prob.kappa,
+                   "precision": "fp64",
                    "parallelism": "CPU oracle, OpenMP over Gaussians / grid points"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": desc},
