@@ -368,18 +368,19 @@ fga_status fga_run_pipeline(fga_plan_t plan, const double* u0, const double* u1,
  * Errors: FGA_ERR_INVALID (tries >= 2^32), FGA_ERR_STATE. */
 fga_status fga_set_wait_budget(fga_plan_t plan, int64_t tries);
 
-/* Measured fused multiply-add throughput of the current GPU/* Measured fused multiply-add throughput of the current GPU/* Budget of the bounded waits in the tensor-core kernels (FGA_MIXED_TF32X3: FBI stage 2
- * and the reconstruction), as polls of the completion barrier of the previous chunk of
- * MMAs before the CTA gives up (no counterpart in the paper: failure detection of the
- * library). tries < 0 restores the defaults (2^22 polls, seconds); 0 makes every such
- * wait give up at once, which exercises the give-up path. A CTA that gives up issues no
- * further MMA, waits for its one outstanding commit with the default budget, releases
- * its tensor memory and sets the plan's status word; the next fga_sync (or call with a
- * host output) returns FGA_ERR_TIMEOUT and marks the plan failed.
- * Errors: FGA_ERR_INVALID (tries >= 2^32), FGA_ERR_STATE. */
-fga_status fga_set_wait_budget(fga_plan_t plan, int64_t tries);
+/* How fga_grad keeps the ray states for its reverse sweep (no counterpart in the paper:
+ * the memory/recomputation trade-off of the discrete adjoint). mode 0 (the default):
+ * every state and RK4 stage state of each resident thread's ray is recorded by the
+ * forward pass when that takes at most half of the free device memory (4 (nsteps + 1)
+ * states of nfields doubles per resident thread of the adjoint kernel, kept by the plan
+ * for later calls), else mode 1's scheme. mode 1: checkpoints every
+ * kseg = ceil(sqrt(nsteps)) steps, and each segment's states recomputed from its
+ * checkpoint during the reverse sweep (one more forward step per ray step, about
+ * 5 (kseg + 1) states per thread). Both give the same gradient up to the order of the
+ * atomic additions. Errors: FGA_ERR_INVALID (mode not 0 or 1), FGA_ERR_STATE. */
+fga_status fga_set_adjoint_checkpointing(fga_plan_t plan, int mode);
 
-/* Measured fused multiply-add throughput of the current GPU/* Measured fused multiply-add throughput of the current GPU (no counterpart in the
+/* Measured fused multiply-add throughput of the current GPU (no counterpart in the
  * paper: the roofline denominator of the FP64-bound kernels). bits = 64 (DFMA) or 32
  * (FFMA); each of 8 blocks of 256 threads per SM runs 8 independent FMA chains for
  * iters x 16 rounds, timed with CUDA events on the legacy default stream after one

@@ -164,14 +164,21 @@ __global__ void __launch_bounds__(128) k_adjoint(GridDev gd, const ShotDev* __re
     }
     double y[NF];
     ray_init<D>(gd, sh, has ? gq[g] : 0, has ? gp[g] : 0, y);
-    // forward with checkpoints every kseg steps; nend = the step the ray stopped at
+    // forward with checkpoints every kseg steps; nend = the step the ray stopped at. With
+    // a single segment (kseg > nsteps) this pass records every state and the stage states
+    // of every step directly, and the reverse sweep recomputes nothing.
+    const bool single = kseg > nsteps;
     int64_t nend = 0;
     bool run = has;
     for (int64_t step = 0; __any_sync(kFull, run); ++step) {
       if (!run) continue;
-      if (step % kseg == 0)
+      if (single) {
+#pragma unroll
+        for (int f = 0; f < NF; ++f) slot(ncheck + step, f) = y[f];
+      } else if (step % kseg == 0) {
 #pragma unroll
         for (int f = 0; f < NF; ++f) slot(step / kseg, f) = y[f];
+      }
       bool done = step >= nsteps;
       if (!done && !integrate_exited) {
 #pragma unroll
@@ -182,6 +189,11 @@ __global__ void __launch_bounds__(128) k_adjoint(GridDev gd, const ShotDev* __re
       if (done) {
         nend = step;
         run = false;
+      } else if (single) {
+        rk4_step_record<D>(gd, y, dt, [&](int st, const double* zz) {
+#pragma unroll
+          for (int f = 0; f < NF; ++f) slot(ncheck + kseg + 3 * step + st, f) = zz[f];
+        });
       } else {
         rk4_step<D>(gd, C, y, dt);
       }
@@ -215,7 +227,7 @@ __global__ void __launch_bounds__(128) k_adjoint(GridDev gd, const ShotDev* __re
           });
       }
     };
-    int64_t seg_loaded = -1;
+    int64_t seg_loaded = single ? 0 : -1;
     for (int64_t nn = nend_w;; --nn) {
       const bool act = has && nn <= nend;
       const int64_t j = nn / kseg;
@@ -313,6 +325,11 @@ int64_t adjoint_slices(fga_plan_s* p, int64_t nthreads) {
   return part_slices(std::max<int64_t>(nthreads / 128, 1), p->grid.npts);
 }
 
+// Width (in steps) of the stop-step buckets the Gaussians are sorted by.
+int64_t adjoint_sort_width(int64_t nsteps) {
+  return std::max<int64_t>(1, std::min<int64_t>(16, nsteps / 64));
+}
+
 cudaError_t launch_adjoint(fga_plan_s* p, const double* residual, double* gradC, double* scratch,
                            int64_t nthreads, int64_t kseg, int64_t ncheck) {
   cudaError_t e = cudaMemsetAsync(p->d_steps + 1, 0, sizeof(unsigned long long), p->stream);
@@ -323,7 +340,7 @@ cudaError_t launch_adjoint(fga_plan_s* p, const double* residual, double* gradC,
   const int64_t slices = adjoint_slices(p, nthreads);
   if (p->part_cap < (size_t)(slices * len)) return cudaErrorInvalidValue;
   // Gaussians by decreasing stop step
-  const int64_t width = kseg, nb = p->nsteps / width + 1;
+  const int64_t width = adjoint_sort_width(p->nsteps), nb = p->nsteps / width + 1;
   if (p->adj_bucket_cap < (size_t)(nb + 1)) return cudaErrorInvalidValue;
   e = cudaMemsetAsync(p->d_adj_bucket, 0, sizeof(int64_t) * (nb + 1), p->stream);
   if (e != cudaSuccess) return e;

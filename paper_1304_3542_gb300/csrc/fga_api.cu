@@ -1012,6 +1012,14 @@ fga_status fga_set_wait_budget(fga_plan_t p, int64_t tries) {
   return FGA_OK;
 }
 
+fga_status fga_set_adjoint_checkpointing(fga_plan_t p, int mode) {
+  fga_status st = check_usable(p);
+  if (st != FGA_OK) return st;
+  if (mode != 0 && mode != 1) return fail(p, FGA_ERR_INVALID, "mode must be 0 or 1");
+  p->adj_force_segments = mode;
+  return FGA_OK;
+}
+
 fga_status fga_sync(fga_plan_t p) {
   fga_status st = check_usable(p);
   if (st != FGA_OK) return st;
@@ -1335,11 +1343,23 @@ fga_status fga_grad(fga_plan_t p, const double* residual, double* grad) {
   CUDA_OR_FAIL(p, fga::launch_gather_rows(p, d_res, p->d_rx_perm, (int64_t)p->nshots * p->rx.nrec,
                                           p->rx.nrx, p->d_resid_int));
   d_res = p->d_resid_int;
-  const int64_t kseg = std::max<int64_t>(1, (int64_t)std::ceil(std::sqrt((double)std::max<int64_t>(p->nsteps, 1))));
-  const int64_t ncheck = p->nsteps / kseg + 2;
   const int64_t nthr = fga::adjoint_threads(p);
   if (nthr <= 0) return fail(p, FGA_ERR_CUDA, "occupancy query for the adjoint kernel failed", true);
-  // checkpoints, the segment's states and the stage states of its steps
+  // Every state and stage state of a ray recorded by the forward pass (one segment) when
+  // that fits in half of the free device memory; otherwise checkpoints every
+  // kseg ~ sqrt(nsteps) steps and one segment of kseg states (and their stage states)
+  // recomputed at a time. Per resident thread: ncheck checkpoints + 4 kseg states.
+  int64_t kseg = p->nsteps + 1, ncheck = 0;
+  {
+    size_t free_b = 0, total_b = 0;
+    CUDA_OR_FAIL(p, cudaMemGetInfo(&free_b, &total_b));
+    const double full = (double)nthr * (double)(4 * kseg) * (double)p->nfields * sizeof(double);
+    const double avail = (double)free_b + (double)p->adj_scratch_cap * sizeof(double);
+    if (p->adj_force_segments || full > 0.5 * avail) {
+      kseg = std::max<int64_t>(1, (int64_t)std::ceil(std::sqrt((double)std::max<int64_t>(p->nsteps, 1))));
+      ncheck = p->nsteps / kseg + 2;
+    }
+  }
   const size_t need = (size_t)nthr * (size_t)(ncheck + 4 * kseg) * (size_t)p->nfields;
   CUDA_OR_FAIL(p, grow(&p->d_adj_scratch, &p->adj_scratch_cap, need));
   double* dst = grad;
@@ -1350,7 +1370,8 @@ fga_status fga_grad(fga_plan_t p, const double* residual, double* grad) {
   }
   CUDA_OR_FAIL(p, grow(&p->d_part, &p->part_cap,
                        (size_t)(fga::adjoint_slices(p, nthr) * gd.npts)));
-  CUDA_OR_FAIL(p, grow(&p->d_adj_bucket, &p->adj_bucket_cap, (size_t)(p->nsteps / kseg + 2)));
+  CUDA_OR_FAIL(p, grow(&p->d_adj_bucket, &p->adj_bucket_cap,
+                       (size_t)(p->nsteps / fga::adjoint_sort_width(p->nsteps) + 2)));
   CUDA_OR_FAIL(p, fga::launch_adjoint(p, d_res, dst, p->d_adj_scratch, nthr, kseg, ncheck));
   if (p->interp == FGA_BSPLINE_INTERP) {
     // dJ/dc = B^{-T} dJ/dC for C = B^{-1} c; B is symmetric, so this is the prefilter again

@@ -242,20 +242,30 @@ __device__ __forceinline__ void medium_cell(const GridDev& gd, const double* __r
 // cell n is constant, all its derivative coefficients being exact zeros). A position a
 // rounding error below a cell boundary evaluates the neighbouring cell's polynomial at
 // offset h: the spline is C2 there, so the two agree to within rounding.
-__device__ __forceinline__ int64_t medium_cell_of(const GridDev& gd, int k, double x, double& off) {
+// clamped is set where the position lies beyond cell -1 or n (the spline is constant
+// along the axis there; the cell's cubic coefficient along the axis need not vanish, so
+// a third derivative along the axis must be taken as 0 there, not from the cell).
+__device__ __forceinline__ int64_t medium_cell_of(const GridDev& gd, int k, double x, double& off,
+                                                  bool& clamped) {
   if (gd.periodic[k]) {
     const double u = (x - gd.o[k]) * gd.inv_h[k];
     double fl = floor(u);
     off = (u - fl) * gd.h[k];
     int64_t i = (int64_t)fl % gd.n[k];
+    clamped = false;
     return (i < 0 ? i + gd.n[k] : i) + 1;
   }
   const double u = fma(x, gd.inv_h[k], gd.mo[k]);
   const int i = __double2int_rd(u);
   const int ic = min(max(i, -1), (int)gd.n[k]);
   off = (u - (double)ic) * gd.h[k];
-  if (i != ic) off = 0.0;
+  clamped = i != ic;
+  if (clamped) off = 0.0;
   return (int64_t)ic + 1;
+}
+__device__ __forceinline__ int64_t medium_cell_of(const GridDev& gd, int k, double x, double& off) {
+  bool clamped;
+  return medium_cell_of(gd, k, x, off, clamped);
 }
 
 // Value, first derivative and half the second derivative of the cubic

@@ -147,7 +147,8 @@ __device__ __forceinline__ void medium_ad_transpose(const GridDev& gd, const Med
   }
 }
 
-// yb += (d f/d y)^T kb and gradC += (d f/d C)^T kb for the right-hand side f of rhs<D>.
+// yb += (d f/d y)^T kb and gradC += (d f/d C)^T kb for the right-hand side f of rhs<D>
+// (1D and 3D; 2D uses rhs2_vjp below).
 template <int D>
 __device__ void rhs_vjp(const GridDev& gd, const double* __restrict__ C, const double* y,
                         const double* kb, double* yb, double* __restrict__ gradC) {
@@ -162,7 +163,7 @@ __device__ void rhs_vjp(const GridDev& gd, const double* __restrict__ C, const d
     P[i] = y[Lo::P + i];
     pn2 += P[i] * P[i];
   }
-  const double rinv = rsqrt(pn2), pn = pn2 * rinv, cop = m.c * rinv;
+  const double rinv = rsqrt_nr(pn2), pn = pn2 * rinv, cop = m.c * rinv;
   double ng = 0, Qd[D];
 #pragma unroll
   for (int i = 0; i < D; ++i) {
@@ -213,7 +214,8 @@ __device__ void rhs_vjp(const GridDev& gd, const double* __restrict__ C, const d
     Dt = Z[0][0] * Z[1][1] - Z[0][1] * Z[1][0];
   }
   const double dd = Dt.r * Dt.r + Dt.i * Dt.i;
-  const cx rD = mk(Dt.r / dd, -Dt.i / dd);
+  const double idd = rcp_nr(dd);
+  const cx rD = mk(Dt.r * idd, -Dt.i * idd);
   const cx q = N * rD;
   const cx F = mk(ng + 0.5 * q.r, 0.5 * q.i);
   const cx a = mk(y[Lo::aR], y[Lo::aI]);
@@ -369,6 +371,223 @@ __device__ void rhs_vjp(const GridDev& gd, const double* __restrict__ C, const d
   // S does not enter f
 }
 
+// Scatter of the adjoints (cb, gb, Kb) of (c, grad c, Hessian) at x to the 16 spline
+// coefficients around x (2D); the tap weights are computed again from x rather than
+// kept from the forward evaluation (they would hold 48 registers through the whole
+// vector-Jacobian product). kxz is the adjoint of the mixed derivative (both K entries).
+// Coefficient (a, b) receives al_a w_b + be_a w'_b + ga_a w''_b with
+// al_a = cb w_a + gx w'_a + kxx' w''_a, be_a = gz w_a + kxz' w'_a, ga_a = kzz' w_a (the
+// 1/h factors of the derivative weights folded into the adjoints).
+__device__ __forceinline__ void medium_scatter2(const GridDev& gd, const double* x, double cb,
+                                                double gb0, double gb1, double kxx, double kxz,
+                                                double kzz, double* __restrict__ gradC) {
+  double w[2][4], dw[2][4], ddw[2][4];
+  int64_t idx[2][4];
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    const double u = (x[k] - gd.o[k]) * gd.inv_h[k];
+    const double fl = floor(u);
+    spline_taps(u - fl, w[k], dw[k], ddw[k]);
+    const int64_t i0 = (int64_t)fl - 1;
+#pragma unroll
+    for (int a = 0; a < 4; ++a) idx[k][a] = tap_index(i0 + a, gd.n[k], gd.periodic[k]);
+  }
+  const double ix = gd.inv_h[0], iz = gd.inv_h[1];
+  const double gx = gb0 * ix, gz = gb1 * iz;
+  const double kx2 = kxx * (ix * ix), kxz2 = kxz * (ix * iz), kz2 = kzz * (iz * iz);
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    const double al = fma(kx2, ddw[0][a], fma(gx, dw[0][a], cb * w[0][a]));
+    const double be = fma(kxz2, dw[0][a], gz * w[0][a]);
+    const double ga = kz2 * w[0][a];
+    double* row = gradC + idx[0][a] * gd.n[1];
+#pragma unroll
+    for (int b = 0; b < 4; ++b)
+      red_add_f64(row + idx[1][b], fma(ga, ddw[1][b], fma(be, dw[1][b], al * w[1][b])));
+  }
+}
+
+// c, grad c, Hessian and the third derivatives (xxx, xxz, xzz, zzz) of c at x (2D) from
+// the per-cell polynomial table gd.tab, by Horner's scheme with derivatives: the same
+// cell and arithmetic as the ray kernels' medium_eval_tab for c, grad c and the Hessian.
+__device__ __forceinline__ void medium_tab3(const GridDev& gd, const double* x, double& c,
+                                            double& g0, double& g1, double& K00, double& K01,
+                                            double& K11, double& T0, double& T1, double& T2,
+                                            double& T3) {
+  double tx, tz;
+  bool clx, clz;
+  const int64_t cx = medium_cell_of(gd, 0, x[0], tx, clx);
+  const int64_t cz = medium_cell_of(gd, 1, x[1], tz, clz);
+  const double2* cell = reinterpret_cast<const double2*>(gd.tab) + (cx * (gd.n[1] + 2) + cz) * 8;
+  // row k (power k of tx): its cubic in tz with d/dz and (d2/dz2)/2, and its tz^3 coefficient
+  double r[4], rz[4], hz[4], a3[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const double2 a01 = __ldg(cell + 2 * k), a23 = __ldg(cell + 2 * k + 1);
+    horner3(a01.x, a01.y, a23.x, a23.y, tz, r[k], rz[k], hz[k]);
+    a3[k] = a23.y;
+  }
+  double cxx_h, cxxz_h, czz_h, cxzz, dummy;
+  horner3(r[0], r[1], r[2], r[3], tx, c, g0, cxx_h);
+  horner3(rz[0], rz[1], rz[2], rz[3], tx, g1, K01, cxxz_h);
+  horner3(hz[0], hz[1], hz[2], hz[3], tx, czz_h, cxzz, dummy);
+  K00 = 2.0 * cxx_h;
+  K11 = 2.0 * czz_h;
+  // beyond the clamped edge of an open axis c is constant along it: the pure third
+  // derivative along that axis is 0 (the mixed ones vanish there with the cell's first and
+  // second derivative coefficients)
+  T0 = clx ? 0.0 : 6.0 * r[3];
+  T1 = 2.0 * cxxz_h;
+  T2 = 2.0 * cxzz;
+  T3 = clz ? 0.0 : 6.0 * fma(fma(fma(a3[3], tx, a3[2]), tx, a3[1]), tx, a3[0]);
+}
+
+// The vector-Jacobian product of rhs2 (the 2D right-hand side) written out with scalars,
+// the same derivative as the generic rhs_vjp term by term (the reverse of
+//   dQ/dt = c n, dP/dt = -|P| g, dA_jk/dt = n_k u_j + (c/|P|) B_jk with
+//   u_j = (A g)_j - (c/|P|)(B n)_j, dB_jk/dt = (A Km)_jk - g_k (B n)_j with Km = -|P| K,
+//   da/dt = a (n.g + N conj(det Z)/(2 |det Z|^2)), N = tr(adj(Z) dZ/dt),
+//   dS/dt = P.dQ/dt - c |P|),
+// arranged so that far fewer values are live at once.
+__device__ __forceinline__ void rhs2_vjp(const GridDev& gd, const double* __restrict__ C,
+                                         const double* y, const double* kb, double* yb,
+                                         double* __restrict__ gradC) {
+  using Lo = Layout<2>;
+  // ---- forward intermediates ----
+  double c, g0, g1, K00, K01, K11, T0, T1, T2, T3;
+  medium_tab3(gd, y + Lo::Q, c, g0, g1, K00, K01, K11, T0, T1, T2, T3);
+  const double P0 = y[Lo::P], P1 = y[Lo::P + 1];
+  const double pn2 = fma(P0, P0, P1 * P1);
+  const double rinv = rsqrt_nr(pn2), pn = pn2 * rinv, cop = c * rinv;
+  const double n0 = P0 * rinv, n1 = P1 * rinv;
+  const double ng = fma(n0, g0, n1 * g1);
+  const double km00 = -pn * K00, km01 = -pn * K01, km11 = -pn * K11;
+  auto Aj = [&](int j, int k) { return mk(y[Lo::AR + 2 * j + k], y[Lo::AI + 2 * j + k]); };
+  auto Bj = [&](int j, int k) { return mk(y[Lo::BR + 2 * j + k], y[Lo::BI + 2 * j + k]); };
+  auto Zj = [&](int j, int k) {  // A + i B
+    return mk(y[Lo::AR + 2 * j + k] - y[Lo::BI + 2 * j + k], y[Lo::AI + 2 * j + k] + y[Lo::BR + 2 * j + k]);
+  };
+  cx bn[2], u[2], Zd[2][2];
+#pragma unroll
+  for (int j = 0; j < 2; ++j) {
+    const cx A0 = Aj(j, 0), A1 = Aj(j, 1), B0 = Bj(j, 0), B1 = Bj(j, 1);
+    bn[j] = n0 * B0 + n1 * B1;
+    u[j] = (g0 * A0 + g1 * A1) - cop * bn[j];
+    const cx Ad0 = n0 * u[j] + cop * B0, Ad1 = n1 * u[j] + cop * B1;
+    const cx Bd0 = (km00 * A0 + km01 * A1) - g0 * bn[j];
+    const cx Bd1 = (km01 * A0 + km11 * A1) - g1 * bn[j];
+    Zd[j][0] = Ad0 + mk(-Bd0.i, Bd0.r);
+    Zd[j][1] = Ad1 + mk(-Bd1.i, Bd1.r);
+  }
+  const cx Z00 = Zj(0, 0), Z01 = Zj(0, 1), Z10 = Zj(1, 0), Z11 = Zj(1, 1);
+  const cx N = Z11 * Zd[0][0] - Z01 * Zd[1][0] - Z10 * Zd[0][1] + Z00 * Zd[1][1];
+  const cx Dt = Z00 * Z11 - Z01 * Z10;
+  const double idd = rcp_nr(fma(Dt.r, Dt.r, Dt.i * Dt.i));
+  const cx rD = mk(Dt.r * idd, -Dt.i * idd);
+  const cx q = N * rD;
+  const cx F = mk(ng + 0.5 * q.r, 0.5 * q.i);
+  // ---- reverse ----
+  const cx a = mk(y[Lo::aR], y[Lo::aI]);
+  const cx kab = mk(kb[Lo::aR], kb[Lo::aI]);
+  const cx ab = mulc(kab, F);
+  yb[Lo::aR] += ab.r;
+  yb[Lo::aI] += ab.i;
+  const cx Fb = mulc(kab, a);
+  const double ngb = Fb.r;
+  const cx qb = 0.5 * Fb;
+  const cx Nb = mulc(qb, rD);
+  const cx Dtb = -1.0 * mulc(mulc(qb, N), rD * rD);
+  // adjoints of Z (det and N) and of dZ/dt (N)
+  cx Zb[2][2], Zdb[2][2];
+  Zb[0][0] = mulc(Dtb, Z11) + mulc(Nb, Zd[1][1]);
+  Zb[1][1] = mulc(Dtb, Z00) + mulc(Nb, Zd[0][0]);
+  Zb[0][1] = -1.0 * (mulc(Dtb, Z10) + mulc(Nb, Zd[1][0]));
+  Zb[1][0] = -1.0 * (mulc(Dtb, Z01) + mulc(Nb, Zd[0][1]));
+  Zdb[0][0] = mulc(Nb, Z11);
+  Zdb[1][1] = mulc(Nb, Z00);
+  Zdb[1][0] = -1.0 * mulc(Nb, Z01);
+  Zdb[0][1] = -1.0 * mulc(Nb, Z10);
+  // dS/dt = P.(c n) - c pn
+  const double Sdb = kb[Lo::S];
+  const double Qdb0 = fma(Sdb, P0, kb[Lo::Q]), Qdb1 = fma(Sdb, P1, kb[Lo::Q + 1]);
+  double Pb0 = Sdb * c * n0, Pb1 = Sdb * c * n1;
+  double cb = -Sdb * pn, pnb = -Sdb * c;
+  double nb0 = 0, nb1 = 0, gb0 = 0, gb1 = 0, copb = 0, kmb00 = 0, kmb01 = 0, kmb11 = 0;
+#pragma unroll
+  for (int j = 0; j < 2; ++j) {
+    const cx A0 = Aj(j, 0), A1 = Aj(j, 1), B0 = Bj(j, 0), B1 = Bj(j, 1);
+    // dZ/dt = dA/dt + i dB/dt, Z = A + i B (the adjoint of i w is -i times w's adjoint)
+    const cx Adb0 = mk(kb[Lo::AR + 2 * j], kb[Lo::AI + 2 * j]) + Zdb[j][0];
+    const cx Adb1 = mk(kb[Lo::AR + 2 * j + 1], kb[Lo::AI + 2 * j + 1]) + Zdb[j][1];
+    const cx Bdb0 = mk(kb[Lo::BR + 2 * j], kb[Lo::BI + 2 * j]) + mk(Zdb[j][0].i, -Zdb[j][0].r);
+    const cx Bdb1 = mk(kb[Lo::BR + 2 * j + 1], kb[Lo::BI + 2 * j + 1]) + mk(Zdb[j][1].i, -Zdb[j][1].r);
+    cx Ab0 = Zb[j][0], Ab1 = Zb[j][1];
+    cx Bb0 = mk(Zb[j][0].i, -Zb[j][0].r), Bb1 = mk(Zb[j][1].i, -Zb[j][1].r);
+    // dB_jk/dt = km_0k A_j0 + km_1k A_j1 - g_k bn_j
+    Ab0 = Ab0 + (km00 * Bdb0 + km01 * Bdb1);
+    Ab1 = Ab1 + (km01 * Bdb0 + km11 * Bdb1);
+    kmb00 += rdot(Bdb0, A0);
+    kmb01 += rdot(Bdb0, A1) + rdot(Bdb1, A0);
+    kmb11 += rdot(Bdb1, A1);
+    gb0 -= rdot(Bdb0, bn[j]);
+    gb1 -= rdot(Bdb1, bn[j]);
+    cx bnb = -1.0 * (g0 * Bdb0 + g1 * Bdb1);
+    // dA_jk/dt = n_k u_j + cop B_jk
+    const cx ub = n0 * Adb0 + n1 * Adb1;
+    nb0 += rdot(Adb0, u[j]);
+    nb1 += rdot(Adb1, u[j]);
+    copb += rdot(Adb0, B0) + rdot(Adb1, B1);
+    Bb0 = Bb0 + cop * Adb0;
+    Bb1 = Bb1 + cop * Adb1;
+    // u_j = ag_j - cop bn_j, ag_j = g0 A_j0 + g1 A_j1
+    bnb = bnb - cop * ub;
+    copb -= rdot(ub, bn[j]);
+    Ab0 = Ab0 + g0 * ub;
+    Ab1 = Ab1 + g1 * ub;
+    gb0 += rdot(ub, A0);
+    gb1 += rdot(ub, A1);
+    // bn_j = n0 B_j0 + n1 B_j1
+    Bb0 = Bb0 + n0 * bnb;
+    Bb1 = Bb1 + n1 * bnb;
+    nb0 += rdot(bnb, B0);
+    nb1 += rdot(bnb, B1);
+    yb[Lo::AR + 2 * j] += Ab0.r;
+    yb[Lo::AI + 2 * j] += Ab0.i;
+    yb[Lo::AR + 2 * j + 1] += Ab1.r;
+    yb[Lo::AI + 2 * j + 1] += Ab1.i;
+    yb[Lo::BR + 2 * j] += Bb0.r;
+    yb[Lo::BI + 2 * j] += Bb0.i;
+    yb[Lo::BR + 2 * j + 1] += Bb1.r;
+    yb[Lo::BI + 2 * j + 1] += Bb1.i;
+  }
+  // km = -pn K (K symmetric: kmb01 collects both of its uses)
+  const double Kb00 = -pn * kmb00, Kbxz = -pn * kmb01, Kb11 = -pn * kmb11;
+  pnb -= K00 * kmb00 + K01 * kmb01 + K11 * kmb11;
+  // ng = n.g; dQ/dt = c n; dP/dt = -pn g
+  const double Pdb0 = kb[Lo::P], Pdb1 = kb[Lo::P + 1];
+  nb0 += ngb * g0 + Qdb0 * c;
+  nb1 += ngb * g1 + Qdb1 * c;
+  gb0 += ngb * n0 - Pdb0 * pn;
+  gb1 += ngb * n1 - Pdb1 * pn;
+  pnb -= Pdb0 * g0 + Pdb1 * g1;
+  cb += Qdb0 * n0 + Qdb1 * n1;
+  // cop = c rinv; n = P rinv; pn = pn2 rinv; rinv = pn2^{-1/2}; pn2 = |P|^2
+  cb += copb * rinv;
+  double rinvb = copb * c + nb0 * P0 + nb1 * P1 + pnb * pn2;
+  Pb0 += nb0 * rinv;
+  Pb1 += nb1 * rinv;
+  const double pn2b = pnb * rinv + rinvb * (-0.5 * rinv * rinv * rinv);
+  Pb0 += 2.0 * P0 * pn2b;
+  Pb1 += 2.0 * P1 * pn2b;
+  // medium at Q
+  yb[Lo::Q] += cb * g0 + gb0 * K00 + gb1 * K01 + Kb00 * T0 + Kbxz * T1 + Kb11 * T2;
+  yb[Lo::Q + 1] += cb * g1 + gb0 * K01 + gb1 * K11 + Kb00 * T1 + Kbxz * T2 + Kb11 * T3;
+  yb[Lo::P] += Pb0;
+  yb[Lo::P + 1] += Pb1;
+  medium_scatter2(gd, y + Lo::Q, cb, gb0, gb1, Kb00, Kbxz, Kb11, gradC);
+  // S does not enter f
+}
+
 // One RK4 step that also hands its stage states z2 = y + h/2 k1, z3 = y + h/2 k2,
 // z4 = y + h k3 to put(stage, z) (the same arithmetic as rk4_step).
 template <int D, typename Put>
@@ -450,6 +669,15 @@ __device__ __forceinline__ void rk4_step(const GridDev& gd, const double* __rest
   }
 }
 
+template <int D>
+__device__ __forceinline__ void vjp(const GridDev& gd, const double* __restrict__ C, const double* y,
+                                    const double* kb, double* yb, double* __restrict__ gradC) {
+  if constexpr (D == 2)
+    rhs2_vjp(gd, C, y, kb, yb, gradC);
+  else
+    rhs_vjp<D>(gd, C, y, kb, yb, gradC);
+}
+
 // lambda <- (d step/d y)^T lambda at the state y (start of the step), gradC accumulated.
 // The three stage states and the incoming lambda live in the caller's shared-memory
 // slots zs[(slot * NF + field) * nt + lane] (4 * NF values per thread) rather than in
@@ -478,7 +706,7 @@ __device__ void rk4_step_adjoint(const GridDev& gd, const double* __restrict__ C
     zb[i] = 0.0;
     z[i] = Z(2, i);
   }
-  rhs_vjp<D>(gd, C, z, kb, zb, gradC);
+  vjp<D>(gd, C, z, kb, zb, gradC);
   // stage 3: k3 bar = h/3 lambda + h z4 bar
 #pragma unroll
   for (int i = 0; i < NF; ++i) {
@@ -487,7 +715,7 @@ __device__ void rk4_step_adjoint(const GridDev& gd, const double* __restrict__ C
     zb[i] = 0.0;
     z[i] = Z(1, i);
   }
-  rhs_vjp<D>(gd, C, z, kb, zb, gradC);
+  vjp<D>(gd, C, z, kb, zb, gradC);
   // stage 2: k2 bar = h/3 lambda + h/2 z3 bar
 #pragma unroll
   for (int i = 0; i < NF; ++i) {
@@ -496,14 +724,14 @@ __device__ void rk4_step_adjoint(const GridDev& gd, const double* __restrict__ C
     zb[i] = 0.0;
     z[i] = Z(0, i);
   }
-  rhs_vjp<D>(gd, C, z, kb, zb, gradC);
+  vjp<D>(gd, C, z, kb, zb, gradC);
   // stage 1: k1 bar = h/6 lambda + h/2 z2 bar, at y itself
 #pragma unroll
   for (int i = 0; i < NF; ++i) {
     lam[i] += zb[i];
     kb[i] = fma(h2, zb[i], h6 * Z(3, i));
   }
-  rhs_vjp<D>(gd, C, y, kb, lam, gradC);
+  vjp<D>(gd, C, y, kb, lam, gradC);
 }
 
 }  // namespace adj

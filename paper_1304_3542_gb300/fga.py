@@ -124,6 +124,8 @@ def load(build_if_missing: bool = True):
     L.fga_run_pipeline.restype = ci
     L.fga_set_wait_budget.argtypes = [P, i64]
     L.fga_set_wait_budget.restype = ci
+    L.fga_set_adjoint_checkpointing.argtypes = [P, ci]
+    L.fga_set_adjoint_checkpointing.restype = ci
     L.fga_grad.argtypes = [P, P, P]
     L.fga_grad.restype = ci
     L.fga_reconstruct_static.argtypes = [ci, P, P, P, P, ctypes.c_double, ctypes.c_double, i64,
@@ -269,6 +271,12 @@ class Plan:
         """fga_set_wait_budget: polls of a tensor-core completion wait before giving up
         (< 0: defaults; 0: give up at once)."""
         self._check(self._L.fga_set_wait_budget(self._h, int(tries)), "fga_set_wait_budget")
+
+    def set_adjoint_checkpointing(self, mode: int):
+        """fga_set_adjoint_checkpointing: 0 = record every ray state when it fits in half
+        of the free device memory, 1 = always checkpoint segments and recompute them."""
+        self._check(self._L.fga_set_adjoint_checkpointing(self._h, int(mode)),
+                    "fga_set_adjoint_checkpointing")
 
     def run_pipeline(self, u0, u1, out):
         """decompose + propagate + reconstruct of every shot as one CUDA graph replay

@@ -160,7 +160,8 @@ def _oracle_keys(prob, c, shot=0, rows=None):
 def test_adjoint_against_oracle_tangent():
     """Reverse mode on the GPU against forward mode in the oracle, same frozen set:
     <fga_grad(w), v> = <w, Re J v> for w = traces and two random w, along two smooth
-    directions and the three cells where the gradient is largest."""
+    directions and the three cells where the gradient is largest; both ways of keeping
+    the ray states for the reverse sweep (all recorded, or checkpointed segments)."""
     prob = _problem()
     c = prob.velocity
     tr, keys, plan = _gpu(prob, c, want_plan=True)
@@ -171,7 +172,13 @@ def test_adjoint_against_oracle_tangent():
     rng = np.random.default_rng(7)
     ws = [np.ascontiguousarray(tr)] + [rng.standard_normal(tr.shape) for _ in range(2)]
     grads = [plan.grad(np.ascontiguousarray(w)) for w in ws]
+    # the other way of keeping the ray states (checkpoints, segments recomputed) gives the
+    # same gradient up to the order of the atomic additions
+    plan.set_adjoint_checkpointing(1)
+    seg = [plan.grad(np.ascontiguousarray(w)) for w in ws]
     plan.close()
+    for a, b in zip(grads, seg):
+        assert np.linalg.norm(a - b) <= 1e-13 * np.linalg.norm(a)
     dirs = [_smooth_direction(prob.n, seed) for seed in (1, 2)]
     for f in np.argsort(-np.abs(grads[0].ravel()))[:3]:
         e = np.zeros(prob.n)
@@ -431,3 +438,13 @@ def test_adjoint_layered_full_size():
         # Gaussian's term at kappa = 6, not part of the derivative) weigh more against
         # the small change of J than for the smooth directions: 5e-3.
         assert abs(grad.ravel()[f] - fd) <= 5e-3 * abs(fd) + 1e-12 * J0, (grad.ravel()[f], fd)
+
+
+def test_adjoint_checkpointing_rejects_unknown_mode():
+    plan = F.plan_from_problem(_problem())
+    with pytest.raises(F.FGAError) as ei:
+        plan.set_adjoint_checkpointing(2)
+    assert ei.value.status == F.FGA_ERR_INVALID
+    plan.set_adjoint_checkpointing(1)
+    plan.set_adjoint_checkpointing(0)
+    plan.close()
