@@ -390,6 +390,13 @@ fga_status fga_plan(const fga_config* cfg, const double* velocity, void* stream,
       sh.np *= nbk;
       sh.ntile[k] = (int)((gd.n[k] + p->grid.tile[k] - 1) / p->grid.tile[k]);
     }
+    if (sh.np > ((int64_t)1 << 31) - 1 - fga::kScanBlock) {
+      delete p;
+      return fail(nullptr, FGA_ERR_INVALID, "a box of 2^31 or more points");
+    }
+    sh.fd_np = fga::make_fastdiv((uint32_t)sh.np);
+    sh.fd_nbl = fga::make_fastdiv((uint32_t)sh.nb[d - 1]);
+    sh.fd_nb12 = fga::make_fastdiv((uint32_t)(d == 3 ? sh.nb[1] * sh.nb[2] : 1));
     sh.tile_off = tile_off;
     int64_t nt = 1;
     for (int k = 0; k < d; ++k) nt *= sh.ntile[k];
@@ -608,8 +615,10 @@ fga_status fga_decompose(fga_plan_t p, const double* u0, const double* u1, int64
   }
   p->blk_first[p->nshots] = psi_total / fga::kScanBlock;
   p->nblocks = psi_total / fga::kScanBlock;
-  CUDA_OR_FAIL(p, grow(&p->d_psi, &p->psi_cap, (size_t)psi_total));
-  CUDA_OR_FAIL(p, grow(&p->d_psi_f1, &p->psi_f1_cap, (size_t)psi_total));
+  // psi and psi_1 in double2 units (FP32 pairs in mixed precision take half of them)
+  const size_t psi_units = fga::psi_is_f32(p) ? (size_t)psi_total / 2 + 1 : (size_t)psi_total;
+  CUDA_OR_FAIL(p, grow(&p->d_psi, &p->psi_cap, psi_units));
+  CUDA_OR_FAIL(p, grow(&p->d_psi_f1, &p->psi_f1_cap, psi_units));
   if (d >= 2) CUDA_OR_FAIL(p, grow(&p->d_g1, &p->g1_cap, (size_t)g1_total));
   if (d == 3) CUDA_OR_FAIL(p, grow(&p->d_g2, &p->g2_cap, (size_t)g2_total));
   CUDA_OR_FAIL(p, grow(&p->d_blk, &p->blk_cap, (size_t)p->nblocks + 1));
@@ -1055,10 +1064,19 @@ fga_status fga_psi(fga_plan_t p, int shot, double* psi_host, double* max_abs) {
   if (psi_host) {
     std::memset(psi_host, 0, sizeof(double) * 2 * nqt * sh.np);
     std::vector<double> seg((size_t)sh.psi_len * 2);
-    if (sh.psi_len > 0)
-      CUDA_OR_FAIL(p, cudaMemcpyAsync(seg.data(), p->d_psi + sh.psi_off, sizeof(double2) * sh.psi_len,
-                                      cudaMemcpyDeviceToHost, p->stream));
-    CUDA_OR_FAIL(p, cudaStreamSynchronize(p->stream));
+    if (fga::psi_is_f32(p)) {  // FP32 pairs (mixed precision), widened exactly
+      std::vector<float> segf((size_t)sh.psi_len * 2);
+      if (sh.psi_len > 0)
+        CUDA_OR_FAIL(p, cudaMemcpyAsync(segf.data(), reinterpret_cast<const float2*>(p->d_psi) + sh.psi_off,
+                                        sizeof(float2) * sh.psi_len, cudaMemcpyDeviceToHost, p->stream));
+      CUDA_OR_FAIL(p, cudaStreamSynchronize(p->stream));
+      for (size_t i = 0; i < segf.size(); ++i) seg[i] = (double)segf[i];
+    } else {
+      if (sh.psi_len > 0)
+        CUDA_OR_FAIL(p, cudaMemcpyAsync(seg.data(), p->d_psi + sh.psi_off, sizeof(double2) * sh.psi_len,
+                                        cudaMemcpyDeviceToHost, p->stream));
+      CUDA_OR_FAIL(p, cudaStreamSynchronize(p->stream));
+    }
     int64_t qtl = sh.psi_len / std::max<int64_t>(sh.np, 1);
     for (int64_t ql = 0; ql < qtl; ++ql) {
       int64_t qf;

@@ -542,16 +542,19 @@ __global__ void k_fbi3_stage3(GridDev gd, const ShotDev* __restrict__ shots,
 // flight (one phase per barrier at most) with the full budget before the tensor memory
 // is released.
 //
-// Epilogue (8 warps, two per TMEM lane quarter, each taking half of the 128 columns):
-// each warp moves its 32 accumulator rows through shared memory (a 32 x 32 block at a
-// time, reusing the stage buffers) so that the branch split runs with lane = p_z column
-// and every store of the warp is one contiguous row segment; the split is FP32
-// arithmetic on the FP32 accumulations (with 1/|p| from rsqrtf), stored as FP64. The
-// maximum of |psi+|^2 is the selection's own FP64 |psi+|^2 of the stored values: a thread
-// screens its values by their FP32 square (relative error below 2^-21) and evaluates the
-// FP64 square only of those within 1e-6 of its running FP32 maximum, which any value
-// whose FP64 square could be the largest is.
-constexpr int FT = 128;        // tile edge in p_x (GEMM M) and p_z (GEMM N)
+// The MMAs compute the transpose psi^T = B_f A^T (B_f as the M operand), so that the
+// accumulator's TMEM lanes are p_z and its columns p_x. Epilogue (8 warps, two per TMEM
+// lane quarter, each taking half of the 128 columns, 16 at a time): a thread holds 16
+// p_x values of its p_z column, and every store of a warp is one contiguous run of 32
+// p_z columns of a p_x row, straight from registers. The branch split is FP32
+// arithmetic on the FP32 accumulations (with 1/|p| from rsqrtf), stored as FP32 pairs:
+// in this precision psi and its psi_1 part are FP32 values, and the selection widens
+// them exactly. The maximum of |psi+|^2 is the selection's own FP64 |psi+|^2 of the
+// stored values: a thread keeps its values in shared memory and afterwards evaluates
+// the FP64 square only of those whose FP32 square (after an exact power-of-two scaling
+// to the range of its largest component) is within 1e-6 of the largest such square,
+// which any value whose FP64 square could be the largest is.
+constexpr int FT = 128;        // tile edge in p_z (GEMM M) and p_x (GEMM N)
 constexpr int FJ = 8;          // complex jx per chunk -> K = 16
 constexpr int FNT = 256;       // 8 warps: warp w reads TMEM lanes 32 (w % 4) .., columns half w / 4
 constexpr int FSTAGES = 3;
@@ -560,9 +563,6 @@ constexpr uint32_t kFbiStage = 8 * kFbiOp;                  // A: 4 parts, B: 2 
 constexpr uint32_t kFbiLBO = 2048, kFbiSBO = 128;
 constexpr size_t kFbiBarOff = (size_t)FSTAGES * kFbiStage;
 constexpr size_t kFbiSmem = kFbiBarOff + 128;
-constexpr int kStageLd = 33;  // float4 per staged row: 32 columns + 1 of padding (no bank conflicts)
-static_assert((size_t)(FNT / 32) * 32 * kStageLd * sizeof(float4) <= kFbiBarOff,
-              "epilogue staging fits the stages");
 constexpr uint32_t kFbiTries = 1u << 22;
 
 // IEEE binary32 -> binary64 in integer arithmetic (exact, keeps the FP64 pipe free):
@@ -588,8 +588,8 @@ __device__ __forceinline__ double widen_f32(float f) {
 __global__ void __launch_bounds__(FNT) k_fbi_stage2_tc(GridDev gd, const ShotDev* __restrict__ shots,
                                                       const double* __restrict__ C,
                                                       const double2* __restrict__ g1,
-                                                      double2* __restrict__ psi,
-                                                      double2* __restrict__ psi_f1,
+                                                      float2* __restrict__ psi,
+                                                      float2* __restrict__ psi_f1,
                                                       unsigned long long* __restrict__ max2,
                                                       int* status, uint32_t tries) {
   const int s = blockIdx.z;
@@ -606,14 +606,11 @@ __global__ void __launch_bounds__(FNT) k_fbi_stage2_tc(GridDev gd, const ShotDev
   uint64_t* empty = full + FSTAGES;
   uint64_t* done = empty + FSTAGES;
   uint32_t* tbase = reinterpret_cast<uint32_t*>(done + 1);
-  __shared__ double cq_s;
+  __shared__ float h2_s, c1_s, psx_s, psz_s;
   __shared__ int aborted_s;
   const int tid = threadIdx.x, warp = tid >> 5;
   const int64_t mxl = ql / sh.qn[1], mzl = ql - mxl * sh.qn[1];
   if (tid == 0) {
-    double q[2] = {gd.o[0] + (double)(sh.s[0] * (sh.qlo[0] + mxl)) * gd.h[0],
-                   gd.o[1] + (double)(sh.s[1] * (sh.qlo[1] + mzl)) * gd.h[1]};
-    cq_s = medium_value<2>(gd, C, q);
     for (int i = 0; i < FSTAGES; ++i) {
       tc::mbar_init(&full[i], 1);
       tc::mbar_init(&empty[i], 1);
@@ -621,6 +618,8 @@ __global__ void __launch_bounds__(FNT) k_fbi_stage2_tc(GridDev gd, const ShotDev
     tc::mbar_init(done, 1);
     tc::fence_mbar_init();
     aborted_s = 0;
+    psx_s = (float)sh.pscale[0];
+    psz_s = (float)sh.pscale[1];
   }
   if (warp == 0) {
     tc::tmem_alloc(tbase, 4 * FT);
@@ -671,13 +670,15 @@ __global__ void __launch_bounds__(FNT) k_fbi_stage2_tc(GridDev gd, const ShotDev
         for (int f = 0; f < 2; ++f)
 #pragma unroll
           for (int cc = 0; cc < 2; ++cc) {
+            // transposed product psi^T = B_f A^T: the accumulator's lanes are p_z, its
+            // columns p_x, so the epilogue stores p_z-contiguous rows from registers
             const uint32_t d = tmem + (uint32_t)((2 * f + cc) * FT);
             const uint32_t ah = base + (2 * cc) * kFbiOp + step, al = ah + kFbiOp;
             const uint32_t bh = base + (4 + 2 * f) * kFbiOp + step, bl = bh + kFbiOp;
-            tc::mma_tf32(d, tc::smem_desc(ah, kFbiLBO, kFbiSBO), tc::smem_desc(bh, kFbiLBO, kFbiSBO), idesc,
+            tc::mma_tf32(d, tc::smem_desc(bh, kFbiLBO, kFbiSBO), tc::smem_desc(ah, kFbiLBO, kFbiSBO), idesc,
                          (c > 0 || ks > 0) ? 1u : 0u);
-            tc::mma_tf32(d, tc::smem_desc(ah, kFbiLBO, kFbiSBO), tc::smem_desc(bl, kFbiLBO, kFbiSBO), idesc, 1u);
-            tc::mma_tf32(d, tc::smem_desc(al, kFbiLBO, kFbiSBO), tc::smem_desc(bh, kFbiLBO, kFbiSBO), idesc, 1u);
+            tc::mma_tf32(d, tc::smem_desc(bl, kFbiLBO, kFbiSBO), tc::smem_desc(ah, kFbiLBO, kFbiSBO), idesc, 1u);
+            tc::mma_tf32(d, tc::smem_desc(bh, kFbiLBO, kFbiSBO), tc::smem_desc(al, kFbiLBO, kFbiSBO), idesc, 1u);
           }
       }
       tc::mma_commit(&empty[st]);
@@ -707,62 +708,106 @@ __global__ void __launch_bounds__(FNT) k_fbi_stage2_tc(GridDev gd, const ShotDev
       tc::mbar_arrive(done);
     }
   }
+  if (tid == 128) {  // the epilogue's constants (c(q) among them) while thread 0 feeds the tensor cores
+    double q[2] = {gd.o[0] + (double)(sh.s[0] * (sh.qlo[0] + mxl)) * gd.h[0],
+                   gd.o[1] + (double)(sh.s[1] * (sh.qlo[1] + mzl)) * gd.h[1]};
+    const double cq = medium_value<2>(gd, C, q);
+    const double hv = gd.h[0] * gd.h[1];
+    h2_s = (float)(0.5 * hv);                 // psi_f = hv * acc; psi+ = psi0/2 + ...
+    c1_s = (float)(0.5 * hv * sh.eps / cq);   // ... i (eps/(2 c(q) |p|)) hv acc1
+  }
   const bool finished = tc::mbar_wait_bounded(done, 0u, tid == 0 ? kFbiTries : (tries > 0 ? tries : 1u));
   const bool ok = __syncthreads_and(finished) && aborted_s == 0;
   if (!ok && tid == 0 && aborted_s == 0) atomicOr(status, kStatusTimeout);
   tc::fence_after_sync();
-  // epilogue: TMEM lane 32 w + l holds p_x row m0 + 32 w + l; a warp stages 32 rows x 32
-  // p_z columns, then sweeps them row by row with lane = column
+  // epilogue: TMEM lane 32 quarter + l holds p_z column n0 + 32 quarter + l, TMEM column
+  // j the p_x row m0 + j; a warp takes 64 of the rows, 16 at a time, and each of its
+  // stores is one contiguous run of 32 p_z columns of a row (FP32 pairs)
   const int lane = tid & 31, quarter = warp & 3, half = warp >> 2;
-  float4* stage = reinterpret_cast<float4*>(smem) + warp * 32 * kStageLd;
-  const double hv = gd.h[0] * gd.h[1];
-  const float h2 = (float)(0.5 * hv);                    // psi_f = hv * acc; psi+ = psi0/2 + ...
-  const float c1 = (float)(0.5 * hv * sh.eps / cq_s);    // ... i (eps/(2 c(q) |p|)) hv acc1
-  const float psx = (float)sh.pscale[0], psz = (float)sh.pscale[1];
-  double2* out0 = psi + sh.psi_off + ql * sh.np;
-  double2* out1 = psi_f1 + sh.psi_off + ql * sh.np;
-  unsigned long long mymax = 0ull;  // bits of the largest |psi+|^2 (non-negative doubles order as integers)
-  float fmax32 = 0.0f;              // running maximum of the FP32 squares (screen)
-  float a0r[32], a0i[32], a1r[32], a1i[32];
+  const float h2 = h2_s, c1 = c1_s;
+  const float psx = psx_s, psz = psz_s;
+  float2* out0 = psi + sh.psi_off + ql * sh.np;
+  float2* out1 = psi_f1 + sh.psi_off + ql * sh.np;
+  const int n = (int)n0 + 32 * quarter + lane;
+  const bool nin = n < (int)nbz;
+  const int mz = n - (int)(nbz / 2);
+  const float pz = (float)mz * psz, pz2 = pz * pz;
+  // this thread's values psi+ for the exact maximum below, in the stage buffers (free once
+  // the MMAs are done): [value k][thread], NaN where no value was stored
+  float2* vs = reinterpret_cast<float2*>(smem);
+  float amax = 0.0f;  // largest |Re|, |Im| of the stored values (fmaxf leaves NaN out)
   if (ok) {
 #pragma unroll 1
-    for (int cb = 64 * half; cb < 64 * half + 64; cb += 32) {
+    for (int cb = 64 * half; cb < 64 * half + 64; cb += 16) {
+      if (m0 + cb >= nbx) break;  // uniform over the warp
       const uint32_t lane_base = tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)cb;
-      tc::tmem_ld_32x32b_x32(lane_base, a0r);
-      tc::tmem_ld_32x32b_x32(lane_base + FT, a0i);
-      tc::tmem_ld_32x32b_x32(lane_base + 2 * FT, a1r);
-      tc::tmem_ld_32x32b_x32(lane_base + 3 * FT, a1i);
+      uint32_t r0r[16], r0i[16], r1r[16], r1i[16];
+      tc::tmem_ld_32x32b_x16(lane_base, r0r);
+      tc::tmem_ld_32x32b_x16(lane_base + FT, r0i);
+      tc::tmem_ld_32x32b_x16(lane_base + 2 * FT, r1r);
+      tc::tmem_ld_32x32b_x16(lane_base + 3 * FT, r1i);
+      tc::tmem_ld_wait();
+      tc::reg_fence16(r0r);
+      tc::reg_fence16(r0i);
+      tc::reg_fence16(r1r);
+      tc::reg_fence16(r1i);
+      const int mb = (int)m0 + cb;                 // p_x row of i = 0
+      const float mxf0 = (float)(mb - (int)(nbx / 2));
+      float2* vk = vs + (cb - 64 * half) * FNT + tid;
 #pragma unroll
-      for (int i = 0; i < 32; ++i) stage[lane * kStageLd + i] = make_float4(a0r[i], a0i[i], a1r[i], a1i[i]);
-      __syncwarp();
-      const int64_t n = n0 + cb + lane;
-      const int mz = (int)(n - nbz / 2);
-      const float pz = (float)mz * psz;
-#pragma unroll 2
-      for (int rr = 0; rr < 32; ++rr) {
-        const int64_t m = m0 + 32 * quarter + rr;  // uniform over the warp
-        if (m >= nbx) break;
-        if (n >= nbz) continue;
-        const float4 v = stage[rr * kStageLd + lane];
-        const int mx = (int)(m - nbx / 2);
-        const float px = (float)mx * psx;
+      for (int i = 0; i < 16; ++i) {
+        const int m = mb + i;
+        const bool in = nin && m < (int)nbx;
+        const float px = (mxf0 + (float)i) * psx;  // (float) mx, exactly
         // left-out p: the Nyquist index of either axis and p = 0 (as psi_plus<2>)
-        const bool valid = m != 0 && n != 0 && !(mx == 0 && mz == 0);
-        const float r = valid ? c1 * rsqrtf(fmaf(px, px, pz * pz)) : 0.0f;
-        const float tx = valid ? -r * v.w : 0.0f, ty = valid ? r * v.z : 0.0f;
-        const float ox = valid ? fmaf(h2, v.x, tx) : 0.0f, oy = valid ? fmaf(h2, v.y, ty) : 0.0f;
-        const double2 o = make_double2(widen_f32(ox), widen_f32(oy));
-        const int64_t jp = m * nbz + n;
-        out0[jp] = o;
-        out1[jp] = make_double2(widen_f32(tx), widen_f32(ty));
-        const float f2 = fmaf(ox, ox, oy * oy);
-        if (f2 >= 0.999999f * fmax32) {  // false for NaN
-          fmax32 = fmaxf(fmax32, f2);
-          const unsigned long long a2 = (unsigned long long)__double_as_longlong(abs2_rn(o));
-          if (a2 <= 0x7ff0000000000000ull && a2 > mymax) mymax = a2;  // NaN left out, as fmax does
+        const bool valid = m != 0 && n != 0 && !(m == (int)(nbx / 2) && mz == 0);
+        const float rr = c1 * rsqrtf(fmaf(px, px, pz2));
+        const float r = valid ? rr : 0.0f, hh = valid ? h2 : 0.0f;
+        const float tx = -r * __uint_as_float(r1i[i]);
+        const float ty = r * __uint_as_float(r1r[i]);
+        const float ox = fmaf(hh, __uint_as_float(r0r[i]), tx);
+        const float oy = fmaf(hh, __uint_as_float(r0i[i]), ty);
+        if (in) {
+          const int64_t jp = (int64_t)m * nbz + n;
+          out0[jp] = make_float2(ox, oy);
+          out1[jp] = make_float2(tx, ty);
+          amax = fmaxf(amax, fmaxf(fabsf(ox), fabsf(oy)));
         }
+        vk[i * FNT] = in ? make_float2(ox, oy) : make_float2(__int_as_float(0x7fc00000), 0.0f);
       }
-      __syncwarp();
+    }
+  }
+  // the largest FP64 |psi+|^2 of the stored values (as the selection computes it). Scaled
+  // by s = 2^k so that s max(|Re|, |Im|) lies in [1, 2), the FP32 squares near the largest
+  // one are within 2^-22 of the exact scaled squares, so only values within 1e-6 of the
+  // largest FP32 square can hold the maximum; only those are squared in FP64. If the
+  // components are all zero the maximum is +0; if the largest is below 2^-100 or not
+  // finite, every stored value is squared in FP64.
+  unsigned long long mymax = 0ull;  // bits of the largest |psi+|^2 (non-negative doubles order as integers)
+  if (ok && amax != 0.0f) {
+    const bool scaled = amax >= 0x1p-100f && amax < INFINITY;
+    const float sc = scaled ? ldexpf(1.0f, -ilogbf(amax)) : 1.0f;
+    const int64_t rows = nbx - (m0 + 64 * half);  // rows of this warp's half that exist
+    const int nk = rows >= 64 ? 64 : (rows > 0 ? (int)rows : 0);
+    float fmx = 0.0f;
+    if (scaled) {
+#pragma unroll 4
+      for (int k = 0; k < nk; ++k) {
+        const float2 v = vs[k * FNT + tid];
+        const float sx = v.x * sc, sy = v.y * sc;
+        fmx = fmaxf(fmx, fmaf(sx, sx, sy * sy));
+      }
+    }
+    const float lim = scaled ? 0.999999f * fmx : 0.0f;
+#pragma unroll 4
+    for (int k = 0; k < nk; ++k) {
+      const float2 v = vs[k * FNT + tid];
+      const float sx = v.x * sc, sy = v.y * sc;
+      if (fmaf(sx, sx, sy * sy) >= lim) {  // false for NaN (no value stored)
+        const double2 o = make_double2(widen_f32(v.x), widen_f32(v.y));
+        const unsigned long long a2 = (unsigned long long)__double_as_longlong(abs2_rn(o));
+        if (a2 <= 0x7ff0000000000000ull && a2 > mymax) mymax = a2;  // NaN left out, as fmax does
+      }
     }
   }
   for (int off = 16; off > 0; off >>= 1) {
@@ -885,7 +930,8 @@ cudaError_t launch_fbi(fga_plan_s* p, const double* u0, const double* u1) {
       tiles = std::max<int64_t>(tiles, ((sh.nb[0] + FT - 1) / FT) * ((sh.nb[1] + FT - 1) / FT));
     dim3 tgrid((unsigned)tiles, (unsigned)maxQ, p->nshots);
     k_fbi_stage2_tc<<<tgrid, FNT, kFbiSmem, p->stream>>>(p->grid, p->d_shots, p->d_coef, p->d_g1,
-                                                        p->d_psi, p->d_psi_f1, p->d_max2,
+                                                        reinterpret_cast<float2*>(p->d_psi),
+                                                        reinterpret_cast<float2*>(p->d_psi_f1), p->d_max2,
                                                         p->d_status,
                                                         p->wait_tries >= 0 ? (uint32_t)p->wait_tries
                                                                            : kFbiTries);

@@ -26,18 +26,119 @@ __device__ __forceinline__ int shot_of_block(const ShotDev* shots, int nshots, i
   return lo;
 }
 
+// Position of a compaction block's first entry in its shot's segment: q row ql0 and p
+// index r0 (one 64-bit division per block, by thread 0); entry k of the block is then
+// q row ql0 + (r0 + k) / np and p index (r0 + k) mod np, found with fast_div. Thread 0
+// also forms the block's threshold thr2 = tau2 max2 and its integer screen: a pair with
+// |Re| < T and |Im| < T, T = sqrt(thr2 / 2) (1 - 2^-40), has |psi|^2 < thr2 even after
+// the rounding of its FP64 square, and the comparisons of non-negative floating-point
+// numbers are those of their bit patterns (Td, Tf: T as FP64 and, rounded down, FP32;
+// 0 where thr2 is NaN or infinite, so that nothing is screened out). FP64 instructions
+// are scarce on this part (two per clock per SM), so none is spent per thread or per
+// rejected entry.
+struct BlockPos {
+  int64_t loc0, ql0;
+  uint32_t r0;
+  double thr2;
+  unsigned long long Td;
+  uint32_t Tf;
+};
+__device__ __forceinline__ BlockPos block_pos(const ShotDev& sh, int64_t base, double tau2,
+                                              const unsigned long long* max2, int s) {
+  __shared__ int64_t s_ql0;
+  __shared__ uint32_t s_r0, s_Tf;
+  __shared__ double s_thr2;
+  __shared__ unsigned long long s_Td;
+  const int64_t loc0 = base - sh.psi_off;
+  if (threadIdx.x == 0) {
+    s_ql0 = loc0 / sh.np;
+    s_r0 = (uint32_t)(loc0 - s_ql0 * sh.np);
+    const double thr2 = max2 ? tau2 * __longlong_as_double((long long)max2[s]) : 0.0;
+    const double T = thr2 >= 0.0 && thr2 < INFINITY ? sqrt(0.5 * thr2) * (1.0 - 0x1p-40) : 0.0;
+    s_thr2 = thr2;
+    s_Td = (unsigned long long)__double_as_longlong(T);
+    s_Tf = __float_as_uint(__double2float_rd(T));
+  }
+  __syncthreads();
+  return BlockPos{loc0, s_ql0, s_r0, s_thr2, s_Td, s_Tf};
+}
+__device__ __forceinline__ bool below(const BlockPos& b, double2 v) {
+  const unsigned long long ax = (unsigned long long)__double_as_longlong(v.x) & 0x7fffffffffffffffull;
+  const unsigned long long ay = (unsigned long long)__double_as_longlong(v.y) & 0x7fffffffffffffffull;
+  return ax < b.Td && ay < b.Td;
+}
+__device__ __forceinline__ bool below(const BlockPos& b, float2 v) {
+  return (__float_as_uint(v.x) & 0x7fffffffu) < b.Tf && (__float_as_uint(v.y) & 0x7fffffffu) < b.Tf;
+}
+
+// The q row and p index (flat and per axis) of one entry, stepped along the segment.
+struct PCur {
+  int64_t ql;
+  uint32_t jp, j0, j1, j2;
+};
+// Entry k of the block (the p index split with fast_div: once per thread, not per entry).
 template <int D>
-__device__ __forceinline__ bool p_valid(const ShotDev& sh, int64_t jp) {
+__device__ __forceinline__ PCur pcur_at(const ShotDev& sh, const BlockPos& b, int k) {
+  PCur c;
+  const uint32_t x = b.r0 + (uint32_t)k;
+  const uint32_t qd = fast_div(sh.fd_np, x);
+  c.jp = x - qd * (uint32_t)sh.np;
+  c.ql = b.ql0 + qd;
+  c.j1 = c.j2 = 0u;
   if constexpr (D == 1) {
-    return jp != 0 && jp != sh.nb[0] / 2;
-  } else if constexpr (D == 3) {
-    const int64_t nb12 = (int64_t)sh.nb[1] * sh.nb[2];
-    const int64_t j0 = jp / nb12, j1 = (jp - j0 * nb12) / sh.nb[2], j2 = jp - j0 * nb12 - j1 * sh.nb[2];
-    return j0 != 0 && j1 != 0 && j2 != 0 &&
-           !(j0 == sh.nb[0] / 2 && j1 == sh.nb[1] / 2 && j2 == sh.nb[2] / 2);
+    c.j0 = c.jp;
+  } else if constexpr (D == 2) {
+    c.j0 = fast_div(sh.fd_nbl, c.jp);
+    c.j1 = c.jp - c.j0 * (uint32_t)sh.nb[1];
   } else {
-    int64_t j0 = jp / sh.nb[1], j1 = jp - j0 * sh.nb[1];
-    return j0 != 0 && j1 != 0 && !(j0 == sh.nb[0] / 2 && j1 == sh.nb[1] / 2);
+    c.j0 = fast_div(sh.fd_nb12, c.jp);
+    const uint32_t r = c.jp - c.j0 * ((uint32_t)sh.nb[1] * (uint32_t)sh.nb[2]);
+    c.j1 = fast_div(sh.fd_nbl, r);
+    c.j2 = r - c.j1 * (uint32_t)sh.nb[2];
+  }
+  return c;
+}
+// The next entry (p index + 1, carried into the axes and the q row).
+template <int D>
+__device__ __forceinline__ void pcur_next(const ShotDev& sh, PCur& c) {
+  ++c.jp;
+  bool wrap;
+  if constexpr (D == 1) {
+    wrap = ++c.j0 == (uint32_t)sh.nb[0];
+  } else if constexpr (D == 2) {
+    wrap = false;
+    if (++c.j1 == (uint32_t)sh.nb[1]) {
+      c.j1 = 0u;
+      wrap = ++c.j0 == (uint32_t)sh.nb[0];
+    }
+  } else {
+    wrap = false;
+    if (++c.j2 == (uint32_t)sh.nb[2]) {
+      c.j2 = 0u;
+      if (++c.j1 == (uint32_t)sh.nb[1]) {
+        c.j1 = 0u;
+        wrap = ++c.j0 == (uint32_t)sh.nb[0];
+      }
+    }
+  }
+  if (wrap) {
+    c.j0 = 0u;
+    c.jp = 0u;
+    ++c.ql;
+  }
+}
+// Valid p: the Nyquist index of an axis and p = 0 are left out (as in the FBI).
+template <int D>
+__device__ __forceinline__ bool pcur_valid(const ShotDev& sh, const PCur& c) {
+  if constexpr (D == 1) {
+    return c.j0 != 0u && c.j0 != (uint32_t)(sh.nb[0] / 2);
+  } else if constexpr (D == 2) {
+    return c.j0 != 0u && c.j1 != 0u &&
+           !(c.j0 == (uint32_t)(sh.nb[0] / 2) && c.j1 == (uint32_t)(sh.nb[1] / 2));
+  } else {
+    return c.j0 != 0u && c.j1 != 0u && c.j2 != 0u &&
+           !(c.j0 == (uint32_t)(sh.nb[0] / 2) && c.j1 == (uint32_t)(sh.nb[1] / 2) &&
+             c.j2 == (uint32_t)(sh.nb[2] / 2));
   }
 }
 
@@ -56,27 +157,46 @@ __device__ __forceinline__ int64_t q_flat(const ShotDev& sh, int64_t ql) {
   }
 }
 
-template <int D>
-__device__ __forceinline__ bool keep(const ShotDev& sh, const double2* psi, int64_t e, double thr2) {
-  int64_t loc = e - sh.psi_off;
-  if (loc < 0 || loc >= sh.psi_len) return false;
-  int64_t jp = loc % sh.np;
-  if (!p_valid<D>(sh, jp)) return false;
-  double2 v = psi[e];
-  return abs2_rn(v) >= thr2;
+// psi is stored as FP64 pairs, or (mixed precision) as FP32 pairs that are widened
+// exactly: every decision below is taken on the FP64 values either way.
+__device__ __forceinline__ double2 widen2(double2 v) { return v; }
+__device__ __forceinline__ double2 widen2(float2 v) { return make_double2((double)v.x, (double)v.y); }
+
+// The exact test |psi|^2 >= thr2 in FP64, out of line: inlined, the compiler evaluates
+// it (widening and all) for every entry instead of branching around it for the entries
+// the screen rejects.
+template <typename V>
+__device__ __noinline__ bool above_exact(V v, double thr2) {
+  return abs2_rn(widen2(v)) >= thr2;
 }
 
-template <int D>
+// Entry k of the block (at cursor c): kept?
+template <int D, typename V>
+__device__ __forceinline__ bool keep(const ShotDev& sh, const BlockPos& b, const PCur& c, const V* psi,
+                                     int64_t base, int k) {
+  if (b.loc0 + k >= sh.psi_len || !pcur_valid<D>(sh, c)) return false;
+  const V v = psi[base + k];
+  if (below(b, v)) return false;  // |psi|^2 < thr2, decided without an FP64 instruction
+  return above_exact(v, b.thr2);
+}
+
+template <int D, typename V>
 __global__ void __launch_bounds__(NT) k_select_count(const ShotDev* __restrict__ shots, int nshots,
-                                                     const double2* __restrict__ psi,
+                                                     const V* __restrict__ psi,
                                                      const unsigned long long* __restrict__ max2,
                                                      double tau2, int64_t* blk) {
   int64_t base = (int64_t)blockIdx.x * kScanBlock;
   int s = shot_of_block(shots, nshots, base);
   const ShotDev& sh = shots[s];
-  double thr2 = tau2 * __longlong_as_double((long long)max2[s]);
+  const BlockPos b = block_pos(sh, base, tau2, max2, s);
+  // thread t counts the PER consecutive entries from PER t
+  const int k0 = threadIdx.x * PER;
+  PCur pc = pcur_at<D>(sh, b, k0);
   int c = 0;
-  for (int i = 0; i < PER; ++i) c += keep<D>(sh, psi, base + threadIdx.x + NT * i, thr2) ? 1 : 0;
+  for (int i = 0; i < PER; ++i) {
+    c += keep<D>(sh, b, pc, psi, base, k0 + i) ? 1 : 0;
+    pcur_next<D>(sh, pc);
+  }
   __shared__ int red[NT / 32];
   for (int off = 16; off > 0; off >>= 1) c += __shfl_xor_sync(0xffffffffu, c, off);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = c;
@@ -123,25 +243,29 @@ __global__ void __launch_bounds__(1024) k_scan_exclusive(int64_t* a, int64_t n) 
   if (threadIdx.x == 0) a[n] = carry;
 }
 
-template <int D>
+template <int D, typename V>
 __global__ void __launch_bounds__(NT) k_select_scatter(const ShotDev* __restrict__ shots, int nshots,
-                                                       const double2* __restrict__ psi,
+                                                       const V* __restrict__ psi,
                                                        const unsigned long long* __restrict__ max2,
                                                        double tau2, const int64_t* __restrict__ blk,
                                                        int32_t* gshot, int64_t* gq, int32_t* gp,
-                                                       double2* gpsi, const double2* __restrict__ psi_f1,
+                                                       double2* gpsi, const V* __restrict__ psi_f1,
                                                        double2* gpsi_f1, int64_t cap) {
   int64_t base = (int64_t)blockIdx.x * kScanBlock;
   int s = shot_of_block(shots, nshots, base);
   const ShotDev& sh = shots[s];
-  double thr2 = tau2 * __longlong_as_double((long long)max2[s]);
+  const BlockPos b = block_pos(sh, base, tau2, max2, s);
   // thread t owns PER consecutive entries, so the block order is the entry order
-  int64_t e0 = base + (int64_t)threadIdx.x * PER;
+  const int k0 = threadIdx.x * PER;
+  int64_t e0 = base + k0;
+  const PCur pc0 = pcur_at<D>(sh, b, k0);
+  PCur pc = pc0;
   bool f[PER];
   int c = 0;
   for (int i = 0; i < PER; ++i) {
-    f[i] = keep<D>(sh, psi, e0 + i, thr2);
+    f[i] = keep<D>(sh, b, pc, psi, base, k0 + i);
     c += f[i] ? 1 : 0;
+    pcur_next<D>(sh, pc);
   }
   __shared__ int warp_tot[NT / 32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -155,16 +279,15 @@ __global__ void __launch_bounds__(NT) k_select_scatter(const ShotDev* __restrict
   int wbase = 0;
   for (int w = 0; w < warp; ++w) wbase += warp_tot[w];
   int64_t pos = blk[blockIdx.x] + wbase + (x - c);
-  for (int i = 0; i < PER; ++i) {
+  pc = pc0;
+  for (int i = 0; i < PER; ++i, pcur_next<D>(sh, pc)) {
     if (!f[i] || pos >= cap) continue;  // beyond the capacity: k_counts_finish flags it
-    int64_t loc = e0 + i - sh.psi_off;
-    int64_t ql = loc / sh.np, jp = loc - ql * sh.np;
-    const int64_t qflat = q_flat<D>(sh, ql);
+    const int64_t qflat = q_flat<D>(sh, pc.ql);
     gshot[pos] = s;
     gq[pos] = qflat;
-    gp[pos] = (int32_t)jp;
-    gpsi[pos] = psi[e0 + i];
-    gpsi_f1[pos] = psi_f1[e0 + i];
+    gp[pos] = (int32_t)pc.jp;
+    gpsi[pos] = widen2(psi[e0 + i]);
+    gpsi_f1[pos] = widen2(psi_f1[e0 + i]);
     ++pos;
   }
 }
@@ -176,12 +299,11 @@ __global__ void __launch_bounds__(NT) k_select_scatter(const ShotDev* __restrict
 // get 0). A radix select over 8 passes of 8 bits (from the top) finds the cut key K and
 // how many entries equal to K are still to take; the entries are then compacted in order:
 // every key > K, and the first `take` keys == K.
-template <int D>
-__device__ __forceinline__ unsigned long long topk_key(const ShotDev& sh, const double2* psi, int64_t e) {
-  const int64_t loc = e - sh.psi_off;
-  if (loc < 0 || loc >= sh.psi_len) return 0ull;
-  if (!p_valid<D>(sh, loc % sh.np)) return 0ull;
-  const double2 v = psi[e];
+template <int D, typename V>
+__device__ __forceinline__ unsigned long long topk_key(const ShotDev& sh, const BlockPos& b, const PCur& c,
+                                                       const V* psi, int64_t base, int k) {
+  if (b.loc0 + k >= sh.psi_len || !pcur_valid<D>(sh, c)) return 0ull;
+  const double2 v = widen2(psi[base + k]);
   return (unsigned long long)__double_as_longlong(abs2_rn(v)) + 1ull;
 }
 
@@ -195,9 +317,9 @@ __global__ void k_topk_init(unsigned long long* topk, int nshots, long long keep
   topk[4 * s + 3] = 0ull;
 }
 
-template <int D>
+template <int D, typename V>
 __global__ void __launch_bounds__(NT) k_topk_hist(const ShotDev* __restrict__ shots, int nshots,
-                                                  const double2* __restrict__ psi,
+                                                  const V* __restrict__ psi,
                                                   const unsigned long long* __restrict__ topk,
                                                   int shift, unsigned long long* hist) {
   __shared__ unsigned int h[256];
@@ -207,8 +329,11 @@ __global__ void __launch_bounds__(NT) k_topk_hist(const ShotDev* __restrict__ sh
   const int s = shot_of_block(shots, nshots, base);
   const ShotDev& sh = shots[s];
   const unsigned long long prefix = topk[4 * s], mask = topk[4 * s + 1];
-  for (int i = 0; i < PER; ++i) {
-    const unsigned long long k = topk_key<D>(sh, psi, base + threadIdx.x + NT * i);
+  const BlockPos b = block_pos(sh, base, 0.0, nullptr, s);
+  const int k0 = threadIdx.x * PER;
+  PCur pc = pcur_at<D>(sh, b, k0);
+  for (int i = 0; i < PER; ++i, pcur_next<D>(sh, pc)) {
+    const unsigned long long k = topk_key<D>(sh, b, pc, psi, base, k0 + i);
     if (k != 0ull && (k & mask) == prefix) atomicAdd(&h[(k >> shift) & 255ull], 1u);
   }
   __syncthreads();
@@ -257,18 +382,21 @@ __device__ __forceinline__ void topk_class(unsigned long long k, const unsigned 
   }
 }
 
-template <int D>
+template <int D, typename V>
 __global__ void __launch_bounds__(NT) k_topk_count(const ShotDev* __restrict__ shots, int nshots,
-                                                   const double2* __restrict__ psi,
+                                                   const V* __restrict__ psi,
                                                    const unsigned long long* __restrict__ topk,
                                                    int64_t* blk_gt, int64_t* blk_eq) {
   const int64_t base = (int64_t)blockIdx.x * kScanBlock;
   const int s = shot_of_block(shots, nshots, base);
   const ShotDev& sh = shots[s];
+  const BlockPos b = block_pos(sh, base, 0.0, nullptr, s);
+  const int k0 = threadIdx.x * PER;
+  PCur pc = pcur_at<D>(sh, b, k0);
   int cg = 0, ce = 0;
-  for (int i = 0; i < PER; ++i) {
+  for (int i = 0; i < PER; ++i, pcur_next<D>(sh, pc)) {
     bool gt, eq;
-    topk_class<D>(topk_key<D>(sh, psi, base + threadIdx.x + NT * i), topk + 4 * s, gt, eq);
+    topk_class<D>(topk_key<D>(sh, b, pc, psi, base, k0 + i), topk + 4 * s, gt, eq);
     cg += gt ? 1 : 0;
     ce += eq ? 1 : 0;
   }
@@ -311,26 +439,30 @@ __global__ void k_topk_counts(ShotDev* shots, int nshots, const int64_t* blk_gt,
   }
 }
 
-template <int D>
+template <int D, typename V>
 __global__ void __launch_bounds__(NT) k_topk_scatter(const ShotDev* __restrict__ shots, int nshots,
-                                                     const double2* __restrict__ psi,
+                                                     const V* __restrict__ psi,
                                                      const unsigned long long* __restrict__ topk,
                                                      const int64_t* __restrict__ blk_gt,
                                                      const int64_t* __restrict__ blk_eq,
                                                      const int64_t* __restrict__ blk_first,
                                                      int32_t* gshot, int64_t* gq, int32_t* gp,
-                                                     double2* gpsi, const double2* __restrict__ psi_f1,
+                                                     double2* gpsi, const V* __restrict__ psi_f1,
                                                      double2* gpsi_f1, int64_t cap) {
   const int64_t base = (int64_t)blockIdx.x * kScanBlock;
   const int s = shot_of_block(shots, nshots, base);
   const ShotDev& sh = shots[s];
   const unsigned long long* t = topk + 4 * s;
   const int64_t take = t[3] ? 0 : (int64_t)t[2];
-  const int64_t e0 = base + (int64_t)threadIdx.x * PER;
+  const BlockPos b = block_pos(sh, base, 0.0, nullptr, s);
+  const int k0 = threadIdx.x * PER;
+  const int64_t e0 = base + k0;
+  const PCur pc0 = pcur_at<D>(sh, b, k0);
+  PCur pc = pc0;
   bool g[PER], q[PER];
   int cg = 0, ce = 0;
-  for (int i = 0; i < PER; ++i) {
-    topk_class<D>(topk_key<D>(sh, psi, e0 + i), t, g[i], q[i]);
+  for (int i = 0; i < PER; ++i, pcur_next<D>(sh, pc)) {
+    topk_class<D>(topk_key<D>(sh, b, pc, psi, base, k0 + i), t, g[i], q[i]);
     cg += g[i] ? 1 : 0;
     ce += q[i] ? 1 : 0;
   }
@@ -357,18 +489,17 @@ __global__ void __launch_bounds__(NT) k_topk_scatter(const ShotDev* __restrict__
   }
   int64_t gt_before = blk_gt[blockIdx.x] - blk_gt[blk_first[s]] + bg + (xg - cg);
   int64_t eq_before = blk_eq[blockIdx.x] - blk_eq[blk_first[s]] + be + (xe - ce);
-  for (int i = 0; i < PER; ++i) {
+  pc = pc0;
+  for (int i = 0; i < PER; ++i, pcur_next<D>(sh, pc)) {
     bool keep = g[i];
     if (q[i]) keep = eq_before < take;
     const int64_t pos = sh.g_off + gt_before + (eq_before < take ? eq_before : take);
     if (keep && pos < cap) {
-      const int64_t loc = e0 + i - sh.psi_off;
-      const int64_t ql = loc / sh.np, jp = loc - ql * sh.np;
       gshot[pos] = s;
-      gq[pos] = q_flat<D>(sh, ql);
-      gp[pos] = (int32_t)jp;
-      gpsi[pos] = psi[e0 + i];
-      gpsi_f1[pos] = psi_f1[e0 + i];
+      gq[pos] = q_flat<D>(sh, pc.ql);
+      gp[pos] = (int32_t)pc.jp;
+      gpsi[pos] = widen2(psi[e0 + i]);
+      gpsi_f1[pos] = widen2(psi_f1[e0 + i]);
     }
     if (g[i]) ++gt_before;
     if (q[i]) ++eq_before;
@@ -409,23 +540,24 @@ __global__ void k_select_counts(ShotDev* shots, int nshots, const int64_t* blk,
 }  // namespace
 
 // N-largest: radix select of the cut key, then the two block counts, their scans and
-// the per-shot counts and offsets.
-static cudaError_t launch_topk_count(fga_plan_s* p) {
+// the per-shot counts and offsets. V: the element type psi is stored in.
+template <typename V>
+static cudaError_t launch_topk_count(fga_plan_s* p, const V* psi) {
   const int D = p->grid.dim;
   const unsigned sb = (unsigned)((p->nshots + 127) / 128);
   k_topk_init<<<sb, 128, 0, p->stream>>>(p->d_topk, p->nshots, (long long)p->keep_n);
   cudaError_t e = cudaMemsetAsync(p->d_topk_hist, 0, sizeof(unsigned long long) * 256 * p->nshots,
                                   p->stream);
   if (e != cudaSuccess) return e;
-  auto hist = D == 1 ? k_topk_hist<1> : (D == 2 ? k_topk_hist<2> : k_topk_hist<3>);
+  auto hist = D == 1 ? k_topk_hist<1, V> : (D == 2 ? k_topk_hist<2, V> : k_topk_hist<3, V>);
   for (int pass = 0; pass < 8; ++pass) {
     const int shift = 56 - 8 * pass;
-    hist<<<(unsigned)p->nblocks, NT, 0, p->stream>>>(p->d_shots, p->nshots, p->d_psi, p->d_topk, shift,
+    hist<<<(unsigned)p->nblocks, NT, 0, p->stream>>>(p->d_shots, p->nshots, psi, p->d_topk, shift,
                                                      p->d_topk_hist);
     k_topk_pick<<<sb, 128, 0, p->stream>>>(p->d_topk, p->d_topk_hist, p->nshots, shift);
   }
-  auto count = D == 1 ? k_topk_count<1> : (D == 2 ? k_topk_count<2> : k_topk_count<3>);
-  count<<<(unsigned)p->nblocks, NT, 0, p->stream>>>(p->d_shots, p->nshots, p->d_psi, p->d_topk, p->d_blk,
+  auto count = D == 1 ? k_topk_count<1, V> : (D == 2 ? k_topk_count<2, V> : k_topk_count<3, V>);
+  count<<<(unsigned)p->nblocks, NT, 0, p->stream>>>(p->d_shots, p->nshots, psi, p->d_topk, p->d_blk,
                                                     p->d_blk_eq);
   k_scan_exclusive<<<1, 1024, 0, p->stream>>>(p->d_blk, p->nblocks);
   k_scan_exclusive<<<1, 1024, 0, p->stream>>>(p->d_blk_eq, p->nblocks);
@@ -435,15 +567,14 @@ static cudaError_t launch_topk_count(fga_plan_s* p) {
   return cudaGetLastError();
 }
 
-// Pass 1 + scan: block counts and offsets; per-shot counts to p->d_counts.
-cudaError_t launch_select_count(fga_plan_s* p) {
-  if (p->nblocks == 0) return cudaSuccess;
-  if (p->keep_n > 0) return launch_topk_count(p);
+template <typename V>
+static cudaError_t select_count(fga_plan_s* p, const V* psi) {
+  if (p->keep_n > 0) return launch_topk_count(p, psi);
   const int64_t* d_blk_first = p->d_blk_first;
   double tau2 = p->tau * p->tau;
-  auto count = p->grid.dim == 1 ? k_select_count<1> : (p->grid.dim == 2 ? k_select_count<2>
-                                                                         : k_select_count<3>);
-  count<<<(unsigned)p->nblocks, NT, 0, p->stream>>>(p->d_shots, p->nshots, p->d_psi, p->d_max2, tau2,
+  auto count = p->grid.dim == 1 ? k_select_count<1, V>
+                                : (p->grid.dim == 2 ? k_select_count<2, V> : k_select_count<3, V>);
+  count<<<(unsigned)p->nblocks, NT, 0, p->stream>>>(p->d_shots, p->nshots, psi, p->d_max2, tau2,
                                                     p->d_blk);
   k_scan_exclusive<<<1, 1024, 0, p->stream>>>(p->d_blk, p->nblocks);
   k_select_counts<<<(p->nshots + 127) / 128, 128, 0, p->stream>>>(p->d_shots, p->nshots, p->d_blk,
@@ -452,27 +583,41 @@ cudaError_t launch_select_count(fga_plan_s* p) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_select(fga_plan_s* p) {
+template <typename V>
+static cudaError_t select_scatter(fga_plan_s* p, const V* psi, const V* psi_f1) {
   double tau2 = p->tau * p->tau;
-  if (p->nblocks == 0) return cudaSuccess;
+  const int D = p->grid.dim;
   if (p->keep_n > 0) {
-    const int D = p->grid.dim;
-    auto scatter = D == 1 ? k_topk_scatter<1> : (D == 2 ? k_topk_scatter<2> : k_topk_scatter<3>);
-    scatter<<<(unsigned)p->nblocks, NT, 0, p->stream>>>(p->d_shots, p->nshots, p->d_psi, p->d_topk,
+    auto scatter = D == 1 ? k_topk_scatter<1, V> : (D == 2 ? k_topk_scatter<2, V> : k_topk_scatter<3, V>);
+    scatter<<<(unsigned)p->nblocks, NT, 0, p->stream>>>(p->d_shots, p->nshots, psi, p->d_topk,
                                                         p->d_blk, p->d_blk_eq, p->d_blk_first,
                                                         p->d_gshot, p->d_gq, p->d_gp, p->d_gpsi,
-                                                        p->d_psi_f1, p->d_gpsi_f1, (int64_t)p->g_cap);
+                                                        psi_f1, p->d_gpsi_f1, (int64_t)p->g_cap);
     p->launches += 1;
     return cudaGetLastError();
   }
-  auto scatter = p->grid.dim == 1 ? k_select_scatter<1>
-                                   : (p->grid.dim == 2 ? k_select_scatter<2> : k_select_scatter<3>);
-  scatter<<<(unsigned)p->nblocks, NT, 0, p->stream>>>(p->d_shots, p->nshots, p->d_psi, p->d_max2,
-                                                      tau2, p->d_blk, p->d_gshot, p->d_gq, p->d_gp,
-                                                      p->d_gpsi, p->d_psi_f1, p->d_gpsi_f1,
+  auto scatter = D == 1 ? k_select_scatter<1, V> : (D == 2 ? k_select_scatter<2, V> : k_select_scatter<3, V>);
+  scatter<<<(unsigned)p->nblocks, NT, 0, p->stream>>>(p->d_shots, p->nshots, psi, p->d_max2, tau2,
+                                                      p->d_blk, p->d_gshot, p->d_gq, p->d_gp,
+                                                      p->d_gpsi, psi_f1, p->d_gpsi_f1,
                                                       (int64_t)p->g_cap);
   p->launches += 1;
   return cudaGetLastError();
+}
+
+// Pass 1 + scan: block counts and offsets; per-shot counts to p->d_counts.
+cudaError_t launch_select_count(fga_plan_s* p) {
+  if (p->nblocks == 0) return cudaSuccess;
+  if (psi_is_f32(p)) return select_count(p, reinterpret_cast<const float2*>(p->d_psi));
+  return select_count(p, static_cast<const double2*>(p->d_psi));
+}
+
+cudaError_t launch_select(fga_plan_s* p) {
+  if (p->nblocks == 0) return cudaSuccess;
+  if (psi_is_f32(p))
+    return select_scatter(p, reinterpret_cast<const float2*>(p->d_psi),
+                          reinterpret_cast<const float2*>(p->d_psi_f1));
+  return select_scatter(p, static_cast<const double2*>(p->d_psi), static_cast<const double2*>(p->d_psi_f1));
 }
 
 cudaError_t launch_counts_finish(fga_plan_s* p) {
