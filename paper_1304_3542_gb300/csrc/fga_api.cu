@@ -241,7 +241,7 @@ fga_status fga_destroy(fga_plan_t p) {
                   p->d_adj_order, p->d_adj_bucket,
                   p->d_run_geo, p->d_run_axis, p->d_run_off, p->d_resid_int,
                   p->d_psi_f1, p->d_gpsi_f1, p->d_adj_scratch, p->d_grad, p->d_resid,
-                  p->d_part, p->d_gm};
+                  p->d_part, p->d_gm, p->d_ganc};
   for (void* b : bufs)
     if (b) cudaFree(b);
   for (double* e : p->E)
@@ -709,6 +709,13 @@ static fga_status reconstruct_capacity(fga_plan_s* p, double headroom = 1.0) {
   CUDA_OR_FAIL(p, grow(&p->d_partial, &p->partial_cap,
                        tc ? (fga::partial_bytes_tc(p) + 7) / 8
                           : fga::partial_items(p) * fga::tile_points(d)));
+  if (tc) {
+    size_t cap = p->ganc_cap;
+    unsigned char* g = static_cast<unsigned char*>(p->d_ganc);
+    CUDA_OR_FAIL(p, grow(&g, &cap, fga::anchor_bytes_tc(p)));
+    p->d_ganc = g;
+    p->ganc_cap = cap;
+  }
   return FGA_OK;
 }
 

@@ -30,7 +30,7 @@ constexpr int CHG = 16;       // Gaussians per chunk -> K = 32
 constexpr int KC = 2 * CHG;   // GEMM K per chunk
 constexpr int KB = KC / 4;    // 16-byte core matrices along K (tf32: 4 per core row)
 constexpr int64_t SEGM = 2048;  // default Gaussians per work item
-constexpr int NTC = 128;      // threads per CTA
+constexpr int NTC = 256;      // threads per CTA: 0..127 make A (x) rows, 128..255 B (z) rows
 constexpr uint32_t kMaxTries = 1u << 22;
 // core-matrix (8 rows x 16 bytes) strides of the K-major operand tiles
 constexpr uint32_t kLBO = 128;       // next core matrix along K
@@ -47,55 +47,62 @@ __device__ __forceinline__ float tf32_head(float v) {
   return __uint_as_float(__float_as_uint(v) & 0xFFFFE000u);
 }
 
-// Per (Gaussian, axis) of a chunk: what every thread needs to make that Gaussian's
-// factor at its own row of the tile.
-struct Anchor {
-  uint32_t u0, ud;  // phase at the tile's first point and per point, as fractions of a turn
-  float d0, h;      // offset of the first point from Q, and the spacing
-  int lo, hi;       // rows inside the window |d| <= cut (empty when lo > hi)
-  float2 cf;        // coefficient (x axis) or 1 (z axis)
+// What a Gaussian's factors on every tile need, per axis, made once per Gaussian in FP64
+// (k_anchor_tc) so that the gather's chunk loop runs no FP64 instruction: with the grid
+// index j of a point, x_j = o + j h,
+//   phase  P (x_j - Q)/eps / (2 pi) = ub + j ud  (turns, 64-bit fixed point: exact
+//          wrap-around sums; the rounding of ud times j stays below 2^-32 turns over the
+//          grid),
+//   offset (x_j - Q)/h = (j - iq) - fq  (rows; iq = floor((Q - o)/h), fq in [0, 1)),
+//   window j in [glo, ghi] where |x_j - Q| <= kappa sqrt(eps).
+struct GaussAnchor {
+  unsigned long long ub[2], ud[2];
+  int iq[2], glo[2], ghi[2];
+  float fq[2];
+  float2 cf;  // the Gaussian's coefficient (carried by the x factor)
 };
 
-// The anchor of one Gaussian on one axis of the tile starting at x0 (FP64: the phase
-// P (x0 - Q)/eps and its per-point step P h/eps as 32-bit fractions of a turn, so that
-// the phase at row r is the exact wrap-around sum u0 + r ud).
-__device__ __forceinline__ Anchor make_anchor(double x0, double h, double inv_h, double Q, double P,
-                                              double cut, double inv_eps, float2 cf) {
-  const double inv_two_pi = 0.15915494309189535;
-  const double d0 = x0 - Q;
-  double t0 = P * d0 * inv_eps * inv_two_pi, td = P * h * inv_eps * inv_two_pi;
-  t0 -= floor(t0);
-  td -= floor(td);
+// One Gaussian on one axis of one tile (first grid index a): the phase at the tile's first
+// point and per point (32-bit turn fractions), the offset of the first point in rows,
+// and the rows of the window.
+struct Anchor {
+  uint32_t u0, ud;
+  float d0;   // (x_a - Q)/h
+  int lo, hi; // rows inside the window (empty when lo > hi)
+  float2 cf;  // coefficient (x axis) or 1 (z axis)
+};
+
+__device__ __forceinline__ Anchor tile_anchor(const GaussAnchor& ga, int axis, int64_t a) {
   Anchor an;
-  an.u0 = (uint32_t)(unsigned long long)floor(t0 * 4294967296.0 + 0.5);
-  an.ud = (uint32_t)(unsigned long long)floor(td * 4294967296.0 + 0.5);
-  an.d0 = (float)d0;
-  an.h = (float)h;
-  double lo = ceil((-cut - d0) * inv_h), hi = floor((cut - d0) * inv_h);
-  lo = lo < 0.0 ? 0.0 : lo;
-  hi = hi > (double)(TM - 1) ? (double)(TM - 1) : hi;
-  an.lo = (int)lo;
-  an.hi = (int)hi;
-  an.cf = cf;
+  const unsigned long long u = ga.ub[axis] + (unsigned long long)a * ga.ud[axis];
+  an.u0 = (uint32_t)((u + 0x80000000ull) >> 32);
+  an.ud = (uint32_t)((ga.ud[axis] + 0x80000000ull) >> 32);
+  an.d0 = (float)(int)(a - ga.iq[axis]) - ga.fq[axis];
+  const int64_t lo = ga.glo[axis] - a, hi = ga.ghi[axis] - a;
+  an.lo = lo < 0 ? 0 : (lo > TM ? TM : (int)lo);
+  an.hi = hi > TM - 1 ? TM - 1 : (hi < -1 ? -1 : (int)hi);
+  an.cf = axis == 0 ? ga.cf : make_float2(1.f, 0.f);
   return an;
 }
 
 __device__ __forceinline__ Anchor make_empty_anchor() {
   Anchor an;
   an.u0 = an.ud = 0u;
-  an.d0 = an.h = 0.f;
+  an.d0 = 0.f;
   an.lo = 1;
   an.hi = 0;
   an.cf = make_float2(0.f, 0.f);
   return an;
 }
 
-// Factor of a Gaussian at row r: cf * exp(i phase - d^2/(2 eps)) (0 outside the window).
-__device__ __forceinline__ float2 row_factor(const Anchor& an, int r, float inv_eps) {
+// Factor of a Gaussian at row r: cf * exp(i phase - d^2/(2 eps)) (0 outside the window);
+// kq = h^2 log2(e) / (2 eps) of the axis, so the envelope is 2^(-kq (d/h)^2).
+__device__ __forceinline__ float2 row_factor(const Anchor& an, int r, float kq) {
   if (r < an.lo || r > an.hi) return make_float2(0.f, 0.f);
   const float ang_scale = 1.4629180792671596e-09f;  // 2 pi / 2^32
-  const float d = fmaf((float)r, an.h, an.d0);
-  const float gs = __expf(-0.5f * d * d * inv_eps);
+  const float dr = an.d0 + (float)r;
+  float gs;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(gs) : "f"(-kq * dr * dr));
   float sn, cs;
   __sincosf((float)(int32_t)(an.u0 + (uint32_t)r * an.ud) * ang_scale, &sn, &cs);
   const float fr = gs * cs, fi = gs * sn;
@@ -108,10 +115,78 @@ __device__ __forceinline__ void store_split4(float* hi, float* lo, int o, float4
   *reinterpret_cast<float4*>(lo + o) = make_float4(v.x - h.x, v.y - h.y, v.z - h.z, v.w - h.w);
 }
 
+// floor(t 2^k) as a two's-complement integer for |t| < 2^(63-k), from the bits of t
+// (no FP64 instruction: FP64 issues at two operations per clock per SM on this part).
+// t = M 2^E with M the 53-bit significand; the result is floor(M 2^(E+k)) for t >= 0 and
+// -ceil(M 2^(E+k)) for t < 0, reduced modulo 2^64 (so that k = 64 gives the fraction of
+// t in units of 2^-64, modulo 1).
+__device__ __forceinline__ unsigned long long fixed_floor(double t, int k) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(t);
+  const int e = (int)((b >> 52) & 0x7ffull);
+  if (e == 0 || e == 0x7ff) return 0ull;  // zero, subnormal (below any unit used here), inf/NaN
+  const unsigned long long M = (b & 0xfffffffffffffull) | (1ull << 52);
+  const int sh = e - 1075 + k;
+  unsigned long long F, rem = 0ull;
+  if (sh >= 64) {
+    F = 0ull;
+  } else if (sh >= 0) {
+    F = M << sh;
+  } else if (sh > -64) {
+    F = M >> (-sh);
+    rem = M & ((1ull << (-sh)) - 1ull);
+  } else {
+    F = 0ull;
+    rem = M;
+  }
+  if (b >> 63) F = 0ull - F - (rem != 0ull ? 1ull : 0ull);  // floor of the negative value
+  return F;
+}
+
+// One thread per Gaussian: its GaussAnchor (once per Gaussian instead of once per
+// (Gaussian, tile) in the gather). G from the device when gm is given (pipeline graph).
+__global__ void k_anchor_tc(GridDev gd, const ShotDev* __restrict__ shots,
+                            const int32_t* __restrict__ gshot, const double* __restrict__ state,
+                            int64_t ld, const double2* __restrict__ coef, int64_t G,
+                            const int64_t* __restrict__ gm, double kappa, GaussAnchor* __restrict__ out) {
+  if (gm) G = gm[0];
+  const double inv_two_pi = 0.15915494309189535;
+  const long long lim = 1ll << 30;
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < G;
+       g += (int64_t)gridDim.x * blockDim.x) {
+    const ShotDev& sh = shots[gshot[g]];
+    const double ce = sh.inv_eps * inv_two_pi;
+    GaussAnchor ga;
+#pragma unroll
+    for (int axis = 0; axis < 2; ++axis) {
+      const double Q = state[axis * ld + g], P = state[(2 + axis) * ld + g];
+      // phase at grid index 0 and per index, as 64-bit fractions of a turn
+      ga.ub[axis] = fixed_floor(P * (gd.o[axis] - Q) * ce, 64);
+      ga.ud[axis] = fixed_floor(P * (gd.h[axis] * ce), 64);
+      // centre (Q - o)/h and half-width kappa sqrt(eps)/h in 32.32 fixed point; the window
+      // is [ceil(u - w), floor(u + w)] (an empty window where it leaves +-2^30)
+      const long long u = (long long)fixed_floor((Q - gd.o[axis]) * gd.inv_h[axis], 32);
+      const long long wd = (long long)fixed_floor(kappa * sh.sqrt_eps * gd.inv_h[axis], 32);
+      const long long glo = (u - wd + 0xffffffffll) >> 32, ghi = (u + wd) >> 32;
+      if (glo > -lim && ghi < lim && (u >> 32) > -lim && (u >> 32) < lim) {
+        ga.iq[axis] = (int)(u >> 32);
+        ga.fq[axis] = (float)(uint32_t)(u & 0xffffffffll) * 2.3283064365386963e-10f;  // 2^-32
+        ga.glo[axis] = (int)glo;
+        ga.ghi[axis] = (int)ghi;
+      } else {
+        ga.iq[axis] = 0;
+        ga.fq[axis] = 0.f;
+        ga.glo[axis] = (int)lim;
+        ga.ghi[axis] = -(int)lim;
+      }
+    }
+    const double2 c = coef[g];
+    ga.cf = make_float2((float)c.x, (float)c.y);
+    out[g] = ga;
+  }
+}
+
 __global__ void __launch_bounds__(NTC) k_gather_tc(GridDev gd, const ShotDev* __restrict__ shots,
-                                                   int nshots, double kappa,
-                                                   const double* __restrict__ state, int64_t ld,
-                                                   const double2* __restrict__ coef,
+                                                   int nshots, const GaussAnchor* __restrict__ ganc,
                                                    const int64_t* __restrict__ off,
                                                    const int32_t* __restrict__ list, int64_t list_cap,
                                                    const int64_t* __restrict__ seg_off, int64_t ntiles,
@@ -122,16 +197,20 @@ __global__ void __launch_bounds__(NTC) k_gather_tc(GridDev gd, const ShotDev* __
   extern __shared__ __align__(1024) unsigned char smem[];
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + kBufBytes);
   uint32_t* tbase = reinterpret_cast<uint32_t*>(smem + kBufBytes + 16);
+  __shared__ float kq_s[2];
   const int tid = threadIdx.x, warp = tid >> 5;
+  const int axis = tid >> 7, row = tid & (TM - 1);  // this thread's operand (A: x, B: z) and row
   const int64_t t = tile_of_item(seg_off, ntiles, w);
   const int s = shot_of_tile(shots, nshots, t);
   const ShotDev& sh = shots[s];
-  const double cut = kappa * sh.sqrt_eps, inv_eps = sh.inv_eps;
   int64_t a[2], b[2];
   tile_box<2>(gd, sh, t - sh.tile_off, a, b);
   if (tid == 0) {
     tc::mbar_init(bar, 1);
     tc::fence_mbar_init();
+    const double log2e = 1.4426950408889634;
+    kq_s[0] = (float)(0.5 * gd.h[0] * gd.h[0] * sh.inv_eps * log2e);
+    kq_s[1] = (float)(0.5 * gd.h[1] * gd.h[1] * sh.inv_eps * log2e);
   }
   if (warp == 0) {
     tc::tmem_alloc(tbase, TM);
@@ -145,31 +224,24 @@ __global__ void __launch_bounds__(NTC) k_gather_tc(GridDev gd, const ShotDev* __
   const int64_t l0 = min(off[t], list_cap) + (w - seg_off[t]) * seg;
   const int64_t l1 = min(min(off[t + 1], list_cap), l0 + seg);
   __shared__ Anchor anc[2][CHG];  // [axis][Gaussian of the chunk]
-  const float inv_eps_f = (float)inv_eps;
+  const float kq = kq_s[axis];
   // One operand buffer (three CTAs share an SM, so one CTA's factors are made while
   // another's MMAs run); before it is overwritten the previous chunk's MMAs must be done.
   float* Ahi = reinterpret_cast<float*>(smem);
   float* Alo = Ahi + TM * KC;
   float* Bhi = Alo + TM * KC;
   float* Blo = Bhi + TM * KC;
+  float* Ohi = axis == 0 ? Ahi : Bhi;  // this thread's operand
+  float* Olo = axis == 0 ? Alo : Blo;
   uint32_t chunks = 0;
   bool gave_up = false;
   for (int64_t c0 = l0; c0 < l1; c0 += CHG) {
     const int nc = (int)((l1 - c0) < CHG ? (l1 - c0) : CHG);
-    // anchors: thread 2 gi + axis (the factors of the previous chunk are already made)
-    Anchor an = make_empty_anchor();
-    const int gi = tid >> 1, axis = tid & 1;
-    if (tid < 2 * CHG && gi < nc) {
-      const int32_t g = list[c0 + gi];
-      const double Q = state[axis * ld + g], P = state[(2 + axis) * ld + g];
-      float2 cf = make_float2(1.f, 0.f);
-      if (axis == 0) {
-        const double2 c = coef[g];
-        cf = make_float2((float)c.x, (float)c.y);
-      }
-      const double x0 = axis == 0 ? gd.o[0] + (double)a[0] * gd.h[0] : gd.o[1] + (double)a[1] * gd.h[1];
-      an = make_anchor(x0, gd.h[axis], gd.inv_h[axis], Q, P, cut, inv_eps, cf);
-    }
+    // anchors: thread gi of each half; every thread has passed the barrier after the
+    // previous chunk's factors, so the anchors can be overwritten before the wait, whose
+    // barrier publishes them
+    if (row < CHG) anc[axis][row] = row < nc ? tile_anchor(ganc[list[c0 + row]], axis, a[axis])
+                                             : make_empty_anchor();
     // the CTA gives up as a whole, with at most the previous commit outstanding
     bool waited = true;
     if (chunks > 0) waited = tc::mbar_wait_bounded(bar, (chunks - 1) & 1u, tries);
@@ -177,19 +249,14 @@ __global__ void __launch_bounds__(NTC) k_gather_tc(GridDev gd, const ShotDev* __
       gave_up = true;
       break;
     }
-    if (tid < 2 * CHG) anc[axis][gi] = an;
-    __syncthreads();
     // operands: thread = row of the tile (x for A, z for B), four K values per store
     // A[x][2g] = Re X_g, A[x][2g+1] = -Im X_g; B[z][2g] = Re Z_g, B[z][2g+1] = Im Z_g
+    const float sg = axis == 0 ? -1.f : 1.f;
 #pragma unroll
     for (int gp = 0; gp < CHG / 2; ++gp) {
-      const float2 x0 = row_factor(anc[0][2 * gp], tid, inv_eps_f);
-      const float2 x1 = row_factor(anc[0][2 * gp + 1], tid, inv_eps_f);
-      const float2 z0 = row_factor(anc[1][2 * gp], tid, inv_eps_f);
-      const float2 z1 = row_factor(anc[1][2 * gp + 1], tid, inv_eps_f);
-      const int o = core_offset(tid, 4 * gp);
-      store_split4(Ahi, Alo, o, make_float4(x0.x, -x0.y, x1.x, -x1.y));
-      store_split4(Bhi, Blo, o, make_float4(z0.x, z0.y, z1.x, z1.y));
+      const float2 f0 = row_factor(anc[axis][2 * gp], row, kq);
+      const float2 f1 = row_factor(anc[axis][2 * gp + 1], row, kq);
+      store_split4(Ohi, Olo, core_offset(row, 4 * gp), make_float4(f0.x, sg * f0.y, f1.x, sg * f1.y));
     }
     tc::fence_proxy_async_smem();
     __syncthreads();
@@ -221,13 +288,15 @@ __global__ void __launch_bounds__(NTC) k_gather_tc(GridDev gd, const ShotDev* __
     tc::mbar_wait_bounded(bar, (chunks - 1) & 1u, kMaxTries);
   }
   tc::fence_after_sync();
-  // epilogue: warp w holds rows (x) 32w .. 32w+31, one row per thread, 128 columns (z)
-  float* dst = partial + (size_t)w * TM * TM + (size_t)(32 * warp + (tid & 31)) * TM;
+  // epilogue: warp w holds rows (x) 32 (w % 4) .. + 31, one row per thread, and takes
+  // the 64 columns (z) of half w / 4
+  const int quarter = warp & 3, half = warp >> 2;
+  float* dst = partial + (size_t)w * TM * TM + (size_t)(32 * quarter + (tid & 31)) * TM;
   float v[32];
 #pragma unroll 1
-  for (int col = 0; col < TM; col += 32) {
+  for (int col = 64 * half; col < 64 * half + 64; col += 32) {
     if (chunks > 0 && ok) {
-      tc::tmem_ld_32x32b_x32(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)col, v);
+      tc::tmem_ld_32x32b_x32(tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)col, v);
     } else {
 #pragma unroll
       for (int i = 0; i < 32; ++i) v[i] = 0.f;
@@ -289,6 +358,8 @@ size_t partial_items_tc(fga_plan_s* p) {
 
 size_t partial_bytes_tc(fga_plan_s* p) { return partial_items_tc(p) * TM * TM * sizeof(float); }
 
+size_t anchor_bytes_tc(fga_plan_s* p) { return std::max<size_t>(p->g_cap, 1) * sizeof(GaussAnchor); }
+
 cudaError_t launch_reconstruct_tc(fga_plan_s* p, double* u_dev) {
   if (p->ntiles == 0) return cudaSuccess;
   static bool attr_set = false;
@@ -304,11 +375,20 @@ cudaError_t launch_reconstruct_tc(fga_plan_s* p, double* u_dev) {
   if (e != cudaSuccess) return e;
   e = launch_scan(p, p->d_seg_off, p->ntiles);
   if (e != cudaSuccess) return e;
+  if (p->ganc_cap < anchor_bytes_tc(p)) return cudaErrorInvalidValue;  // sized by reconstruct_capacity
+  GaussAnchor* ganc = reinterpret_cast<GaussAnchor*>(p->d_ganc);
+  const int64_t G = p->dev_counts ? (int64_t)p->g_cap : p->G;
+  if (G > 0) {
+    const unsigned gb = (unsigned)std::min<int64_t>((G + 255) / 256, 4096);
+    k_anchor_tc<<<gb, 256, 0, p->stream>>>(p->grid, p->d_shots, p->d_gshot, p->d_state,
+                                            (int64_t)p->g_cap, p->d_gcoef, G,
+                                            p->dev_counts ? p->d_gm : nullptr, p->kappa, ganc);
+    p->launches += 1;
+  }
   const unsigned items = (unsigned)partial_items_tc(p);
   k_gather_tc<<<items, NTC, kSmemBytes, p->stream>>>(
-      p->grid, p->d_shots, p->nshots, p->kappa, p->d_state, (int64_t)p->g_cap, p->d_gcoef,
-      p->d_tile_off, p->d_tile_list, (int64_t)p->list_cap, p->d_seg_off, p->ntiles,
-      segment_len_tc(p), reinterpret_cast<float*>(p->d_partial), p->d_status,
+      p->grid, p->d_shots, p->nshots, ganc, p->d_tile_off, p->d_tile_list, (int64_t)p->list_cap,
+      p->d_seg_off, p->ntiles, segment_len_tc(p), reinterpret_cast<float*>(p->d_partial), p->d_status,
       p->wait_tries >= 0 ? (uint32_t)p->wait_tries : kMaxTries);
   k_reduce_tc<<<(unsigned)p->ntiles, 256, 0, p->stream>>>(p->grid, p->d_shots, p->nshots,
                                                           p->d_seg_off,
