@@ -169,7 +169,7 @@ fga_status fga_reconstruct(fga_plan_t plan, double* u_out);
 
 /* Receivers for traces: the field of Eq. recons (Re u, as fga_reconstruct writes it)
  * at the points xr (host or device, [nrx][dim] FP64, inside the grid, open axes only;
- * 1D and 2D; not with FGA_Z_DIVIDED)
+ * not with FGA_Z_DIVIDED)
  * at the record times t_m = m * record_every * dt, m = 0 .. T/(record_every dt)
  * (record_every must divide T/dt). fga_propagate then accumulates the traces while it
  * integrates the rays. nrx = 0 removes the receivers. Errors: FGA_ERR_INVALID,
@@ -190,11 +190,12 @@ fga_status fga_traces(fga_plan_t plan, double* traces);
  * traces - data and grad = dJ/dc). c_i are the velocity samples, which are the spline
  * coefficients of the medium; c enters through the rays (c, grad c, Hessian of c in
  * Eqs. characline, dzQ, dzP, a_formu) and through c(q) in the branch split (Eq. psi).
- * The derivative is that of the computed traces (discrete adjoint of the RK4 scheme,
- * checkpoints every ceil(sqrt(T/dt)) steps, segments recomputed in the reverse sweep).
+ * The derivative is that of the computed traces (discrete adjoint of the RK4 scheme; the
+ * ray states are recorded or checkpointed as fga_set_adjoint_checkpointing says).
  * residual: host or device [nshots][nrec][nrx]; grad: host or device [n...], overwritten.
  * Rays that left the grid for good contribute nothing after they stop (as in the
- * forward). Needs fga_set_receivers and fga_propagate. Synchronises the stream.
+ * forward). 1D and 2D (FGA_ERR_INVALID in 3D). Needs fga_set_receivers and
+ * fga_propagate. Synchronises the stream.
  * Errors: FGA_ERR_STATE, FGA_ERR_INVALID, FGA_ERR_OOM, FGA_ERR_CUDA. */
 fga_status fga_grad(fga_plan_t plan, const double* residual, double* grad);
 

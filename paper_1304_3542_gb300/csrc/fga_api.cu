@@ -1205,7 +1205,6 @@ fga_status fga_set_receivers(fga_plan_t p, int64_t nrx, const double* xr, int64_
     return fail(p, FGA_ERR_INVALID, "need 0 < nrx < 2^31 and receiver positions");
   if (record_every < 1 || p->nsteps % record_every != 0)
     return fail(p, FGA_ERR_INVALID, "record_every must be >= 1 and divide T/dt");
-  if (d == 3) return fail(p, FGA_ERR_INVALID, "receivers (traces, fga_grad) are supported in 1D and 2D");
   if (p->z_method != FGA_Z_DYNAMIC)
     return fail(p, FGA_ERR_INVALID, "receivers (traces, fga_grad) need z_method FGA_Z_DYNAMIC");
   for (int k = 0; k < d; ++k)
@@ -1224,7 +1223,7 @@ fga_status fga_set_receivers(fga_plan_t p, int64_t nrx, const double* xr, int64_
   std::vector<int64_t> run_off(1, 0);
   std::vector<char> in_run((size_t)nrx, 0);
   const int64_t kMinRun = 4;
-  for (int a = 0; a < d; ++a) {
+  for (int a = 0; a < (d <= 2 ? d : 0); ++a) {  // in 3D no runs: every receiver by its tile
     std::map<uint64_t, std::vector<int32_t>> groups;  // by the exact coordinate across axis a
     for (int64_t r = 0; r < nrx; ++r) {
       if (in_run[r]) continue;
@@ -1354,6 +1353,7 @@ fga_status fga_grad(fga_plan_t p, const double* residual, double* grad) {
   if (p->nrx == 0) return fail(p, FGA_ERR_STATE, "fga_grad needs receivers (fga_set_receivers)");
   if (p->stage < 2) return fail(p, FGA_ERR_STATE, "fga_grad before fga_propagate");
   if (!residual || !grad) return fail(p, FGA_ERR_INVALID, "residual and grad must not be NULL");
+  if (p->grid.dim == 3) return fail(p, FGA_ERR_INVALID, "fga_grad is supported in 1D and 2D");
   const GridDev& gd = p->grid;
   const size_t nres = (size_t)p->nshots * p->rx.nrec * p->rx.nrx;
   const double* d_res = residual;

@@ -324,7 +324,8 @@ __device__ __forceinline__ bool ray_store(const ShotDev& sh, int64_t g, const do
 template <int D, typename Fn>
 __device__ __forceinline__ void for_receivers_X(const GridDev& gd, const RxDev& rx, const double* Q,
                                                 const double* P, double cut, double inv_eps, Fn fn) {
-  for (int64_t j = 0; j < rx.nruns; ++j) {
+  // runs (1D and 2D: in 3D every receiver is evaluated from its coordinates)
+  if constexpr (D <= 2) for (int64_t j = 0; j < rx.nruns; ++j) {
     // the run's axis is a runtime value: select with conditionals rather than index Q
     // and P with it (a runtime index would move the ray state to local memory)
     const bool a1 = D == 2 && rx.run_axis[j] == 1;
@@ -408,12 +409,19 @@ __device__ __forceinline__ void for_receivers_X(const GridDev& gd, const RxDev& 
   if constexpr (D == 1) {
     for (int64_t t0 = tlo[0]; t0 <= thi[0]; ++t0)
       for (int64_t r = rx.off[t0]; r < rx.off[t0 + 1]; ++r) direct(r);
-  } else {
+  } else if constexpr (D == 2) {
     for (int64_t t0 = tlo[0]; t0 <= thi[0]; ++t0)
       for (int64_t t1 = tlo[1]; t1 <= thi[1]; ++t1) {
         const int64_t bin = t0 * rx.ntile[1] + t1;
         for (int64_t r = rx.off[bin]; r < rx.off[bin + 1]; ++r) direct(r);
       }
+  } else {
+    for (int64_t t0 = tlo[0]; t0 <= thi[0]; ++t0)
+      for (int64_t t1 = tlo[1]; t1 <= thi[1]; ++t1)
+        for (int64_t t2 = tlo[2]; t2 <= thi[2]; ++t2) {
+          const int64_t bin = (t0 * rx.ntile[1] + t1) * rx.ntile[2] + t2;
+          for (int64_t r = rx.off[bin]; r < rx.off[bin + 1]; ++r) direct(r);
+        }
   }
 }
 
@@ -422,9 +430,8 @@ __device__ __forceinline__ void for_receivers_X(const GridDev& gd, const RxDev& 
 // made trace recording about 8x slower).
 template <int D>
 __device__ __forceinline__ void add_traces(const GridDev& gd, const RxDev& rx, double cut, double inv_eps,
-                                        double q0, double q1, double p0, double p1, double er,
-                                        double ei, double* __restrict__ tr) {
-  const double Q[2] = {q0, q1}, P[2] = {p0, p1};
+                                        const double* Q, const double* P, double er, double ei,
+                                        double* __restrict__ tr) {
   for_receivers_X<D>(gd, rx, Q, P, cut, inv_eps, [&](int64_t r, const double*, double2 X) {
     red_add_f64(tr + r, er * X.x - ei * X.y);
   });
@@ -437,7 +444,6 @@ __device__ __forceinline__ void record_traces(const GridDev& gd, const ShotDev& 
                                               double kappa, const double* y, double2 psi, int s,
                                               int64_t m, double* __restrict__ traces) {
   using Lo = Layout<D>;
-  if constexpr (D == 3) return;  // receivers are not supported in 3D (rejected at the boundary)
   const double cut = kappa * sh.sqrt_eps;
   double sc = 2.0 * sh.W * sh.norm;
   double ar = y[Lo::aR], ai = y[Lo::aI];
@@ -446,8 +452,7 @@ __device__ __forceinline__ void record_traces(const GridDev& gd, const ShotDev& 
   sincos(y[Lo::S] * sh.inv_eps, &sn, &cs);
   const double er = pr * cs - pi * sn, ei = pr * sn + pi * cs;
   double* tr = traces + ((int64_t)s * rx.nrec + m) * rx.nrx;
-  add_traces<D>(gd, rx, cut, sh.inv_eps, y[Lo::Q], D == 2 ? y[Lo::Q + D - 1] : 0.0, y[Lo::P],
-                D == 2 ? y[Lo::P + D - 1] : 0.0, er, ei, tr);
+  add_traces<D>(gd, rx, cut, sh.inv_eps, y + Lo::Q, y + Lo::P, er, ei, tr);
 }
 
 }  // namespace fga

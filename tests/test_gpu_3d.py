@@ -1,6 +1,7 @@
 """The 3D path (d = 3, FP64) against the FP64 CPU oracle, element by element: the
 three-stage FBI with the branch split, the Gaussian set, the 45-value ray states and the
-field on a 20^3 grid (two 16-point tiles per axis, the second ragged)."""
+field on a 20^3 grid (two 16-point tiles per axis, the second ragged); the traces recorded
+inside the 3D ray kernel at receiver points against the oracle's traces."""
 
 import math
 
@@ -8,6 +9,7 @@ import numpy as np
 import pytest
 
 import oracle as O
+from paper_1304_3542_gb300 import fga as F
 from paper_1304_3542_gb300 import workloads as WL
 from test_gpu_parity import FIELD_TOL, _grid, check_decomposition, check_rays, oracle_field, rel, run_gpu
 
@@ -54,3 +56,49 @@ def test_lens_3d_hamiltonian_conserved():
     assert np.max(np.abs(H1 - H0) / H0) <= 1e-8
     assert np.all(np.isfinite(u)) and np.all(np.isfinite(st["A"])) and np.all(np.isfinite(st["a"]))
     plan.close()
+
+
+REC = 5
+
+
+def _receivers_3d():
+    """Two 5 x 5 layers of receivers across the packet's path (z = 0.35, 0.42) and a few
+    loose points, spread over both 16-point tiles of each axis."""
+    g = np.linspace(0.38, 0.62, 5)
+    X, Y = np.meshgrid(g, g, indexing="ij")
+    layers = [np.stack([X.ravel(), Y.ravel(), np.full(X.size, z)], axis=1) for z in (0.35, 0.42)]
+    loose = np.array([[0.5, 0.5, 0.5], [0.81, 0.47, 0.37], [0.2, 0.9, 0.4], [0.55, 0.52, 0.95]])
+    return np.ascontiguousarray(np.concatenate(layers + [loose]))
+
+
+def test_traces_3d_match_oracle():
+    """Re u at 54 receivers every 5 steps to T = 0.02 s, recorded by the 3D ray kernel,
+    against the oracle's traces of the same Gaussians (both branches summed literally by
+    the oracle): rel-L2 <= 1e-10."""
+    import torch
+
+    prob = _problem()
+    xr = _receivers_3d()
+    plan = F.plan_from_problem(prob, stream=torch.cuda.current_stream().cuda_stream,
+                               integrate_exited=True)
+    plan.set_receivers(xr, REC)
+    u0, u1 = F.stacked_initial_data(prob)
+    plan.decompose(torch.from_numpy(u0).cuda(), torch.from_numpy(u1).cuda())
+    plan.propagate()
+    tr = plan.traces()
+    with pytest.raises(F.FGAError) as ei:  # the adjoint is 1D and 2D only
+        plan.grad(np.zeros_like(tr))
+    assert ei.value.status == F.FGA_ERR_INVALID
+    plan.close()
+    sh = prob.shots[0]
+    g = _grid(prob)
+    dec = O.decompose(g, prob.velocity, sh.u0, sh.u1, sh.eps, sh.q_stride, sh.box, prob.tau)
+    gs = dec["gauss"]
+    W = O.quadrature_weight(g, sh.eps, sh.q_stride, sh.box)
+    ot = O.traces(g, prob.velocity, prob.nsteps, prob.dt, REC, gs["sigma"], gs["q"], gs["p"],
+                  gs["psi"], sh.eps, prob.kappa, W, xr)
+    assert np.linalg.norm(ot.imag) <= 1e-12 * np.linalg.norm(ot.real)
+    assert np.linalg.norm(ot.real) > 0
+    err = np.linalg.norm(tr[0] - ot.real) / np.linalg.norm(ot.real)
+    print("3D traces vs oracle: rel-L2 %.3e" % err)
+    assert err <= 1e-10, err
