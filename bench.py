@@ -45,11 +45,13 @@ L2_FLUSH_BYTES = 256 << 20
 # FP64 operations of one RK4 ray step in 2D, counted from the source of the ray
 # kernel (add/sub/mul/rsqrt/reciprocal = 1, fma = 2; conversions, compares and the
 # Newton steps that refine the hardware's rsqrt and reciprocal not counted): 4
-# right-hand sides of 285 (medium from the per-cell polynomial table 86: cell offsets 8,
+# right-hand sides of 280 (medium from the per-cell polynomial table 86: cell offsets 8,
 # four rows in z by Horner with derivatives 48, combination in x 30; |P|, n, dQ/dt,
 # dP/dt and -|P| K 18; dynamic rays 96; Z, dZ/dt, tr(adj Z dZ/dt) and det Z 60; da/dt
-# 20; dS/dt 5) plus 322 for the stage combinations of the 23 state values (7 fma each).
-FLOPS_PER_RAY_STEP_2D = 1462
+# 20) plus 308 for the stage combinations of the 22 integrated state values (7 fma
+# each; the action S has a right-hand side that vanishes identically and is carried, not
+# integrated).
+FLOPS_PER_RAY_STEP_2D = 1428
 # FP64 peak from the unit counts and clocks: 152 SMs x 2 DFMA/clk/SM x 2 flop x 2.07 GHz
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 

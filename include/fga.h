@@ -213,7 +213,8 @@ fga_status fga_run_graph(fga_plan_t plan, double* u_dev);
  * budget (variant 0: up to 255 registers per thread; 1: 168, so that 3 blocks of 128
  * fit an SM), both on a short integration of at most 64 steps, and (1) the split-K
  * segment length of the reconstruction gather (Gaussians per (tile, segment) work item;
- * 5 powers of two), then runs the full fga_propagate and fga_reconstruct with them into
+ * 5 powers of two: 256 ... 4096 in FP64, 128 ... 2048 on the tensor cores, where the
+ * FP32 accumulation of longer segments costs accuracy), then runs the full fga_propagate and fga_reconstruct with them into
  * the device buffer u_dev. Blocks the host until done. The choice stays with the plan
  * and is written to choice[3] when choice is not NULL. Ray states are identical for
  * every choice; the field changes only by the order of the FP64 (or FP32 tensor-core)

@@ -8,9 +8,15 @@
 
 namespace fga {
 
+// State of one ray: Q, P, A = dQ/dz, B = dP/dz (real and imaginary parts), a, S. S is
+// carried but not integrated: for H = c(Q)|P|, homogeneous of degree 1 in P,
+// P.dH/dP = H, so dS/dt = P.dQ/dt - H vanishes identically and S keeps its initial
+// value 0 (RK4 on a zero right-hand side is the identity). The RK4 scheme integrates the
+// first NI = NF - 1 fields.
 template <int D>
 struct Layout {
   static constexpr int NF = 2 * D + 4 * D * D + 3;
+  static constexpr int NI = NF - 1;
   static constexpr int Q = 0, P = D, AR = 2 * D, AI = 2 * D + D * D, BR = 2 * D + 2 * D * D,
                        BI = 2 * D + 3 * D * D, aR = 2 * D + 4 * D * D, aI = aR + 1, S = aR + 2;
 };
@@ -123,7 +129,6 @@ __device__ __forceinline__ bool rhs2(const GridDev& gd, const double* y, double*
   const double ar = y[Lo::aR], ai = y[Lo::aI];
   k[Lo::aR] = fma(ar, fr, -ai * qi);
   k[Lo::aI] = fma(ar, qi, ai * fr);
-  k[Lo::S] = fma(-m.c, pn, fma(p0, k[Lo::Q], p1 * k[Lo::Q + 1]));
   return pn2 > 0.0 && dd > 0.0;
 }
 
@@ -246,10 +251,6 @@ __device__ __forceinline__ bool rhs(const GridDev& gd, const double* y, double* 
   double ar = y[Lo::aR], ai = y[Lo::aI];
   k[Lo::aR] = ar * fr - ai * fi;
   k[Lo::aI] = ar * fi + ai * fr;
-  double pq = 0;
-#pragma unroll
-  for (int i = 0; i < D; ++i) pq = fma(y[Lo::P + i], k[Lo::Q + i], pq);
-  k[Lo::S] = pq - m.c * pn;
   return pn2 > 0.0 && dd > 0.0;
 }
 

@@ -164,11 +164,10 @@ __device__ void rhs_vjp(const GridDev& gd, const double* __restrict__ C, const d
     pn2 += P[i] * P[i];
   }
   const double rinv = rsqrt_nr(pn2), pn = pn2 * rinv, cop = m.c * rinv;
-  double ng = 0, Qd[D];
+  double ng = 0;
 #pragma unroll
   for (int i = 0; i < D; ++i) {
     n[i] = P[i] * rinv;
-    Qd[i] = m.c * n[i];
     ng += n[i] * m.g[i];
   }
   cx A[D][D], B[D][D], ag[D], bn[D], ak[D][D], Ad[D][D], Bd[D][D];
@@ -285,16 +284,10 @@ __device__ void rhs_vjp(const GridDev& gd, const double* __restrict__ C, const d
       Ab[j][k] = Ab[j][k] + Zb[j][k];
       Bb[j][k] = Bb[j][k] + mk(Zb[j][k].i, -Zb[j][k].r);
     }
-  // dS/dt = P.Qd - c pn
-  const double Sdb = kb[Lo::S];
+  // (S has no right-hand side: Layout)
   double Qdb[D];
 #pragma unroll
-  for (int i = 0; i < D; ++i) {
-    Qdb[i] = kb[Lo::Q + i] + Sdb * P[i];
-    Pb[i] += Sdb * Qd[i];
-  }
-  cb += -Sdb * pn;
-  pnb += -Sdb * m.c;
+  for (int i = 0; i < D; ++i) Qdb[i] = kb[Lo::Q + i];
   // Bd_jk = -(pn ak_jk + g_k bn_j);  Ad_jk = n_k ag_j + cop (B_jk - n_k bn_j)
 #pragma unroll
   for (int j = 0; j < D; ++j)
@@ -507,11 +500,10 @@ __device__ __forceinline__ void rhs2_vjp(const GridDev& gd, const double* __rest
   Zdb[1][1] = mulc(Nb, Z00);
   Zdb[1][0] = -1.0 * mulc(Nb, Z01);
   Zdb[0][1] = -1.0 * mulc(Nb, Z10);
-  // dS/dt = P.(c n) - c pn
-  const double Sdb = kb[Lo::S];
-  const double Qdb0 = fma(Sdb, P0, kb[Lo::Q]), Qdb1 = fma(Sdb, P1, kb[Lo::Q + 1]);
-  double Pb0 = Sdb * c * n0, Pb1 = Sdb * c * n1;
-  double cb = -Sdb * pn, pnb = -Sdb * c;
+  // (S has no right-hand side: Layout)
+  const double Qdb0 = kb[Lo::Q], Qdb1 = kb[Lo::Q + 1];
+  double Pb0 = 0.0, Pb1 = 0.0;
+  double cb = 0.0, pnb = 0.0;
   double nb0 = 0, nb1 = 0, gb0 = 0, gb1 = 0, copb = 0, kmb00 = 0, kmb01 = 0, kmb11 = 0;
 #pragma unroll
   for (int j = 0; j < 2; ++j) {
@@ -594,32 +586,34 @@ template <int D, typename Put>
 __device__ __forceinline__ void rk4_step_record(const GridDev& gd, double* y, double dt, Put put) {
   using Lo = Layout<D>;
   constexpr int NF = Lo::NF;
+  constexpr int NI = Lo::NI;  // S is not integrated (Layout)
   double acc[NF], tmp[NF], k[NF];
+  tmp[Lo::S] = y[Lo::S];
   const double h2 = 0.5 * dt, h6 = dt / 6.0, h3 = dt / 3.0;
   rhs<D>(gd, y, k);
 #pragma unroll
-  for (int i = 0; i < NF; ++i) {
+  for (int i = 0; i < NI; ++i) {
     acc[i] = fma(h6, k[i], y[i]);
     tmp[i] = fma(h2, k[i], y[i]);
   }
   put(0, tmp);
   rhs<D>(gd, tmp, k);
 #pragma unroll
-  for (int i = 0; i < NF; ++i) {
+  for (int i = 0; i < NI; ++i) {
     acc[i] = fma(h3, k[i], acc[i]);
     tmp[i] = fma(h2, k[i], y[i]);
   }
   put(1, tmp);
   rhs<D>(gd, tmp, k);
 #pragma unroll
-  for (int i = 0; i < NF; ++i) {
+  for (int i = 0; i < NI; ++i) {
     acc[i] = fma(h3, k[i], acc[i]);
     tmp[i] = fma(dt, k[i], y[i]);
   }
   put(2, tmp);
   rhs<D>(gd, tmp, k);
 #pragma unroll
-  for (int i = 0; i < NF; ++i) y[i] = fma(h6, k[i], acc[i]);
+  for (int i = 0; i < NI; ++i) y[i] = fma(h6, k[i], acc[i]);
 #pragma unroll
   for (int i = 0; i < D; ++i) {
     if (gd.periodic[i]) {
@@ -636,29 +630,31 @@ __device__ __forceinline__ void rk4_step(const GridDev& gd, const double* __rest
                                          double dt) {
   using Lo = Layout<D>;
   constexpr int NF = Lo::NF;
+  constexpr int NI = Lo::NI;  // S is not integrated (Layout)
   double acc[NF], tmp[NF], k[NF];
+  tmp[Lo::S] = y[Lo::S];
   const double h2 = 0.5 * dt, h6 = dt / 6.0, h3 = dt / 3.0;
   rhs<D>(gd, y, k);
 #pragma unroll
-  for (int i = 0; i < NF; ++i) {
+  for (int i = 0; i < NI; ++i) {
     acc[i] = fma(h6, k[i], y[i]);
     tmp[i] = fma(h2, k[i], y[i]);
   }
   rhs<D>(gd, tmp, k);
 #pragma unroll
-  for (int i = 0; i < NF; ++i) {
+  for (int i = 0; i < NI; ++i) {
     acc[i] = fma(h3, k[i], acc[i]);
     tmp[i] = fma(h2, k[i], y[i]);
   }
   rhs<D>(gd, tmp, k);
 #pragma unroll
-  for (int i = 0; i < NF; ++i) {
+  for (int i = 0; i < NI; ++i) {
     acc[i] = fma(h3, k[i], acc[i]);
     tmp[i] = fma(dt, k[i], y[i]);
   }
   rhs<D>(gd, tmp, k);
 #pragma unroll
-  for (int i = 0; i < NF; ++i) y[i] = fma(h6, k[i], acc[i]);
+  for (int i = 0; i < NI; ++i) y[i] = fma(h6, k[i], acc[i]);
 #pragma unroll
   for (int i = 0; i < D; ++i) {
     if (gd.periodic[i]) {
@@ -699,9 +695,13 @@ __device__ void rk4_step_adjoint(const GridDev& gd, const double* __restrict__ C
 #pragma unroll
   for (int i = 0; i < NF; ++i) Z(3, i) = lam[i];  // lambda in
   double kb[NF], zb[NF], z[NF];
+  // S is not integrated (Layout): its stage cotangents are 0 and lambda_S passes through
+  constexpr int NI = Lo::NI;
+  kb[Lo::S] = zb[Lo::S] = 0.0;
+  z[Lo::S] = Z(2, Lo::S);
   // stage 4: k4 bar = h/6 lambda
 #pragma unroll
-  for (int i = 0; i < NF; ++i) {
+  for (int i = 0; i < NI; ++i) {
     kb[i] = h6 * Z(3, i);
     zb[i] = 0.0;
     z[i] = Z(2, i);
@@ -709,7 +709,7 @@ __device__ void rk4_step_adjoint(const GridDev& gd, const double* __restrict__ C
   vjp<D>(gd, C, z, kb, zb, gradC);
   // stage 3: k3 bar = h/3 lambda + h z4 bar
 #pragma unroll
-  for (int i = 0; i < NF; ++i) {
+  for (int i = 0; i < NI; ++i) {
     lam[i] += zb[i];
     kb[i] = fma(dt, zb[i], h3 * Z(3, i));
     zb[i] = 0.0;
@@ -718,7 +718,7 @@ __device__ void rk4_step_adjoint(const GridDev& gd, const double* __restrict__ C
   vjp<D>(gd, C, z, kb, zb, gradC);
   // stage 2: k2 bar = h/3 lambda + h/2 z3 bar
 #pragma unroll
-  for (int i = 0; i < NF; ++i) {
+  for (int i = 0; i < NI; ++i) {
     lam[i] += zb[i];
     kb[i] = fma(h2, zb[i], h3 * Z(3, i));
     zb[i] = 0.0;
@@ -727,7 +727,7 @@ __device__ void rk4_step_adjoint(const GridDev& gd, const double* __restrict__ C
   vjp<D>(gd, C, z, kb, zb, gradC);
   // stage 1: k1 bar = h/6 lambda + h/2 z2 bar, at y itself
 #pragma unroll
-  for (int i = 0; i < NF; ++i) {
+  for (int i = 0; i < NI; ++i) {
     lam[i] += zb[i];
     kb[i] = fma(h2, zb[i], h6 * Z(3, i));
   }

@@ -121,28 +121,31 @@ __global__ void __launch_bounds__(128, MINB) k_rays(GridDev gd, const ShotDev* _
         ++trip;
         continue;
       }
+      // S (the last field) is not integrated: its right-hand side vanishes (Layout)
+      constexpr int NI = Lo::NI;
       double acc[NF], tmp[NF], k[NF];
+      tmp[Lo::S] = y[Lo::S];
       ok &= rhs<D>(gd, y, k);
 #pragma unroll
-      for (int i = 0; i < NF; ++i) {
+      for (int i = 0; i < NI; ++i) {
         acc[i] = fma(h6, k[i], y[i]);
         tmp[i] = fma(h2, k[i], y[i]);
       }
       ok &= rhs<D>(gd, tmp, k);
 #pragma unroll
-      for (int i = 0; i < NF; ++i) {
+      for (int i = 0; i < NI; ++i) {
         acc[i] = fma(h3, k[i], acc[i]);
         tmp[i] = fma(h2, k[i], y[i]);
       }
       ok &= rhs<D>(gd, tmp, k);
 #pragma unroll
-      for (int i = 0; i < NF; ++i) {
+      for (int i = 0; i < NI; ++i) {
         acc[i] = fma(h3, k[i], acc[i]);
         tmp[i] = fma(dt, k[i], y[i]);
       }
       ok &= rhs<D>(gd, tmp, k);
 #pragma unroll
-      for (int i = 0; i < NF; ++i) y[i] = fma(h6, k[i], acc[i]);
+      for (int i = 0; i < NI; ++i) y[i] = fma(h6, k[i], acc[i]);
 #pragma unroll
       for (int i = 0; i < D; ++i) {
         if (gd.periodic[i]) {

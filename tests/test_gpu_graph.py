@@ -142,13 +142,17 @@ def test_autotune_choice_and_results(precision):
         tuned_plan.sync()
     assert tuned_plan.tuning() == (per_sm, seg, variant)
     assert 1 <= per_sm <= 64 and variant in (0, 1)
-    base = 512 if precision == F.FGA_MIXED_TF32X3 else 256
+    base = 128 if precision == F.FGA_MIXED_TF32X3 else 256
     assert seg in [base << k for k in range(5)]  # a small case: no raise for memory
     st = tuned_plan.state(0)
     for k in ref_state:
         assert np.array_equal(st[k], ref_state[k]), k
     u_ref, u_tuned = ref.cpu().numpy(), out.cpu().numpy()
-    tol = 1e-13 if precision == F.FGA_FP64 else 1e-6
+    # FP64: sums in another order. Mixed precision: each work item's partial tile is an
+    # FP32 accumulation in tensor memory whose rounding grows with the segment length, so
+    # two segment lengths differ by up to the mixed form's own error against the FP64
+    # path, which the precision policy bounds by 1e-4
+    tol = 1e-13 if precision == F.FGA_FP64 else 1e-4
     assert np.linalg.norm(u_tuned - u_ref) <= tol * np.linalg.norm(u_ref)
     with torch.cuda.stream(stream):
         again = fresh()
