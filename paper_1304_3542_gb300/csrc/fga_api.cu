@@ -241,7 +241,7 @@ fga_status fga_destroy(fga_plan_t p) {
                   p->d_adj_order, p->d_adj_bucket,
                   p->d_run_geo, p->d_run_axis, p->d_run_off, p->d_resid_int,
                   p->d_psi_f1, p->d_gpsi_f1, p->d_adj_scratch, p->d_grad, p->d_resid,
-                  p->d_part, p->d_gm, p->d_ganc};
+                  p->d_part, p->d_gm, p->d_ganc, p->d_ray_bucket};
   for (void* b : bufs)
     if (b) cudaFree(b);
   for (double* e : p->E)
@@ -535,7 +535,10 @@ static fga_status alloc_gaussians(fga_plan_s* p, size_t need) {
   c = 0; if (p->d_gsteps) { cudaFree(p->d_gsteps); p->d_gsteps = nullptr; }
   CUDA_OR_FAIL(p, grow(&p->d_gsteps, &c, cap));
   c = 0; if (p->d_adj_order) { cudaFree(p->d_adj_order); p->d_adj_order = nullptr; }
-  CUDA_OR_FAIL(p, grow(&p->d_adj_order, &c, cap));
+  CUDA_OR_FAIL(p, grow(&p->d_adj_order, &c, cap));  // also the rays' longest-first order
+  if (!p->d_ray_bucket)
+    CUDA_OR_FAIL(p, cudaMalloc(&p->d_ray_bucket,
+                               sizeof(int64_t) * (size_t)(p->nsteps / fga::ray_order_width(p->nsteps) + 2)));
   p->g_cap = cap;
   return FGA_OK;
 }

@@ -52,7 +52,8 @@ __global__ void __launch_bounds__(128, MINB) k_rays(GridDev gd, const ShotDev* _
                                               double* __restrict__ trace_part, int64_t slice_len,
                                               int slices, unsigned long long mult,
                                               int32_t* __restrict__ gsteps,
-                                              const int64_t* __restrict__ gm) {
+                                              const int64_t* __restrict__ gm,
+                                              const int32_t* __restrict__ order) {
   using Lo = Layout<D>;
   constexpr int NF = Lo::NF;
   if (gm) {  // counts kept on the device (pipeline graph)
@@ -62,7 +63,11 @@ __global__ void __launch_bounds__(128, MINB) k_rays(GridDev gd, const ShotDev* _
   // this block's private slice of the trace sums (no other block adds into it)
   double* traces = rx.every > 0 ? trace_part + (int64_t)(blockIdx.x % slices) * slice_len : nullptr;
   unsigned long long w = atomicAdd(next, 1ull);
-  int64_t g = w < (unsigned long long)G ? work_order(w, G, mult) : G;
+  // the w-th Gaussian to integrate: longest estimated ray first when an order is given
+  auto nth = [&](unsigned long long w) -> int64_t {
+    return order ? (int64_t)order[w] : work_order(w, G, mult);
+  };
+  int64_t g = w < (unsigned long long)G ? nth(w) : G;
   unsigned long long my_steps = 0;
   bool ok = true;
   if (g < G) {
@@ -106,7 +111,7 @@ __global__ void __launch_bounds__(128, MINB) k_rays(GridDev gd, const ShotDev* _
         my_steps += (unsigned long long)step;
         w = atomicAdd(next, 1ull);
         if (w >= (unsigned long long)G) break;
-        g = work_order(w, G, mult);
+        g = nth(w);
         s = gshot[g];
         ray_init<D>(gd, shots[s], gq[g], gp[g], y);
         if (rx.every > 0) psi = gpsi[g];
@@ -167,6 +172,66 @@ __global__ void __launch_bounds__(128, MINB) k_rays(GridDev gd, const ShotDev* _
 
 namespace {
 
+// Longest-first order of the rays (the persistent kernel's tail: the rays taken last
+// should be the short ones). The length of a ray is estimated from its initial state as
+// the straight-line time to the exit box of the ray kernel (the grid widened by
+// kappa sqrt(eps) + 2h on every open axis) at the speed c(q): exact for a constant medium
+// and a ray that leaves, a ranking heuristic otherwise (the integrated rays do not depend
+// on the order). est[g] receives the estimated steps (overwritten by the ray kernel with
+// the steps taken); cnt[b] counts the rays of bucket b = (nsteps - est) / width.
+template <int D>
+__global__ void k_ray_estimate(GridDev gd, const ShotDev* __restrict__ shots, const double* __restrict__ C,
+                               int64_t G, const int64_t* __restrict__ gm, const int32_t* __restrict__ gshot,
+                               const int64_t* __restrict__ gq, const int32_t* __restrict__ gp,
+                               int64_t nsteps, double dt, double kappa, int32_t* __restrict__ est,
+                               int64_t width, unsigned long long* __restrict__ cnt) {
+  using Lo = Layout<D>;
+  if (gm) G = gm[0];
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < G;
+       g += (int64_t)gridDim.x * blockDim.x) {
+    const ShotDev& sh = shots[gshot[g]];
+    double y[Lo::NF];
+    ray_init<D>(gd, sh, gq[g], gp[g], y);
+    const double c = medium_value<D>(gd, C, y + Lo::Q);
+    double pn2 = 0.0;
+#pragma unroll
+    for (int k = 0; k < D; ++k) pn2 = fma(y[Lo::P + k], y[Lo::P + k], pn2);
+    const double cop = pn2 > 0.0 ? c / sqrt(pn2) : 0.0;
+    double t = (double)nsteps * dt;
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      if (gd.periodic[k]) continue;
+      const double reach = kappa * sh.sqrt_eps + 2.0 * gd.h[k];
+      const double lo = gd.o[k] - reach, hi = gd.o[k] + (double)(gd.n[k] - 1) * gd.h[k] + reach;
+      const double v = cop * y[Lo::P + k], q = y[Lo::Q + k];
+      if (v > 0.0) t = fmin(t, (hi - q) / v);
+      if (v < 0.0) t = fmin(t, (lo - q) / v);
+    }
+    const double st = t / dt;
+    const int64_t e = st >= (double)nsteps ? nsteps : (st > 0.0 ? (int64_t)st : 0);
+    est[g] = (int32_t)e;
+    atomicAdd(cnt + (nsteps - e) / width, 1ull);
+  }
+}
+
+// Scatter of the Gaussians into the buckets' ranges (offsets fill[b] after the scan), in
+// the spread order work_order(w) within a bucket, so that rays running at the same time
+// still come from all over the list.
+__global__ void k_ray_order(int64_t G, const int64_t* __restrict__ gm, unsigned long long mult,
+                            const int32_t* __restrict__ est, int64_t nsteps, int64_t width,
+                            unsigned long long* __restrict__ fill, int32_t* __restrict__ order) {
+  if (gm) {
+    G = gm[0];
+    mult = (unsigned long long)gm[1];
+  }
+  for (int64_t w = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; w < G;
+       w += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t g = work_order((unsigned long long)w, G, mult);
+    const int64_t b = (nsteps - est[g]) / width;
+    order[atomicAdd(fill + b, 1ull)] = (int32_t)g;
+  }
+}
+
 // One thread per table cell (cells -1 .. n per axis, stored at index + 1).
 template <int D>
 __global__ void k_medium_table(GridDev gd, const double* __restrict__ C, double* __restrict__ tab) {
@@ -222,6 +287,8 @@ cudaError_t launch_medium_table(fga_plan_s* p) {
 }
 
 unsigned long long work_order_mult(int64_t G) { return work_order_mult_of(G); }
+
+int64_t ray_order_width(int64_t nsteps) { return std::max<int64_t>(1, std::min<int64_t>(16, nsteps / 64)); }
 
 namespace {
 using RayKernel = decltype(&k_rays<2, 1>);
@@ -308,13 +375,41 @@ cudaError_t launch_rays_steps(fga_plan_s* p, int64_t nsteps, bool record) {
     rx.every = 0;
   }
   const unsigned long long mult = work_order_mult(p->G);
+  // longest estimated ray first (full integrations of rays that stop at the exit box)
+  const int32_t* order = nullptr;
+  if (!p->integrate_exited && nsteps == p->nsteps && p->d_ray_bucket) {
+    const int64_t width = ray_order_width(p->nsteps), nb = p->nsteps / width + 1;
+    e = cudaMemsetAsync(p->d_ray_bucket, 0, sizeof(int64_t) * (nb + 1), p->stream);
+    if (e != cudaSuccess) return e;
+    const int64_t Gl = p->dev_counts ? (int64_t)p->g_cap : p->G;
+    const unsigned gb = (unsigned)std::max<int64_t>(1, std::min<int64_t>((Gl + 255) / 256, 4096));
+    const int64_t* gm = p->dev_counts ? p->d_gm : nullptr;
+    unsigned long long* cnt = reinterpret_cast<unsigned long long*>(p->d_ray_bucket);
+    if (p->grid.dim == 1)
+      k_ray_estimate<1><<<gb, 256, 0, p->stream>>>(p->grid, p->d_shots, p->d_coef, p->G, gm, p->d_gshot,
+                                                  p->d_gq, p->d_gp, nsteps, p->dt, p->kappa, p->d_gsteps,
+                                                  width, cnt);
+    else if (p->grid.dim == 2)
+      k_ray_estimate<2><<<gb, 256, 0, p->stream>>>(p->grid, p->d_shots, p->d_coef, p->G, gm, p->d_gshot,
+                                                  p->d_gq, p->d_gp, nsteps, p->dt, p->kappa, p->d_gsteps,
+                                                  width, cnt);
+    else
+      k_ray_estimate<3><<<gb, 256, 0, p->stream>>>(p->grid, p->d_shots, p->d_coef, p->G, gm, p->d_gshot,
+                                                  p->d_gq, p->d_gp, nsteps, p->dt, p->kappa, p->d_gsteps,
+                                                  width, cnt);
+    e = launch_scan(p, p->d_ray_bucket, nb);
+    if (e != cudaSuccess) return e;
+    k_ray_order<<<gb, 256, 0, p->stream>>>(p->G, gm, mult, p->d_gsteps, nsteps, width, cnt, p->d_adj_order);
+    p->launches += 2;
+    order = p->d_adj_order;
+  }
   auto kern = ray_kernel(p);
   kern<<<blocks, 128, 0, p->stream>>>(p->grid, p->d_shots, p->d_coef, p->G, p->d_gshot, p->d_gq,
                                       p->d_gp, p->d_gpsi, nsteps, p->dt, p->kappa,
                                       p->integrate_exited, p->d_state, (int64_t)p->g_cap,
                                       p->d_gcoef, p->d_status, p->d_steps, p->d_steps + 1, rx,
                                       p->d_part, len, (int)slices, mult, p->d_gsteps,
-                                      p->dev_counts ? p->d_gm : nullptr);
+                                      p->dev_counts ? p->d_gm : nullptr, order);
   p->launches += 1;
   e = cudaGetLastError();
   if (e != cudaSuccess || len == 0) return e;
