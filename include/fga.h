@@ -194,8 +194,7 @@ fga_status fga_traces(fga_plan_t plan, double* traces);
  * ray states are recorded or checkpointed as fga_set_adjoint_checkpointing says).
  * residual: host or device [nshots][nrec][nrx]; grad: host or device [n...], overwritten.
  * Rays that left the grid for good contribute nothing after they stop (as in the
- * forward). 1D and 2D (FGA_ERR_INVALID in 3D). Needs fga_set_receivers and
- * fga_propagate. Synchronises the stream.
+ * forward). Needs fga_set_receivers and fga_propagate. Synchronises the stream.
  * Errors: FGA_ERR_STATE, FGA_ERR_INVALID, FGA_ERR_OOM, FGA_ERR_CUDA. */
 fga_status fga_grad(fga_plan_t plan, const double* residual, double* grad);
 

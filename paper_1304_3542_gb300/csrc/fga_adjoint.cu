@@ -266,6 +266,11 @@ __global__ void __launch_bounds__(128) k_adjoint(GridDev gd, const ShotDev* __re
       int64_t qm[D];
       if constexpr (D == 1) {
         qm[0] = qf;
+      } else if constexpr (D == 3) {
+        const int64_t nq12 = sh.nq[1] * sh.nq[2];
+        qm[0] = qf / nq12;
+        qm[1] = (qf - qm[0] * nq12) / sh.nq[2];
+        qm[2] = qf - qm[0] * nq12 - qm[1] * sh.nq[2];
       } else {
         qm[0] = qf / sh.nq[1];
         qm[1] = qf - qm[0] * sh.nq[1];
@@ -295,10 +300,11 @@ __global__ void __launch_bounds__(128) k_adjoint(GridDev gd, const ShotDev* __re
 size_t adjoint_smem(int dim) { return (size_t)4 * state_fields(dim) * 128 * sizeof(double); }
 
 cudaError_t set_adjoint_smem(int dim) {
-  return dim == 1 ? cudaFuncSetAttribute(k_adjoint<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)adjoint_smem(1))
-                  : cudaFuncSetAttribute(k_adjoint<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)adjoint_smem(2));
+  if (dim == 1)
+    return cudaFuncSetAttribute(k_adjoint<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)adjoint_smem(1));
+  if (dim == 2)
+    return cudaFuncSetAttribute(k_adjoint<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)adjoint_smem(2));
+  return cudaFuncSetAttribute(k_adjoint<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)adjoint_smem(3));
 }
 
 // Resident threads of the adjoint kernel and the scratch doubles they need.
@@ -307,11 +313,13 @@ int64_t adjoint_threads(fga_plan_s* p) {
   if (cudaGetDevice(&dev) != cudaSuccess) return 0;
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
   if (set_adjoint_smem(p->grid.dim) != cudaSuccess) return 0;
-  cudaError_t e = p->grid.dim == 1
-                      ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_adjoint<1>, 128,
-                                                                      adjoint_smem(1))
-                      : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_adjoint<2>, 128,
-                                                                      adjoint_smem(2));
+  const int d = p->grid.dim;
+  cudaError_t e = d == 1 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_adjoint<1>, 128,
+                                                                         adjoint_smem(1))
+                  : d == 2 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_adjoint<2>, 128,
+                                                                           adjoint_smem(2))
+                           : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_adjoint<3>, 128,
+                                                                           adjoint_smem(3));
   if (e != cudaSuccess) return 0;
   int64_t blocks = (int64_t)sms * (per_sm > 0 ? per_sm : 1);
   blocks = std::min<int64_t>(blocks, (p->G + 127) / 128);
@@ -356,6 +364,12 @@ cudaError_t launch_adjoint(fga_plan_s* p, const double* residual, double* gradC,
   RxDev rx = p->rx;
   if (p->grid.dim == 1)
     k_adjoint<1><<<blocks, 128, adjoint_smem(1), p->stream>>>(p->grid, p->d_shots, p->d_coef, p->G, p->d_gshot,
+                                                p->d_gq, p->d_gp, p->d_gpsi, p->d_gpsi_f1, p->nsteps,
+                                                p->dt, p->kappa, p->integrate_exited, rx, residual,
+                                                p->d_part, len, (int)slices, scratch, kseg, ncheck,
+                                                p->d_steps + 1, p->d_adj_order);
+  else if (p->grid.dim == 3)
+    k_adjoint<3><<<blocks, 128, adjoint_smem(3), p->stream>>>(p->grid, p->d_shots, p->d_coef, p->G, p->d_gshot,
                                                 p->d_gq, p->d_gp, p->d_gpsi, p->d_gpsi_f1, p->nsteps,
                                                 p->dt, p->kappa, p->integrate_exited, rx, residual,
                                                 p->d_part, len, (int)slices, scratch, kseg, ncheck,

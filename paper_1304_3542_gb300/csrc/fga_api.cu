@@ -1359,7 +1359,6 @@ fga_status fga_grad(fga_plan_t p, const double* residual, double* grad) {
   if (p->nrx == 0) return fail(p, FGA_ERR_STATE, "fga_grad needs receivers (fga_set_receivers)");
   if (p->stage < 2) return fail(p, FGA_ERR_STATE, "fga_grad before fga_propagate");
   if (!residual || !grad) return fail(p, FGA_ERR_INVALID, "residual and grad must not be NULL");
-  if (p->grid.dim == 3) return fail(p, FGA_ERR_INVALID, "fga_grad is supported in 1D and 2D");
   const GridDev& gd = p->grid;
   const size_t nres = (size_t)p->nshots * p->rx.nrec * p->rx.nrx;
   const double* d_res = residual;

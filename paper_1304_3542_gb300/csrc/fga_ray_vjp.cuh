@@ -29,10 +29,21 @@ __device__ __forceinline__ double rdot(cx a, cx b) { return a.r * b.r + a.i * b.
 // weights kept for the transposed scatter.
 template <int D>
 struct MedAD {
-  double c, g[D], K[D][D], T3[4];  // 2D third derivatives: xxx, xxz, xzz, zzz
+  // third derivatives: 2D xxx, xxz, xzz, zzz; 3D the ten of t3_index
+  double c, g[D], K[D][D], T3[D == 3 ? 10 : 4];
   int64_t idx[D][4];
   double w[D][4], dw[D][4], ddw[D][4], dddw[D][4];
 };
+
+// Index of the third derivative d^3 c / dx_i dx_j dx_k (3D) among the ten distinct ones,
+// ordered by the derivative orders (nx, ny, nz) as xxx, xxy, xxz, xyy, xyz, xzz, yyy,
+// yyz, yzz, zzz.
+__host__ __device__ constexpr int t3_index(int i, int j, int k) {
+  const int nx = (i == 0) + (j == 0) + (k == 0), ny = (i == 1) + (j == 1) + (k == 1);
+  // position of (nx, ny, nz) in the list above: orders with larger nx first, then larger ny
+  return nx == 3 ? 0 : nx == 2 ? (ny == 1 ? 1 : 2) : nx == 1 ? (ny == 2 ? 3 : ny == 1 ? 4 : 5)
+                                                             : (ny == 3 ? 6 : ny == 2 ? 7 : ny == 1 ? 8 : 9);
+}
 
 template <int D>
 __device__ __forceinline__ void medium_ad(const GridDev& gd, const double* __restrict__ C,
@@ -66,6 +77,69 @@ __device__ __forceinline__ void medium_ad(const GridDev& gd, const double* __res
     m.K[0][0] = c2 * ih * ih;
     m.T3[0] = c3 * ih * ih * ih;
     m.T3[1] = m.T3[2] = m.T3[3] = 0.0;
+  } else if constexpr (D == 3) {
+    // contract z (orders 0..3), then y, then x, keeping every combination of total order <= 3
+    double t[4][10];  // [x tap][(ny, nz) with ny + nz <= 3]: 00 01 02 03 10 11 12 20 21 30
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+#pragma unroll
+      for (int e = 0; e < 10; ++e) t[a][e] = 0.0;
+#pragma unroll
+      for (int b = 0; b < 4; ++b) {
+        const double* row = C + (m.idx[0][a] * gd.n[1] + m.idx[1][b]) * gd.n[2];
+        double sz[4] = {0, 0, 0, 0};
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const double v = __ldg(row + m.idx[2][e]);
+          sz[0] += m.w[2][e] * v;
+          sz[1] += m.dw[2][e] * v;
+          sz[2] += m.ddw[2][e] * v;
+          sz[3] += m.dddw[2][e] * v;
+        }
+        const double wy[4] = {m.w[1][b], m.dw[1][b], m.ddw[1][b], m.dddw[1][b]};
+        t[a][0] += wy[0] * sz[0];
+        t[a][1] += wy[0] * sz[1];
+        t[a][2] += wy[0] * sz[2];
+        t[a][3] += wy[0] * sz[3];
+        t[a][4] += wy[1] * sz[0];
+        t[a][5] += wy[1] * sz[1];
+        t[a][6] += wy[1] * sz[2];
+        t[a][7] += wy[2] * sz[0];
+        t[a][8] += wy[2] * sz[1];
+        t[a][9] += wy[3] * sz[0];
+      }
+    }
+    // out[(nx, ny, nz)] = sum_a wx^(nx)_a t[a][(ny, nz)]
+    auto contract = [&](int nx, int e) {
+      double v = 0.0;
+#pragma unroll
+      for (int a = 0; a < 4; ++a) {
+        const double wx = nx == 0 ? m.w[0][a] : nx == 1 ? m.dw[0][a] : nx == 2 ? m.ddw[0][a] : m.dddw[0][a];
+        v += wx * t[a][e];
+      }
+      return v;
+    };
+    const double ix = gd.inv_h[0], iy = gd.inv_h[1], iz = gd.inv_h[2];
+    m.c = contract(0, 0);
+    m.g[0] = contract(1, 0) * ix;
+    m.g[1] = contract(0, 4) * iy;
+    m.g[2] = contract(0, 1) * iz;
+    m.K[0][0] = contract(2, 0) * ix * ix;
+    m.K[1][1] = contract(0, 7) * iy * iy;
+    m.K[2][2] = contract(0, 2) * iz * iz;
+    m.K[0][1] = m.K[1][0] = contract(1, 4) * ix * iy;
+    m.K[0][2] = m.K[2][0] = contract(1, 1) * ix * iz;
+    m.K[1][2] = m.K[2][1] = contract(0, 5) * iy * iz;
+    m.T3[0] = contract(3, 0) * ix * ix * ix;  // xxx
+    m.T3[1] = contract(2, 4) * ix * ix * iy;  // xxy
+    m.T3[2] = contract(2, 1) * ix * ix * iz;  // xxz
+    m.T3[3] = contract(1, 7) * ix * iy * iy;  // xyy
+    m.T3[4] = contract(1, 5) * ix * iy * iz;  // xyz
+    m.T3[5] = contract(1, 2) * ix * iz * iz;  // xzz
+    m.T3[6] = contract(0, 9) * iy * iy * iy;  // yyy
+    m.T3[7] = contract(0, 8) * iy * iy * iz;  // yyz
+    m.T3[8] = contract(0, 6) * iy * iz * iz;  // yzz
+    m.T3[9] = contract(0, 3) * iz * iz * iz;  // zzz
   } else {
     double r[4][4];  // row sums along z: value, d, dd, ddd
 #pragma unroll
@@ -119,7 +193,42 @@ template <int D>
 __device__ __forceinline__ void medium_ad_transpose(const GridDev& gd, const MedAD<D>& m, double cb,
                                                     const double* gb, const double (*Kb)[D],
                                                     double* Qb, double* __restrict__ gradC) {
-  if constexpr (D == 1) {
+  if constexpr (D == 3) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      double q = cb * m.g[k];
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        q += gb[i] * m.K[i][k];
+#pragma unroll
+        for (int j = 0; j < 3; ++j) q += Kb[i][j] * m.T3[t3_index(i, j, k)];
+      }
+      Qb[k] += q;
+    }
+    // coefficient (a, b, e) receives al w_e + be w'_e + ga w''_e, the x and y factors of
+    // the ten terms gathered per (a, b)
+    const double ix = gd.inv_h[0], iy = gd.inv_h[1], iz = gd.inv_h[2];
+    const double kxy = (Kb[0][1] + Kb[1][0]) * ix * iy, kxz = (Kb[0][2] + Kb[2][0]) * ix * iz,
+                 kyz = (Kb[1][2] + Kb[2][1]) * iy * iz;
+    const double kxx = Kb[0][0] * ix * ix, kyy = Kb[1][1] * iy * iy, kzz = Kb[2][2] * iz * iz;
+    const double gx = gb[0] * ix, gy = gb[1] * iy, gz = gb[2] * iz;
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) {
+        const double wa = m.w[0][a], da = m.dw[0][a], dda = m.ddw[0][a];
+        const double wb = m.w[1][b], db = m.dw[1][b], ddb = m.ddw[1][b];
+        const double ww = wa * wb;
+        const double al = cb * ww + gx * da * wb + gy * wa * db + kxx * dda * wb + kyy * wa * ddb +
+                          kxy * da * db;
+        const double be = gz * ww + kxz * da * wb + kyz * wa * db;
+        const double ga = kzz * ww;
+        double* row = gradC + (m.idx[0][a] * gd.n[1] + m.idx[1][b]) * gd.n[2];
+#pragma unroll
+        for (int e = 0; e < 4; ++e)
+          red_add_f64(row + m.idx[2][e], al * m.w[2][e] + be * m.dw[2][e] + ga * m.ddw[2][e]);
+      }
+  } else if constexpr (D == 1) {
     Qb[0] += cb * m.g[0] + gb[0] * m.K[0][0] + Kb[0][0] * m.T3[0];
     double ih = gd.inv_h[0];
 #pragma unroll
@@ -205,9 +314,25 @@ __device__ void rhs_vjp(const GridDev& gd, const double* __restrict__ C, const d
       Zd[j][k] = Ad[j][k] + mk(-Bd[j][k].i, Bd[j][k].r);
     }
   cx N, Dt;
+  cx Cf[D == 3 ? 3 : 1][D == 3 ? 3 : 1];  // 3D: the cofactors of Z
   if constexpr (D == 1) {
     N = Zd[0][0];
     Dt = Z[0][0];
+  } else if constexpr (D == 3) {
+    // cofactor C[i][j] = (-1)^{i+j} det(minor ij) (cyclic minors carry the sign);
+    // N = tr(adj(Z) dZ) = sum C[i][j] dZ[i][j], det Z = sum_j Z[0][j] C[0][j]
+    N = mk(0, 0);
+    Dt = mk(0, 0);
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        const int r0 = (i + 1) % 3, r1 = (i + 2) % 3, c0 = (j + 1) % 3, c1 = (j + 2) % 3;
+        Cf[i][j] = Z[r0][c0] * Z[r1][c1] - Z[r0][c1] * Z[r1][c0];
+        N = N + Cf[i][j] * Zd[i][j];
+      }
+#pragma unroll
+    for (int j = 0; j < 3; ++j) Dt = Dt + Z[0][j] * Cf[0][j];
   } else {
     N = Z[1][1] * Zd[0][0] - Z[0][1] * Zd[1][0] - Z[1][0] * Zd[0][1] + Z[0][0] * Zd[1][1];
     Dt = Z[0][0] * Z[1][1] - Z[0][1] * Z[1][0];
@@ -260,6 +385,31 @@ __device__ void rhs_vjp(const GridDev& gd, const double* __restrict__ C, const d
   if constexpr (D == 1) {
     Zdb[0][0] = Zdb[0][0] + Nb;
     Zb[0][0] = Zb[0][0] + Dtb;
+  } else if constexpr (D == 3) {
+    // N = sum C dZ; det Z = sum_j Z[0][j] C[0][j]; C[i][j] = Z[r0][c0] Z[r1][c1] - Z[r0][c1] Z[r1][c0]
+    cx Cb[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        Zdb[i][j] = Zdb[i][j] + mulc(Nb, Cf[i][j]);
+        Cb[i][j] = mulc(Nb, Zd[i][j]);
+      }
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      Zb[0][j] = Zb[0][j] + mulc(Dtb, Cf[0][j]);
+      Cb[0][j] = Cb[0][j] + mulc(Dtb, Z[0][j]);
+    }
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        const int r0 = (i + 1) % 3, r1 = (i + 2) % 3, c0 = (j + 1) % 3, c1 = (j + 2) % 3;
+        Zb[r0][c0] = Zb[r0][c0] + mulc(Cb[i][j], Z[r1][c1]);
+        Zb[r1][c1] = Zb[r1][c1] + mulc(Cb[i][j], Z[r0][c0]);
+        Zb[r0][c1] = Zb[r0][c1] - mulc(Cb[i][j], Z[r1][c0]);
+        Zb[r1][c0] = Zb[r1][c0] - mulc(Cb[i][j], Z[r0][c1]);
+      }
   } else {
     Zb[0][0] = Zb[0][0] + mulc(Dtb, Z[1][1]);
     Zb[1][1] = Zb[1][1] + mulc(Dtb, Z[0][0]);

@@ -1,7 +1,8 @@
 """The 3D path (d = 3, FP64) against the FP64 CPU oracle, element by element: the
 three-stage FBI with the branch split, the Gaussian set, the 45-value ray states and the
 field on a 20^3 grid (two 16-point tiles per axis, the second ragged); the traces recorded
-inside the 3D ray kernel at receiver points against the oracle's traces."""
+inside the 3D ray kernel at receiver points against the oracle's traces; the 3D adjoint
+against the oracle's forward-mode derivative (dot-product test)."""
 
 import math
 
@@ -86,9 +87,6 @@ def test_traces_3d_match_oracle():
     plan.decompose(torch.from_numpy(u0).cuda(), torch.from_numpy(u1).cuda())
     plan.propagate()
     tr = plan.traces()
-    with pytest.raises(F.FGAError) as ei:  # the adjoint is 1D and 2D only
-        plan.grad(np.zeros_like(tr))
-    assert ei.value.status == F.FGA_ERR_INVALID
     plan.close()
     sh = prob.shots[0]
     g = _grid(prob)
@@ -102,3 +100,66 @@ def test_traces_3d_match_oracle():
     err = np.linalg.norm(tr[0] - ot.real) / np.linalg.norm(ot.real)
     print("3D traces vs oracle: rel-L2 %.3e" % err)
     assert err <= 1e-10, err
+
+
+def _smooth_direction_3d(n, seed):
+    rng = np.random.default_rng(seed)
+    ax = [np.linspace(0, 1, k) for k in n]
+    X, Y, Z = np.meshgrid(*ax, indexing="ij")
+    v = np.zeros(n)
+    for _ in range(4):
+        kx, ky, kz = rng.uniform(1, 3, 3)
+        v += rng.standard_normal() * (np.sin(2 * np.pi * (kx * X + rng.uniform())) *
+                                      np.cos(2 * np.pi * (ky * Y + rng.uniform())) *
+                                      np.sin(2 * np.pi * (kz * Z + rng.uniform())))
+    return v / np.abs(v).max()
+
+
+def test_adjoint_3d_against_oracle_tangent():
+    """The 3D adjoint (reverse mode through the 45-value ray state, the 64-tap spline with
+    its third derivatives and the 3 x 3 cofactor form of tr(Z^-1 dZ/dt)) against the
+    oracle's forward mode on the same frozen set: <fga_grad(w), v> = <w, Re J v> for
+    w = the traces and a random w, along a smooth v and the two cells where the gradient
+    is largest, <= 1e-12 relative."""
+    import torch
+
+    prob = _problem()
+    xr = _receivers_3d()
+    c = prob.velocity
+    plan = F.plan_from_problem(prob, stream=torch.cuda.current_stream().cuda_stream,
+                               integrate_exited=True)
+    plan.set_receivers(xr, REC)
+    u0, u1 = F.stacked_initial_data(prob)
+    plan.decompose(torch.from_numpy(u0).cuda(), torch.from_numpy(u1).cuda())
+    plan.propagate()
+    tr = plan.traces()
+    qi, pi, _ = plan.gaussians(0)
+    keys = set(zip(qi.tolist(), pi.tolist()))
+    rng = np.random.default_rng(11)
+    ws = [np.ascontiguousarray(tr), rng.standard_normal(tr.shape)]
+    grads = [plan.grad(np.ascontiguousarray(w)) for w in ws]
+    plan.close()
+    assert np.all(np.isfinite(grads[0])) and np.abs(grads[0]).max() > 0
+    sh = prob.shots[0]
+    g = _grid(prob)
+    dec = O.decompose(g, c, sh.u0, sh.u1, sh.eps, sh.q_stride, sh.box, prob.tau)
+    gk = dec["gauss"]
+    okeys = (gk["sigma"], gk["qidx"], gk["pidx"])
+    plus = okeys[0] == 1
+    assert set(zip(okeys[1][plus].tolist(), okeys[2][plus].tolist())) == keys
+    dirs = [_smooth_direction_3d(prob.n, 1)]
+    for f in np.argsort(-np.abs(grads[0].ravel()))[:2]:
+        e = np.zeros(prob.n)
+        e.ravel()[f] = 1.0
+        dirs.append(e)
+    worst = 0.0
+    for v in dirs:
+        _, jv = O.frozen_set_traces_tangent(g, c, v, sh.u0, sh.u1, sh.eps, sh.q_stride, sh.box,
+                                            okeys, prob.nsteps, prob.dt, REC, prob.kappa, xr)
+        for w, gr in zip(ws, grads):
+            lhs = float(np.sum(gr * v))
+            rhs = float(np.sum(w[0] * jv.real))
+            err = abs(lhs - rhs) / (np.linalg.norm(w) * np.linalg.norm(jv.real))
+            worst = max(worst, err)
+            assert err <= 1e-12, (lhs, rhs, err)
+    print("3D adjoint vs oracle tangent, worst relative difference %.3e" % worst)
