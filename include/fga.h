@@ -67,8 +67,8 @@ typedef enum {
 } fga_precision;
 
 typedef struct {
-  int dim;            /* 1, 2 or 3 (3: FP64 only, boxes of at most 64 points per axis,
-                         no receivers) */
+  int dim;            /* 1, 2 or 3 (3: FP64 only; psi is held for every active q, so
+                         large boxes need nq x prod(n_b) x 32 bytes of device memory) */
   int64_t n[3];       /* grid points per axis (>= 4) */
   double h[3];        /* grid spacing per axis (> 0) */
   double origin[3];   /* first grid point per axis */

@@ -373,10 +373,6 @@ fga_status fga_plan(const fga_config* cfg, const double* velocity, void* stream,
         delete p;
         return fail(nullptr, FGA_ERR_INVALID, "box must be even, >= 2 and <= 4096");
       }
-      if (d == 3 && nbk > 64) {
-        delete p;
-        return fail(nullptr, FGA_ERR_INVALID, "in 3D the box must be at most 64 points per axis");
-      }
       if (cfg->precision == FGA_MIXED_TF32X3 && k == 0 && nbk % 8 != 0) {
         delete p;
         return fail(nullptr, FGA_ERR_INVALID,

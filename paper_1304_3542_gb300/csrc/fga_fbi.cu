@@ -392,7 +392,7 @@ __global__ void __launch_bounds__(NT) k_fbi_stage2(GridDev gd, const ShotDev* __
 
 // ---------------------------------------------------------------------------
 // 3D: three separable stages over all active q of a shot, one thread per output
-// entry (FP64; boxes of at most 64 points per axis):
+// entry (FP64; the stage outputs and psi are held for every active q):
 //   stage 1 (z): G1_f[x][y][q_z][p_z]     = sum_jz f(x, y, z(q_z, jz)) E_z[p_z][jz]
 //   stage 2 (y): G2_f[x][q_y][q_z][p_y][p_z] = sum_jy E_y[p_y][jy] G1_f[x][y(q_y, jy)][q_z][p_z]
 //   stage 3 (x): psi_f[q][p_x][p_y][p_z]   = h^3 sum_jx E_x[p_x][jx] G2_f[x(q_x, jx)][q_y][q_z][p_y][p_z]

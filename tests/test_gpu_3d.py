@@ -39,6 +39,29 @@ def test_lens_3d_elementwise():
     plan.close()
 
 
+def test_lens_3d_box_above_64_points():
+    """Boxes of 72 points per axis on a 32^3 lens (q-stride 8: 4^3 q, 373 248 p per q):
+    psi+ element by element against the oracle's FFT route, the kept set outside the guard
+    band, sampled rays, and the field at 4000 sampled grid points against the oracle's
+    sum over every kept Gaussian of both branches."""
+    prob = WL.lens_3d(N=32, eps=0.012, s=8, box=72, tau=5e-2, T=0.01, k0=10 * math.pi,
+                      width2=0.02)
+    plan, counts, u = run_gpu(prob)
+    sh = prob.shots[0]
+    g = _grid(prob)
+    dec = O.decompose(g, prob.velocity, sh.u0, sh.u1, sh.eps, sh.q_stride, sh.box, prob.tau)
+    qi, pi = check_decomposition(plan, prob, dec)
+    assert counts[0] > 10000
+    check_rays(plan, prob, 0, qi[::97], pi[::97], tol_q=1e-12, tol_a=1e-11)
+    rng = np.random.default_rng(5)
+    pts = prob.grid_points()
+    pick = rng.choice(pts.shape[0], 4000, replace=False)
+    uo = oracle_field(prob, 0, dec, pts[pick])
+    assert np.linalg.norm(uo.imag) <= 1e-12 * np.linalg.norm(uo.real)
+    assert rel(u[0].ravel()[pick], uo.real) <= FIELD_TOL
+    plan.close()
+
+
 def test_lens_3d_hamiltonian_conserved():
     """T = 0.1 s (100 RK4 steps): c(Q)|P| (the Hamiltonian of the + branch) stays within
     1e-8 of its initial value along every ray, and every state is finite."""
