@@ -168,3 +168,27 @@ def test_autotune_choice_and_results(precision):
         again.set_tuning(2, 1 << 21)
     with pytest.raises(F.FGAError):
         again.set_tuning(2, 1024, 2)
+
+
+def test_ray_kernel_variants_give_identical_states():
+    """The two register budgets of the 2D ray kernel (255 and 168 registers per thread)
+    integrate every ray bit for bit alike, at full occupancy and at one block per SM."""
+    import torch
+
+    prob = _problem(N=96, T=0.05)
+    u0, u1 = F.stacked_initial_data(prob)
+    ref = None
+    for variant in (0, 1):
+        for per_sm in (0, 1):
+            plan = F.plan_from_problem(prob, stream=torch.cuda.current_stream().cuda_stream)
+            plan.set_tuning(per_sm, 0, variant)
+            plan.decompose(torch.from_numpy(u0).cuda(), torch.from_numpy(u1).cuda())
+            plan.propagate()
+            plan.sync()
+            st = plan.state(0)
+            plan.close()
+            if ref is None:
+                ref = st
+            else:
+                for k in ref:
+                    assert np.array_equal(st[k], ref[k]), (variant, per_sm, k)
