@@ -457,9 +457,10 @@ fga_status fga_plan(const fga_config* cfg, const double* velocity, void* stream,
       if (k == 0 && cfg->precision == FGA_MIXED_TF32X3) {
         // A operands of the tensor-core stage 2: Re-part rows (Re E, -Im E) and Im-part rows
         // (Im E, Re E) over K = 2 jx, each split into a TF32 head and an FP32 tail, laid
-        // out as the shared-memory image one bulk copy fills per K chunk of 8 complex jx:
-        // [m tile of 128 p_x][chunk][part: Re head, Re tail, Im head, Im tail][K quad 4]
-        // [8-row group 16][row 8][4 floats], rows past n_b zero (fga::fbi_a_image_floats)
+        // out as the shared-memory image one bulk copy fills per K chunk of 8 complex jx,
+        // the Re-part and Im-part rows stacked as one 256-row operand:
+        // [m tile of 128 p_x][chunk][head, tail][K quad 4][8-row group 32: Re part 0..15,
+        // Im part 16..31][row 8][4 floats], rows past n_b zero (fga::fbi_a_image_floats)
         const int nb = sh.nb[0];
         const int mtiles = (nb + 127) / 128, nchunk = nb / 8;
         std::vector<float> A((size_t)mtiles * nchunk * 4 * 4 * 512, 0.0f);
@@ -482,7 +483,7 @@ fga_status fga_plan(const fga_config* cfg, const double* velocity, void* stream,
                 split(vals[part][c], hi, lo);
                 for (int hl = 0; hl < 2; ++hl) {
                   const size_t at =
-                      ((((((size_t)mt * nchunk + chunk) * 4 + (2 * part + hl)) * 4 + quad) * 16 +
+                      ((((((size_t)mt * nchunk + chunk) * 2 + hl) * 4 + quad) * 32 + 16 * part +
                         row / 8) * 8 + row % 8) * 4 + 2 * slot + c;
                   A[at] = hl == 0 ? hi : lo;
                 }

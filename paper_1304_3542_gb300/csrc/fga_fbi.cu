@@ -532,10 +532,15 @@ __global__ void k_fbi3_stage3(GridDev gd, const ShotDev* __restrict__ shots,
 // the B image is what stage 1 writes (for each q column the pairs of stage-1 rows of
 // either parity, so that every q's box, whatever the parity of its first row, reads its
 // chunk as one contiguous block). K-major without swizzle: the core matrices (8 rows x
-// 16 bytes) of one K quad lie for all sixteen 8-row groups in a row (SBO = 128 B), the
-// four K quads of a chunk 2 KiB apart (LBO). One thread runs a 3-stage pipeline: bulk
+// 16 bytes) of one K quad lie for all 8-row groups in a row (SBO = 128 B), the four K
+// quads of a chunk 2 KiB apart (LBO) in the B image; the A image stacks the Re-part and
+// Im-part rows (32 groups, K quads 4 KiB apart), so that one MMA of N = 256 fills both
+// accumulators of a field. The tensor cores read their operands from shared memory at
+// about 128 B per clock; two MMAs of 128 x 128 x 8 (8 KiB each) per field would keep
+// that bandwidth saturated, one of 128 x 256 x 8 (12 KiB) leaves room for the bulk
+// copies. One thread runs a 3-stage pipeline: bulk
 // copies (TMA, cp.async.bulk) of a chunk's A (32 KiB) and B (4 x 8 KiB) into a stage
-// complete on the stage's "full" mbarrier; the chunk's 24 MMAs are committed to its
+// complete on the stage's "full" mbarrier; the chunk's 12 MMAs are committed to its
 // "empty" mbarrier, after which the stage is refilled three chunks ahead; the last
 // commit goes to "done", which the whole CTA waits on before the epilogue. Every wait
 // is bounded; a thread that gives up issues nothing more and waits for what it has in
@@ -543,8 +548,8 @@ __global__ void k_fbi3_stage3(GridDev gd, const ShotDev* __restrict__ shots,
 // is released.
 //
 // The MMAs compute the transpose psi^T = B_f A^T (B_f as the M operand), so that the
-// accumulator's TMEM lanes are p_z and its columns p_x. Epilogue (8 warps, two per TMEM
-// lane quarter, each taking half of the 128 columns, 16 at a time): a thread holds 16
+// accumulator's TMEM lanes are p_z and its columns p_x. Epilogue (16 warps, four per
+// TMEM lane quarter, each taking a quarter of the 128 columns, 16 at a time): a thread holds 16
 // p_x values of its p_z column, and every store of a warp is one contiguous run of 32
 // p_z columns of a p_x row, straight from registers. The branch split is FP32
 // arithmetic on the FP32 accumulations (with 1/|p| from rsqrtf), stored as FP32 pairs:
@@ -556,13 +561,17 @@ __global__ void k_fbi3_stage3(GridDev gd, const ShotDev* __restrict__ shots,
 // which any value whose FP64 square could be the largest is.
 constexpr int FT = 128;        // tile edge in p_z (GEMM M) and p_x (GEMM N)
 constexpr int FJ = 8;          // complex jx per chunk -> K = 16
-constexpr int FNT = 256;       // 8 warps: warp w reads TMEM lanes 32 (w % 4) .., columns half w / 4
+constexpr int FNT = 512;       // 16 warps: warp w reads TMEM lanes 32 (w % 4) .., column quarter w / 4
+constexpr int FCOLS = 32;      // p_x columns of the accumulators per epilogue warp
 constexpr int FSTAGES = 3;
 constexpr uint32_t kFbiOp = FT * 2 * FJ * sizeof(float);   // one operand part of a chunk: 8 KiB
-constexpr uint32_t kFbiStage = 8 * kFbiOp;                  // A: 4 parts, B: 2 fields x 2 parts
-constexpr uint32_t kFbiLBO = 2048, kFbiSBO = 128;
+constexpr uint32_t kFbiStage = 8 * kFbiOp;  // A: head and tail of 256 rows, B: 2 fields x 2 parts
+constexpr uint32_t kFbiLBO = 2048, kFbiSBO = 128;  // B operand (128 rows): K quads 2 KiB apart
+constexpr uint32_t kFbiALBO = 4096;                 // A operand (256 stacked rows): K quads 4 KiB apart
 constexpr size_t kFbiBarOff = (size_t)FSTAGES * kFbiStage;
 constexpr size_t kFbiSmem = kFbiBarOff + 128;
+static_assert((size_t)FCOLS * FNT * sizeof(float2) <= kFbiBarOff,
+              "the epilogue's values fit in the stage buffers");
 constexpr uint32_t kFbiTries = 1u << 22;
 
 // IEEE binary32 -> binary64 in integer arithmetic (exact, keeps the FP64 pipe free):
@@ -650,7 +659,10 @@ __global__ void __launch_bounds__(FNT) k_fbi_stage2_tc(GridDev gd, const ShotDev
           tc::bulk_g2s(base + (4 + 2 * f + part) * kFbiOp, src, kFbiOp, &full[st]);
         }
     };
-    const uint32_t idesc = tc::idesc_f32acc(tc::kFmtTF32, FT, FT);
+    // N = 256: the A image stacks the Re-part and Im-part rows, so one MMA fills both
+    // accumulators of a field (half the instructions and a quarter less shared-memory
+    // operand traffic than two 128-column MMAs)
+    const uint32_t idesc = tc::idesc_f32acc(tc::kFmtTF32, FT, 2 * FT);
     int loaded = 0, fulled = 0, committed = 0, emptied = 0;  // chunks issued / observed
     bool ok = true;
     for (; loaded < FSTAGES && loaded < nchunk; ++loaded) load(loaded);
@@ -665,21 +677,19 @@ __global__ void __launch_bounds__(FNT) k_fbi_stage2_tc(GridDev gd, const ShotDev
       const uint32_t base = tc::smem_u32(smem + (size_t)st * kFbiStage);
 #pragma unroll
       for (int ks = 0; ks < 2; ++ks) {
-        const uint32_t step = ks * 2 * kFbiLBO;  // two K quads = 8 tf32
 #pragma unroll
-        for (int f = 0; f < 2; ++f)
-#pragma unroll
-          for (int cc = 0; cc < 2; ++cc) {
-            // transposed product psi^T = B_f A^T: the accumulator's lanes are p_z, its
-            // columns p_x, so the epilogue stores p_z-contiguous rows from registers
-            const uint32_t d = tmem + (uint32_t)((2 * f + cc) * FT);
-            const uint32_t ah = base + (2 * cc) * kFbiOp + step, al = ah + kFbiOp;
-            const uint32_t bh = base + (4 + 2 * f) * kFbiOp + step, bl = bh + kFbiOp;
-            tc::mma_tf32(d, tc::smem_desc(bh, kFbiLBO, kFbiSBO), tc::smem_desc(ah, kFbiLBO, kFbiSBO), idesc,
-                         (c > 0 || ks > 0) ? 1u : 0u);
-            tc::mma_tf32(d, tc::smem_desc(bl, kFbiLBO, kFbiSBO), tc::smem_desc(ah, kFbiLBO, kFbiSBO), idesc, 1u);
-            tc::mma_tf32(d, tc::smem_desc(bh, kFbiLBO, kFbiSBO), tc::smem_desc(al, kFbiLBO, kFbiSBO), idesc, 1u);
-          }
+        for (int f = 0; f < 2; ++f) {
+          // transposed product psi^T = B_f A^T: the accumulator's lanes are p_z, its
+          // columns p_x (Re part in the first 128, Im part in the next 128), so the
+          // epilogue stores p_z-contiguous rows from registers
+          const uint32_t d = tmem + (uint32_t)(2 * f * FT);
+          const uint32_t ah = base + ks * 2 * kFbiALBO, al = ah + 2 * kFbiOp;
+          const uint32_t bh = base + (4 + 2 * f) * kFbiOp + ks * 2 * kFbiLBO, bl = bh + kFbiOp;
+          tc::mma_tf32(d, tc::smem_desc(bh, kFbiLBO, kFbiSBO), tc::smem_desc(ah, kFbiALBO, kFbiSBO), idesc,
+                       (c > 0 || ks > 0) ? 1u : 0u);
+          tc::mma_tf32(d, tc::smem_desc(bl, kFbiLBO, kFbiSBO), tc::smem_desc(ah, kFbiALBO, kFbiSBO), idesc, 1u);
+          tc::mma_tf32(d, tc::smem_desc(bh, kFbiLBO, kFbiSBO), tc::smem_desc(al, kFbiALBO, kFbiSBO), idesc, 1u);
+        }
       }
       tc::mma_commit(&empty[st]);
       ++committed;
@@ -723,7 +733,7 @@ __global__ void __launch_bounds__(FNT) k_fbi_stage2_tc(GridDev gd, const ShotDev
   // epilogue: TMEM lane 32 quarter + l holds p_z column n0 + 32 quarter + l, TMEM column
   // j the p_x row m0 + j; a warp takes 64 of the rows, 16 at a time, and each of its
   // stores is one contiguous run of 32 p_z columns of a row (FP32 pairs)
-  const int lane = tid & 31, quarter = warp & 3, half = warp >> 2;
+  const int lane = tid & 31, quarter = warp & 3, part = warp >> 2;
   const float h2 = h2_s, c1 = c1_s;
   const float psx = psx_s, psz = psz_s;
   float2* out0 = psi + sh.psi_off + ql * sh.np;
@@ -738,7 +748,7 @@ __global__ void __launch_bounds__(FNT) k_fbi_stage2_tc(GridDev gd, const ShotDev
   float amax = 0.0f;  // largest |Re|, |Im| of the stored values (fmaxf leaves NaN out)
   if (ok) {
 #pragma unroll 1
-    for (int cb = 64 * half; cb < 64 * half + 64; cb += 16) {
+    for (int cb = FCOLS * part; cb < FCOLS * part + FCOLS; cb += 16) {
       if (m0 + cb >= nbx) break;  // uniform over the warp
       const uint32_t lane_base = tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)cb;
       uint32_t r0r[16], r0i[16], r1r[16], r1i[16];
@@ -753,7 +763,7 @@ __global__ void __launch_bounds__(FNT) k_fbi_stage2_tc(GridDev gd, const ShotDev
       tc::reg_fence16(r1i);
       const int mb = (int)m0 + cb;                 // p_x row of i = 0
       const float mxf0 = (float)(mb - (int)(nbx / 2));
-      float2* vk = vs + (cb - 64 * half) * FNT + tid;
+      float2* vk = vs + (cb - FCOLS * part) * FNT + tid;
 #pragma unroll
       for (int i = 0; i < 16; ++i) {
         const int m = mb + i;
@@ -787,8 +797,8 @@ __global__ void __launch_bounds__(FNT) k_fbi_stage2_tc(GridDev gd, const ShotDev
   if (ok && amax != 0.0f) {
     const bool scaled = amax >= 0x1p-100f && amax < INFINITY;
     const float sc = scaled ? ldexpf(1.0f, -ilogbf(amax)) : 1.0f;
-    const int64_t rows = nbx - (m0 + 64 * half);  // rows of this warp's half that exist
-    const int nk = rows >= 64 ? 64 : (rows > 0 ? (int)rows : 0);
+    const int64_t rows = nbx - (m0 + FCOLS * part);  // rows of this warp's part that exist
+    const int nk = rows >= FCOLS ? FCOLS : (rows > 0 ? (int)rows : 0);
     float fmx = 0.0f;
     if (scaled) {
 #pragma unroll 4
