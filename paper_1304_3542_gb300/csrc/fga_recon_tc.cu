@@ -109,12 +109,6 @@ __device__ __forceinline__ float2 row_factor(const Anchor& an, int r, float kq) 
   return make_float2(an.cf.x * fr - an.cf.y * fi, an.cf.x * fi + an.cf.y * fr);
 }
 
-__device__ __forceinline__ void store_split4(float* hi, float* lo, int o, float4 v) {
-  const float4 h = make_float4(tf32_head(v.x), tf32_head(v.y), tf32_head(v.z), tf32_head(v.w));
-  *reinterpret_cast<float4*>(hi + o) = h;
-  *reinterpret_cast<float4*>(lo + o) = make_float4(v.x - h.x, v.y - h.y, v.z - h.z, v.w - h.w);
-}
-
 // floor(t 2^k) as a two's-complement integer for |t| < 2^(63-k), from the bits of t
 // (no FP64 instruction: FP64 issues at two operations per clock per SM on this part).
 // t = M 2^E with M the 53-bit significand; the result is floor(M 2^(E+k)) for t >= 0 and
@@ -249,14 +243,41 @@ __global__ void __launch_bounds__(NTC) k_gather_tc(GridDev gd, const ShotDev* __
       gave_up = true;
       break;
     }
-    // operands: thread = row of the tile (x for A, z for B), four K values per store
-    // A[x][2g] = Re X_g, A[x][2g+1] = -Im X_g; B[z][2g] = Re Z_g, B[z][2g+1] = Im Z_g
-    const float sg = axis == 0 ? -1.f : 1.f;
+    // operands: A[x][2g] = Re X_g, A[x][2g+1] = -Im X_g; B[z][2g] = Re Z_g, B[z][2g+1] =
+    // Im Z_g. Thread (g, t8) of the half makes Gaussian g's factors on the 16 rows
+    // t8 + 8j by the recurrence f(r + 8) = f(r) R(r), R(r + 8) = R(r) C: the first row of
+    // the window in that class is evaluated directly (coefficient included), so no factor
+    // starts from an underflowed value; the other rows cost a complex product each
+    {
+      const float sg = axis == 0 ? -1.f : 1.f;
+      const int g = row >> 3, t8 = row & 7;
+      const Anchor an = anc[axis][g];
+      const int r0 = an.lo + ((t8 - an.lo) & 7);  // first row >= lo with row = t8 (mod 8)
+      float2 f = row_factor(an, r0 <= an.hi ? r0 : an.lo, kq);  // zero for an empty window
+      // R(r0) = exp(-kq (2 (d0 + r0) 8 + 64)) e^{i 8 ud 2 pi / 2^32} (kq already in log2 units)
+      const float ang8 = (float)(int32_t)(8u * an.ud) * 1.4629180792671596e-09f;
+      float s8, c8;
+      __sincosf(ang8, &s8, &c8);
+      float g8;
+      asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(g8) : "f"(-kq * (16.0f * (an.d0 + (float)r0) + 64.0f)));
+      float Rr = g8 * c8, Ri = g8 * s8, cc;
+      asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(cc) : "f"(-128.0f * kq));  // C = exp(-kq 2 8^2)
 #pragma unroll
-    for (int gp = 0; gp < CHG / 2; ++gp) {
-      const float2 f0 = row_factor(anc[axis][2 * gp], row, kq);
-      const float2 f1 = row_factor(anc[axis][2 * gp + 1], row, kq);
-      store_split4(Ohi, Olo, core_offset(row, 4 * gp), make_float4(f0.x, sg * f0.y, f1.x, sg * f1.y));
+      for (int j = 0; j < 16; ++j) {
+        const int r = t8 + 8 * j;
+        const bool in = r >= r0 && r <= an.hi;
+        const float vr = in ? f.x : 0.f, vi = in ? sg * f.y : 0.f;
+        const int o = core_offset(r, 2 * g);
+        const float hr = tf32_head(vr), hi = tf32_head(vi);
+        *reinterpret_cast<float2*>(Ohi + o) = make_float2(hr, hi);
+        *reinterpret_cast<float2*>(Olo + o) = make_float2(vr - hr, vi - hi);
+        if (r >= r0) {  // advance to row r + 8
+          const float nr = f.x * Rr - f.y * Ri, ni = f.x * Ri + f.y * Rr;
+          f = make_float2(nr, ni);
+          Rr *= cc;
+          Ri *= cc;
+        }
+      }
     }
     tc::fence_proxy_async_smem();
     __syncthreads();
