@@ -16,6 +16,8 @@
 #include <algorithm>
 #include <climits>
 
+#include <type_traits>
+
 #include "fga_internal.cuh"
 #include "fga_medium.cuh"
 #include "fga_tc.cuh"
@@ -114,7 +116,24 @@ __device__ __forceinline__ double psi_plus(const ShotDev& sh, int64_t jp, double
   return abs2_rn(out);
 }
 
-// TF32 head and FP32 tail of a complex value: (Re head, Re tail, Im head, Im tail).
+// Scalar and complex types of stage 1: FP64 (the FP64 path) or FP32 (the mixed path).
+template <typename T> struct Cplx;
+template <> struct Cplx<double> {
+  using type = double2;
+  static __device__ __forceinline__ double2 make(double x, double y) { return make_double2(x, y); }
+};
+template <> struct Cplx<float> {
+  using type = float2;
+  static __device__ __forceinline__ float2 make(float x, float y) { return make_float2(x, y); }
+};
+
+// TF32 head and FP32 tail of a complex value: (Re head, Re tail, Im head, Im tail); for
+// an FP32 value head + tail is the value itself.
+__device__ __forceinline__ float4 split4(float2 v) {
+  const float hr = __uint_as_float(__float_as_uint(v.x) & 0xFFFFE000u);
+  const float hi = __uint_as_float(__float_as_uint(v.y) & 0xFFFFE000u);
+  return make_float4(hr, v.x - hr, hi, v.y - hi);
+}
 __device__ __forceinline__ float4 split4(double2 v) {
   const float xr = (float)v.x, xi = (float)v.y;
   const float hr = __uint_as_float(__float_as_uint(xr) & 0xFFFFE000u);
@@ -126,7 +145,11 @@ __device__ __forceinline__ float4 split4(double2 v) {
 // D == 2: m = (row r, q_z local), k runs along the last axis of the box; the
 //         result goes to the stage-1 buffer.
 // D == 1: m = q local, and the epilogue forms psi+.
-template <int D>
+// T: the arithmetic (double; float in the mixed path, 2D, where the result becomes the
+// split-TF32 B operand of the tensor-core stage 2: FP32 products, each an exact FP32
+// rounding and so finer than the TF32 split products that consume them, accumulated in
+// FP32 on the CUDA cores, which run FP32 at 62 times the FP64 rate).
+template <int D, typename T = double>
 __global__ void __launch_bounds__(NT) k_fbi_stage1(GridDev gd, const ShotDev* __restrict__ shots,
                                                    const double* __restrict__ u0,
                                                    const double* __restrict__ u1,
@@ -144,19 +167,20 @@ __global__ void __launch_bounds__(NT) k_fbi_stage1(GridDev gd, const ShotDev* __
   const int64_t N = nbl, K = nbl;
   const int64_t m0 = (int64_t)blockIdx.y * BM, n0 = (int64_t)blockIdx.x * BN;
   if (m0 >= M || n0 >= N) return;
-  __shared__ double As[2][BK][BM];
-  __shared__ double2 Bs[BK][BN];
+  using T2 = typename Cplx<T>::type;
+  __shared__ T As[2][BK][BM];
+  __shared__ T2 Bs[BK][BN];
   __shared__ double cq_s[BM];
   const int t = threadIdx.x, tx = t % 16, ty = t / 16;
   const double* f0 = u0 + (int64_t)s * gd.npts;
   const double* f1 = u1 + (int64_t)s * gd.npts;
-  double2 acc0[2][2], acc1[2][2];
+  T2 acc0[2][2], acc1[2][2];
 #pragma unroll
   for (int i = 0; i < 2; ++i)
 #pragma unroll
     for (int j = 0; j < 2; ++j) {
-      acc0[i][j] = make_double2(0, 0);
-      acc1[i][j] = make_double2(0, 0);
+      acc0[i][j] = Cplx<T>::make(0, 0);
+      acc1[i][j] = Cplx<T>::make(0, 0);
     }
   const double2* ELAST = sh.E[L];  // last-axis window-DFT matrix [n_b][n_b]
   for (int64_t k0 = 0; k0 < K; k0 += BK) {
@@ -183,8 +207,8 @@ __global__ void __launch_bounds__(NT) k_fbi_stage1(GridDev gd, const ShotDev* __
           v1 = __ldg(f1 + idx);
         }
       }
-      As[0][kk][mm] = v0;
-      As[1][kk][mm] = v1;
+      As[0][kk][mm] = (T)v0;
+      As[1][kk][mm] = (T)v1;
     }
 #pragma unroll
     for (int i = 0; i < 2; ++i) {
@@ -193,13 +217,13 @@ __global__ void __launch_bounds__(NT) k_fbi_stage1(GridDev gd, const ShotDev* __
       int64_t n = n0 + nn, k = k0 + kk;
       double2 v = make_double2(0, 0);
       if (n < N && k < K) v = __ldg(ELAST + n * K + k);
-      Bs[kk][nn] = v;
+      Bs[kk][nn] = Cplx<T>::make((T)v.x, (T)v.y);
     }
     __syncthreads();
 #pragma unroll
     for (int kk = 0; kk < BK; ++kk) {
-      double a0[2], a1[2];
-      double2 b[2];
+      T a0[2], a1[2];
+      T2 b[2];
 #pragma unroll
       for (int i = 0; i < 2; ++i) {
         a0[i] = As[0][kk][ty + 16 * i];
@@ -247,13 +271,13 @@ __global__ void __launch_bounds__(NT) k_fbi_stage1(GridDev gd, const ShotDev* __
                 *reinterpret_cast<float2*>(img + b + npair * 512) = make_float2(v.y, v.w);   // tail
               }
             }
-          } else {
+          } else if constexpr (std::is_same<T, double>::value) {
             g1[sh.g1_off + m * N + n] = acc0[i][j];
             g1[sh.g1_off + plane + m * N + n] = acc1[i][j];
           }
         }
       }
-  } else {
+  } else if constexpr (std::is_same<T, double>::value) {
     // c(q) for the rows of this tile
     if (t < BM) {
       int64_t m = m0 + t;
@@ -922,9 +946,12 @@ cudaError_t launch_fbi(fga_plan_s* p, const double* u0, const double* u1) {
     p->launches += 1;
     return cudaGetLastError();
   }
-  k_fbi_stage1<2><<<g1grid, NT, 0, p->stream>>>(p->grid, p->d_shots, u0, u1, p->d_coef, p->d_g1,
-                                                p->d_psi, p->d_psi_f1, p->d_max2,
-                                                p->precision == FGA_MIXED_TF32X3 ? 1 : 0);
+  if (p->precision == FGA_MIXED_TF32X3)
+    k_fbi_stage1<2, float><<<g1grid, NT, 0, p->stream>>>(p->grid, p->d_shots, u0, u1, p->d_coef, p->d_g1,
+                                                        p->d_psi, p->d_psi_f1, p->d_max2, 1);
+  else
+    k_fbi_stage1<2><<<g1grid, NT, 0, p->stream>>>(p->grid, p->d_shots, u0, u1, p->d_coef, p->d_g1,
+                                                  p->d_psi, p->d_psi_f1, p->d_max2, 0);
   if (maxQ > 65535) return cudaErrorInvalidConfiguration;
   p->launches += 2;
   if (p->precision == FGA_MIXED_TF32X3) {
