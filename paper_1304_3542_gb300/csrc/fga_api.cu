@@ -241,7 +241,7 @@ fga_status fga_destroy(fga_plan_t p) {
                   p->d_adj_order, p->d_adj_bucket,
                   p->d_run_geo, p->d_run_axis, p->d_run_off, p->d_resid_int,
                   p->d_psi_f1, p->d_gpsi_f1, p->d_adj_scratch, p->d_grad, p->d_resid,
-                  p->d_part, p->d_gm, p->d_ganc, p->d_ray_bucket};
+                  p->d_part, p->d_gm, p->d_ganc, p->d_ray_bucket, p->d_rng};
   for (void* b : bufs)
     if (b) cudaFree(b);
   for (double* e : p->E)
@@ -705,6 +705,7 @@ static fga_status reconstruct_capacity(fga_plan_s* p, double headroom = 1.0) {
   int64_t chunk;
   fga::bin_splits(p, &nsplit, &chunk);
   CUDA_OR_FAIL(p, grow(&p->d_bin_off, &p->bin_cap, (size_t)p->ntiles * nsplit + 1));
+  CUDA_OR_FAIL(p, grow(&p->d_rng, &p->rng_cap, (size_t)d * 2 * std::max<size_t>(p->g_cap, 1)));
   const bool tc = p->precision == FGA_MIXED_TF32X3;
   CUDA_OR_FAIL(p, grow(&p->d_partial, &p->partial_cap,
                        tc ? (fga::partial_bytes_tc(p) + 7) / 8

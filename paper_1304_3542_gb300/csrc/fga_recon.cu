@@ -94,6 +94,87 @@ __global__ void __launch_bounds__(NT) k_bin(GridDev gd, const ShotDev* __restric
   if (!FILL && threadIdx.x == 0) cnt[blockIdx.x] = total;
 }
 
+// The conservative grid-index window [lo, hi] of every Gaussian along every axis (as
+// window_range, once per Gaussian instead of once per (Gaussian, tile) in each binning
+// pass): rng[(2 k) ld + g] = lo, rng[(2 k + 1) ld + g] = hi, clamped to +-2^30. G from the
+// device when gm is given (pipeline graph).
+template <int D>
+__global__ void k_bin_ranges(GridDev gd, const ShotDev* __restrict__ shots,
+                             const int32_t* __restrict__ gshot, double kappa,
+                             const double* __restrict__ state, int64_t ld, int64_t G,
+                             const int64_t* __restrict__ gm, int32_t* __restrict__ rng) {
+  if (gm) G = gm[0];
+  const double lim = 1073741824.0;
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < G;
+       g += (int64_t)gridDim.x * blockDim.x) {
+    const double cut = kappa * shots[gshot[g]].sqrt_eps;
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      const double Q = state[k * ld + g];
+      const double lo = floor((Q - cut - gd.o[k]) * gd.inv_h[k]) - 1.0;
+      const double hi = ceil((Q + cut - gd.o[k]) * gd.inv_h[k]) + 1.0;
+      rng[(2 * k) * ld + g] = (int32_t)fmin(fmax(lo, -lim), lim);
+      rng[(2 * k + 1) * ld + g] = (int32_t)fmin(fmax(hi, -lim), lim);
+    }
+  }
+}
+
+// k_bin with the windows of k_bin_ranges: integer tests only (on a periodic axis the
+// images l = -2 .. 2 shift the range by l n).
+template <int D, bool FILL>
+__global__ void __launch_bounds__(NT) k_bin_r(GridDev gd, const ShotDev* __restrict__ shots, int nshots,
+                                              const int32_t* __restrict__ rng, int64_t ld,
+                                              int64_t* __restrict__ cnt, const int64_t* __restrict__ off,
+                                              int32_t* __restrict__ list, int64_t list_cap, int nsplit,
+                                              int64_t chunk, int* __restrict__ status) {
+  const int64_t t = blockIdx.x / nsplit;
+  const int64_t split = blockIdx.x - t * nsplit;
+  const int s = shot_of_tile(shots, nshots, t);
+  const ShotDev& sh = shots[s];
+  int64_t a[D], b[D];
+  tile_box<D>(gd, sh, t - sh.tile_off, a, b);
+  __shared__ int warp_tot[NT / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t gend = sh.g_off + sh.g_cnt;
+  const int64_t gb = sh.g_off + split * chunk;
+  const int64_t ge = gb < gend && gend - gb > chunk ? gb + chunk : gend;
+  int64_t base = FILL ? off[blockIdx.x] : 0;
+  int64_t total = 0;
+  for (int64_t g0 = gb; g0 < ge; g0 += NT) {
+    int64_t g = g0 + threadIdx.x;
+    bool f = false;
+    if (g < ge) {
+      f = true;
+#pragma unroll
+      for (int k = 0; k < D; ++k) {
+        const int64_t lo = rng[(2 * k) * ld + g], hi = rng[(2 * k + 1) * ld + g];
+        bool any = lo <= b[k] && hi >= a[k];
+        if (gd.periodic[k])
+          for (int l = -2; l <= 2; ++l) any = any || (lo + l * gd.n[k] <= b[k] && hi + l * gd.n[k] >= a[k]);
+        f = f && any;
+      }
+    }
+    unsigned bal = __ballot_sync(0xffffffffu, f);
+    if (lane == 0) warp_tot[warp] = __popc(bal);
+    __syncthreads();
+    int before = 0, all = 0;
+    for (int w = 0; w < NT / 32; ++w) {
+      if (w < warp) before += warp_tot[w];
+      all += warp_tot[w];
+    }
+    if (FILL && f) {
+      int64_t at = base + total + before + __popc(bal & ((1u << lane) - 1u));
+      if (at < list_cap)
+        list[at] = (int32_t)g;
+      else
+        atomicOr(status, kStatusCapacity);
+    }
+    total += all;
+    __syncthreads();
+  }
+  if (!FILL && threadIdx.x == 0) cnt[blockIdx.x] = total;
+}
+
 // Offsets of the tiles' lists from the scanned (tile, split) offsets (entry ntiles: the
 // total).
 __global__ void k_tile_offsets(const int64_t* __restrict__ split_off, int nsplit, int64_t ntiles,
@@ -423,10 +504,19 @@ cudaError_t launch_binning(fga_plan_s* p) {
   bin_splits(p, &nsplit, &chunk);
   const int64_t items = p->ntiles * nsplit;
   if ((size_t)items + 1 > p->bin_cap) return cudaErrorInvalidValue;  // capacity not set up
-  auto bin = p->grid.dim == 1 ? k_bin<1, false> : (p->grid.dim == 2 ? k_bin<2, false> : k_bin<3, false>);
-  bin<<<(unsigned)items, NT, 0, p->stream>>>(p->grid, p->d_shots, p->nshots, p->kappa, p->d_state,
-                                             (int64_t)p->g_cap, p->d_bin_off, nullptr, nullptr, 0,
-                                             nsplit, chunk, p->d_status);
+  if (p->rng_cap < (size_t)p->grid.dim * 2 * p->g_cap) return cudaErrorInvalidValue;  // not set up
+  const int64_t G = p->dev_counts ? (int64_t)p->g_cap : p->G;
+  const int64_t* gm = p->dev_counts ? p->d_gm : nullptr;
+  if (G > 0) {
+    const unsigned gbk = (unsigned)std::max<int64_t>(1, std::min<int64_t>((G + 255) / 256, 4096));
+    auto ranges = p->grid.dim == 1 ? k_bin_ranges<1> : (p->grid.dim == 2 ? k_bin_ranges<2> : k_bin_ranges<3>);
+    ranges<<<gbk, 256, 0, p->stream>>>(p->grid, p->d_shots, p->d_gshot, p->kappa, p->d_state,
+                                       (int64_t)p->g_cap, G, gm, p->d_rng);
+    p->launches += 1;
+  }
+  auto bin = p->grid.dim == 1 ? k_bin_r<1, false> : (p->grid.dim == 2 ? k_bin_r<2, false> : k_bin_r<3, false>);
+  bin<<<(unsigned)items, NT, 0, p->stream>>>(p->grid, p->d_shots, p->nshots, p->d_rng, (int64_t)p->g_cap,
+                                             p->d_bin_off, nullptr, nullptr, 0, nsplit, chunk, p->d_status);
   p->launches += 1;
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
@@ -445,11 +535,11 @@ cudaError_t launch_binning_fill(fga_plan_s* p) {
   bin_splits(p, &nsplit, &chunk);
   const int64_t items = p->ntiles * nsplit;
   if ((size_t)items + 1 > p->bin_cap) return cudaErrorInvalidValue;
-  auto fill = p->grid.dim == 1 ? k_bin<1, true> : (p->grid.dim == 2 ? k_bin<2, true> : k_bin<3, true>);
-  fill<<<(unsigned)items, NT, 0, p->stream>>>(p->grid, p->d_shots, p->nshots, p->kappa, p->d_state,
-                                              (int64_t)p->g_cap, nullptr, p->d_bin_off,
-                                              p->d_tile_list, (int64_t)p->list_cap, nsplit, chunk,
-                                              p->d_status);
+  if (p->rng_cap < (size_t)p->grid.dim * 2 * p->g_cap) return cudaErrorInvalidValue;
+  auto fill = p->grid.dim == 1 ? k_bin_r<1, true> : (p->grid.dim == 2 ? k_bin_r<2, true> : k_bin_r<3, true>);
+  fill<<<(unsigned)items, NT, 0, p->stream>>>(p->grid, p->d_shots, p->nshots, p->d_rng, (int64_t)p->g_cap,
+                                              nullptr, p->d_bin_off, p->d_tile_list, (int64_t)p->list_cap,
+                                              nsplit, chunk, p->d_status);
   p->launches += 1;
   return cudaGetLastError();
 }
