@@ -52,7 +52,7 @@ def _plan(**kw):
     (dict(dt=0.3), "T/dt"),
     (dict(dim=0, n=(), h=(), origin=(), periodic=(), velocity=np.ones(1)), "dim"),
     (dict(dim=3, n=(8, 8, 8), h=(1, 1, 1), origin=(0, 0, 0), periodic=(0, 0, 0),
-          velocity=np.ones(512), box=[[66, 8, 8]]), "3D"),
+          velocity=np.ones(512), box=[[8, 8, 7]]), "box"),
     (dict(dim=3, n=(8, 8, 8), h=(1, 1, 1), origin=(0, 0, 0), periodic=(0, 0, 0),
           velocity=np.ones(512), precision=F.FGA_MIXED_TF32X3), "2D"),
     (dict(eps=[-1.0]), "eps"),
