@@ -39,6 +39,8 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
+from paper_1304_3542_gb300.workloads import window_evals  # noqa: E402
+
 METRIC = "FGA Gaussian·gridpoint evals/s and rel-L2 err; mixed-prec vs FP64, 1 GB300"
 UNIT = "evals/s"
 L2_FLUSH_BYTES = 256 << 20
@@ -67,22 +69,6 @@ def workload_name(prob):
     return ("layered model %dx%d at %.1f m, 1 shot %g Hz Ricker ring at (%.2f, %.2f) km, "
             "T=%g s, dt=%g s" % (prob.n[0], prob.n[1], prob.h[0] * 1000, sh.freq, sh.source[0],
                                   sh.source[1], prob.T, prob.dt))
-
-
-def window_evals(prob, Q, eps):
-    """Grid points inside the kappa sqrt(eps) square window of each centre, summed."""
-    cut = prob.kappa * math.sqrt(eps)
-    tot = np.ones(Q.shape[0])
-    for k in range(prob.dim):
-        lo = np.ceil((Q[:, k] - cut - prob.origin[k]) / prob.h[k])
-        hi = np.floor((Q[:, k] + cut - prob.origin[k]) / prob.h[k])
-        lo = np.clip(lo, 0, prob.n[k] - 1)
-        hi = np.clip(hi, 0, prob.n[k] - 1)
-        cnt = np.where((Q[:, k] + cut >= prob.origin[k]) &
-                       (Q[:, k] - cut <= prob.origin[k] + (prob.n[k] - 1) * prob.h[k]),
-                       hi - lo + 1, 0)
-        tot *= np.maximum(cnt, 0)
-    return float(tot.sum())
 
 
 def source_hash(files):

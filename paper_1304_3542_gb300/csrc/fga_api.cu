@@ -436,13 +436,9 @@ fga_status fga_plan(const fga_config* cfg, const double* velocity, void* stream,
                               cudaMemcpyHostToDevice, p->stream));
     PLAN_CUDA(cudaStreamSynchronize(p->stream));
   }
-  if (d == 3) {
-    p->grid.tab = p->d_coef;  // 3D: the ray kernels read the samples (64-tap form)
-  } else {
-    PLAN_CUDA(cudaMalloc(&p->d_medtab, sizeof(double) * fga::medium_table_doubles(p->grid)));
-    p->grid.tab = p->d_medtab;
-    PLAN_CUDA(fga::launch_medium_table(p));
-  }
+  PLAN_CUDA(cudaMalloc(&p->d_medtab, sizeof(double) * fga::medium_table_doubles(p->grid)));
+  p->grid.tab = p->d_medtab;
+  PLAN_CUDA(fga::launch_medium_table(p));
   PLAN_CUDA(cudaMemsetAsync(p->d_status, 0, sizeof(int), p->stream));
   p->E.assign((size_t)cfg->nshots * d, nullptr);
   for (int s = 0; s < cfg->nshots; ++s) {

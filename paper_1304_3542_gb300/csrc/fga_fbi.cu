@@ -91,13 +91,6 @@ __device__ __forceinline__ double psi_plus(const ShotDev& sh, int64_t jp, double
     int64_t m = jp - sh.nb[0] / 2;
     valid = (jp != 0) && (m != 0);
     pn = fabs((double)m) * sh.pscale[0];
-  } else if constexpr (D == 3) {
-    const int64_t nb12 = (int64_t)sh.nb[1] * sh.nb[2];
-    const int64_t j0 = jp / nb12, j1 = (jp - j0 * nb12) / sh.nb[2], j2 = jp - j0 * nb12 - j1 * sh.nb[2];
-    const int64_t m0 = j0 - sh.nb[0] / 2, m1 = j1 - sh.nb[1] / 2, m2 = j2 - sh.nb[2] / 2;
-    valid = j0 != 0 && j1 != 0 && j2 != 0 && !(m0 == 0 && m1 == 0 && m2 == 0);
-    const double a = (double)m0 * sh.pscale[0], b = (double)m1 * sh.pscale[1], c = (double)m2 * sh.pscale[2];
-    pn = sqrt(a * a + b * b + c * c);
   } else {
     int64_t j0 = jp / sh.nb[1], j1 = jp - j0 * sh.nb[1];
     int64_t m0 = j0 - sh.nb[0] / 2, m1 = j1 - sh.nb[1] / 2;
@@ -494,47 +487,84 @@ __global__ void k_fbi3_stage2(const ShotDev* __restrict__ shots, const double2* 
   }
 }
 
-__global__ void k_fbi3_stage3(GridDev gd, const ShotDev* __restrict__ shots,
-                              const double* __restrict__ C, const double2* __restrict__ g2,
-                              double2* __restrict__ psi, double2* __restrict__ psi_f1,
-                              unsigned long long* __restrict__ max2) {
+// Stage 3 and the branch split: one block per (active q, shot), its threads over the p
+// indices of the box. c(q) is evaluated once per block; a thread steps its p index
+// (j0, j1, j2) by the block size with carries instead of dividing.
+__global__ void __launch_bounds__(256) k_fbi3_stage3(GridDev gd, const ShotDev* __restrict__ shots,
+                                                     const double* __restrict__ C,
+                                                     const double2* __restrict__ g2,
+                                                     double2* __restrict__ psi,
+                                                     double2* __restrict__ psi_f1,
+                                                     unsigned long long* __restrict__ max2) {
   const int s = blockIdx.y;
   const ShotDev& sh = shots[s];
-  const int64_t nbx = sh.nb[0], nby = sh.nb[1], nbz = sh.nb[2];
-  const int64_t plane2 = sh.nrows * sh.qn[1] * sh.qn[2] * nby * nbz;
-  const int64_t qtot = sh.qn[0] * sh.qn[1] * sh.qn[2];
-  const int64_t total = qtot * sh.np;
-  const double2* Ex = sh.E[0];
+  const int64_t qn12 = sh.qn[1] * sh.qn[2];
+  const int64_t ql = blockIdx.x;
+  if (ql >= sh.qn[0] * qn12) return;  // the whole block
+  const int nbx = sh.nb[0], nby = sh.nb[1], nbz = sh.nb[2], nbyz = nby * nbz;
+  const int64_t mx = ql / qn12, myz = ql - mx * qn12;
+  __shared__ double epc_s;  // eps / c(q)
+  if (threadIdx.x == 0) {
+    const int64_t my = myz / sh.qn[2], mz = myz - my * sh.qn[2];
+    const double q[3] = {gd.o[0] + (double)(sh.s[0] * (sh.qlo[0] + mx)) * gd.h[0],
+                         gd.o[1] + (double)(sh.s[1] * (sh.qlo[1] + my)) * gd.h[1],
+                         gd.o[2] + (double)(sh.s[2] * (sh.qlo[2] + mz)) * gd.h[2]};
+    epc_s = sh.eps / medium_value<3>(gd, C, q);
+  }
+  __syncthreads();
+  const double epc = epc_s;
   const double hv = gd.h[0] * gd.h[1] * gd.h[2];
+  const int64_t plane2 = sh.nrows * qn12 * nbyz;
+  const int64_t xstride = qn12 * nbyz;  // G2 entries between consecutive data rows x
+  const double2* G0 = g2 + sh.g2_off + ((int64_t)sh.s[0] * mx * qn12 + myz) * nbyz;
+  const double2* G1 = G0 + plane2;
+  double2* out0 = psi + sh.psi_off + ql * sh.np;
+  double2* out1 = psi_f1 + sh.psi_off + ql * sh.np;
+  const int step = blockDim.x;
+  int j0 = threadIdx.x / nbyz, j1 = (threadIdx.x - j0 * nbyz) / nbz;
+  int j2 = threadIdx.x - j0 * nbyz - j1 * nbz;
+  const int d0 = step / nbyz, d1 = (step - d0 * nbyz) / nbz, d2 = step - d0 * nbyz - d1 * nbz;
   double mymax = 0.0;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t ql = e / sh.np, jp = e - ql * sh.np;
-    const int64_t qn12 = sh.qn[1] * sh.qn[2];
-    const int64_t mx = ql / qn12, myz = ql - mx * qn12;  // myz = q_y * qn_z + q_z
-    const int64_t px = jp / (nby * nbz), pyz = jp - px * nby * nbz;
+  for (int64_t jp = threadIdx.x; jp < sh.np; jp += step) {
+    const int pyz = j1 * nbz + j2;
+    const double2* b0p = G0 + pyz;
+    const double2* b1p = G1 + pyz;
+    const double2* Ep = sh.E[0] + (int64_t)j0 * nbx;
     double2 a0 = make_double2(0.0, 0.0), a1 = a0;
-    for (int64_t jx = 0; jx < nbx; ++jx) {
-      const int64_t xr = (int64_t)sh.s[0] * mx + jx;
-      const int64_t off = (xr * qn12 + myz) * nby * nbz + pyz;
-      const double2 b0 = g2[sh.g2_off + off], b1 = g2[sh.g2_off + plane2 + off];
-      const double2 E = __ldg(Ex + px * nbx + jx);
+    for (int jx = 0; jx < nbx; ++jx, b0p += xstride, b1p += xstride) {
+      const double2 b0 = *b0p, b1 = *b1p;
+      const double2 E = __ldg(Ep + jx);
       a0.x = fma(E.x, b0.x, fma(-E.y, b0.y, a0.x));
       a0.y = fma(E.x, b0.y, fma(E.y, b0.x, a0.y));
       a1.x = fma(E.x, b1.x, fma(-E.y, b1.y, a1.x));
       a1.y = fma(E.x, b1.y, fma(E.y, b1.x, a1.y));
     }
-    const int64_t my = myz / sh.qn[2], mz = myz - my * sh.qn[2];
-    const double q[3] = {gd.o[0] + (double)(sh.s[0] * (sh.qlo[0] + mx)) * gd.h[0],
-                         gd.o[1] + (double)(sh.s[1] * (sh.qlo[1] + my)) * gd.h[1],
-                         gd.o[2] + (double)(sh.s[2] * (sh.qlo[2] + mz)) * gd.h[2]};
-    const double cq = medium_value<3>(gd, C, q);
-    double2 o, tt;
-    const double a2 = psi_plus<3>(sh, jp, make_double2(hv * a0.x, hv * a0.y),
-                                  make_double2(hv * a1.x, hv * a1.y), cq, o, tt);
-    psi[sh.psi_off + e] = o;
-    psi_f1[sh.psi_off + e] = tt;
-    mymax = fmax(mymax, a2);
+    // Eq. psi: psi+ = psi_0/2 + t, t = i eps psi_1/(2 c(q)|p|); the Nyquist index of any
+    // axis and p = 0 are left out
+    const int m0 = j0 - nbx / 2, m1 = j1 - nby / 2, m2 = j2 - nbz / 2;
+    double2 o = make_double2(0.0, 0.0), tt = o;
+    if (j0 != 0 && j1 != 0 && j2 != 0 && !(m0 == 0 && m1 == 0 && m2 == 0)) {
+      const double a = (double)m0 * sh.pscale[0], b = (double)m1 * sh.pscale[1],
+                   c = (double)m2 * sh.pscale[2];
+      const double r = epc * rsqrt_nr(fma(a, a, fma(b, b, c * c)));
+      const double2 p0 = make_double2(hv * a0.x, hv * a0.y), p1 = make_double2(hv * a1.x, hv * a1.y);
+      tt = make_double2(-0.5 * r * p1.y, 0.5 * r * p1.x);
+      o = make_double2(0.5 * p0.x + tt.x, 0.5 * p0.y + tt.y);
+      mymax = fmax(mymax, abs2_rn(o));
+    }
+    out0[jp] = o;
+    out1[jp] = tt;
+    j2 += d2;
+    j1 += d1;
+    j0 += d0;
+    if (j2 >= nbz) {
+      j2 -= nbz;
+      ++j1;
+    }
+    if (j1 >= nby) {
+      j1 -= nby;
+      ++j0;
+    }
   }
   for (int off = 16; off > 0; off >>= 1) mymax = fmax(mymax, __shfl_xor_sync(0xffffffffu, mymax, off));
   if ((threadIdx.x & 31) == 0) atomic_max_nonneg(max2 + s, mymax);
@@ -931,9 +961,12 @@ cudaError_t launch_fbi(fga_plan_s* p, const double* u0, const double* u1) {
     const unsigned blocks = 1024;
     k_fbi3_stage1<<<dim3(blocks, p->nshots), 256, 0, p->stream>>>(p->grid, p->d_shots, u0, u1, p->d_g1);
     k_fbi3_stage2<<<dim3(blocks, p->nshots), 256, 0, p->stream>>>(p->d_shots, p->d_g1, p->d_g2);
-    k_fbi3_stage3<<<dim3(blocks, p->nshots), 256, 0, p->stream>>>(p->grid, p->d_shots, p->d_coef,
-                                                                 p->d_g2, p->d_psi, p->d_psi_f1,
-                                                                 p->d_max2);
+    int64_t qmax = 0;
+    for (const auto& sh : p->shots) qmax = std::max<int64_t>(qmax, sh.qn[0] * sh.qn[1] * sh.qn[2]);
+    if (qmax >= ((int64_t)1 << 31)) return cudaErrorInvalidConfiguration;
+    k_fbi3_stage3<<<dim3((unsigned)qmax, p->nshots), 256, 0, p->stream>>>(p->grid, p->d_shots, p->d_coef,
+                                                                          p->d_g2, p->d_psi, p->d_psi_f1,
+                                                                          p->d_max2);
     p->launches += 3;
     return cudaGetLastError();
   }

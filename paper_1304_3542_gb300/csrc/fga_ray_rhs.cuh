@@ -30,30 +30,6 @@ __device__ __forceinline__ int64_t work_order(unsigned long long w, int64_t G, u
   return (int64_t)((w * mult) % (unsigned long long)G);
 }
 
-// 1/x for x > 0: the hardware's approximate reciprocal (PTX rcp.approx.ftz.f64, about
-// 20 correct bits) refined by two Newton-Raphson steps r <- r + r (1 - x r), each
-// doubling the correct bits (within an ulp of 1/x; measured on GB300 over x in
-// [2^-40, 2^40]).
-__device__ __forceinline__ double rcp_nr(double x) {
-  double r;
-  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(x));
-  double e = fma(-x, r, 1.0);
-  r = fma(r, e, r);
-  e = fma(-x, r, 1.0);
-  return fma(r, e, r);
-}
-
-// 1/sqrt(x) for x > 0: the hardware's approximation (PTX rsqrt.approx.ftz.f64, about
-// 20 correct bits) refined by one third-order Householder step for x^{-1/2}: with
-// e = 1 - x y^2, y <- y (1 + e/2 + 3 e^2/8), which cubes the relative error (about one
-// ulp remains; measured on GB300 over x in [2^-40, 2^40]).
-__device__ __forceinline__ double rsqrt_nr(double x) {
-  double y;
-  asm("rsqrt.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
-  const double e = fma(-x * y, y, 1.0);
-  return fma(y * e, fma(0.375, e, 0.5), y);
-}
-
 // The right-hand side in 2D with the algebra arranged for fused multiply-adds (the same
 // equations as the generic form below; only the rounding differs):
 //   dQ/dt = (c/|P|) P,  dP/dt = -|P| g,
@@ -132,126 +108,133 @@ __device__ __forceinline__ bool rhs2(const GridDev& gd, const double* y, double*
   return pn2 > 0.0 && dd > 0.0;
 }
 
-// The medium comes from the per-cell polynomial table gd.tab.
-template <int D>
-__device__ __forceinline__ bool rhs(const GridDev& gd, const double* y, double* k) {
-  if constexpr (D == 2) return rhs2(gd, y, k);
-  using Lo = Layout<D>;
+// The right-hand side in 3D, arranged like rhs2 (the same equations; only the rounding
+// differs from a literal transcription):
+//   dA_jk/dt = ((A g)_j - (c/|P|)(B n)_j) n_k + (c/|P|) B_jk,
+//   dB_jk/dt = (A Km)_jk - (B n)_j g_k,  Km = -|P| K,
+//   da/dt = a (n.g + tr(adj(Z) dZ/dt) conj(det Z)/(2 |det Z|^2)),
+// with adj(Z) from the cofactors of the 3 x 3 complex Z = A + iB.
+__device__ __forceinline__ bool rhs3(const GridDev& gd, const double* y, double* k) {
+  using Lo = Layout<3>;
   Med m;
-  medium_eval_tab<D>(gd, y + Lo::Q, m);
-  double pn2 = 0;
+  medium_eval_tab<3>(gd, y + Lo::Q, m);
+  const double p0 = y[Lo::P], p1 = y[Lo::P + 1], p2 = y[Lo::P + 2];
+  const double pn2 = fma(p0, p0, fma(p1, p1, p2 * p2));
+  const double rinv = rsqrt_nr(pn2);
+  const double pn = pn2 * rinv;
+  const double n[3] = {p0 * rinv, p1 * rinv, p2 * rinv};
+  const double cop = m.c * rinv;  // c/|P|
+  k[Lo::Q] = cop * p0;
+  k[Lo::Q + 1] = cop * p1;
+  k[Lo::Q + 2] = cop * p2;
 #pragma unroll
-  for (int i = 0; i < D; ++i) pn2 = fma(y[Lo::P + i], y[Lo::P + i], pn2);
-  double rinv = rsqrt(pn2);
-  double pn = pn2 * rinv;
-  double n[D];
+  for (int i = 0; i < 3; ++i) k[Lo::P + i] = -pn * m.g[i];
+  const double ng = fma(n[0], m.g[0], fma(n[1], m.g[1], n[2] * m.g[2]));
+  double km[3][3];
 #pragma unroll
-  for (int i = 0; i < D; ++i) n[i] = y[Lo::P + i] * rinv;
-  double cop = m.c * rinv;  // c/|P|
-  double ng = 0;
+  for (int l = 0; l < 3; ++l)
 #pragma unroll
-  for (int i = 0; i < D; ++i) {
-    k[Lo::Q + i] = m.c * n[i];
-    k[Lo::P + i] = -pn * m.g[i];
-    ng = fma(n[i], m.g[i], ng);
-  }
-  // dynamic rays
-#pragma unroll
-  for (int j = 0; j < D; ++j) {
-    double agr = 0, agi = 0, bnr = 0, bni = 0;
-#pragma unroll
-    for (int l = 0; l < D; ++l) {
-      agr = fma(y[Lo::AR + j * D + l], m.g[l], agr);
-      agi = fma(y[Lo::AI + j * D + l], m.g[l], agi);
-      bnr = fma(y[Lo::BR + j * D + l], n[l], bnr);
-      bni = fma(y[Lo::BI + j * D + l], n[l], bni);
+    for (int kk = l; kk < 3; ++kk) {
+      km[l][kk] = -pn * m.K[l][kk];
+      km[kk][l] = km[l][kk];
     }
 #pragma unroll
-    for (int kk = 0; kk < D; ++kk) {
-      double akr = 0, aki = 0;
+  for (int j = 0; j < 3; ++j) {
+    const double* ar = y + Lo::AR + 3 * j;
+    const double* ai = y + Lo::AI + 3 * j;
+    const double* br = y + Lo::BR + 3 * j;
+    const double* bi = y + Lo::BI + 3 * j;
+    const double bnr = fma(br[0], n[0], fma(br[1], n[1], br[2] * n[2]));
+    const double bni = fma(bi[0], n[0], fma(bi[1], n[1], bi[2] * n[2]));
+    const double ur = fma(-cop, bnr, fma(ar[0], m.g[0], fma(ar[1], m.g[1], ar[2] * m.g[2])));
+    const double ui = fma(-cop, bni, fma(ai[0], m.g[0], fma(ai[1], m.g[1], ai[2] * m.g[2])));
 #pragma unroll
-      for (int l = 0; l < D; ++l) {
-        akr = fma(y[Lo::AR + j * D + l], m.K[l][kk], akr);
-        aki = fma(y[Lo::AI + j * D + l], m.K[l][kk], aki);
-      }
-      k[Lo::AR + j * D + kk] = fma(agr, n[kk], cop * fma(-bnr, n[kk], y[Lo::BR + j * D + kk]));
-      k[Lo::AI + j * D + kk] = fma(agi, n[kk], cop * fma(-bni, n[kk], y[Lo::BI + j * D + kk]));
-      k[Lo::BR + j * D + kk] = -fma(pn, akr, bnr * m.g[kk]);
-      k[Lo::BI + j * D + kk] = -fma(pn, aki, bni * m.g[kk]);
+    for (int kk = 0; kk < 3; ++kk) {
+      k[Lo::AR + 3 * j + kk] = fma(ur, n[kk], cop * br[kk]);
+      k[Lo::AI + 3 * j + kk] = fma(ui, n[kk], cop * bi[kk]);
+      k[Lo::BR + 3 * j + kk] = fma(ar[0], km[0][kk], fma(ar[1], km[1][kk], fma(ar[2], km[2][kk], -bnr * m.g[kk])));
+      k[Lo::BI + 3 * j + kk] = fma(ai[0], km[0][kk], fma(ai[1], km[1][kk], fma(ai[2], km[2][kk], -bni * m.g[kk])));
     }
   }
-  // tr(Z^{-1} dZ/dt), Z = A + iB, dZ/dt = dA + i dB
-  double trr, tri, detr, deti;
-  if constexpr (D == 1) {
-    double zr = y[Lo::AR] - y[Lo::BI], zi = y[Lo::AI] + y[Lo::BR];
-    double dzr = k[Lo::AR] - k[Lo::BI], dzi = k[Lo::AI] + k[Lo::BR];
-    trr = dzr;
-    tri = dzi;
-    detr = zr;
-    deti = zi;
-  } else if constexpr (D == 3) {
-    // Z = A + iB and dZ/dt (3 x 3 complex); tr(adj(Z) dZ) and det Z by cofactors
-    double zr[9], zi[9], dzr[9], dzi[9];
+  // Z = A + iB and dZ/dt; cofactor C[i][j] = (-1)^{i+j} det(minor ij) (the cyclic minors
+  // carry the sign), adj(Z)[j][i] = C[i][j]; tr(adj(Z) dZ) = sum C[i][j] dZ[i][j] and
+  // det Z = sum_j Z[0][j] C[0][j]
+  double zr[9], zi[9], dzr[9], dzi[9];
 #pragma unroll
-    for (int e = 0; e < 9; ++e) {
-      zr[e] = y[Lo::AR + e] - y[Lo::BI + e];
-      zi[e] = y[Lo::AI + e] + y[Lo::BR + e];
-      dzr[e] = k[Lo::AR + e] - k[Lo::BI + e];
-      dzi[e] = k[Lo::AI + e] + k[Lo::BR + e];
-    }
-    // cofactor C[i][j] = (-1)^{i+j} det(minor ij); adj(Z)[j][i] = C[i][j]
-    double cr[9], ci[9];
+  for (int e = 0; e < 9; ++e) {
+    zr[e] = y[Lo::AR + e] - y[Lo::BI + e];
+    zi[e] = y[Lo::AI + e] + y[Lo::BR + e];
+    dzr[e] = k[Lo::AR + e] - k[Lo::BI + e];
+    dzi[e] = k[Lo::AI + e] + k[Lo::BR + e];
+  }
+  double trr = 0.0, tri = 0.0, detr = 0.0, deti = 0.0;
 #pragma unroll
-    for (int i = 0; i < 3; ++i)
-#pragma unroll
-      for (int j = 0; j < 3; ++j) {
-        const int r0 = (i + 1) % 3, r1 = (i + 2) % 3, c0 = (j + 1) % 3, c1 = (j + 2) % 3;
-        // cyclic minors carry the sign (-1)^{i+j} already
-        const double ar = zr[r0 * 3 + c0], ai = zi[r0 * 3 + c0], br = zr[r1 * 3 + c1], bi = zi[r1 * 3 + c1];
-        const double er = zr[r0 * 3 + c1], ei = zi[r0 * 3 + c1], fr = zr[r1 * 3 + c0], fi = zi[r1 * 3 + c0];
-        cr[i * 3 + j] = (ar * br - ai * bi) - (er * fr - ei * fi);
-        ci[i * 3 + j] = (ar * bi + ai * br) - (er * fi + ei * fr);
-      }
-    // tr(adj(Z) dZ) = sum_{i,j} C[i][j] dZ[i][j];  det Z = sum_j Z[0][j] C[0][j]
-    trr = 0.0;
-    tri = 0.0;
-#pragma unroll
-    for (int e = 0; e < 9; ++e) {
-      trr += cr[e] * dzr[e] - ci[e] * dzi[e];
-      tri += cr[e] * dzi[e] + ci[e] * dzr[e];
-    }
-    detr = 0.0;
-    deti = 0.0;
+  for (int i = 0; i < 3; ++i)
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
-      detr += zr[j] * cr[j] - zi[j] * ci[j];
-      deti += zr[j] * ci[j] + zi[j] * cr[j];
+      const int r0 = (i + 1) % 3, r1 = (i + 2) % 3, c0 = (j + 1) % 3, c1 = (j + 2) % 3;
+      const double ar = zr[r0 * 3 + c0], ai = zi[r0 * 3 + c0], br = zr[r1 * 3 + c1], bi = zi[r1 * 3 + c1];
+      const double er = zr[r0 * 3 + c1], ei = zi[r0 * 3 + c1], fr = zr[r1 * 3 + c0], fi = zi[r1 * 3 + c0];
+      const double cr = fma(ar, br, fma(-ai, bi, fma(-er, fr, ei * fi)));
+      const double ci = fma(ar, bi, fma(ai, br, fma(-er, fi, -ei * fr)));
+      const int e = i * 3 + j;
+      trr = fma(cr, dzr[e], fma(-ci, dzi[e], trr));
+      tri = fma(cr, dzi[e], fma(ci, dzr[e], tri));
+      if (i == 0) {
+        detr = fma(zr[j], cr, fma(-zi[j], ci, detr));
+        deti = fma(zr[j], ci, fma(zi[j], cr, deti));
+      }
     }
-  } else {
-    double zr[4], zi[4], dzr[4], dzi[4];
-#pragma unroll
-    for (int e = 0; e < 4; ++e) {
-      zr[e] = y[Lo::AR + e] - y[Lo::BI + e];
-      zi[e] = y[Lo::AI + e] + y[Lo::BR + e];
-      dzr[e] = k[Lo::AR + e] - k[Lo::BI + e];
-      dzi[e] = k[Lo::AI + e] + k[Lo::BR + e];
-    }
-    // adj(Z) : dZ = Z11 dZ00 - Z01 dZ10 - Z10 dZ01 + Z00 dZ11
-    trr = zr[3] * dzr[0] - zi[3] * dzi[0] - (zr[1] * dzr[2] - zi[1] * dzi[2]) -
-          (zr[2] * dzr[1] - zi[2] * dzi[1]) + zr[0] * dzr[3] - zi[0] * dzi[3];
-    tri = zr[3] * dzi[0] + zi[3] * dzr[0] - (zr[1] * dzi[2] + zi[1] * dzr[2]) -
-          (zr[2] * dzi[1] + zi[2] * dzr[1]) + zr[0] * dzi[3] + zi[0] * dzr[3];
-    detr = zr[0] * zr[3] - zi[0] * zi[3] - (zr[1] * zr[2] - zi[1] * zi[2]);
-    deti = zr[0] * zi[3] + zi[0] * zr[3] - (zr[1] * zi[2] + zi[1] * zr[2]);
-  }
-  double dd = fma(detr, detr, deti * deti);
-  double idd = 1.0 / dd;
-  double qr = (trr * detr + tri * deti) * idd, qi = (tri * detr - trr * deti) * idd;
-  double fr = ng + 0.5 * qr, fi = 0.5 * qi;
-  double ar = y[Lo::aR], ai = y[Lo::aI];
-  k[Lo::aR] = ar * fr - ai * fi;
-  k[Lo::aI] = ar * fi + ai * fr;
+  const double dd = fma(detr, detr, deti * deti);
+  const double ih = 0.5 * rcp_nr(dd);  // 1/(2 |det Z|^2)
+  const double qr = fma(trr, detr, tri * deti) * ih, qi = fma(tri, detr, -trr * deti) * ih;
+  const double fr = ng + qr;
+  const double ar = y[Lo::aR], ai = y[Lo::aI];
+  k[Lo::aR] = fma(ar, fr, -ai * qi);
+  k[Lo::aI] = fma(ar, qi, ai * fr);
   return pn2 > 0.0 && dd > 0.0;
+}
+
+// The right-hand side in 1D (Z = A + iB is a scalar: tr(Z^{-1} dZ/dt) = dZ/Z), and the
+// dispatch to the 2D and 3D forms. The medium comes from the per-cell polynomial table
+// gd.tab.
+template <int D>
+__device__ __forceinline__ bool rhs(const GridDev& gd, const double* y, double* k) {
+  if constexpr (D == 2) {
+    return rhs2(gd, y, k);
+  } else if constexpr (D == 3) {
+    return rhs3(gd, y, k);
+  } else {
+    using Lo = Layout<1>;
+    Med m;
+    medium_eval_tab<1>(gd, y + Lo::Q, m);
+    const double p = y[Lo::P];
+    const double pn2 = p * p;
+    const double rinv = rsqrt_nr(pn2);
+    const double pn = pn2 * rinv, n = p * rinv;
+    const double cop = m.c * rinv;  // c/|P|
+    const double g = m.g[0], K = m.K[0][0];
+    k[Lo::Q] = m.c * n;
+    k[Lo::P] = -pn * g;
+    const double ng = n * g;
+    // dA/dt = (A g) n + (c/|P|)(B - (B n) n) (the second term vanishes for n = +-1, kept
+    // as written), dB/dt = -(|P| A K + (B n) g)
+    const double bnr = y[Lo::BR] * n, bni = y[Lo::BI] * n;
+    k[Lo::AR] = fma(y[Lo::AR] * g, n, cop * fma(-bnr, n, y[Lo::BR]));
+    k[Lo::AI] = fma(y[Lo::AI] * g, n, cop * fma(-bni, n, y[Lo::BI]));
+    k[Lo::BR] = -fma(pn, y[Lo::AR] * K, bnr * g);
+    k[Lo::BI] = -fma(pn, y[Lo::AI] * K, bni * g);
+    const double zr = y[Lo::AR] - y[Lo::BI], zi = y[Lo::AI] + y[Lo::BR];
+    const double dzr = k[Lo::AR] - k[Lo::BI], dzi = k[Lo::AI] + k[Lo::BR];
+    const double dd = fma(zr, zr, zi * zi);
+    const double ih = 0.5 * rcp_nr(dd);
+    const double qr = fma(dzr, zr, dzi * zi) * ih, qi = fma(dzi, zr, -dzr * zi) * ih;
+    const double fr = ng + qr;
+    const double ar = y[Lo::aR], ai = y[Lo::aI];
+    k[Lo::aR] = fma(ar, fr, -ai * qi);
+    k[Lo::aI] = fma(ar, qi, ai * fr);
+    return pn2 > 0.0 && dd > 0.0;
+  }
 }
 
 // Initial state of Gaussian (q index qf, p index pj): Q = q, P = p, A = I, B = -iI,

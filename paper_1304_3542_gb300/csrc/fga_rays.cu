@@ -72,7 +72,13 @@ __global__ void __launch_bounds__(128, MINB) k_rays(GridDev gd, const ShotDev* _
   bool ok = true;
   if (g < G) {
     int s = gshot[g];
-    double y[NF];
+    // In 3D the step's starting state (45 values) lives in shared memory, a thread's
+    // values NF (odd) doubles apart, which keeps a warp's accesses free of bank conflicts:
+    // with the stage state, the accumulator and the right-hand side in registers it would
+    // not fit in 255 registers.
+    __shared__ double y_sm[D == 3 ? 128 * NF : 1];
+    double y_reg[D == 3 ? 1 : NF];
+    double* const y = D == 3 ? y_sm + threadIdx.x * NF : y_reg;
     ray_init<D>(gd, shots[s], gq[g], gp[g], y);
     // exit box: beyond these bounds on an open axis the window misses the grid and the
     // spline's taps are all clamped, so c does not depend on Q_k there
@@ -130,27 +136,56 @@ __global__ void __launch_bounds__(128, MINB) k_rays(GridDev gd, const ShotDev* _
       constexpr int NI = Lo::NI;
       double acc[NF], tmp[NF], k[NF];
       tmp[Lo::S] = y[Lo::S];
-      ok &= rhs<D>(gd, y, k);
+      if constexpr (D == 3) {
+        // the four stages as a loop around one copy of the (long) 3D right-hand side, so
+        // that the kernel's code fits the instruction cache; the same operations in the
+        // same order as the unrolled form
 #pragma unroll
-      for (int i = 0; i < NI; ++i) {
-        acc[i] = fma(h6, k[i], y[i]);
-        tmp[i] = fma(h2, k[i], y[i]);
+        for (int i = 0; i < NI; ++i) tmp[i] = y[i];
+#pragma unroll 1
+        for (int st = 0; st < 4; ++st) {
+          ok &= rhs<D>(gd, tmp, k);
+          if (st == 0) {
+#pragma unroll
+            for (int i = 0; i < NI; ++i) {
+              acc[i] = fma(h6, k[i], y[i]);
+              tmp[i] = fma(h2, k[i], y[i]);
+            }
+          } else if (st < 3) {
+            const double wt = st == 1 ? h2 : dt;
+#pragma unroll
+            for (int i = 0; i < NI; ++i) {
+              acc[i] = fma(h3, k[i], acc[i]);
+              tmp[i] = fma(wt, k[i], y[i]);
+            }
+          } else {
+#pragma unroll
+            for (int i = 0; i < NI; ++i) y[i] = fma(h6, k[i], acc[i]);
+          }
+        }
+      } else {
+        ok &= rhs<D>(gd, y, k);
+#pragma unroll
+        for (int i = 0; i < NI; ++i) {
+          acc[i] = fma(h6, k[i], y[i]);
+          tmp[i] = fma(h2, k[i], y[i]);
+        }
+        ok &= rhs<D>(gd, tmp, k);
+#pragma unroll
+        for (int i = 0; i < NI; ++i) {
+          acc[i] = fma(h3, k[i], acc[i]);
+          tmp[i] = fma(h2, k[i], y[i]);
+        }
+        ok &= rhs<D>(gd, tmp, k);
+#pragma unroll
+        for (int i = 0; i < NI; ++i) {
+          acc[i] = fma(h3, k[i], acc[i]);
+          tmp[i] = fma(dt, k[i], y[i]);
+        }
+        ok &= rhs<D>(gd, tmp, k);
+#pragma unroll
+        for (int i = 0; i < NI; ++i) y[i] = fma(h6, k[i], acc[i]);
       }
-      ok &= rhs<D>(gd, tmp, k);
-#pragma unroll
-      for (int i = 0; i < NI; ++i) {
-        acc[i] = fma(h3, k[i], acc[i]);
-        tmp[i] = fma(h2, k[i], y[i]);
-      }
-      ok &= rhs<D>(gd, tmp, k);
-#pragma unroll
-      for (int i = 0; i < NI; ++i) {
-        acc[i] = fma(h3, k[i], acc[i]);
-        tmp[i] = fma(dt, k[i], y[i]);
-      }
-      ok &= rhs<D>(gd, tmp, k);
-#pragma unroll
-      for (int i = 0; i < NI; ++i) y[i] = fma(h6, k[i], acc[i]);
 #pragma unroll
       for (int i = 0; i < D; ++i) {
         if (gd.periodic[i]) {
@@ -235,15 +270,27 @@ __global__ void k_ray_order(int64_t G, const int64_t* __restrict__ gm, unsigned 
 // One thread per table cell (cells -1 .. n per axis, stored at index + 1).
 template <int D>
 __global__ void k_medium_table(GridDev gd, const double* __restrict__ C, double* __restrict__ tab) {
+  constexpr int NC = D == 1 ? 4 : (D == 2 ? 16 : 64);
   const int64_t n1 = D == 1 ? 1 : gd.n[1] + 2;
-  const int64_t cells = (gd.n[0] + 2) * n1;
+  const int64_t n2 = D == 3 ? gd.n[2] + 2 : 1;
+  const int64_t cells = (gd.n[0] + 2) * n1 * n2;
   for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < cells;
        c += (int64_t)gridDim.x * blockDim.x) {
-    int64_t ci[2] = {D == 1 ? c : c / n1, D == 1 ? 0 : c % n1};
-    double a[D == 1 ? 4 : 16];
+    int64_t ci[3];
+    if constexpr (D == 1) {
+      ci[0] = c;
+    } else if constexpr (D == 2) {
+      ci[0] = c / n1;
+      ci[1] = c % n1;
+    } else {
+      ci[0] = c / (n1 * n2);
+      ci[1] = (c / n2) % n1;
+      ci[2] = c % n2;
+    }
+    double a[NC];
     medium_cell<D>(gd, C, ci, a);
 #pragma unroll
-    for (int k = 0; k < (D == 1 ? 4 : 16); ++k) tab[c * (D == 1 ? 4 : 16) + k] = a[k];
+    for (int k = 0; k < NC; ++k) tab[c * NC + k] = a[k];
   }
 }
 
@@ -269,19 +316,21 @@ __global__ void k_gather_rows(const double* __restrict__ in, const int32_t* __re
 
 }  // namespace
 
-// 0 in 3D: the ray kernels evaluate the 64 taps of the samples there.
 size_t medium_table_doubles(const GridDev& gd) {
-  if (gd.dim == 3) return 0;
-  return gd.dim == 1 ? (size_t)(gd.n[0] + 2) * 4 : (size_t)(gd.n[0] + 2) * (gd.n[1] + 2) * 16;
+  size_t cells = 1;
+  for (int k = 0; k < gd.dim; ++k) cells *= (size_t)(gd.n[k] + 2);
+  return cells * ((size_t)1 << (2 * gd.dim));
 }
 
 cudaError_t launch_medium_table(fga_plan_s* p) {
-  const size_t cells = medium_table_doubles(p->grid) / (p->grid.dim == 1 ? 4 : 16);
+  const size_t cells = medium_table_doubles(p->grid) >> (2 * p->grid.dim);
   const unsigned blocks = (unsigned)std::min<size_t>((cells + 255) / 256, 4096);
   if (p->grid.dim == 1)
     k_medium_table<1><<<blocks, 256, 0, p->stream>>>(p->grid, p->d_coef, p->d_medtab);
-  else
+  else if (p->grid.dim == 2)
     k_medium_table<2><<<blocks, 256, 0, p->stream>>>(p->grid, p->d_coef, p->d_medtab);
+  else
+    k_medium_table<3><<<blocks, 256, 0, p->stream>>>(p->grid, p->d_coef, p->d_medtab);
   p->launches += 1;
   return cudaGetLastError();
 }

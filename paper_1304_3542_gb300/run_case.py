@@ -1,10 +1,11 @@
 """Run one workload through libfga and print the Gaussian count and stage times.
 
-  python -m paper_1304_3542_gb300.run_case [--workload layered_single] [--T 0.1]
+  python -m paper_1304_3542_gb300.run_case [--workload layered_single|lens_2d|lens_3d|...] [--T 0.1]
                                            [--tau 1e-3] [--repeat 1] [--nshots 4]
                                            [--precision fp64|mixed] [--receivers] [--grad]
                                            [--z-method dynamic|divided] [--dz-eta 0.1]
                                            [--interp approx|interp] [--keep-n N]
+                                           [--N 48 --eps 0.00694 --box 48 --stride 2 --k0 37.7]
 
 A small driver for trying the library on the seeded workloads (and the command
 the kernel profiles are taken with).
@@ -26,7 +27,7 @@ def main():
 
     ap = argparse.ArgumentParser()
     ap.add_argument("--workload", default="layered_single",
-                    choices=["layered_single", "layered_batch", "lens_2d", "periodic_1d"])
+                    choices=["layered_single", "layered_batch", "lens_2d", "lens_3d", "periodic_1d"])
     ap.add_argument("--T", type=float, default=None)
     ap.add_argument("--tau", type=float, default=None)
     ap.add_argument("--nshots", type=int, default=4)
@@ -40,8 +41,18 @@ def main():
     ap.add_argument("--dz-eta", type=float, default=0.1)
     ap.add_argument("--interp", choices=["approx", "interp"], default="approx")
     ap.add_argument("--keep-n", type=int, default=0)
+    ap.add_argument("--N", type=int, default=None, help="lens workloads: grid points per axis")
+    ap.add_argument("--eps", type=float, default=None, help="lens workloads: eps")
+    ap.add_argument("--box", type=int, default=None, help="lens workloads: FBI box edge n_b")
+    ap.add_argument("--stride", type=int, default=None, help="lens workloads: q-stride s")
+    ap.add_argument("--k0", type=float, default=None, help="lens workloads: packet wavenumber")
     args = ap.parse_args()
     kw = {}
+    for name, key in (("N", "N"), ("eps", "eps"), ("box", "box"), ("stride", "s"), ("k0", "k0")):
+        if getattr(args, name) is not None:
+            if not args.workload.startswith("lens"):
+                ap.error("--%s applies to the lens workloads only" % name)
+            kw[key] = getattr(args, name)
     if args.T is not None:
         kw["T"] = args.T
     if args.tau is not None:
@@ -76,7 +87,12 @@ def main():
         g = plan.grad(np.ascontiguousarray(tr))
         extra = {"grad_max": float(np.abs(g).max())}
     times, launches = plan.stage_times()
+    # (Gaussian, grid point) pairs inside the windows of the + branch (the reconstruction's
+    # algorithmic work: one complex multiply-add each)
+    pairs = sum(WL.window_evals(prob, plan.state(s)["Q"], prob.shots[s].eps)
+                for s in range(len(prob.shots)))
     print(json.dumps({"workload": args.workload, "counts": counts.tolist(),
+                      "ray_steps": plan.ray_steps(), "window_pairs": pairs,
                       "stage_ms": {k: float(v) for k, v in times.items()},
                       "launches": launches, "field_norm": float(out.norm()), **extra}))
     plan.close()

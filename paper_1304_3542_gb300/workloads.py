@@ -316,3 +316,19 @@ def by_name(name: str, **kw) -> Problem:
         "layered_batch": layered_batch,
     }
     return table[name](**kw)
+
+
+def window_evals(prob, Q, eps):
+    """Grid points inside the kappa sqrt(eps) square window of each centre, summed."""
+    cut = prob.kappa * math.sqrt(eps)
+    tot = np.ones(Q.shape[0])
+    for k in range(prob.dim):
+        lo = np.ceil((Q[:, k] - cut - prob.origin[k]) / prob.h[k])
+        hi = np.floor((Q[:, k] + cut - prob.origin[k]) / prob.h[k])
+        lo = np.clip(lo, 0, prob.n[k] - 1)
+        hi = np.clip(hi, 0, prob.n[k] - 1)
+        cnt = np.where((Q[:, k] + cut >= prob.origin[k]) &
+                       (Q[:, k] - cut <= prob.origin[k] + (prob.n[k] - 1) * prob.h[k]),
+                       hi - lo + 1, 0)
+        tot *= np.maximum(cnt, 0)
+    return float(tot.sum())
