@@ -202,18 +202,19 @@ __device__ __forceinline__ double2 axis_factor(const Axis& ax, int64_t i, double
   return make_double2(re, im);
 }
 
-// Factors of one Gaussian along an open axis at the 8 grid points i0 .. i0+7,
+// Factors of one Gaussian along an open axis at the N grid points i0 .. i0+N-1,
 // times cf: E_i = exp(-d_i^2/(2 eps)) exp(i P d_i/eps), d_i = x_i - Q, zero outside
 // |d_i| <= cut. Evaluated directly at the first point inside the window and then by
 // the exact recurrence E_{i+1} = E_i R_i rot, R_{i+1} = R_i rho with
 // R_i = exp(-(d_i h + h^2/2)/eps), rot = exp(i P h/eps), rho = exp(-h^2/eps)
-// (relative rounding growth below 1e-14 over 8 points).
-__device__ __forceinline__ void axis_factors8(double xi0, double h, double Q, double P, double cut,
-                                              double inv_eps, double2 cf, double2* dst) {
+// (relative rounding growth below 1e-14 over 8 points, 2e-14 over 16).
+template <int N>
+__device__ __forceinline__ void axis_factors(double xi0, double h, double Q, double P, double cut,
+                                             double inv_eps, double2 cf, double2* dst) {
   int r0 = 0;
-  while (r0 < 8 && fabs(fma((double)r0, h, xi0) - Q) > cut) ++r0;
+  while (r0 < N && fabs(fma((double)r0, h, xi0) - Q) > cut) ++r0;
   for (int r = 0; r < r0; ++r) dst[r] = make_double2(0.0, 0.0);
-  if (r0 == 8) return;
+  if (r0 == N) return;
   double d = fma((double)r0, h, xi0) - Q;
   double gs = exp(-0.5 * d * d * inv_eps);
   double sn, cs;
@@ -223,7 +224,7 @@ __device__ __forceinline__ void axis_factors8(double xi0, double h, double Q, do
   double rs, rc;
   sincos(P * h * inv_eps, &rs, &rc);
   const double rho = exp(-h * h * inv_eps);
-  for (int r = r0; r < 8; ++r) {
+  for (int r = r0; r < N; ++r) {
     double dr = fma((double)r, h, xi0) - Q;
     if (fabs(dr) <= cut)
       dst[r] = make_double2(cf.x * er - cf.y * ei, cf.x * ei + cf.y * er);
@@ -338,7 +339,7 @@ __global__ void __launch_bounds__(NT) k_gather2(GridDev gd, const ShotDev* __res
           }
         } else {
           double xi0 = ax.o + (double)(a_ax + part * 8) * ax.h;
-          axis_factors8(xi0, ax.h, Q, P, cut, inv_eps, cf, dst);
+          axis_factors<8>(xi0, ax.h, Q, P, cut, inv_eps, cf, dst);
         }
         if (part == 0) {
           if (ax.periodic) {
@@ -381,8 +382,9 @@ __global__ void __launch_bounds__(NT) k_gather2(GridDev gd, const ShotDev* __res
 // Ordered sum of the partial tiles of every tile into the output grid.
 // 3D gather of one work item: a 16^3 tile, thread = (x, y) column of 16 points along z;
 // per chunk of 16 Gaussians the per-axis factors (16 points each, the x factor carrying
-// the coefficient) are made in shared memory, then every thread adds
-// Re(X_g(x) Y_g(y) Z_g(z)) to its 16 points. Writes partial[w][16][16][16].
+// the coefficient) and each window's range in the tile are made in shared memory, then
+// every thread adds Re(X_g(x) Y_g(y) Z_g(z)) to its points inside the window (by
+// quarters of 4 along z). Writes partial[w][16][16][16].
 __global__ void __launch_bounds__(NT) k_gather3(GridDev gd, const ShotDev* __restrict__ shots,
                                                 int nshots, double kappa,
                                                 const double* __restrict__ state, int64_t ld,
@@ -400,6 +402,9 @@ __global__ void __launch_bounds__(NT) k_gather3(GridDev gd, const ShotDev* __res
   int64_t a[3], b[3];
   tile_box<3>(gd, sh, t - sh.tile_off, a, b);
   __shared__ double2 F[3][CH3][T3];  // [axis][gaussian][point]
+  // per Gaussian and axis: a range of tile points outside which its factor is zero
+  // (conservative, clipped to the tile; empty when lo > hi)
+  __shared__ int W[CH3][3][2];
   const int ix = threadIdx.x / T3, iy = threadIdx.x % T3;
   double acc[T3];
 #pragma unroll
@@ -417,28 +422,45 @@ __global__ void __launch_bounds__(NT) k_gather3(GridDev gd, const ShotDev* __res
         const double2 cf = axis == 0 ? coef[g] : make_double2(1.0, 0.0);
         const Axis ax = grid_axis(gd, axis);
         const int64_t a_ax = axis == 0 ? a[0] : (axis == 1 ? a[1] : a[2]);
+        int wl = 0, wh = T3 - 1;
         if (ax.periodic) {
           for (int r = 0; r < T3; ++r) {
             const double2 f = axis_factor(ax, a_ax + r, Q, P, cut, inv_eps);
             dst[r] = make_double2(cf.x * f.x - cf.y * f.y, cf.x * f.y + cf.y * f.x);
           }
         } else {
-          axis_factors8(ax.o + (double)a_ax * ax.h, ax.h, Q, P, cut, inv_eps, cf, dst);
-          axis_factors8(ax.o + (double)(a_ax + 8) * ax.h, ax.h, Q, P, cut, inv_eps, cf, dst + 8);
+          axis_factors<T3>(ax.o + (double)a_ax * ax.h, ax.h, Q, P, cut, inv_eps, cf, dst);
+          int64_t lo, hi;
+          window_range_ax(ax, Q, cut, lo, hi);
+          lo -= a_ax;
+          hi -= a_ax;
+          wl = (int)(lo < 0 ? 0 : (lo > T3 ? T3 : lo));
+          wh = (int)(hi > T3 - 1 ? T3 - 1 : (hi < -1 ? -1 : hi));
         }
+        W[gi][axis][0] = wl;
+        W[gi][axis][1] = wh;
       } else {
         for (int r = 0; r < T3; ++r) dst[r] = make_double2(0.0, 0.0);
+        W[gi][axis][0] = T3;
+        W[gi][axis][1] = -1;
       }
     }
     __syncthreads();
     for (int gi = 0; gi < nc; ++gi) {
+      // outside the window the factors are exact zeros and add nothing: skip the column,
+      // and the quarters of it (4 points) that miss the window along z
+      if (ix < W[gi][0][0] || ix > W[gi][0][1] || iy < W[gi][1][0] || iy > W[gi][1][1]) continue;
+      const int z0 = W[gi][2][0] >> 2, z1 = W[gi][2][1] >> 2;
       const double2 X = F[0][gi][ix], Y = F[1][gi][iy];
       const double xr = X.x * Y.x - X.y * Y.y, xi = X.x * Y.y + X.y * Y.x;
-      if (xr == 0.0 && xi == 0.0) continue;
 #pragma unroll
-      for (int i = 0; i < T3; ++i) {
-        const double2 Z = F[2][gi][i];
-        acc[i] = fma(xr, Z.x, fma(-xi, Z.y, acc[i]));
+      for (int qz = 0; qz < T3 / 4; ++qz) {
+        if (qz < z0 || qz > z1) continue;
+#pragma unroll
+        for (int i = 4 * qz; i < 4 * qz + 4; ++i) {
+          const double2 Z = F[2][gi][i];
+          acc[i] = fma(xr, Z.x, fma(-xi, Z.y, acc[i]));
+        }
       }
     }
     __syncthreads();
@@ -678,7 +700,7 @@ __global__ void __launch_bounds__(NT) k_gather2_tile_add(GridDev gd, const ShotD
           }
         } else {
           double xi0 = ax.o + (double)(a_ax + part * 8) * ax.h;
-          axis_factors8(xi0, ax.h, Q, P, cut, inv_eps, cf, dst);
+          axis_factors<8>(xi0, ax.h, Q, P, cut, inv_eps, cf, dst);
         }
         if (part == 0) {
           if (ax.periodic) {
