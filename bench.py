@@ -312,7 +312,10 @@ def run_ours(args, rank, world, local_rank):
             "frac": achieved / FP64_PEAK_TFLOPS,
             "traffic": ncu_traffic(),
             "flops_per_launch": ray_flops,
-            "peak_source": "FP64 from unit counts and clock (152 SM x 2 DFMA/clk x 2.07 GHz)",
+            "peak_source": ("FP64 from unit counts and clock (152 SM x 2 DFMA/clk x 2.07 GHz); "
+                            "the same figure measured by fga_fma_peak, 1.2553 and 1.2572 "
+                            "TFLOP/s (profiles/fma_peak_microbenchmark.md), and again in "
+                            "this run (peak_measured)"),
             "peak_measured": {"fp64_tflops": fp64_meas, "fp32_tflops": fp32_meas,
                               "frac_of_measured_fp64": achieved / fp64_meas,
                               "by": "fga_fma_peak (csrc/fga_peaks.cu): 8 FMA chains per "
