@@ -250,19 +250,25 @@ __global__ void k_ray_estimate(GridDev gd, const ShotDev* __restrict__ shots, co
   }
 }
 
-// Scatter of the Gaussians into the buckets' ranges (offsets fill[b] after the scan), in
-// the spread order work_order(w) within a bucket, so that rays running at the same time
-// still come from all over the list.
+// Scatter of the Gaussians into the buckets' ranges (offsets fill[b] after the scan).
+// With spread set (traces recorded), in the spread order work_order(w) within a bucket,
+// so that rays running at the same time still come from all over the list and add into
+// different trace entries. Without traces, in index order within a bucket: neighbouring
+// Gaussians (one q, adjacent p) then run at the same time and end at about the same
+// step, so the 8-byte state stores of the four rays that share a 32-byte sector of each
+// state row meet in L2 and leave it as whole sectors instead of partial ones that are
+// read back to be filled.
 __global__ void k_ray_order(int64_t G, const int64_t* __restrict__ gm, unsigned long long mult,
-                            const int32_t* __restrict__ est, int64_t nsteps, int64_t width,
-                            unsigned long long* __restrict__ fill, int32_t* __restrict__ order) {
+                            int spread, const int32_t* __restrict__ est, int64_t nsteps,
+                            int64_t width, unsigned long long* __restrict__ fill,
+                            int32_t* __restrict__ order) {
   if (gm) {
     G = gm[0];
     mult = (unsigned long long)gm[1];
   }
   for (int64_t w = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; w < G;
        w += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t g = work_order((unsigned long long)w, G, mult);
+    const int64_t g = spread ? work_order((unsigned long long)w, G, mult) : w;
     const int64_t b = (nsteps - est[g]) / width;
     order[atomicAdd(fill + b, 1ull)] = (int32_t)g;
   }
@@ -449,7 +455,8 @@ cudaError_t launch_rays_steps(fga_plan_s* p, int64_t nsteps, bool record) {
                                                   width, cnt);
     e = launch_scan(p, p->d_ray_bucket, nb);
     if (e != cudaSuccess) return e;
-    k_ray_order<<<gb, 256, 0, p->stream>>>(p->G, gm, mult, p->d_gsteps, nsteps, width, cnt, p->d_adj_order);
+    k_ray_order<<<gb, 256, 0, p->stream>>>(p->G, gm, mult, rx.every > 0 ? 1 : 0, p->d_gsteps, nsteps,
+                                           width, cnt, p->d_adj_order);
     p->launches += 2;
     order = p->d_adj_order;
   }
