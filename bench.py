@@ -292,7 +292,8 @@ def run_ours(args, rank, world, local_rank):
             "precision": ("fp64" if precision == F.FGA_FP64 else
                           "mixed: FBI stage 2 and the reconstruction on tensor cores "
                           "(TF32 head/tail operands, 3 products, FP32 accumulate; FP64 phase "
-                          "anchors and segment sums); FBI stage 1, selection and rays FP64"),
+                          "anchors and segment sums); FBI stage 1 in FP32 on the CUDA cores, "
+                          "psi stored as FP32 pairs; selection and rays FP64"),
             "fp64_path_value": fp64_value,
             "tuning": {"ray_blocks_per_sm": tuning[0], "gather_segment": tuning[1],
                        "ray_register_variant": tuning[2],

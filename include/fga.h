@@ -60,9 +60,12 @@ typedef enum {
   FGA_MIXED_TF32X3 = 1, /* the two contractions on the tensor cores, operands split into a
                            TF32 head and tail, hi*hi + hi*lo + lo*hi accumulated in FP32:
                            stage 2 of the FBI (the branch split in FP32 on its
-                           accumulators) and the reconstruction (phase anchored in FP64).
-                           Stage 1 of the FBI, the selection, the rays and the final sum
-                           over segments stay FP64. 2D grids with open axes only. */
+                           accumulators; psi kept as FP32 pairs) and the reconstruction
+                           (phase anchored in FP64). Stage 1 of the FBI runs in FP32 on
+                           the CUDA cores (its output is stage 2's split operand); the
+                           selection (on the exactly widened values), the rays and the
+                           final sum over segments stay FP64. 2D grids with open axes
+                           only. */
   FGA_MIXED_BF16X3 = 2  /* reserved (rejected by fga_plan) */
 } fga_precision;
 
